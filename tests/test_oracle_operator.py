@@ -1,0 +1,85 @@
+"""Pins for the oracle's operator K and direct solve (CPU only)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import direct as D
+from oracle import geometry as G
+from oracle import operator as O
+from oracle import transforms as T
+
+
+@pytest.mark.parametrize("domain", ["cross", "T", "L"])
+@pytest.mark.parametrize("kappa", [0.0, -10.0])
+def test_K_symmetric_negative_definite(domain, kappa):
+    """R_ij = R_ji^T (Sec. 2.3) makes K symmetric; with kappa <= 0 the 5-point
+    operator is negative definite (so every A_i is invertible)."""
+    K = O.assemble(domain, 6, kappa)
+    assert abs(K - K.T).max() == 0.0
+    ev = np.linalg.eigvalsh(K.toarray())
+    assert ev.max() < 0.0
+
+
+@pytest.mark.parametrize("nx,ny", [(5, 5), (7, 4), (4, 9)])
+def test_centre_block_is_the_rectangle_operator(nx, ny):
+    """The C block read off K equals the Kronecker form of Eq. "mat_Poisson"."""
+    n = 8
+    K = O.assemble("cross", n, -3.0)
+    A = O.rectangle(n, n, 1.0 / (n + 1), -3.0)
+    assert abs(K[: n * n, : n * n] - A).max() < 1e-9
+    # and the rectangle operator of any shape has the textbook eigenpairs
+    h = 0.1
+    R = O.rectangle(nx, ny, h, -2.5)
+    for k, l in [(1, 1), (nx, 1), (2, ny), (nx, ny)]:
+        v = T.rectangle_mode(k, l, nx, ny)
+        lam = T.rectangle_eigenvalue(k, l, nx, ny, h, -2.5)
+        assert np.allclose(R @ v, lam * v, rtol=1e-12, atol=1e-9)
+
+
+def test_five_point_stencil_is_exact_on_quadratics():
+    """Away from the edge, (K q)_I = lap q + kappa q for any quadratic q
+    (the central second difference is exact on quadratics)."""
+    n = 10
+    m = n + 1
+    K = O.assemble("cross", n, -1.5)
+    pts = G.block_order_points("cross", n)
+    inside = set(pts)
+    q = lambda x, y: 0.3 + 1.1 * x - 0.7 * y + 2.0 * x * x - 0.5 * x * y + 1.5 * y * y
+    lap = 2.0 * 2.0 + 2.0 * 1.5
+    vals = np.array([q(I / m, J / m) for I, J in pts])
+    Kq = K @ vals
+    for k, (I, J) in enumerate(pts):
+        if all(nb in inside for nb in ((I + 1, J), (I - 1, J), (I, J + 1), (I, J - 1))):
+            assert abs(Kq[k] - (lap - 1.5 * vals[k])) < 1e-8
+
+
+def test_second_order_convergence_manufactured():
+    """The discrete solution converges at O(h^2) to the manufactured p (the
+    paper's accuracy claim, Sec. 3.1): the max error falls ~4x per halving of h."""
+    errs = []
+    for n in (15, 31, 63):
+        K = O.assemble("cross", n, 0.0)
+        p = D.solve(K, W.manufactured_rhs("cross", n, 0.0))
+        errs.append(np.abs(p - W.manufactured_solution("cross", n)).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.6 < r1 < 4.4 and 3.8 < r2 < 4.2, errs
+
+
+def test_direct_dense_and_sparse_agree():
+    n = 20
+    K = O.assemble("cross", n, -10.0)
+    b = W.fourier_rhs("cross", n, 1)
+    x_sparse = D.Factor(K).solve(b)
+    x_dense = np.linalg.solve(K.toarray(), b)
+    assert np.abs(x_sparse - x_dense).max() < 1e-12 * np.abs(x_dense).max()
+    assert O.global_residual(K, b, x_sparse) < 1e-14
+
+
+def test_brute_force_tiny_inverse():
+    """On a tiny cross the solve equals the explicit inverse applied to b."""
+    n = 3
+    K = O.assemble("cross", n, -10.0).toarray()
+    b = W.fourier_rhs("cross", n, 2)
+    x = D.solve(sp.csr_matrix(K), b)
+    assert np.allclose(np.linalg.inv(K) @ b, x, rtol=1e-12, atol=1e-14)

@@ -1,0 +1,165 @@
+"""Seeded synthetic inputs for the block-domain Helmholtz-Poisson solver.
+
+This module is the one piece shared by the CPU oracle and the CUDA path: it
+turns (geometry, n, kappa, seed) into right-hand-side vectors f in the library's
+block-order layout. It contains none of the solver's arithmetic (no operator, no
+transform, no Krylov step) -- only the definition of the synthetic workloads.
+
+Layout (the library's I/O convention, the same one `include/fpg.h` documents):
+  * One instance has one grid size n; the spacing is h = 1/(n+1).
+  * Blocks are stored one after another: the centre C, then the arms present in
+    the geometry in the order W, E, S, N.
+      cross = C, W, E, S, N    T = C, W, E, S    L = C, E, N
+  * C = [0,1]^2 holds the n x n nodes (i h, j h), i, j = 1..n.
+  * Each arm owns the grid line it shares with C, so W and E hold (n+1) x n
+    nodes (n+1 along x) and S and N hold n x (n+1) nodes (n+1 along y):
+      W: x = -1 + i h, i = 1..n+1        E: x = 1 + (i-1) h, i = 1..n+1
+      S: y = -1 + j h, j = 1..n+1        N: y = 1 + (j-1) h, j = 1..n+1
+  * Inside a block the values are row-major with x fastest.
+
+Workloads (synthetic; the paper uses no external data, Sec. 3):
+  * "manufactured": p = sin(pi x) sin(pi y) exp(0.3 x), which vanishes on every
+    edge of the L, T and cross domains (all edges lie on integer coordinates), so
+    the Dirichlet data is zero and f = lap(p) + kappa p in closed form.
+  * "fourier": per block, 16 modes sin(kx pi xi) sin(ky pi eta) / (kx^2 + ky^2)
+    with N(0,1) coefficients and (kx, ky) uniform on {1..8}^2, in block-local
+    coordinates (xi, eta) in [0,1]^2; generator numpy PCG64 seeded with
+    seed*1000 + block_id.  Zero on every block edge.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GEOMETRY_BLOCKS = {
+    "cross": ("C", "W", "E", "S", "N"),
+    "T": ("C", "W", "E", "S"),
+    "L": ("C", "E", "N"),
+}
+GEOMETRY_CODE = {"L": 0, "T": 1, "cross": 2}
+BLOCK_ID = {"C": 0, "W": 1, "E": 2, "S": 3, "N": 4}
+# Box [x0, x1] x [y0, y1] of each block, in units of the centre block's side.
+BLOCK_BOX = {
+    "C": (0.0, 1.0, 0.0, 1.0),
+    "W": (-1.0, 0.0, 0.0, 1.0),
+    "E": (1.0, 2.0, 0.0, 1.0),
+    "S": (0.0, 1.0, -1.0, 0.0),
+    "N": (0.0, 1.0, 1.0, 2.0),
+}
+
+
+def block_shape(name: str, n: int) -> tuple[int, int]:
+    """(nx, ny) of a block: C is n x n, W/E are (n+1) x n, S/N are n x (n+1)."""
+    if name == "C":
+        return n, n
+    if name in ("W", "E"):
+        return n + 1, n
+    return n, n + 1
+
+
+def block_first_node(name: str, n: int) -> tuple[int, int]:
+    """Integer grid coordinates (I, J) of the block's node with i = j = 1;
+    the physical position is (I h, J h) with h = 1/(n+1)."""
+    m = n + 1
+    return {
+        "C": (1, 1),
+        "W": (-m + 1, 1),
+        "E": (m, 1),
+        "S": (1, -m + 1),
+        "N": (1, m),
+    }[name]
+
+
+def block_coords(name: str, n: int) -> tuple[np.ndarray, np.ndarray]:
+    """Physical x, y of every node of a block, shaped (ny, nx) (x fastest)."""
+    nx, ny = block_shape(name, n)
+    i0, j0 = block_first_node(name, n)
+    h = 1.0 / (n + 1)
+    xs = (i0 + np.arange(nx)) * h
+    ys = (j0 + np.arange(ny)) * h
+    return np.meshgrid(xs, ys, indexing="xy")
+
+
+def total_unknowns(geometry: str, n: int) -> int:
+    return sum(int(np.prod(block_shape(b, n))) for b in GEOMETRY_BLOCKS[geometry])
+
+
+def manufactured_solution(geometry: str, n: int) -> np.ndarray:
+    """p = sin(pi x) sin(pi y) exp(0.3 x) at every unknown, in block order."""
+    parts = []
+    for b in GEOMETRY_BLOCKS[geometry]:
+        x, y = block_coords(b, n)
+        parts.append((np.sin(math.pi * x) * np.sin(math.pi * y) * np.exp(0.3 * x)).ravel())
+    return np.concatenate(parts)
+
+
+def manufactured_rhs(geometry: str, n: int, kappa: float = 0.0) -> np.ndarray:
+    """f = lap(p) + kappa p for the manufactured p, in block order."""
+    parts = []
+    pi = math.pi
+    for b in GEOMETRY_BLOCKS[geometry]:
+        x, y = block_coords(b, n)
+        e = np.exp(0.3 * x)
+        lap = e * np.sin(pi * y) * ((0.09 - 2.0 * pi * pi) * np.sin(pi * x) + 0.6 * pi * np.cos(pi * x))
+        p = np.sin(pi * x) * np.sin(pi * y) * e
+        parts.append((lap + kappa * p).ravel())
+    return np.concatenate(parts)
+
+
+def fourier_rhs(geometry: str, n: int, seed: int, modes: int = 16, kmax: int = 8) -> np.ndarray:
+    """Random smooth right-hand side (see module docstring), in block order."""
+    parts = []
+    for b in GEOMETRY_BLOCKS[geometry]:
+        rng = np.random.default_rng(seed * 1000 + BLOCK_ID[b])
+        kx = rng.integers(1, kmax + 1, size=modes)
+        ky = rng.integers(1, kmax + 1, size=modes)
+        c = rng.standard_normal(modes)
+        x, y = block_coords(b, n)
+        x0, x1, y0, y1 = BLOCK_BOX[b]
+        xi = (x - x0) / (x1 - x0)
+        eta = (y - y0) / (y1 - y0)
+        f = np.zeros_like(x)
+        for q in range(modes):
+            f += c[q] * np.sin(kx[q] * math.pi * xi) * np.sin(ky[q] * math.pi * eta) / (kx[q] ** 2 + ky[q] ** 2)
+        parts.append(f.ravel())
+    return np.concatenate(parts)
+
+
+def rhs_batch(geometry: str, n: int, seeds, kind: str = "fourier", kappa: float = 0.0) -> np.ndarray:
+    """Stack of right-hand sides, shape (len(seeds), total_unknowns)."""
+    rows = []
+    for s in seeds:
+        if kind == "fourier":
+            rows.append(fourier_rhs(geometry, n, int(s)))
+        elif kind == "manufactured":
+            rows.append(manufactured_rhs(geometry, n, kappa))
+        else:
+            raise ValueError(f"unknown workload kind {kind!r}")
+    return np.ascontiguousarray(np.stack(rows))
+
+
+def random_block_vectors(nvec: int, size: int, seed: int) -> np.ndarray:
+    """Plain N(0,1) test vectors (operator-level parity inputs), shape (nvec, size)."""
+    return np.random.default_rng(seed).standard_normal((nvec, size))
+
+
+def serving_requests(count: int, rate_per_s: float, seed: int = 0,
+                     sizes=(64, 128, 256, 512, 1024), max_rhs: int = 8):
+    """Poisson-arrival request stream: list of dicts with arrival time (s),
+    geometry, n, number of RHS, kappa and a per-request seed."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=count))
+    geoms = ("L", "T", "cross")
+    reqs = []
+    for i in range(count):
+        reqs.append({
+            "id": i,
+            "arrival_s": float(t[i]),
+            "geometry": geoms[int(rng.integers(0, 3))],
+            "n": int(sizes[int(rng.integers(0, len(sizes)))]),
+            "nrhs": int(rng.integers(1, max_rhs + 1)),
+            "kappa": (0.0, -10.0)[int(rng.integers(0, 2))],
+            "seed": int(rng.integers(0, 2**31 - 1)),
+        })
+    return reqs
