@@ -1,0 +1,195 @@
+/*
+ * fpg.h -- C ABI of the GB300 FFT-preconditioned Schur-complement GMRES solver
+ * for the discrete 5-point Helmholtz-Poisson equation on block domains.
+ *
+ * Problem (Eq. 1 with the central differences of Eq. "Poisson_central"):
+ *     (p[i+1,j] + p[i-1,j] + p[i,j+1] + p[i,j-1] - 4 p[i,j]) / h^2 + kappa p[i,j] = f[i,j]
+ * on the L, T or cross domain built from unit squares (Sec. 2.3, Sec. 3), one
+ * grid size n per domain, h = 1/(n+1), zero Dirichlet data on the outer edge.
+ *
+ * Method (Sec. 2.3-2.4, Alg. "fft_dd_solver"): the arms are "independent"
+ * blocks and the centre C is the one "coupled" block.  The arms are eliminated
+ * exactly (Eq. "Schur_subeq"), the Schur system L_c p_c = f'_c of the centre is
+ * solved by GMRES with the paper's preconditioner A_c^{-1} applied on the right
+ * (flexible GMRES), each application being one fast solve (DST-I along x,
+ * Thomas along y per mode, inverse DST-I; Eqs. "eigen_trans"-"trans_subeq"), and
+ * the arms are recovered by back substitution.
+ *
+ * Vector layout (all FP64 unless stated; "block order"):
+ *   the centre C (n x n nodes (i h, j h), i,j = 1..n), then the arms present in
+ *   the order W, E, S, N (cross = C,W,E,S,N; T = C,W,E,S; L = C,E,N).  Each arm
+ *   owns the grid line it shares with C: W and E hold (n+1) x n nodes, S and N
+ *   hold n x (n+1).  Inside a block: row-major, x fastest.  Several right-hand
+ *   sides are stored one full vector after another.
+ *
+ * Memory: the library never allocates device memory on the solve path.  The
+ * caller passes one device workspace (size from fpg_workspace_bytes) at
+ * creation and owns it; the handle itself is host memory owned by the library.
+ * All device work is ordered on the stream given at creation; functions that
+ * return host results synchronise that stream.
+ *
+ * Errors: every call returns an fpg_status; no C++ exception crosses the ABI.
+ * Device waits are bounded: a wait that gives up sets FPG_ETIMEOUT.
+ */
+#ifndef FPG_H
+#define FPG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FPG_OK = 0,
+  FPG_EINVAL = 1,       /* bad argument or descriptor */
+  FPG_ENOMEM = 2,       /* workspace smaller than fpg_workspace_bytes() */
+  FPG_ECUDA = 3,        /* a CUDA call failed; see fpg_last_cuda_error() */
+  FPG_ENOCONV = 4,      /* max_iters reached: p holds the last iterate */
+  FPG_ETIMEOUT = 5,     /* a bounded device wait gave up */
+  FPG_EUNSUPPORTED = 6, /* valid request this build does not provide */
+  FPG_EBUDGET = 7       /* admission refused: over the memory budget */
+} fpg_status;
+
+typedef enum { FPG_GEOM_L = 0, FPG_GEOM_T = 1, FPG_GEOM_CROSS = 2 } fpg_geometry;
+
+typedef enum {
+  FPG_SCHUR_REDUCED = 0, /* arm response by its exact interface table (DST, x g_k, DST) */
+  FPG_SCHUR_LITERAL = 1  /* arm response by a full fast solve of every arm (Eq. "precond_basis_equ") */
+} fpg_schur_mode;
+
+typedef struct {
+  int32_t geometry;          /* fpg_geometry */
+  int32_t n;                 /* interior points per side of the centre block, 2 <= n <= 4096 */
+  double kappa;              /* Helmholtz shift, kappa <= 0 */
+  int32_t nrhs;              /* right-hand sides solved together, >= 1 */
+  int32_t restart;           /* GMRES restart length m, 1..128 */
+  double rtol;               /* stop when ||f - K p||_2 <= rtol ||f||_2 (global vectors) */
+  int32_t max_iters;         /* cap on total GMRES steps per right-hand side */
+  int32_t precond_precision; /* 64: FP64 fast solve; 32: FP32 fast solve (FP64 outer loop) */
+  int32_t schur_mode;        /* fpg_schur_mode */
+  int32_t reserved;          /* must be 0 */
+} fpg_domain_desc;
+
+typedef struct {
+  int32_t iterations;   /* GMRES steps taken */
+  int32_t restarts;     /* restart cycles run */
+  int32_t status;       /* fpg_status of this right-hand side */
+  int32_t reserved;
+  double residual;      /* final ||f - K p||_2 / ||f||_2, computed on the device */
+  double schur_residual;/* final GMRES estimate |g_{j+1}| / ||f||_2 */
+} fpg_solve_info;
+
+typedef struct fpg_domain fpg_domain;
+
+/* Human-readable name of a status code (static storage). */
+const char* fpg_status_string(fpg_status s);
+/* Text of the last CUDA error this thread saw (static storage). */
+const char* fpg_last_cuda_error(void);
+/* Library version string. */
+const char* fpg_version(void);
+
+/* Number of unknowns of one right-hand side: n^2 + arms * n (n+1). */
+fpg_status fpg_unknowns(const fpg_domain_desc* desc, int64_t* count);
+
+/* Device workspace needed by fpg_create_domain for this descriptor (bytes).
+ * Pure host computation; allocates nothing. */
+fpg_status fpg_workspace_bytes(const fpg_domain_desc* desc, size_t* bytes);
+
+/* Build a domain: host tables (eigenvalues, Thomas pivots, DST twiddles,
+ * interface table g_k) computed in FP64 and copied into the caller's
+ * workspace on `stream` (a cudaStream_t, NULL = legacy default stream).
+ * dev_workspace must stay valid until fpg_destroy_domain.
+ * Errors: FPG_EINVAL (descriptor), FPG_ENOMEM (bytes too small), FPG_ECUDA. */
+fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* dev_workspace, size_t bytes,
+                             void* stream, fpg_domain** out);
+
+/* Copy right-hand side(s) into the domain (stream-ordered device-to-device copy).
+ * f_dev: device pointer, block order; rhs_index = -1 copies all nrhs vectors
+ * (nrhs * unknowns doubles), otherwise one vector into slot rhs_index.
+ * The caller may reuse f_dev once the stream has passed this point. */
+fpg_status fpg_set_rhs(fpg_domain* d, const double* f_dev, int32_t rhs_index);
+
+/* Same as fpg_set_rhs from HOST memory (pinned for best speed): one
+ * host-to-device copy on the domain's stream. */
+fpg_status fpg_set_rhs_host(fpg_domain* d, const double* f_host, int32_t rhs_index);
+
+/* Solve K p = f for every right-hand side (Alg. "fft_dd_solver").
+ * p_dev: caller-owned device buffer of nrhs * unknowns doubles (block order).
+ * info_host: nrhs entries (may be NULL).  Synchronises the stream.
+ * Returns FPG_OK when every right-hand side met rtol, FPG_ENOCONV when some did
+ * not (their p holds the last iterate), FPG_ETIMEOUT or FPG_ECUDA. */
+fpg_status fpg_solve(fpg_domain* d, double* p_dev, fpg_solve_info* info_host);
+
+/* Launch the solve without waiting (graph-friendly form of fpg_solve): the
+ * result and the per-RHS info land on the stream; call fpg_solve_finish to
+ * wait and read the info.  Restart decisions are taken on the device. */
+fpg_status fpg_solve_async(fpg_domain* d, double* p_dev);
+fpg_status fpg_solve_finish(fpg_domain* d, fpg_solve_info* info_host);
+
+/* End-to-end convenience: host f -> device -> solve -> host p (both pinned for
+ * best speed), all on the domain's stream. */
+fpg_status fpg_solve_host(fpg_domain* d, const double* f_host, double* p_host,
+                          fpg_solve_info* info_host);
+
+void fpg_destroy_domain(fpg_domain* d);
+
+/* ---- operator entry points: each hot-path step on its own ------------------ */
+
+/* a1: preconditioner apply z = A_c^{-1} v for nvec centre-block vectors
+ * (n*n doubles each).  z is FP64 for precond_precision 64, FP32 for 32.
+ * One fast solve per vector (DST-I along x, Thomas along y, inverse DST-I;
+ * Eqs. "eigen_trans"-"trans_subeq"). */
+fpg_status fpg_apply_precond(fpg_domain* d, const double* v_dev, void* z_dev, int32_t nvec);
+
+/* Fast solve on one kind of block for nvec vectors: block 0 = centre C,
+ * 1..4 = arm W, E, S, N (the arm must exist in the geometry).  FP64 in/out. */
+fpg_status fpg_block_solve(fpg_domain* d, int32_t block, const double* v_dev, double* z_dev,
+                           int32_t nvec);
+
+/* a2: Schur matvec w = L_c z = A_c z - sum_a R_ca A_a^{-1} R_ac z (Eq.
+ * "Schur_subeq") for nvec centre vectors.  z_prec = 64 (double) or 32 (float). */
+fpg_status fpg_apply_schur(fpg_domain* d, const void* z_dev, int32_t z_prec, double* w_dev,
+                           int32_t nvec);
+
+/* a3: one Arnoldi step by modified Gram-Schmidt for nvec independent systems.
+ * V_dev: (j+1) basis vectors per system, layout [j+1][nvec][len]; w_dev: [nvec][len],
+ * overwritten by v_{j+1}; h_dev: [nvec][j+2] doubles receives h_{0..j} and h_{j+1,j}. */
+fpg_status fpg_arnoldi_mgs(fpg_domain* d, const double* V_dev, int32_t j, double* w_dev,
+                           double* h_dev, int64_t len, int32_t nvec);
+
+/* a4: Givens step on column j of Hbar for nvec systems (device arrays):
+ * Hcol [nvec][j+2] (in/out), cs, sn [nvec][m], g [nvec][m+1] (in/out).
+ * res_dev [nvec] receives |g_{j+1}|. */
+fpg_status fpg_givens(fpg_domain* d, double* Hcol_dev, double* cs_dev, double* sn_dev,
+                      double* g_dev, double* res_dev, int32_t j, int32_t m, int32_t nvec);
+
+/* a7: global relative residual ||f - K p||_2 / ||f||_2 for nvec full vectors;
+ * out_host receives nvec doubles.  Synchronises. */
+fpg_status fpg_global_residual(fpg_domain* d, const double* f_dev, const double* p_dev,
+                               double* out_host, int32_t nvec);
+
+/* Global operator y = K p for nvec full vectors (block order). */
+fpg_status fpg_apply_global(fpg_domain* d, const double* p_dev, double* y_dev, int32_t nvec);
+
+/* ---- measurement ----------------------------------------------------------- */
+
+/* Kernel-level timing of the last fpg_solve on this domain: launches issued and
+ * the device time (ms, CUDA events on the domain stream) of each phase.
+ * phase: 0 = preconditioner (a1), 1 = Schur matvec (a2), 2 = Arnoldi (a3),
+ * 3 = Givens (a4), 4 = cycle end (a5), 5 = setup/finish (a6), 6 = residual (a7).
+ * Timing is only collected when enabled with fpg_set_profiling(d, 1). */
+fpg_status fpg_set_profiling(fpg_domain* d, int32_t on);
+fpg_status fpg_phase_stats(fpg_domain* d, int32_t phase, int64_t* launches, double* ms);
+/* Total kernel launches issued by the library on this domain so far. */
+fpg_status fpg_launch_count(fpg_domain* d, int64_t* launches);
+
+/* FMA throughput of this GPU measured by a short library kernel (FLOP/s,
+ * 2 per FMA): precision 64 or 32.  Used as the ALU roofline. */
+fpg_status fpg_probe_fma_peak(int32_t precision, double* flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPG_H */

@@ -29,7 +29,9 @@ class Factor:
 
     def solve(self, b: np.ndarray) -> np.ndarray:
         if self._dense is not None:
-            return np.linalg.solve(self._dense, b)
+            if b.ndim == 1:
+                return np.linalg.solve(self._dense, b)
+            return np.linalg.solve(self._dense, b.T).T.copy()
         if b.ndim == 1:
             return self._lu.solve(b)
         return self._lu.solve(np.asfortranarray(b.T)).T.copy()

@@ -1,0 +1,242 @@
+"""Thin Python binding of the C ABI in include/fpg.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA library libfpg.so; this module only
+turns torch tensors (device memory, streams) into the plain pointers and sizes
+the C functions take.  If the library is missing the import fails loudly: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfpg.so")
+
+GEOMETRY = {"L": 0, "T": 1, "cross": 2}
+SCHUR = {"reduced": 0, "literal": 1}
+STATUS = {0: "FPG_OK", 1: "FPG_EINVAL", 2: "FPG_ENOMEM", 3: "FPG_ECUDA", 4: "FPG_ENOCONV",
+          5: "FPG_ETIMEOUT", 6: "FPG_EUNSUPPORTED", 7: "FPG_EBUDGET"}
+FPG_OK, FPG_EINVAL, FPG_ENOMEM, FPG_ECUDA, FPG_ENOCONV = 0, 1, 2, 3, 4
+PHASES = ("precond", "schur", "arnoldi", "givens", "cycle_end", "setup_finish", "residual")
+
+
+class DomainDesc(ctypes.Structure):
+    _fields_ = [("geometry", ctypes.c_int32), ("n", ctypes.c_int32), ("kappa", ctypes.c_double),
+                ("nrhs", ctypes.c_int32), ("restart", ctypes.c_int32), ("rtol", ctypes.c_double),
+                ("max_iters", ctypes.c_int32), ("precond_precision", ctypes.c_int32),
+                ("schur_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("residual", ctypes.c_double), ("schur_residual", ctypes.c_double)]
+
+
+class FpgError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        super().__init__(f"{where}: {STATUS.get(status, status)} {detail}".strip())
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_SIGS = {
+    "fpg_status_string": ([_I32], ctypes.c_char_p),
+    "fpg_last_cuda_error": ([], ctypes.c_char_p),
+    "fpg_version": ([], ctypes.c_char_p),
+    "fpg_unknowns": ([_P, ctypes.POINTER(_I64)], _I32),
+    "fpg_workspace_bytes": ([_P, ctypes.POINTER(ctypes.c_size_t)], _I32),
+    "fpg_create_domain": ([_P, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)], _I32),
+    "fpg_set_rhs": ([_P, _P, _I32], _I32),
+    "fpg_set_rhs_host": ([_P, _P, _I32], _I32),
+    "fpg_solve": ([_P, _P, _P], _I32),
+    "fpg_solve_async": ([_P, _P], _I32),
+    "fpg_solve_finish": ([_P, _P], _I32),
+    "fpg_solve_host": ([_P, _P, _P, _P], _I32),
+    "fpg_destroy_domain": ([_P], None),
+    "fpg_apply_precond": ([_P, _P, _P, _I32], _I32),
+    "fpg_block_solve": ([_P, _I32, _P, _P, _I32], _I32),
+    "fpg_apply_schur": ([_P, _P, _I32, _P, _I32], _I32),
+    "fpg_arnoldi_mgs": ([_P, _P, _I32, _P, _P, _I64, _I32], _I32),
+    "fpg_givens": ([_P, _P, _P, _P, _P, _P, _I32, _I32, _I32], _I32),
+    "fpg_global_residual": ([_P, _P, _P, _P, _I32], _I32),
+    "fpg_apply_global": ([_P, _P, _P, _I32], _I32),
+    "fpg_set_profiling": ([_P, _I32], _I32),
+    "fpg_phase_stats": ([_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D)], _I32),
+    "fpg_launch_count": ([_P, ctypes.POINTER(_I64)], _I32),
+    "fpg_probe_fma_peak": ([_I32, ctypes.POINTER(_D)], _I32),
+}
+EXPORTED = tuple(_SIGS)
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libfpg.so (built by paper_2509_23180_gb300.build) and declare its ABI."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2509_23180_gb300.build`")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str) -> int:
+    if status not in (FPG_OK,):
+        lib = load()
+        detail = lib.fpg_last_cuda_error().decode() if status == FPG_ECUDA else ""
+        raise FpgError(status, where, detail)
+    return status
+
+
+def make_desc(geometry="cross", n=64, kappa=0.0, nrhs=1, restart=30, rtol=1e-10, max_iters=None,
+              precond_precision=64, schur_mode="reduced") -> DomainDesc:
+    if max_iters is None:
+        max_iters = 50 * restart
+    return DomainDesc(GEOMETRY[geometry] if isinstance(geometry, str) else int(geometry), int(n), float(kappa),
+                      int(nrhs), int(restart), float(rtol), int(max_iters), int(precond_precision),
+                      SCHUR[schur_mode] if isinstance(schur_mode, str) else int(schur_mode), 0)
+
+
+def unknowns(desc: DomainDesc) -> int:
+    out = _I64()
+    _check(load().fpg_unknowns(ctypes.byref(desc), ctypes.byref(out)), "fpg_unknowns")
+    return int(out.value)
+
+
+def workspace_bytes(desc: DomainDesc) -> int:
+    out = ctypes.c_size_t()
+    _check(load().fpg_workspace_bytes(ctypes.byref(desc), ctypes.byref(out)), "fpg_workspace_bytes")
+    return int(out.value)
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+class Domain:
+    """A domain handle with its caller-owned device workspace (a torch uint8 tensor)."""
+
+    def __init__(self, desc: DomainDesc, stream=None, device="cuda"):
+        import torch
+        self.lib = load()
+        self.desc = desc
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.nbytes = workspace_bytes(desc)
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        self.N = unknowns(desc)
+        self.nc = desc.n * desc.n
+        h = _P()
+        _check(self.lib.fpg_create_domain(ctypes.byref(desc), _ptr(self.workspace), self.nbytes,
+                                          self.stream.cuda_stream, ctypes.byref(h)), "fpg_create_domain")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.fpg_destroy_domain(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- solve -----------------------------------------------------------
+    def set_rhs(self, f, index: int = -1):
+        _check(self.lib.fpg_set_rhs(self.handle, _ptr(f), index), "fpg_set_rhs")
+
+    def set_rhs_host(self, f_host, index: int = -1):
+        _check(self.lib.fpg_set_rhs_host(self.handle, _ptr(f_host), index), "fpg_set_rhs_host")
+
+    def _infos(self):
+        return (SolveInfo * self.desc.nrhs)()
+
+    @staticmethod
+    def _info_list(arr):
+        return [{"iterations": i.iterations, "restarts": i.restarts, "status": i.status,
+                 "residual": i.residual, "schur_residual": i.schur_residual} for i in arr]
+
+    def solve(self, p, check: bool = True):
+        infos = self._infos()
+        st = self.lib.fpg_solve(self.handle, _ptr(p), infos)
+        if check and st != FPG_ENOCONV:
+            _check(st, "fpg_solve")
+        return st, self._info_list(infos)
+
+    def solve_async(self, p):
+        _check(self.lib.fpg_solve_async(self.handle, _ptr(p)), "fpg_solve_async")
+
+    def solve_finish(self):
+        infos = self._infos()
+        st = self.lib.fpg_solve_finish(self.handle, infos)
+        if st != FPG_ENOCONV:
+            _check(st, "fpg_solve_finish")
+        return st, self._info_list(infos)
+
+    def solve_host(self, f_host, p_host):
+        infos = self._infos()
+        st = self.lib.fpg_solve_host(self.handle, _ptr(f_host), _ptr(p_host), infos)
+        if st != FPG_ENOCONV:
+            _check(st, "fpg_solve_host")
+        return st, self._info_list(infos)
+
+    # -- operators ------------------------------------------------------
+    def apply_precond(self, v, z, nvec: int):
+        _check(self.lib.fpg_apply_precond(self.handle, _ptr(v), _ptr(z), nvec), "fpg_apply_precond")
+
+    def block_solve(self, block: int, v, z, nvec: int):
+        _check(self.lib.fpg_block_solve(self.handle, block, _ptr(v), _ptr(z), nvec), "fpg_block_solve")
+
+    def apply_schur(self, z, zprec: int, w, nvec: int):
+        _check(self.lib.fpg_apply_schur(self.handle, _ptr(z), zprec, _ptr(w), nvec), "fpg_apply_schur")
+
+    def arnoldi_mgs(self, V, j: int, w, h, length: int, nvec: int):
+        _check(self.lib.fpg_arnoldi_mgs(self.handle, _ptr(V), j, _ptr(w), _ptr(h), length, nvec),
+               "fpg_arnoldi_mgs")
+
+    def givens(self, Hcol, cs, sn, g, res, j: int, m: int, nvec: int):
+        _check(self.lib.fpg_givens(self.handle, _ptr(Hcol), _ptr(cs), _ptr(sn), _ptr(g), _ptr(res), j, m, nvec),
+               "fpg_givens")
+
+    def global_residual(self, f, p, nvec: int):
+        out = (ctypes.c_double * nvec)()
+        _check(self.lib.fpg_global_residual(self.handle, _ptr(f), _ptr(p), out, nvec), "fpg_global_residual")
+        return list(out)
+
+    def apply_global(self, p, y, nvec: int):
+        _check(self.lib.fpg_apply_global(self.handle, _ptr(p), _ptr(y), nvec), "fpg_apply_global")
+
+    # -- measurement -----------------------------------------------------
+    def set_profiling(self, on: bool):
+        _check(self.lib.fpg_set_profiling(self.handle, 1 if on else 0), "fpg_set_profiling")
+
+    def phase_stats(self):
+        out = {}
+        for i, name in enumerate(PHASES):
+            ln, ms = _I64(), _D()
+            _check(self.lib.fpg_phase_stats(self.handle, i, ctypes.byref(ln), ctypes.byref(ms)), "fpg_phase_stats")
+            out[name] = {"launches": int(ln.value), "ms": float(ms.value)}
+        return out
+
+    def launch_count(self) -> int:
+        out = _I64()
+        _check(self.lib.fpg_launch_count(self.handle, ctypes.byref(out)), "fpg_launch_count")
+        return int(out.value)
+
+
+def probe_fma_peak(precision: int = 64) -> float:
+    """FLOP/s of FMA on this GPU, measured by the library's own probe kernel."""
+    out = _D()
+    _check(load().fpg_probe_fma_peak(precision, ctypes.byref(out)), "fpg_probe_fma_peak")
+    return float(out.value)

@@ -1,0 +1,804 @@
+// C ABI of the solver (include/fpg.h): domain set-up, workspace carving, host
+// tables in FP64, the flexible-GMRES driver of Alg. "fft_dd_solver", and the
+// per-step operator entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fpg_internal.cuh"
+
+namespace fpg {
+
+cudaError_t launch_fast_solve(int prec, int out_prec, const FastSolveTables& tb, LineLayout L, const double* in,
+                              BatchDesc ib, void* out, BatchDesc ob, int nblk, void* scratch, const int* active,
+                              int nper_active, cudaStream_t st, int* launches);
+cudaError_t launch_schur_reduced(const void* z, int zprec, long long zstride, int n, const double* ctab,
+                                 const int* arms_dev, int narms, double* corr, const int* active, int nrhs,
+                                 cudaStream_t st);
+cudaError_t launch_stencil_c(const void* z, int zprec, long long zstride, double* w, long long wstride, int n,
+                             double delta, double kappa, const double* corr, int armmask, const int* active,
+                             int nrhs, int gx, cudaStream_t st);
+cudaError_t launch_literal_inject(const void* z, int zprec, long long zstride, int n, double delta,
+                                  double* armbuf, long long rhs_stride, ArmOffsets ao, const int* active,
+                                  int nrhs, int gx, cudaStream_t st);
+cudaError_t launch_literal_extract(const double* armsol, long long rhs_stride, ArmOffsets ao, int n,
+                                   double delta, double* corr, const int* active, int nrhs, cudaStream_t st);
+cudaError_t launch_mgs(const double* V, long long vstride, double* w, double* vout, long long len, int j,
+                       int nrhs, double* part, int gmax, double* H, int hcol_stride, int hrhs_stride,
+                       const int* active, int gx, cudaStream_t st, int* launches);
+cudaError_t launch_givens(double* H, int hcol_stride, int hrhs_stride, double* cs, double* sn, double* g,
+                          double* res, int j, int m, int nrhs, const double* tolabs, int* active, int* kcyc,
+                          int* iters, int max_iters, cudaStream_t st);
+cudaError_t launch_cycle_end(const double* H, int hcol_stride, int hrhs_stride, const double* g, double* y,
+                             int m, int nrhs, const int* kcyc, double* u, const void* Z, int zprec,
+                             long long zvstride, long long len, int gx, cudaStream_t st);
+cudaError_t launch_restart(const double* fc, const double* w, double* v0, long long len, int nrhs, double* part,
+                           int gmax, double* g, int m, const double* tolabs, double* rnorm, int* done,
+                           int* active, int* kcyc, const int* iters, int max_iters, int gx, cudaStream_t st);
+cudaError_t launch_reduce_rhs(const double* f, const double* q, long long ntot, int n, double delta,
+                              ArmOffsets ao, double* fc, int nrhs, int gx, cudaStream_t st);
+cudaError_t launch_arm_rhs(const double* f, const double* u, long long ntot, int n, double delta, ArmOffsets ao,
+                           double* out, double* p, int nrhs, int gx, cudaStream_t st);
+cudaError_t launch_global_apply(const double* p, double* y, const double* f, long long ntot, int n, double delta,
+                                double kappa, ArmOffsets ao, double* part, int gmax, int nrhs, int gx,
+                                double* rel_out, double* fnorm_out, double rtol, double* tolabs,
+                                cudaStream_t st);
+cudaError_t launch_fma_probe(int prec, int blocks, int iters, cudaStream_t st);
+
+static thread_local char g_last_err[256] = "no error";
+
+void record_cuda_error(cudaError_t e, const char* where) {
+  snprintf(g_last_err, sizeof(g_last_err), "%s: %s", cudaGetErrorString(e), where);
+}
+
+}  // namespace fpg
+
+using namespace fpg;
+
+namespace {
+
+constexpr int kGmax = 1024;
+constexpr int kPhases = 7;
+constexpr int kMaxEvents = 8192;
+
+// Bump allocator over the caller's workspace (256-byte aligned regions).  With
+// base == nullptr it only measures.
+struct Carver {
+  char* base;
+  size_t used = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  void* take(size_t bytes) {
+    used = (used + 255) & ~(size_t)255;
+    void* p = base ? base + used : nullptr;
+    used += bytes;
+    return p;
+  }
+};
+
+struct Layout {
+  int n, narms, armmask;
+  long long nc, na, ntot;
+  ArmOffsets ao;
+  int arm_slots[4];
+};
+
+bool make_layout(const fpg_domain_desc* d, Layout* L) {
+  const int n = d->n;
+  L->n = n;
+  L->nc = (long long)n * n;
+  L->na = (long long)n * (n + 1);
+  static const int slots_cross[] = {0, 1, 2, 3};
+  static const int slots_t[] = {0, 1, 2};
+  static const int slots_l[] = {1, 3};
+  const int* slots;
+  int cnt;
+  switch (d->geometry) {
+    case FPG_GEOM_CROSS: slots = slots_cross; cnt = 4; break;
+    case FPG_GEOM_T: slots = slots_t; cnt = 3; break;
+    case FPG_GEOM_L: slots = slots_l; cnt = 2; break;
+    default: return false;
+  }
+  L->narms = cnt;
+  L->armmask = 0;
+  for (int a = 0; a < 4; ++a) L->ao.off[a] = -1;
+  long long off = L->nc;
+  for (int i = 0; i < cnt; ++i) {
+    L->arm_slots[i] = slots[i];
+    L->ao.off[slots[i]] = off;
+    L->armmask |= 1 << slots[i];
+    off += L->na;
+  }
+  L->ntot = off;
+  return true;
+}
+
+fpg_status validate(const fpg_domain_desc* d) {
+  if (!d) return FPG_EINVAL;
+  if (d->geometry < 0 || d->geometry > 2) return FPG_EINVAL;
+  if (d->n < 2 || d->n > 4096) return FPG_EINVAL;
+  if (!(d->kappa <= 0.0) || !std::isfinite(d->kappa)) return FPG_EINVAL;
+  if (d->nrhs < 1 || d->nrhs > 4096) return FPG_EINVAL;
+  if (d->restart < 1 || d->restart > 128) return FPG_EINVAL;
+  if (!(d->rtol > 0.0) || !(d->rtol < 1.0)) return FPG_EINVAL;
+  if (d->max_iters < 1) return FPG_EINVAL;
+  if (d->precond_precision != 64 && d->precond_precision != 32) return FPG_EINVAL;
+  if (d->schur_mode != FPG_SCHUR_REDUCED && d->schur_mode != FPG_SCHUR_LITERAL) return FPG_EINVAL;
+  if (d->reserved != 0) return FPG_EINVAL;
+  return FPG_OK;
+}
+
+int pick_gx(long long len, int nrhs) {
+  long long want = (4LL * 152 + nrhs - 1) / nrhs;
+  long long cap = (len + 255) / 256;
+  long long g = std::min(want, cap);
+  g = std::max(1LL, std::min(g, (long long)kGmax));
+  return (int)g;
+}
+
+}  // namespace
+
+struct fpg_domain {
+  fpg_domain_desc desc;
+  Layout L;
+  cudaStream_t st;
+  double delta;
+  int prec;
+  LineLayout LC, LWE, LSN;
+  BatchDesc we, sn;  // arm groups inside full vectors
+  FastSolveTables tC64, tC32, tA64, tA32;
+  double* ctab;
+  int* arms_dev;
+  double *f, *tmp, *lit_in, *lit_out, *corr, *gres, *fnorm;
+  void* scratch;
+  KrylovState ks;
+  int gx, gxf;
+  // host mirrors
+  std::vector<int> h_done, h_iters, h_kcyc;
+  // measurement
+  bool profiling = false;
+  long long launches = 0;
+  double phase_ms[kPhases] = {0};
+  long long phase_launches[kPhases] = {0};
+  std::vector<cudaEvent_t> evpool;
+  std::vector<std::pair<int, int>> ev_used;  // (phase, event index of start)
+  int ev_next = 0;
+  int cycles_run = 0;
+};
+
+namespace {
+
+// Host tables in FP64 -------------------------------------------------------
+void fill_sintab(int n, std::vector<double>& s) {
+  const int p = n + 1;
+  s.resize(2 * p);
+  for (int m = 0; m < 2 * p; ++m) {
+    // sin(pi m / p) with the argument folded to [0, pi/2] by exact integer symmetry
+    int q = m % (2 * p);
+    double sign = 1.0;
+    if (q >= p) { q -= p; sign = -1.0; }          // sin(x + pi) = -sin x
+    if (2 * q > p) q = p - q;                     // sin(pi - x) = sin x
+    s[m] = sign * std::sin(M_PI * (double)q / (double)p);
+  }
+}
+
+double cos_pi_frac(long long num, long long den) {
+  // cos(pi num / den) with exact folding to [0, pi/2]
+  long long q = num % (2 * den);
+  if (q < 0) q += 2 * den;
+  if (q > den) q = 2 * den - q;                   // cos(2pi - x) = cos x
+  double sign = 1.0;
+  if (2 * q > den) { q = den - q; sign = -1.0; }  // cos(pi - x) = -cos x
+  return sign * std::cos(M_PI * (double)q / (double)den);
+}
+
+// Reciprocal Thomas pivots for tridiag(delta, d_k, delta) of length ns, all modes:
+// r[s][k-1], d_k = -4 delta + 2 delta cos(k pi/(n+1)) + kappa.
+void fill_pivots(int n, int ns, double delta, double kappa, std::vector<double>& r) {
+  r.resize((size_t)ns * n);
+  for (int k = 1; k <= n; ++k) {
+    const double d = -4.0 * delta + 2.0 * delta * cos_pi_frac(k, n + 1) + kappa;
+    double rp = 1.0 / d;
+    r[(size_t)k - 1] = rp;
+    for (int s = 1; s < ns; ++s) {
+      rp = 1.0 / (d - delta * delta * rp);
+      r[(size_t)s * n + k - 1] = rp;
+    }
+  }
+}
+
+// Interface table of the reduced Schur form: c(m) = delta^2/(n+1) sum_k g_k cos(pi k m/(n+1)),
+// m = 0..2n+1, with g_k = [T_k^{-1}]_{N,N} (N = n+1, the arm's sweep length) = last reciprocal pivot.
+void fill_ctab(int n, double delta, const std::vector<double>& rpivA, std::vector<double>& c) {
+  const int N = n + 1;
+  c.resize(2 * n + 2);
+  std::vector<double> g(n);
+  for (int k = 1; k <= n; ++k) g[k - 1] = rpivA[(size_t)(N - 1) * n + k - 1];
+  for (int m = 0; m < 2 * n + 2; ++m) {
+    long double acc = 0.0L;
+    for (int k = 1; k <= n; ++k) acc += (long double)g[k - 1] * (long double)cos_pi_frac((long long)k * m, n + 1);
+    c[m] = (double)(acc * (long double)delta * (long double)delta / (long double)(n + 1));
+  }
+}
+
+struct Regions {
+  size_t sintab64, sintab32, pivC64, pivC32, pivA64, pivA32, ctab, arms;
+};
+
+// Carves every region; with base == nullptr only sizes are computed.
+void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, Carver& c) {
+  const int n = d->n, nrhs = d->nrhs, m = d->restart;
+  const int p2 = 2 * (n + 1);
+  const size_t zel = d->precond_precision == 64 ? 8 : 4;
+  void* p;
+  p = c.take(sizeof(double) * p2);            if (D) D->tC64.sintab = p, D->tA64.sintab = p;
+  p = c.take(sizeof(float) * p2);             if (D) D->tC32.sintab = p, D->tA32.sintab = p;
+  p = c.take(sizeof(double) * L.nc);          if (D) D->tC64.rpiv = p;
+  p = c.take(sizeof(float) * L.nc);           if (D) D->tC32.rpiv = p;
+  p = c.take(sizeof(double) * L.na);          if (D) D->tA64.rpiv = p;
+  p = c.take(sizeof(float) * L.na);           if (D) D->tA32.rpiv = p;
+  p = c.take(sizeof(double) * (2 * n + 2));   if (D) D->ctab = (double*)p;
+  p = c.take(sizeof(int) * 4);                if (D) D->arms_dev = (int*)p;
+  p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->f = (double*)p;
+  p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->tmp = (double*)p;
+  if (d->schur_mode == FPG_SCHUR_LITERAL) {
+    p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->lit_in = (double*)p;
+    p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->lit_out = (double*)p;
+  } else if (D) {
+    D->lit_in = D->lit_out = nullptr;
+  }
+  p = c.take(sizeof(double) * nrhs * 4 * n); if (D) D->corr = (double*)p;
+  const long long sc = (long long)nrhs * std::max(L.nc, 2 * L.na);
+  p = c.take(sizeof(double) * sc);            if (D) D->scratch = p;
+  p = c.take(sizeof(double) * nrhs);          if (D) D->gres = (double*)p;
+  KrylovState* k = D ? &D->ks : nullptr;
+  p = c.take(sizeof(double) * (size_t)(m + 1) * nrhs * L.nc); if (k) k->V = (double*)p;
+  p = c.take(zel * (size_t)m * nrhs * L.nc);                  if (k) k->Z = p;
+  p = c.take(sizeof(double) * nrhs * L.nc);   if (k) k->w = (double*)p;
+  p = c.take(sizeof(double) * nrhs * L.nc);   if (k) k->u = (double*)p;
+  p = c.take(sizeof(double) * nrhs * L.nc);   if (k) k->fc = (double*)p;
+  p = c.take(sizeof(double) * (size_t)nrhs * m * (m + 1)); if (k) k->H = (double*)p;
+  p = c.take(sizeof(double) * nrhs * m);      if (k) k->cs = (double*)p;
+  p = c.take(sizeof(double) * nrhs * m);      if (k) k->sn = (double*)p;
+  p = c.take(sizeof(double) * nrhs * (m + 1)); if (k) k->g = (double*)p;
+  p = c.take(sizeof(double) * nrhs * m);      if (k) k->y = (double*)p;
+  p = c.take(sizeof(double) * 2 * nrhs * kGmax); if (k) k->part = (double*)p;
+  p = c.take(sizeof(double) * nrhs);          if (k) k->tolabs = (double*)p;
+  p = c.take(sizeof(double) * nrhs);          if (k) k->fnorm = (double*)p;
+  p = c.take(sizeof(double) * nrhs);          if (k) k->res = (double*)p;
+  p = c.take(sizeof(double) * nrhs);          if (k) k->rnorm = (double*)p;
+  p = c.take(sizeof(int) * nrhs);             if (k) k->active = (int*)p;
+  p = c.take(sizeof(int) * nrhs);             if (k) k->done = (int*)p;
+  p = c.take(sizeof(int) * nrhs);             if (k) k->kcyc = (int*)p;
+  p = c.take(sizeof(int) * nrhs);             if (k) k->iters = (int*)p;
+}
+
+// Phase timing helpers (only when profiling is on).
+int ev_begin(fpg_domain* D, int phase) {
+  if (!D->profiling || D->ev_next + 2 > (int)D->evpool.size()) return -1;
+  const int i = D->ev_next;
+  D->ev_next += 2;
+  cudaEventRecord(D->evpool[i], D->st);
+  D->ev_used.push_back({phase, i});
+  return i;
+}
+void ev_end(fpg_domain* D, int i) {
+  if (i >= 0) cudaEventRecord(D->evpool[i + 1], D->st);
+}
+void ev_collect(fpg_domain* D) {
+  if (!D->profiling) return;
+  cudaStreamSynchronize(D->st);
+  for (auto& pr : D->ev_used) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, D->evpool[pr.second], D->evpool[pr.second + 1]) == cudaSuccess)
+      D->phase_ms[pr.first] += ms;
+  }
+  D->ev_used.clear();
+  D->ev_next = 0;
+}
+
+inline void count(fpg_domain* D, int phase, int n) {
+  D->launches += n;
+  D->phase_launches[phase] += n;
+}
+
+// ---- building blocks used by the driver and the entry points ---------------
+
+// a1 on nvec centre vectors (nvec <= nrhs): v (FP64, stride nc) -> z (prec).
+fpg_status precond(fpg_domain* D, const double* v, void* z, int nvec, const int* active) {
+  const Layout& L = D->L;
+  BatchDesc ib{L.nc, {0, 0, 0, 0}, 1};
+  int nl = 0;
+  const FastSolveTables& tb = D->prec == 64 ? D->tC64 : D->tC32;
+  FPG_CUDA_TRY(launch_fast_solve(D->prec, D->prec, tb, D->LC, v, ib, z, ib, nvec, D->scratch, active, 1, D->st,
+                                 &nl));
+  count(D, 0, nl);
+  return FPG_OK;
+}
+
+// Fast solves on the arms of nvec full vectors (FP64): in -> out (arm blocks only).
+fpg_status arm_solves(fpg_domain* D, const double* in, double* out, int nvec, int phase) {
+  int nl = 0;
+  if (D->we.nper > 0)
+    FPG_CUDA_TRY(launch_fast_solve(64, 64, D->tA64, D->LWE, in, D->we, out, D->we, nvec * D->we.nper, D->scratch,
+                                   nullptr, 1, D->st, &nl));
+  if (D->sn.nper > 0)
+    FPG_CUDA_TRY(launch_fast_solve(64, 64, D->tA64, D->LSN, in, D->sn, out, D->sn, nvec * D->sn.nper, D->scratch,
+                                   nullptr, 1, D->st, &nl));
+  count(D, phase, nl);
+  return FPG_OK;
+}
+
+// a2 on nvec centre vectors (nvec <= nrhs): z (zprec) -> w.
+fpg_status schur(fpg_domain* D, const void* z, int zprec, double* w, int nvec, const int* active) {
+  const Layout& L = D->L;
+  if (D->desc.schur_mode == FPG_SCHUR_REDUCED) {
+    FPG_CUDA_TRY(launch_schur_reduced(z, zprec, L.nc, L.n, D->ctab, D->arms_dev, L.narms, D->corr, active, nvec,
+                                      D->st));
+    count(D, 1, 1);
+  } else {
+    FPG_CUDA_TRY(launch_literal_inject(z, zprec, L.nc, L.n, D->delta, D->lit_in, L.ntot, L.ao, active, nvec,
+                                       D->gxf, D->st));
+    count(D, 1, 1);
+    int nl = 0;
+    if (D->we.nper > 0)
+      FPG_CUDA_TRY(launch_fast_solve(64, 64, D->tA64, D->LWE, D->lit_in, D->we, D->lit_out, D->we,
+                                     nvec * D->we.nper, D->scratch, active, D->we.nper, D->st, &nl));
+    if (D->sn.nper > 0)
+      FPG_CUDA_TRY(launch_fast_solve(64, 64, D->tA64, D->LSN, D->lit_in, D->sn, D->lit_out, D->sn,
+                                     nvec * D->sn.nper, D->scratch, active, D->sn.nper, D->st, &nl));
+    count(D, 1, nl);
+    FPG_CUDA_TRY(launch_literal_extract(D->lit_out, L.ntot, L.ao, L.n, D->delta, D->corr, active, nvec, D->st));
+    count(D, 1, 1);
+  }
+  FPG_CUDA_TRY(launch_stencil_c(z, zprec, L.nc, w, L.nc, L.n, D->delta, D->desc.kappa, D->corr, L.armmask, active,
+                                nvec, D->gx, D->st));
+  count(D, 1, 1);
+  return FPG_OK;
+}
+
+fpg_status check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    record_cuda_error(e, "kernel launch");
+    return FPG_ECUDA;
+  }
+  return FPG_OK;
+}
+
+#define FPG_TRY(x)                   \
+  do {                               \
+    fpg_status _s = (x);             \
+    if (_s != FPG_OK) return _s;     \
+  } while (0)
+
+// Launch the whole solve on the stream (host loop over restart cycles; the only
+// host synchronisation is one read of the per-RHS "done" flags per cycle).
+fpg_status solve_launch(fpg_domain* D, double* p) {
+  const Layout& L = D->L;
+  KrylovState& k = D->ks;
+  const int nrhs = D->desc.nrhs, m = D->desc.restart;
+  const int hcol = m + 1, hrhs = m * (m + 1);
+  const int zprec = D->prec;
+  const size_t zel = zprec == 64 ? 8 : 4;
+  D->cycles_run = 0;
+
+  // ||f|| per RHS and the absolute tolerance
+  int e = ev_begin(D, 5);
+  FPG_CUDA_TRY(launch_global_apply(D->f, nullptr, D->f, L.ntot, L.n, D->delta, D->desc.kappa, L.ao, k.part, kGmax,
+                                   nrhs, D->gxf, nullptr, k.fnorm, D->desc.rtol, k.tolabs, D->st));
+  count(D, 5, 2);
+  // Alg. 1 steps 1-3: q_a = A_a^{-1} f_a (into p's arm blocks), f'_c = f_c - sum R_ca q_a
+  FPG_TRY(arm_solves(D, D->f, p, nrhs, 5));
+  FPG_CUDA_TRY(launch_reduce_rhs(D->f, p, L.ntot, L.n, D->delta, L.ao, k.fc, nrhs, D->gx, D->st));
+  count(D, 5, 1);
+  FPG_CUDA_TRY(cudaMemsetAsync(k.u, 0, sizeof(double) * nrhs * L.nc, D->st));
+  FPG_CUDA_TRY(cudaMemsetAsync(k.done, 0, sizeof(int) * nrhs, D->st));
+  FPG_CUDA_TRY(cudaMemsetAsync(k.iters, 0, sizeof(int) * nrhs, D->st));
+  FPG_CUDA_TRY(cudaMemsetAsync(k.w, 0, sizeof(double) * nrhs * L.nc, D->st));
+  ev_end(D, e);
+
+  const int max_cycles = (D->desc.max_iters + m - 1) / m + 2;
+  bool first = true;
+  for (int cyc = 0; cyc < max_cycles; ++cyc) {
+    // restart: w = L_c u (skipped while u = 0), r = f'_c - w -> V[0], beta, flags
+    e = ev_begin(D, 4);
+    if (!first) FPG_TRY(schur(D, k.u, 64, k.w, nrhs, nullptr));
+    FPG_CUDA_TRY(launch_restart(k.fc, k.w, k.V, L.nc, nrhs, k.part, kGmax, k.g, m, k.tolabs, k.rnorm, k.done,
+                                k.active, k.kcyc, k.iters, D->desc.max_iters, D->gx, D->st));
+    count(D, 4, 2);
+    ev_end(D, e);
+    first = false;
+    FPG_CUDA_TRY(cudaMemcpyAsync(D->h_done.data(), k.done, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, D->st));
+    FPG_CUDA_TRY(cudaStreamSynchronize(D->st));
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r) all = all && D->h_done[r];
+    if (all) break;
+    D->cycles_run++;
+    for (int j = 0; j < m; ++j) {
+      double* vj = k.V + (size_t)j * nrhs * L.nc;
+      void* zj = (char*)k.Z + zel * (size_t)j * nrhs * L.nc;
+      e = ev_begin(D, 0);
+      FPG_TRY(precond(D, vj, zj, nrhs, k.active));
+      ev_end(D, e);
+      e = ev_begin(D, 1);
+      FPG_TRY(schur(D, zj, zprec, k.w, nrhs, k.active));
+      ev_end(D, e);
+      e = ev_begin(D, 2);
+      int nl = 0;
+      FPG_CUDA_TRY(launch_mgs(k.V, (long long)nrhs * L.nc, k.w, k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j, nrhs,
+                              k.part, kGmax, k.H, hcol, hrhs, k.active, D->gx, D->st, &nl));
+      count(D, 2, nl);
+      ev_end(D, e);
+      e = ev_begin(D, 3);
+      FPG_CUDA_TRY(launch_givens(k.H, hcol, hrhs, k.cs, k.sn, k.g, k.res, j, m, nrhs, k.tolabs, k.active, k.kcyc,
+                                 k.iters, D->desc.max_iters, D->st));
+      count(D, 3, 1);
+      ev_end(D, e);
+    }
+    e = ev_begin(D, 4);
+    FPG_CUDA_TRY(launch_cycle_end(k.H, hcol, hrhs, k.g, k.y, m, nrhs, k.kcyc, k.u, k.Z, zprec,
+                                  (long long)nrhs * L.nc, L.nc, D->gx, D->st));
+    count(D, 4, 2);
+    ev_end(D, e);
+  }
+  // Alg. 1 steps 5-7: f'_a = f_a - R_ac p_c, p_a = A_a^{-1} f'_a, p_c = u
+  e = ev_begin(D, 5);
+  FPG_CUDA_TRY(launch_arm_rhs(D->f, k.u, L.ntot, L.n, D->delta, L.ao, D->tmp, p, nrhs, D->gxf, D->st));
+  count(D, 5, 1);
+  FPG_TRY(arm_solves(D, D->tmp, p, nrhs, 5));
+  ev_end(D, e);
+  // a7: global relative residual
+  e = ev_begin(D, 6);
+  FPG_CUDA_TRY(launch_global_apply(p, nullptr, D->f, L.ntot, L.n, D->delta, D->desc.kappa, L.ao, k.part, kGmax,
+                                   nrhs, D->gxf, D->gres, nullptr, 0.0, nullptr, D->st));
+  count(D, 6, 2);
+  ev_end(D, e);
+  return check_launch();
+}
+
+fpg_status collect_info(fpg_domain* D, fpg_solve_info* info) {
+  const int nrhs = D->desc.nrhs;
+  std::vector<double> gres(nrhs), res(nrhs), fn(nrhs), rn(nrhs);
+  std::vector<int> iters(nrhs), done(nrhs);
+  KrylovState& k = D->ks;
+  FPG_CUDA_TRY(cudaMemcpyAsync(gres.data(), D->gres, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, D->st));
+  FPG_CUDA_TRY(cudaMemcpyAsync(rn.data(), k.rnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, D->st));
+  FPG_CUDA_TRY(cudaMemcpyAsync(fn.data(), k.fnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, D->st));
+  FPG_CUDA_TRY(cudaMemcpyAsync(iters.data(), k.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, D->st));
+  FPG_CUDA_TRY(cudaStreamSynchronize(D->st));
+  ev_collect(D);
+  fpg_status all = FPG_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    const bool ok = gres[r] <= D->desc.rtol;
+    const fpg_status s = ok ? FPG_OK : FPG_ENOCONV;
+    if (s != FPG_OK) all = FPG_ENOCONV;
+    if (info) {
+      info[r].iterations = iters[r];
+      info[r].restarts = D->cycles_run;
+      info[r].status = s;
+      info[r].reserved = 0;
+      info[r].residual = gres[r];
+      info[r].schur_residual = fn[r] > 0 ? rn[r] / fn[r] : rn[r];
+    }
+  }
+  return all;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char* fpg_status_string(fpg_status s) {
+  switch (s) {
+    case FPG_OK: return "FPG_OK";
+    case FPG_EINVAL: return "FPG_EINVAL: invalid argument";
+    case FPG_ENOMEM: return "FPG_ENOMEM: workspace too small";
+    case FPG_ECUDA: return "FPG_ECUDA: CUDA error";
+    case FPG_ENOCONV: return "FPG_ENOCONV: not converged";
+    case FPG_ETIMEOUT: return "FPG_ETIMEOUT: device wait gave up";
+    case FPG_EUNSUPPORTED: return "FPG_EUNSUPPORTED";
+    case FPG_EBUDGET: return "FPG_EBUDGET: over the memory budget";
+  }
+  return "unknown status";
+}
+
+const char* fpg_last_cuda_error(void) { return g_last_err; }
+const char* fpg_version(void) { return "fpg 0.1 (sm_103a)"; }
+
+fpg_status fpg_unknowns(const fpg_domain_desc* desc, int64_t* count) {
+  if (!count) return FPG_EINVAL;
+  FPG_TRY(validate(desc));
+  Layout L;
+  make_layout(desc, &L);
+  *count = L.ntot;
+  return FPG_OK;
+}
+
+fpg_status fpg_workspace_bytes(const fpg_domain_desc* desc, size_t* bytes) {
+  if (!bytes) return FPG_EINVAL;
+  FPG_TRY(validate(desc));
+  Layout L;
+  make_layout(desc, &L);
+  Carver c(nullptr);
+  carve(nullptr, desc, L, c);
+  *bytes = c.used + 256;
+  return FPG_OK;
+}
+
+fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes, void* stream, fpg_domain** out) {
+  if (!out || !ws) return FPG_EINVAL;
+  *out = nullptr;
+  FPG_TRY(validate(desc));
+  size_t need = 0;
+  fpg_workspace_bytes(desc, &need);
+  if (bytes < need) return FPG_ENOMEM;
+  fpg_domain* D = new (std::nothrow) fpg_domain();
+  if (!D) return FPG_ENOMEM;
+  D->desc = *desc;
+  make_layout(desc, &D->L);
+  const Layout& L = D->L;
+  const int n = desc->n;
+  D->st = (cudaStream_t)stream;
+  D->delta = (double)(n + 1) * (double)(n + 1);
+  D->prec = desc->precond_precision;
+  D->LC = LineLayout{n, n, 1, n};
+  D->LWE = LineLayout{n, n + 1, n + 1, 1};
+  D->LSN = LineLayout{n, n + 1, 1, n};
+  D->we = BatchDesc{L.ntot, {0, 0, 0, 0}, 0};
+  D->sn = BatchDesc{L.ntot, {0, 0, 0, 0}, 0};
+  for (int a = 0; a < 4; ++a) {
+    if (L.ao.off[a] < 0) continue;
+    BatchDesc& g = a < 2 ? D->we : D->sn;
+    g.off[g.nper++] = L.ao.off[a];
+  }
+  for (auto* t : {&D->tC64, &D->tC32}) { t->n = n; t->ns = n; t->delta = D->delta; }
+  for (auto* t : {&D->tA64, &D->tA32}) { t->n = n; t->ns = n + 1; t->delta = D->delta; }
+  Carver c(ws);
+  carve(D, desc, L, c);
+  const int nrhs = desc->nrhs;
+  D->gx = pick_gx(L.nc, nrhs);
+  D->gxf = pick_gx(L.ntot, nrhs);
+  D->ks.nrhs = nrhs;
+  D->ks.m = desc->restart;
+  D->ks.n = n;
+  D->ks.nc = L.nc;
+  D->ks.gx = D->gx;
+  D->h_done.assign(nrhs, 0);
+  // host tables
+  std::vector<double> sint, pc, pa, ct;
+  fill_sintab(n, sint);
+  fill_pivots(n, n, D->delta, desc->kappa, pc);
+  fill_pivots(n, n + 1, D->delta, desc->kappa, pa);
+  fill_ctab(n, D->delta, pa, ct);
+  std::vector<float> sint32(sint.begin(), sint.end()), pc32(pc.begin(), pc.end()), pa32(pa.begin(), pa.end());
+  int arms[4] = {0, 0, 0, 0};
+  for (int i = 0; i < L.narms; ++i) arms[i] = L.arm_slots[i];
+  auto cp = [&](const void* dst, const void* src, size_t b) {
+    return cudaMemcpyAsync(const_cast<void*>(dst), src, b, cudaMemcpyHostToDevice, D->st);
+  };
+  cudaError_t err = cudaSuccess;
+  if (!err) err = cp(D->tC64.sintab, sint.data(), sizeof(double) * sint.size());
+  if (!err) err = cp(D->tC32.sintab, sint32.data(), sizeof(float) * sint32.size());
+  if (!err) err = cp(D->tC64.rpiv, pc.data(), sizeof(double) * pc.size());
+  if (!err) err = cp(D->tC32.rpiv, pc32.data(), sizeof(float) * pc32.size());
+  if (!err) err = cp(D->tA64.rpiv, pa.data(), sizeof(double) * pa.size());
+  if (!err) err = cp(D->tA32.rpiv, pa32.data(), sizeof(float) * pa32.size());
+  if (!err) err = cp(D->ctab, ct.data(), sizeof(double) * ct.size());
+  if (!err) err = cp(D->arms_dev, arms, sizeof(arms));
+  if (!err) err = cudaMemsetAsync(D->f, 0, sizeof(double) * nrhs * L.ntot, D->st);
+  if (!err) err = cudaStreamSynchronize(D->st);
+  if (err) {
+    record_cuda_error(err, "fpg_create_domain");
+    delete D;
+    return FPG_ECUDA;
+  }
+  *out = D;
+  return FPG_OK;
+}
+
+void fpg_destroy_domain(fpg_domain* d) {
+  if (!d) return;
+  for (auto ev : d->evpool) cudaEventDestroy(ev);
+  delete d;
+}
+
+fpg_status fpg_set_rhs(fpg_domain* d, const double* f_dev, int32_t rhs_index) {
+  if (!d || !f_dev || rhs_index < -1 || rhs_index >= d->desc.nrhs) return FPG_EINVAL;
+  const size_t one = sizeof(double) * d->L.ntot;
+  if (rhs_index < 0)
+    FPG_CUDA_TRY(cudaMemcpyAsync(d->f, f_dev, one * d->desc.nrhs, cudaMemcpyDeviceToDevice, d->st));
+  else
+    FPG_CUDA_TRY(cudaMemcpyAsync(d->f + (size_t)rhs_index * d->L.ntot, f_dev, one, cudaMemcpyDeviceToDevice, d->st));
+  return FPG_OK;
+}
+
+fpg_status fpg_set_rhs_host(fpg_domain* d, const double* f_host, int32_t rhs_index) {
+  if (!d || !f_host || rhs_index < -1 || rhs_index >= d->desc.nrhs) return FPG_EINVAL;
+  const size_t one = sizeof(double) * d->L.ntot;
+  if (rhs_index < 0)
+    FPG_CUDA_TRY(cudaMemcpyAsync(d->f, f_host, one * d->desc.nrhs, cudaMemcpyHostToDevice, d->st));
+  else
+    FPG_CUDA_TRY(cudaMemcpyAsync(d->f + (size_t)rhs_index * d->L.ntot, f_host, one, cudaMemcpyHostToDevice, d->st));
+  return FPG_OK;
+}
+
+fpg_status fpg_solve(fpg_domain* d, double* p_dev, fpg_solve_info* info) {
+  if (!d || !p_dev) return FPG_EINVAL;
+  FPG_TRY(solve_launch(d, p_dev));
+  return collect_info(d, info);
+}
+
+fpg_status fpg_solve_async(fpg_domain* d, double* p_dev) {
+  if (!d || !p_dev) return FPG_EINVAL;
+  return solve_launch(d, p_dev);
+}
+
+fpg_status fpg_solve_finish(fpg_domain* d, fpg_solve_info* info) {
+  if (!d) return FPG_EINVAL;
+  return collect_info(d, info);
+}
+
+fpg_status fpg_solve_host(fpg_domain* d, const double* f_host, double* p_host, fpg_solve_info* info) {
+  if (!d || !f_host || !p_host) return FPG_EINVAL;
+  FPG_TRY(fpg_set_rhs_host(d, f_host, -1));
+  FPG_TRY(solve_launch(d, d->tmp));
+  FPG_CUDA_TRY(cudaMemcpyAsync(p_host, d->tmp, sizeof(double) * d->L.ntot * d->desc.nrhs, cudaMemcpyDeviceToHost,
+                               d->st));
+  return collect_info(d, info);
+}
+
+// ---- operator entry points --------------------------------------------------
+
+fpg_status fpg_apply_precond(fpg_domain* d, const double* v, void* z, int32_t nvec) {
+  if (!d || !v || !z || nvec < 0) return FPG_EINVAL;
+  const size_t zel = d->prec == 64 ? 8 : 4;
+  for (int s = 0; s < nvec; s += d->desc.nrhs) {
+    const int c = std::min(d->desc.nrhs, nvec - s);
+    FPG_TRY(precond(d, v + (size_t)s * d->L.nc, (char*)z + zel * (size_t)s * d->L.nc, c, nullptr));
+  }
+  return check_launch();
+}
+
+fpg_status fpg_block_solve(fpg_domain* d, int32_t block, const double* v, double* z, int32_t nvec) {
+  if (!d || !v || !z || nvec < 0 || block < 0 || block > 4) return FPG_EINVAL;
+  const Layout& L = d->L;
+  if (block > 0 && L.ao.off[block - 1] < 0) return FPG_EINVAL;
+  const long long len = block == 0 ? L.nc : L.na;
+  const LineLayout& LL = block == 0 ? d->LC : (block <= 2 ? d->LWE : d->LSN);
+  const FastSolveTables& tb = block == 0 ? d->tC64 : d->tA64;
+  const int cap = (int)std::max(1LL, ((long long)d->desc.nrhs * std::max(L.nc, 2 * L.na)) / len);
+  for (int s = 0; s < nvec; s += cap) {
+    const int c = std::min(cap, nvec - s);
+    BatchDesc bd{len, {0, 0, 0, 0}, 1};
+    int nl = 0;
+    FPG_CUDA_TRY(launch_fast_solve(64, 64, tb, LL, v + (size_t)s * len, bd, z + (size_t)s * len, bd, c,
+                                   d->scratch, nullptr, 1, d->st, &nl));
+    d->launches += nl;
+  }
+  return check_launch();
+}
+
+fpg_status fpg_apply_schur(fpg_domain* d, const void* z, int32_t zprec, double* w, int32_t nvec) {
+  if (!d || !z || !w || nvec < 0 || (zprec != 64 && zprec != 32)) return FPG_EINVAL;
+  const size_t zel = zprec == 64 ? 8 : 4;
+  for (int s = 0; s < nvec; s += d->desc.nrhs) {
+    const int c = std::min(d->desc.nrhs, nvec - s);
+    FPG_TRY(schur(d, (const char*)z + zel * (size_t)s * d->L.nc, zprec, w + (size_t)s * d->L.nc, c, nullptr));
+  }
+  return check_launch();
+}
+
+fpg_status fpg_arnoldi_mgs(fpg_domain* d, const double* V, int32_t j, double* w, double* h, int64_t len,
+                           int32_t nvec) {
+  if (!d || !V || !w || !h || j < 0 || len <= 0 || nvec <= 0 || nvec > d->desc.nrhs) return FPG_EINVAL;
+  int nl = 0;
+  // v_{j+1} overwrites w: normalise in place
+  FPG_CUDA_TRY(launch_mgs(V, (long long)nvec * len, w, w, len, j, nvec, d->ks.part, kGmax, h, 0, j + 2, nullptr,
+                          pick_gx(len, nvec), d->st, &nl));
+  d->launches += nl;
+  return check_launch();
+}
+
+fpg_status fpg_givens(fpg_domain* d, double* Hcol, double* cs, double* sn, double* g, double* res, int32_t j,
+                      int32_t m, int32_t nvec) {
+  if (!d || !Hcol || !cs || !sn || !g || !res || j < 0 || j >= m || nvec <= 0) return FPG_EINVAL;
+  FPG_CUDA_TRY(launch_givens(Hcol, 0, j + 2, cs, sn, g, res, j, m, nvec, nullptr, nullptr, nullptr, nullptr, 0,
+                             d->st));
+  d->launches += 1;
+  return check_launch();
+}
+
+fpg_status fpg_global_residual(fpg_domain* d, const double* f, const double* p, double* out_host, int32_t nvec) {
+  if (!d || !f || !p || !out_host || nvec <= 0) return FPG_EINVAL;
+  const Layout& L = d->L;
+  for (int s = 0; s < nvec; s += d->desc.nrhs) {
+    const int c = std::min(d->desc.nrhs, nvec - s);
+    FPG_CUDA_TRY(launch_global_apply(p + (size_t)s * L.ntot, nullptr, f + (size_t)s * L.ntot, L.ntot, L.n, d->delta,
+                                     d->desc.kappa, L.ao, d->ks.part, kGmax, c, d->gxf, d->gres, nullptr, 0.0,
+                                     nullptr, d->st));
+    d->launches += 2;
+    FPG_CUDA_TRY(cudaMemcpyAsync(out_host + s, d->gres, sizeof(double) * c, cudaMemcpyDeviceToHost, d->st));
+    FPG_CUDA_TRY(cudaStreamSynchronize(d->st));
+  }
+  return FPG_OK;
+}
+
+fpg_status fpg_apply_global(fpg_domain* d, const double* p, double* y, int32_t nvec) {
+  if (!d || !p || !y || nvec <= 0) return FPG_EINVAL;
+  const Layout& L = d->L;
+  FPG_CUDA_TRY(launch_global_apply(p, y, nullptr, L.ntot, L.n, d->delta, d->desc.kappa, L.ao, d->ks.part, kGmax,
+                                   nvec, d->gxf, nullptr, nullptr, 0.0, nullptr, d->st));
+  d->launches += 1;
+  return check_launch();
+}
+
+fpg_status fpg_set_profiling(fpg_domain* d, int32_t on) {
+  if (!d) return FPG_EINVAL;
+  d->profiling = on != 0;
+  if (d->profiling && d->evpool.empty()) {
+    d->evpool.resize(kMaxEvents);
+    for (auto& ev : d->evpool) FPG_CUDA_TRY(cudaEventCreate(&ev));
+  }
+  for (int i = 0; i < kPhases; ++i) {
+    d->phase_ms[i] = 0;
+    d->phase_launches[i] = 0;
+  }
+  return FPG_OK;
+}
+
+fpg_status fpg_phase_stats(fpg_domain* d, int32_t phase, int64_t* launches, double* ms) {
+  if (!d || phase < 0 || phase >= kPhases) return FPG_EINVAL;
+  if (launches) *launches = d->phase_launches[phase];
+  if (ms) *ms = d->phase_ms[phase];
+  return FPG_OK;
+}
+
+fpg_status fpg_launch_count(fpg_domain* d, int64_t* launches) {
+  if (!d || !launches) return FPG_EINVAL;
+  *launches = d->launches;
+  return FPG_OK;
+}
+
+fpg_status fpg_probe_fma_peak(int32_t precision, double* flops) {
+  if (!flops || (precision != 64 && precision != 32)) return FPG_EINVAL;
+  int dev = 0, sms = 0;
+  FPG_CUDA_TRY(cudaGetDevice(&dev));
+  FPG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t st;
+  FPG_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = sms * 8;
+  const int iters = precision == 64 ? 256 : 8192;
+  launch_fma_probe(precision, blocks, 16, st);  // warm-up
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, st);
+    launch_fma_probe(precision, blocks, iters, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+  }
+  cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  if (err != cudaSuccess) {
+    record_cuda_error(err, "fma probe");
+    return FPG_ECUDA;
+  }
+  // 256 threads x 8 chains x 8 unrolled FMAs x iters, 2 flops each
+  *flops = 2.0 * blocks * 256.0 * 64.0 * iters / (best * 1e-3);
+  return FPG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// Fast solve z = A^{-1} v on batches of Dirichlet rectangles (Sec. 2.1).
+//
+// A is the 5-point operator of one block with all four sides Dirichlet.  Along
+// the transform axis t (length n) the line operator has the DST-I eigenvectors
+// q_{j,k} = sqrt(2/(n+1)) sin(j k pi/(n+1)) (Eq. "eigvector_Diri"); in that basis
+// every mode k decouples into the tridiagonal system of Eq. "trans_subeq",
+// tridiag(delta, lambda_k + kappa, delta) along the sweep axis s, with
+// lambda_k = -4 delta + 2 delta cos(k pi/(n+1)) (Eq. "Poisson_spectral_eigen",
+// dx = dy).  So  z = (2/(n+1)) S T^{-1} S v  with S the unnormalised DST-I.
+//
+// Three launches per batch: forward DST of every line into a scratch array laid
+// out [block][s][k] (k fastest), one Thomas solve per (block, mode), inverse DST
+// back into the block layout.  Compute precision T is double or float; inputs
+// are always FP64, the output is written as To.
+#include <cuda_runtime.h>
+
+#include "fpg_internal.cuh"
+
+namespace fpg {
+
+namespace {
+
+constexpr int kFsThreads = 256;
+
+__device__ __forceinline__ const double* batch_ptr(const double* base, const BatchDesc& d, int b) {
+  return base + (long long)(b / d.nper) * d.rhs_stride + d.off[b % d.nper];
+}
+template <typename To>
+__device__ __forceinline__ To* batch_ptr_out(To* base, const BatchDesc& d, int b) {
+  return base + (long long)(b / d.nper) * d.rhs_stride + d.off[b % d.nper];
+}
+
+// Unnormalised DST-I of the nl lines in `lines` (pitch `pitch`), output k of
+// line l handed to emit(l, k, value).  Dense form: y_k = sum_t x_t sin(pi (t+1)(k+1)/p),
+// with the sine read from a table of one period (index (t+1)(k+1) mod 2p).
+// `kfast` chooses the (l, k) walk order so that the caller's stores coalesce.
+template <typename T, typename Emit>
+__device__ __forceinline__ void dst_dense_lines(const T* lines, int nl, int n, int pitch,
+                                                const T* sintab, bool kfast, Emit emit) {
+  const int twop = 2 * (n + 1);
+  const int total = nl * n;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    int l, k;
+    if (kfast) { l = idx / n; k = idx - l * n; } else { k = idx / nl; l = idx - k * nl; }
+    const T* x = lines + l * pitch;
+    const int step = k + 1;
+    int m = step;
+    T acc = T(0);
+    for (int t = 0; t < n; ++t) {
+      acc = fma(x[t], sintab[m], acc);
+      m += step;
+      if (m >= twop) m -= twop;
+    }
+    emit(l, k, acc);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFsThreads)
+k_dst_forward(const double* __restrict__ in, BatchDesc ib, LineLayout L, int n,
+              const T* __restrict__ sintab_g, T* __restrict__ scratch, int lpb,
+              const int* __restrict__ active, int nper_active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.y;
+  if (active != nullptr && !active[b / nper_active]) return;
+  const int p2 = 2 * (n + 1);
+  const int pitch = n + 1;
+  T* sintab = reinterpret_cast<T*>(smem_raw);
+  T* lines = sintab + p2;
+  const int s0 = blockIdx.x * lpb;
+  const int nl = min(lpb, L.ns - s0);
+  const double* src = batch_ptr(in, ib, b);
+  for (int i = threadIdx.x; i < p2; i += blockDim.x) sintab[i] = sintab_g[i];
+  const int total = nl * n;
+  if (L.st == 1) {
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int l = idx / n, t = idx - l * n;
+      lines[l * pitch + t] = (T)src[t + (long long)(s0 + l) * L.ss];
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int t = idx / nl, l = idx - t * nl;
+      lines[l * pitch + t] = (T)src[(long long)t * L.st + (long long)(s0 + l) * L.ss];
+    }
+  }
+  __syncthreads();
+  T* dst = scratch + ((long long)b * L.ns + s0) * n;
+  dst_dense_lines<T>(lines, nl, n, pitch, sintab, true,
+                     [&](int l, int k, T v) { dst[(long long)l * n + k] = v; });
+}
+
+// One Thomas solve per (block, mode k) on scratch[b][s][k] in place.
+// Forward: y_0 = f_0 r_0, y_s = (f_s - delta y_{s-1}) r_s; backward:
+// x_{N-1} = y_{N-1}, x_s = y_s - delta r_s x_{s+1}; r_s are the reciprocal pivots.
+template <typename T>
+__global__ void k_thomas(T* __restrict__ scratch, int n, int ns, T delta, const T* __restrict__ rpiv,
+                         const int* __restrict__ active, int nper_active) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (k >= n) return;
+  if (active != nullptr && !active[b / nper_active]) return;
+  T* col = scratch + (long long)b * ns * n + k;
+  const T* r = rpiv + k;
+  T y = col[0] * r[0];
+  col[0] = y;
+  for (int s = 1; s < ns; ++s) {
+    y = (col[(long long)s * n] - delta * y) * r[(long long)s * n];
+    col[(long long)s * n] = y;
+  }
+  T x = y;
+  for (int s = ns - 2; s >= 0; --s) {
+    x = col[(long long)s * n] - delta * r[(long long)s * n] * x;
+    col[(long long)s * n] = x;
+  }
+}
+
+template <typename T, typename To>
+__global__ void __launch_bounds__(kFsThreads)
+k_dst_inverse(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc ob, LineLayout L, int n,
+              const T* __restrict__ sintab_g, int lpb, const int* __restrict__ active, int nper_active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.y;
+  if (active != nullptr && !active[b / nper_active]) return;
+  const int p2 = 2 * (n + 1);
+  const int pitch = n + 1;
+  T* sintab = reinterpret_cast<T*>(smem_raw);
+  T* lines = sintab + p2;
+  const int s0 = blockIdx.x * lpb;
+  const int nl = min(lpb, L.ns - s0);
+  for (int i = threadIdx.x; i < p2; i += blockDim.x) sintab[i] = sintab_g[i];
+  const T* src = scratch + ((long long)b * L.ns + s0) * n;
+  for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+    const int l = idx / n, t = idx - l * n;
+    lines[l * pitch + t] = src[(long long)l * n + t];
+  }
+  __syncthreads();
+  To* dst = batch_ptr_out(out, ob, b);
+  const T scale = T(2) / T(n + 1);
+  const bool kfast = (L.st == 1);
+  dst_dense_lines<T>(lines, nl, n, pitch, sintab, kfast, [&](int l, int k, T v) {
+    dst[(long long)k * L.st + (long long)(s0 + l) * L.ss] = (To)(v * scale);
+  });
+}
+
+template <typename T>
+int lines_per_block(int n) {
+  const size_t budget = 96 * 1024;
+  const size_t tab = sizeof(T) * 2 * (n + 1);
+  const size_t line = sizeof(T) * (n + 1);
+  long long l = (long long)((budget - tab) / line);
+  if (l > 16) l = 16;
+  if (l < 1) l = 1;
+  return (int)l;
+}
+
+template <typename T>
+size_t fs_smem_bytes(int n, int lpb) {
+  return sizeof(T) * (2 * (n + 1) + (size_t)lpb * (n + 1));
+}
+
+template <typename T, typename To>
+cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib,
+                            To* out, BatchDesc ob, int nblk, T* scratch, const int* active,
+                            int nper_active, cudaStream_t st) {
+  const int n = tb.n;
+  const int lpb = lines_per_block<T>(n);
+  const size_t smem = fs_smem_bytes<T>(n, lpb);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_dst_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dst_inverse<T, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  dim3 grid((L.ns + lpb - 1) / lpb, nblk);
+  k_dst_forward<T><<<grid, kFsThreads, smem, st>>>(in, ib, L, n, (const T*)tb.sintab, scratch, lpb,
+                                                    active, nper_active);
+  dim3 tg((n + 127) / 128, nblk);
+  k_thomas<T><<<tg, 128, 0, st>>>(scratch, n, L.ns, (T)tb.delta, (const T*)tb.rpiv, active, nper_active);
+  k_dst_inverse<T, To><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, n, (const T*)tb.sintab, lpb,
+                                                        active, nper_active);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Public (library-internal) entry: precision 64 -> double everywhere; 32 ->
+// float compute, output type chosen by out_prec (64 or 32).
+cudaError_t launch_fast_solve(int prec, int out_prec, const FastSolveTables& tb, LineLayout L,
+                              const double* in, BatchDesc ib, void* out, BatchDesc ob, int nblk,
+                              void* scratch, const int* active, int nper_active, cudaStream_t st,
+                              int* launches) {
+  if (nblk <= 0) return cudaSuccess;
+  if (launches) *launches += 3;
+  if (prec == 64) {
+    return fast_solve_impl<double, double>(tb, L, in, ib, (double*)out, ob, nblk, (double*)scratch, active,
+                                           nper_active, st);
+  }
+  if (out_prec == 64) {
+    return fast_solve_impl<float, double>(tb, L, in, ib, (double*)out, ob, nblk, (float*)scratch, active,
+                                          nper_active, st);
+  }
+  return fast_solve_impl<float, float>(tb, L, in, ib, (float*)out, ob, nblk, (float*)scratch, active,
+                                       nper_active, st);
+}
+
+}  // namespace fpg

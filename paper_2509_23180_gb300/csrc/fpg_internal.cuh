@@ -1,0 +1,127 @@
+// Internal declarations shared by the library's translation units.
+// Nothing here crosses the C ABI (include/fpg.h is the public surface).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fpg.h"
+
+namespace fpg {
+
+// ---------------------------------------------------------------------------
+// Batch of blocks of one shape inside larger vectors.  Block b of a launch lives
+// at base + (b / nper) * rhs_stride + off[b % nper]: nper blocks per right-hand
+// side (e.g. the two arms W and E), one right-hand side after another.
+struct BatchDesc {
+  long long rhs_stride;
+  long long off[4];
+  int nper;
+};
+
+// Memory layout of one block kind, seen as "lines": the fast solve transforms
+// along t (length nt) and runs the tridiagonal sweep along s (length ns).
+// Element (t, s) sits at t * st + s * ss inside the block.
+struct LineLayout {
+  int nt, ns;
+  long long st, ss;
+};
+
+// Everything the fast-solve kernels need for one block kind.
+struct FastSolveTables {
+  int n;              // transform length (= domain n)
+  int ns;             // sweep length
+  double delta;       // 1/h^2
+  const void* sintab; // sin(pi m/(n+1)), m = 0..2(n+1)-1, in the compute precision
+  const void* rpiv;   // Thomas reciprocal pivots, [ns][n], compute precision
+};
+
+// Offsets of the arm blocks W, E, S, N inside one full vector (-1 = absent).
+struct ArmOffsets {
+  long long off[4];
+};
+
+// Tables for the interface (Schur) correction, reduced form:
+// G_a = delta^2 Q diag(g_k) Q = Toeplitz-minus-Hankel with entries
+// c(|i-j|) - c(i+j+2) (0-based i, j), c(m) for m = 0..2n+1.
+struct SchurTables {
+  const double* ctab;
+};
+
+// Device-side state of one domain's GMRES (all pointers into the workspace).
+struct KrylovState {
+  int nrhs, m, n;
+  long long nc;           // n*n
+  double* V;              // [m+1][nrhs][nc]
+  void* Z;                // [m][nrhs][nc] (double or float)
+  double* w;              // [nrhs][nc]
+  double* u;              // [nrhs][nc] current centre iterate
+  double* fc;             // [nrhs][nc] reduced right-hand side f'_c
+  double* H;              // [nrhs][m][m+1] column-major Hessenberg
+  double* cs;             // [nrhs][m]
+  double* sn;             // [nrhs][m]
+  double* g;              // [nrhs][m+1]
+  double* y;              // [nrhs][m]
+  double* part;           // [2][nrhs][gmax] reduction partials
+  double* tolabs;         // [nrhs] rtol * ||f||
+  double* fnorm;          // [nrhs] ||f||
+  double* res;            // [nrhs] last |g_{j+1}|
+  double* rnorm;          // [nrhs] last true Schur residual norm
+  int* active;            // [nrhs] 1 while this right-hand side iterates in the cycle
+  int* done;              // [nrhs] 1 once converged
+  int* kcyc;              // [nrhs] Arnoldi steps taken in the current cycle
+  int* iters;             // [nrhs] total steps
+  int gx;                 // CTAs per right-hand side in point-wise kernels
+};
+
+// Error recording (thread-local text of the last CUDA error).
+void record_cuda_error(cudaError_t e, const char* where);
+
+}  // namespace fpg
+
+#define FPG_CUDA_TRY(expr)                                   \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) {                                 \
+      fpg::record_cuda_error(_e, #expr);                     \
+      return FPG_ECUDA;                                      \
+    }                                                        \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Device helpers.
+#ifdef __CUDACC__
+namespace fpg {
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+  // Butterfly: every lane ends with the same total, the order is fixed.
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum of one double per thread (blockDim.x a multiple of
+// 32, <= 1024).  Returns the total to every thread.  `red` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = (lane < nw) ? red[lane] : 0.0;
+  t = warp_sum(t);
+  return t;
+}
+
+// Sum of cnt partials p[0..cnt) in a fixed order, done by one warp; every lane
+// of the calling warp gets the total.
+__device__ __forceinline__ double warp_sum_partials(const double* p, int cnt) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < cnt; i += 32) s += p[i];
+  return warp_sum(s);
+}
+
+}  // namespace fpg
+#endif

@@ -1,0 +1,644 @@
+// GMRES-side kernels: Schur matvec, Arnoldi (MGS), Givens, cycle end, the
+// Schur reduction / back substitution of Alg. "fft_dd_solver", and the global
+// operator K for the acceptance residual.  All FP64.
+//
+// Reductions are deterministic: each CTA reduces its share in a fixed tree and
+// writes one partial; the consumer sums the partials of a right-hand side in a
+// fixed order (one warp), so a result never depends on scheduling.
+#include <cuda_runtime.h>
+
+#include "fpg_internal.cuh"
+
+namespace fpg {
+
+// Arm slots everywhere: 0 = W, 1 = E, 2 = S, 3 = N (offset < 0 when the arm is absent).
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename Tz>
+__device__ __forceinline__ double ld(const Tz* p, long long i) {
+  return (double)p[i];
+}
+
+// Value of C's line that faces arm `a`, position q (0..n-1).
+template <typename Tz>
+__device__ __forceinline__ double c_line(const Tz* z, int n, int a, int q) {
+  switch (a) {
+    case 0: return ld(z, (long long)q * n);                 // x = h column
+    case 1: return ld(z, (long long)q * n + n - 1);         // x = 1 - h column
+    case 2: return ld(z, q);                                // y = h row
+    default: return ld(z, (long long)(n - 1) * n + q);      // y = 1 - h row
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a2, reduced form: corr[r][a][i] = sum_j (c(|i-j|) - c(i+j+2)) line_a[j], i.e.
+// delta^2 Q diag(g_k) Q applied to C's line next to arm a (the exact interface
+// response R_ca A_a^{-1} R_ac restricted to that line).
+template <typename Tz>
+__global__ void __launch_bounds__(128)
+k_schur_lines(const Tz* __restrict__ z, long long zstride, int n, const double* __restrict__ ctab,
+              const int* __restrict__ arms, int narms, double* __restrict__ corr,
+              const int* __restrict__ active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* line = reinterpret_cast<double*>(smem_raw);
+  double* c = line + n;
+  const int r = blockIdx.y / narms;
+  const int a = arms[blockIdx.y % narms];
+  if (active != nullptr && !active[r]) return;
+  const Tz* zr = z + (long long)r * zstride;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) line[q] = c_line(zr, n, a, q);
+  for (int q = threadIdx.x; q < 2 * n + 2; q += blockDim.x) c[q] = ctab[q];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const int d = i > j ? i - j : j - i;
+    acc = fma(c[d] - c[i + j + 2], line[j], acc);
+  }
+  corr[((long long)r * 4 + a) * n + i] = acc;
+}
+
+// a2, stencil part fused with the interface corrections:
+// w = A_c z - sum_a corr_a on the lines next to the arms.
+template <typename Tz>
+__global__ void __launch_bounds__(kThreads)
+k_stencil_c(const Tz* __restrict__ z, long long zstride, double* __restrict__ w, long long wstride, int n,
+            double delta, double kappa, const double* __restrict__ corr, int armmask,
+            const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (active != nullptr && !active[r]) return;
+  const Tz* zr = z + (long long)r * zstride;
+  double* wr = w + (long long)r * wstride;
+  const double* cr = corr + (long long)r * 4 * n;
+  const long long nc = (long long)n * n;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nc;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / n), i = (int)(idx - (long long)j * n);
+    const double zc = ld(zr, idx);
+    double s = -4.0 * zc;
+    if (i > 0) s += ld(zr, idx - 1);
+    if (i < n - 1) s += ld(zr, idx + 1);
+    if (j > 0) s += ld(zr, idx - n);
+    if (j < n - 1) s += ld(zr, idx + n);
+    double v = fma(delta, s, kappa * zc);
+    if (i == 0 && (armmask & 1)) v -= cr[0 * n + j];
+    if (i == n - 1 && (armmask & 2)) v -= cr[1 * n + j];
+    if (j == 0 && (armmask & 4)) v -= cr[2 * n + i];
+    if (j == n - 1 && (armmask & 8)) v -= cr[3 * n + i];
+    wr[idx] = v;
+  }
+}
+
+// a2, literal form, step 1: every arm buffer gets zero except its interface
+// line, which receives delta * (C's facing line)  (= R_ac z).
+template <typename Tz>
+__global__ void k_literal_inject(const Tz* __restrict__ z, long long zstride, int n, double delta,
+                                 double* __restrict__ armbuf, long long rhs_stride, ArmOffsets ao,
+                                 const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (active != nullptr && !active[r]) return;
+  const Tz* zr = z + (long long)r * zstride;
+  const long long na = (long long)n * (n + 1);
+  for (int a = 0; a < 4; ++a) {
+    if (ao.off[a] < 0) continue;
+    double* ab = armbuf + (long long)r * rhs_stride + ao.off[a];
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < na;
+         idx += (long long)gridDim.x * blockDim.x) {
+      double v = 0.0;
+      if (a < 2) {  // W/E: (n+1) x n, x fastest
+        const int j = (int)(idx / (n + 1)), i = (int)(idx - (long long)j * (n + 1));
+        const int iface = (a == 0) ? n : 0;
+        if (i == iface) v = delta * c_line(zr, n, a, j);
+      } else {      // S/N: n x (n+1)
+        const int j = (int)(idx / n), i = (int)(idx - (long long)j * n);
+        const int iface = (a == 2) ? n : 0;
+        if (j == iface) v = delta * c_line(zr, n, a, i);
+      }
+      ab[idx] = v;
+    }
+  }
+}
+
+// a2, literal form, step 3: corr = delta * (arm solution on its interface line) (= R_ca A_a^{-1} R_ac z).
+__global__ void k_literal_extract(const double* __restrict__ armsol, long long rhs_stride, ArmOffsets ao,
+                                  int n, double delta, double* __restrict__ corr,
+                                  const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (active != nullptr && !active[r]) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  for (int a = 0; a < 4; ++a) {
+    if (ao.off[a] < 0) continue;
+    const double* s = armsol + (long long)r * rhs_stride + ao.off[a];
+    double v;
+    if (a == 0) v = s[(long long)q * (n + 1) + n];
+    else if (a == 1) v = s[(long long)q * (n + 1)];
+    else if (a == 2) v = s[(long long)n * n + q];
+    else v = s[q];
+    corr[((long long)r * 4 + a) * n + q] = delta * v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a3: modified Gram-Schmidt, one launch per step k of Arnoldi step j.
+// Step k (0 <= k <= j+1): fold the previous projection (k >= 1: h_{k-1} from the
+// partials of step k-1, w -= h_{k-1} v_{k-1}), then accumulate the partial of
+// <w, v_k> (k <= j) or of ||w||^2 (k = j+1).
+__global__ void __launch_bounds__(kThreads)
+k_mgs_step(const double* __restrict__ V, long long vstride /* per basis vector: nrhs*len */,
+           double* __restrict__ w, long long len, int k, int j, int nrhs, double* __restrict__ part,
+           int gmax, double* __restrict__ H, int hcol_stride, int hrhs_stride,
+           const int* __restrict__ active) {
+  __shared__ double red[32];
+  __shared__ double hprev_s;
+  const int r = blockIdx.y;
+  if (active != nullptr && !active[r]) return;
+  double hprev = 0.0;
+  if (k >= 1) {
+    if (threadIdx.x < 32) {
+      const double s = warp_sum_partials(part + ((long long)((k - 1) & 1) * nrhs + r) * gmax, gridDim.x);
+      if (threadIdx.x == 0) hprev_s = s;
+    }
+    __syncthreads();
+    hprev = hprev_s;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && H != nullptr)
+      H[(long long)r * hrhs_stride + (long long)j * hcol_stride + (k - 1)] = hprev;
+  }
+  double* wr = w + (long long)r * len;
+  const double* vp = (k >= 1) ? V + (long long)(k - 1) * vstride + (long long)r * len : nullptr;
+  const double* vk = (k <= j) ? V + (long long)k * vstride + (long long)r * len : nullptr;
+  double acc = 0.0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < len;
+       idx += (long long)gridDim.x * blockDim.x) {
+    double wv = wr[idx];
+    if (vp) {
+      wv = fma(-hprev, vp[idx], wv);
+      wr[idx] = wv;
+    }
+    acc = vk ? fma(wv, vk[idx], acc) : fma(wv, wv, acc);
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[((long long)(k & 1) * nrhs + r) * gmax + blockIdx.x] = acc;
+}
+
+// a3 tail: h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j} (written to vout).
+__global__ void __launch_bounds__(kThreads)
+k_mgs_normalize(const double* __restrict__ w, double* __restrict__ vout, long long len, int j, int nrhs,
+                const double* __restrict__ part, int gmax, double* __restrict__ H, int hcol_stride,
+                int hrhs_stride, const int* __restrict__ active) {
+  __shared__ double hn_s;
+  const int r = blockIdx.y;
+  if (active != nullptr && !active[r]) return;
+  if (threadIdx.x < 32) {
+    const double s = warp_sum_partials(part + ((long long)((j + 1) & 1) * nrhs + r) * gmax, gridDim.x);
+    if (threadIdx.x == 0) hn_s = sqrt(s);
+  }
+  __syncthreads();
+  const double hn = hn_s;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && H != nullptr)
+    H[(long long)r * hrhs_stride + (long long)j * hcol_stride + (j + 1)] = hn;
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  const double* wr = w + (long long)r * len;
+  double* vr = vout + (long long)r * len;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < len;
+       idx += (long long)gridDim.x * blockDim.x)
+    vr[idx] = wr[idx] * inv;
+}
+
+// ---------------------------------------------------------------------------
+// a4: Givens step on column j, one thread per right-hand side.
+__global__ void k_givens(double* __restrict__ H, int hcol_stride, int hrhs_stride, double* __restrict__ cs,
+                         double* __restrict__ sn, double* __restrict__ g, double* __restrict__ res, int j,
+                         int m, int nrhs, const double* __restrict__ tolabs, int* __restrict__ active,
+                         int* __restrict__ kcyc, int* __restrict__ iters, int max_iters) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  if (active != nullptr && !active[r]) return;
+  double* h = H + (long long)r * hrhs_stride + (long long)j * hcol_stride;
+  double* c = cs + (long long)r * m;
+  double* s = sn + (long long)r * m;
+  double* gr = g + (long long)r * (m + 1);
+  for (int i = 0; i < j; ++i) {
+    const double a = h[i], b = h[i + 1];
+    h[i] = c[i] * a + s[i] * b;
+    h[i + 1] = -s[i] * a + c[i] * b;
+  }
+  const double a = h[j], b = h[j + 1];
+  const double rr = hypot(a, b);
+  double cc = 1.0, ss = 0.0;
+  if (rr != 0.0) {
+    cc = a / rr;
+    ss = b / rr;
+  }
+  c[j] = cc;
+  s[j] = ss;
+  h[j] = rr;
+  h[j + 1] = 0.0;
+  gr[j + 1] = -ss * gr[j];
+  gr[j] = cc * gr[j];
+  const double rj = fabs(gr[j + 1]);
+  res[r] = rj;
+  if (kcyc) kcyc[r] = j + 1;
+  if (iters) iters[r] += 1;
+  if (active != nullptr && tolabs != nullptr) {
+    if (rj <= tolabs[r] || b == 0.0 || (iters && iters[r] >= max_iters)) active[r] = 0;
+  }
+}
+
+// a5: y = R^{-1} g over the kcyc[r] steps of this cycle (one thread per RHS).
+__global__ void k_backsolve(const double* __restrict__ H, int hcol_stride, int hrhs_stride,
+                            const double* __restrict__ g, double* __restrict__ y, int m, int nrhs,
+                            const int* __restrict__ kcyc) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const int k = kcyc[r];
+  const double* h = H + (long long)r * hrhs_stride;
+  const double* gr = g + (long long)r * (m + 1);
+  double* yr = y + (long long)r * m;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = gr[i];
+    for (int l = i + 1; l < k; ++l) s -= h[(long long)l * hcol_stride + i] * yr[l];
+    yr[i] = s / h[(long long)i * hcol_stride + i];
+  }
+}
+
+// a5: u += Z y (k = kcyc[r] columns).
+template <typename Tz>
+__global__ void __launch_bounds__(kThreads)
+k_update_u(double* __restrict__ u, const Tz* __restrict__ Z, long long zvstride, long long len,
+           const double* __restrict__ y, int m, const int* __restrict__ kcyc) {
+  const int r = blockIdx.y;
+  const int k = kcyc[r];
+  if (k == 0) return;
+  const double* yr = y + (long long)r * m;
+  double* ur = u + (long long)r * len;
+  const Tz* Zr = Z + (long long)r * len;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < len;
+       idx += (long long)gridDim.x * blockDim.x) {
+    double s = ur[idx];
+    for (int i = 0; i < k; ++i) s = fma(yr[i], (double)Zr[(long long)i * zvstride + idx], s);
+    ur[idx] = s;
+  }
+}
+
+// Restart, part 1: rvec = fc - w (w = L_c u); partials of ||rvec||^2.
+__global__ void __launch_bounds__(kThreads)
+k_residual_partials(const double* __restrict__ fc, const double* __restrict__ w, double* __restrict__ rvec,
+                    long long len, int nrhs, double* __restrict__ part, int gmax,
+                    const int* __restrict__ done) {
+  __shared__ double red[32];
+  const int r = blockIdx.y;
+  if (done != nullptr && done[r]) return;
+  const double* f = fc + (long long)r * len;
+  const double* wr = w + (long long)r * len;
+  double* rv = rvec + (long long)r * len;
+  double acc = 0.0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < len;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const double v = f[idx] - wr[idx];
+    rv[idx] = v;
+    acc = fma(v, v, acc);
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[(long long)r * gmax + blockIdx.x] = acc;
+}
+
+// Restart, part 2: beta = ||rvec||; converged -> done; else v_0 = rvec / beta,
+// g = beta e_1, active = 1, kcyc = 0.
+__global__ void __launch_bounds__(kThreads)
+k_restart(double* __restrict__ v0, long long len, int nrhs, const double* __restrict__ part, int gmax,
+          double* __restrict__ g, int m, const double* __restrict__ tolabs, double* __restrict__ rnorm,
+          int* __restrict__ done, int* __restrict__ active, int* __restrict__ kcyc,
+          const int* __restrict__ iters, int max_iters) {
+  __shared__ double beta_s;
+  const int r = blockIdx.y;
+  if (done[r]) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      active[r] = 0;
+      kcyc[r] = 0;
+    }
+    return;
+  }
+  if (threadIdx.x < 32) {
+    const double s = warp_sum_partials(part + (long long)r * gmax, gridDim.x);
+    if (threadIdx.x == 0) beta_s = sqrt(s);
+  }
+  __syncthreads();
+  const double beta = beta_s;
+  const bool conv = beta <= tolabs[r];
+  const bool out_of_steps = iters[r] >= max_iters;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    rnorm[r] = beta;
+    kcyc[r] = 0;
+    if (conv || out_of_steps) {
+      done[r] = 1;
+      active[r] = 0;
+    } else {
+      active[r] = 1;
+      double* gr = g + (long long)r * (m + 1);
+      gr[0] = beta;
+      for (int i = 1; i <= m; ++i) gr[i] = 0.0;
+    }
+  }
+  if (conv || out_of_steps) return;
+  const double inv = 1.0 / beta;
+  double* vr = v0 + (long long)r * len;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < len;
+       idx += (long long)gridDim.x * blockDim.x)
+    vr[idx] *= inv;
+}
+
+// ---------------------------------------------------------------------------
+// a6: Alg. 1 step 3, f'_c = f_c - sum_a R_ca q_a, with q_a held in the arm
+// blocks of `q` (full vectors).  R_ca picks delta * (arm value on its interface line).
+__global__ void __launch_bounds__(kThreads)
+k_reduce_rhs(const double* __restrict__ f, const double* __restrict__ q, long long ntot, int n,
+             double delta, ArmOffsets ao, double* __restrict__ fc) {
+  const int r = blockIdx.y;
+  const double* fr = f + (long long)r * ntot;
+  const double* qr = q + (long long)r * ntot;
+  double* out = fc + (long long)r * n * n;
+  const long long nc = (long long)n * n;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nc;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / n), i = (int)(idx - (long long)j * n);
+    double v = fr[idx];
+    if (i == 0 && ao.off[0] >= 0) v -= delta * qr[ao.off[0] + (long long)j * (n + 1) + n];
+    if (i == n - 1 && ao.off[1] >= 0) v -= delta * qr[ao.off[1] + (long long)j * (n + 1)];
+    if (j == 0 && ao.off[2] >= 0) v -= delta * qr[ao.off[2] + (long long)n * n + i];
+    if (j == n - 1 && ao.off[3] >= 0) v -= delta * qr[ao.off[3] + i];
+    out[idx] = v;
+  }
+}
+
+// a6: Alg. 1 step 5, f'_a = f_a - R_ac p_c for every arm (into `out`, full vectors),
+// and the centre block of `p` receives u.
+__global__ void __launch_bounds__(kThreads)
+k_arm_rhs(const double* __restrict__ f, const double* __restrict__ u, long long ntot, int n, double delta,
+          ArmOffsets ao, double* __restrict__ out, double* __restrict__ p) {
+  const int r = blockIdx.y;
+  const double* fr = f + (long long)r * ntot;
+  const double* ur = u + (long long)r * n * n;
+  double* o = out + (long long)r * ntot;
+  double* pr = p + (long long)r * ntot;
+  const long long nc = (long long)n * n;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < ntot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    if (idx < nc) {
+      pr[idx] = ur[idx];
+      continue;
+    }
+    double v = fr[idx];
+    for (int a = 0; a < 4; ++a) {
+      const long long off = ao.off[a];
+      if (off < 0 || idx < off || idx >= off + (long long)n * (n + 1)) continue;
+      const long long li = idx - off;
+      if (a < 2) {
+        const int j = (int)(li / (n + 1)), i = (int)(li - (long long)j * (n + 1));
+        if (a == 0 && i == n) v -= delta * ur[(long long)j * n];
+        if (a == 1 && i == 0) v -= delta * ur[(long long)j * n + n - 1];
+      } else {
+        const int j = (int)(li / n), i = (int)(li - (long long)j * n);
+        if (a == 2 && j == n) v -= delta * ur[i];
+        if (a == 3 && j == 0) v -= delta * ur[(long long)(n - 1) * n + i];
+      }
+    }
+    o[idx] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Global operator K (a7): value of the neighbour (di, dj) of local node (i, j)
+// of block `blk` (0 = C, 1..4 = W, E, S, N); zero on the domain's edge.
+__device__ __forceinline__ double nb_value(const double* pr, int n, const ArmOffsets& ao, int blk, int i,
+                                           int j, int di, int dj) {
+  const int ni = i + di, nj = j + dj;
+  const long long nc = (long long)n * n;
+  if (blk == 0) {
+    if (ni >= 0 && ni < n && nj >= 0 && nj < n) return pr[(long long)nj * n + ni];
+    if (ni < 0) return ao.off[0] >= 0 ? pr[ao.off[0] + (long long)nj * (n + 1) + n] : 0.0;
+    if (ni >= n) return ao.off[1] >= 0 ? pr[ao.off[1] + (long long)nj * (n + 1)] : 0.0;
+    if (nj < 0) return ao.off[2] >= 0 ? pr[ao.off[2] + (long long)n * n + ni] : 0.0;
+    return ao.off[3] >= 0 ? pr[ao.off[3] + ni] : 0.0;
+  }
+  const int a = blk - 1;
+  const long long off = ao.off[a];
+  if (a < 2) {  // (n+1) x n
+    if (ni >= 0 && ni <= n && nj >= 0 && nj < n) return pr[off + (long long)nj * (n + 1) + ni];
+    if (a == 0 && ni == n + 1) return pr[(long long)nj * n];          // W -> C column 0
+    if (a == 1 && ni == -1) return pr[(long long)nj * n + n - 1];     // E -> C column n-1
+    return 0.0;
+  }
+  if (ni >= 0 && ni < n && nj >= 0 && nj <= n) return pr[off + (long long)nj * n + ni];
+  if (a == 2 && nj == n + 1) return pr[ni];                           // S -> C row 0
+  if (a == 3 && nj == -1) return pr[(long long)(n - 1) * n + ni];     // N -> C row n-1
+  (void)nc;
+  return 0.0;
+}
+
+__device__ __forceinline__ void locate(long long idx, int n, const ArmOffsets& ao, int* blk, int* i, int* j) {
+  const long long nc = (long long)n * n;
+  if (idx < nc) {
+    *blk = 0;
+    *j = (int)(idx / n);
+    *i = (int)(idx - (long long)(*j) * n);
+    return;
+  }
+  for (int a = 0; a < 4; ++a) {
+    const long long off = ao.off[a];
+    if (off < 0 || idx < off || idx >= off + (long long)n * (n + 1)) continue;
+    const long long li = idx - off;
+    *blk = a + 1;
+    const int nx = (a < 2) ? n + 1 : n;
+    *j = (int)(li / nx);
+    *i = (int)(li - (long long)(*j) * nx);
+    return;
+  }
+  *blk = -1;
+  *i = *j = 0;
+}
+
+// y = K p; with f != nullptr also accumulates partials of ||f - K p||^2 and ||f||^2.
+__global__ void __launch_bounds__(kThreads)
+k_global_apply(const double* __restrict__ p, double* __restrict__ y, const double* __restrict__ f,
+               long long ntot, int n, double delta, double kappa, ArmOffsets ao, double* __restrict__ part,
+               int gmax, int nrhs) {
+  __shared__ double red[32];
+  const int r = blockIdx.y;
+  const double* pr = p + (long long)r * ntot;
+  double rr = 0.0, ff = 0.0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < ntot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int blk, i, j;
+    locate(idx, n, ao, &blk, &i, &j);
+    const double pc = pr[idx];
+    double s = -4.0 * pc;
+    s += nb_value(pr, n, ao, blk, i, j, 1, 0);
+    s += nb_value(pr, n, ao, blk, i, j, -1, 0);
+    s += nb_value(pr, n, ao, blk, i, j, 0, 1);
+    s += nb_value(pr, n, ao, blk, i, j, 0, -1);
+    const double kp = fma(delta, s, kappa * pc);
+    if (y) y[(long long)r * ntot + idx] = kp;
+    if (f) {
+      const double fv = f[(long long)r * ntot + idx];
+      const double d = fv - kp;
+      rr = fma(d, d, rr);
+      ff = fma(fv, fv, ff);
+    }
+  }
+  if (f) {
+    rr = block_sum(rr, red);
+    ff = block_sum(ff, red);
+    if (threadIdx.x == 0) {
+      part[((long long)0 * nrhs + r) * gmax + blockIdx.x] = rr;
+      part[((long long)1 * nrhs + r) * gmax + blockIdx.x] = ff;
+    }
+  }
+}
+
+// out[r] = sqrt(sum rr) / sqrt(sum ff) (relative residual); fnorm_out[r] = sqrt(sum ff).
+__global__ void k_residual_finalize(const double* __restrict__ part, int gmax, int cnt, int nrhs,
+                                    double* __restrict__ out, double* __restrict__ fnorm_out,
+                                    double rtol, double* __restrict__ tolabs) {
+  const int r = blockIdx.x;
+  if (threadIdx.x >= 32) return;
+  const double rr = warp_sum_partials(part + ((long long)0 * nrhs + r) * gmax, cnt);
+  const double ff = warp_sum_partials(part + ((long long)1 * nrhs + r) * gmax, cnt);
+  if (threadIdx.x == 0) {
+    const double fn = sqrt(ff);
+    if (out) out[r] = fn > 0.0 ? sqrt(rr) / fn : sqrt(rr);
+    if (fnorm_out) fnorm_out[r] = fn;
+    if (tolabs) tolabs[r] = rtol * fn;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers (library-internal).
+cudaError_t launch_schur_reduced(const void* z, int zprec, long long zstride, int n, const double* ctab,
+                                 const int* arms_dev, int narms, double* corr, const int* active, int nrhs,
+                                 cudaStream_t st) {
+  dim3 grid((n + 127) / 128, nrhs * narms);
+  const size_t smem = sizeof(double) * (3 * n + 2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_schur_lines<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_schur_lines<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  if (zprec == 64)
+    k_schur_lines<double><<<grid, 128, smem, st>>>((const double*)z, zstride, n, ctab, arms_dev, narms, corr,
+                                                    active);
+  else
+    k_schur_lines<float><<<grid, 128, smem, st>>>((const float*)z, zstride, n, ctab, arms_dev, narms, corr,
+                                                   active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_c(const void* z, int zprec, long long zstride, double* w, long long wstride, int n,
+                             double delta, double kappa, const double* corr, int armmask, const int* active,
+                             int nrhs, int gx, cudaStream_t st) {
+  dim3 grid(gx, nrhs);
+  if (zprec == 64)
+    k_stencil_c<double><<<grid, kThreads, 0, st>>>((const double*)z, zstride, w, wstride, n, delta, kappa, corr,
+                                                    armmask, active);
+  else
+    k_stencil_c<float><<<grid, kThreads, 0, st>>>((const float*)z, zstride, w, wstride, n, delta, kappa, corr,
+                                                   armmask, active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_literal_inject(const void* z, int zprec, long long zstride, int n, double delta,
+                                  double* armbuf, long long rhs_stride, ArmOffsets ao, const int* active,
+                                  int nrhs, int gx, cudaStream_t st) {
+  dim3 grid(gx, nrhs);
+  if (zprec == 64)
+    k_literal_inject<double><<<grid, kThreads, 0, st>>>((const double*)z, zstride, n, delta, armbuf, rhs_stride,
+                                                         ao, active);
+  else
+    k_literal_inject<float><<<grid, kThreads, 0, st>>>((const float*)z, zstride, n, delta, armbuf, rhs_stride,
+                                                        ao, active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_literal_extract(const double* armsol, long long rhs_stride, ArmOffsets ao, int n,
+                                   double delta, double* corr, const int* active, int nrhs, cudaStream_t st) {
+  dim3 grid((n + 127) / 128, nrhs);
+  k_literal_extract<<<grid, 128, 0, st>>>(armsol, rhs_stride, ao, n, delta, corr, active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mgs(const double* V, long long vstride, double* w, double* vout, long long len, int j,
+                       int nrhs, double* part, int gmax, double* H, int hcol_stride, int hrhs_stride,
+                       const int* active, int gx, cudaStream_t st, int* launches) {
+  dim3 grid(gx, nrhs);
+  for (int k = 0; k <= j + 1; ++k) {
+    k_mgs_step<<<grid, kThreads, 0, st>>>(V, vstride, w, len, k, j, nrhs, part, gmax, H, hcol_stride,
+                                          hrhs_stride, active);
+  }
+  k_mgs_normalize<<<grid, kThreads, 0, st>>>(w, vout, len, j, nrhs, part, gmax, H, hcol_stride, hrhs_stride,
+                                             active);
+  if (launches) *launches += j + 3;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_givens(double* H, int hcol_stride, int hrhs_stride, double* cs, double* sn, double* g,
+                          double* res, int j, int m, int nrhs, const double* tolabs, int* active, int* kcyc,
+                          int* iters, int max_iters, cudaStream_t st) {
+  k_givens<<<(nrhs + 63) / 64, 64, 0, st>>>(H, hcol_stride, hrhs_stride, cs, sn, g, res, j, m, nrhs, tolabs,
+                                            active, kcyc, iters, max_iters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cycle_end(const double* H, int hcol_stride, int hrhs_stride, const double* g, double* y,
+                             int m, int nrhs, const int* kcyc, double* u, const void* Z, int zprec,
+                             long long zvstride, long long len, int gx, cudaStream_t st) {
+  k_backsolve<<<(nrhs + 63) / 64, 64, 0, st>>>(H, hcol_stride, hrhs_stride, g, y, m, nrhs, kcyc);
+  dim3 grid(gx, nrhs);
+  if (zprec == 64)
+    k_update_u<double><<<grid, kThreads, 0, st>>>(u, (const double*)Z, zvstride, len, y, m, kcyc);
+  else
+    k_update_u<float><<<grid, kThreads, 0, st>>>(u, (const float*)Z, zvstride, len, y, m, kcyc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restart(const double* fc, const double* w, double* v0, long long len, int nrhs, double* part,
+                           int gmax, double* g, int m, const double* tolabs, double* rnorm, int* done,
+                           int* active, int* kcyc, const int* iters, int max_iters, int gx, cudaStream_t st) {
+  dim3 grid(gx, nrhs);
+  k_residual_partials<<<grid, kThreads, 0, st>>>(fc, w, v0, len, nrhs, part, gmax, done);
+  k_restart<<<grid, kThreads, 0, st>>>(v0, len, nrhs, part, gmax, g, m, tolabs, rnorm, done, active, kcyc, iters,
+                                       max_iters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_rhs(const double* f, const double* q, long long ntot, int n, double delta,
+                              ArmOffsets ao, double* fc, int nrhs, int gx, cudaStream_t st) {
+  dim3 grid(gx, nrhs);
+  k_reduce_rhs<<<grid, kThreads, 0, st>>>(f, q, ntot, n, delta, ao, fc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_arm_rhs(const double* f, const double* u, long long ntot, int n, double delta, ArmOffsets ao,
+                           double* out, double* p, int nrhs, int gx, cudaStream_t st) {
+  dim3 grid(gx, nrhs);
+  k_arm_rhs<<<grid, kThreads, 0, st>>>(f, u, ntot, n, delta, ao, out, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_global_apply(const double* p, double* y, const double* f, long long ntot, int n, double delta,
+                                double kappa, ArmOffsets ao, double* part, int gmax, int nrhs, int gx,
+                                double* rel_out, double* fnorm_out, double rtol, double* tolabs,
+                                cudaStream_t st) {
+  dim3 grid(gx, nrhs);
+  k_global_apply<<<grid, kThreads, 0, st>>>(p, y, f, ntot, n, delta, kappa, ao, part, gmax, nrhs);
+  if (f) k_residual_finalize<<<nrhs, 32, 0, st>>>(part, gmax, gx, nrhs, rel_out, fnorm_out, rtol, tolabs);
+  return cudaGetLastError();
+}
+
+}  // namespace fpg

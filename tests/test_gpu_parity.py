@@ -1,0 +1,326 @@
+"""GPU parity: every hot-path step through the C ABI against the FP64 oracle.
+
+Tolerances: FP64 paths are compared at 1e-11 relative (each step is a few
+hundred FP64 operations per output, so rounding stays near 1e-13 and the bound
+leaves a wide margin); the FP32 fast solve at 2e-5 (conditioning of the lowest
+mode ~ 1/(1 - cos(pi/(n+1))) times FP32 rounding); whole solves to 1e-9
+relative error against K^{-1} f with rtol 1e-12, and to the requested residual.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import direct as D
+from oracle import krylov as Kr
+from oracle import operator as O
+from oracle import schur as S
+from oracle import transforms as T
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def domain(B, geom="cross", n=16, kappa=0.0, **kw):
+    return B.Domain(B.make_desc(geom, n, kappa, **kw))
+
+
+BLOCK_NAMES = ["C", "W", "E", "S", "N"]
+
+
+# ---------------------------------------------------------------- a1 fast solve
+@pytest.mark.parametrize("n", [2, 7, 16, 33, 64, 100])
+def test_fast_solve_eigenmodes(lib, n):
+    """A^{-1} of a rectangle mode is the mode over its closed-form eigenvalue."""
+    from paper_2509_23180_gb300 import binding as B
+    kappa = -10.0
+    d = domain(B, "cross", n, kappa, nrhs=2)
+    h = 1.0 / (n + 1)
+    for blk, name in enumerate(BLOCK_NAMES):
+        nx, ny = W.block_shape(name, n)
+        modes = [(1, 1), (nx, ny), (max(1, nx // 2), 1), (1, ny)]
+        v = np.stack([T.rectangle_mode(k, l, nx, ny) for k, l in modes])
+        want = np.stack([v[i] / T.rectangle_eigenvalue(k, l, nx, ny, h, kappa) for i, (k, l) in enumerate(modes)])
+        z = torch.zeros_like(dev(v))
+        d.block_solve(blk, dev(v), z, len(modes))
+        assert rel(host(z), want) < 1e-11, (name, n)
+
+
+@pytest.mark.parametrize("geom,n,kappa", [("cross", 9, 0.0), ("cross", 31, -10.0), ("T", 20, -3.0),
+                                          ("L", 12, 0.0)])
+def test_fast_solve_random_vs_oracle(lib, geom, n, kappa):
+    from paper_2509_23180_gb300 import binding as B
+    K = O.assemble(geom, n, kappa)
+    bs = S.BlockSystem(K, geom, n)
+    d = domain(B, geom, n, kappa, nrhs=3)
+    for blk, name in enumerate(BLOCK_NAMES):
+        if name not in bs.names:
+            continue
+        nx, ny = W.block_shape(name, n)
+        v = W.random_block_vectors(5, nx * ny, seed=blk + 10 * n)
+        z = torch.zeros_like(dev(v))
+        d.block_solve(blk, dev(v), z, 5)
+        want = np.stack([bs.block_solve(name, vi) for vi in v])
+        assert rel(host(z), want) < 1e-11, name
+
+
+@pytest.mark.parametrize("prec,tol", [(64, 1e-11), (32, 2e-5)])
+@pytest.mark.parametrize("n", [8, 48, 64])
+def test_apply_precond_vs_oracle(lib, prec, tol, n):
+    """a1: z = A_c^{-1} v in FP64 and in FP32 (FP64 in, FP32 out)."""
+    from paper_2509_23180_gb300 import binding as B
+    K = O.assemble("cross", n, -10.0)
+    bs = S.BlockSystem(K, "cross", n)
+    d = domain(B, "cross", n, -10.0, nrhs=4, precond_precision=prec)
+    v = W.random_block_vectors(6, n * n, seed=n)
+    z = torch.zeros((6, n * n), dtype=torch.float64 if prec == 64 else torch.float32, device="cuda")
+    d.apply_precond(dev(v), z, 6)
+    want = np.stack([bs.block_solve("C", vi) for vi in v])
+    assert rel(host(z).astype(np.float64), want) < tol
+
+
+# ---------------------------------------------------------------- a2 Schur matvec
+@pytest.mark.parametrize("mode", ["reduced", "literal"])
+@pytest.mark.parametrize("geom,n,kappa", [("cross", 10, 0.0), ("cross", 37, -10.0), ("T", 16, 0.0),
+                                          ("L", 23, -10.0)])
+def test_schur_matvec_vs_oracle(lib, mode, geom, n, kappa):
+    from paper_2509_23180_gb300 import binding as B
+    K = O.assemble(geom, n, kappa)
+    bs = S.BlockSystem(K, geom, n)
+    d = domain(B, geom, n, kappa, nrhs=3, schur_mode=mode)
+    zv = W.random_block_vectors(4, n * n, seed=3 * n)
+    w = torch.zeros((4, n * n), dtype=torch.float64, device="cuda")
+    d.apply_schur(dev(zv), 64, w, 4)
+    want = np.stack([bs.schur_apply(zi) for zi in zv])
+    assert rel(host(w), want) < 1e-11
+    # FP32 input (the stored FP32 basis of the precision variant) is read exactly
+    z32 = torch.as_tensor(zv, dtype=torch.float32, device="cuda")
+    d.apply_schur(z32, 32, w, 4)
+    want32 = np.stack([bs.schur_apply(zi) for zi in zv.astype(np.float32).astype(np.float64)])
+    assert rel(host(w), want32) < 1e-11
+
+
+# ---------------------------------------------------------------- a3 Arnoldi
+@pytest.mark.parametrize("j,length", [(0, 1000), (3, 4096), (12, 70001)])
+def test_arnoldi_mgs_vs_oracle(lib, j, length):
+    from paper_2509_23180_gb300 import binding as B
+    d = domain(B, "cross", 8, 0.0, nrhs=2)
+    nvec = 2
+    rng = np.random.default_rng(j)
+    Vs, ws, hs, vns = [], [], [], []
+    for r in range(nvec):
+        A = rng.standard_normal((j + 1, length))
+        Q, _ = np.linalg.qr(A.T)
+        V = Q.T.copy()
+        w = rng.standard_normal(length) + 3.0 * V[0]
+        h, hn, vn = Kr.arnoldi_mgs(V, w)
+        Vs.append(V); ws.append(w); hs.append(np.append(h, hn)); vns.append(vn)
+    Vdev = dev(np.stack([np.stack([Vs[r][i] for r in range(nvec)]) for i in range(j + 1)]))
+    wdev = dev(np.stack(ws))
+    hdev = torch.zeros((nvec, j + 2), dtype=torch.float64, device="cuda")
+    d.arnoldi_mgs(Vdev, j, wdev, hdev, length, nvec)
+    assert np.allclose(host(hdev), np.stack(hs), rtol=1e-12, atol=1e-12)
+    assert rel(host(wdev), np.stack(vns)) < 1e-12
+
+
+# ---------------------------------------------------------------- a4 Givens
+def test_givens_vs_oracle(lib):
+    from paper_2509_23180_gb300 import binding as B
+    d = domain(B, "cross", 8, 0.0, nrhs=3)
+    m, nvec = 12, 3
+    rng = np.random.default_rng(7)
+    Hbar = [np.triu(rng.standard_normal((m + 1, m)), -1) for _ in range(nvec)]
+    cs = torch.zeros((nvec, m), dtype=torch.float64, device="cuda")
+    sn = torch.zeros_like(cs)
+    g = torch.zeros((nvec, m + 1), dtype=torch.float64, device="cuda")
+    g[:, 0] = 2.0
+    res = torch.zeros(nvec, dtype=torch.float64, device="cuda")
+    ocs, osn, og = np.zeros((nvec, m)), np.zeros((nvec, m)), np.zeros((nvec, m + 1))
+    og[:, 0] = 2.0
+    for j in range(m):
+        col = np.stack([Hbar[r][: j + 2, j] for r in range(nvec)])
+        cdev = dev(col)
+        d.givens(cdev, cs, sn, g, res, j, m, nvec)
+        for r in range(nvec):
+            c = col[r].copy()
+            rr = Kr.givens_step(c, ocs[r], osn[r], og[r], j)
+            assert abs(host(res)[r] - rr) <= 1e-13 * max(1.0, rr)
+            assert np.allclose(host(cdev)[r], c, rtol=1e-13, atol=1e-14)
+    assert np.allclose(host(g), og, rtol=1e-13, atol=1e-14)
+
+
+# ---------------------------------------------------------------- a7 global operator
+@pytest.mark.parametrize("geom,n", [("cross", 11), ("T", 6), ("L", 30)])
+def test_global_operator_vs_oracle(lib, geom, n):
+    from paper_2509_23180_gb300 import binding as B
+    K = O.assemble(geom, n, -10.0)
+    d = domain(B, geom, n, -10.0, nrhs=2)
+    p = W.random_block_vectors(2, K.shape[0], seed=n)
+    y = torch.zeros_like(dev(p))
+    d.apply_global(dev(p), y, 2)
+    want = np.stack([K @ pi for pi in p])
+    assert rel(host(y), want) < 1e-13
+    f = W.random_block_vectors(2, K.shape[0], seed=n + 1)
+    got = d.global_residual(dev(f), dev(p), 2)
+    for r in range(2):
+        assert abs(got[r] - O.global_residual(K, f[r], p[r])) < 1e-12
+
+
+# ---------------------------------------------------------------- whole solve
+@pytest.mark.parametrize("geom", ["cross", "T", "L"])
+@pytest.mark.parametrize("n,kappa", [(8, 0.0), (17, -10.0), (64, 0.0)])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_solve_vs_direct(lib, geom, n, kappa, prec):
+    """Alg. 1 on the GPU reproduces p = K^{-1} f (rtol 1e-12; error <= 1e-9)."""
+    from paper_2509_23180_gb300 import binding as B
+    K = O.assemble(geom, n, kappa)
+    f = W.rhs_batch(geom, n, [0, 1, 2], kind="fourier")
+    ref = D.Factor(K).solve(f)
+    d = domain(B, geom, n, kappa, nrhs=3, rtol=1e-12, precond_precision=prec)
+    d.set_rhs(dev(f))
+    p = torch.zeros_like(dev(f))
+    st, info = d.solve(p)
+    assert st == B.FPG_OK, info
+    P = host(p)
+    for r in range(3):
+        assert rel(P[r], ref[r]) < 1e-9
+        assert info[r]["residual"] <= 1e-12
+        assert O.global_residual(K, f[r], P[r]) <= 1.01e-12
+
+
+@pytest.mark.parametrize("fname,geom,n,kappa,kind,seed",
+                         __import__("tests.golden.make_golden", fromlist=["CASES"]).CASES)
+def test_solve_matches_golden(lib, fname, geom, n, kappa, kind, seed):
+    from paper_2509_23180_gb300 import binding as B
+    from tests.test_oracle_golden import load_golden
+    f = W.rhs_batch(geom, n, [seed], kind=kind, kappa=kappa)
+    d = domain(B, geom, n, kappa, nrhs=1, rtol=1e-13)
+    d.set_rhs(dev(f))
+    p = torch.zeros_like(dev(f))
+    st, info = d.solve(p)
+    assert st == B.FPG_OK
+    assert rel(host(p)[0], load_golden(fname)) < 1e-10
+
+
+def test_manufactured_config_n64(lib):
+    """The 64^2-per-block cross with the manufactured solution, m = 30, rtol
+    1e-10: residual met, error to the direct solve within 1e-9 relative, and the
+    discretisation error to the analytic p is O(h^2) small."""
+    from paper_2509_23180_gb300 import binding as B
+    n = 64
+    K = O.assemble("cross", n, 0.0)
+    f = W.manufactured_rhs("cross", n, 0.0)[None, :]
+    ref = D.solve(K, f[0])
+    d = domain(B, "cross", n, 0.0, nrhs=1, restart=30, rtol=1e-10)
+    d.set_rhs(dev(f))
+    p = torch.zeros_like(dev(f))
+    st, info = d.solve(p)
+    P = host(p)[0]
+    assert st == B.FPG_OK and info[0]["residual"] <= 1e-10
+    assert O.global_residual(K, f[0], P) <= 1.01e-10
+    assert rel(P, ref) < 1e-9
+    assert np.abs(P - W.manufactured_solution("cross", n)).max() < 2e-3
+
+
+def test_batch_invariance(lib):
+    """A right-hand side gives the same answer alone and inside a batch."""
+    from paper_2509_23180_gb300 import binding as B
+    n = 24
+    f = W.rhs_batch("cross", n, [5, 6, 7, 8], kind="fourier")
+    d4 = domain(B, "cross", n, -10.0, nrhs=4, rtol=1e-12)
+    d4.set_rhs(dev(f))
+    p4 = torch.zeros_like(dev(f))
+    d4.solve(p4)
+    d1 = domain(B, "cross", n, -10.0, nrhs=1, rtol=1e-12)
+    for r in range(4):
+        d1.set_rhs(dev(f[r:r + 1]))
+        p1 = torch.zeros_like(dev(f[r:r + 1]))
+        d1.solve(p1)
+        assert rel(host(p1)[0], host(p4)[r]) < 1e-11
+
+
+def test_zero_rhs_and_mixed_difficulty(lib):
+    """f = 0 converges at once to p = 0; it does not disturb its batch mates."""
+    from paper_2509_23180_gb300 import binding as B
+    n = 20
+    f = W.rhs_batch("T", n, [1, 2], kind="fourier")
+    f[1] = 0.0
+    d = domain(B, "T", n, 0.0, nrhs=2, rtol=1e-11)
+    d.set_rhs(dev(f))
+    p = torch.full_like(dev(f), 3.0)
+    st, info = d.solve(p)
+    P = host(p)
+    assert np.all(P[1] == 0.0)
+    K = O.assemble("T", n, 0.0)
+    assert O.global_residual(K, f[0], P[0]) < 1.01e-11
+    assert info[1]["iterations"] == 0
+
+
+def test_restart_and_noconv(lib):
+    """A short restart forces several cycles and still converges; a tiny
+    max_iters returns FPG_ENOCONV with the last iterate."""
+    from paper_2509_23180_gb300 import binding as B
+    n = 32
+    K = O.assemble("cross", n, 0.0)
+    f = W.rhs_batch("cross", n, [3], kind="fourier")
+    d = domain(B, "cross", n, 0.0, nrhs=1, restart=3, rtol=1e-11)
+    d.set_rhs(dev(f))
+    p = torch.zeros_like(dev(f))
+    st, info = d.solve(p)
+    assert st == B.FPG_OK and info[0]["restarts"] >= 2
+    assert O.global_residual(K, f[0], host(p)[0]) < 1.01e-11
+    d2 = domain(B, "cross", n, 0.0, nrhs=1, restart=3, rtol=1e-12, max_iters=2)
+    d2.set_rhs(dev(f))
+    st, info = d2.solve(p)
+    assert st == B.FPG_ENOCONV and info[0]["status"] == B.FPG_ENOCONV
+    assert info[0]["iterations"] <= 3
+
+
+def test_schur_modes_agree_in_solve(lib):
+    from paper_2509_23180_gb300 import binding as B
+    n = 40
+    f = W.rhs_batch("cross", n, [9], kind="fourier")
+    out = []
+    for mode in ("reduced", "literal"):
+        d = domain(B, "cross", n, -10.0, nrhs=1, rtol=1e-12, schur_mode=mode)
+        d.set_rhs(dev(f))
+        p = torch.zeros_like(dev(f))
+        st, info = d.solve(p)
+        assert st == B.FPG_OK
+        out.append(host(p)[0])
+    assert rel(out[0], out[1]) < 1e-10
+
+
+@pytest.mark.parametrize("kappa", [0.0, -10.0])
+def test_full_size_256_bench_configuration(lib, kappa):
+    """The 256^2-per-block cross, 10 seeded right-hand sides, m = 30, rtol 1e-10,
+    as the benchmark runs it: every residual is re-checked on the CPU with the
+    oracle's K, and every solution against the oracle's direct solve."""
+    from paper_2509_23180_gb300 import binding as B
+    n = 256
+    K = O.assemble("cross", n, kappa)
+    F = D.Factor(K)
+    f = W.rhs_batch("cross", n, list(range(10)), kind="fourier")
+    d = domain(B, "cross", n, kappa, nrhs=10, restart=30, rtol=1e-10)
+    d.set_rhs(dev(f))
+    p = torch.zeros_like(dev(f))
+    st, info = d.solve(p)
+    assert st == B.FPG_OK
+    P = host(p)
+    ref = F.solve(f)
+    for r in range(10):
+        assert O.global_residual(K, f[r], P[r]) <= 1.01e-10
+        assert rel(P[r], ref[r]) < 1e-9

@@ -83,3 +83,14 @@ def test_brute_force_tiny_inverse():
     b = W.fourier_rhs("cross", n, 2)
     x = D.solve(sp.csr_matrix(K), b)
     assert np.allclose(np.linalg.inv(K) @ b, x, rtol=1e-12, atol=1e-14)
+
+
+def test_direct_batch_of_rhs_dense_and_sparse():
+    """(nrhs, N) right-hand sides give the same rows as one-by-one solves."""
+    for n in (4, 24):
+        K = O.assemble("T", n, -1.0)
+        b = np.stack([W.fourier_rhs("T", n, s) for s in (0, 1, 2)])
+        F = D.Factor(K)
+        X = F.solve(b)
+        for r in range(3):
+            assert np.allclose(X[r], F.solve(b[r]), rtol=1e-13, atol=1e-15)
