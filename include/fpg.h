@@ -173,6 +173,18 @@ fpg_status fpg_global_residual(fpg_domain* d, const double* f_dev, const double*
 /* Global operator y = K p for nvec full vectors (block order). */
 fpg_status fpg_apply_global(fpg_domain* d, const double* p_dev, double* y_dev, int32_t nvec);
 
+/* ---- options --------------------------------------------------------------- */
+
+typedef enum {
+  /* 1 (default): run each Arnoldi step (a3) and its Givens step (a4) as one
+   * launch, one thread-block cluster per right-hand side, for centre blocks of
+   * up to 262144 unknowns; 0: one launch per modified Gram-Schmidt step. */
+  FPG_OPT_ARNOLDI_CLUSTER = 1
+} fpg_option;
+
+/* Set an option on a domain (affects later calls).  FPG_EINVAL if unknown. */
+fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value);
+
 /* ---- measurement ----------------------------------------------------------- */
 
 /* Kernel-level timing of the last fpg_solve on this domain: launches issued and

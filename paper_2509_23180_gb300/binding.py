@@ -18,6 +18,7 @@ SCHUR = {"reduced": 0, "literal": 1}
 STATUS = {0: "FPG_OK", 1: "FPG_EINVAL", 2: "FPG_ENOMEM", 3: "FPG_ECUDA", 4: "FPG_ENOCONV",
           5: "FPG_ETIMEOUT", 6: "FPG_EUNSUPPORTED", 7: "FPG_EBUDGET"}
 FPG_OK, FPG_EINVAL, FPG_ENOMEM, FPG_ECUDA, FPG_ENOCONV = 0, 1, 2, 3, 4
+OPT_ARNOLDI_CLUSTER = 1
 PHASES = ("precond", "schur", "arnoldi", "givens", "cycle_end", "setup_finish", "residual")
 
 
@@ -64,6 +65,7 @@ _SIGS = {
     "fpg_givens": ([_P, _P, _P, _P, _P, _P, _I32, _I32, _I32], _I32),
     "fpg_global_residual": ([_P, _P, _P, _P, _I32], _I32),
     "fpg_apply_global": ([_P, _P, _P, _I32], _I32),
+    "fpg_set_option": ([_P, _I32, _I32], _I32),
     "fpg_set_profiling": ([_P, _I32], _I32),
     "fpg_phase_stats": ([_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D)], _I32),
     "fpg_launch_count": ([_P, ctypes.POINTER(_I64)], _I32),
@@ -216,6 +218,9 @@ class Domain:
 
     def apply_global(self, p, y, nvec: int):
         _check(self.lib.fpg_apply_global(self.handle, _ptr(p), _ptr(y), nvec), "fpg_apply_global")
+
+    def set_option(self, option: int, value: int):
+        _check(self.lib.fpg_set_option(self.handle, option, value), "fpg_set_option")
 
     # -- measurement -----------------------------------------------------
     def set_profiling(self, on: bool):

@@ -49,6 +49,16 @@ cudaError_t launch_global_apply(const double* p, double* y, const double* f, lon
                                 double* rel_out, double* fnorm_out, double rtol, double* tolabs,
                                 cudaStream_t st);
 cudaError_t launch_fma_probe(int prec, int blocks, int iters, cudaStream_t st);
+int arnoldi_cluster_size(long long len);
+cudaError_t launch_arnoldi_cluster(int csz, const double* V, long long vstride, double* w, double* vout,
+                                   long long len, int j, int nrhs, double* H, int hcol_stride, int hrhs_stride,
+                                   double* cs, double* sn, double* g, double* res, int m, const double* tolabs,
+                                   int* active, int* kcyc, int* iters, int max_iters, int do_givens,
+                                   cudaStream_t st);
+cudaError_t launch_arm_residual(const double* rhs, const double* x, double* out, long long ntot, int n, double delta,
+                                double kappa, ArmOffsets ao, int nrhs, int gx, cudaStream_t st);
+cudaError_t launch_arm_add(double* x, const double* e, long long ntot, int n, ArmOffsets ao, int nrhs, int gx,
+                           cudaStream_t st);
 
 static thread_local char g_last_err[256] = "no error";
 
@@ -65,6 +75,10 @@ namespace {
 constexpr int kGmax = 1024;
 constexpr int kPhases = 7;
 constexpr int kMaxEvents = 8192;
+// The Schur iteration stops at this fraction of the requested relative residual,
+// so that the global residual (which adds the rounding of the arm back
+// substitution) still meets the request.
+constexpr double kInnerMargin = 0.9;
 
 // Bump allocator over the caller's workspace (256-byte aligned regions).  With
 // base == nullptr it only measures.
@@ -153,7 +167,7 @@ struct fpg_domain {
   FastSolveTables tC64, tC32, tA64, tA32;
   double* ctab;
   int* arms_dev;
-  double *f, *tmp, *lit_in, *lit_out, *corr, *gres, *fnorm;
+  double *f, *tmp, *tmp2, *pbuf, *lit_in, *lit_out, *corr, *gres, *fnorm;
   void* scratch;
   KrylovState ks;
   int gx, gxf;
@@ -168,24 +182,12 @@ struct fpg_domain {
   std::vector<std::pair<int, int>> ev_used;  // (phase, event index of start)
   int ev_next = 0;
   int cycles_run = 0;
+  bool use_cluster = true;
 };
 
 namespace {
 
 // Host tables in FP64 -------------------------------------------------------
-void fill_sintab(int n, std::vector<double>& s) {
-  const int p = n + 1;
-  s.resize(2 * p);
-  for (int m = 0; m < 2 * p; ++m) {
-    // sin(pi m / p) with the argument folded to [0, pi/2] by exact integer symmetry
-    int q = m % (2 * p);
-    double sign = 1.0;
-    if (q >= p) { q -= p; sign = -1.0; }          // sin(x + pi) = -sin x
-    if (2 * q > p) q = p - q;                     // sin(pi - x) = sin x
-    s[m] = sign * std::sin(M_PI * (double)q / (double)p);
-  }
-}
-
 double cos_pi_frac(long long num, long long den) {
   // cos(pi num / den) with exact folding to [0, pi/2]
   long long q = num % (2 * den);
@@ -225,26 +227,170 @@ void fill_ctab(int n, double delta, const std::vector<double>& rpivA, std::vecto
   }
 }
 
-struct Regions {
-  size_t sintab64, sintab32, pivC64, pivC32, pivA64, pivA32, ctab, arms;
+// DST plan for transform length n: radices of the Stockham FFT (4s, then a 2,
+// then odd primes up to 43), Rader for a prime p whose p-1 factors that way,
+// the dense fallback otherwise.
+struct HostPlan {
+  int mode = DST_DENSE, N = 0, nrad = 0, rad[kMaxRadices] = {0};
+  std::vector<double> W, sinp, Bhat, dense;
+  std::vector<int> pin, pout;
 };
 
+bool radices_for(int N, int* rad, int* nrad) {
+  static const int odd[] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43};
+  int m = N, twos = 0, cnt = 0;
+  while (m % 2 == 0) { m /= 2; ++twos; }
+  while (twos >= 2) { if (cnt >= kMaxRadices) return false; rad[cnt++] = 4; twos -= 2; }
+  if (twos == 1) { if (cnt >= kMaxRadices) return false; rad[cnt++] = 2; }
+  for (int q : odd) {
+    while (m % q == 0) { if (cnt >= kMaxRadices) return false; rad[cnt++] = q; m /= q; }
+  }
+  *nrad = cnt;
+  return m == 1 && cnt > 0;
+}
+
+bool is_prime(int p) {
+  if (p < 2) return false;
+  for (int d = 2; (long long)d * d <= p; ++d) if (p % d == 0) return false;
+  return true;
+}
+
+int primitive_root(int p) {
+  std::vector<int> fs;
+  int m = p - 1;
+  for (int d = 2; (long long)d * d <= m; ++d) {
+    if (m % d == 0) { fs.push_back(d); while (m % d == 0) m /= d; }
+  }
+  if (m > 1) fs.push_back(m);
+  for (int g = 2; g < p; ++g) {
+    bool ok = true;
+    for (int q : fs) {
+      long long r = 1, b = g, e = (p - 1) / q;
+      while (e) { if (e & 1) r = r * b % p; b = b * b % p; e >>= 1; }
+      if (r == 1) { ok = false; break; }
+    }
+    if (ok) return g;
+  }
+  return -1;
+}
+
+// exp(-2 pi i num/den) with exact folding of the argument
+void cexp_neg(long long num, long long den, double* re, double* im) {
+  *re = cos_pi_frac(2 * num, den);
+  // sin(2 pi num/den) = cos(pi (4 num - den) / (2 den))
+  *im = -cos_pi_frac(4 * num - den, 2 * den);
+}
+
+HostPlan build_plan(int n) {
+  HostPlan P;
+  const int p = n + 1;
+  P.sinp.resize(p);
+  for (int j = 0; j < p; ++j) P.sinp[j] = cos_pi_frac(2 * j - p, 2 * p);  // sin(pi j/p) = cos(pi (j/p - 1/2))
+  P.dense.resize(2 * p);
+  for (int m = 0; m < 2 * p; ++m) P.dense[m] = cos_pi_frac(2 * m - p, 2 * p);
+  int rad[kMaxRadices], nrad = 0;
+  if (radices_for(p, rad, &nrad)) {
+    P.mode = DST_STOCKHAM;
+    P.N = p;
+  } else if (is_prime(p) && radices_for(p - 1, rad, &nrad)) {
+    P.mode = DST_RADER;
+    P.N = p - 1;
+  } else {
+    P.mode = DST_DENSE;
+    P.N = 1;
+    nrad = 0;
+  }
+  P.nrad = nrad;
+  for (int i = 0; i < nrad; ++i) P.rad[i] = rad[i];
+  P.W.resize(2 * P.N);
+  for (int m = 0; m < P.N; ++m) cexp_neg(m, P.N, &P.W[2 * m], &P.W[2 * m + 1]);
+  if (P.mode == DST_RADER) {
+    const int N = P.N, g = primitive_root(p);
+    long long ginv = 1;
+    {  // g^{p-2} mod p
+      long long b = g, e = p - 2;
+      while (e) { if (e & 1) ginv = ginv * b % p; b = b * b % p; e >>= 1; }
+    }
+    P.pin.resize(N);
+    P.pout.resize(N);
+    long long a = 1, c = 1;
+    for (int b = 0; b < N; ++b) {
+      P.pin[b] = (int)a;
+      P.pout[b] = (int)c;
+      a = a * g % p;
+      c = c * ginv % p;
+    }
+    // Bhat = DFT_N(B) / N with B_c = exp(-2 pi i g^{-c} / p)
+    std::vector<double> Br(N), Bi(N);
+    for (int q = 0; q < N; ++q) cexp_neg(P.pout[q], p, &Br[q], &Bi[q]);
+    P.Bhat.resize(2 * N);
+    for (int k = 0; k < N; ++k) {
+      long double sr = 0, si = 0;
+      for (int q = 0; q < N; ++q) {
+        double wr, wi;
+        cexp_neg((long long)q * k % N, N, &wr, &wi);
+        sr += (long double)Br[q] * wr - (long double)Bi[q] * wi;
+        si += (long double)Br[q] * wi + (long double)Bi[q] * wr;
+      }
+      P.Bhat[2 * k] = (double)(sr / N);
+      P.Bhat[2 * k + 1] = (double)(si / N);
+    }
+  }
+  return P;
+}
+
+// Radix plan only (sizes), no tables: used for workspace sizing.
+HostPlan plan_shape(int n) {
+  HostPlan P;
+  const int p = n + 1;
+  int rad[kMaxRadices], nrad = 0;
+  if (radices_for(p, rad, &nrad)) { P.mode = DST_STOCKHAM; P.N = p; }
+  else if (is_prime(p) && radices_for(p - 1, rad, &nrad)) { P.mode = DST_RADER; P.N = p - 1; }
+  else { P.mode = DST_DENSE; P.N = 1; nrad = 0; }
+  P.nrad = nrad;
+  for (int i = 0; i < nrad; ++i) P.rad[i] = rad[i];
+  return P;
+}
+
 // Carves every region; with base == nullptr only sizes are computed.
-void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, Carver& c) {
+void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostPlan* plan, Carver& c) {
   const int n = d->n, nrhs = d->nrhs, m = d->restart;
-  const int p2 = 2 * (n + 1);
   const size_t zel = d->precond_precision == 64 ? 8 : 4;
   void* p;
-  p = c.take(sizeof(double) * p2);            if (D) D->tC64.sintab = p, D->tA64.sintab = p;
-  p = c.take(sizeof(float) * p2);             if (D) D->tC32.sintab = p, D->tA32.sintab = p;
+  {
+    const HostPlan& hp = *plan;
+    const int N = hp.N, pp = n + 1;
+    for (int prec = 64; prec >= 32; prec -= 32) {
+      const size_t el = prec == 64 ? 8 : 4;
+      DstPlan dp{};
+      dp.n = n; dp.p = pp; dp.mode = hp.mode; dp.N = N; dp.nrad = hp.nrad;
+      for (int i = 0; i < kMaxRadices; ++i) dp.rad[i] = hp.rad[i];
+      dp.W = c.take(el * 2 * N);
+      dp.sinp = c.take(el * pp);
+      dp.Bhat = hp.mode == DST_RADER ? c.take(el * 2 * N) : nullptr;
+      dp.dense = c.take(el * 2 * pp);
+      dp.pin = hp.mode == DST_RADER ? (const int*)c.take(sizeof(int) * N) : nullptr;
+      dp.pout = hp.mode == DST_RADER ? (const int*)c.take(sizeof(int) * N) : nullptr;
+      if (D) {
+        if (prec == 64) D->tC64.plan = D->tA64.plan = dp;
+        else D->tC32.plan = D->tA32.plan = dp;
+      }
+    }
+  }
   p = c.take(sizeof(double) * L.nc);          if (D) D->tC64.rpiv = p;
   p = c.take(sizeof(float) * L.nc);           if (D) D->tC32.rpiv = p;
   p = c.take(sizeof(double) * L.na);          if (D) D->tA64.rpiv = p;
   p = c.take(sizeof(float) * L.na);           if (D) D->tA32.rpiv = p;
+  p = c.take(sizeof(double) * L.nc);          if (D) D->tC64.mneg = p;
+  p = c.take(sizeof(float) * L.nc);           if (D) D->tC32.mneg = p;
+  p = c.take(sizeof(double) * L.na);          if (D) D->tA64.mneg = p;
+  p = c.take(sizeof(float) * L.na);           if (D) D->tA32.mneg = p;
   p = c.take(sizeof(double) * (2 * n + 2));   if (D) D->ctab = (double*)p;
   p = c.take(sizeof(int) * 4);                if (D) D->arms_dev = (int*)p;
   p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->f = (double*)p;
   p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->tmp = (double*)p;
+  p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->tmp2 = (double*)p;
+  p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->pbuf = (double*)p;
   if (d->schur_mode == FPG_SCHUR_LITERAL) {
     p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->lit_in = (double*)p;
     p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->lit_out = (double*)p;
@@ -333,6 +479,21 @@ fpg_status arm_solves(fpg_domain* D, const double* in, double* out, int nvec, in
   return FPG_OK;
 }
 
+// Arm solves with one step of FP64 iterative refinement: out = A_a^{-1} in, then
+// e = A_a^{-1}(in - A_a out), out += e.  The fast solve's forward error (DST
+// rounding, ~1e-15..1e-14 relative) would otherwise leave a residual of about
+// cond(A_a) times that in the global system; the refinement brings it down to
+// the rounding of the residual evaluation itself.  `work` must not alias in/out.
+fpg_status arm_solves_refined(fpg_domain* D, const double* in, double* out, double* work, int nvec, int phase) {
+  const Layout& L = D->L;
+  FPG_TRY(arm_solves(D, in, out, nvec, phase));
+  FPG_CUDA_TRY(launch_arm_residual(in, out, work, L.ntot, L.n, D->delta, D->desc.kappa, L.ao, nvec, D->gxf, D->st));
+  FPG_TRY(arm_solves(D, work, work, nvec, phase));
+  FPG_CUDA_TRY(launch_arm_add(out, work, L.ntot, L.n, L.ao, nvec, D->gxf, D->st));
+  count(D, phase, 2);
+  return FPG_OK;
+}
+
 // a2 on nvec centre vectors (nvec <= nrhs): z (zprec) -> w.
 fpg_status schur(fpg_domain* D, const void* z, int zprec, double* w, int nvec, const int* active) {
   const Layout& L = D->L;
@@ -370,11 +531,6 @@ fpg_status check_launch() {
   return FPG_OK;
 }
 
-#define FPG_TRY(x)                   \
-  do {                               \
-    fpg_status _s = (x);             \
-    if (_s != FPG_OK) return _s;     \
-  } while (0)
 
 // Launch the whole solve on the stream (host loop over restart cycles; the only
 // host synchronisation is one read of the per-RHS "done" flags per cycle).
@@ -390,10 +546,10 @@ fpg_status solve_launch(fpg_domain* D, double* p) {
   // ||f|| per RHS and the absolute tolerance
   int e = ev_begin(D, 5);
   FPG_CUDA_TRY(launch_global_apply(D->f, nullptr, D->f, L.ntot, L.n, D->delta, D->desc.kappa, L.ao, k.part, kGmax,
-                                   nrhs, D->gxf, nullptr, k.fnorm, D->desc.rtol, k.tolabs, D->st));
+                                   nrhs, D->gxf, nullptr, k.fnorm, kInnerMargin * D->desc.rtol, k.tolabs, D->st));
   count(D, 5, 2);
   // Alg. 1 steps 1-3: q_a = A_a^{-1} f_a (into p's arm blocks), f'_c = f_c - sum R_ca q_a
-  FPG_TRY(arm_solves(D, D->f, p, nrhs, 5));
+  FPG_TRY(arm_solves_refined(D, D->f, p, D->tmp2, nrhs, 5));
   FPG_CUDA_TRY(launch_reduce_rhs(D->f, p, L.ntot, L.n, D->delta, L.ao, k.fc, nrhs, D->gx, D->st));
   count(D, 5, 1);
   FPG_CUDA_TRY(cudaMemsetAsync(k.u, 0, sizeof(double) * nrhs * L.nc, D->st));
@@ -429,16 +585,27 @@ fpg_status solve_launch(fpg_domain* D, double* p) {
       FPG_TRY(schur(D, zj, zprec, k.w, nrhs, k.active));
       ev_end(D, e);
       e = ev_begin(D, 2);
-      int nl = 0;
-      FPG_CUDA_TRY(launch_mgs(k.V, (long long)nrhs * L.nc, k.w, k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j, nrhs,
-                              k.part, kGmax, k.H, hcol, hrhs, k.active, D->gx, D->st, &nl));
-      count(D, 2, nl);
-      ev_end(D, e);
-      e = ev_begin(D, 3);
-      FPG_CUDA_TRY(launch_givens(k.H, hcol, hrhs, k.cs, k.sn, k.g, k.res, j, m, nrhs, k.tolabs, k.active, k.kcyc,
-                                 k.iters, D->desc.max_iters, D->st));
-      count(D, 3, 1);
-      ev_end(D, e);
+      const int csz = D->use_cluster ? arnoldi_cluster_size(L.nc) : 0;
+      if (csz > 0) {
+        // a3 + a4 fused: one cluster per right-hand side
+        FPG_CUDA_TRY(launch_arnoldi_cluster(csz, k.V, (long long)nrhs * L.nc, k.w,
+                                            k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j, nrhs, k.H, hcol, hrhs,
+                                            k.cs, k.sn, k.g, k.res, m, k.tolabs, k.active, k.kcyc, k.iters,
+                                            D->desc.max_iters, 1, D->st));
+        count(D, 2, 1);
+        ev_end(D, e);
+      } else {
+        int nl = 0;
+        FPG_CUDA_TRY(launch_mgs(k.V, (long long)nrhs * L.nc, k.w, k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j,
+                                nrhs, k.part, kGmax, k.H, hcol, hrhs, k.active, D->gx, D->st, &nl));
+        count(D, 2, nl);
+        ev_end(D, e);
+        e = ev_begin(D, 3);
+        FPG_CUDA_TRY(launch_givens(k.H, hcol, hrhs, k.cs, k.sn, k.g, k.res, j, m, nrhs, k.tolabs, k.active,
+                                   k.kcyc, k.iters, D->desc.max_iters, D->st));
+        count(D, 3, 1);
+        ev_end(D, e);
+      }
     }
     e = ev_begin(D, 4);
     FPG_CUDA_TRY(launch_cycle_end(k.H, hcol, hrhs, k.g, k.y, m, nrhs, k.kcyc, k.u, k.Z, zprec,
@@ -450,7 +617,7 @@ fpg_status solve_launch(fpg_domain* D, double* p) {
   e = ev_begin(D, 5);
   FPG_CUDA_TRY(launch_arm_rhs(D->f, k.u, L.ntot, L.n, D->delta, L.ao, D->tmp, p, nrhs, D->gxf, D->st));
   count(D, 5, 1);
-  FPG_TRY(arm_solves(D, D->tmp, p, nrhs, 5));
+  FPG_TRY(arm_solves_refined(D, D->tmp, p, D->tmp2, nrhs, 5));
   ev_end(D, e);
   // a7: global relative residual
   e = ev_begin(D, 6);
@@ -525,8 +692,9 @@ fpg_status fpg_workspace_bytes(const fpg_domain_desc* desc, size_t* bytes) {
   FPG_TRY(validate(desc));
   Layout L;
   make_layout(desc, &L);
+  HostPlan hp = plan_shape(desc->n);
   Carver c(nullptr);
-  carve(nullptr, desc, L, c);
+  carve(nullptr, desc, L, &hp, c);
   *bytes = c.used + 256;
   return FPG_OK;
 }
@@ -559,8 +727,9 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   }
   for (auto* t : {&D->tC64, &D->tC32}) { t->n = n; t->ns = n; t->delta = D->delta; }
   for (auto* t : {&D->tA64, &D->tA32}) { t->n = n; t->ns = n + 1; t->delta = D->delta; }
+  HostPlan hp = build_plan(n);
   Carver c(ws);
-  carve(D, desc, L, c);
+  carve(D, desc, L, &hp, c);
   const int nrhs = desc->nrhs;
   D->gx = pick_gx(L.nc, nrhs);
   D->gxf = pick_gx(L.ntot, nrhs);
@@ -571,24 +740,49 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   D->ks.gx = D->gx;
   D->h_done.assign(nrhs, 0);
   // host tables
-  std::vector<double> sint, pc, pa, ct;
-  fill_sintab(n, sint);
+  std::vector<double> pc, pa, ct;
   fill_pivots(n, n, D->delta, desc->kappa, pc);
   fill_pivots(n, n + 1, D->delta, desc->kappa, pa);
   fill_ctab(n, D->delta, pa, ct);
-  std::vector<float> sint32(sint.begin(), sint.end()), pc32(pc.begin(), pc.end()), pa32(pa.begin(), pa.end());
+  std::vector<float> pc32(pc.begin(), pc.end()), pa32(pa.begin(), pa.end());
+  std::vector<double> mc(pc.size()), ma(pa.size());
+  for (size_t i = 0; i < pc.size(); ++i) mc[i] = -D->delta * pc[i];
+  for (size_t i = 0; i < pa.size(); ++i) ma[i] = -D->delta * pa[i];
+  std::vector<float> mc32(mc.begin(), mc.end()), ma32(ma.begin(), ma.end());
+  std::vector<float> W32(hp.W.begin(), hp.W.end()), s32(hp.sinp.begin(), hp.sinp.end()),
+      B32(hp.Bhat.begin(), hp.Bhat.end()), d32(hp.dense.begin(), hp.dense.end());
   int arms[4] = {0, 0, 0, 0};
   for (int i = 0; i < L.narms; ++i) arms[i] = L.arm_slots[i];
   auto cp = [&](const void* dst, const void* src, size_t b) {
     return cudaMemcpyAsync(const_cast<void*>(dst), src, b, cudaMemcpyHostToDevice, D->st);
   };
   cudaError_t err = cudaSuccess;
-  if (!err) err = cp(D->tC64.sintab, sint.data(), sizeof(double) * sint.size());
-  if (!err) err = cp(D->tC32.sintab, sint32.data(), sizeof(float) * sint32.size());
+  {
+    const DstPlan& p64 = D->tC64.plan;
+    const DstPlan& p32 = D->tC32.plan;
+    if (!err) err = cp(p64.W, hp.W.data(), sizeof(double) * hp.W.size());
+    if (!err) err = cp(p32.W, W32.data(), sizeof(float) * W32.size());
+    if (!err) err = cp(p64.sinp, hp.sinp.data(), sizeof(double) * hp.sinp.size());
+    if (!err) err = cp(p32.sinp, s32.data(), sizeof(float) * s32.size());
+    if (!err) err = cp(p64.dense, hp.dense.data(), sizeof(double) * hp.dense.size());
+    if (!err) err = cp(p32.dense, d32.data(), sizeof(float) * d32.size());
+    if (hp.mode == DST_RADER) {
+      if (!err) err = cp(p64.Bhat, hp.Bhat.data(), sizeof(double) * hp.Bhat.size());
+      if (!err) err = cp(p32.Bhat, B32.data(), sizeof(float) * B32.size());
+      if (!err) err = cp(p64.pin, hp.pin.data(), sizeof(int) * hp.pin.size());
+      if (!err) err = cp(p64.pout, hp.pout.data(), sizeof(int) * hp.pout.size());
+      if (!err) err = cp(p32.pin, hp.pin.data(), sizeof(int) * hp.pin.size());
+      if (!err) err = cp(p32.pout, hp.pout.data(), sizeof(int) * hp.pout.size());
+    }
+  }
   if (!err) err = cp(D->tC64.rpiv, pc.data(), sizeof(double) * pc.size());
   if (!err) err = cp(D->tC32.rpiv, pc32.data(), sizeof(float) * pc32.size());
   if (!err) err = cp(D->tA64.rpiv, pa.data(), sizeof(double) * pa.size());
   if (!err) err = cp(D->tA32.rpiv, pa32.data(), sizeof(float) * pa32.size());
+  if (!err) err = cp(D->tC64.mneg, mc.data(), sizeof(double) * mc.size());
+  if (!err) err = cp(D->tC32.mneg, mc32.data(), sizeof(float) * mc32.size());
+  if (!err) err = cp(D->tA64.mneg, ma.data(), sizeof(double) * ma.size());
+  if (!err) err = cp(D->tA32.mneg, ma32.data(), sizeof(float) * ma32.size());
   if (!err) err = cp(D->ctab, ct.data(), sizeof(double) * ct.size());
   if (!err) err = cp(D->arms_dev, arms, sizeof(arms));
   if (!err) err = cudaMemsetAsync(D->f, 0, sizeof(double) * nrhs * L.ntot, D->st);
@@ -647,8 +841,8 @@ fpg_status fpg_solve_finish(fpg_domain* d, fpg_solve_info* info) {
 fpg_status fpg_solve_host(fpg_domain* d, const double* f_host, double* p_host, fpg_solve_info* info) {
   if (!d || !f_host || !p_host) return FPG_EINVAL;
   FPG_TRY(fpg_set_rhs_host(d, f_host, -1));
-  FPG_TRY(solve_launch(d, d->tmp));
-  FPG_CUDA_TRY(cudaMemcpyAsync(p_host, d->tmp, sizeof(double) * d->L.ntot * d->desc.nrhs, cudaMemcpyDeviceToHost,
+  FPG_TRY(solve_launch(d, d->pbuf));
+  FPG_CUDA_TRY(cudaMemcpyAsync(p_host, d->pbuf, sizeof(double) * d->L.ntot * d->desc.nrhs, cudaMemcpyDeviceToHost,
                                d->st));
   return collect_info(d, info);
 }
@@ -697,11 +891,19 @@ fpg_status fpg_apply_schur(fpg_domain* d, const void* z, int32_t zprec, double* 
 fpg_status fpg_arnoldi_mgs(fpg_domain* d, const double* V, int32_t j, double* w, double* h, int64_t len,
                            int32_t nvec) {
   if (!d || !V || !w || !h || j < 0 || len <= 0 || nvec <= 0 || nvec > d->desc.nrhs) return FPG_EINVAL;
-  int nl = 0;
-  // v_{j+1} overwrites w: normalise in place
-  FPG_CUDA_TRY(launch_mgs(V, (long long)nvec * len, w, w, len, j, nvec, d->ks.part, kGmax, h, 0, j + 2, nullptr,
-                          pick_gx(len, nvec), d->st, &nl));
-  d->launches += nl;
+  // v_{j+1} overwrites w: normalise in place; same kernel choice as the solver
+  const int csz = d->use_cluster ? arnoldi_cluster_size(len) : 0;
+  if (csz > 0) {
+    FPG_CUDA_TRY(launch_arnoldi_cluster(csz, V, (long long)nvec * len, w, w, len, j, nvec, h, 0, j + 2, nullptr,
+                                        nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0, 0,
+                                        d->st));
+    d->launches += 1;
+  } else {
+    int nl = 0;
+    FPG_CUDA_TRY(launch_mgs(V, (long long)nvec * len, w, w, len, j, nvec, d->ks.part, kGmax, h, 0, j + 2, nullptr,
+                            pick_gx(len, nvec), d->st, &nl));
+    d->launches += nl;
+  }
   return check_launch();
 }
 
@@ -736,6 +938,14 @@ fpg_status fpg_apply_global(fpg_domain* d, const double* p, double* y, int32_t n
                                    nvec, d->gxf, nullptr, nullptr, 0.0, nullptr, d->st));
   d->launches += 1;
   return check_launch();
+}
+
+fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
+  if (!d) return FPG_EINVAL;
+  switch (option) {
+    case FPG_OPT_ARNOLDI_CLUSTER: d->use_cluster = value != 0; return FPG_OK;
+    default: return FPG_EINVAL;
+  }
 }
 
 fpg_status fpg_set_profiling(fpg_domain* d, int32_t on) {

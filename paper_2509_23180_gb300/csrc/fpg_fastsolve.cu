@@ -57,7 +57,7 @@ __device__ __forceinline__ void dst_dense_lines(const T* lines, int nl, int n, i
 
 template <typename T>
 __global__ void __launch_bounds__(kFsThreads)
-k_dst_forward(const double* __restrict__ in, BatchDesc ib, LineLayout L, int n,
+k_dense_forward(const double* __restrict__ in, BatchDesc ib, LineLayout L, int n,
               const T* __restrict__ sintab_g, T* __restrict__ scratch, int lpb,
               const int* __restrict__ active, int nper_active) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -114,9 +114,143 @@ __global__ void k_thomas(T* __restrict__ scratch, int n, int ns, T delta, const 
   }
 }
 
+// The same Thomas recurrences, evaluated in parallel along the sweep: with
+// m_s = -delta r_s, the forward pass is y_s = r_s f_s + m_s y_{s-1} and the back
+// substitution x_s = y_s + m_s x_{s+1}.  Both are first-order linear recurrences,
+// so each warp takes one mode, its 32 lanes take contiguous chunks of rows, a
+// lane scan of the (chunk result, chunk multiplier) pairs supplies the carries
+// and a fix-up pass adds them.  Same operations as the sequential sweep up to
+// the association of the carries.  A CTA owns MT modes of one block, staged in
+// shared memory together with their r and m columns.
+template <typename T, int MT>
+__global__ void __launch_bounds__(256)
+k_thomas_scan(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv, const T* __restrict__ mneg,
+              const int* __restrict__ active, int nper_active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.y;
+  if (active != nullptr && !active[b / nper_active]) return;
+  constexpr int P = MT + 1;
+  const int k0 = blockIdx.x * MT;
+  const int mt = min(MT, n - k0);
+  T* xs = reinterpret_cast<T*>(smem_raw);
+  T* rs = xs + (size_t)ns * P;
+  T* ms = rs + (size_t)ns * P;
+  T* col = scratch + (long long)b * ns * n + k0;
+  for (int idx = threadIdx.x; idx < ns * MT; idx += blockDim.x) {
+    const int s = idx / MT, k = idx - s * MT;
+    if (k < mt) {
+      const long long g = (long long)s * n + k;
+      xs[s * P + k] = col[g];
+      rs[s * P + k] = rpiv[g + k0];
+      ms[s * P + k] = mneg[g + k0];
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int c = (ns + 31) / 32;
+  const int s0 = min(ns, lane * c), s1 = min(ns, s0 + c);
+  for (int k = warp; k < mt; k += nw) {
+    // forward: y_s = r_s f_s + m_s y_{s-1}
+    T acc = T(0), pr = T(1);
+    for (int s = s0; s < s1; ++s) {
+      const T m = ms[s * P + k];
+      acc = fma(m, acc, rs[s * P + k] * xs[s * P + k]);
+      pr *= m;
+      xs[s * P + k] = acc;
+    }
+    T Y = acc, Pp = pr;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T Yo = __shfl_up_sync(0xffffffffu, Y, o), Po = __shfl_up_sync(0xffffffffu, Pp, o);
+      if (lane >= o) {
+        Y = fma(Pp, Yo, Y);
+        Pp *= Po;
+      }
+    }
+    T cin = __shfl_up_sync(0xffffffffu, Y, 1);
+    if (lane == 0) cin = T(0);
+    if (cin != T(0)) {
+      T q = T(1);
+      for (int s = s0; s < s1; ++s) {
+        q *= ms[s * P + k];
+        xs[s * P + k] = fma(q, cin, xs[s * P + k]);
+      }
+    }
+    // backward: x_s = y_s + m_s x_{s+1}
+    acc = T(0);
+    pr = T(1);
+    for (int s = s1 - 1; s >= s0; --s) {
+      const T m = ms[s * P + k];
+      acc = fma(m, acc, xs[s * P + k]);
+      pr *= m;
+      xs[s * P + k] = acc;
+    }
+    Y = acc;
+    Pp = pr;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T Yo = __shfl_down_sync(0xffffffffu, Y, o), Po = __shfl_down_sync(0xffffffffu, Pp, o);
+      if (lane + o < 32) {
+        Y = fma(Pp, Yo, Y);
+        Pp *= Po;
+      }
+    }
+    T cdn = __shfl_down_sync(0xffffffffu, Y, 1);
+    if (lane == 31) cdn = T(0);
+    if (cdn != T(0)) {
+      T q = T(1);
+      for (int s = s1 - 1; s >= s0; --s) {
+        q *= ms[s * P + k];
+        xs[s * P + k] = fma(q, cdn, xs[s * P + k]);
+      }
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < ns * MT; idx += blockDim.x) {
+    const int s = idx / MT, k = idx - s * MT;
+    if (k < mt) col[(long long)s * n + k] = xs[s * P + k];
+  }
+}
+
+template <typename T, int MT>
+size_t thomas_smem(int ns) {
+  return 3 * sizeof(T) * (size_t)ns * (MT + 1);
+}
+
+// Launch the scanned Thomas solve with the widest mode tile that fits 64 KB.
+template <typename T>
+cudaError_t launch_thomas_scan(T* scratch, int n, int ns, const T* rpiv, const T* mneg, int nblk,
+                               const int* active, int nper_active, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_thomas_scan<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_thomas_scan<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_thomas_scan<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_thomas_scan<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_thomas_scan<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  const size_t budget = 64 * 1024;
+#define FPG_THOMAS_TRY(MTV)                                                                              \
+  if (thomas_smem<T, MTV>(ns) <= budget || MTV == 1) {                                                  \
+    dim3 grid((n + MTV - 1) / MTV, nblk);                                                               \
+    const int threads = 32 * (MTV < 8 ? MTV : 8);                                                       \
+    k_thomas_scan<T, MTV><<<grid, threads, thomas_smem<T, MTV>(ns), st>>>(scratch, n, ns, rpiv, mneg,  \
+                                                                         active, nper_active);          \
+    return cudaGetLastError();                                                                          \
+  }
+  FPG_THOMAS_TRY(16)
+  FPG_THOMAS_TRY(8)
+  FPG_THOMAS_TRY(4)
+  FPG_THOMAS_TRY(2)
+  FPG_THOMAS_TRY(1)
+#undef FPG_THOMAS_TRY
+  return cudaErrorInvalidValue;
+}
+
 template <typename T, typename To>
 __global__ void __launch_bounds__(kFsThreads)
-k_dst_inverse(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc ob, LineLayout L, int n,
+k_dense_inverse(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc ob, LineLayout L, int n,
               const T* __restrict__ sintab_g, int lpb, const int* __restrict__ active, int nper_active) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.y;
@@ -142,6 +276,71 @@ k_dst_inverse(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc ob,
   });
 }
 
+// FFT engine versions: 2Q lines per CTA.
+template <typename T>
+__global__ void __launch_bounds__(kFsThreads)
+k_fft_forward(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPlan pl, T* __restrict__ scratch,
+              int Q, const int* __restrict__ active, int nper_active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.y;
+  if (active != nullptr && !active[b / nper_active]) return;
+  const int n = pl.n;
+  const int lpb = 2 * Q;
+  const int s0 = blockIdx.x * lpb;
+  const int nl = min(lpb, L.ns - s0);
+  DstSmem<T> sm = dst_smem_carve<T>(smem_raw, pl, Q);
+  dst_load_tables<T>(pl, sm);
+  const double* src = batch_ptr(in, ib, b);
+  const int total = lpb * n;
+  if (L.st == 1) {
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int l = idx / n, t = idx - l * n;
+      sm.xin[idx] = l < nl ? (T)src[t + (long long)(s0 + l) * L.ss] : T(0);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int t = idx / lpb, l = idx - t * lpb;
+      sm.xin[l * n + t] = l < nl ? (T)src[(long long)t * L.st + (long long)(s0 + l) * L.ss] : T(0);
+    }
+  }
+  __syncthreads();
+  const T* y = dst_lines<T>(pl, sm, Q);
+  T* dst = scratch + ((long long)b * L.ns + s0) * n;
+  for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) dst[idx] = y[idx];
+}
+
+template <typename T, typename To>
+__global__ void __launch_bounds__(kFsThreads)
+k_fft_inverse(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc ob, LineLayout L, DstPlan pl, int Q,
+              const int* __restrict__ active, int nper_active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.y;
+  if (active != nullptr && !active[b / nper_active]) return;
+  const int n = pl.n;
+  const int lpb = 2 * Q;
+  const int s0 = blockIdx.x * lpb;
+  const int nl = min(lpb, L.ns - s0);
+  DstSmem<T> sm = dst_smem_carve<T>(smem_raw, pl, Q);
+  dst_load_tables<T>(pl, sm);
+  const T* src = scratch + ((long long)b * L.ns + s0) * n;
+  for (int idx = threadIdx.x; idx < lpb * n; idx += blockDim.x) sm.xin[idx] = idx < nl * n ? src[idx] : T(0);
+  __syncthreads();
+  const T* y = dst_lines<T>(pl, sm, Q);
+  To* dst = batch_ptr_out(out, ob, b);
+  const T scale = T(2) / T(n + 1);
+  if (L.st == 1) {
+    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+      const int l = idx / n, k = idx - l * n;
+      dst[k + (long long)(s0 + l) * L.ss] = (To)(y[idx] * scale);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+      const int k = idx / nl, l = idx - k * nl;
+      dst[(long long)k * L.st + (long long)(s0 + l) * L.ss] = (To)(y[l * n + k] * scale);
+    }
+  }
+}
+
 template <typename T>
 int lines_per_block(int n) {
   const size_t budget = 96 * 1024;
@@ -158,26 +357,47 @@ size_t fs_smem_bytes(int n, int lpb) {
   return sizeof(T) * (2 * (n + 1) + (size_t)lpb * (n + 1));
 }
 
+// Line pairs per CTA for the FFT kernels: as many as fit ~100 KB of shared
+// memory (two CTAs per SM), reduced while the grid has fewer than two CTAs per SM.
+template <typename T>
+int pairs_per_block(const DstPlan& pl, int ns, int nblk) {
+  int Q = 8;
+  while (Q > 1 && dst_smem_bytes<T>(pl.p, pl.N, Q, pl.mode) > 100 * 1024) --Q;
+  while (Q > 1 && (long long)nblk * ((ns + 2 * Q - 1) / (2 * Q)) < 2 * 152) --Q;
+  return Q;
+}
+
 template <typename T, typename To>
 cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib,
                             To* out, BatchDesc ob, int nblk, T* scratch, const int* active,
                             int nper_active, cudaStream_t st) {
   const int n = tb.n;
-  const int lpb = lines_per_block<T>(n);
-  const size_t smem = fs_smem_bytes<T>(n, lpb);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_dst_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_dst_inverse<T, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dense_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dense_inverse<T, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fft_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fft_inverse<T, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  dim3 grid((L.ns + lpb - 1) / lpb, nblk);
-  k_dst_forward<T><<<grid, kFsThreads, smem, st>>>(in, ib, L, n, (const T*)tb.sintab, scratch, lpb,
-                                                    active, nper_active);
-  dim3 tg((n + 127) / 128, nblk);
-  k_thomas<T><<<tg, 128, 0, st>>>(scratch, n, L.ns, (T)tb.delta, (const T*)tb.rpiv, active, nper_active);
-  k_dst_inverse<T, To><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, n, (const T*)tb.sintab, lpb,
-                                                        active, nper_active);
+  const DstPlan& pl = tb.plan;
+  if (pl.mode == DST_DENSE) {
+    const int lpb = lines_per_block<T>(n);
+    const size_t smem = fs_smem_bytes<T>(n, lpb);
+    dim3 grid((L.ns + lpb - 1) / lpb, nblk);
+    k_dense_forward<T><<<grid, kFsThreads, smem, st>>>(in, ib, L, n, (const T*)pl.dense, scratch, lpb, active,
+                                                      nper_active);
+    launch_thomas_scan<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st);
+    k_dense_inverse<T, To><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, n, (const T*)pl.dense, lpb,
+                                                          active, nper_active);
+    return cudaGetLastError();
+  }
+  const int Q = pairs_per_block<T>(pl, L.ns, nblk);
+  const size_t smem = dst_smem_bytes<T>(pl.p, pl.N, Q, pl.mode);
+  dim3 grid((L.ns + 2 * Q - 1) / (2 * Q), nblk);
+  k_fft_forward<T><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
+  launch_thomas_scan<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st);
+  k_fft_inverse<T, To><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "fpg.h"
+#include "fpg_dst.cuh"
 
 namespace fpg {
 
@@ -32,8 +33,9 @@ struct FastSolveTables {
   int n;              // transform length (= domain n)
   int ns;             // sweep length
   double delta;       // 1/h^2
-  const void* sintab; // sin(pi m/(n+1)), m = 0..2(n+1)-1, in the compute precision
-  const void* rpiv;   // Thomas reciprocal pivots, [ns][n], compute precision
+  DstPlan plan;       // DST-I plan and tables in the compute precision
+  const void* rpiv;   // Thomas reciprocal pivots r_s, [ns][n], compute precision
+  const void* mneg;   // -delta r_s, [ns][n], compute precision
 };
 
 // Offsets of the arm blocks W, E, S, N inside one full vector (-1 = absent).
@@ -86,6 +88,12 @@ void record_cuda_error(cudaError_t e, const char* where);
       fpg::record_cuda_error(_e, #expr);                     \
       return FPG_ECUDA;                                      \
     }                                                        \
+  } while (0)
+
+#define FPG_TRY(x)               \
+  do {                           \
+    fpg_status _s = (x);         \
+    if (_s != FPG_OK) return _s; \
   } while (0)
 
 // ---------------------------------------------------------------------------

@@ -5,6 +5,7 @@
 // Reductions are deterministic: each CTA reduces its share in a fixed tree and
 // writes one partial; the consumer sums the partials of a right-hand side in a
 // fixed order (one warp), so a result never depends on scheduling.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "fpg_internal.cuh"
@@ -210,6 +211,97 @@ k_mgs_normalize(const double* __restrict__ w, double* __restrict__ vout, long lo
 }
 
 // ---------------------------------------------------------------------------
+// a3 + a4 in one launch: one thread-block cluster per right-hand side runs the
+// whole modified Gram-Schmidt chain of Arnoldi step j.  Each CTA owns a slice
+// of the vector; the dot product of every MGS step is reduced inside the CTA,
+// its per-CTA partials are exchanged through distributed shared memory after a
+// cluster barrier, and every CTA sums them in the same rank order (so all CTAs
+// hold the identical h).  The tail normalises v_{j+1} and, in rank 0, applies
+// the Givens step of column j (same arithmetic as k_givens).
+__global__ void __launch_bounds__(kThreads)
+k_arnoldi_cluster(const double* __restrict__ V, long long vstride, double* __restrict__ w, double* __restrict__ vout,
+                  long long len, int j, double* __restrict__ H, int hcol_stride, int hrhs_stride,
+                  double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g, double* __restrict__ res,
+                  int m, const double* __restrict__ tolabs, int* __restrict__ active, int* __restrict__ kcyc,
+                  int* __restrict__ iters, int max_iters, int do_givens) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int csz = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int r = blockIdx.x / csz;
+  __shared__ double red[32];
+  __shared__ double part[2];
+  __shared__ double hval;
+  if (active != nullptr && !active[r]) return;  // uniform over the cluster
+  const long long chunk = (len + csz - 1) / csz;
+  const long long lo = (long long)rank * chunk;
+  const long long hi = lo + chunk < len ? lo + chunk : len;
+  double* wr = w + (long long)r * len;
+  double hprev = 0.0;
+  for (int k = 0; k <= j + 1; ++k) {
+    const double* vp = (k >= 1) ? V + (long long)(k - 1) * vstride + (long long)r * len : nullptr;
+    const double* vk = (k <= j) ? V + (long long)k * vstride + (long long)r * len : nullptr;
+    double acc = 0.0;
+    for (long long idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
+      double wv = wr[idx];
+      if (vp) {
+        wv = fma(-hprev, vp[idx], wv);
+        wr[idx] = wv;
+      }
+      acc = vk ? fma(wv, vk[idx], acc) : fma(wv, wv, acc);
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) part[k & 1] = acc;
+    cl.sync();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int q = 0; q < csz; ++q) sum += *cl.map_shared_rank(&part[k & 1], q);
+      hval = sum;
+    }
+    __syncthreads();
+    hprev = hval;
+    if (rank == 0 && threadIdx.x == 0 && k <= j) H[(long long)r * hrhs_stride + (long long)j * hcol_stride + k] = hprev;
+  }
+  const double hn = sqrt(hprev);
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  double* vr = vout + (long long)r * len;
+  for (long long idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) vr[idx] = wr[idx] * inv;
+  if (rank == 0 && threadIdx.x == 0) {
+    double* h = H + (long long)r * hrhs_stride + (long long)j * hcol_stride;
+    h[j + 1] = hn;
+    if (do_givens) {
+      double* c = cs + (long long)r * m;
+      double* s = sn + (long long)r * m;
+      double* gr = g + (long long)r * (m + 1);
+      for (int i = 0; i < j; ++i) {
+        const double a = h[i], b = h[i + 1];
+        h[i] = c[i] * a + s[i] * b;
+        h[i + 1] = -s[i] * a + c[i] * b;
+      }
+      const double a = h[j], b = h[j + 1];
+      const double rr = hypot(a, b);
+      double cc = 1.0, ss = 0.0;
+      if (rr != 0.0) {
+        cc = a / rr;
+        ss = b / rr;
+      }
+      c[j] = cc;
+      s[j] = ss;
+      h[j] = rr;
+      h[j + 1] = 0.0;
+      gr[j + 1] = -ss * gr[j];
+      gr[j] = cc * gr[j];
+      const double rj = fabs(gr[j + 1]);
+      res[r] = rj;
+      kcyc[r] = j + 1;
+      iters[r] += 1;
+      if (rj <= tolabs[r] || b == 0.0 || iters[r] >= max_iters) active[r] = 0;
+    }
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// ---------------------------------------------------------------------------
 // a4: Givens step on column j, one thread per right-hand side.
 __global__ void k_givens(double* __restrict__ H, int hcol_stride, int hrhs_stride, double* __restrict__ cs,
                          double* __restrict__ sn, double* __restrict__ g, double* __restrict__ res, int j,
@@ -411,6 +503,50 @@ k_arm_rhs(const double* __restrict__ f, const double* __restrict__ u, long long 
   }
 }
 
+// a6 refinement: out_a = rhs_a - A_a x_a on every arm block (A_a: the arm's own
+// 5-point operator, its interface line treated as Dirichlet), full-vector layout.
+__global__ void __launch_bounds__(kThreads)
+k_arm_residual(const double* __restrict__ rhs, const double* __restrict__ x, double* __restrict__ out,
+               long long ntot, int n, double delta, double kappa, ArmOffsets ao) {
+  const int r = blockIdx.y;
+  const long long na = (long long)n * (n + 1);
+  for (int a = 0; a < 4; ++a) {
+    const long long off = ao.off[a];
+    if (off < 0) continue;
+    const int nx = a < 2 ? n + 1 : n, ny = a < 2 ? n : n + 1;
+    const double* xr = x + (long long)r * ntot + off;
+    const double* fr = rhs + (long long)r * ntot + off;
+    double* o = out + (long long)r * ntot + off;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < na;
+         idx += (long long)gridDim.x * blockDim.x) {
+      const int j = (int)(idx / nx), i = (int)(idx - (long long)j * nx);
+      const double xc = xr[idx];
+      double s = -4.0 * xc;
+      if (i > 0) s += xr[idx - 1];
+      if (i < nx - 1) s += xr[idx + 1];
+      if (j > 0) s += xr[idx - nx];
+      if (j < ny - 1) s += xr[idx + nx];
+      o[idx] = fr[idx] - fma(delta, s, kappa * xc);
+    }
+  }
+}
+
+// x_a += e_a on every arm block.
+__global__ void __launch_bounds__(kThreads)
+k_arm_add(double* __restrict__ x, const double* __restrict__ e, long long ntot, int n, ArmOffsets ao) {
+  const int r = blockIdx.y;
+  const long long na = (long long)n * (n + 1);
+  for (int a = 0; a < 4; ++a) {
+    const long long off = ao.off[a];
+    if (off < 0) continue;
+    double* xr = x + (long long)r * ntot + off;
+    const double* er = e + (long long)r * ntot + off;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < na;
+         idx += (long long)gridDim.x * blockDim.x)
+      xr[idx] += er[idx];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Global operator K (a7): value of the neighbour (di, dj) of local node (i, j)
 // of block `blk` (0 = C, 1..4 = W, E, S, N); zero on the domain's edge.
@@ -587,6 +723,42 @@ cudaError_t launch_mgs(const double* V, long long vstride, double* w, double* vo
   return cudaGetLastError();
 }
 
+// Cluster size for the fused Arnoldi kernel, 0 when the multi-launch MGS is
+// the better choice (long vectors: a 16-CTA cluster would leave the GPU idle).
+int arnoldi_cluster_size(long long len) {
+  if (len > 262144) return 0;
+  long long c = (len + 2047) / 2048;
+  if (c > 16) c = 16;
+  if (c < 1) c = 1;
+  return (int)c;
+}
+
+cudaError_t launch_arnoldi_cluster(int csz, const double* V, long long vstride, double* w, double* vout,
+                                   long long len, int j, int nrhs, double* H, int hcol_stride, int hrhs_stride,
+                                   double* cs, double* sn, double* g, double* res, int m, const double* tolabs,
+                                   int* active, int* kcyc, int* iters, int max_iters, int do_givens,
+                                   cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_arnoldi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(csz * nrhs, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = csz;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_arnoldi_cluster, V, vstride, w, vout, len, j, H, hcol_stride, hrhs_stride, cs,
+                            sn, g, res, m, tolabs, active, kcyc, iters, max_iters, do_givens);
+}
+
 cudaError_t launch_givens(double* H, int hcol_stride, int hrhs_stride, double* cs, double* sn, double* g,
                           double* res, int j, int m, int nrhs, const double* tolabs, int* active, int* kcyc,
                           int* iters, int max_iters, cudaStream_t st) {
@@ -628,6 +800,20 @@ cudaError_t launch_arm_rhs(const double* f, const double* u, long long ntot, int
                            double* out, double* p, int nrhs, int gx, cudaStream_t st) {
   dim3 grid(gx, nrhs);
   k_arm_rhs<<<grid, kThreads, 0, st>>>(f, u, ntot, n, delta, ao, out, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_arm_residual(const double* rhs, const double* x, double* out, long long ntot, int n, double delta,
+                                double kappa, ArmOffsets ao, int nrhs, int gx, cudaStream_t st) {
+  dim3 grid(gx, nrhs);
+  k_arm_residual<<<grid, kThreads, 0, st>>>(rhs, x, out, ntot, n, delta, kappa, ao);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_arm_add(double* x, const double* e, long long ntot, int n, ArmOffsets ao, int nrhs, int gx,
+                           cudaStream_t st) {
+  dim3 grid(gx, nrhs);
+  k_arm_add<<<grid, kThreads, 0, st>>>(x, e, ntot, n, ao);
   return cudaGetLastError();
 }
 

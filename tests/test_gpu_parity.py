@@ -42,7 +42,10 @@ BLOCK_NAMES = ["C", "W", "E", "S", "N"]
 
 
 # ---------------------------------------------------------------- a1 fast solve
-@pytest.mark.parametrize("n", [2, 7, 16, 33, 64, 100])
+# n covers every DST plan kind: p = n + 1 = 3, 8, 17 (radix 17), 34, 65 (5*13),
+# 101 and 89 (Rader), 94 (dense fallback), 129 (3*43), 257 (Rader, 4^4),
+# 513 (3^3*19), 1025 (5^2*41).
+@pytest.mark.parametrize("n", [2, 7, 16, 33, 64, 100, 88, 93, 128, 256, 512, 1024])
 def test_fast_solve_eigenmodes(lib, n):
     """A^{-1} of a rectangle mode is the mode over its closed-form eigenvalue."""
     from paper_2509_23180_gb300 import binding as B
@@ -114,7 +117,8 @@ def test_schur_matvec_vs_oracle(lib, mode, geom, n, kappa):
 
 
 # ---------------------------------------------------------------- a3 Arnoldi
-@pytest.mark.parametrize("j,length", [(0, 1000), (3, 4096), (12, 70001)])
+# lengths up to 262144 run the cluster kernel, longer ones the multi-launch MGS
+@pytest.mark.parametrize("j,length", [(0, 1000), (3, 4096), (12, 70001), (5, 300007)])
 def test_arnoldi_mgs_vs_oracle(lib, j, length):
     from paper_2509_23180_gb300 import binding as B
     d = domain(B, "cross", 8, 0.0, nrhs=2)
@@ -289,6 +293,24 @@ def test_restart_and_noconv(lib):
     assert info[0]["iterations"] <= 3
 
 
+@pytest.mark.parametrize("cluster", [0, 1])
+def test_arnoldi_paths_agree_in_solve(lib, cluster):
+    """The cluster-fused and the multi-launch Arnoldi give the same solution."""
+    from paper_2509_23180_gb300 import binding as B
+    n = 48
+    K = O.assemble("cross", n, -10.0)
+    f = W.rhs_batch("cross", n, [1, 2, 3], kind="fourier")
+    d = domain(B, "cross", n, -10.0, nrhs=3, rtol=1e-12)
+    d.set_option(B.OPT_ARNOLDI_CLUSTER, cluster)
+    d.set_rhs(dev(f))
+    p = torch.zeros_like(dev(f))
+    st, info = d.solve(p)
+    assert st == B.FPG_OK
+    ref = D.Factor(K).solve(f)
+    for r in range(3):
+        assert rel(host(p)[r], ref[r]) < 1e-9
+
+
 def test_schur_modes_agree_in_solve(lib):
     from paper_2509_23180_gb300 import binding as B
     n = 40
@@ -324,3 +346,19 @@ def test_full_size_256_bench_configuration(lib, kappa):
     for r in range(10):
         assert O.global_residual(K, f[r], P[r]) <= 1.01e-10
         assert rel(P[r], ref[r]) < 1e-9
+
+
+def test_solve_host_matches_device_path(lib):
+    """fpg_solve_host (host buffers, copies inside) gives the device path's answer."""
+    from paper_2509_23180_gb300 import binding as B
+    n = 30
+    f = W.rhs_batch("L", n, [4, 5], kind="fourier")
+    d = domain(B, "L", n, -10.0, nrhs=2, rtol=1e-11)
+    fh = torch.as_tensor(f).pin_memory()
+    ph = torch.zeros_like(fh).pin_memory()
+    st, info = d.solve_host(fh, ph)
+    assert st == B.FPG_OK
+    d.set_rhs(dev(f))
+    p = torch.zeros_like(dev(f))
+    d.solve(p)
+    assert np.array_equal(ph.numpy(), host(p))
