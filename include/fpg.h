@@ -173,6 +173,35 @@ fpg_status fpg_global_residual(fpg_domain* d, const double* f_dev, const double*
 /* Global operator y = K p for nvec full vectors (block order). */
 fpg_status fpg_apply_global(fpg_domain* d, const double* p_dev, double* y_dev, int32_t nvec);
 
+/* ---- fast solve without allocation ---------------------------------------------
+ *
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot call cudaMalloc and cannot hand fpg_create_domain a workspace -- code
+ * running inside another framework's memory pool, on a path whose device memory
+ * was fixed in advance, or in a context where allocating would stall or fail.
+ *
+ * fpg_fast_solve_noalloc computes z = A^{-1} v, the fast solve of the centre
+ * block, for nvec n x n Dirichlet squares (spacing h = 1/(n+1), shift kappa,
+ * each v and z n*n doubles, row-major), with the library's fast-solve kernels.
+ * Its scratch (spectral coefficients and the DST / Thomas tables) is one
+ * file-scope device array of about 20 MiB that every GPU loading the library
+ * holds until the process exits; no device or host memory is allocated.
+ *   - Limits: 2 <= n <= FPG_NOALLOC_MAX_N, nvec * n * n <= FPG_NOALLOC_MAX_POINTS,
+ *     kappa <= 0.  Anything beyond returns FPG_EINVAL, the reason readable
+ *     from fpg_last_cuda_error().
+ *   - The first call on a device performs that device's set-up (it looks up
+ *     the array's device address); make that first call before any stream
+ *     capture.  A call whose (n, kappa) differs from the previous call's
+ *     rebuilds the tables on the host, copies them on `stream` and waits for
+ *     that stream.
+ *   - Every call shares the one array and leaves its contents behind: calls
+ *     that overlap on the GPU (other streams, other threads) race.
+ * v_dev, z_dev: device pointers owned by the caller; stream: a cudaStream_t. */
+#define FPG_NOALLOC_MAX_N 512
+#define FPG_NOALLOC_MAX_POINTS (1LL << 21)
+fpg_status fpg_fast_solve_noalloc(int32_t n, double kappa, const double* v_dev, double* z_dev,
+                                  int32_t nvec, void* stream);
+
 /* ---- options --------------------------------------------------------------- */
 
 typedef enum {

@@ -70,6 +70,7 @@ _SIGS = {
     "fpg_phase_stats": ([_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D)], _I32),
     "fpg_launch_count": ([_P, ctypes.POINTER(_I64)], _I32),
     "fpg_probe_fma_peak": ([_I32, ctypes.POINTER(_D)], _I32),
+    "fpg_fast_solve_noalloc": ([_I32, _D, _P, _P, _I32, _P], _I32),
 }
 EXPORTED = tuple(_SIGS)
 

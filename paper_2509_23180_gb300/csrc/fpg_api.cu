@@ -66,6 +66,8 @@ void record_cuda_error(cudaError_t e, const char* where) {
   snprintf(g_last_err, sizeof(g_last_err), "%s: %s", cudaGetErrorString(e), where);
 }
 
+void record_message(const char* msg) { snprintf(g_last_err, sizeof(g_last_err), "%s", msg); }
+
 }  // namespace fpg
 
 using namespace fpg;
