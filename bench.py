@@ -22,6 +22,7 @@ import subprocess
 import sys
 import tempfile
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -42,6 +43,8 @@ def parse():
     ap.add_argument("--seeds", type=int, default=10)
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--schedule", default="concurrent", choices=["sequential", "concurrent"],
+                    help="solve the two kappa domains one after the other, or concurrently on two streams")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -52,7 +55,8 @@ def workload(args):
             "geometry": "cross", "n": args.n, "unknowns_per_rhs": args.n ** 2 + 4 * args.n * (args.n + 1),
             "kappas": [0.0, -10.0], "rhs_per_kappa": args.seeds, "solves_per_step": 2 * args.seeds,
             "restart": args.restart, "rtol": args.rtol, "precond_precision": args.precision,
-            "schur_mode": "reduced", "l2": "flushed before every step (512 MiB write)"}
+            "schur_mode": "reduced", "schedule": args.schedule,
+            "l2": "flushed before every step (512 MiB write)"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -183,6 +187,83 @@ def algorithmic_costs(n, iters_per_solve, m):
             "per_solve_bytes": per_iter_bytes * iters_per_solve}
 
 
+class Runner:
+    """The workload on the GPU: one domain per kappa, each with its own stream and
+    host thread (the library call releases the GIL), solved concurrently."""
+
+    def __init__(self, args, f_host, precision, nrhs, flush, concurrent=False):
+        import torch
+        from paper_2509_23180_gb300 import binding as B
+        self.torch, self.B = torch, B
+        self.kappas = tuple(f_host)
+        self.nrhs = nrhs
+        self.args = args
+        self.flush = flush
+        self.main = torch.cuda.Stream()
+        self.streams, self.doms, self.fdev, self.pdev = {}, {}, {}, {}
+        for k in self.kappas:
+            self.streams[k] = torch.cuda.Stream()
+            desc = B.make_desc("cross", args.n, k, nrhs=nrhs, restart=args.restart, rtol=args.rtol,
+                               precond_precision=precision)
+            self.doms[k] = B.Domain(desc, stream=self.streams[k])
+            self.fdev[k] = torch.as_tensor(f_host[k], device="cuda")
+            self.pdev[k] = torch.zeros_like(self.fdev[k])
+        self.pool = ThreadPoolExecutor(max_workers=len(self.kappas))
+        self.concurrent = concurrent
+        torch.cuda.synchronize()
+
+    def _solve_domain(self, k):
+        out = []
+        total = self.fdev[k].shape[0]
+        for s0 in range(0, total, self.nrhs):
+            self.doms[k].set_rhs(self.fdev[k][s0:s0 + self.nrhs])
+            st, info = self.doms[k].solve(self.pdev[k][s0:s0 + self.nrhs], check=False)
+            out += [(st, i) for i in info]
+        return out
+
+    def timed_step(self, s):
+        """Device time of one step: an event on `main` starts it after the L2
+        flush, both domain streams wait on it, `main` waits on both to end it."""
+        torch = self.torch
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(self.main):
+            self.flush.fill_(float(s))
+            a.record(self.main)
+        for k in self.kappas:
+            self.streams[k].wait_event(a)
+        if self.concurrent:
+            res = list(self.pool.map(self._solve_domain, self.kappas))
+        else:
+            res = [self._solve_domain(k) for k in self.kappas]
+        for k in self.kappas:
+            e = torch.cuda.Event()
+            e.record(self.streams[k])
+            self.main.wait_event(e)
+        b.record(self.main)
+        return a, b, [x for r in res for x in r]
+
+    def launches(self):
+        return sum(self.doms[k].launch_count() for k in self.kappas)
+
+    def set_profiling(self, on):
+        for k in self.kappas:
+            self.doms[k].set_profiling(on)
+
+    def phases(self):
+        out = {}
+        for k in self.kappas:
+            for name, v in self.doms[k].phase_stats().items():
+                ph = out.setdefault(name, {"launches": 0, "ms": 0.0})
+                ph["launches"] += v["launches"]
+                ph["ms"] += v["ms"]
+        return out
+
+    def close(self):
+        for k in self.kappas:
+            self.doms[k].close()
+        self.pool.shutdown()
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -198,57 +279,30 @@ def run_ours(args, rank, world):
         Bd.build()
     B.load()
     seeds = list(range(args.seeds))
-    kappas = (0.0, -10.0)
-    f_host = {k: W.rhs_batch("cross", args.n, seeds, kind="fourier") for k in kappas}
-    doms, fdev, pdev = {}, {}, {}
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        for k in kappas:
-            desc = B.make_desc("cross", args.n, k, nrhs=args.seeds, restart=args.restart, rtol=args.rtol,
-                               precond_precision=args.precision)
-            doms[k] = B.Domain(desc, stream=stream)
-            fdev[k] = torch.as_tensor(f_host[k], device="cuda")
-            pdev[k] = torch.zeros_like(fdev[k])
+    f_host = {k: W.rhs_batch("cross", args.n, seeds, kind="fourier") for k in (0.0, -10.0)}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-
-    def step(profile=False):
-        infos = []
-        for k in kappas:
-            doms[k].set_rhs(fdev[k])
-            st, info = doms[k].solve(pdev[k], check=False)
-            infos.append((st, info))
-        return infos
-
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step()
+    run = Runner(args, f_host, args.precision, args.seeds, flush, args.schedule == "concurrent")
+    for s in range(args.warmup):
+        run.timed_step(s)
+    torch.cuda.synchronize()
+    run.set_profiling(True)
+    launches0 = run.launches()
+    evs, infos = [], []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev_index) as clk:
+        for s in range(args.steps):
+            a, b, out = run.timed_step(s)
+            evs.append((a, b))
+            infos += out
         torch.cuda.synchronize()
-        for k in kappas:
-            doms[k].set_profiling(True)
-        launches0 = sum(doms[k].launch_count() for k in kappas)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        step_infos = []
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        with ClockSampler(dev_index) as clk:
-            for s in range(args.steps):
-                flush.fill_(float(s))
-                ev[s][0].record(stream)
-                step_infos.append(step())
-                ev[s][1].record(stream)
-            torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        launches = sum(doms[k].launch_count() for k in kappas) - launches0
-        step_ms = [a.elapsed_time(b) for a, b in ev]
-        phases = {}
-        for k in kappas:
-            for name, v in doms[k].phase_stats().items():
-                ph = phases.setdefault(name, {"launches": 0, "ms": 0.0})
-                ph["launches"] += v["launches"]
-                ph["ms"] += v["ms"]
-            doms[k].set_profiling(False)
+    if world > 1:
+        torch.distributed.barrier()
+    launches = run.launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    phases = run.phases()
+    run.set_profiling(False)
 
     total_ms = sum(step_ms)
     if world > 1:
@@ -258,40 +312,32 @@ def run_ours(args, rank, world):
     ms_per_step = total_ms / args.steps
     solves_per_step = 2 * args.seeds
     value = world * solves_per_step / (ms_per_step * 1e-3)
-
-    # correctness of every timed solve (device residuals)
-    resid = [i["residual"] for step_i in step_infos for (_, info) in step_i for i in info]
-    iters = [i["iterations"] for step_i in step_infos for (_, info) in step_i for i in info]
-    ok = all(st == B.FPG_OK for step_i in step_infos for (st, _) in step_i)
+    resid = [i["residual"] for _, i in infos]
+    iters = [i["iterations"] for _, i in infos]
+    ok = all(st == B.FPG_OK for st, _ in infos)
 
     # e2e: host buffers through fpg_solve_host, copies inside the timed region
-    fpin = {k: torch.as_tensor(f_host[k]).pin_memory() for k in kappas}
-    ppin = {k: torch.empty_like(fpin[k]).pin_memory() for k in kappas}
-    with torch.cuda.stream(stream):
-        for k in kappas:  # warm the pinned path once
-            doms[k].solve_host(fpin[k], ppin[k])
-        torch.cuda.synchronize()
+    fpin = {k: torch.as_tensor(f_host[k]).pin_memory() for k in f_host}
+    ppin = {k: torch.empty_like(fpin[k]).pin_memory() for k in f_host}
+    host_solve = lambda k: run.doms[k].solve_host(fpin[k], ppin[k])
+    list(run.pool.map(host_solve, f_host))  # warm the pinned path once
+    torch.cuda.synchronize()
     e2e_total = 0.0
-    with torch.cuda.stream(stream):
-        for s in range(args.steps):
-            flush.fill_(float(s))
-            torch.cuda.synchronize()
-            ta = time.perf_counter()
-            for k in kappas:
-                doms[k].solve_host(fpin[k], ppin[k])
-            e2e_total += time.perf_counter() - ta
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        list(run.pool.map(host_solve, f_host))
+        e2e_total += time.perf_counter() - ta
     e2e_val = world * solves_per_step * args.steps / e2e_total
-    bytes_h2d = sum(fpin[k].numel() * 8 for k in kappas)
+    bytes_h2d = sum(fpin[k].numel() * 8 for k in f_host)
 
-    # roofline of the dominant kernel group, from the in-run phase events
     iters_mean = float(np.mean(iters)) if iters else 0.0
     costs = algorithmic_costs(args.n, iters_mean, args.restart)
     peaks = measured_peaks()
     fp64_peak = B.probe_fma_peak(64)
     fp32_peak = B.probe_fma_peak(32)
-    dom_phase = max(("precond", "arnoldi", "schur"), key=lambda p: phases[p]["ms"])
-    roof = roofline(dom_phase, phases, costs, args, peaks, fp64_peak, fp32_peak, args.seeds, kappas)
-
+    roof = roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, args.seeds)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -310,61 +356,41 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": bytes_h2d},
         "clocks": clk.summary(),
     }
+    run.close()
     if rank == 0 and not args.no_variants:
-        line["variants"] = variants(args, f_host, stream, flush)
+        line["variants"] = variants(args, f_host, flush)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, f_host)
-    for k in kappas:
-        doms[k].close()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def variants(args, f_host, stream, flush):
-    """Same workload, other forms of the method (device-timed, L2 flushed)."""
+def variants(args, f_host, flush):
+    """Same workload and schedule, other forms of the method (device-timed)."""
     import torch
     from paper_2509_23180_gb300 import binding as B
-    out = {}
-    kappas = (0.0, -10.0)
-    forms = {"fp32_precond": dict(precond_precision=32, nrhs=args.seeds),
-             "fp64_single_rhs": dict(precond_precision=64, nrhs=1)}
+    other = args.schedule != "concurrent"
+    forms = {"fp32_precond": (32, args.seeds, False), "fp64_single_rhs": (64, 1, False),
+             ("fp64_concurrent" if other else "fp64_sequential"): (64, args.seeds, other)}
     if args.precision == 32:
-        forms = {"fp64_plain": dict(precond_precision=64, nrhs=args.seeds)}
-    for name, kw in forms.items():
-        with torch.cuda.stream(stream):
-            doms = {k: B.Domain(B.make_desc("cross", args.n, k, restart=args.restart, rtol=args.rtol, **kw),
-                                stream=stream) for k in kappas}
-            nr = kw["nrhs"]
-            fd = {k: torch.as_tensor(f_host[k], device="cuda") for k in kappas}
-            pd = {k: torch.zeros_like(fd[k]) for k in kappas}
-
-            def one_step():
-                its = []
-                for k in kappas:
-                    for s0 in range(0, args.seeds, nr):
-                        doms[k].set_rhs(fd[k][s0:s0 + nr])
-                        st, info = doms[k].solve(pd[k][s0:s0 + nr], check=False)
-                        its += [(st, i) for i in info]
-                return its
-            one_step()
+        forms = {"fp64_plain": (64, args.seeds, False)}
+    out = {}
+    for name, (prec, nrhs, conc) in forms.items():
+        run = Runner(args, f_host, prec, nrhs, flush, conc)
+        run.timed_step(0)
+        torch.cuda.synchronize()
+        nsteps = max(1, min(args.steps, 3))
+        tot, infos = 0.0, []
+        for s in range(nsteps):
+            a, b, res = run.timed_step(s)
             torch.cuda.synchronize()
-            tot = 0.0
-            its = []
-            for s in range(max(1, min(args.steps, 3))):
-                flush.fill_(float(s))
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                its += one_step()
-                b.record(stream)
-                torch.cuda.synchronize()
-                tot += a.elapsed_time(b)
-            nsteps = max(1, min(args.steps, 3))
-            out[name] = {"solves_per_s": 2 * args.seeds * nsteps / (tot * 1e-3),
-                         "iterations_mean": sum(i["iterations"] for _, i in its) / len(its),
-                         "residual_max": max(i["residual"] for _, i in its),
-                         "all_converged": all(st == B.FPG_OK for st, _ in its)}
-            for k in kappas:
-                doms[k].close()
+            tot += a.elapsed_time(b)
+            infos += res
+        out[name] = {"solves_per_s": 2 * args.seeds * nsteps / (tot * 1e-3),
+                     "iterations_mean": sum(i["iterations"] for _, i in infos) / len(infos),
+                     "residual_max": max(i["residual"] for _, i in infos),
+                     "all_converged": all(st == B.FPG_OK for st, _ in infos)}
+        run.close()
     return out
 
 
@@ -375,44 +401,71 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def roofline(phase, phases, costs, args, peaks, fp64_peak, fp32_peak, nrhs, kappas):
-    """Roofline entry for the dominant kernel group: algorithmic work per launch
-    over its average device duration (CUDA events inside the timed region)."""
-    ph = phases[phase]
-    calls = max(1, ph["launches"])
+def roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, nrhs):
+    """Roofline of the dominant kernel: its algorithmic work per launch over its
+    average device duration, both from CUDA events recorded inside the timed
+    region (the library brackets each fast-solve kernel when profiling is on;
+    the Arnoldi step is one launch of k_arnoldi_cluster)."""
+    import math
     nc = args.n * args.n
+    pts = nc * nrhs
     hbm = peaks.get("hbm_gbs", 6800.0)
-    if phase == "precond":
-        # 3 launches per application (forward DST, Thomas, inverse DST) over nrhs blocks
-        apps = calls / 3.0
-        t = ph["ms"] * 1e-3 / apps
-        flops = costs["fast_solve_flops"] * nrhs
-        byts = (16.0 if args.precision == 64 else 12.0) * nc * nrhs
-        if args.precision == 64:
-            ach = flops / t
-            return {"kernel": "fast_solve (forward DST, Thomas, inverse DST; per application)", "bound": "alu",
-                    "achieved": ach / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                    "traffic": None, "hbm_frac": byts / t / 1e9 / hbm,
-                    "peak_source": "library FP64 FMA probe on this GPU"}
-        ach = byts / t
-        return {"kernel": "fast_solve (FP32; per application)", "bound": "hbm", "achieved": ach / 1e9,
-                "peak": hbm, "unit": "GB/s", "frac": ach / 1e9 / hbm, "traffic": None,
-                "alu_frac": flops / t / fp32_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
-    if phase == "arnoldi":
-        # per Arnoldi step: one MGS chain over nrhs vectors
-        steps = max(1, phases["givens"]["launches"])
-        t = ph["ms"] * 1e-3 / steps
-        flops = costs["arnoldi_flops"] * nrhs
-        ach = flops / t
-        return {"kernel": "arnoldi_mgs (one Arnoldi step)", "bound": "alu", "achieved": ach / 1e12,
-                "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
-                "hbm_frac": costs["arnoldi_bytes"] * nrhs / t / 1e9 / hbm,
-                "peak_source": "library FP64 FMA probe on this GPU"}
-    steps = max(1, phases["givens"]["launches"])
-    t = ph["ms"] * 1e-3 / steps
-    byts = 16.0 * nc * nrhs
-    return {"kernel": "schur_matvec", "bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm, "unit": "GB/s",
-            "frac": byts / t / 1e9 / hbm, "traffic": None}
+    te = 8 if args.precision == 64 else 4
+    alu = fp64_peak if args.precision == 64 else fp32_peak
+    dst_flops = 2.5 * math.log2(args.n) * pts
+    cands = {
+        "k_fft_forward": (dst_flops, (8 + te) * pts, alu),
+        "k_thomas_scan": (5.0 * pts, 2 * te * pts, alu),
+        "k_fft_inverse": (dst_flops + pts, (te + te) * pts, alu),
+        "k_arnoldi_cluster": (costs["arnoldi_flops"] * nrhs, costs["arnoldi_bytes"] * nrhs, fp64_peak),
+    }
+    phase_of = {"k_arnoldi_cluster": "arnoldi"}
+    best, best_ms = None, -1.0
+    for name in cands:
+        ph = phases.get(phase_of.get(name, name), {"ms": 0.0, "launches": 0})
+        if ph["launches"] and ph["ms"] > best_ms:
+            best, best_ms = name, ph["ms"]
+    flops, byts, peak_alu = cands[best]
+    ph = phases[phase_of.get(best, best)]
+    t = ph["ms"] * 1e-3 / ph["launches"]
+    ach_alu = flops / t
+    ach_hbm = byts / t / 1e9
+    fp64_kernel = best == "k_arnoldi_cluster" or args.precision == 64
+    out = {"kernel": best, "avg_launch_us": t * 1e6, "launches": ph["launches"],
+           "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
+           "traffic": traffic_for(best, args)}
+    if fp64_kernel:
+        out.update({"bound": "alu", "achieved": ach_alu / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
+                    "frac": ach_alu / peak_alu, "hbm_frac": ach_hbm / hbm,
+                    "peak_source": "measured: library FP64 FMA probe on this GPU (2 flops per FMA)"})
+    else:
+        out.update({"bound": "hbm", "achieved": ach_hbm, "peak": hbm, "unit": "GB/s", "frac": ach_hbm / hbm,
+                    "alu_frac": ach_alu / peak_alu, "peak_source": "measured: MEASURED_PEAKS.json hbm_gbs"})
+    return out
+
+
+def traffic_for(kernel, args):
+    """DRAM bytes per launch from the committed ncu summary, when it was taken on
+    this workload and the kernel sources have not changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    srcs = ["paper_2509_23180_gb300/csrc/fpg_fastsolve.cu", "paper_2509_23180_gb300/csrc/fpg_dst.cuh",
+            "paper_2509_23180_gb300/csrc/fpg_krylov.cu"]
+    h = hashlib.sha1()
+    for s in srcs:
+        h.update(open(os.path.join(ROOT, s), "rb").read())
+    sha = h.hexdigest()[:12]
+    try:
+        for line in open(path):
+            if line.startswith("#") or not line.strip():
+                continue
+            f = dict(kv.split("=", 1) for kv in line.split())
+            if (f.get("kernel") == kernel and f.get("n") == str(args.n) and f.get("prec") == str(args.precision)
+                    and f.get("nrhs") == str(args.seeds) and f.get("src") == sha):
+                return float(f["dram_bytes"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
 
 
 def main():

@@ -135,6 +135,17 @@ fpg_status fpg_solve_host(fpg_domain* d, const double* f_host, double* p_host,
 
 void fpg_destroy_domain(fpg_domain* d);
 
+/* Solve several domains together -- mixed geometries, sizes, kappas and
+ * precisions (the batching form of Alg. "fft_dd_solver").  Each domain's work is
+ * issued on the stream it was created with; their restart cycles are
+ * interleaved from this one host thread, so the kernels of different domains
+ * overlap on the GPU when their streams differ.  p_dev[i]: solution buffer of
+ * domain i (its right-hand sides set with fpg_set_rhs); infos[i]: nrhs_i
+ * entries or NULL (infos itself may be NULL).  Returns FPG_OK when every
+ * right-hand side of every domain met its rtol, else the first other status. */
+fpg_status fpg_solve_many(fpg_domain* const* doms, int32_t count, double* const* p_dev,
+                          fpg_solve_info* const* infos);
+
 /* ---- operator entry points: each hot-path step on its own ------------------ */
 
 /* a1: preconditioner apply z = A_c^{-1} v for nvec centre-block vectors
@@ -207,7 +218,9 @@ fpg_status fpg_fast_solve_noalloc(int32_t n, double kappa, const double* v_dev, 
 typedef enum {
   /* 1 (default): run each Arnoldi step (a3) and its Givens step (a4) as one
    * launch, one thread-block cluster per right-hand side, for centre blocks of
-   * up to 262144 unknowns; 0: one launch per modified Gram-Schmidt step. */
+   * up to 262144 unknowns; when a CTA's slice fits in registers the launch also
+   * forms the Schur matvec's stencil (a2).  2: the cluster launch without the
+   * register-resident form.  0: one launch per modified Gram-Schmidt step. */
   FPG_OPT_ARNOLDI_CLUSTER = 1
 } fpg_option;
 
@@ -219,7 +232,8 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value);
 /* Kernel-level timing of the last fpg_solve on this domain: launches issued and
  * the device time (ms, CUDA events on the domain stream) of each phase.
  * phase: 0 = preconditioner (a1), 1 = Schur matvec (a2), 2 = Arnoldi (a3),
- * 3 = Givens (a4), 4 = cycle end (a5), 5 = setup/finish (a6), 6 = residual (a7).
+ * 3 = Givens (a4), 4 = cycle end (a5), 5 = setup/finish (a6), 6 = residual (a7);
+ * 7, 8, 9 = the three kernels of a1 on their own (forward DST, Thomas, inverse DST).
  * Timing is only collected when enabled with fpg_set_profiling(d, 1). */
 fpg_status fpg_set_profiling(fpg_domain* d, int32_t on);
 fpg_status fpg_phase_stats(fpg_domain* d, int32_t phase, int64_t* launches, double* ms);

@@ -19,7 +19,8 @@ STATUS = {0: "FPG_OK", 1: "FPG_EINVAL", 2: "FPG_ENOMEM", 3: "FPG_ECUDA", 4: "FPG
           5: "FPG_ETIMEOUT", 6: "FPG_EUNSUPPORTED", 7: "FPG_EBUDGET"}
 FPG_OK, FPG_EINVAL, FPG_ENOMEM, FPG_ECUDA, FPG_ENOCONV = 0, 1, 2, 3, 4
 OPT_ARNOLDI_CLUSTER = 1
-PHASES = ("precond", "schur", "arnoldi", "givens", "cycle_end", "setup_finish", "residual")
+PHASES = ("precond", "schur", "arnoldi", "givens", "cycle_end", "setup_finish", "residual",
+          "k_fft_forward", "k_thomas_scan", "k_fft_inverse")
 
 
 class DomainDesc(ctypes.Structure):
@@ -58,6 +59,7 @@ _SIGS = {
     "fpg_solve_finish": ([_P, _P], _I32),
     "fpg_solve_host": ([_P, _P, _P, _P], _I32),
     "fpg_destroy_domain": ([_P], None),
+    "fpg_solve_many": ([_P, _I32, _P, _P], _I32),
     "fpg_apply_precond": ([_P, _P, _P, _I32], _I32),
     "fpg_block_solve": ([_P, _I32, _P, _P, _I32], _I32),
     "fpg_apply_schur": ([_P, _P, _I32, _P, _I32], _I32),
@@ -239,6 +241,21 @@ class Domain:
         out = _I64()
         _check(self.lib.fpg_launch_count(self.handle, ctypes.byref(out)), "fpg_launch_count")
         return int(out.value)
+
+
+def solve_many(domains, ps):
+    """fpg_solve_many over Domain objects and their solution tensors; returns
+    (status, [infos per domain])."""
+    lib = load()
+    n = len(domains)
+    hs = (_P * n)(*[d.handle for d in domains])
+    pp = (_P * n)(*[p.data_ptr() for p in ps])
+    arrs = [d._infos() for d in domains]
+    ip = (_P * n)(*[ctypes.cast(a, _P) for a in arrs])
+    st = lib.fpg_solve_many(hs, n, pp, ip)
+    if st not in (FPG_OK, FPG_ENOCONV):
+        _check(st, "fpg_solve_many")
+    return st, [Domain._info_list(a) for a in arrs]
 
 
 def probe_fma_peak(precision: int = 64) -> float:

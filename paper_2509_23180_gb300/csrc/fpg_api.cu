@@ -16,7 +16,7 @@ namespace fpg {
 
 cudaError_t launch_fast_solve(int prec, int out_prec, const FastSolveTables& tb, LineLayout L, const double* in,
                               BatchDesc ib, void* out, BatchDesc ob, int nblk, void* scratch, const int* active,
-                              int nper_active, cudaStream_t st, int* launches);
+                              int nper_active, cudaStream_t st, int* launches, cudaEvent_t* ev = nullptr);
 cudaError_t launch_schur_reduced(const void* z, int zprec, long long zstride, int n, const double* ctab,
                                  const int* arms_dev, int narms, double* corr, const int* active, int nrhs,
                                  cudaStream_t st);
@@ -50,6 +50,13 @@ cudaError_t launch_global_apply(const double* p, double* y, const double* f, lon
                                 cudaStream_t st);
 cudaError_t launch_fma_probe(int prec, int blocks, int iters, cudaStream_t st);
 int arnoldi_cluster_size(long long len);
+int arnoldi_reg_ept(long long len, int csz);
+cudaError_t launch_arnoldi_reg(int csz, const double* V, long long vstride, const double* w, const void* z,
+                               int zprec, const double* corr, int n, double delta, double kappa, int armmask,
+                               double* vout, long long len, int j, int nrhs, double* H, int hcol_stride,
+                               int hrhs_stride, double* cs, double* sn, double* g, double* res, int m,
+                               const double* tolabs, int* active, int* kcyc, int* iters, int max_iters, int do_givens,
+                               cudaStream_t st);
 cudaError_t launch_arnoldi_cluster(int csz, const double* V, long long vstride, double* w, double* vout,
                                    long long len, int j, int nrhs, double* H, int hcol_stride, int hrhs_stride,
                                    double* cs, double* sn, double* g, double* res, int m, const double* tolabs,
@@ -75,7 +82,7 @@ using namespace fpg;
 namespace {
 
 constexpr int kGmax = 1024;
-constexpr int kPhases = 7;
+constexpr int kPhases = 10;  // 7..9: the three fast-solve kernels of a1 on their own
 constexpr int kMaxEvents = 8192;
 // The Schur iteration stops at this fraction of the requested relative residual,
 // so that the global residual (which adds the rounding of the arm back
@@ -185,6 +192,12 @@ struct fpg_domain {
   int ev_next = 0;
   int cycles_run = 0;
   bool use_cluster = true;
+  int arnoldi_mode = 1;  // 1: register-resident fused kernel when it fits; 2: global-w cluster kernel
+  // staged solve
+  bool first_cycle = true;
+  double* p_cur = nullptr;
+  int* h_done_pinned = nullptr;  // pinned host copy of the done flags
+  cudaEvent_t ev_flags = nullptr;
 };
 
 namespace {
@@ -462,9 +475,24 @@ fpg_status precond(fpg_domain* D, const double* v, void* z, int nvec, const int*
   BatchDesc ib{L.nc, {0, 0, 0, 0}, 1};
   int nl = 0;
   const FastSolveTables& tb = D->prec == 64 ? D->tC64 : D->tC32;
+  cudaEvent_t* evp = nullptr;
+  if (D->profiling && D->ev_next + 6 <= (int)D->evpool.size()) {
+    // pool events i..i+5: start/end of the forward DST, the Thomas solve, the inverse DST
+    const int i = D->ev_next;
+    D->ev_next += 6;
+    evp = &D->evpool[i];
+    D->ev_used.push_back({7, i});
+    D->ev_used.push_back({8, i + 2});
+    D->ev_used.push_back({9, i + 4});
+  }
   FPG_CUDA_TRY(launch_fast_solve(D->prec, D->prec, tb, D->LC, v, ib, z, ib, nvec, D->scratch, active, 1, D->st,
-                                 &nl));
+                                 &nl, evp));
   count(D, 0, nl);
+  if (evp) {
+    D->phase_launches[7] += 1;
+    D->phase_launches[8] += 1;
+    D->phase_launches[9] += 1;
+  }
   return FPG_OK;
 }
 
@@ -496,8 +524,8 @@ fpg_status arm_solves_refined(fpg_domain* D, const double* in, double* out, doub
   return FPG_OK;
 }
 
-// a2 on nvec centre vectors (nvec <= nrhs): z (zprec) -> w.
-fpg_status schur(fpg_domain* D, const void* z, int zprec, double* w, int nvec, const int* active) {
+// a2, interface part: corr[r][a][:] = R_ca A_a^{-1} R_ac z on C's line next to arm a.
+fpg_status schur_corr(fpg_domain* D, const void* z, int zprec, int nvec, const int* active) {
   const Layout& L = D->L;
   if (D->desc.schur_mode == FPG_SCHUR_REDUCED) {
     FPG_CUDA_TRY(launch_schur_reduced(z, zprec, L.nc, L.n, D->ctab, D->arms_dev, L.narms, D->corr, active, nvec,
@@ -518,6 +546,13 @@ fpg_status schur(fpg_domain* D, const void* z, int zprec, double* w, int nvec, c
     FPG_CUDA_TRY(launch_literal_extract(D->lit_out, L.ntot, L.ao, L.n, D->delta, D->corr, active, nvec, D->st));
     count(D, 1, 1);
   }
+  return FPG_OK;
+}
+
+// a2 on nvec centre vectors (nvec <= nrhs): z (zprec) -> w.
+fpg_status schur(fpg_domain* D, const void* z, int zprec, double* w, int nvec, const int* active) {
+  const Layout& L = D->L;
+  FPG_TRY(schur_corr(D, z, zprec, nvec, active));
   FPG_CUDA_TRY(launch_stencil_c(z, zprec, L.nc, w, L.nc, L.n, D->delta, D->desc.kappa, D->corr, L.armmask, active,
                                 nvec, D->gx, D->st));
   count(D, 1, 1);
@@ -534,17 +569,19 @@ fpg_status check_launch() {
 }
 
 
-// Launch the whole solve on the stream (host loop over restart cycles; the only
-// host synchronisation is one read of the per-RHS "done" flags per cycle).
-fpg_status solve_launch(fpg_domain* D, double* p) {
+// The solve in stages, so that several domains can be interleaved from one host
+// thread: setup (Alg. 1 steps 1-3), restart (true residual, restart flags and an
+// asynchronous read of the "done" flags into pinned host memory), poll (wait
+// for that read), cycle (m Arnoldi steps and the cycle end), finish (Alg. 1
+// steps 5-7 and the acceptance residual).  The only host synchronisation is
+// the poll, once per restart cycle.
+fpg_status stage_setup(fpg_domain* D, double* p) {
   const Layout& L = D->L;
   KrylovState& k = D->ks;
-  const int nrhs = D->desc.nrhs, m = D->desc.restart;
-  const int hcol = m + 1, hrhs = m * (m + 1);
-  const int zprec = D->prec;
-  const size_t zel = zprec == 64 ? 8 : 4;
+  const int nrhs = D->desc.nrhs;
   D->cycles_run = 0;
-
+  D->first_cycle = true;
+  D->p_cur = p;
   // ||f|| per RHS and the absolute tolerance
   int e = ev_begin(D, 5);
   FPG_CUDA_TRY(launch_global_apply(D->f, nullptr, D->f, L.ntot, L.n, D->delta, D->desc.kappa, L.ao, k.part, kGmax,
@@ -559,75 +596,129 @@ fpg_status solve_launch(fpg_domain* D, double* p) {
   FPG_CUDA_TRY(cudaMemsetAsync(k.iters, 0, sizeof(int) * nrhs, D->st));
   FPG_CUDA_TRY(cudaMemsetAsync(k.w, 0, sizeof(double) * nrhs * L.nc, D->st));
   ev_end(D, e);
+  return FPG_OK;
+}
 
-  const int max_cycles = (D->desc.max_iters + m - 1) / m + 2;
-  bool first = true;
-  for (int cyc = 0; cyc < max_cycles; ++cyc) {
-    // restart: w = L_c u (skipped while u = 0), r = f'_c - w -> V[0], beta, flags
-    e = ev_begin(D, 4);
-    if (!first) FPG_TRY(schur(D, k.u, 64, k.w, nrhs, nullptr));
-    FPG_CUDA_TRY(launch_restart(k.fc, k.w, k.V, L.nc, nrhs, k.part, kGmax, k.g, m, k.tolabs, k.rnorm, k.done,
-                                k.active, k.kcyc, k.iters, D->desc.max_iters, D->gx, D->st));
-    count(D, 4, 2);
+fpg_status stage_restart(fpg_domain* D) {
+  const Layout& L = D->L;
+  KrylovState& k = D->ks;
+  const int nrhs = D->desc.nrhs, m = D->desc.restart;
+  // restart: w = L_c u (skipped while u = 0), r = f'_c - w -> V[0], beta, flags
+  int e = ev_begin(D, 4);
+  if (!D->first_cycle) FPG_TRY(schur(D, k.u, 64, k.w, nrhs, nullptr));
+  FPG_CUDA_TRY(launch_restart(k.fc, k.w, k.V, L.nc, nrhs, k.part, kGmax, k.g, m, k.tolabs, k.rnorm, k.done, k.active,
+                              k.kcyc, k.iters, D->desc.max_iters, D->gx, D->st));
+  count(D, 4, 2);
+  ev_end(D, e);
+  D->first_cycle = false;
+  FPG_CUDA_TRY(cudaMemcpyAsync(D->h_done_pinned, k.done, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, D->st));
+  FPG_CUDA_TRY(cudaEventRecord(D->ev_flags, D->st));
+  return FPG_OK;
+}
+
+fpg_status stage_poll(fpg_domain* D, bool* all_done) {
+  FPG_CUDA_TRY(cudaEventSynchronize(D->ev_flags));
+  bool all = true;
+  for (int r = 0; r < D->desc.nrhs; ++r) all = all && D->h_done_pinned[r];
+  const int max_cycles = (D->desc.max_iters + D->desc.restart - 1) / D->desc.restart + 2;
+  *all_done = all || D->cycles_run >= max_cycles;
+  return FPG_OK;
+}
+
+fpg_status stage_cycle(fpg_domain* D) {
+  const Layout& L = D->L;
+  KrylovState& k = D->ks;
+  const int nrhs = D->desc.nrhs, m = D->desc.restart;
+  const int hcol = m + 1, hrhs = m * (m + 1);
+  const int zprec = D->prec;
+  const size_t zel = zprec == 64 ? 8 : 4;
+  int e;
+  D->cycles_run++;
+  for (int j = 0; j < m; ++j) {
+    double* vj = k.V + (size_t)j * nrhs * L.nc;
+    void* zj = (char*)k.Z + zel * (size_t)j * nrhs * L.nc;
+    e = ev_begin(D, 0);
+    FPG_TRY(precond(D, vj, zj, nrhs, k.active));
     ev_end(D, e);
-    first = false;
-    FPG_CUDA_TRY(cudaMemcpyAsync(D->h_done.data(), k.done, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, D->st));
-    FPG_CUDA_TRY(cudaStreamSynchronize(D->st));
-    bool all = true;
-    for (int r = 0; r < nrhs; ++r) all = all && D->h_done[r];
-    if (all) break;
-    D->cycles_run++;
-    for (int j = 0; j < m; ++j) {
-      double* vj = k.V + (size_t)j * nrhs * L.nc;
-      void* zj = (char*)k.Z + zel * (size_t)j * nrhs * L.nc;
-      e = ev_begin(D, 0);
-      FPG_TRY(precond(D, vj, zj, nrhs, k.active));
-      ev_end(D, e);
+    const int csz = D->use_cluster ? arnoldi_cluster_size(L.nc) : 0;
+    const int ept = (csz > 0 && D->arnoldi_mode == 1) ? arnoldi_reg_ept(L.nc, csz) : 0;
+    if (ept > 0) {
+      // a2's interface part, then one launch for a2's stencil + a3 + a4
       e = ev_begin(D, 1);
-      FPG_TRY(schur(D, zj, zprec, k.w, nrhs, k.active));
+      FPG_TRY(schur_corr(D, zj, zprec, nrhs, k.active));
       ev_end(D, e);
       e = ev_begin(D, 2);
-      const int csz = D->use_cluster ? arnoldi_cluster_size(L.nc) : 0;
-      if (csz > 0) {
-        // a3 + a4 fused: one cluster per right-hand side
-        FPG_CUDA_TRY(launch_arnoldi_cluster(csz, k.V, (long long)nrhs * L.nc, k.w,
-                                            k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j, nrhs, k.H, hcol, hrhs,
-                                            k.cs, k.sn, k.g, k.res, m, k.tolabs, k.active, k.kcyc, k.iters,
-                                            D->desc.max_iters, 1, D->st));
-        count(D, 2, 1);
-        ev_end(D, e);
-      } else {
-        int nl = 0;
-        FPG_CUDA_TRY(launch_mgs(k.V, (long long)nrhs * L.nc, k.w, k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j,
-                                nrhs, k.part, kGmax, k.H, hcol, hrhs, k.active, D->gx, D->st, &nl));
-        count(D, 2, nl);
-        ev_end(D, e);
-        e = ev_begin(D, 3);
-        FPG_CUDA_TRY(launch_givens(k.H, hcol, hrhs, k.cs, k.sn, k.g, k.res, j, m, nrhs, k.tolabs, k.active,
-                                   k.kcyc, k.iters, D->desc.max_iters, D->st));
-        count(D, 3, 1);
-        ev_end(D, e);
-      }
+      FPG_CUDA_TRY(launch_arnoldi_reg(csz, k.V, (long long)nrhs * L.nc, nullptr, zj, zprec, D->corr, L.n, D->delta,
+                                      D->desc.kappa, L.armmask, k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j, nrhs,
+                                      k.H, hcol, hrhs, k.cs, k.sn, k.g, k.res, m, k.tolabs, k.active, k.kcyc,
+                                      k.iters, D->desc.max_iters, 1, D->st));
+      count(D, 2, 1);
+      ev_end(D, e);
+      continue;
     }
-    e = ev_begin(D, 4);
-    FPG_CUDA_TRY(launch_cycle_end(k.H, hcol, hrhs, k.g, k.y, m, nrhs, k.kcyc, k.u, k.Z, zprec,
-                                  (long long)nrhs * L.nc, L.nc, D->gx, D->st));
-    count(D, 4, 2);
+    e = ev_begin(D, 1);
+    FPG_TRY(schur(D, zj, zprec, k.w, nrhs, k.active));
     ev_end(D, e);
+    e = ev_begin(D, 2);
+    if (csz > 0) {
+      // a3 + a4 fused: one cluster per right-hand side
+      FPG_CUDA_TRY(launch_arnoldi_cluster(csz, k.V, (long long)nrhs * L.nc, k.w, k.V + (size_t)(j + 1) * nrhs * L.nc,
+                                          L.nc, j, nrhs, k.H, hcol, hrhs, k.cs, k.sn, k.g, k.res, m, k.tolabs,
+                                          k.active, k.kcyc, k.iters, D->desc.max_iters, 1, D->st));
+      count(D, 2, 1);
+      ev_end(D, e);
+    } else {
+      int nl = 0;
+      FPG_CUDA_TRY(launch_mgs(k.V, (long long)nrhs * L.nc, k.w, k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j, nrhs,
+                              k.part, kGmax, k.H, hcol, hrhs, k.active, D->gx, D->st, &nl));
+      count(D, 2, nl);
+      ev_end(D, e);
+      e = ev_begin(D, 3);
+      FPG_CUDA_TRY(launch_givens(k.H, hcol, hrhs, k.cs, k.sn, k.g, k.res, j, m, nrhs, k.tolabs, k.active, k.kcyc,
+                                 k.iters, D->desc.max_iters, D->st));
+      count(D, 3, 1);
+      ev_end(D, e);
+    }
   }
+  e = ev_begin(D, 4);
+  FPG_CUDA_TRY(launch_cycle_end(k.H, hcol, hrhs, k.g, k.y, m, nrhs, k.kcyc, k.u, k.Z, zprec, (long long)nrhs * L.nc,
+                                L.nc, D->gx, D->st));
+  count(D, 4, 2);
+  ev_end(D, e);
+  return FPG_OK;
+}
+
+fpg_status stage_finish(fpg_domain* D) {
+  const Layout& L = D->L;
+  KrylovState& k = D->ks;
+  const int nrhs = D->desc.nrhs;
+  double* p = D->p_cur;
   // Alg. 1 steps 5-7: f'_a = f_a - R_ac p_c, p_a = A_a^{-1} f'_a, p_c = u
-  e = ev_begin(D, 5);
+  int e = ev_begin(D, 5);
   FPG_CUDA_TRY(launch_arm_rhs(D->f, k.u, L.ntot, L.n, D->delta, L.ao, D->tmp, p, nrhs, D->gxf, D->st));
   count(D, 5, 1);
   FPG_TRY(arm_solves_refined(D, D->tmp, p, D->tmp2, nrhs, 5));
   ev_end(D, e);
   // a7: global relative residual
   e = ev_begin(D, 6);
-  FPG_CUDA_TRY(launch_global_apply(p, nullptr, D->f, L.ntot, L.n, D->delta, D->desc.kappa, L.ao, k.part, kGmax,
-                                   nrhs, D->gxf, D->gres, nullptr, 0.0, nullptr, D->st));
+  FPG_CUDA_TRY(launch_global_apply(p, nullptr, D->f, L.ntot, L.n, D->delta, D->desc.kappa, L.ao, k.part, kGmax, nrhs,
+                                   D->gxf, D->gres, nullptr, 0.0, nullptr, D->st));
   count(D, 6, 2);
   ev_end(D, e);
   return check_launch();
+}
+
+// One domain, start to finish (the host waits once per restart cycle).
+fpg_status solve_launch(fpg_domain* D, double* p) {
+  FPG_TRY(stage_setup(D, p));
+  for (;;) {
+    FPG_TRY(stage_restart(D));
+    bool done = false;
+    FPG_TRY(stage_poll(D, &done));
+    if (done) break;
+    FPG_TRY(stage_cycle(D));
+  }
+  return stage_finish(D);
 }
 
 fpg_status collect_info(fpg_domain* D, fpg_solve_info* info) {
@@ -789,8 +880,11 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   if (!err) err = cp(D->arms_dev, arms, sizeof(arms));
   if (!err) err = cudaMemsetAsync(D->f, 0, sizeof(double) * nrhs * L.ntot, D->st);
   if (!err) err = cudaStreamSynchronize(D->st);
+  if (!err) err = cudaMallocHost((void**)&D->h_done_pinned, sizeof(int) * nrhs);
+  if (!err) err = cudaEventCreateWithFlags(&D->ev_flags, cudaEventDisableTiming);
   if (err) {
     record_cuda_error(err, "fpg_create_domain");
+    if (D->h_done_pinned) cudaFreeHost(D->h_done_pinned);
     delete D;
     return FPG_ECUDA;
   }
@@ -801,7 +895,41 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
 void fpg_destroy_domain(fpg_domain* d) {
   if (!d) return;
   for (auto ev : d->evpool) cudaEventDestroy(ev);
+  if (d->ev_flags) cudaEventDestroy(d->ev_flags);
+  if (d->h_done_pinned) cudaFreeHost(d->h_done_pinned);
   delete d;
+}
+
+fpg_status fpg_solve_many(fpg_domain* const* doms, int32_t count, double* const* p_dev,
+                          fpg_solve_info* const* infos) {
+  if (!doms || !p_dev || count < 0) return FPG_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!doms[i] || !p_dev[i]) return FPG_EINVAL;
+  std::vector<char> live(count, 1);
+  for (int i = 0; i < count; ++i) FPG_TRY(stage_setup(doms[i], p_dev[i]));
+  int remaining = count;
+  while (remaining > 0) {
+    for (int i = 0; i < count; ++i)
+      if (live[i]) FPG_TRY(stage_restart(doms[i]));
+    for (int i = 0; i < count; ++i) {
+      if (!live[i]) continue;
+      bool done = false;
+      FPG_TRY(stage_poll(doms[i], &done));
+      if (done) {
+        FPG_TRY(stage_finish(doms[i]));
+        live[i] = 0;
+        --remaining;
+      } else {
+        FPG_TRY(stage_cycle(doms[i]));
+      }
+    }
+  }
+  fpg_status all = FPG_OK;
+  for (int i = 0; i < count; ++i) {
+    const fpg_status s = collect_info(doms[i], infos ? infos[i] : nullptr);
+    if (s != FPG_OK && all == FPG_OK) all = s;
+  }
+  return all;
 }
 
 fpg_status fpg_set_rhs(fpg_domain* d, const double* f_dev, int32_t rhs_index) {
@@ -895,7 +1023,13 @@ fpg_status fpg_arnoldi_mgs(fpg_domain* d, const double* V, int32_t j, double* w,
   if (!d || !V || !w || !h || j < 0 || len <= 0 || nvec <= 0 || nvec > d->desc.nrhs) return FPG_EINVAL;
   // v_{j+1} overwrites w: normalise in place; same kernel choice as the solver
   const int csz = d->use_cluster ? arnoldi_cluster_size(len) : 0;
-  if (csz > 0) {
+  const int ept = (csz > 0 && d->arnoldi_mode == 1) ? arnoldi_reg_ept(len, csz) : 0;
+  if (ept > 0) {
+    FPG_CUDA_TRY(launch_arnoldi_reg(csz, V, (long long)nvec * len, w, nullptr, 64, nullptr, 0, 0.0, 0.0, 0, w, len, j,
+                                    nvec, h, 0, j + 2, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
+                                    nullptr, nullptr, 0, 0, d->st));
+    d->launches += 1;
+  } else if (csz > 0) {
     FPG_CUDA_TRY(launch_arnoldi_cluster(csz, V, (long long)nvec * len, w, w, len, j, nvec, h, 0, j + 2, nullptr,
                                         nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0, 0,
                                         d->st));
@@ -945,7 +1079,11 @@ fpg_status fpg_apply_global(fpg_domain* d, const double* p, double* y, int32_t n
 fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
   if (!d) return FPG_EINVAL;
   switch (option) {
-    case FPG_OPT_ARNOLDI_CLUSTER: d->use_cluster = value != 0; return FPG_OK;
+    case FPG_OPT_ARNOLDI_CLUSTER:
+      if (value < 0 || value > 2) return FPG_EINVAL;
+      d->use_cluster = value != 0;
+      d->arnoldi_mode = value == 2 ? 2 : 1;
+      return FPG_OK;
     default: return FPG_EINVAL;
   }
 }

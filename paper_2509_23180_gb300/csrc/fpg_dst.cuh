@@ -125,7 +125,9 @@ __device__ __forceinline__ void stockham_stage(const C2<T>* __restrict__ in, C2<
   }
 }
 
-template <typename T>
+// MAXR bounds the radices compiled into one kernel: a kernel built for small
+// radices does not carry the register footprint of the large ones.
+template <typename T, int MAXR>
 __device__ __forceinline__ void stockham_dispatch(int R, const C2<T>* in, C2<T>* out, int Q, int N, int Ns,
                                                   int pitch, const C2<T>* W) {
   switch (R) {
@@ -133,23 +135,40 @@ __device__ __forceinline__ void stockham_dispatch(int R, const C2<T>* in, C2<T>*
     case 3: stockham_stage<3, T>(in, out, Q, N, Ns, pitch, W); break;
     case 4: stockham_stage<4, T>(in, out, Q, N, Ns, pitch, W); break;
     case 5: stockham_stage<5, T>(in, out, Q, N, Ns, pitch, W); break;
-    case 7: stockham_stage<7, T>(in, out, Q, N, Ns, pitch, W); break;
-    case 11: stockham_stage<11, T>(in, out, Q, N, Ns, pitch, W); break;
-    case 13: stockham_stage<13, T>(in, out, Q, N, Ns, pitch, W); break;
-    case 17: stockham_stage<17, T>(in, out, Q, N, Ns, pitch, W); break;
-    case 19: stockham_stage<19, T>(in, out, Q, N, Ns, pitch, W); break;
-    case 23: stockham_stage<23, T>(in, out, Q, N, Ns, pitch, W); break;
-    case 29: stockham_stage<29, T>(in, out, Q, N, Ns, pitch, W); break;
-    case 31: stockham_stage<31, T>(in, out, Q, N, Ns, pitch, W); break;
-    case 37: stockham_stage<37, T>(in, out, Q, N, Ns, pitch, W); break;
-    case 41: stockham_stage<41, T>(in, out, Q, N, Ns, pitch, W); break;
-    case 43: stockham_stage<43, T>(in, out, Q, N, Ns, pitch, W); break;
-    default: break;  // plans only contain the radices above
+    default:
+      if constexpr (MAXR >= 13) {
+        switch (R) {
+          case 7: stockham_stage<7, T>(in, out, Q, N, Ns, pitch, W); break;
+          case 11: stockham_stage<11, T>(in, out, Q, N, Ns, pitch, W); break;
+          case 13: stockham_stage<13, T>(in, out, Q, N, Ns, pitch, W); break;
+          default:
+            if constexpr (MAXR >= 43) {
+              switch (R) {
+                case 17: stockham_stage<17, T>(in, out, Q, N, Ns, pitch, W); break;
+                case 19: stockham_stage<19, T>(in, out, Q, N, Ns, pitch, W); break;
+                case 23: stockham_stage<23, T>(in, out, Q, N, Ns, pitch, W); break;
+                case 29: stockham_stage<29, T>(in, out, Q, N, Ns, pitch, W); break;
+                case 31: stockham_stage<31, T>(in, out, Q, N, Ns, pitch, W); break;
+                case 37: stockham_stage<37, T>(in, out, Q, N, Ns, pitch, W); break;
+                case 41: stockham_stage<41, T>(in, out, Q, N, Ns, pitch, W); break;
+                case 43: stockham_stage<43, T>(in, out, Q, N, Ns, pitch, W); break;
+                default: break;  // plans only contain the radices above
+              }
+            }
+        }
+      }
   }
 }
 
+// Largest radix family a plan needs: 5, 13 or 43.
+__host__ __device__ inline int plan_maxr(const DstPlan& pl) {
+  int mx = 2;
+  for (int i = 0; i < pl.nrad; ++i) mx = pl.rad[i] > mx ? pl.rad[i] : mx;
+  return mx <= 5 ? 5 : (mx <= 13 ? 13 : 43);
+}
+
 // Runs all stages; returns the buffer holding the result (b0 or b1).
-template <typename T>
+template <typename T, int MAXR>
 __device__ __forceinline__ C2<T>* stockham_fft(const DstPlan& pl, C2<T>* b0, C2<T>* b1, int Q, int pitch,
                                                const C2<T>* W) {
   C2<T>* in = b0;
@@ -157,7 +176,7 @@ __device__ __forceinline__ C2<T>* stockham_fft(const DstPlan& pl, C2<T>* b0, C2<
   int Ns = 1;
   for (int s = 0; s < pl.nrad; ++s) {
     const int R = pl.rad[s];
-    stockham_dispatch<T>(R, in, out, Q, pl.N, Ns, pitch, W);
+    stockham_dispatch<T, MAXR>(R, in, out, Q, pl.N, Ns, pitch, W);
     __syncthreads();
     Ns *= R;
     C2<T>* t = in;
@@ -240,7 +259,7 @@ __device__ __forceinline__ void dst_load_tables(const DstPlan& pl, DstSmem<T>& s
 // DST-I of the 2Q real lines s.xin[l * n + t] (lines >= nl must hold zeros).
 // Returns a pointer to the outputs y[l * n + k] (staged in shared memory).
 // Must be called by the whole CTA; contains __syncthreads().
-template <typename T>
+template <typename T, int MAXR>
 __device__ T* dst_lines(const DstPlan& pl, DstSmem<T>& s, int Q) {
   const int n = pl.n, p = pl.p;
   // 1. pack line pairs into z (b0), j = 0..p-1
@@ -264,7 +283,7 @@ __device__ T* dst_lines(const DstPlan& pl, DstSmem<T>& s, int Q) {
   C2<T>* Z;
   C2<T>* freebuf;
   if (pl.mode == DST_STOCKHAM) {
-    Z = stockham_fft<T>(pl, s.b0, s.b1, Q, p, s.W);
+    Z = stockham_fft<T, MAXR>(pl, s.b0, s.b1, Q, p, s.W);
     freebuf = (Z == s.b0) ? s.b1 : s.b0;
   } else {
     const int N = pl.N;
@@ -292,7 +311,7 @@ __device__ T* dst_lines(const DstPlan& pl, DstSmem<T>& s, int Q) {
       s.b1[(size_t)q * p + b] = s.b0[(size_t)q * p + s.pin[b]];
     }
     __syncthreads();
-    C2<T>* A = stockham_fft<T>(pl, s.b1, s.b0, Q, p, s.W);
+    C2<T>* A = stockham_fft<T, MAXR>(pl, s.b1, s.b0, Q, p, s.W);
     for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
       const int q = idx / N, b = idx - q * N;
       C2<T>& v = A[(size_t)q * p + b];
@@ -300,7 +319,7 @@ __device__ T* dst_lines(const DstPlan& pl, DstSmem<T>& s, int Q) {
     }
     __syncthreads();
     C2<T>* other = (A == s.b0) ? s.b1 : s.b0;
-    C2<T>* Cv = stockham_fft<T>(pl, A, other, Q, p, s.W);
+    C2<T>* Cv = stockham_fft<T, MAXR>(pl, A, other, Q, p, s.W);
     C2<T>* X = (Cv == s.b0) ? s.b1 : s.b0;
     for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
       const int q = idx / N, a = idx - q * N;

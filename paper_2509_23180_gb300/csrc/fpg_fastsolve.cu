@@ -277,7 +277,7 @@ k_dense_inverse(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc o
 }
 
 // FFT engine versions: 2Q lines per CTA.
-template <typename T>
+template <typename T, int MAXR>
 __global__ void __launch_bounds__(kFsThreads)
 k_fft_forward(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPlan pl, T* __restrict__ scratch,
               int Q, const int* __restrict__ active, int nper_active) {
@@ -304,12 +304,12 @@ k_fft_forward(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPlan
     }
   }
   __syncthreads();
-  const T* y = dst_lines<T>(pl, sm, Q);
+  const T* y = dst_lines<T, MAXR>(pl, sm, Q);
   T* dst = scratch + ((long long)b * L.ns + s0) * n;
   for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) dst[idx] = y[idx];
 }
 
-template <typename T, typename To>
+template <typename T, typename To, int MAXR>
 __global__ void __launch_bounds__(kFsThreads)
 k_fft_inverse(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc ob, LineLayout L, DstPlan pl, int Q,
               const int* __restrict__ active, int nper_active) {
@@ -325,7 +325,7 @@ k_fft_inverse(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc ob,
   const T* src = scratch + ((long long)b * L.ns + s0) * n;
   for (int idx = threadIdx.x; idx < lpb * n; idx += blockDim.x) sm.xin[idx] = idx < nl * n ? src[idx] : T(0);
   __syncthreads();
-  const T* y = dst_lines<T>(pl, sm, Q);
+  const T* y = dst_lines<T, MAXR>(pl, sm, Q);
   To* dst = batch_ptr_out(out, ob, b);
   const T scale = T(2) / T(n + 1);
   if (L.st == 1) {
@@ -370,14 +370,18 @@ int pairs_per_block(const DstPlan& pl, int ns, int nblk) {
 template <typename T, typename To>
 cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib,
                             To* out, BatchDesc ob, int nblk, T* scratch, const int* active,
-                            int nper_active, cudaStream_t st) {
+                            int nper_active, cudaStream_t st, cudaEvent_t* ev) {
   const int n = tb.n;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_dense_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dense_inverse<T, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_fft_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_fft_inverse<T, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fft_forward<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fft_forward<T, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fft_forward<T, 43>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fft_inverse<T, To, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fft_inverse<T, To, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fft_inverse<T, To, 43>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   const DstPlan& pl = tb.plan;
@@ -395,9 +399,27 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
   const int Q = pairs_per_block<T>(pl, L.ns, nblk);
   const size_t smem = dst_smem_bytes<T>(pl.p, pl.N, Q, pl.mode);
   dim3 grid((L.ns + 2 * Q - 1) / (2 * Q), nblk);
-  k_fft_forward<T><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
+  // ev (optional): start/end pairs around the three kernels
+  const int maxr = plan_maxr(pl);
+  if (ev) cudaEventRecord(ev[0], st);
+  if (maxr == 5)
+    k_fft_forward<T, 5><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
+  else if (maxr == 13)
+    k_fft_forward<T, 13><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
+  else
+    k_fft_forward<T, 43><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
+  if (ev) cudaEventRecord(ev[1], st);
+  if (ev) cudaEventRecord(ev[2], st);
   launch_thomas_scan<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st);
-  k_fft_inverse<T, To><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
+  if (ev) cudaEventRecord(ev[3], st);
+  if (ev) cudaEventRecord(ev[4], st);
+  if (maxr == 5)
+    k_fft_inverse<T, To, 5><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
+  else if (maxr == 13)
+    k_fft_inverse<T, To, 13><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
+  else
+    k_fft_inverse<T, To, 43><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
+  if (ev) cudaEventRecord(ev[5], st);
   return cudaGetLastError();
 }
 
@@ -408,19 +430,19 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
 cudaError_t launch_fast_solve(int prec, int out_prec, const FastSolveTables& tb, LineLayout L,
                               const double* in, BatchDesc ib, void* out, BatchDesc ob, int nblk,
                               void* scratch, const int* active, int nper_active, cudaStream_t st,
-                              int* launches) {
+                              int* launches, cudaEvent_t* ev) {
   if (nblk <= 0) return cudaSuccess;
   if (launches) *launches += 3;
   if (prec == 64) {
     return fast_solve_impl<double, double>(tb, L, in, ib, (double*)out, ob, nblk, (double*)scratch, active,
-                                           nper_active, st);
+                                           nper_active, st, ev);
   }
   if (out_prec == 64) {
     return fast_solve_impl<float, double>(tb, L, in, ib, (double*)out, ob, nblk, (float*)scratch, active,
-                                          nper_active, st);
+                                          nper_active, st, ev);
   }
   return fast_solve_impl<float, float>(tb, L, in, ib, (float*)out, ob, nblk, (float*)scratch, active,
-                                       nper_active, st);
+                                       nper_active, st, ev);
 }
 
 }  // namespace fpg

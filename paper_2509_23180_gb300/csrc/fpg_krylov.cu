@@ -302,6 +302,135 @@ k_arnoldi_cluster(const double* __restrict__ V, long long vstride, double* __res
 }
 
 // ---------------------------------------------------------------------------
+// Register-resident form of the fused Arnoldi step, for centre vectors of up
+// to 16 * kThreads elements per CTA.  Each thread keeps its EPT elements of w in
+// registers for the whole MGS chain and carries v_k over to the next step's
+// axpy, so every basis vector is read once and w is never written back.  With
+// z != nullptr the kernel first forms w = A_c z - sum_a corr_a (the Schur
+// matvec's stencil, a2) straight into those registers.  Partials of each MGS
+// step are gathered from the cluster's CTAs by one warp, one remote load per
+// lane, and summed in a fixed lane order.
+template <typename Tz, int EPT>
+__global__ void __launch_bounds__(kThreads)
+k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const double* __restrict__ w,
+                      const Tz* __restrict__ z, const double* __restrict__ corr, int n, double delta, double kappa,
+                      int armmask, double* __restrict__ vout, long long len, int j, double* __restrict__ H,
+                      int hcol_stride, int hrhs_stride, double* __restrict__ cs, double* __restrict__ sn,
+                      double* __restrict__ g, double* __restrict__ res, int m, const double* __restrict__ tolabs,
+                      int* __restrict__ active, int* __restrict__ kcyc, int* __restrict__ iters, int max_iters,
+                      int do_givens) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int csz = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int r = blockIdx.x / csz;
+  __shared__ double red[32];
+  __shared__ double part[2];
+  __shared__ double hval;
+  if (active != nullptr && !active[r]) return;  // uniform over the cluster
+  const long long chunk = (len + csz - 1) / csz;
+  const long long lo = (long long)rank * chunk;
+  const long long hi = lo + chunk < len ? lo + chunk : len;
+  double wv[EPT], vp[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const long long idx = lo + threadIdx.x + (long long)e * blockDim.x;
+    double x = 0.0;
+    if (idx < hi) {
+      if (z == nullptr) {
+        x = w[(long long)r * len + idx];
+      } else {
+        const Tz* zr = z + (long long)r * len;
+        const double* cr = corr + (long long)r * 4 * n;
+        const int jj = (int)(idx / n), ii = (int)(idx - (long long)jj * n);
+        const double zc = (double)zr[idx];
+        double sacc = -4.0 * zc;
+        if (ii > 0) sacc += (double)zr[idx - 1];
+        if (ii < n - 1) sacc += (double)zr[idx + 1];
+        if (jj > 0) sacc += (double)zr[idx - n];
+        if (jj < n - 1) sacc += (double)zr[idx + n];
+        x = fma(delta, sacc, kappa * zc);
+        if (ii == 0 && (armmask & 1)) x -= cr[0 * n + jj];
+        if (ii == n - 1 && (armmask & 2)) x -= cr[1 * n + jj];
+        if (jj == 0 && (armmask & 4)) x -= cr[2 * n + ii];
+        if (jj == n - 1 && (armmask & 8)) x -= cr[3 * n + ii];
+      }
+    }
+    wv[e] = x;
+    vp[e] = 0.0;
+  }
+  double hprev = 0.0;
+  for (int k = 0; k <= j + 1; ++k) {
+    const double* vk = (k <= j) ? V + (long long)k * vstride + (long long)r * len : nullptr;
+    double acc = 0.0;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const long long idx = lo + threadIdx.x + (long long)e * blockDim.x;
+      if (k >= 1) wv[e] = fma(-hprev, vp[e], wv[e]);
+      if (vk) {
+        const double v = idx < hi ? vk[idx] : 0.0;
+        acc = fma(wv[e], v, acc);
+        vp[e] = v;
+      } else {
+        acc = fma(wv[e], wv[e], acc);
+      }
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) part[k & 1] = acc;
+    cl.sync();
+    if (threadIdx.x < 32) {
+      const double q = threadIdx.x < csz ? *cl.map_shared_rank(&part[k & 1], (unsigned)threadIdx.x) : 0.0;
+      const double sum = warp_sum(q);
+      if (threadIdx.x == 0) hval = sum;
+    }
+    __syncthreads();
+    hprev = hval;
+    if (rank == 0 && threadIdx.x == 0 && k <= j) H[(long long)r * hrhs_stride + (long long)j * hcol_stride + k] = hprev;
+  }
+  const double hn = sqrt(hprev);
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  double* vr = vout + (long long)r * len;
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const long long idx = lo + threadIdx.x + (long long)e * blockDim.x;
+    if (idx < hi) vr[idx] = wv[e] * inv;
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    double* h = H + (long long)r * hrhs_stride + (long long)j * hcol_stride;
+    h[j + 1] = hn;
+    if (do_givens) {
+      double* c = cs + (long long)r * m;
+      double* s = sn + (long long)r * m;
+      double* gr = g + (long long)r * (m + 1);
+      for (int i = 0; i < j; ++i) {
+        const double a = h[i], b = h[i + 1];
+        h[i] = c[i] * a + s[i] * b;
+        h[i + 1] = -s[i] * a + c[i] * b;
+      }
+      const double a = h[j], b = h[j + 1];
+      const double rr = hypot(a, b);
+      double cc = 1.0, ss = 0.0;
+      if (rr != 0.0) {
+        cc = a / rr;
+        ss = b / rr;
+      }
+      c[j] = cc;
+      s[j] = ss;
+      h[j] = rr;
+      h[j + 1] = 0.0;
+      gr[j + 1] = -ss * gr[j];
+      gr[j] = cc * gr[j];
+      const double rj = fabs(gr[j + 1]);
+      res[r] = rj;
+      kcyc[r] = j + 1;
+      iters[r] += 1;
+      if (rj <= tolabs[r] || b == 0.0 || iters[r] >= max_iters) active[r] = 0;
+    }
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// ---------------------------------------------------------------------------
 // a4: Givens step on column j, one thread per right-hand side.
 __global__ void k_givens(double* __restrict__ H, int hcol_stride, int hrhs_stride, double* __restrict__ cs,
                          double* __restrict__ sn, double* __restrict__ g, double* __restrict__ res, int j,
@@ -757,6 +886,73 @@ cudaError_t launch_arnoldi_cluster(int csz, const double* V, long long vstride, 
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_arnoldi_cluster, V, vstride, w, vout, len, j, H, hcol_stride, hrhs_stride, cs,
                             sn, g, res, m, tolabs, active, kcyc, iters, max_iters, do_givens);
+}
+
+// Register-resident fused Arnoldi: returns cudaErrorInvalidValue when the
+// slice per CTA is too long for it (the caller then uses k_arnoldi_cluster).
+int arnoldi_reg_ept(long long len, int csz) {
+  const long long chunk = (len + csz - 1) / csz;
+  const long long ept = (chunk + kThreads - 1) / kThreads;
+  if (ept <= 1) return 1;
+  if (ept <= 2) return 2;
+  if (ept <= 4) return 4;
+  if (ept <= 8) return 8;
+  if (ept <= 16) return 16;
+  return 0;
+}
+
+template <typename Tz, int EPT>
+cudaError_t launch_reg_impl(int csz, const double* V, long long vstride, const double* w, const Tz* z,
+                            const double* corr, int n, double delta, double kappa, int armmask, double* vout,
+                            long long len, int j, int nrhs, double* H, int hcol_stride, int hrhs_stride, double* cs,
+                            double* sn, double* g, double* res, int m, const double* tolabs, int* active, int* kcyc,
+                            int* iters, int max_iters, int do_givens, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_arnoldi_cluster_reg<Tz, EPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(csz * nrhs, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = csz;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_arnoldi_cluster_reg<Tz, EPT>, V, vstride, w, z, corr, n, delta, kappa, armmask,
+                            vout, len, j, H, hcol_stride, hrhs_stride, cs, sn, g, res, m, tolabs, active, kcyc,
+                            iters, max_iters, do_givens);
+}
+
+// z == nullptr: w is read from `w`; otherwise w = A_c z - corr is formed in the kernel (zprec 64 or 32).
+cudaError_t launch_arnoldi_reg(int csz, const double* V, long long vstride, const double* w, const void* z,
+                               int zprec, const double* corr, int n, double delta, double kappa, int armmask,
+                               double* vout, long long len, int j, int nrhs, double* H, int hcol_stride,
+                               int hrhs_stride, double* cs, double* sn, double* g, double* res, int m,
+                               const double* tolabs, int* active, int* kcyc, int* iters, int max_iters, int do_givens,
+                               cudaStream_t st) {
+  const int ept = arnoldi_reg_ept(len, csz);
+#define FPG_REG_CASE(E)                                                                                            \
+  if (ept == E) {                                                                                                  \
+    if (z != nullptr && zprec == 32)                                                                               \
+      return launch_reg_impl<float, E>(csz, V, vstride, w, (const float*)z, corr, n, delta, kappa, armmask, vout,  \
+                                       len, j, nrhs, H, hcol_stride, hrhs_stride, cs, sn, g, res, m, tolabs, active, \
+                                       kcyc, iters, max_iters, do_givens, st);                                     \
+    return launch_reg_impl<double, E>(csz, V, vstride, w, (const double*)z, corr, n, delta, kappa, armmask, vout,  \
+                                      len, j, nrhs, H, hcol_stride, hrhs_stride, cs, sn, g, res, m, tolabs, active, \
+                                      kcyc, iters, max_iters, do_givens, st);                                      \
+  }
+  FPG_REG_CASE(1)
+  FPG_REG_CASE(2)
+  FPG_REG_CASE(4)
+  FPG_REG_CASE(8)
+  FPG_REG_CASE(16)
+#undef FPG_REG_CASE
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_givens(double* H, int hcol_stride, int hrhs_stride, double* cs, double* sn, double* g,

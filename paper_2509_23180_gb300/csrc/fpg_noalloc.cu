@@ -24,7 +24,7 @@
 namespace fpg {
 cudaError_t launch_fast_solve(int prec, int out_prec, const FastSolveTables& tb, LineLayout L, const double* in,
                               BatchDesc ib, void* out, BatchDesc ob, int nblk, void* scratch, const int* active,
-                              int nper_active, cudaStream_t st, int* launches);
+                              int nper_active, cudaStream_t st, int* launches, cudaEvent_t* ev = nullptr);
 void record_message(const char* msg);
 }  // namespace fpg
 

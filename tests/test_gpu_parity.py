@@ -293,9 +293,10 @@ def test_restart_and_noconv(lib):
     assert info[0]["iterations"] <= 3
 
 
-@pytest.mark.parametrize("cluster", [0, 1])
+@pytest.mark.parametrize("cluster", [0, 1, 2])
 def test_arnoldi_paths_agree_in_solve(lib, cluster):
-    """The cluster-fused and the multi-launch Arnoldi give the same solution."""
+    """All three Arnoldi paths (multi-launch MGS, register-resident cluster kernel
+    with the fused stencil, global-memory cluster kernel) give the solution."""
     from paper_2509_23180_gb300 import binding as B
     n = 48
     K = O.assemble("cross", n, -10.0)
@@ -362,3 +363,33 @@ def test_solve_host_matches_device_path(lib):
     p = torch.zeros_like(dev(f))
     d.solve(p)
     assert np.array_equal(ph.numpy(), host(p))
+
+
+def test_solve_many_mixed_batch_same_as_alone(lib):
+    """Mixed batch (L, T, cross; different n, kappa and preconditioner precision,
+    each domain on its own stream) solved together by fpg_solve_many: every
+    domain's result is bit-for-bit what it gets alone, and matches K^{-1} f."""
+    from paper_2509_23180_gb300 import binding as B
+    cases = [("L", 20, 0.0, 2, 64), ("T", 33, -10.0, 1, 64), ("cross", 16, 0.0, 3, 32), ("cross", 40, -10.0, 2, 64)]
+    doms, fs, ps, streams = [], [], [], []
+    for geom, n, kappa, nrhs, prec in cases:
+        st = torch.cuda.Stream()
+        streams.append(st)
+        d = B.Domain(B.make_desc(geom, n, kappa, nrhs=nrhs, rtol=1e-12, precond_precision=prec), stream=st)
+        f = W.rhs_batch(geom, n, list(range(nrhs)), kind="fourier")
+        fd = dev(f)
+        torch.cuda.synchronize()
+        d.set_rhs(fd)
+        doms.append(d); fs.append(f); ps.append(torch.zeros_like(fd))
+    st, infos = B.solve_many(doms, ps)
+    assert st == B.FPG_OK, infos
+    many = [host(p) for p in ps]
+    for (geom, n, kappa, nrhs, prec), d, f, P in zip(cases, doms, fs, many):
+        p1 = torch.zeros_like(dev(f))
+        d.set_rhs(dev(f))
+        s1, _ = d.solve(p1)
+        assert s1 == B.FPG_OK
+        assert np.array_equal(host(p1), P), (geom, n)
+        ref = D.Factor(O.assemble(geom, n, kappa)).solve(f)
+        for r in range(nrhs):
+            assert rel(P[r], ref[r]) < 1e-9
