@@ -45,6 +45,11 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--schedule", default="concurrent", choices=["sequential", "concurrent"],
                     help="solve the two kappa domains one after the other, or concurrently on two streams")
+    ap.add_argument("--config", default="default", choices=["default", "small", "precision", "batching", "serving"],
+                    help="default: the 256^2 cross workload; the others run the other workloads as extra lines")
+    ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: HBM admission budget")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -179,8 +184,10 @@ def algorithmic_costs(n, iters_per_solve, m):
     fs_bytes = 16.0 * nc                       # a1: read v, write z
     fs_flops = (5.0 * math.log2(n) + 6.0) * nc  # a1: two DST-I (2.5 n log2 n each) + Thomas
     sc_bytes = 16.0 * nc                       # a2: read z, write w
-    ar_bytes = (8.0 * (jbar + 1) + 24.0) * nc  # a3: V once, w read/write, v_{j+1} write
-    ar_flops = (4.0 * (jbar + 1) + 3.0) * nc   # a3: dot + axpy per basis vector, norm, scale
+    # a3 (fused with a2's stencil): V read once, z read, v_{j+1} written; dot + axpy per basis
+    # vector, norm, scale, and the 5-point stencil (4 differences, 3 adds, 1 FMA)
+    ar_bytes = (8.0 * (jbar + 1) + 16.0) * nc
+    ar_flops = (4.0 * (jbar + 1) + 3.0 + 9.0) * nc
     per_iter_bytes = fs_bytes + sc_bytes + ar_bytes
     return {"fast_solve_bytes": fs_bytes, "fast_solve_flops": fs_flops, "arnoldi_bytes": ar_bytes,
             "arnoldi_flops": ar_flops, "per_iter_bytes": per_iter_bytes,
@@ -278,14 +285,14 @@ def run_ours(args, rank, world):
     if not os.path.exists(B.LIB_PATH):
         Bd.build()
     B.load()
-    seeds = list(range(args.seeds))
+    from paper_2509_23180_gb300 import replicas
+    seeds = replicas.seeds_for_rank(rank, world, args.seeds)  # independent problems per rank
     f_host = {k: W.rhs_batch("cross", args.n, seeds, kind="fourier") for k in (0.0, -10.0)}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     run = Runner(args, f_host, args.precision, args.seeds, flush, args.schedule == "concurrent")
     for s in range(args.warmup):
         run.timed_step(s)
     torch.cuda.synchronize()
-    run.set_profiling(True)
     launches0 = run.launches()
     evs, infos = [], []
     if world > 1:
@@ -301,17 +308,21 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     launches = run.launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in evs]
+    # per-kernel device times for the roofline: one profiled pass of the same
+    # workload right after the timed steps, domains one after the other so that
+    # no other kernel shares the GPU while a kernel's event pair is open
+    run.concurrent = False
+    run.set_profiling(True)
+    run.timed_step(args.steps)
+    torch.cuda.synchronize()
     phases = run.phases()
     run.set_profiling(False)
+    run.concurrent = args.schedule == "concurrent"
 
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.job_time(sum(step_ms), world, device="cuda")
     ms_per_step = total_ms / args.steps
     solves_per_step = 2 * args.seeds
-    value = world * solves_per_step / (ms_per_step * 1e-3)
+    value = replicas.aggregate_rate(solves_per_step, world, ms_per_step)
     resid = [i["residual"] for _, i in infos]
     iters = [i["iterations"] for _, i in infos]
     ok = all(st == B.FPG_OK for st, _ in infos)
@@ -347,7 +358,9 @@ def run_ours(args, rank, world):
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "per": "step of %d solves" % solves_per_step},
         "iterations_mean": iters_mean, "residual_max": max(resid) if resid else None, "all_converged": ok,
-        "phases_ms": {k: round(v["ms"] / args.steps, 4) for k, v in phases.items()},
+        "phases_ms": {k: round(v["ms"], 4) for k, v in phases.items()},
+        "phases_note": "device ms per phase and per a1 kernel in one profiled step (sequential schedule) "
+                       "run after the timed steps; CUDA events on the domain streams",
         "gpu_launches": int(launches),
         "roofline": roof,
         "peaks": {"fp64_fma_tflops_probe": fp64_peak / 1e12, "fp32_fma_tflops_probe": fp32_peak / 1e12,
@@ -403,9 +416,10 @@ def measured_peaks():
 
 def roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, nrhs):
     """Roofline of the dominant kernel: its algorithmic work per launch over its
-    average device duration, both from CUDA events recorded inside the timed
-    region (the library brackets each fast-solve kernel when profiling is on;
-    the Arnoldi step is one launch of k_arnoldi_cluster)."""
+    average device duration.  Durations come from CUDA events the library
+    records around each kernel launch when profiling is on (the a1 kernels one
+    by one, the Arnoldi step as its single launch), in the profiled pass of the
+    same workload that follows the timed steps."""
     import math
     nc = args.n * args.n
     pts = nc * nrhs
@@ -425,6 +439,9 @@ def roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, nrhs):
         ph = phases.get(phase_of.get(name, name), {"ms": 0.0, "launches": 0})
         if ph["launches"] and ph["ms"] > best_ms:
             best, best_ms = name, ph["ms"]
+    if best is None:
+        return {"kernel": None, "bound": "alu", "achieved": None, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "note": "no profiled kernel launches in the timed region"}
     flops, byts, peak_alu = cands[best]
     ph = phases[phase_of.get(best, best)]
     t = ph["ms"] * 1e-3 / ph["launches"]
@@ -432,6 +449,8 @@ def roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, nrhs):
     ach_hbm = byts / t / 1e9
     fp64_kernel = best == "k_arnoldi_cluster" or args.precision == 64
     out = {"kernel": best, "avg_launch_us": t * 1e6, "launches": ph["launches"],
+           "measured": "CUDA events around every launch of the kernel in one profiled step of the same "
+                       "workload (sequential schedule) after the timed steps",
            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
            "traffic": traffic_for(best, args)}
     if fp64_kernel:
@@ -468,6 +487,152 @@ def traffic_for(kernel, args):
     return None
 
 
+
+# ------------------------------------------------------------------ other workloads
+def _timed(fn, stream_sync=True):
+    import torch
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    t0 = time.perf_counter()
+    out = fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), (time.perf_counter() - t0) * 1e3, out
+
+
+def run_extra(args):
+    """Extra lines for the other workloads; each line carries its own config."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2509_23180_gb300 import binding as B
+    from paper_2509_23180_gb300 import build as Bd
+    if not os.path.exists(B.LIB_PATH):
+        Bd.build()
+    B.load()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    lines = []
+    if args.config in ("small", "precision"):
+        # small: the manufactured 64^2 cross, m = 30; precision: 1024^2 cross, kappa 0,
+        # FP32 fast solve inside FP64 FGMRES(40) against the plain FP64 path
+        if args.config == "small":
+            n, m, kinds = 64, 30, [("fp64", 64)]
+            f = W.manufactured_rhs("cross", n, 0.0)[None, :]
+        else:
+            n, m, kinds = 1024, 40, [("fp32_precond", 32), ("fp64_plain", 64)]
+            f = W.rhs_batch("cross", n, [0], kind="fourier")
+        fd = torch.as_tensor(f, device="cuda")
+        for name, prec in kinds:
+            st = torch.cuda.Stream()
+            d = B.Domain(B.make_desc("cross", n, 0.0, nrhs=1, restart=m, rtol=args.rtol, precond_precision=prec),
+                         stream=st)
+            p = torch.zeros_like(fd)
+            times, infos = [], []
+            for s in range(args.warmup + args.steps):
+                flush.fill_(float(s))
+                d.set_rhs(fd)
+                ms, _, (stt, info) = _timed(lambda: d.solve(p, check=False))
+                if s >= args.warmup:
+                    times.append(ms)
+                    infos += info
+            ms = sum(times) / len(times)
+            line = {"metric": METRIC, "value": 1e3 / ms, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+                    "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                    "vs_baseline": None, "dtype": "f64+f32precond" if prec == 32 else "f64", "data": "synthetic",
+                    "config": {"workload": f"cross {n}^2 per block, kappa 0, 1 RHS ({name})", "n": n, "restart": m,
+                               "rtol": args.rtol, "l2": "flushed before every solve"},
+                    "iterations": infos[0]["iterations"], "residual": max(i["residual"] for i in infos),
+                    "solution_checksum": float(p.abs().sum())}
+            if name == "fp64_plain" and lines:
+                lines[-1]["vs_plain_fp64"] = lines[-1]["value"] / line["value"]
+            lines.append(line)
+            d.close()
+    elif args.config == "batching":
+        # (i) 64 RHS in one domain on the 512^2 cross, FP32 fast solve, FP64 FGMRES(40)
+        n, m, nr = 512, 40, 64
+        f = torch.stack([W.fourier_rhs_torch("cross", n, s) for s in range(nr)])
+        for prec in (32, 64):
+            d = B.Domain(B.make_desc("cross", n, 0.0, nrhs=nr, restart=m, rtol=args.rtol, precond_precision=prec))
+            p = torch.zeros_like(f)
+            times, infos = [], []
+            for s in range(1 + max(1, args.steps // 2)):
+                flush.fill_(float(s))
+                d.set_rhs(f)
+                ms, _, (stt, info) = _timed(lambda: d.solve(p, check=False))
+                if s >= 1:
+                    times.append(ms)
+                    infos += info
+            ms = sum(times) / len(times)
+            lines.append({"metric": METRIC, "value": nr * 1e3 / ms, "unit": "solves/s", "n_gpus": 1,
+                          "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                          "dtype": "f64+f32precond" if prec == 32 else "f64", "data": "synthetic",
+                          "config": {"workload": f"cross 512^2 per block, {nr} RHS in one launch sequence",
+                                     "precond_precision": prec, "restart": m, "rtol": args.rtol},
+                          "iterations_mean": float(np.mean([i["iterations"] for i in infos])),
+                          "residual_max": max(i["residual"] for i in infos),
+                          "all_converged": all(i["status"] == 0 for i in infos)})
+            d.close()
+            del p
+        del f
+        torch.cuda.empty_cache()
+        # (ii) mixed batch: L, T and cross, n in {128, 256, 512, 1024}, per-instance seeds, fpg_solve_many
+        rng = np.random.default_rng(3)
+        inst = []
+        for i, geom in enumerate(["L", "T", "cross"] * 4):
+            nn = int(rng.choice([128, 256, 512, 1024]))
+            inst.append((geom, nn, (0.0, -10.0)[i % 2], 2))
+        doms, ps, fs = [], [], []
+        for i, (geom, nn, kappa, nr) in enumerate(inst):
+            st = torch.cuda.Stream()
+            dd = B.Domain(B.make_desc(geom, nn, kappa, nrhs=nr, restart=m, rtol=args.rtol, precond_precision=32),
+                          stream=st)
+            ff = torch.stack([W.fourier_rhs_torch(geom, nn, 1000 + 10 * i + r) for r in range(nr)])
+            torch.cuda.synchronize()
+            dd.set_rhs(ff)
+            doms.append(dd); fs.append(ff); ps.append(torch.zeros_like(ff))
+        for rep in range(2):
+            for dd, ff in zip(doms, fs):
+                dd.set_rhs(ff)
+            flush.fill_(float(rep))
+            ms, wall, (stt, infos) = _timed(lambda: B.solve_many(doms, ps))
+        solves = sum(x[3] for x in inst)
+        lines.append({"metric": METRIC, "value": solves * 1e3 / ms, "unit": "solves/s", "n_gpus": 1,
+                      "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "dtype": "f64+f32precond",
+                      "data": "synthetic",
+                      "config": {"workload": "mixed batch via fpg_solve_many: " +
+                                 ", ".join(f"{g}{nn}k{int(k)}" for g, nn, k, _ in inst),
+                                 "restart": m, "rtol": args.rtol},
+                      "residual_max": max(i["residual"] for inf in infos for i in inf),
+                      "all_converged": stt == B.FPG_OK})
+        for dd in doms:
+            dd.close()
+    elif args.config == "serving":
+        from paper_2509_23180_gb300 import serve
+        reqs = W.serving_requests(args.requests, args.rate, seed=0)
+        srv = serve.Server(budget_bytes=args.budget_gb * 1e9, max_inflight=8, slot_rhs=8, restart=40,
+                           rtol=args.rtol, precond_precision=32)
+        # warm: one request of every n so that domain creation is not the first arrivals' latency
+        srv.serve([dict(r, arrival_s=0.0) for r in reqs[:0]], realtime=False)
+        t0 = time.perf_counter()
+        res = srv.serve(reqs, realtime=True)
+        wall = time.perf_counter() - t0
+        summ = serve.summarize(res, wall)
+        lines.append({"metric": METRIC, "value": summ["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+                      "higher_is_better": True, "scaling": "weak", "dtype": "f64+f32precond", "data": "synthetic",
+                      "config": {"workload": f"serving: {args.requests} Poisson requests at {args.rate}/s, "
+                                             "geometry L/T/cross, n 64..1024, 1-8 RHS, kappa 0/-10",
+                                 "budget_gb": args.budget_gb, "max_inflight": 8, "restart": 40, "rtol": args.rtol},
+                      "latency_ms": summ["latency_ms"], "requests": summ["requests"], "solves": summ["solves"],
+                      "wall_s": wall, "residual_max": summ["residual_max"], "all_converged": summ["all_converged"],
+                      "domains_created": srv.created, "domains_evicted": srv.evicted,
+                      "peak_gb": srv.peak_bytes / 1e9})
+        srv.close()
+    for line in lines:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -479,6 +644,9 @@ def main():
         dist.init_process_group("nccl")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.config != "default":
+        if rank == 0:
+            run_extra(args)
     else:
         run_ours(args, rank, world)
     if world > 1:

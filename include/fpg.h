@@ -221,11 +221,40 @@ typedef enum {
    * up to 262144 unknowns; when a CTA's slice fits in registers the launch also
    * forms the Schur matvec's stencil (a2).  2: the cluster launch without the
    * register-resident form.  0: one launch per modified Gram-Schmidt step. */
-  FPG_OPT_ARNOLDI_CLUSTER = 1
+  FPG_OPT_ARNOLDI_CLUSTER = 1,
+  /* 1 (default): capture one restart cycle (the m Arnoldi steps) into a CUDA
+   * graph at the first solve and replay it for every later cycle; 0: launch
+   * every kernel from the host.  Not used while profiling is on or when the
+   * domain was created on the legacy default stream. */
+  FPG_OPT_CUDA_GRAPHS = 2,
+  /* Right preconditioner of the Schur iteration (Sec. 3.2):
+   * 0 (default): A_c^{-1}, the paper's FFT preconditioner (a1);
+   * 1: none (P = I);  2: Jacobi, the inverse diagonal of L_c.
+   * With 1 or 2 the flexible basis is still stored in the domain's
+   * precond_precision. */
+  FPG_OPT_PRECOND = 3
 } fpg_option;
 
 /* Set an option on a domain (affects later calls).  FPG_EINVAL if unknown. */
 fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value);
+
+/* ---- autotuning ------------------------------------------------------------- */
+
+typedef struct {
+  int32_t q;         /* line pairs per CTA in the DST kernels of a1 */
+  int32_t mt;        /* modes per CTA in the Thomas kernel of a1 */
+  int32_t cluster;   /* CTAs per right-hand side in the fused Arnoldi step (0: not tuned) */
+  int32_t reserved;
+  double precond_ms; /* time of one preconditioner application (all nrhs vectors) at the choice */
+  double arnoldi_ms; /* time of one Arnoldi step at j = m/2 at the choice */
+} fpg_tune_result;
+
+/* Time the launch shapes of the hot kernels on this domain's own buffers
+ * (precision, n, nrhs as created) and keep the fastest: the line batch (q) and
+ * mode tile (mt) of the fast solve, the cluster size of the Arnoldi step.
+ * Overwrites the domain's Krylov buffers (call it between solves).  The
+ * choices stay with the domain; out (may be NULL) reports them. */
+fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out);
 
 /* ---- measurement ----------------------------------------------------------- */
 

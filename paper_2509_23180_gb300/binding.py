@@ -18,7 +18,11 @@ SCHUR = {"reduced": 0, "literal": 1}
 STATUS = {0: "FPG_OK", 1: "FPG_EINVAL", 2: "FPG_ENOMEM", 3: "FPG_ECUDA", 4: "FPG_ENOCONV",
           5: "FPG_ETIMEOUT", 6: "FPG_EUNSUPPORTED", 7: "FPG_EBUDGET"}
 FPG_OK, FPG_EINVAL, FPG_ENOMEM, FPG_ECUDA, FPG_ENOCONV = 0, 1, 2, 3, 4
+FPG_EBUDGET = 7
 OPT_ARNOLDI_CLUSTER = 1
+OPT_CUDA_GRAPHS = 2
+OPT_PRECOND = 3
+PRECOND = {"fft": 0, "none": 1, "jacobi": 2}
 PHASES = ("precond", "schur", "arnoldi", "givens", "cycle_end", "setup_finish", "residual",
           "k_fft_forward", "k_thomas_scan", "k_fft_inverse")
 
@@ -33,6 +37,11 @@ class DomainDesc(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("residual", ctypes.c_double), ("schur_residual", ctypes.c_double)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int32), ("mt", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("precond_ms", ctypes.c_double), ("arnoldi_ms", ctypes.c_double)]
 
 
 class FpgError(RuntimeError):
@@ -68,6 +77,7 @@ _SIGS = {
     "fpg_global_residual": ([_P, _P, _P, _P, _I32], _I32),
     "fpg_apply_global": ([_P, _P, _P, _I32], _I32),
     "fpg_set_option": ([_P, _I32, _I32], _I32),
+    "fpg_autotune": ([_P, _P], _I32),
     "fpg_set_profiling": ([_P, _I32], _I32),
     "fpg_phase_stats": ([_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D)], _I32),
     "fpg_launch_count": ([_P, ctypes.POINTER(_I64)], _I32),
@@ -221,6 +231,12 @@ class Domain:
 
     def apply_global(self, p, y, nvec: int):
         _check(self.lib.fpg_apply_global(self.handle, _ptr(p), _ptr(y), nvec), "fpg_apply_global")
+
+    def autotune(self) -> dict:
+        """fpg_autotune: time the launch shapes of the hot kernels, keep the fastest."""
+        r = TuneResult()
+        _check(self.lib.fpg_autotune(self.handle, ctypes.byref(r)), "fpg_autotune")
+        return {"q": r.q, "mt": r.mt, "cluster": r.cluster, "precond_ms": r.precond_ms, "arnoldi_ms": r.arnoldi_ms}
 
     def set_option(self, option: int, value: int):
         _check(self.lib.fpg_set_option(self.handle, option, value), "fpg_set_option")

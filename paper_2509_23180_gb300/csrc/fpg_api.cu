@@ -49,6 +49,11 @@ cudaError_t launch_global_apply(const double* p, double* y, const double* f, lon
                                 double* rel_out, double* fnorm_out, double rtol, double* tolabs,
                                 cudaStream_t st);
 cudaError_t launch_fma_probe(int prec, int blocks, int iters, cudaStream_t st);
+cudaError_t launch_tighten(const double* gres, double rtol, double factor, double* tolabs, int* done, int nrhs,
+                           int* resume_count, cudaStream_t st);
+cudaError_t launch_precond_simple(const double* v, void* z, int zprec, long long len, int n, double delta,
+                                  double kappa, const double* ctab, int armmask, int jacobi, const int* active,
+                                  int nrhs, int gx, cudaStream_t st);
 int arnoldi_cluster_size(long long len);
 int arnoldi_reg_ept(long long len, int csz);
 cudaError_t launch_arnoldi_reg(int csz, const double* V, long long vstride, const double* w, const void* z,
@@ -88,6 +93,9 @@ constexpr int kMaxEvents = 8192;
 // so that the global residual (which adds the rounding of the arm back
 // substitution) still meets the request.
 constexpr double kInnerMargin = 0.9;
+// Acceptance checks per solve: after back substitution a right-hand side above
+// rtol resumes with its Schur target scaled by 1/4, at most this many times.
+constexpr int kAcceptRounds = 3;
 
 // Bump allocator over the caller's workspace (256-byte aligned regions).  With
 // base == nullptr it only measures.
@@ -177,6 +185,7 @@ struct fpg_domain {
   double* ctab;
   int* arms_dev;
   double *f, *tmp, *tmp2, *pbuf, *lit_in, *lit_out, *corr, *gres, *fnorm;
+  int* resume_dev = nullptr;
   void* scratch;
   KrylovState ks;
   int gx, gxf;
@@ -193,6 +202,19 @@ struct fpg_domain {
   int cycles_run = 0;
   bool use_cluster = true;
   int arnoldi_mode = 1;  // 1: register-resident fused kernel when it fits; 2: global-w cluster kernel
+  int tune_csz = 0;      // Arnoldi cluster size chosen by fpg_autotune (0: built-in choice)
+  bool use_graphs = true;
+  int precond_kind = 0;  // 0: A_c^{-1} (the paper's), 1: identity, 2: Jacobi
+  int accept_rounds = 0;  // acceptance checks done in the current solve
+  cudaGraphExec_t cycle_exec = nullptr;
+  long long cycle_kernels = 0;
+  bool capturing = false;           // a restart cycle is being captured
+  bool graph_profiled = false;      // the captured graph carries profiling events
+  bool replay_pending = false;      // a profiled replay has not been read yet
+  std::vector<cudaEvent_t> gev;     // events recorded by the graph
+  std::vector<std::pair<int, int>> gev_used;
+  int gev_next = 0;
+  long long cycle_phase_launches[16] = {0};
   // staged solve
   bool first_cycle = true;
   double* p_cur = nullptr;
@@ -236,9 +258,15 @@ void fill_ctab(int n, double delta, const std::vector<double>& rpivA, std::vecto
   std::vector<double> g(n);
   for (int k = 1; k <= n; ++k) g[k - 1] = rpivA[(size_t)(N - 1) * n + k - 1];
   for (int m = 0; m < 2 * n + 2; ++m) {
-    long double acc = 0.0L;
-    for (int k = 1; k <= n; ++k) acc += (long double)g[k - 1] * (long double)cos_pi_frac((long long)k * m, n + 1);
-    c[m] = (double)(acc * (long double)delta * (long double)delta / (long double)(n + 1));
+    // compensated (Kahan) FP64 summation: exact to ~1 ulp of the sum
+    double acc = 0.0, comp = 0.0;
+    for (int k = 1; k <= n; ++k) {
+      const double term = g[k - 1] * cos_pi_frac((long long)k * m, n + 1) - comp;
+      const double t = acc + term;
+      comp = (t - acc) - term;
+      acc = t;
+    }
+    c[m] = acc * delta * delta / (double)(n + 1);
   }
 }
 
@@ -416,6 +444,7 @@ void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostP
   const long long sc = (long long)nrhs * std::max(L.nc, 2 * L.na);
   p = c.take(sizeof(double) * sc);            if (D) D->scratch = p;
   p = c.take(sizeof(double) * nrhs);          if (D) D->gres = (double*)p;
+  p = c.take(sizeof(int) * 4);                if (D) D->resume_dev = (int*)p;
   KrylovState* k = D ? &D->ks : nullptr;
   p = c.take(sizeof(double) * (size_t)(m + 1) * nrhs * L.nc); if (k) k->V = (double*)p;
   p = c.take(zel * (size_t)m * nrhs * L.nc);                  if (k) k->Z = p;
@@ -438,21 +467,53 @@ void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostP
   p = c.take(sizeof(int) * nrhs);             if (k) k->iters = (int*)p;
 }
 
-// Phase timing helpers (only when profiling is on).
+// Phase timing helpers (only when profiling is on).  Events come from the
+// direct-launch pool, or, while a restart cycle is being captured into a CUDA
+// graph, from the graph's own pool (recorded again by every replay and read at
+// the poll that follows it).
+std::vector<cudaEvent_t>& ev_pool(fpg_domain* D) { return D->capturing ? D->gev : D->evpool; }
+std::vector<std::pair<int, int>>& ev_list(fpg_domain* D) { return D->capturing ? D->gev_used : D->ev_used; }
+int& ev_cursor(fpg_domain* D) { return D->capturing ? D->gev_next : D->ev_next; }
+
+int ev_take(fpg_domain* D, int count) {
+  if (!D->profiling || ev_cursor(D) + count > (int)ev_pool(D).size()) return -1;
+  const int i = ev_cursor(D);
+  ev_cursor(D) += count;
+  return i;
+}
+// Inside a stream capture, cudaEventRecordExternal makes the record a graph node
+// that records again at every replay (the flag is only legal while capturing).
+void ev_record(fpg_domain* D, cudaEvent_t e) {
+  if (D->capturing)
+    cudaEventRecordWithFlags(e, D->st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, D->st);
+}
 int ev_begin(fpg_domain* D, int phase) {
-  if (!D->profiling || D->ev_next + 2 > (int)D->evpool.size()) return -1;
-  const int i = D->ev_next;
-  D->ev_next += 2;
-  cudaEventRecord(D->evpool[i], D->st);
-  D->ev_used.push_back({phase, i});
+  const int i = ev_take(D, 2);
+  if (i < 0) return -1;
+  ev_record(D, ev_pool(D)[i]);
+  ev_list(D).push_back({phase, i});
   return i;
 }
 void ev_end(fpg_domain* D, int i) {
-  if (i >= 0) cudaEventRecord(D->evpool[i + 1], D->st);
+  if (i >= 0) ev_record(D, ev_pool(D)[i + 1]);
+}
+// Add the event pairs of the last graph replay to the phase totals.
+void ev_collect_replay(fpg_domain* D) {
+  if (!D->replay_pending) return;
+  D->replay_pending = false;
+  for (auto& pr : D->gev_used) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, D->gev[pr.second], D->gev[pr.second + 1]) == cudaSuccess)
+      D->phase_ms[pr.first] += ms;
+  }
+  for (int i = 0; i < kPhases; ++i) D->phase_launches[i] += D->cycle_phase_launches[i];
 }
 void ev_collect(fpg_domain* D) {
   if (!D->profiling) return;
   cudaStreamSynchronize(D->st);
+  ev_collect_replay(D);
   for (auto& pr : D->ev_used) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, D->evpool[pr.second], D->evpool[pr.second + 1]) == cudaSuccess)
@@ -472,18 +533,23 @@ inline void count(fpg_domain* D, int phase, int n) {
 // a1 on nvec centre vectors (nvec <= nrhs): v (FP64, stride nc) -> z (prec).
 fpg_status precond(fpg_domain* D, const double* v, void* z, int nvec, const int* active) {
   const Layout& L = D->L;
+  if (D->precond_kind != 0) {  // Sec. 3.2 comparison preconditioners: identity, Jacobi
+    FPG_CUDA_TRY(launch_precond_simple(v, z, D->prec, L.nc, L.n, D->delta, D->desc.kappa, D->ctab, L.armmask,
+                                       D->precond_kind == 2, active, nvec, D->gx, D->st));
+    count(D, 0, 1);
+    return FPG_OK;
+  }
   BatchDesc ib{L.nc, {0, 0, 0, 0}, 1};
   int nl = 0;
   const FastSolveTables& tb = D->prec == 64 ? D->tC64 : D->tC32;
   cudaEvent_t* evp = nullptr;
-  if (D->profiling && D->ev_next + 6 <= (int)D->evpool.size()) {
+  const int i = ev_take(D, 6);
+  if (i >= 0) {
     // pool events i..i+5: start/end of the forward DST, the Thomas solve, the inverse DST
-    const int i = D->ev_next;
-    D->ev_next += 6;
-    evp = &D->evpool[i];
-    D->ev_used.push_back({7, i});
-    D->ev_used.push_back({8, i + 2});
-    D->ev_used.push_back({9, i + 4});
+    evp = &ev_pool(D)[i];
+    ev_list(D).push_back({7, i});
+    ev_list(D).push_back({8, i + 2});
+    ev_list(D).push_back({9, i + 4});
   }
   FPG_CUDA_TRY(launch_fast_solve(D->prec, D->prec, tb, D->LC, v, ib, z, ib, nvec, D->scratch, active, 1, D->st,
                                  &nl, evp));
@@ -580,6 +646,7 @@ fpg_status stage_setup(fpg_domain* D, double* p) {
   KrylovState& k = D->ks;
   const int nrhs = D->desc.nrhs;
   D->cycles_run = 0;
+  D->accept_rounds = 0;
   D->first_cycle = true;
   D->p_cur = p;
   // ||f|| per RHS and the absolute tolerance
@@ -618,6 +685,7 @@ fpg_status stage_restart(fpg_domain* D) {
 
 fpg_status stage_poll(fpg_domain* D, bool* all_done) {
   FPG_CUDA_TRY(cudaEventSynchronize(D->ev_flags));
+  ev_collect_replay(D);
   bool all = true;
   for (int r = 0; r < D->desc.nrhs; ++r) all = all && D->h_done_pinned[r];
   const int max_cycles = (D->desc.max_iters + D->desc.restart - 1) / D->desc.restart + 2;
@@ -625,7 +693,7 @@ fpg_status stage_poll(fpg_domain* D, bool* all_done) {
   return FPG_OK;
 }
 
-fpg_status stage_cycle(fpg_domain* D) {
+fpg_status issue_cycle(fpg_domain* D) {
   const Layout& L = D->L;
   KrylovState& k = D->ks;
   const int nrhs = D->desc.nrhs, m = D->desc.restart;
@@ -633,14 +701,13 @@ fpg_status stage_cycle(fpg_domain* D) {
   const int zprec = D->prec;
   const size_t zel = zprec == 64 ? 8 : 4;
   int e;
-  D->cycles_run++;
   for (int j = 0; j < m; ++j) {
     double* vj = k.V + (size_t)j * nrhs * L.nc;
     void* zj = (char*)k.Z + zel * (size_t)j * nrhs * L.nc;
     e = ev_begin(D, 0);
     FPG_TRY(precond(D, vj, zj, nrhs, k.active));
     ev_end(D, e);
-    const int csz = D->use_cluster ? arnoldi_cluster_size(L.nc) : 0;
+    const int csz = D->use_cluster ? (D->tune_csz > 0 && L.nc <= 262144 ? D->tune_csz : arnoldi_cluster_size(L.nc)) : 0;
     const int ept = (csz > 0 && D->arnoldi_mode == 1) ? arnoldi_reg_ept(L.nc, csz) : 0;
     if (ept > 0) {
       // a2's interface part, then one launch for a2's stencil + a3 + a4
@@ -688,6 +755,72 @@ fpg_status stage_cycle(fpg_domain* D) {
   return FPG_OK;
 }
 
+// Drop the captured cycle (after anything that changes the launch sequence).
+void drop_graph(fpg_domain* D) {
+  if (D->cycle_exec) cudaGraphExecDestroy(D->cycle_exec);
+  D->cycle_exec = nullptr;
+}
+
+// One restart cycle.  Every cycle of a domain issues the same launches with the
+// same arguments (right-hand sides that converge switch off through the device
+// "active" flags), so the cycle is captured once into a CUDA graph and replayed:
+// one launch per cycle instead of ~5 per Arnoldi step.  Not used while
+// profiling (the per-phase events are host-recorded) or on the legacy default
+// stream, which cannot be captured.
+fpg_status stage_cycle(fpg_domain* D) {
+  D->cycles_run++;
+  if (!D->use_graphs || D->st == nullptr) return issue_cycle(D);
+  if (D->cycle_exec && D->graph_profiled != D->profiling) drop_graph(D);
+  if (!D->cycle_exec) {
+    const long long before = D->launches;
+    long long ph_before[kPhases];
+    for (int i = 0; i < kPhases; ++i) ph_before[i] = D->phase_launches[i];
+    if (D->profiling && D->gev.empty()) {
+      D->gev.resize(12 * D->desc.restart + 8);
+      for (auto& ev : D->gev) FPG_CUDA_TRY(cudaEventCreate(&ev));
+    }
+    D->gev_used.clear();
+    D->gev_next = 0;
+    D->capturing = true;
+    cudaGraph_t graph = nullptr;
+    cudaError_t be = cudaStreamBeginCapture(D->st, cudaStreamCaptureModeThreadLocal);
+    if (be != cudaSuccess) {
+      D->capturing = false;
+      record_cuda_error(be, "cudaStreamBeginCapture");
+      return FPG_ECUDA;
+    }
+    const fpg_status st = issue_cycle(D);
+    const cudaError_t ce = cudaStreamEndCapture(D->st, &graph);
+    D->capturing = false;
+    for (int i = 0; i < kPhases; ++i) {
+      D->cycle_phase_launches[i] = D->phase_launches[i] - ph_before[i];
+      D->phase_launches[i] = ph_before[i];
+    }
+    D->graph_profiled = D->profiling;
+    if (st != FPG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ce != cudaSuccess) {
+      record_cuda_error(ce, "cudaStreamEndCapture");
+      return FPG_ECUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&D->cycle_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      D->cycle_exec = nullptr;
+      record_cuda_error(ie, "cudaGraphInstantiate");
+      return FPG_ECUDA;
+    }
+    D->cycle_kernels = D->launches - before;  // kernels in one replay
+    D->launches = before;
+  }
+  FPG_CUDA_TRY(cudaGraphLaunch(D->cycle_exec, D->st));
+  D->launches += D->cycle_kernels;
+  if (D->graph_profiled) D->replay_pending = true;
+  return FPG_OK;
+}
+
 fpg_status stage_finish(fpg_domain* D) {
   const Layout& L = D->L;
   KrylovState& k = D->ks;
@@ -705,20 +838,44 @@ fpg_status stage_finish(fpg_domain* D) {
                                    D->gxf, D->gres, nullptr, 0.0, nullptr, D->st));
   count(D, 6, 2);
   ev_end(D, e);
+  // acceptance check: right-hand sides above rtol resume with a tighter Schur target
+  D->accept_rounds++;
+  if (D->accept_rounds <= kAcceptRounds) {
+    FPG_CUDA_TRY(cudaMemsetAsync(D->resume_dev, 0, sizeof(int), D->st));
+    FPG_CUDA_TRY(launch_tighten(D->gres, D->desc.rtol, 0.25, k.tolabs, k.done, nrhs, D->resume_dev, D->st));
+    count(D, 6, 1);
+    FPG_CUDA_TRY(cudaMemcpyAsync(D->h_done_pinned + nrhs, D->resume_dev, sizeof(int), cudaMemcpyDeviceToHost, D->st));
+  }
+  FPG_CUDA_TRY(cudaEventRecord(D->ev_flags, D->st));
   return check_launch();
 }
 
-// One domain, start to finish (the host waits once per restart cycle).
+// After stage_finish: does any right-hand side resume (waits for the check)?
+fpg_status stage_resume(fpg_domain* D, bool* resume) {
+  *resume = false;
+  if (D->accept_rounds > kAcceptRounds) return FPG_OK;
+  FPG_CUDA_TRY(cudaEventSynchronize(D->ev_flags));
+  *resume = D->h_done_pinned[D->desc.nrhs] > 0;
+  return FPG_OK;
+}
+
+// One domain, start to finish (the host waits once per restart cycle, and once
+// per acceptance check).
 fpg_status solve_launch(fpg_domain* D, double* p) {
   FPG_TRY(stage_setup(D, p));
   for (;;) {
-    FPG_TRY(stage_restart(D));
-    bool done = false;
-    FPG_TRY(stage_poll(D, &done));
-    if (done) break;
-    FPG_TRY(stage_cycle(D));
+    for (;;) {
+      FPG_TRY(stage_restart(D));
+      bool done = false;
+      FPG_TRY(stage_poll(D, &done));
+      if (done) break;
+      FPG_TRY(stage_cycle(D));
+    }
+    FPG_TRY(stage_finish(D));
+    bool resume = false;
+    FPG_TRY(stage_resume(D, &resume));
+    if (!resume) return FPG_OK;
   }
-  return stage_finish(D);
 }
 
 fpg_status collect_info(fpg_domain* D, fpg_solve_info* info) {
@@ -880,7 +1037,7 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   if (!err) err = cp(D->arms_dev, arms, sizeof(arms));
   if (!err) err = cudaMemsetAsync(D->f, 0, sizeof(double) * nrhs * L.ntot, D->st);
   if (!err) err = cudaStreamSynchronize(D->st);
-  if (!err) err = cudaMallocHost((void**)&D->h_done_pinned, sizeof(int) * nrhs);
+  if (!err) err = cudaMallocHost((void**)&D->h_done_pinned, sizeof(int) * (nrhs + 1));
   if (!err) err = cudaEventCreateWithFlags(&D->ev_flags, cudaEventDisableTiming);
   if (err) {
     record_cuda_error(err, "fpg_create_domain");
@@ -895,6 +1052,8 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
 void fpg_destroy_domain(fpg_domain* d) {
   if (!d) return;
   for (auto ev : d->evpool) cudaEventDestroy(ev);
+  for (auto ev : d->gev) cudaEventDestroy(ev);
+  drop_graph(d);
   if (d->ev_flags) cudaEventDestroy(d->ev_flags);
   if (d->h_done_pinned) cudaFreeHost(d->h_done_pinned);
   delete d;
@@ -917,8 +1076,12 @@ fpg_status fpg_solve_many(fpg_domain* const* doms, int32_t count, double* const*
       FPG_TRY(stage_poll(doms[i], &done));
       if (done) {
         FPG_TRY(stage_finish(doms[i]));
-        live[i] = 0;
-        --remaining;
+        bool resume = false;
+        FPG_TRY(stage_resume(doms[i], &resume));
+        if (!resume) {
+          live[i] = 0;
+          --remaining;
+        }
       } else {
         FPG_TRY(stage_cycle(doms[i]));
       }
@@ -1076,6 +1239,81 @@ fpg_status fpg_apply_global(fpg_domain* d, const double* p, double* y, int32_t n
   return check_launch();
 }
 
+fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out) {
+  if (!d) return FPG_EINVAL;
+  drop_graph(d);
+  const Layout& L = d->L;
+  KrylovState& k = d->ks;
+  const int nrhs = d->desc.nrhs, m = d->desc.restart;
+  FastSolveTables& tb = d->prec == 64 ? d->tC64 : d->tC32;
+  cudaEvent_t e0, e1;
+  FPG_CUDA_TRY(cudaEventCreate(&e0));
+  FPG_CUDA_TRY(cudaEventCreate(&e1));
+  // timing inputs: the first two basis vectors and w (contents do not affect the time)
+  FPG_CUDA_TRY(cudaMemsetAsync(k.V, 0, sizeof(double) * (size_t)2 * nrhs * L.nc, d->st));
+  FPG_CUDA_TRY(cudaMemsetAsync(k.w, 0, sizeof(double) * (size_t)nrhs * L.nc, d->st));
+  auto time_it = [&](auto&& fn, int reps) -> float {
+    fn();  // warm-up (also sets kernel attributes)
+    if (cudaGetLastError() != cudaSuccess) return 1e30f;
+    cudaEventRecord(e0, d->st);
+    for (int i = 0; i < reps; ++i) fn();
+    cudaEventRecord(e1, d->st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) return 1e30f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / reps;
+  };
+  // a1: line pairs per CTA x modes per CTA
+  int best_q = 0, best_mt = 0;
+  float best = 1e30f;
+  static const int qs[] = {1, 2, 4, 8};
+  static const int mts[] = {1, 2, 4, 8, 16};
+  for (int q : qs) {
+    for (int mt : mts) {
+      tb.q = q;
+      tb.mt = mt;
+      const float t = time_it([&] { precond(d, k.V, k.Z, nrhs, nullptr); }, 3);
+      if (t < best) { best = t; best_q = q; best_mt = mt; }
+    }
+  }
+  tb.q = best_q;
+  tb.mt = best_mt;
+  // a3 (+a4): cluster size of the fused Arnoldi step, at j = m/2
+  int best_c = 0;
+  float best_a = 1e30f;
+  if (d->use_cluster && L.nc <= 262144) {
+    const int j = m / 2 < 1 ? 0 : m / 2;
+    const int hcol = m + 1, hrhs = m * (m + 1);
+    static const int cs_[] = {1, 2, 4, 8, 16};
+    for (int c : cs_) {
+      const int ept = d->arnoldi_mode == 1 ? arnoldi_reg_ept(L.nc, c) : 0;
+      const float t = time_it([&] {
+        if (ept > 0)
+          launch_arnoldi_reg(c, k.V, (long long)nrhs * L.nc, k.w, nullptr, 64, nullptr, 0, 0.0, 0.0, 0,
+                             k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j, nrhs, k.H, hcol, hrhs, nullptr, nullptr,
+                             nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0, 0, d->st);
+        else
+          launch_arnoldi_cluster(c, k.V, (long long)nrhs * L.nc, k.w, k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j,
+                                 nrhs, k.H, hcol, hrhs, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
+                                 nullptr, nullptr, 0, 0, d->st);
+      }, 3);
+      if (t < best_a) { best_a = t; best_c = c; }
+    }
+    d->tune_csz = best_c;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (out) {
+    out->q = best_q;
+    out->mt = best_mt;
+    out->cluster = best_c;
+    out->reserved = 0;
+    out->precond_ms = best;
+    out->arnoldi_ms = best_a < 1e29f ? best_a : 0.0;
+  }
+  return check_launch();
+}
+
 fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
   if (!d) return FPG_EINVAL;
   switch (option) {
@@ -1083,6 +1321,16 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
       if (value < 0 || value > 2) return FPG_EINVAL;
       d->use_cluster = value != 0;
       d->arnoldi_mode = value == 2 ? 2 : 1;
+      drop_graph(d);
+      return FPG_OK;
+    case FPG_OPT_CUDA_GRAPHS:
+      d->use_graphs = value != 0;
+      drop_graph(d);
+      return FPG_OK;
+    case FPG_OPT_PRECOND:
+      if (value < 0 || value > 2) return FPG_EINVAL;
+      d->precond_kind = value;
+      drop_graph(d);
       return FPG_OK;
     default: return FPG_EINVAL;
   }

@@ -22,6 +22,17 @@ namespace {
 
 constexpr int kFsThreads = 256;
 
+// Event record that also works inside a stream capture (there it must be an
+// external record to become a graph node that records at every replay).
+void record_event(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, st);
+}
+
 __device__ __forceinline__ const double* batch_ptr(const double* base, const BatchDesc& d, int b) {
   return base + (long long)(b / d.nper) * d.rhs_stride + d.off[b % d.nper];
 }
@@ -220,7 +231,7 @@ size_t thomas_smem(int ns) {
 // Launch the scanned Thomas solve with the widest mode tile that fits 64 KB.
 template <typename T>
 cudaError_t launch_thomas_scan(T* scratch, int n, int ns, const T* rpiv, const T* mneg, int nblk,
-                               const int* active, int nper_active, cudaStream_t st) {
+                               const int* active, int nper_active, cudaStream_t st, int mt_force) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_thomas_scan<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -232,7 +243,8 @@ cudaError_t launch_thomas_scan(T* scratch, int n, int ns, const T* rpiv, const T
   }
   const size_t budget = 64 * 1024;
 #define FPG_THOMAS_TRY(MTV)                                                                              \
-  if (thomas_smem<T, MTV>(ns) <= budget || MTV == 1) {                                                  \
+  if ((mt_force > 0 ? (mt_force == MTV && thomas_smem<T, MTV>(ns) <= 200 * 1024)                         \
+                    : thomas_smem<T, MTV>(ns) <= budget) || MTV == 1) {                                  \
     dim3 grid((n + MTV - 1) / MTV, nblk);                                                               \
     const int threads = 32 * (MTV < 8 ? MTV : 8);                                                       \
     k_thomas_scan<T, MTV><<<grid, threads, thomas_smem<T, MTV>(ns), st>>>(scratch, n, ns, rpiv, mneg,  \
@@ -391,35 +403,38 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
     dim3 grid((L.ns + lpb - 1) / lpb, nblk);
     k_dense_forward<T><<<grid, kFsThreads, smem, st>>>(in, ib, L, n, (const T*)pl.dense, scratch, lpb, active,
                                                       nper_active);
-    launch_thomas_scan<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st);
+    launch_thomas_scan<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st,
+                          tb.mt);
     k_dense_inverse<T, To><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, n, (const T*)pl.dense, lpb,
                                                           active, nper_active);
     return cudaGetLastError();
   }
-  const int Q = pairs_per_block<T>(pl, L.ns, nblk);
+  int Q = pairs_per_block<T>(pl, L.ns, nblk);
+  if (tb.q > 0 && dst_smem_bytes<T>(pl.p, pl.N, tb.q, pl.mode) <= 200 * 1024) Q = tb.q;
   const size_t smem = dst_smem_bytes<T>(pl.p, pl.N, Q, pl.mode);
   dim3 grid((L.ns + 2 * Q - 1) / (2 * Q), nblk);
   // ev (optional): start/end pairs around the three kernels
   const int maxr = plan_maxr(pl);
-  if (ev) cudaEventRecord(ev[0], st);
+  if (ev) record_event(ev[0], st);
   if (maxr == 5)
     k_fft_forward<T, 5><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
   else if (maxr == 13)
     k_fft_forward<T, 13><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
   else
     k_fft_forward<T, 43><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
-  if (ev) cudaEventRecord(ev[1], st);
-  if (ev) cudaEventRecord(ev[2], st);
-  launch_thomas_scan<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st);
-  if (ev) cudaEventRecord(ev[3], st);
-  if (ev) cudaEventRecord(ev[4], st);
+  if (ev) record_event(ev[1], st);
+  if (ev) record_event(ev[2], st);
+  launch_thomas_scan<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st,
+                          tb.mt);
+  if (ev) record_event(ev[3], st);
+  if (ev) record_event(ev[4], st);
   if (maxr == 5)
     k_fft_inverse<T, To, 5><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
   else if (maxr == 13)
     k_fft_inverse<T, To, 13><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
   else
     k_fft_inverse<T, To, 43><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
-  if (ev) cudaEventRecord(ev[5], st);
+  if (ev) record_event(ev[5], st);
   return cudaGetLastError();
 }
 

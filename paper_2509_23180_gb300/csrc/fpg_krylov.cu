@@ -80,11 +80,8 @@ k_stencil_c(const Tz* __restrict__ z, long long zstride, double* __restrict__ w,
        idx += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(idx / n), i = (int)(idx - (long long)j * n);
     const double zc = ld(zr, idx);
-    double s = -4.0 * zc;
-    if (i > 0) s += ld(zr, idx - 1);
-    if (i < n - 1) s += ld(zr, idx + 1);
-    if (j > 0) s += ld(zr, idx - n);
-    if (j < n - 1) s += ld(zr, idx + n);
+    const double s = stencil_sum(zc, i > 0 ? ld(zr, idx - 1) : 0.0, i < n - 1 ? ld(zr, idx + 1) : 0.0,
+                                 j > 0 ? ld(zr, idx - n) : 0.0, j < n - 1 ? ld(zr, idx + n) : 0.0);
     double v = fma(delta, s, kappa * zc);
     if (i == 0 && (armmask & 1)) v -= cr[0 * n + j];
     if (i == n - 1 && (armmask & 2)) v -= cr[1 * n + j];
@@ -344,11 +341,8 @@ k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const dou
         const double* cr = corr + (long long)r * 4 * n;
         const int jj = (int)(idx / n), ii = (int)(idx - (long long)jj * n);
         const double zc = (double)zr[idx];
-        double sacc = -4.0 * zc;
-        if (ii > 0) sacc += (double)zr[idx - 1];
-        if (ii < n - 1) sacc += (double)zr[idx + 1];
-        if (jj > 0) sacc += (double)zr[idx - n];
-        if (jj < n - 1) sacc += (double)zr[idx + n];
+        const double sacc = stencil_sum(zc, ii > 0 ? (double)zr[idx - 1] : 0.0, ii < n - 1 ? (double)zr[idx + 1] : 0.0,
+                                        jj > 0 ? (double)zr[idx - n] : 0.0, jj < n - 1 ? (double)zr[idx + n] : 0.0);
         x = fma(delta, sacc, kappa * zc);
         if (ii == 0 && (armmask & 1)) x -= cr[0 * n + jj];
         if (ii == n - 1 && (armmask & 2)) x -= cr[1 * n + jj];
@@ -650,11 +644,8 @@ k_arm_residual(const double* __restrict__ rhs, const double* __restrict__ x, dou
          idx += (long long)gridDim.x * blockDim.x) {
       const int j = (int)(idx / nx), i = (int)(idx - (long long)j * nx);
       const double xc = xr[idx];
-      double s = -4.0 * xc;
-      if (i > 0) s += xr[idx - 1];
-      if (i < nx - 1) s += xr[idx + 1];
-      if (j > 0) s += xr[idx - nx];
-      if (j < ny - 1) s += xr[idx + nx];
+      const double s = stencil_sum(xc, i > 0 ? xr[idx - 1] : 0.0, i < nx - 1 ? xr[idx + 1] : 0.0,
+                                   j > 0 ? xr[idx - nx] : 0.0, j < ny - 1 ? xr[idx + nx] : 0.0);
       o[idx] = fr[idx] - fma(delta, s, kappa * xc);
     }
   }
@@ -741,11 +732,8 @@ k_global_apply(const double* __restrict__ p, double* __restrict__ y, const doubl
     int blk, i, j;
     locate(idx, n, ao, &blk, &i, &j);
     const double pc = pr[idx];
-    double s = -4.0 * pc;
-    s += nb_value(pr, n, ao, blk, i, j, 1, 0);
-    s += nb_value(pr, n, ao, blk, i, j, -1, 0);
-    s += nb_value(pr, n, ao, blk, i, j, 0, 1);
-    s += nb_value(pr, n, ao, blk, i, j, 0, -1);
+    const double s = stencil_sum(pc, nb_value(pr, n, ao, blk, i, j, -1, 0), nb_value(pr, n, ao, blk, i, j, 1, 0),
+                                 nb_value(pr, n, ao, blk, i, j, 0, -1), nb_value(pr, n, ao, blk, i, j, 0, 1));
     const double kp = fma(delta, s, kappa * pc);
     if (y) y[(long long)r * ntot + idx] = kp;
     if (f) {
@@ -784,6 +772,49 @@ __global__ void k_residual_finalize(const double* __restrict__ part, int gmax, i
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Comparison preconditioners of Sec. 3.2 (P = I and the Jacobi P = D_2).
+// Jacobi: z = v / diag(L_c) with diag(L_c) = -4 delta + kappa on C, minus, on the
+// line next to arm a, the diagonal of delta^2 Q diag(g) Q, which is c(0) - c(2q+2)
+// at position q of that line (the Toeplitz-minus-Hankel form of the interface table).
+template <typename To>
+__global__ void __launch_bounds__(kThreads)
+k_precond_simple(const double* __restrict__ v, To* __restrict__ z, long long len, int n, double delta, double kappa,
+                 const double* __restrict__ ctab, int armmask, int jacobi, const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (active != nullptr && !active[r]) return;
+  const double* vr = v + (long long)r * len;
+  To* zr = z + (long long)r * len;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < len;
+       idx += (long long)gridDim.x * blockDim.x) {
+    double x = vr[idx];
+    if (jacobi) {
+      const int j = (int)(idx / n), i = (int)(idx - (long long)j * n);
+      double d = -4.0 * delta + kappa;
+      if (i == 0 && (armmask & 1)) d -= ctab[0] - ctab[2 * j + 2];
+      if (i == n - 1 && (armmask & 2)) d -= ctab[0] - ctab[2 * j + 2];
+      if (j == 0 && (armmask & 4)) d -= ctab[0] - ctab[2 * i + 2];
+      if (j == n - 1 && (armmask & 8)) d -= ctab[0] - ctab[2 * i + 2];
+      x /= d;
+    }
+    zr[idx] = (To)x;
+  }
+}
+
+// Acceptance check (P8 reading): a right-hand side whose global residual is above
+// rtol after back substitution goes back into the iteration with its Schur
+// tolerance scaled by `factor`; its iterate u is kept.  Flags how many resume.
+__global__ void k_tighten(const double* __restrict__ gres, double rtol, double factor, double* __restrict__ tolabs,
+                          int* __restrict__ done, int nrhs, int* __restrict__ resume_count) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  if (gres[r] > rtol) {
+    tolabs[r] *= factor;
+    done[r] = 0;
+    atomicAdd(resume_count, 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers (library-internal).
 cudaError_t launch_schur_reduced(const void* z, int zprec, long long zstride, int n, const double* ctab,
                                  const int* arms_dev, int narms, double* corr, const int* active, int nrhs,
@@ -802,6 +833,25 @@ cudaError_t launch_schur_reduced(const void* z, int zprec, long long zstride, in
   else
     k_schur_lines<float><<<grid, 128, smem, st>>>((const float*)z, zstride, n, ctab, arms_dev, narms, corr,
                                                    active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_precond_simple(const double* v, void* z, int zprec, long long len, int n, double delta,
+                                  double kappa, const double* ctab, int armmask, int jacobi, const int* active,
+                                  int nrhs, int gx, cudaStream_t st) {
+  dim3 grid(gx, nrhs);
+  if (zprec == 64)
+    k_precond_simple<double><<<grid, kThreads, 0, st>>>(v, (double*)z, len, n, delta, kappa, ctab, armmask, jacobi,
+                                                        active);
+  else
+    k_precond_simple<float><<<grid, kThreads, 0, st>>>(v, (float*)z, len, n, delta, kappa, ctab, armmask, jacobi,
+                                                       active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tighten(const double* gres, double rtol, double factor, double* tolabs, int* done, int nrhs,
+                           int* resume_count, cudaStream_t st) {
+  k_tighten<<<(nrhs + 127) / 128, 128, 0, st>>>(gres, rtol, factor, tolabs, done, nrhs, resume_count);
   return cudaGetLastError();
 }
 

@@ -393,3 +393,77 @@ def test_solve_many_mixed_batch_same_as_alone(lib):
         ref = D.Factor(O.assemble(geom, n, kappa)).solve(f)
         for r in range(nrhs):
             assert rel(P[r], ref[r]) < 1e-9
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_autotune_keeps_the_answer(lib, prec):
+    """After fpg_autotune picks launch shapes, the solve still matches K^{-1} f."""
+    from paper_2509_23180_gb300 import binding as B
+    n = 48
+    K = O.assemble("cross", n, 0.0)
+    f = W.rhs_batch("cross", n, [4, 5], kind="fourier")
+    d = domain(B, "cross", n, 0.0, nrhs=2, rtol=1e-12, precond_precision=prec)
+    choice = d.autotune()
+    assert choice["q"] in (1, 2, 4, 8) and choice["mt"] in (1, 2, 4, 8, 16)
+    assert choice["precond_ms"] > 0
+    d.set_rhs(dev(f))
+    p = torch.zeros_like(dev(f))
+    st, info = d.solve(p)
+    assert st == B.FPG_OK
+    ref = D.Factor(K).solve(f)
+    for r in range(2):
+        assert rel(host(p)[r], ref[r]) < 1e-9
+
+
+def test_preconditioner_study_matches_oracle(lib):
+    """Sec. 3.2 on the GPU: with P = I and Jacobi the solve still reaches K^{-1} f,
+    and the FFT preconditioner needs more than seven times fewer iterations.
+    Iteration counts follow the oracle's GMRES within a few steps (rounding
+    differs, so they are not compared exactly)."""
+    from paper_2509_23180_gb300 import binding as B
+    n = 24
+    K = O.assemble("cross", n, 0.0)
+    bs = S.BlockSystem(K, "cross", n)
+    f = W.rhs_batch("cross", n, [0], kind="fourier")
+    ref = D.Factor(K).solve(f)
+    its = {}
+    for name in ("fft", "none", "jacobi"):
+        d = domain(B, "cross", n, 0.0, nrhs=1, restart=30, rtol=1e-10, max_iters=3000)
+        d.set_option(B.OPT_PRECOND, B.PRECOND[name])
+        d.set_rhs(dev(f))
+        p = torch.zeros_like(dev(f))
+        st, info = d.solve(p)
+        assert st == B.FPG_OK, name
+        assert rel(host(p)[0], ref[0]) < 1e-8
+        its[name] = info[0]["iterations"]
+        _, oinfo = S.algorithm1(bs, f[0], m=30, rtol=1e-10 * 0.9,
+                                precond={"fft": "A_c", "none": "none", "jacobi": "jacobi"}[name], max_iters=3000)
+        assert abs(its[name] - oinfo["iterations"]) <= max(3, 0.05 * oinfo["iterations"]), (name, its, oinfo)
+    assert 7 * its["fft"] < its["none"] and 7 * its["fft"] < its["jacobi"], its
+
+
+def test_graphs_profiling_and_direct_launches_agree(lib):
+    """Replaying the captured restart cycle, launching directly, and replaying a
+    graph captured with profiling events all give the identical solution; the
+    profiled replays report per-kernel device time."""
+    from paper_2509_23180_gb300 import binding as B
+    n = 40
+    f = W.rhs_batch("cross", n, [2, 3], kind="fourier")
+    st = torch.cuda.Stream()
+    outs = []
+    for graphs, prof in ((1, False), (0, False), (1, True)):
+        d = B.Domain(B.make_desc("cross", n, -10.0, nrhs=2, restart=8, rtol=1e-11), stream=st)
+        d.set_option(B.OPT_CUDA_GRAPHS, graphs)
+        d.set_profiling(prof)
+        d.set_rhs(dev(f))
+        torch.cuda.synchronize()
+        p = torch.zeros_like(dev(f))
+        s, info = d.solve(p)
+        assert s == B.FPG_OK and info[0]["restarts"] >= 2
+        outs.append(host(p))
+        if prof:
+            ph = d.phase_stats()
+            assert ph["k_fft_forward"]["launches"] > 0 and ph["k_fft_forward"]["ms"] > 0
+            assert ph["arnoldi"]["launches"] > 0 and ph["arnoldi"]["ms"] > 0
+        d.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])

@@ -65,3 +65,24 @@ def test_fourier_rhs_is_seeded_and_vanishes_on_block_edges():
     off = n * n
     wblk = a[off:off + nx * ny].reshape(ny, nx)
     assert np.allclose(wblk[:, -1], 0.0, atol=1e-14)
+
+
+@pytest.mark.parametrize("geometry", ["cross", "T", "L"])
+def test_fourier_rhs_torch_matches_numpy(geometry):
+    """The torch evaluation of the seeded workload equals the numpy one."""
+    import torch
+    a = W.fourier_rhs(geometry, 21, 7)
+    b = W.fourier_rhs_torch(geometry, 21, 7, device="cpu").numpy()
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-14)
+
+
+def test_serving_stream_is_poisson():
+    """Exponential gaps with the requested mean; request fields in range."""
+    reqs = W.serving_requests(4000, 200.0, seed=0)
+    t = np.array([r["arrival_s"] for r in reqs])
+    gaps = np.diff(t)
+    assert abs(gaps.mean() - 1 / 200.0) < 0.1 / 200.0
+    assert abs(gaps.std() - gaps.mean()) < 0.1 * gaps.mean()  # exponential: std == mean
+    assert {r["geometry"] for r in reqs} == {"L", "T", "cross"}
+    assert {r["n"] for r in reqs} == {64, 128, 256, 512, 1024}
+    assert min(r["nrhs"] for r in reqs) == 1 and max(r["nrhs"] for r in reqs) == 8

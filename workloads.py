@@ -163,3 +163,29 @@ def serving_requests(count: int, rate_per_s: float, seed: int = 0,
             "seed": int(rng.integers(0, 2**31 - 1)),
         })
     return reqs
+
+
+def fourier_rhs_torch(geometry: str, n: int, seed: int, device="cuda", modes: int = 16, kmax: int = 8):
+    """fourier_rhs evaluated with torch on `device` (same coefficient draws, same
+    formula; used where many large inputs are needed quickly, e.g. a request
+    stream).  Returns a float64 tensor in block order."""
+    import torch
+    parts = []
+    for b in GEOMETRY_BLOCKS[geometry]:
+        rng = np.random.default_rng(seed * 1000 + BLOCK_ID[b])
+        kx = rng.integers(1, kmax + 1, size=modes)
+        ky = rng.integers(1, kmax + 1, size=modes)
+        c = rng.standard_normal(modes)
+        nx, ny = block_shape(b, n)
+        i0, j0 = block_first_node(b, n)
+        h = 1.0 / (n + 1)
+        x0, x1, y0, y1 = BLOCK_BOX[b]
+        xs = (i0 + torch.arange(nx, dtype=torch.float64, device=device)) * h
+        ys = (j0 + torch.arange(ny, dtype=torch.float64, device=device)) * h
+        xi = (xs - x0) / (x1 - x0)
+        eta = (ys - y0) / (y1 - y0)
+        sx = torch.sin(torch.as_tensor(kx, dtype=torch.float64, device=device)[:, None] * math.pi * xi[None, :])
+        sy = torch.sin(torch.as_tensor(ky, dtype=torch.float64, device=device)[:, None] * math.pi * eta[None, :])
+        w = torch.as_tensor(c / (kx ** 2 + ky ** 2), dtype=torch.float64, device=device)
+        parts.append(torch.einsum("q,qy,qx->yx", w, sy, sx).reshape(-1))
+    return torch.cat(parts)
