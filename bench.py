@@ -45,11 +45,13 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--schedule", default="concurrent", choices=["sequential", "concurrent"],
                     help="solve the two kappa domains one after the other, or concurrently on two streams")
-    ap.add_argument("--config", default="default", choices=["default", "small", "precision", "batching", "serving"],
+    ap.add_argument("--config", default="default",
+                    choices=["default", "small", "precision", "batching", "serving", "fastsolve"],
                     help="default: the 256^2 cross workload; the others run the other workloads as extra lines")
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: HBM admission budget")
+    ap.add_argument("--no-fused", action="store_true", help="fastsolve: force the three-kernel fast solve")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -431,6 +433,7 @@ def roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, nrhs):
         "k_fft_forward": (dst_flops, (8 + te) * pts, alu),
         "k_thomas_scan": (5.0 * pts, 2 * te * pts, alu),
         "k_fft_inverse": (dst_flops + pts, (te + te) * pts, alu),
+        "k_fast_solve_fused": (2 * dst_flops + 6.0 * pts, (8 + te) * pts, alu),
         "k_arnoldi_cluster": (costs["arnoldi_flops"] * nrhs, costs["arnoldi_bytes"] * nrhs, fp64_peak),
     }
     phase_of = {"k_arnoldi_cluster": "arnoldi"}
@@ -608,6 +611,51 @@ def run_extra(args):
                       "all_converged": stt == B.FPG_OK})
         for dd in doms:
             dd.close()
+    elif args.config == "fastsolve":
+        # a1 on its own: the preconditioner applied to a batch of centre vectors
+        # that does not fit in L2 (default 64 x 512^2: 128 MB in, 64 MB out in FP32)
+        n, nv = args.n, args.seeds
+        d = B.Domain(B.make_desc("cross", n, 0.0, nrhs=nv, restart=1, rtol=args.rtol,
+                                 precond_precision=args.precision))
+        if args.no_fused:
+            d.set_option(B.OPT_FUSED_FASTSOLVE, 0)
+        v = torch.as_tensor(W.random_block_vectors(nv, n * n, 5), device="cuda")
+        z = torch.zeros((nv, n * n), dtype=torch.float64 if args.precision == 64 else torch.float32, device="cuda")
+        for _ in range(args.warmup):
+            d.apply_precond(v, z, nv)
+        d.set_profiling(True)
+        tot = 0.0
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            ms, _, _ = _timed(lambda: d.apply_precond(v, z, nv))
+            tot += ms
+        ph = d.phase_stats()
+        d.set_profiling(False)
+        peaks = measured_peaks()
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        te = 8 if args.precision == 64 else 4
+        pts = nv * n * n
+        kern = {}
+        for name, byts in (("k_fft_forward", (8 + te) * pts), ("k_thomas_scan", 2 * te * pts),
+                           ("k_fft_inverse", 2 * te * pts), ("k_fast_solve_fused", (8 + te) * pts)):
+            q = ph[name]
+            if not q["launches"] or q["ms"] <= 0:
+                continue
+            t = q["ms"] / q["launches"] * 1e-3
+            kern[name] = {"avg_launch_us": t * 1e6, "algorithmic_bytes": byts, "achieved_gbs": byts / t / 1e9,
+                          "hbm_frac": byts / t / 1e9 / hbm}
+        ms = tot / args.steps
+        byts = (8 + te) * pts
+        lines.append({"metric": "fast solve (a1) HBM GB/s", "value": byts / (ms * 1e-3) / 1e9, "unit": "GB/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "f32" if args.precision == 32 else "f64",
+                      "data": "synthetic",
+                      "config": {"workload": f"a1 on {nv} x {n}^2 centre vectors (FP64 in, "
+                                             f"{'FP32' if te == 4 else 'FP64'} out)",
+                                 "algorithmic_bytes_per_application": byts, "l2": "flushed before every step"},
+                      "hbm_frac_per_application": byts / (ms * 1e-3) / 1e9 / hbm, "kernels": kern,
+                      "peak_gbs": hbm})
+        d.close()
     elif args.config == "serving":
         from paper_2509_23180_gb300 import serve
         reqs = W.serving_requests(args.requests, args.rate, seed=0)

@@ -232,7 +232,14 @@ typedef enum {
    * 1: none (P = I);  2: Jacobi, the inverse diagonal of L_c.
    * With 1 or 2 the flexible basis is still stored in the domain's
    * precond_precision. */
-  FPG_OPT_PRECOND = 3
+  FPG_OPT_PRECOND = 3,
+  /* 1: the fast solve (a1, and the arm solves) runs as one kernel per batch --
+   * one thread-block cluster per block, the block's spectral coefficients kept
+   * in the cluster's shared memory, v read once and z written once -- when the
+   * block fits (n <= 512 in FP64 or FP32).  0 (default; faster on GB300 at the
+   * sizes measured so far) and larger blocks: three kernels (DST, Thomas,
+   * inverse DST) through a scratch array. */
+  FPG_OPT_FUSED_FASTSOLVE = 4
 } fpg_option;
 
 /* Set an option on a domain (affects later calls).  FPG_EINVAL if unknown. */
@@ -262,7 +269,8 @@ fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out);
  * the device time (ms, CUDA events on the domain stream) of each phase.
  * phase: 0 = preconditioner (a1), 1 = Schur matvec (a2), 2 = Arnoldi (a3),
  * 3 = Givens (a4), 4 = cycle end (a5), 5 = setup/finish (a6), 6 = residual (a7);
- * 7, 8, 9 = the three kernels of a1 on their own (forward DST, Thomas, inverse DST).
+ * 7, 8, 9 = the three kernels of a1 on their own (forward DST, Thomas, inverse DST);
+ * 10 = the fused one-pass fast-solve kernel of a1.
  * Timing is only collected when enabled with fpg_set_profiling(d, 1). */
 fpg_status fpg_set_profiling(fpg_domain* d, int32_t on);
 fpg_status fpg_phase_stats(fpg_domain* d, int32_t phase, int64_t* launches, double* ms);

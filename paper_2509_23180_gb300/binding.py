@@ -22,9 +22,10 @@ FPG_EBUDGET = 7
 OPT_ARNOLDI_CLUSTER = 1
 OPT_CUDA_GRAPHS = 2
 OPT_PRECOND = 3
+OPT_FUSED_FASTSOLVE = 4
 PRECOND = {"fft": 0, "none": 1, "jacobi": 2}
 PHASES = ("precond", "schur", "arnoldi", "givens", "cycle_end", "setup_finish", "residual",
-          "k_fft_forward", "k_thomas_scan", "k_fft_inverse")
+          "k_fft_forward", "k_thomas_scan", "k_fft_inverse", "k_fast_solve_fused")
 
 
 class DomainDesc(ctypes.Structure):

@@ -87,7 +87,7 @@ using namespace fpg;
 namespace {
 
 constexpr int kGmax = 1024;
-constexpr int kPhases = 10;  // 7..9: the three fast-solve kernels of a1 on their own
+constexpr int kPhases = 11;  // 7..9: the three fast-solve kernels of a1; 10: the fused one-pass kernel
 constexpr int kMaxEvents = 8192;
 // The Schur iteration stops at this fraction of the requested relative residual,
 // so that the global residual (which adds the rounding of the arm back
@@ -543,21 +543,27 @@ fpg_status precond(fpg_domain* D, const double* v, void* z, int nvec, const int*
   int nl = 0;
   const FastSolveTables& tb = D->prec == 64 ? D->tC64 : D->tC32;
   cudaEvent_t* evp = nullptr;
-  const int i = ev_take(D, 6);
+  const int i = ev_take(D, 8);
   if (i >= 0) {
-    // pool events i..i+5: start/end of the forward DST, the Thomas solve, the inverse DST
+    // pool events i..i+7: start/end of the forward DST, the Thomas solve, the
+    // inverse DST and the fused kernel (the path not taken records empty pairs)
     evp = &ev_pool(D)[i];
     ev_list(D).push_back({7, i});
     ev_list(D).push_back({8, i + 2});
     ev_list(D).push_back({9, i + 4});
+    ev_list(D).push_back({10, i + 6});
   }
   FPG_CUDA_TRY(launch_fast_solve(D->prec, D->prec, tb, D->LC, v, ib, z, ib, nvec, D->scratch, active, 1, D->st,
                                  &nl, evp));
   count(D, 0, nl);
   if (evp) {
-    D->phase_launches[7] += 1;
-    D->phase_launches[8] += 1;
-    D->phase_launches[9] += 1;
+    if (nl == 1) {
+      D->phase_launches[10] += 1;
+    } else {
+      D->phase_launches[7] += 1;
+      D->phase_launches[8] += 1;
+      D->phase_launches[9] += 1;
+    }
   }
   return FPG_OK;
 }
@@ -1327,6 +1333,10 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
       d->use_graphs = value != 0;
       drop_graph(d);
       return FPG_OK;
+    case FPG_OPT_FUSED_FASTSOLVE:
+      for (auto* t : {&d->tC64, &d->tC32, &d->tA64, &d->tA32}) t->fused = value != 0;
+      drop_graph(d);
+      return FPG_OK;
     case FPG_OPT_PRECOND:
       if (value < 0 || value > 2) return FPG_EINVAL;
       d->precond_kind = value;
@@ -1352,6 +1362,7 @@ fpg_status fpg_set_profiling(fpg_domain* d, int32_t on) {
 
 fpg_status fpg_phase_stats(fpg_domain* d, int32_t phase, int64_t* launches, double* ms) {
   if (!d || phase < 0 || phase >= kPhases) return FPG_EINVAL;
+  ev_collect(d);  // events of operator calls made since the last solve
   if (launches) *launches = d->phase_launches[phase];
   if (ms) *ms = d->phase_ms[phase];
   return FPG_OK;

@@ -142,17 +142,22 @@ __device__ __forceinline__ void stockham_dispatch(int R, const C2<T>* in, C2<T>*
           case 11: stockham_stage<11, T>(in, out, Q, N, Ns, pitch, W); break;
           case 13: stockham_stage<13, T>(in, out, Q, N, Ns, pitch, W); break;
           default:
-            if constexpr (MAXR >= 43) {
+            if constexpr (MAXR >= 19) {
               switch (R) {
                 case 17: stockham_stage<17, T>(in, out, Q, N, Ns, pitch, W); break;
                 case 19: stockham_stage<19, T>(in, out, Q, N, Ns, pitch, W); break;
-                case 23: stockham_stage<23, T>(in, out, Q, N, Ns, pitch, W); break;
-                case 29: stockham_stage<29, T>(in, out, Q, N, Ns, pitch, W); break;
-                case 31: stockham_stage<31, T>(in, out, Q, N, Ns, pitch, W); break;
-                case 37: stockham_stage<37, T>(in, out, Q, N, Ns, pitch, W); break;
-                case 41: stockham_stage<41, T>(in, out, Q, N, Ns, pitch, W); break;
-                case 43: stockham_stage<43, T>(in, out, Q, N, Ns, pitch, W); break;
-                default: break;  // plans only contain the radices above
+                default:
+                  if constexpr (MAXR >= 43) {
+                    switch (R) {
+                      case 23: stockham_stage<23, T>(in, out, Q, N, Ns, pitch, W); break;
+                      case 29: stockham_stage<29, T>(in, out, Q, N, Ns, pitch, W); break;
+                      case 31: stockham_stage<31, T>(in, out, Q, N, Ns, pitch, W); break;
+                      case 37: stockham_stage<37, T>(in, out, Q, N, Ns, pitch, W); break;
+                      case 41: stockham_stage<41, T>(in, out, Q, N, Ns, pitch, W); break;
+                      case 43: stockham_stage<43, T>(in, out, Q, N, Ns, pitch, W); break;
+                      default: break;  // plans only contain the radices above
+                    }
+                  }
               }
             }
         }
@@ -160,11 +165,11 @@ __device__ __forceinline__ void stockham_dispatch(int R, const C2<T>* in, C2<T>*
   }
 }
 
-// Largest radix family a plan needs: 5, 13 or 43.
+// Largest radix family a plan needs: 5, 13, 19 or 43.
 __host__ __device__ inline int plan_maxr(const DstPlan& pl) {
   int mx = 2;
   for (int i = 0; i < pl.nrad; ++i) mx = pl.rad[i] > mx ? pl.rad[i] : mx;
-  return mx <= 5 ? 5 : (mx <= 13 ? 13 : 43);
+  return mx <= 5 ? 5 : (mx <= 13 ? 13 : (mx <= 19 ? 19 : 43));
 }
 
 // Runs all stages; returns the buffer holding the result (b0 or b1).

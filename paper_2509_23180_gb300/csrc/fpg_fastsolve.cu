@@ -143,31 +143,35 @@ k_thomas_scan(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv
   constexpr int P = MT + 1;
   const int k0 = blockIdx.x * MT;
   const int mt = min(MT, n - k0);
+  const int c = (ns + 31) / 32;  // rows per lane
+  // element (s, k) at s*P + k + s/c: the one-word skew per lane chunk makes the
+  // lane-to-lane stride c*P + 1 odd, so the 32 lanes hit 32 different banks
+  const size_t span = (size_t)ns * P + 32;
   T* xs = reinterpret_cast<T*>(smem_raw);
-  T* rs = xs + (size_t)ns * P;
-  T* ms = rs + (size_t)ns * P;
+  T* rs = xs + span;
+  T* ms = rs + span;
+#define FPG_SK(s, k) ((s) * P + (k) + (s) / c)
   T* col = scratch + (long long)b * ns * n + k0;
   for (int idx = threadIdx.x; idx < ns * MT; idx += blockDim.x) {
     const int s = idx / MT, k = idx - s * MT;
     if (k < mt) {
       const long long g = (long long)s * n + k;
-      xs[s * P + k] = col[g];
-      rs[s * P + k] = rpiv[g + k0];
-      ms[s * P + k] = mneg[g + k0];
+      xs[FPG_SK(s, k)] = col[g];
+      rs[FPG_SK(s, k)] = rpiv[g + k0];
+      ms[FPG_SK(s, k)] = mneg[g + k0];
     }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int c = (ns + 31) / 32;
   const int s0 = min(ns, lane * c), s1 = min(ns, s0 + c);
   for (int k = warp; k < mt; k += nw) {
     // forward: y_s = r_s f_s + m_s y_{s-1}
     T acc = T(0), pr = T(1);
     for (int s = s0; s < s1; ++s) {
-      const T m = ms[s * P + k];
-      acc = fma(m, acc, rs[s * P + k] * xs[s * P + k]);
+      const T m = ms[FPG_SK(s, k)];
+      acc = fma(m, acc, rs[FPG_SK(s, k)] * xs[FPG_SK(s, k)]);
       pr *= m;
-      xs[s * P + k] = acc;
+      xs[FPG_SK(s, k)] = acc;
     }
     T Y = acc, Pp = pr;
 #pragma unroll
@@ -183,18 +187,18 @@ k_thomas_scan(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv
     if (cin != T(0)) {
       T q = T(1);
       for (int s = s0; s < s1; ++s) {
-        q *= ms[s * P + k];
-        xs[s * P + k] = fma(q, cin, xs[s * P + k]);
+        q *= ms[FPG_SK(s, k)];
+        xs[FPG_SK(s, k)] = fma(q, cin, xs[FPG_SK(s, k)]);
       }
     }
     // backward: x_s = y_s + m_s x_{s+1}
     acc = T(0);
     pr = T(1);
     for (int s = s1 - 1; s >= s0; --s) {
-      const T m = ms[s * P + k];
-      acc = fma(m, acc, xs[s * P + k]);
+      const T m = ms[FPG_SK(s, k)];
+      acc = fma(m, acc, xs[FPG_SK(s, k)]);
       pr *= m;
-      xs[s * P + k] = acc;
+      xs[FPG_SK(s, k)] = acc;
     }
     Y = acc;
     Pp = pr;
@@ -211,21 +215,22 @@ k_thomas_scan(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv
     if (cdn != T(0)) {
       T q = T(1);
       for (int s = s1 - 1; s >= s0; --s) {
-        q *= ms[s * P + k];
-        xs[s * P + k] = fma(q, cdn, xs[s * P + k]);
+        q *= ms[FPG_SK(s, k)];
+        xs[FPG_SK(s, k)] = fma(q, cdn, xs[FPG_SK(s, k)]);
       }
     }
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < ns * MT; idx += blockDim.x) {
     const int s = idx / MT, k = idx - s * MT;
-    if (k < mt) col[(long long)s * n + k] = xs[s * P + k];
+    if (k < mt) col[(long long)s * n + k] = xs[FPG_SK(s, k)];
   }
+#undef FPG_SK
 }
 
 template <typename T, int MT>
 size_t thomas_smem(int ns) {
-  return 3 * sizeof(T) * (size_t)ns * (MT + 1);
+  return 3 * sizeof(T) * ((size_t)ns * (MT + 1) + 32);
 }
 
 // Launch the scanned Thomas solve with the widest mode tile that fits 64 KB.
@@ -390,9 +395,11 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
     cudaFuncSetAttribute(k_dense_inverse<T, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_fft_forward<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_fft_forward<T, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fft_forward<T, 19>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_fft_forward<T, 43>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_fft_inverse<T, To, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_fft_inverse<T, To, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fft_inverse<T, To, 19>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_fft_inverse<T, To, 43>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
@@ -420,6 +427,8 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
     k_fft_forward<T, 5><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
   else if (maxr == 13)
     k_fft_forward<T, 13><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
+  else if (maxr == 19)
+    k_fft_forward<T, 19><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
   else
     k_fft_forward<T, 43><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
   if (ev) record_event(ev[1], st);
@@ -432,6 +441,8 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
     k_fft_inverse<T, To, 5><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
   else if (maxr == 13)
     k_fft_inverse<T, To, 13><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
+  else if (maxr == 19)
+    k_fft_inverse<T, To, 19><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
   else
     k_fft_inverse<T, To, 43><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
   if (ev) record_event(ev[5], st);
@@ -440,13 +451,36 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
 
 }  // namespace
 
+cudaError_t launch_fast_solve_fused(int prec, int out_prec, const FastSolveTables& tb, LineLayout L,
+                                    const double* in, BatchDesc ib, void* out, BatchDesc ob, int nblk,
+                                    const int* active, int nper_active, cudaStream_t st);
+
 // Public (library-internal) entry: precision 64 -> double everywhere; 32 ->
-// float compute, output type chosen by out_prec (64 or 32).
+// float compute, output type chosen by out_prec (64 or 32).  The fused
+// one-pass kernel runs when the block fits one cluster (and tb.fused); the
+// three-kernel path otherwise.  ev (optional): 8 events, start/end pairs of the
+// forward DST, Thomas, inverse DST and the fused kernel.
 cudaError_t launch_fast_solve(int prec, int out_prec, const FastSolveTables& tb, LineLayout L,
                               const double* in, BatchDesc ib, void* out, BatchDesc ob, int nblk,
                               void* scratch, const int* active, int nper_active, cudaStream_t st,
                               int* launches, cudaEvent_t* ev) {
   if (nblk <= 0) return cudaSuccess;
+  if (tb.fused) {
+    if (ev) record_event(ev[6], st);
+    const cudaError_t e = launch_fast_solve_fused(prec, out_prec, tb, L, in, ib, out, ob, nblk, active, nper_active, st);
+    if (e == cudaSuccess) {
+      if (ev) {
+        record_event(ev[7], st);
+        for (int i = 0; i < 6; ++i) record_event(ev[i], st);
+      }
+      if (launches) *launches += 1;
+      return cudaSuccess;
+    }
+    if (e != cudaErrorNotSupported) return e;
+    cudaGetLastError();  // not a launch failure: this shape goes the three-kernel way
+  }
+  if (ev) record_event(ev[6], st);
+  if (ev) record_event(ev[7], st);
   if (launches) *launches += 3;
   if (prec == 64) {
     return fast_solve_impl<double, double>(tb, L, in, ib, (double*)out, ob, nblk, (double*)scratch, active,

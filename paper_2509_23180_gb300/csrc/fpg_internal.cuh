@@ -38,6 +38,7 @@ struct FastSolveTables {
   const void* mneg;   // -delta r_s, [ns][n], compute precision
   int q = 0;          // line pairs per CTA in the DST kernels (0: built-in choice)
   int mt = 0;         // modes per CTA in the Thomas kernel (0: built-in choice)
+  int fused = 0;      // 1: one-pass cluster kernel when the block fits
 };
 
 // Offsets of the arm blocks W, E, S, N inside one full vector (-1 = absent).

@@ -463,7 +463,33 @@ def test_graphs_profiling_and_direct_launches_agree(lib):
         outs.append(host(p))
         if prof:
             ph = d.phase_stats()
-            assert ph["k_fft_forward"]["launches"] > 0 and ph["k_fft_forward"]["ms"] > 0
+            fs = "k_fast_solve_fused" if ph["k_fast_solve_fused"]["launches"] > 0 else "k_fft_forward"
+            assert ph[fs]["launches"] > 0 and ph[fs]["ms"] > 0
             assert ph["arnoldi"]["launches"] > 0 and ph["arnoldi"]["ms"] > 0
         d.close()
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("fused", [1, 0])
+@pytest.mark.parametrize("prec,tol", [(64, 1e-11), (32, 5e-5)])
+@pytest.mark.parametrize("n", [6, 64, 100, 256])
+def test_fused_and_three_kernel_fast_solve(lib, fused, prec, tol, n):
+    """The one-pass cluster kernel and the three-kernel path both reproduce the
+    oracle's A^{-1} v on the centre block and on the arms (both layouts)."""
+    from paper_2509_23180_gb300 import binding as B
+    kappa = -10.0
+    K = O.assemble("cross", n, kappa)
+    bs = S.BlockSystem(K, "cross", n)
+    d = domain(B, "cross", n, kappa, nrhs=3, precond_precision=prec)
+    d.set_option(B.OPT_FUSED_FASTSOLVE, fused)
+    v = W.random_block_vectors(3, n * n, seed=n)
+    z = torch.zeros((3, n * n), dtype=torch.float64 if prec == 64 else torch.float32, device="cuda")
+    d.apply_precond(dev(v), z, 3)
+    want = np.stack([bs.block_solve("C", vi) for vi in v])
+    assert rel(host(z).astype(np.float64), want) < tol
+    for blk, name in ((1, "W"), (3, "S")):  # arm solves are FP64 in both modes
+        nx, ny = W.block_shape(name, n)
+        va = W.random_block_vectors(2, nx * ny, seed=blk)
+        za = torch.zeros_like(dev(va))
+        d.block_solve(blk, dev(va), za, 2)
+        assert rel(host(za), np.stack([bs.block_solve(name, x) for x in va])) < 1e-11
