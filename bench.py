@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: HBM admission budget")
-    ap.add_argument("--no-fused", action="store_true", help="fastsolve: force the three-kernel fast solve")
+    ap.add_argument("--option", action="append", default=[], metavar="NAME=VALUE",
+                    help="fpg_set_option on every domain, e.g. DST_ENGINE=1, FUSED_FASTSOLVE=1, ARNOLDI_THREADS=512")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -62,7 +63,7 @@ def workload(args):
             "geometry": "cross", "n": args.n, "unknowns_per_rhs": args.n ** 2 + 4 * args.n * (args.n + 1),
             "kappas": [0.0, -10.0], "rhs_per_kappa": args.seeds, "solves_per_step": 2 * args.seeds,
             "restart": args.restart, "rtol": args.rtol, "precond_precision": args.precision,
-            "schur_mode": "reduced", "schedule": args.schedule,
+            "schur_mode": "reduced", "schedule": args.schedule, "options": list(args.option),
             "l2": "flushed before every step (512 MiB write)"}
 
 
@@ -215,6 +216,7 @@ class Runner:
             desc = B.make_desc("cross", args.n, k, nrhs=nrhs, restart=args.restart, rtol=args.rtol,
                                precond_precision=precision)
             self.doms[k] = B.Domain(desc, stream=self.streams[k])
+            apply_options(self.doms[k], args)
             self.fdev[k] = torch.as_tensor(f_host[k], device="cuda")
             self.pdev[k] = torch.zeros_like(self.fdev[k])
         self.pool = ThreadPoolExecutor(max_workers=len(self.kappas))
@@ -350,7 +352,8 @@ def run_ours(args, rank, world):
     peaks = measured_peaks()
     fp64_peak = B.probe_fma_peak(64)
     fp32_peak = B.probe_fma_peak(32)
-    roof = roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, args.seeds)
+    roof = roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, args.seeds,
+                    run.doms[run.kappas[0]].fast_solve_path())
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -409,6 +412,14 @@ def variants(args, f_host, flush):
     return out
 
 
+def apply_options(d, args):
+    """--option NAME=VALUE: fpg_set_option(d, FPG_OPT_NAME, VALUE)."""
+    from paper_2509_23180_gb300 import binding as B
+    for opt in args.option:
+        name, val = opt.split("=", 1)
+        d.set_option(getattr(B, "OPT_" + name.strip().upper()), int(val))
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -416,7 +427,7 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, nrhs):
+def roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, nrhs, fs_path=0):
     """Roofline of the dominant kernel: its algorithmic work per launch over its
     average device duration.  Durations come from CUDA events the library
     records around each kernel launch when profiling is on (the a1 kernels one
@@ -429,33 +440,36 @@ def roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, nrhs):
     te = 8 if args.precision == 64 else 4
     alu = fp64_peak if args.precision == 64 else fp32_peak
     dst_flops = 2.5 * math.log2(args.n) * pts
+    # keyed by the library's phase slot; the kernel behind it is named below
     cands = {
-        "k_fft_forward": (dst_flops, (8 + te) * pts, alu),
-        "k_thomas_scan": (5.0 * pts, 2 * te * pts, alu),
-        "k_fft_inverse": (dst_flops + pts, (te + te) * pts, alu),
-        "k_fast_solve_fused": (2 * dst_flops + 6.0 * pts, (8 + te) * pts, alu),
-        "k_arnoldi_cluster": (costs["arnoldi_flops"] * nrhs, costs["arnoldi_bytes"] * nrhs, fp64_peak),
+        "dst_forward": (dst_flops, (8 + te) * pts, alu),
+        "thomas": (5.0 * pts, 2 * te * pts, alu),
+        "dst_inverse": (dst_flops + pts, (te + te) * pts, alu),
+        "fast_solve_fused": (2 * dst_flops + 6.0 * pts, (8 + te) * pts, alu),
+        "arnoldi": (costs["arnoldi_flops"] * nrhs, costs["arnoldi_bytes"] * nrhs, fp64_peak),
     }
-    phase_of = {"k_arnoldi_cluster": "arnoldi"}
+    from paper_2509_23180_gb300 import binding as B
+    names = dict(B.FAST_SOLVE_KERNELS.get(fs_path, {}), arnoldi="k_arnoldi_cluster_reg")
     best, best_ms = None, -1.0
     for name in cands:
-        ph = phases.get(phase_of.get(name, name), {"ms": 0.0, "launches": 0})
+        ph = phases.get(name, {"ms": 0.0, "launches": 0})
         if ph["launches"] and ph["ms"] > best_ms:
             best, best_ms = name, ph["ms"]
     if best is None:
         return {"kernel": None, "bound": "alu", "achieved": None, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
                 "frac": None, "traffic": None, "note": "no profiled kernel launches in the timed region"}
     flops, byts, peak_alu = cands[best]
-    ph = phases[phase_of.get(best, best)]
+    ph = phases[best]
     t = ph["ms"] * 1e-3 / ph["launches"]
     ach_alu = flops / t
     ach_hbm = byts / t / 1e9
-    fp64_kernel = best == "k_arnoldi_cluster" or args.precision == 64
-    out = {"kernel": best, "avg_launch_us": t * 1e6, "launches": ph["launches"],
+    fp64_kernel = best == "arnoldi" or args.precision == 64
+    kname = names.get(best, best)
+    out = {"kernel": kname, "phase": best, "avg_launch_us": t * 1e6, "launches": ph["launches"],
            "measured": "CUDA events around every launch of the kernel in one profiled step of the same "
                        "workload (sequential schedule) after the timed steps",
            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
-           "traffic": traffic_for(best, args)}
+           "traffic": traffic_for(kname, args)}
     if fp64_kernel:
         out.update({"bound": "alu", "achieved": ach_alu / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
                     "frac": ach_alu / peak_alu, "hbm_frac": ach_hbm / hbm,
@@ -472,7 +486,8 @@ def traffic_for(kernel, args):
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     srcs = ["paper_2509_23180_gb300/csrc/fpg_fastsolve.cu", "paper_2509_23180_gb300/csrc/fpg_dst.cuh",
-            "paper_2509_23180_gb300/csrc/fpg_krylov.cu"]
+            "paper_2509_23180_gb300/csrc/fpg_krylov.cu", "paper_2509_23180_gb300/csrc/fpg_dstline.cuh",
+            "paper_2509_23180_gb300/csrc/fpg_dstline_impl.cuh"]
     h = hashlib.sha1()
     for s in srcs:
         h.update(open(os.path.join(ROOT, s), "rb").read())
@@ -617,8 +632,7 @@ def run_extra(args):
         n, nv = args.n, args.seeds
         d = B.Domain(B.make_desc("cross", n, 0.0, nrhs=nv, restart=1, rtol=args.rtol,
                                  precond_precision=args.precision))
-        if args.no_fused:
-            d.set_option(B.OPT_FUSED_FASTSOLVE, 0)
+        apply_options(d, args)
         v = torch.as_tensor(W.random_block_vectors(nv, n * n, 5), device="cuda")
         z = torch.zeros((nv, n * n), dtype=torch.float64 if args.precision == 64 else torch.float32, device="cuda")
         for _ in range(args.warmup):
@@ -636,13 +650,14 @@ def run_extra(args):
         te = 8 if args.precision == 64 else 4
         pts = nv * n * n
         kern = {}
-        for name, byts in (("k_fft_forward", (8 + te) * pts), ("k_thomas_scan", 2 * te * pts),
-                           ("k_fft_inverse", 2 * te * pts), ("k_fast_solve_fused", (8 + te) * pts)):
+        knames = B.FAST_SOLVE_KERNELS.get(d.fast_solve_path(), {})
+        for name, byts in (("dst_forward", (8 + te) * pts), ("thomas", 2 * te * pts),
+                           ("dst_inverse", 2 * te * pts), ("fast_solve_fused", (8 + te) * pts)):
             q = ph[name]
             if not q["launches"] or q["ms"] <= 0:
                 continue
             t = q["ms"] / q["launches"] * 1e-3
-            kern[name] = {"avg_launch_us": t * 1e6, "algorithmic_bytes": byts, "achieved_gbs": byts / t / 1e9,
+            kern[knames.get(name, name)] = {"avg_launch_us": t * 1e6, "algorithmic_bytes": byts, "achieved_gbs": byts / t / 1e9,
                           "hbm_frac": byts / t / 1e9 / hbm}
         ms = tot / args.steps
         byts = (8 + te) * pts

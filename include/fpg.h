@@ -239,7 +239,19 @@ typedef enum {
    * block fits (n <= 512 in FP64 or FP32).  0 (default; faster on GB300 at the
    * sizes measured so far) and larger blocks: three kernels (DST, Thomas,
    * inverse DST) through a scratch array. */
-  FPG_OPT_FUSED_FASTSOLVE = 4
+  FPG_OPT_FUSED_FASTSOLVE = 4,
+  /* CTAs per right-hand side of the fused Arnoldi step, 1..16 (0: built-in
+   * choice or the autotuner's).  Only used for centre vectors of at most
+   * 262144 points. */
+  FPG_OPT_ARNOLDI_CSZ = 5,
+  /* Thread cap per CTA of the register-resident Arnoldi kernel: 256 or 512
+   * (0: 256 when the centre slice of one CTA fits, else 512). */
+  FPG_OPT_ARNOLDI_THREADS = 6,
+  /* DST kernels of the fast solve: 0 (default) the size-specialised line DST
+   * where one is compiled for the length and pays off (see
+   * fpg_fast_solve_path), 1 always the generic FFT engine, 2 the specialised
+   * kernels wherever one is compiled. */
+  FPG_OPT_DST_ENGINE = 7
 } fpg_option;
 
 /* Set an option on a domain (affects later calls).  FPG_EINVAL if unknown. */
@@ -251,14 +263,15 @@ typedef struct {
   int32_t q;         /* line pairs per CTA in the DST kernels of a1 */
   int32_t mt;        /* modes per CTA in the Thomas kernel of a1 */
   int32_t cluster;   /* CTAs per right-hand side in the fused Arnoldi step (0: not tuned) */
-  int32_t reserved;
+  int32_t threads;   /* thread cap per CTA of that step (256 or 512; 0: not tuned) */
   double precond_ms; /* time of one preconditioner application (all nrhs vectors) at the choice */
   double arnoldi_ms; /* time of one Arnoldi step at j = m/2 at the choice */
 } fpg_tune_result;
 
 /* Time the launch shapes of the hot kernels on this domain's own buffers
  * (precision, n, nrhs as created) and keep the fastest: the line batch (q) and
- * mode tile (mt) of the fast solve, the cluster size of the Arnoldi step.
+ * mode tile (mt) of the fast solve, the cluster size and CTA width of the
+ * Arnoldi step.
  * Overwrites the domain's Krylov buffers (call it between solves).  The
  * choices stay with the domain; out (may be NULL) reports them. */
 fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out);
@@ -276,6 +289,25 @@ fpg_status fpg_set_profiling(fpg_domain* d, int32_t on);
 fpg_status fpg_phase_stats(fpg_domain* d, int32_t phase, int64_t* launches, double* ms);
 /* Total kernel launches issued by the library on this domain so far. */
 fpg_status fpg_launch_count(fpg_domain* d, int64_t* launches);
+
+/* Element-wise conversion between FP64 and FP32 on the device, done with the
+ * integer-pipe routines of the mixed-precision path (GB300 runs the hardware
+ * conversion on its FP64 pipe).  (in_prec, out_prec) is (64, 32): round to
+ * nearest even, magnitudes below 2^-126 give a signed zero, 2^128 and above,
+ * inf and NaN give inf; or (32, 64): exact, binary32 subnormals give a signed
+ * zero.  in and out are device arrays of count elements; the kernel runs on
+ * `stream` (a cudaStream_t, NULL = default stream).  FPG_EINVAL on null
+ * pointers, count < 0 or another precision pair. */
+fpg_status fpg_convert(const void* in, int32_t in_prec, void* out, int32_t out_prec, int64_t count, void* stream);
+
+/* Kernels the preconditioner of this domain runs for the centre block:
+ * 0 = generic FFT engine (k_fft_forward, k_thomas_scan, k_fft_inverse),
+ * 1 = size-specialised line DST (k_dst_lines_fwd, k_thomas_scan, k_dst_lines_inv;
+ *     n = 64, 256, 512 in FP64 -- when the batch of nrhs centre blocks is large
+ *     enough to fill the GPU -- and also 1024 in FP32),
+ * 2 = dense DST (lengths with no FFT plan), 3 = fused one-pass cluster kernel
+ * (FPG_OPT_FUSED_FASTSOLVE), 4 = no fast solve (identity or Jacobi). */
+fpg_status fpg_fast_solve_path(fpg_domain* d, int32_t* path);
 
 /* FMA throughput of this GPU measured by a short library kernel (FLOP/s,
  * 2 per FMA): precision 64 or 32.  Used as the ALU roofline. */

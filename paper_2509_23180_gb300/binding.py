@@ -23,9 +23,20 @@ OPT_ARNOLDI_CLUSTER = 1
 OPT_CUDA_GRAPHS = 2
 OPT_PRECOND = 3
 OPT_FUSED_FASTSOLVE = 4
+OPT_ARNOLDI_CSZ = 5
+OPT_ARNOLDI_THREADS = 6
+OPT_DST_ENGINE = 7
 PRECOND = {"fft": 0, "none": 1, "jacobi": 2}
 PHASES = ("precond", "schur", "arnoldi", "givens", "cycle_end", "setup_finish", "residual",
-          "k_fft_forward", "k_thomas_scan", "k_fft_inverse", "k_fast_solve_fused")
+          "dst_forward", "thomas", "dst_inverse", "fast_solve_fused")
+# fpg_fast_solve_path -> kernel names of the a1 phases
+FAST_SOLVE_KERNELS = {
+    0: {"dst_forward": "k_fft_forward", "thomas": "k_thomas_scan", "dst_inverse": "k_fft_inverse"},
+    1: {"dst_forward": "k_dst_lines_fwd", "thomas": "k_thomas_scan", "dst_inverse": "k_dst_lines_inv"},
+    2: {"dst_forward": "k_dense_forward", "thomas": "k_thomas_scan", "dst_inverse": "k_dense_inverse"},
+    3: {"fast_solve_fused": "k_fast_solve_fused"},
+    4: {},
+}
 
 
 class DomainDesc(ctypes.Structure):
@@ -42,7 +53,7 @@ class SolveInfo(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int32), ("mt", ctypes.c_int32), ("cluster", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("precond_ms", ctypes.c_double), ("arnoldi_ms", ctypes.c_double)]
+                ("threads", ctypes.c_int32), ("precond_ms", ctypes.c_double), ("arnoldi_ms", ctypes.c_double)]
 
 
 class FpgError(RuntimeError):
@@ -82,6 +93,8 @@ _SIGS = {
     "fpg_set_profiling": ([_P, _I32], _I32),
     "fpg_phase_stats": ([_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D)], _I32),
     "fpg_launch_count": ([_P, ctypes.POINTER(_I64)], _I32),
+    "fpg_fast_solve_path": ([_P, ctypes.POINTER(_I32)], _I32),
+    "fpg_convert": ([_P, _I32, _P, _I32, _I64, _P], _I32),
     "fpg_probe_fma_peak": ([_I32, ctypes.POINTER(_D)], _I32),
     "fpg_fast_solve_noalloc": ([_I32, _D, _P, _P, _I32, _P], _I32),
 }
@@ -237,7 +250,7 @@ class Domain:
         """fpg_autotune: time the launch shapes of the hot kernels, keep the fastest."""
         r = TuneResult()
         _check(self.lib.fpg_autotune(self.handle, ctypes.byref(r)), "fpg_autotune")
-        return {"q": r.q, "mt": r.mt, "cluster": r.cluster, "precond_ms": r.precond_ms, "arnoldi_ms": r.arnoldi_ms}
+        return {"q": r.q, "mt": r.mt, "cluster": r.cluster, "threads": r.threads, "precond_ms": r.precond_ms, "arnoldi_ms": r.arnoldi_ms}
 
     def set_option(self, option: int, value: int):
         _check(self.lib.fpg_set_option(self.handle, option, value), "fpg_set_option")
@@ -254,10 +267,27 @@ class Domain:
             out[name] = {"launches": int(ln.value), "ms": float(ms.value)}
         return out
 
+    def fast_solve_path(self) -> int:
+        """fpg_fast_solve_path: which kernels the preconditioner runs (see FAST_SOLVE_KERNELS)."""
+        out = _I32()
+        _check(self.lib.fpg_fast_solve_path(self.handle, ctypes.byref(out)), "fpg_fast_solve_path")
+        return int(out.value)
+
     def launch_count(self) -> int:
         out = _I64()
         _check(self.lib.fpg_launch_count(self.handle, ctypes.byref(out)), "fpg_launch_count")
         return int(out.value)
+
+
+def convert(src, dst, stream=None):
+    """fpg_convert: FP64 <-> FP32 with the library's integer-pipe conversion
+    (src and dst are CUDA tensors of the same length)."""
+    import torch
+    lib = load()
+    prec = {torch.float64: 64, torch.float32: 32}
+    st = stream if stream is not None else torch.cuda.current_stream(src.device)
+    _check(lib.fpg_convert(_ptr(src), prec[src.dtype], _ptr(dst), prec[dst.dtype], src.numel(), st.cuda_stream),
+           "fpg_convert")
 
 
 def solve_many(domains, ps):

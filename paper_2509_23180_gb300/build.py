@@ -63,7 +63,7 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
         return obj
 
     srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 8))) as ex:
         objs = list(ex.map(compile_one, srcs))
     if not _newer(LIB, objs):
         cmd = [nv, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]

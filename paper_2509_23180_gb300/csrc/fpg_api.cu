@@ -55,9 +55,10 @@ cudaError_t launch_precond_simple(const double* v, void* z, int zprec, long long
                                   double kappa, const double* ctab, int armmask, int jacobi, const int* active,
                                   int nrhs, int gx, cudaStream_t st);
 int arnoldi_cluster_size(long long len);
-int arnoldi_reg_ept(long long len, int csz);
-cudaError_t launch_arnoldi_reg(int csz, const double* V, long long vstride, const double* w, const void* z,
-                               int zprec, const double* corr, int n, double delta, double kappa, int armmask,
+int fast_solve_path(int prec, const FastSolveTables& tb, LineLayout L, int nblk);
+int arnoldi_reg_ept(long long len, int csz, int ntcap);
+cudaError_t launch_arnoldi_reg(int csz, int ntcap, const double* V, long long vstride, const double* w,
+                               const void* z, int zprec, const double* corr, int n, double delta, double kappa, int armmask,
                                double* vout, long long len, int j, int nrhs, double* H, int hcol_stride,
                                int hrhs_stride, double* cs, double* sn, double* g, double* res, int m,
                                const double* tolabs, int* active, int* kcyc, int* iters, int max_iters, int do_givens,
@@ -203,6 +204,7 @@ struct fpg_domain {
   bool use_cluster = true;
   int arnoldi_mode = 1;  // 1: register-resident fused kernel when it fits; 2: global-w cluster kernel
   int tune_csz = 0;      // Arnoldi cluster size chosen by fpg_autotune (0: built-in choice)
+  int tune_nt = 0;       // thread cap per CTA of the register Arnoldi kernel (0: 256, else 512)
   bool use_graphs = true;
   int precond_kind = 0;  // 0: A_c^{-1} (the paper's), 1: identity, 2: Jacobi
   int accept_rounds = 0;  // acceptance checks done in the current solve
@@ -714,14 +716,14 @@ fpg_status issue_cycle(fpg_domain* D) {
     FPG_TRY(precond(D, vj, zj, nrhs, k.active));
     ev_end(D, e);
     const int csz = D->use_cluster ? (D->tune_csz > 0 && L.nc <= 262144 ? D->tune_csz : arnoldi_cluster_size(L.nc)) : 0;
-    const int ept = (csz > 0 && D->arnoldi_mode == 1) ? arnoldi_reg_ept(L.nc, csz) : 0;
+    const int ept = (csz > 0 && D->arnoldi_mode == 1) ? arnoldi_reg_ept(L.nc, csz, D->tune_nt) : 0;
     if (ept > 0) {
       // a2's interface part, then one launch for a2's stencil + a3 + a4
       e = ev_begin(D, 1);
       FPG_TRY(schur_corr(D, zj, zprec, nrhs, k.active));
       ev_end(D, e);
       e = ev_begin(D, 2);
-      FPG_CUDA_TRY(launch_arnoldi_reg(csz, k.V, (long long)nrhs * L.nc, nullptr, zj, zprec, D->corr, L.n, D->delta,
+      FPG_CUDA_TRY(launch_arnoldi_reg(csz, D->tune_nt, k.V, (long long)nrhs * L.nc, nullptr, zj, zprec, D->corr, L.n, D->delta,
                                       D->desc.kappa, L.armmask, k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j, nrhs,
                                       k.H, hcol, hrhs, k.cs, k.sn, k.g, k.res, m, k.tolabs, k.active, k.kcyc,
                                       k.iters, D->desc.max_iters, 1, D->st));
@@ -1191,10 +1193,11 @@ fpg_status fpg_arnoldi_mgs(fpg_domain* d, const double* V, int32_t j, double* w,
                            int32_t nvec) {
   if (!d || !V || !w || !h || j < 0 || len <= 0 || nvec <= 0 || nvec > d->desc.nrhs) return FPG_EINVAL;
   // v_{j+1} overwrites w: normalise in place; same kernel choice as the solver
-  const int csz = d->use_cluster ? arnoldi_cluster_size(len) : 0;
-  const int ept = (csz > 0 && d->arnoldi_mode == 1) ? arnoldi_reg_ept(len, csz) : 0;
+  const int csz =
+      d->use_cluster ? (d->tune_csz > 0 && len <= 262144 ? d->tune_csz : arnoldi_cluster_size(len)) : 0;
+  const int ept = (csz > 0 && d->arnoldi_mode == 1) ? arnoldi_reg_ept(len, csz, d->tune_nt) : 0;
   if (ept > 0) {
-    FPG_CUDA_TRY(launch_arnoldi_reg(csz, V, (long long)nvec * len, w, nullptr, 64, nullptr, 0, 0.0, 0.0, 0, w, len, j,
+    FPG_CUDA_TRY(launch_arnoldi_reg(csz, d->tune_nt, V, (long long)nvec * len, w, nullptr, 64, nullptr, 0, 0.0, 0.0, 0, w, len, j,
                                     nvec, h, 0, j + 2, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
                                     nullptr, nullptr, 0, 0, d->st));
     d->launches += 1;
@@ -1272,7 +1275,7 @@ fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out) {
   // a1: line pairs per CTA x modes per CTA
   int best_q = 0, best_mt = 0;
   float best = 1e30f;
-  static const int qs[] = {1, 2, 4, 8};
+  static const int qs[] = {0, 1, 2, 4, 8};  // 0: size-specialised kernels where compiled, else built-in Q
   static const int mts[] = {1, 2, 4, 8, 16};
   for (int q : qs) {
     for (int mt : mts) {
@@ -1284,28 +1287,33 @@ fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out) {
   }
   tb.q = best_q;
   tb.mt = best_mt;
-  // a3 (+a4): cluster size of the fused Arnoldi step, at j = m/2
-  int best_c = 0;
+  // a3 (+a4): cluster size (and thread cap) of the fused Arnoldi step, at j = m/2
+  int best_c = 0, best_nt = 0;
   float best_a = 1e30f;
   if (d->use_cluster && L.nc <= 262144) {
     const int j = m / 2 < 1 ? 0 : m / 2;
     const int hcol = m + 1, hrhs = m * (m + 1);
-    static const int cs_[] = {1, 2, 4, 8, 16};
+    static const int cs_[] = {1, 2, 4, 8, 10, 12, 14, 15, 16};
+    static const int nts[] = {256, 512};
     for (int c : cs_) {
-      const int ept = d->arnoldi_mode == 1 ? arnoldi_reg_ept(L.nc, c) : 0;
-      const float t = time_it([&] {
-        if (ept > 0)
-          launch_arnoldi_reg(c, k.V, (long long)nrhs * L.nc, k.w, nullptr, 64, nullptr, 0, 0.0, 0.0, 0,
-                             k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j, nrhs, k.H, hcol, hrhs, nullptr, nullptr,
-                             nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0, 0, d->st);
-        else
-          launch_arnoldi_cluster(c, k.V, (long long)nrhs * L.nc, k.w, k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j,
-                                 nrhs, k.H, hcol, hrhs, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
-                                 nullptr, nullptr, 0, 0, d->st);
-      }, 3);
-      if (t < best_a) { best_a = t; best_c = c; }
+      for (int nt : nts) {
+        const int ept = d->arnoldi_mode == 1 ? arnoldi_reg_ept(L.nc, c, nt) : 0;
+        if (d->arnoldi_mode != 1 && nt != nts[0]) continue;
+        const float t = time_it([&] {
+          if (ept > 0)
+            launch_arnoldi_reg(c, nt, k.V, (long long)nrhs * L.nc, k.w, nullptr, 64, nullptr, 0, 0.0, 0.0, 0,
+                               k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j, nrhs, k.H, hcol, hrhs, nullptr, nullptr,
+                               nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0, 0, d->st);
+          else
+            launch_arnoldi_cluster(c, k.V, (long long)nrhs * L.nc, k.w, k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc,
+                                   j, nrhs, k.H, hcol, hrhs, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
+                                   nullptr, nullptr, 0, 0, d->st);
+        }, 3);
+        if (t < best_a) { best_a = t; best_c = c; best_nt = nt; }
+      }
     }
     d->tune_csz = best_c;
+    d->tune_nt = best_nt;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1313,7 +1321,7 @@ fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out) {
     out->q = best_q;
     out->mt = best_mt;
     out->cluster = best_c;
-    out->reserved = 0;
+    out->threads = best_nt;
     out->precond_ms = best;
     out->arnoldi_ms = best_a < 1e29f ? best_a : 0.0;
   }
@@ -1342,6 +1350,21 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
       d->precond_kind = value;
       drop_graph(d);
       return FPG_OK;
+    case FPG_OPT_DST_ENGINE:
+      if (value < 0 || value > 2) return FPG_EINVAL;
+      for (auto* t : {&d->tC64, &d->tC32, &d->tA64, &d->tA32}) t->generic = value;
+      drop_graph(d);
+      return FPG_OK;
+    case FPG_OPT_ARNOLDI_CSZ:
+      if (value < 0 || value > 16) return FPG_EINVAL;
+      d->tune_csz = value;
+      drop_graph(d);
+      return FPG_OK;
+    case FPG_OPT_ARNOLDI_THREADS:
+      if (value != 0 && value != 256 && value != 512) return FPG_EINVAL;
+      d->tune_nt = value;
+      drop_graph(d);
+      return FPG_OK;
     default: return FPG_EINVAL;
   }
 }
@@ -1365,6 +1388,17 @@ fpg_status fpg_phase_stats(fpg_domain* d, int32_t phase, int64_t* launches, doub
   ev_collect(d);  // events of operator calls made since the last solve
   if (launches) *launches = d->phase_launches[phase];
   if (ms) *ms = d->phase_ms[phase];
+  return FPG_OK;
+}
+
+fpg_status fpg_fast_solve_path(fpg_domain* d, int32_t* path) {
+  if (!d || !path) return FPG_EINVAL;
+  if (d->precond_kind != 0) {
+    *path = 4;
+    return FPG_OK;
+  }
+  const FastSolveTables& tb = d->prec == 64 ? d->tC64 : d->tC32;
+  *path = fast_solve_path(d->prec, tb, d->LC, d->desc.nrhs);
   return FPG_OK;
 }
 

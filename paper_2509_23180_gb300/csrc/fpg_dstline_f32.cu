@@ -1,0 +1,39 @@
+// Size-specialised line DST kernels, FP32 compute (FP64 input, FP32 or FP64 output).
+#include "fpg_dstline_impl.cuh"
+
+namespace fpg {
+
+bool dst_lines_supported_f32(int p) { return p == 65 || p == 257 || p == 513 || p == 1025; }
+
+cudaError_t dst_lines_fwd_f32(int p, const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl, float* scratch,
+                              int nblk, const int* active, int nper_active, int vec, cudaStream_t st) {
+  switch (p) {
+    case 65: return dl::fwd_one<float, 65>(in, ib, L, pl, scratch, nblk, active, nper_active, vec, st);
+    case 257: return dl::fwd_one<float, 257>(in, ib, L, pl, scratch, nblk, active, nper_active, vec, st);
+    case 513: return dl::fwd_one<float, 513>(in, ib, L, pl, scratch, nblk, active, nper_active, vec, st);
+    case 1025: return dl::fwd_one<float, 1025>(in, ib, L, pl, scratch, nblk, active, nper_active, vec, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+template <typename To>
+static cudaError_t inv_f32(int p, const float* scratch, To* out, BatchDesc ob, LineLayout L, const DstPlan& pl,
+                           int nblk, const int* active, int nper_active, int vec, cudaStream_t st) {
+  switch (p) {
+    case 65: return dl::inv_one<float, To, 65>(scratch, out, ob, L, pl, nblk, active, nper_active, vec, st);
+    case 257: return dl::inv_one<float, To, 257>(scratch, out, ob, L, pl, nblk, active, nper_active, vec, st);
+    case 513: return dl::inv_one<float, To, 513>(scratch, out, ob, L, pl, nblk, active, nper_active, vec, st);
+    case 1025: return dl::inv_one<float, To, 1025>(scratch, out, ob, L, pl, nblk, active, nper_active, vec, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+cudaError_t dst_lines_inv_f32(int p, const float* scratch, void* out, int out_prec, BatchDesc ob, LineLayout L,
+                              const DstPlan& pl, int nblk, const int* active, int nper_active, int vec,
+                              cudaStream_t st) {
+  if (out_prec == 64)
+    return inv_f32<double>(p, scratch, (double*)out, ob, L, pl, nblk, active, nper_active, vec, st);
+  return inv_f32<float>(p, scratch, (float*)out, ob, L, pl, nblk, active, nper_active, vec, st);
+}
+
+}  // namespace fpg

@@ -1,0 +1,45 @@
+// Size-specialised line DST kernels, FP64 compute.
+#include "fpg_dstline_impl.cuh"
+
+namespace fpg {
+
+bool dst_lines_supported_f64(int p) { return p == 65 || p == 257 || p == 513; }
+
+// The specialised kernels run one thread per sub-DFT, (lines / 2) * max(A, B)
+// threads per pass.  FP64 needs enough of them to keep the FP64 pipe busy (10
+// blocks of 256^2 give ~4 warps per SM, where the generic engine's four radix-4
+// passes are faster); below that the generic engine is used.
+bool dst_lines_profitable_f64(int p, int nblk, int ns) {
+  int ab = 0;
+  switch (p) {
+    case 65: ab = dl::LineCfg<double, 65>::A; break;
+    case 257: ab = dl::LineCfg<double, 257>::A; break;
+    case 513: ab = dl::LineCfg<double, 513>::A; break;
+    default: return false;
+  }
+  return (long long)nblk * ((ns + 1) / 2) * ab >= 40000;
+}
+
+cudaError_t dst_lines_fwd_f64(int p, const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl,
+                              double* scratch, int nblk, const int* active, int nper_active, int vec,
+                              cudaStream_t st) {
+  switch (p) {
+    case 65: return dl::fwd_one<double, 65>(in, ib, L, pl, scratch, nblk, active, nper_active, vec, st);
+    case 257: return dl::fwd_one<double, 257>(in, ib, L, pl, scratch, nblk, active, nper_active, vec, st);
+    case 513: return dl::fwd_one<double, 513>(in, ib, L, pl, scratch, nblk, active, nper_active, vec, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+cudaError_t dst_lines_inv_f64(int p, const double* scratch, double* out, BatchDesc ob, LineLayout L,
+                              const DstPlan& pl, int nblk, const int* active, int nper_active, int vec,
+                              cudaStream_t st) {
+  switch (p) {
+    case 65: return dl::inv_one<double, double, 65>(scratch, out, ob, L, pl, nblk, active, nper_active, vec, st);
+    case 257: return dl::inv_one<double, double, 257>(scratch, out, ob, L, pl, nblk, active, nper_active, vec, st);
+    case 513: return dl::inv_one<double, double, 513>(scratch, out, ob, L, pl, nblk, active, nper_active, vec, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace fpg

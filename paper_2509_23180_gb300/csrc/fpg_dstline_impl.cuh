@@ -1,0 +1,391 @@
+// Kernels of the size-specialised line DST (forward: FP64 block -> spectral
+// scratch; inverse: spectral scratch -> block, scaled).  Included by one
+// translation unit per compute precision.
+#pragma once
+
+#include "fpg_dstline.cuh"
+#include "fpg_internal.cuh"
+
+namespace fpg {
+namespace dl {
+
+// Launch shape per (compute type, p): the DFT of length p (or p - 1 under
+// Rader) is A * B; Q line pairs per CTA; NT threads.
+template <typename T, int P>
+struct LineCfg;
+
+#define FPG_LINECFG(TY, PP, AA, BB, RD, QQ, NTT)   \
+  template <>                                      \
+  struct LineCfg<TY, PP> {                         \
+    static constexpr int A = AA, B = BB, Q = QQ;   \
+    static constexpr int NT = NTT;                 \
+    static constexpr bool rader = RD;              \
+  };
+FPG_LINECFG(float, 65, 13, 5, false, 16, 256)
+FPG_LINECFG(float, 257, 16, 16, true, 16, 256)
+FPG_LINECFG(float, 513, 27, 19, false, 8, 256)
+FPG_LINECFG(float, 1025, 25, 41, false, 4, 192)
+FPG_LINECFG(double, 65, 13, 5, false, 16, 256)
+FPG_LINECFG(double, 257, 16, 16, true, 8, 128)
+FPG_LINECFG(double, 513, 27, 19, false, 4, 128)
+#undef FPG_LINECFG
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
+
+template <typename T, int P>
+struct LineShape {
+  using C = LineCfg<T, P>;
+  static constexpr int n = P - 1;
+  static constexpr int A = C::A, B = C::B, Q = C::Q, NT = C::NT;
+  static constexpr bool rader = C::rader;
+  static constexpr int N = A * B;             // DFT length run by the two passes
+  static constexpr int YB = (B % 2 == 0) ? B + 1 : B;  // odd pitch: pass-2 reads hit distinct banks
+  static constexpr int K = (P + 1) / 2;       // unpack terms
+  static constexpr int CK = (K + 31) / 32;    // unpack terms per lane
+  static_assert(N == (rader ? P - 1 : P), "plan shape");
+  // shared memory, in bytes, 16-byte aligned pieces
+  static constexpr size_t o_sinp = 0;
+  static constexpr size_t o_tw = align16(o_sinp + sizeof(T) * P);
+  static constexpr size_t o_bhat = align16(o_tw + sizeof(C2<T>) * N);
+  static constexpr size_t o_pin = align16(o_bhat + (rader ? sizeof(C2<T>) * N : 0));
+  static constexpr size_t o_pout = align16(o_pin + (rader ? sizeof(int) * N : 0));
+  static constexpr size_t o_dc = align16(o_pout + (rader ? sizeof(int) * N : 0));
+  static constexpr size_t o_lines = align16(o_dc + sizeof(C2<T>) * Q);
+  static constexpr size_t o_y = align16(o_lines + sizeof(T) * 2 * Q * n);
+  static constexpr size_t o_x = align16(o_y + sizeof(C2<T>) * Q * A * YB);
+  static constexpr size_t bytes = align16(o_x + sizeof(C2<T>) * Q * P);
+};
+
+template <typename T, int P>
+struct LineSmem {
+  using S = LineShape<T, P>;
+  T* sinp;
+  C2<T>* tw;    // [ka][jb] = w_N^{ka jb}
+  C2<T>* bhat;  // Rader kernel spectrum
+  int* pin;
+  int* pout;
+  C2<T>* dc;
+  T* lines;  // [2Q][n] real lines (input, then output)
+  C2<T>* y;  // [Q][A][YB]
+  C2<T>* x;  // [Q][P]
+  __device__ __forceinline__ explicit LineSmem(unsigned char* base) {
+    sinp = reinterpret_cast<T*>(base + S::o_sinp);
+    tw = reinterpret_cast<C2<T>*>(base + S::o_tw);
+    bhat = reinterpret_cast<C2<T>*>(base + S::o_bhat);
+    pin = reinterpret_cast<int*>(base + S::o_pin);
+    pout = reinterpret_cast<int*>(base + S::o_pout);
+    dc = reinterpret_cast<C2<T>*>(base + S::o_dc);
+    lines = reinterpret_cast<T*>(base + S::o_lines);
+    y = reinterpret_cast<C2<T>*>(base + S::o_y);
+    x = reinterpret_cast<C2<T>*>(base + S::o_x);
+  }
+};
+
+template <typename T, int P>
+__device__ __forceinline__ void load_tables(DstPlan pl, LineSmem<T, P>& s) {
+  using S = LineShape<T, P>;
+  const C2<T>* W = reinterpret_cast<const C2<T>*>(pl.W);  // w_N^m, m < N
+  const T* sp = reinterpret_cast<const T*>(pl.sinp);
+  for (int i = threadIdx.x; i < P; i += S::NT) s.sinp[i] = sp[i];
+  for (int i = threadIdx.x; i < S::N; i += S::NT) {
+    const int ka = i / S::B, jb = i - ka * S::B;
+    s.tw[i] = W[ka * jb];  // ka * jb < N
+  }
+  if constexpr (S::rader) {
+    const C2<T>* Bh = reinterpret_cast<const C2<T>*>(pl.Bhat);
+    for (int i = threadIdx.x; i < S::N; i += S::NT) {
+      s.bhat[i] = Bh[i];
+      s.pin[i] = pl.pin[i];
+      s.pout[i] = pl.pout[i];
+    }
+  }
+}
+
+// z_j of line pair q (j in 1..p-1): u_j = sin(pi j/p)(x_j + x_{p-j}) + (x_j - x_{p-j})/2
+// for the two lines, packed as real and imaginary part.
+template <typename T, int P>
+__device__ __forceinline__ C2<T> pack(const LineSmem<T, P>& s, int q, int j) {
+  constexpr int n = P - 1;
+  const T* la = s.lines + (2 * q) * n;
+  const T* lb = la + n;
+  const T a1 = la[j - 1], a2 = la[P - j - 1], b1 = lb[j - 1], b2 = lb[P - j - 1];
+  const T sj = s.sinp[j];
+  return C2<T>{fma(sj, a1 + a2, T(0.5) * (a1 - a2)), fma(sj, b1 + b2, T(0.5) * (b1 - b2))};
+}
+
+// Pass 1 of the two-pass DFT: per (pair q, jb) a DFT of length A over ja of
+// in(q, B ja + jb), times w_N^{jb ka}, into y[q][ka][jb].
+template <typename T, int P, typename In>
+__device__ __forceinline__ void pass1(LineSmem<T, P>& s, In in) {
+  using S = LineShape<T, P>;
+  constexpr int A = S::A, B = S::B;
+  for (int t = threadIdx.x; t < S::Q * B; t += S::NT) {
+    const int q = t / B, jb = t - q * B;
+    C2<T> v[A];
+    static_for<A>([&](auto ja) { v[decltype(ja)::value] = in(q, B * decltype(ja)::value + jb); });
+    dft<A, T>(v);
+    C2<T>* yq = s.y + q * (A * S::YB) + jb;
+    const C2<T>* tw = s.tw + jb;
+    yq[0] = v[0];
+    static_for<A - 1>([&](auto kai) {
+      constexpr int ka = decltype(kai)::value + 1;
+      yq[ka * S::YB] = c_mul(v[ka], tw[ka * B]);
+    });
+  }
+}
+
+// Pass 2: per (pair q, ka) a DFT of length B over jb of y[q][ka][jb]; output
+// k = ka + A kb handed to out(q, k, value).
+template <typename T, int P, typename Out>
+__device__ __forceinline__ void pass2(LineSmem<T, P>& s, Out out) {
+  using S = LineShape<T, P>;
+  constexpr int A = S::A, B = S::B;
+  for (int t = threadIdx.x; t < S::Q * A; t += S::NT) {
+    const int q = t / A, ka = t - q * A;
+    C2<T> v[B];
+    const C2<T>* yq = s.y + q * (A * S::YB) + ka * S::YB;
+    static_for<B>([&](auto jb) { v[decltype(jb)::value] = yq[decltype(jb)::value]; });
+    dft<B, T>(v);
+    static_for<B>([&](auto kb) { out(q, ka + A * decltype(kb)::value, v[decltype(kb)::value]); });
+  }
+}
+
+// DFT of length p of every packed line pair; result in s.x[q][k].
+template <typename T, int P>
+__device__ __forceinline__ void dft_p(LineSmem<T, P>& s) {
+  using S = LineShape<T, P>;
+  if constexpr (!S::rader) {
+    pass1<T, P>(s, [&](int q, int j) { return j == 0 ? C2<T>{T(0), T(0)} : pack<T, P>(s, q, j); });
+    __syncthreads();
+    pass2<T, P>(s, [&](int q, int k, C2<T> v) { s.x[q * P + k] = v; });
+    __syncthreads();
+  } else {
+    // Rader: with g a generator mod p, A_b = z_{g^b}; X_{g^{-a}} = (A (*) w)[a],
+    // w_c = w_p^{g^{-c}}, a cyclic convolution of length N = p - 1; X_0 = sum_b A_b
+    // (z_0 = 0 because x_0 = x_p = 0).
+    constexpr int N = S::N;
+    pass1<T, P>(s, [&](int q, int b) { return pack<T, P>(s, q, s.pin[b]); });
+    __syncthreads();
+    pass2<T, P>(s, [&](int q, int k, C2<T> v) {
+      if (k == 0) s.dc[q] = v;
+      const C2<T> m = c_mul(v, s.bhat[k]);  // bhat carries the 1/N of the inverse DFT
+      s.x[q * P + k] = C2<T>{m.x, -m.y};    // conj: the inverse DFT as a forward one
+    });
+    __syncthreads();
+    pass1<T, P>(s, [&](int q, int j) { return s.x[q * P + j]; });
+    __syncthreads();
+    pass2<T, P>(s, [&](int q, int a, C2<T> v) { s.x[q * P + s.pout[a]] = C2<T>{v.x, -v.y}; });
+    for (int q = threadIdx.x; q < S::Q; q += S::NT) s.x[q * P] = s.dc[q];
+    static_assert(N == P - 1, "Rader length");
+    __syncthreads();
+  }
+}
+
+// Unpack the spectra of s.x into the 2Q real output lines (in s.lines), scaled
+// by 2 (the 1/2 factors are left out): for each pair, with U = (Z_k + conj Z_{p-k})/2
+// (line a) and (Z_k - conj Z_{p-k})/(2i) (line b),
+//   y_{2k} = -Im U_k,  y_1 = Re U_0 / 2,  y_{2k+1} = y_{2k-1} + Re U_k,
+// one warp per pair, each lane a contiguous run of CK terms, a warp scan for
+// the prefix sum.
+template <typename T, int P>
+__device__ __forceinline__ void unpack(LineSmem<T, P>& s) {
+  using S = LineShape<T, P>;
+  constexpr int n = S::n, K = S::K, CK = S::CK;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int NW = S::NT / 32;
+  for (int q = wid; q < S::Q; q += NW) {
+    const C2<T>* Z = s.x + q * P;
+    T* ya = s.lines + (2 * q) * n;
+    T* yb = ya + n;
+    const int k0 = lane * CK;
+    T ra[CK], rb[CK], oa[CK], ob[CK];
+    T sa = T(0), sb = T(0);
+    static_for<CK>([&](auto ii) {
+      constexpr int i = decltype(ii)::value;
+      const int k = k0 + i;
+      ra[i] = rb[i] = oa[i] = ob[i] = T(0);
+      if (k < K) {
+        const C2<T> zk = Z[k];
+        if (k == 0) {
+          ra[i] = zk.x;
+          rb[i] = zk.y;
+        } else {
+          const C2<T> zr = Z[P - k];
+          ra[i] = zk.x + zr.x;
+          rb[i] = zk.y + zr.y;
+          oa[i] = -(zk.y - zr.y);
+          ob[i] = zk.x - zr.x;
+        }
+        sa += ra[i];
+        sb += rb[i];
+      }
+    });
+    T ia = sa, ib = sb;  // inclusive scan of the lane totals
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T ta = __shfl_up_sync(0xffffffffu, ia, o), tb = __shfl_up_sync(0xffffffffu, ib, o);
+      if (lane >= o) {
+        ia += ta;
+        ib += tb;
+      }
+    }
+    T acca = __shfl_up_sync(0xffffffffu, ia, 1), accb = __shfl_up_sync(0xffffffffu, ib, 1);
+    if (lane == 0) acca = accb = T(0);
+    static_for<CK>([&](auto ii) {
+      constexpr int i = decltype(ii)::value;
+      const int k = k0 + i;
+      if (k < K) {
+        acca += ra[i];
+        accb += rb[i];
+        if (2 * k + 1 <= n) {
+          ya[2 * k] = acca;
+          yb[2 * k] = accb;
+        }
+        if (k >= 1 && 2 * k <= n) {
+          ya[2 * k - 1] = oa[i];
+          yb[2 * k - 1] = ob[i];
+        }
+      }
+    });
+  }
+}
+
+// Offset of block b of a batch (selects among the four offsets without
+// indexing the parameter array, which would place it in local memory).
+__device__ __forceinline__ long long boff(const BatchDesc& d, int b) {
+  const int i = b % d.nper;
+  const long long o = i == 0 ? d.off[0] : (i == 1 ? d.off[1] : (i == 2 ? d.off[2] : d.off[3]));
+  return (long long)(b / d.nper) * d.rhs_stride + o;
+}
+
+// Forward: 2Q lines (t along the line) of block b -> DST -> scratch[b][s][k]
+// (k fastest), in the compute precision, scaled by 2.
+template <typename T, int P>
+__global__ void __launch_bounds__(LineShape<T, P>::NT)
+k_dst_lines_fwd(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPlan pl, T* __restrict__ scratch,
+                const int* __restrict__ active, int nper_active, int vec) {
+  using S = LineShape<T, P>;
+  constexpr int n = S::n, Q = S::Q, NT = S::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.y;
+  if (active != nullptr && !active[b / nper_active]) return;
+  LineSmem<T, P> s(smem_raw);
+  const int s0 = blockIdx.x * 2 * Q;
+  const int nl = min(2 * Q, L.ns - s0);
+  load_tables<T, P>(pl, s);
+  const double* src = in + boff(ib, b);
+  if (vec) {  // rows contiguous (st == 1) and 16-byte aligned: two values per load
+    for (int i = threadIdx.x; i < Q * n; i += NT) {
+      const int l = i / (n / 2), t2 = i - l * (n / 2);
+      double2 v = make_double2(0.0, 0.0);
+      if (l < nl) v = *reinterpret_cast<const double2*>(src + (long long)(s0 + l) * L.ss + 2 * t2);
+      s.lines[l * n + 2 * t2] = convert<T>(v.x);
+      s.lines[l * n + 2 * t2 + 1] = convert<T>(v.y);
+    }
+  } else {
+    for (int i = threadIdx.x; i < 2 * Q * n; i += NT) {
+      const int l = i / n, t = i - l * n;
+      const double v = l < nl ? src[(long long)t * L.st + (long long)(s0 + l) * L.ss] : 0.0;
+      s.lines[i] = convert<T>(v);
+    }
+  }
+  __syncthreads();
+  dft_p<T, P>(s);
+  unpack<T, P>(s);
+  __syncthreads();
+  T* dst = scratch + ((long long)b * L.ns + s0) * n;
+  if constexpr (sizeof(T) == 4) {
+    const float4* y4 = reinterpret_cast<const float4*>(s.lines);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (int i = threadIdx.x; i < nl * n / 4; i += NT) d4[i] = y4[i];
+  } else {
+    const double2* y2 = reinterpret_cast<const double2*>(s.lines);
+    double2* d2 = reinterpret_cast<double2*>(dst);
+    for (int i = threadIdx.x; i < nl * n / 2; i += NT) d2[i] = y2[i];
+  }
+}
+
+// Inverse: scratch[b][s][k] -> DST -> out block (To), times `scale`.
+template <typename T, typename To, int P>
+__global__ void __launch_bounds__(LineShape<T, P>::NT)
+k_dst_lines_inv(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc ob, LineLayout L, DstPlan pl, T scale,
+                const int* __restrict__ active, int nper_active, int vec) {
+  using S = LineShape<T, P>;
+  constexpr int n = S::n, Q = S::Q, NT = S::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.y;
+  if (active != nullptr && !active[b / nper_active]) return;
+  LineSmem<T, P> s(smem_raw);
+  const int s0 = blockIdx.x * 2 * Q;
+  const int nl = min(2 * Q, L.ns - s0);
+  load_tables<T, P>(pl, s);
+  const T* src = scratch + ((long long)b * L.ns + s0) * n;
+  if constexpr (sizeof(T) == 4) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* l4 = reinterpret_cast<float4*>(s.lines);
+    for (int i = threadIdx.x; i < 2 * Q * n / 4; i += NT)
+      l4[i] = i < nl * n / 4 ? s4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+    double2* l2 = reinterpret_cast<double2*>(s.lines);
+    for (int i = threadIdx.x; i < 2 * Q * n / 2; i += NT) l2[i] = i < nl * n / 2 ? s2[i] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  dft_p<T, P>(s);
+  unpack<T, P>(s);
+  __syncthreads();
+  To* dst = out + boff(ob, b);
+  if (vec) {  // rows contiguous and aligned for two-element stores
+    for (int i = threadIdx.x; i < nl * (n / 2); i += NT) {
+      const int l = i / (n / 2), t2 = i - l * (n / 2);
+      const To a = convert<To>(s.lines[l * n + 2 * t2] * scale);
+      const To c = convert<To>(s.lines[l * n + 2 * t2 + 1] * scale);
+      To* d = dst + (long long)(s0 + l) * L.ss + 2 * t2;
+      if constexpr (sizeof(To) == 8) {
+        *reinterpret_cast<double2*>(d) = make_double2(a, c);
+      } else {
+        *reinterpret_cast<float2*>(d) = make_float2(a, c);
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < nl * n; i += NT) {
+      const int l = i / n, k = i - l * n;
+      dst[(long long)k * L.st + (long long)(s0 + l) * L.ss] = convert<To>(s.lines[i] * scale);
+    }
+  }
+}
+
+// Host side --------------------------------------------------------------------
+
+template <typename T, int P>
+cudaError_t fwd_one(const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl, T* scratch, int nblk,
+                    const int* active, int nper_active, int vec, cudaStream_t st) {
+  using S = LineShape<T, P>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_dst_lines_fwd<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    attr = true;
+  }
+  dim3 grid((L.ns + 2 * S::Q - 1) / (2 * S::Q), nblk);
+  k_dst_lines_fwd<T, P><<<grid, S::NT, S::bytes, st>>>(in, ib, L, pl, scratch, active, nper_active, vec);
+  return cudaGetLastError();
+}
+
+template <typename T, typename To, int P>
+cudaError_t inv_one(const T* scratch, To* out, BatchDesc ob, LineLayout L, const DstPlan& pl, int nblk,
+                    const int* active, int nper_active, int vec, cudaStream_t st) {
+  using S = LineShape<T, P>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_dst_lines_inv<T, To, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    attr = true;
+  }
+  // 2/p for the normalisation, 1/4 for the two left-out factors 1/2 (exact)
+  const T scale = (T(2) / T(P)) * T(0.25);
+  dim3 grid((L.ns + 2 * S::Q - 1) / (2 * S::Q), nblk);
+  k_dst_lines_inv<T, To, P><<<grid, S::NT, S::bytes, st>>>(scratch, out, ob, L, pl, scale, active, nper_active, vec);
+  return cudaGetLastError();
+}
+
+}  // namespace dl
+}  // namespace fpg

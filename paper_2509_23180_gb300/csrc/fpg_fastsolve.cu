@@ -13,7 +13,9 @@
 // back into the block layout.  Compute precision T is double or float; inputs
 // are always FP64, the output is written as To.
 #include <cuda_runtime.h>
+#include <stdint.h>
 
+#include "fpg_dstline.cuh"
 #include "fpg_internal.cuh"
 
 namespace fpg {
@@ -86,12 +88,12 @@ k_dense_forward(const double* __restrict__ in, BatchDesc ib, LineLayout L, int n
   if (L.st == 1) {
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
       const int l = idx / n, t = idx - l * n;
-      lines[l * pitch + t] = (T)src[t + (long long)(s0 + l) * L.ss];
+      lines[l * pitch + t] = dl::convert<T>(src[t + (long long)(s0 + l) * L.ss]);
     }
   } else {
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
       const int t = idx / nl, l = idx - t * nl;
-      lines[l * pitch + t] = (T)src[(long long)t * L.st + (long long)(s0 + l) * L.ss];
+      lines[l * pitch + t] = dl::convert<T>(src[(long long)t * L.st + (long long)(s0 + l) * L.ss]);
     }
   }
   __syncthreads();
@@ -289,73 +291,8 @@ k_dense_inverse(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc o
   const T scale = T(2) / T(n + 1);
   const bool kfast = (L.st == 1);
   dst_dense_lines<T>(lines, nl, n, pitch, sintab, kfast, [&](int l, int k, T v) {
-    dst[(long long)k * L.st + (long long)(s0 + l) * L.ss] = (To)(v * scale);
+    dst[(long long)k * L.st + (long long)(s0 + l) * L.ss] = dl::convert<To>(v * scale);
   });
-}
-
-// FFT engine versions: 2Q lines per CTA.
-template <typename T, int MAXR>
-__global__ void __launch_bounds__(kFsThreads)
-k_fft_forward(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPlan pl, T* __restrict__ scratch,
-              int Q, const int* __restrict__ active, int nper_active) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int b = blockIdx.y;
-  if (active != nullptr && !active[b / nper_active]) return;
-  const int n = pl.n;
-  const int lpb = 2 * Q;
-  const int s0 = blockIdx.x * lpb;
-  const int nl = min(lpb, L.ns - s0);
-  DstSmem<T> sm = dst_smem_carve<T>(smem_raw, pl, Q);
-  dst_load_tables<T>(pl, sm);
-  const double* src = batch_ptr(in, ib, b);
-  const int total = lpb * n;
-  if (L.st == 1) {
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int l = idx / n, t = idx - l * n;
-      sm.xin[idx] = l < nl ? (T)src[t + (long long)(s0 + l) * L.ss] : T(0);
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int t = idx / lpb, l = idx - t * lpb;
-      sm.xin[l * n + t] = l < nl ? (T)src[(long long)t * L.st + (long long)(s0 + l) * L.ss] : T(0);
-    }
-  }
-  __syncthreads();
-  const T* y = dst_lines<T, MAXR>(pl, sm, Q);
-  T* dst = scratch + ((long long)b * L.ns + s0) * n;
-  for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) dst[idx] = y[idx];
-}
-
-template <typename T, typename To, int MAXR>
-__global__ void __launch_bounds__(kFsThreads)
-k_fft_inverse(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc ob, LineLayout L, DstPlan pl, int Q,
-              const int* __restrict__ active, int nper_active) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int b = blockIdx.y;
-  if (active != nullptr && !active[b / nper_active]) return;
-  const int n = pl.n;
-  const int lpb = 2 * Q;
-  const int s0 = blockIdx.x * lpb;
-  const int nl = min(lpb, L.ns - s0);
-  DstSmem<T> sm = dst_smem_carve<T>(smem_raw, pl, Q);
-  dst_load_tables<T>(pl, sm);
-  const T* src = scratch + ((long long)b * L.ns + s0) * n;
-  for (int idx = threadIdx.x; idx < lpb * n; idx += blockDim.x) sm.xin[idx] = idx < nl * n ? src[idx] : T(0);
-  __syncthreads();
-  const T* y = dst_lines<T, MAXR>(pl, sm, Q);
-  To* dst = batch_ptr_out(out, ob, b);
-  const T scale = T(2) / T(n + 1);
-  if (L.st == 1) {
-    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-      const int l = idx / n, k = idx - l * n;
-      dst[k + (long long)(s0 + l) * L.ss] = (To)(y[idx] * scale);
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-      const int k = idx / nl, l = idx - k * nl;
-      dst[(long long)k * L.st + (long long)(s0 + l) * L.ss] = (To)(y[l * n + k] * scale);
-    }
-  }
 }
 
 template <typename T>
@@ -384,6 +321,80 @@ int pairs_per_block(const DstPlan& pl, int ns, int nblk) {
   return Q;
 }
 
+}  // namespace
+
+// Generic-engine DST kernels, one translation unit per radix family (fpg_fft_r*.cu).
+#define FPG_FFT_FAMILY_DECL(R)                                                                                    \
+  cudaError_t fft_family_fwd_##R(int prec, dim3 grid, size_t smem, cudaStream_t st, const double* in,            \
+                                 BatchDesc ib, LineLayout L, const DstPlan& pl, void* scratch, int Q,            \
+                                 const int* active, int nper_active);                                            \
+  cudaError_t fft_family_inv_##R(int prec, int out_prec, dim3 grid, size_t smem, cudaStream_t st,                \
+                                 const void* scratch, void* out, BatchDesc ob, LineLayout L, const DstPlan& pl,  \
+                                 int Q, const int* active, int nper_active);
+FPG_FFT_FAMILY_DECL(5)
+FPG_FFT_FAMILY_DECL(13)
+FPG_FFT_FAMILY_DECL(19)
+FPG_FFT_FAMILY_DECL(43)
+#undef FPG_FFT_FAMILY_DECL
+
+// Size-specialised line DST kernels (fpg_dstline_f32.cu / fpg_dstline_f64.cu).
+bool dst_lines_supported_f32(int p);
+bool dst_lines_supported_f64(int p);
+bool dst_lines_profitable_f64(int p, int nblk, int ns);
+cudaError_t dst_lines_fwd_f32(int p, const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl, float* scratch,
+                              int nblk, const int* active, int nper_active, int vec, cudaStream_t st);
+cudaError_t dst_lines_inv_f32(int p, const float* scratch, void* out, int out_prec, BatchDesc ob, LineLayout L,
+                              const DstPlan& pl, int nblk, const int* active, int nper_active, int vec,
+                              cudaStream_t st);
+cudaError_t dst_lines_fwd_f64(int p, const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl,
+                              double* scratch, int nblk, const int* active, int nper_active, int vec,
+                              cudaStream_t st);
+cudaError_t dst_lines_inv_f64(int p, const double* scratch, double* out, BatchDesc ob, LineLayout L,
+                              const DstPlan& pl, int nblk, const int* active, int nper_active, int vec,
+                              cudaStream_t st);
+
+namespace {
+
+// Two-element vector access is possible when lines are contiguous and every
+// block of the batch starts 16 bytes aligned (elements of 8 bytes) or 8 bytes
+// aligned (4 bytes).
+bool pairs_aligned(const void* base, size_t esize, const BatchDesc& d, const LineLayout& L) {
+  if (L.st != 1 || (L.ss & 1) || (L.nt & 1)) return false;
+  if ((reinterpret_cast<uintptr_t>(base) % (2 * esize)) != 0 || (d.rhs_stride & 1)) return false;
+  for (int i = 0; i < d.nper; ++i)
+    if (d.off[i] & 1) return false;
+  return true;
+}
+
+// engine: FastSolveTables::generic (0 auto, 1 generic, 2 specialised where compiled)
+template <typename T>
+bool lines_engine(int p, int nblk, int ns, int engine) {
+  if (engine == 1) return false;
+  if (sizeof(T) == 4) return dst_lines_supported_f32(p);
+  return engine == 2 ? dst_lines_supported_f64(p) : dst_lines_profitable_f64(p, nblk, ns);
+}
+
+template <typename T, typename To>
+cudaError_t lines_fwd(const DstPlan& pl, const double* in, BatchDesc ib, LineLayout L, T* scratch, int nblk,
+                      const int* active, int nper_active, cudaStream_t st) {
+  const int vec = pairs_aligned(in, 8, ib, L) ? 1 : 0;
+  if constexpr (sizeof(T) == 8)
+    return dst_lines_fwd_f64(pl.p, in, ib, L, pl, scratch, nblk, active, nper_active, vec, st);
+  else
+    return dst_lines_fwd_f32(pl.p, in, ib, L, pl, scratch, nblk, active, nper_active, vec, st);
+}
+
+template <typename T, typename To>
+cudaError_t lines_inv(const DstPlan& pl, const T* scratch, To* out, BatchDesc ob, LineLayout L, int nblk,
+                      const int* active, int nper_active, cudaStream_t st) {
+  const int vec = pairs_aligned(out, sizeof(To), ob, L) ? 1 : 0;
+  if constexpr (sizeof(T) == 8)
+    return dst_lines_inv_f64(pl.p, scratch, out, ob, L, pl, nblk, active, nper_active, vec, st);
+  else
+    return dst_lines_inv_f32(pl.p, scratch, out, sizeof(To) == 8 ? 64 : 32, ob, L, pl, nblk, active, nper_active,
+                             vec, st);
+}
+
 template <typename T, typename To>
 cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib,
                             To* out, BatchDesc ob, int nblk, T* scratch, const int* active,
@@ -393,14 +404,6 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
   if (!attr_set) {
     cudaFuncSetAttribute(k_dense_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dense_inverse<T, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_fft_forward<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_fft_forward<T, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_fft_forward<T, 19>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_fft_forward<T, 43>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_fft_inverse<T, To, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_fft_inverse<T, To, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_fft_inverse<T, To, 19>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_fft_inverse<T, To, 43>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   const DstPlan& pl = tb.plan;
@@ -416,6 +419,21 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
                                                           active, nper_active);
     return cudaGetLastError();
   }
+  if (tb.q == 0 && lines_engine<T>(pl.p, nblk, L.ns, tb.generic)) {
+    // size-specialised kernels: forward DST, Thomas, inverse DST
+    if (ev) record_event(ev[0], st);
+    cudaError_t e = lines_fwd<T, To>(pl, in, ib, L, scratch, nblk, active, nper_active, st);
+    if (e != cudaSuccess) return e;
+    if (ev) record_event(ev[1], st);
+    if (ev) record_event(ev[2], st);
+    launch_thomas_scan<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st,
+                          tb.mt);
+    if (ev) record_event(ev[3], st);
+    if (ev) record_event(ev[4], st);
+    e = lines_inv<T, To>(pl, scratch, out, ob, L, nblk, active, nper_active, st);
+    if (ev) record_event(ev[5], st);
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
   int Q = pairs_per_block<T>(pl, L.ns, nblk);
   if (tb.q > 0 && dst_smem_bytes<T>(pl.p, pl.N, tb.q, pl.mode) <= 200 * 1024) Q = tb.q;
   const size_t smem = dst_smem_bytes<T>(pl.p, pl.N, Q, pl.mode);
@@ -423,30 +441,30 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
   // ev (optional): start/end pairs around the three kernels
   const int maxr = plan_maxr(pl);
   if (ev) record_event(ev[0], st);
-  if (maxr == 5)
-    k_fft_forward<T, 5><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
-  else if (maxr == 13)
-    k_fft_forward<T, 13><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
-  else if (maxr == 19)
-    k_fft_forward<T, 19><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
-  else
-    k_fft_forward<T, 43><<<grid, kFsThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
+  const int prec = sizeof(T) == 8 ? 64 : 32;
+  cudaError_t e = cudaSuccess;
+  switch (maxr) {
+    case 5: e = fft_family_fwd_5(prec, grid, smem, st, in, ib, L, pl, scratch, Q, active, nper_active); break;
+    case 13: e = fft_family_fwd_13(prec, grid, smem, st, in, ib, L, pl, scratch, Q, active, nper_active); break;
+    case 19: e = fft_family_fwd_19(prec, grid, smem, st, in, ib, L, pl, scratch, Q, active, nper_active); break;
+    default: e = fft_family_fwd_43(prec, grid, smem, st, in, ib, L, pl, scratch, Q, active, nper_active); break;
+  }
+  if (e != cudaSuccess) return e;
   if (ev) record_event(ev[1], st);
   if (ev) record_event(ev[2], st);
   launch_thomas_scan<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st,
                           tb.mt);
   if (ev) record_event(ev[3], st);
   if (ev) record_event(ev[4], st);
-  if (maxr == 5)
-    k_fft_inverse<T, To, 5><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
-  else if (maxr == 13)
-    k_fft_inverse<T, To, 13><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
-  else if (maxr == 19)
-    k_fft_inverse<T, To, 19><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
-  else
-    k_fft_inverse<T, To, 43><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
+  const int oprec = sizeof(To) == 8 ? 64 : 32;
+  switch (maxr) {
+    case 5: e = fft_family_inv_5(prec, oprec, grid, smem, st, scratch, out, ob, L, pl, Q, active, nper_active); break;
+    case 13: e = fft_family_inv_13(prec, oprec, grid, smem, st, scratch, out, ob, L, pl, Q, active, nper_active); break;
+    case 19: e = fft_family_inv_19(prec, oprec, grid, smem, st, scratch, out, ob, L, pl, Q, active, nper_active); break;
+    default: e = fft_family_inv_43(prec, oprec, grid, smem, st, scratch, out, ob, L, pl, Q, active, nper_active); break;
+  }
   if (ev) record_event(ev[5], st);
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace
@@ -454,6 +472,19 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
 cudaError_t launch_fast_solve_fused(int prec, int out_prec, const FastSolveTables& tb, LineLayout L,
                                     const double* in, BatchDesc ib, void* out, BatchDesc ob, int nblk,
                                     const int* active, int nper_active, cudaStream_t st);
+
+// Which kernels the fast solve of this block kind runs: 0 generic FFT engine
+// (k_fft_forward / k_thomas_scan / k_fft_inverse), 1 size-specialised
+// (k_dst_lines_fwd / k_thomas_scan / k_dst_lines_inv), 2 dense DST, 3 the fused
+// one-pass cluster kernel.
+bool fast_solve_fused_fits(int prec, const FastSolveTables& tb, LineLayout L);
+int fast_solve_path(int prec, const FastSolveTables& tb, LineLayout L, int nblk) {
+  if (tb.fused && fast_solve_fused_fits(prec, tb, L)) return 3;
+  if (tb.plan.mode == DST_DENSE) return 2;
+  const bool special = prec == 64 ? lines_engine<double>(tb.plan.p, nblk, L.ns, tb.generic)
+                                  : lines_engine<float>(tb.plan.p, nblk, L.ns, tb.generic);
+  return (tb.q == 0 && special) ? 1 : 0;
+}
 
 // Public (library-internal) entry: precision 64 -> double everywhere; 32 ->
 // float compute, output type chosen by out_prec (64 or 32).  The fused

@@ -39,6 +39,7 @@ struct FastSolveTables {
   int q = 0;          // line pairs per CTA in the DST kernels (0: built-in choice)
   int mt = 0;         // modes per CTA in the Thomas kernel (0: built-in choice)
   int fused = 0;      // 1: one-pass cluster kernel when the block fits
+  int generic = 0;    // DST engine: 0 auto, 1 generic FFT engine, 2 size-specialised where compiled
 };
 
 // Offsets of the arm blocks W, E, S, N inside one full vector (-1 = absent).

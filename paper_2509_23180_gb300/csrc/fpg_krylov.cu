@@ -8,6 +8,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include "fpg_dstline.cuh"
 #include "fpg_internal.cuh"
 
 namespace fpg {
@@ -20,7 +21,7 @@ constexpr int kThreads = 256;
 
 template <typename Tz>
 __device__ __forceinline__ double ld(const Tz* p, long long i) {
-  return (double)p[i];
+  return dl::convert<double>(p[i]);  // integer-pipe widening for FP32 z
 }
 
 // Value of C's line that faces arm `a`, position q (0..n-1).
@@ -299,16 +300,55 @@ k_arnoldi_cluster(const double* __restrict__ V, long long vstride, double* __res
 }
 
 // ---------------------------------------------------------------------------
-// Register-resident form of the fused Arnoldi step, for centre vectors of up
-// to 16 * kThreads elements per CTA.  Each thread keeps its EPT elements of w in
-// registers for the whole MGS chain and carries v_k over to the next step's
-// axpy, so every basis vector is read once and w is never written back.  With
-// z != nullptr the kernel first forms w = A_c z - sum_a corr_a (the Schur
-// matvec's stencil, a2) straight into those registers.  Partials of each MGS
-// step are gathered from the cluster's CTAs by one warp, one remote load per
-// lane, and summed in a fixed lane order.
+// Register-resident form of the fused Arnoldi step, for slices of up to
+// 16 * 512 elements per CTA (blockDim.x <= kRegMaxThreads, chosen by the host).
+// Each thread keeps its EPT elements of w in registers for the whole MGS chain;
+// basis vector v_{k+1} is loaded while step k's reduction is in flight, so every
+// basis vector is read once, its load latency is hidden, and w is never written
+// back.  With z != nullptr the kernel first forms w = A_c z - sum_a corr_a (the
+// Schur matvec's stencil, a2) straight into those registers.
+//
+// Reduction of one MGS step (fixed order, identical in every CTA): the thread
+// partials go to shared memory, warp 0 sums them lane-strided and across lanes,
+// pushes the CTA partial into slot [rank] of every CTA of the cluster, and after
+// one cluster barrier each CTA sums the csz slots in lane order.  That costs one
+// block barrier, one cluster barrier and ~17 FP64 warp instructions per CTA
+// (a butterfly in every warp would cost 5 per warp).
+constexpr int kRegMaxThreads = 512;
+
+struct ClusterReduce {
+  double* red;         // [blockDim.x]
+  double (*slots)[16]; // [2][16]
+  double* hval;
+};
+
+__device__ __forceinline__ double cluster_reduce(double acc, int k, const ClusterReduce& R, int csz, int rank) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  R.red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) s += R.red[i];
+    s = warp_sum(s);
+    if ((int)threadIdx.x < csz) *cl.map_shared_rank(&R.slots[k & 1][rank], threadIdx.x) = s;
+  }
+  cl.sync();
+  if (threadIdx.x < 32) {
+    const double q = (int)threadIdx.x < csz ? R.slots[k & 1][threadIdx.x] : 0.0;
+    const double sum = warp_sum(q);
+    if (threadIdx.x == 0) *R.hval = sum;
+  }
+  __syncthreads();
+  return *R.hval;
+}
+
+// Largest CTA of the register kernel at EPT elements per thread (keeps w, v_k
+// and the prefetched v_{k+1} in registers without spilling).
+__host__ __device__ constexpr int reg_max_threads(int ept) { return ept >= 16 ? 256 : kRegMaxThreads; }
+
 template <typename Tz, int EPT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(reg_max_threads(EPT))
 k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const double* __restrict__ w,
                       const Tz* __restrict__ z, const double* __restrict__ corr, int n, double delta, double kappa,
                       int armmask, double* __restrict__ vout, long long len, int j, double* __restrict__ H,
@@ -321,28 +361,38 @@ k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const dou
   const int csz = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int r = blockIdx.x / csz;
-  __shared__ double red[32];
-  __shared__ double part[2];
+  __shared__ double red[kRegMaxThreads];
+  __shared__ double slots[2][16];
   __shared__ double hval;
+  const ClusterReduce R{red, slots, &hval};
   if (active != nullptr && !active[r]) return;  // uniform over the cluster
   const long long chunk = (len + csz - 1) / csz;
   const long long lo = (long long)rank * chunk;
   const long long hi = lo + chunk < len ? lo + chunk : len;
-  double wv[EPT], vp[EPT];
+  const long long base = (long long)r * len;
+  double wv[EPT], vc[EPT], vn[EPT];
+  {
+    const double* v0 = V + base;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const long long idx = lo + threadIdx.x + (long long)e * blockDim.x;
+      vc[e] = idx < hi ? v0[idx] : 0.0;
+    }
+  }
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
     const long long idx = lo + threadIdx.x + (long long)e * blockDim.x;
     double x = 0.0;
     if (idx < hi) {
       if (z == nullptr) {
-        x = w[(long long)r * len + idx];
+        x = w[base + idx];
       } else {
-        const Tz* zr = z + (long long)r * len;
+        const Tz* zr = z + base;
         const double* cr = corr + (long long)r * 4 * n;
         const int jj = (int)(idx / n), ii = (int)(idx - (long long)jj * n);
-        const double zc = (double)zr[idx];
-        const double sacc = stencil_sum(zc, ii > 0 ? (double)zr[idx - 1] : 0.0, ii < n - 1 ? (double)zr[idx + 1] : 0.0,
-                                        jj > 0 ? (double)zr[idx - n] : 0.0, jj < n - 1 ? (double)zr[idx + n] : 0.0);
+        const double zc = ld(zr, idx);
+        const double sacc = stencil_sum(zc, ii > 0 ? ld(zr, idx - 1) : 0.0, ii < n - 1 ? ld(zr, idx + 1) : 0.0,
+                                        jj > 0 ? ld(zr, idx - n) : 0.0, jj < n - 1 ? ld(zr, idx + n) : 0.0);
         x = fma(delta, sacc, kappa * zc);
         if (ii == 0 && (armmask & 1)) x -= cr[0 * n + jj];
         if (ii == n - 1 && (armmask & 2)) x -= cr[1 * n + jj];
@@ -351,46 +401,41 @@ k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const dou
       }
     }
     wv[e] = x;
-    vp[e] = 0.0;
   }
-  double hprev = 0.0;
-  for (int k = 0; k <= j + 1; ++k) {
-    const double* vk = (k <= j) ? V + (long long)k * vstride + (long long)r * len : nullptr;
-    double acc = 0.0;
+  double* hcol = H + (long long)r * hrhs_stride + (long long)j * hcol_stride;
+  for (int k = 0; k <= j; ++k) {
+    if (k < j) {  // prefetch v_{k+1}; consumed after this step's reduction
+      const double* vk1 = V + (long long)(k + 1) * vstride + base;
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      const long long idx = lo + threadIdx.x + (long long)e * blockDim.x;
-      if (k >= 1) wv[e] = fma(-hprev, vp[e], wv[e]);
-      if (vk) {
-        const double v = idx < hi ? vk[idx] : 0.0;
-        acc = fma(wv[e], v, acc);
-        vp[e] = v;
-      } else {
-        acc = fma(wv[e], wv[e], acc);
+      for (int e = 0; e < EPT; ++e) {
+        const long long idx = lo + threadIdx.x + (long long)e * blockDim.x;
+        vn[e] = idx < hi ? vk1[idx] : 0.0;
       }
     }
-    acc = block_sum(acc, red);
-    if (threadIdx.x == 0) part[k & 1] = acc;
-    cl.sync();
-    if (threadIdx.x < 32) {
-      const double q = threadIdx.x < csz ? *cl.map_shared_rank(&part[k & 1], (unsigned)threadIdx.x) : 0.0;
-      const double sum = warp_sum(q);
-      if (threadIdx.x == 0) hval = sum;
+    double acc = 0.0;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) acc = fma(wv[e], vc[e], acc);
+    const double h = cluster_reduce(acc, k, R, csz, rank);
+    if (rank == 0 && threadIdx.x == 0) hcol[k] = h;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      wv[e] = fma(-h, vc[e], wv[e]);
+      vc[e] = vn[e];
     }
-    __syncthreads();
-    hprev = hval;
-    if (rank == 0 && threadIdx.x == 0 && k <= j) H[(long long)r * hrhs_stride + (long long)j * hcol_stride + k] = hprev;
   }
-  const double hn = sqrt(hprev);
+  double acc = 0.0;
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) acc = fma(wv[e], wv[e], acc);
+  const double hn = sqrt(cluster_reduce(acc, j + 1, R, csz, rank));
   const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
-  double* vr = vout + (long long)r * len;
+  double* vr = vout + base;
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
     const long long idx = lo + threadIdx.x + (long long)e * blockDim.x;
     if (idx < hi) vr[idx] = wv[e] * inv;
   }
   if (rank == 0 && threadIdx.x == 0) {
-    double* h = H + (long long)r * hrhs_stride + (long long)j * hcol_stride;
+    double* h = hcol;
     h[j + 1] = hn;
     if (do_givens) {
       double* c = cs + (long long)r * m;
@@ -421,7 +466,8 @@ k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const dou
       if (rj <= tolabs[r] || b == 0.0 || iters[r] >= max_iters) active[r] = 0;
     }
   }
-  cl.sync();  // no CTA leaves while another may still read its shared memory
+  // Every remote store into a CTA's slots precedes a cluster barrier that CTA
+  // also waits on, so no CTA's shared memory is touched after it exits.
 }
 
 // ---------------------------------------------------------------------------
@@ -495,7 +541,7 @@ k_update_u(double* __restrict__ u, const Tz* __restrict__ Z, long long zvstride,
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < len;
        idx += (long long)gridDim.x * blockDim.x) {
     double s = ur[idx];
-    for (int i = 0; i < k; ++i) s = fma(yr[i], (double)Zr[(long long)i * zvstride + idx], s);
+    for (int i = 0; i < k; ++i) s = fma(yr[i], ld(Zr, (long long)i * zvstride + idx), s);
     ur[idx] = s;
   }
 }
@@ -940,15 +986,30 @@ cudaError_t launch_arnoldi_cluster(int csz, const double* V, long long vstride, 
 
 // Register-resident fused Arnoldi: returns cudaErrorInvalidValue when the
 // slice per CTA is too long for it (the caller then uses k_arnoldi_cluster).
-int arnoldi_reg_ept(long long len, int csz) {
+// Elements per thread of the register Arnoldi kernel for a slice of
+// ceil(len/csz) elements under a cap of ntcap threads per CTA (0: 256 when the
+// slice fits, else 512 -- narrow CTAs with 16 elements each let two domains'
+// kernels share an SM); 0 when the slice is too long.
+int arnoldi_reg_ept(long long len, int csz, int ntcap) {
+  if (ntcap <= 0) {
+    const int e = arnoldi_reg_ept(len, csz, 256);
+    return e > 0 ? e : arnoldi_reg_ept(len, csz, kRegMaxThreads);
+  }
+  if (ntcap > kRegMaxThreads) ntcap = kRegMaxThreads;
   const long long chunk = (len + csz - 1) / csz;
-  const long long ept = (chunk + kThreads - 1) / kThreads;
-  if (ept <= 1) return 1;
-  if (ept <= 2) return 2;
-  if (ept <= 4) return 4;
-  if (ept <= 8) return 8;
-  if (ept <= 16) return 16;
+  static const int epts[] = {2, 4, 8, 12, 16};
+  for (int e : epts) {
+    const long long nt = ((chunk + e - 1) / e + 31) / 32 * 32;
+    if (nt <= ntcap && nt <= reg_max_threads(e)) return e;
+  }
   return 0;
+}
+
+// Threads per CTA for a slice of ceil(len/csz) elements at EPT per thread.
+int arnoldi_reg_threads(long long len, int csz, int ept) {
+  const long long chunk = (len + csz - 1) / csz;
+  const long long t = (chunk + ept - 1) / ept;
+  return (int)((t + 31) / 32 * 32);
 }
 
 template <typename Tz, int EPT>
@@ -964,7 +1025,7 @@ cudaError_t launch_reg_impl(int csz, const double* V, long long vstride, const d
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(csz * nrhs, 1, 1);
-  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.blockDim = dim3(arnoldi_reg_threads(len, csz, EPT), 1, 1);
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -979,13 +1040,13 @@ cudaError_t launch_reg_impl(int csz, const double* V, long long vstride, const d
 }
 
 // z == nullptr: w is read from `w`; otherwise w = A_c z - corr is formed in the kernel (zprec 64 or 32).
-cudaError_t launch_arnoldi_reg(int csz, const double* V, long long vstride, const double* w, const void* z,
-                               int zprec, const double* corr, int n, double delta, double kappa, int armmask,
+cudaError_t launch_arnoldi_reg(int csz, int ntcap, const double* V, long long vstride, const double* w,
+                               const void* z, int zprec, const double* corr, int n, double delta, double kappa, int armmask,
                                double* vout, long long len, int j, int nrhs, double* H, int hcol_stride,
                                int hrhs_stride, double* cs, double* sn, double* g, double* res, int m,
                                const double* tolabs, int* active, int* kcyc, int* iters, int max_iters, int do_givens,
                                cudaStream_t st) {
-  const int ept = arnoldi_reg_ept(len, csz);
+  const int ept = arnoldi_reg_ept(len, csz, ntcap);
 #define FPG_REG_CASE(E)                                                                                            \
   if (ept == E) {                                                                                                  \
     if (z != nullptr && zprec == 32)                                                                               \
@@ -996,10 +1057,10 @@ cudaError_t launch_arnoldi_reg(int csz, const double* V, long long vstride, cons
                                       len, j, nrhs, H, hcol_stride, hrhs_stride, cs, sn, g, res, m, tolabs, active, \
                                       kcyc, iters, max_iters, do_givens, st);                                      \
   }
-  FPG_REG_CASE(1)
   FPG_REG_CASE(2)
   FPG_REG_CASE(4)
   FPG_REG_CASE(8)
+  FPG_REG_CASE(12)
   FPG_REG_CASE(16)
 #undef FPG_REG_CASE
   return cudaErrorInvalidValue;

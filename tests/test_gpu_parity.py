@@ -463,7 +463,7 @@ def test_graphs_profiling_and_direct_launches_agree(lib):
         outs.append(host(p))
         if prof:
             ph = d.phase_stats()
-            fs = "k_fast_solve_fused" if ph["k_fast_solve_fused"]["launches"] > 0 else "k_fft_forward"
+            fs = "fast_solve_fused" if ph["fast_solve_fused"]["launches"] > 0 else "dst_forward"
             assert ph[fs]["launches"] > 0 and ph[fs]["ms"] > 0
             assert ph["arnoldi"]["launches"] > 0 and ph["arnoldi"]["ms"] > 0
         d.close()
