@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--schedule", default="concurrent", choices=["sequential", "concurrent"],
                     help="solve the two kappa domains one after the other, or concurrently on two streams")
     ap.add_argument("--config", default="default",
-                    choices=["default", "small", "precision", "batching", "serving", "fastsolve"],
+                    choices=["default", "small", "precision", "batching", "serving", "fastsolve", "study"],
                     help="default: the 256^2 cross workload; the others run the other workloads as extra lines")
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
@@ -567,6 +567,43 @@ def run_extra(args):
                 lines[-1]["vs_plain_fp64"] = lines[-1]["value"] / line["value"]
             lines.append(line)
             d.close()
+    elif args.config == "study":
+        # Sec. 3.2-3.3 on the GPU: (i) GMRES iterations with P = A_c^{-1} (the fast
+        # solve), Jacobi and none, over n; (ii) iterations and solve time of the
+        # FFT-preconditioned solve against the Krylov dimension m (the paper finds
+        # an optimum near m = 80).  Cross, kappa 0, random Fourier RHS seed 0.
+        def solve_once(n, m, precond, max_iters):
+            f = torch.as_tensor(W.rhs_batch("cross", n, [0], kind="fourier"), device="cuda")
+            d = B.Domain(B.make_desc("cross", n, 0.0, nrhs=1, restart=m, rtol=args.rtol, max_iters=max_iters))
+            d.set_option(B.OPT_PRECOND, B.PRECOND[precond])
+            p = torch.zeros_like(f)
+            res = []
+            for s in range(2):  # second solve timed (first pays the one-time setup)
+                d.set_rhs(f)
+                ms, _, (stt, info) = _timed(lambda: d.solve(p, check=False))
+                res.append((ms, stt, info[0]))
+            d.close()
+            ms, stt, info = res[-1]
+            return {"iterations": info["iterations"], "ms": ms, "converged": stt == B.FPG_OK,
+                    "residual": info["residual"]}
+        pre = {}
+        for n in (16, 32, 64, 128, 256):
+            pre[n] = {}
+            for pc in ("fft", "jacobi", "none"):
+                if pc != "fft" and n > 64:
+                    continue  # unpreconditioned GMRES needs thousands of iterations there
+                pre[n][pc] = solve_once(n, 30, pc, 20000)
+        msweep = {m: solve_once(256, m, "fft", 5000) for m in (10, 20, 30, 40, 60, 80, 120)}
+        best_m = min(msweep, key=lambda m: msweep[m]["ms"])
+        ratio = {n: {pc: v["iterations"] / max(1, pre[n]["fft"]["iterations"]) for pc, v in r.items() if pc != "fft"}
+                 for n, r in pre.items()}
+        lines.append({"metric": "GMRES iterations and solve time vs preconditioner and Krylov dimension",
+                      "value": msweep[best_m]["ms"], "unit": "ms", "n_gpus": 1, "higher_is_better": False,
+                      "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "cross, kappa 0, fourier RHS seed 0, rtol %g" % args.rtol,
+                                 "precond_study_m": 30, "m_sweep_n": 256},
+                      "precond_iterations": pre, "iterations_ratio_vs_fft": ratio,
+                      "m_sweep": msweep, "best_m": best_m})
     elif args.config == "batching":
         # (i) 64 RHS in one domain on the 512^2 cross, FP32 fast solve, FP64 FGMRES(40)
         n, m, nr = 512, 40, 64

@@ -261,7 +261,7 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value);
 
 typedef struct {
   int32_t q;         /* line pairs per CTA in the DST kernels of a1 */
-  int32_t mt;        /* modes per CTA in the Thomas kernel of a1 */
+  int32_t mt;        /* modes (one warp each) per CTA in the Thomas kernel of a1 */
   int32_t cluster;   /* CTAs per right-hand side in the fused Arnoldi step (0: not tuned) */
   int32_t threads;   /* thread cap per CTA of that step (256 or 512; 0: not tuned) */
   double precond_ms; /* time of one preconditioner application (all nrhs vectors) at the choice */
@@ -270,7 +270,7 @@ typedef struct {
 
 /* Time the launch shapes of the hot kernels on this domain's own buffers
  * (precision, n, nrhs as created) and keep the fastest: the line batch (q) and
- * mode tile (mt) of the fast solve, the cluster size and CTA width of the
+ * Thomas CTA width (mt) of the fast solve, the cluster size and CTA width of the
  * Arnoldi step.
  * Overwrites the domain's Krylov buffers (call it between solves).  The
  * choices stay with the domain; out (may be NULL) reports them. */
@@ -301,8 +301,8 @@ fpg_status fpg_launch_count(fpg_domain* d, int64_t* launches);
 fpg_status fpg_convert(const void* in, int32_t in_prec, void* out, int32_t out_prec, int64_t count, void* stream);
 
 /* Kernels the preconditioner of this domain runs for the centre block:
- * 0 = generic FFT engine (k_fft_forward, k_thomas_scan, k_fft_inverse),
- * 1 = size-specialised line DST (k_dst_lines_fwd, k_thomas_scan, k_dst_lines_inv;
+ * 0 = generic FFT engine (k_fft_forward, k_thomas_reg, k_fft_inverse),
+ * 1 = size-specialised line DST (k_dst_lines_fwd, k_thomas_reg, k_dst_lines_inv;
  *     n = 64, 256, 512 in FP64 -- when the batch of nrhs centre blocks is large
  *     enough to fill the GPU -- and also 1024 in FP32),
  * 2 = dense DST (lengths with no FFT plan), 3 = fused one-pass cluster kernel

@@ -31,9 +31,9 @@ PHASES = ("precond", "schur", "arnoldi", "givens", "cycle_end", "setup_finish", 
           "dst_forward", "thomas", "dst_inverse", "fast_solve_fused")
 # fpg_fast_solve_path -> kernel names of the a1 phases
 FAST_SOLVE_KERNELS = {
-    0: {"dst_forward": "k_fft_forward", "thomas": "k_thomas_scan", "dst_inverse": "k_fft_inverse"},
-    1: {"dst_forward": "k_dst_lines_fwd", "thomas": "k_thomas_scan", "dst_inverse": "k_dst_lines_inv"},
-    2: {"dst_forward": "k_dense_forward", "thomas": "k_thomas_scan", "dst_inverse": "k_dense_inverse"},
+    0: {"dst_forward": "k_fft_forward", "thomas": "k_thomas_reg", "dst_inverse": "k_fft_inverse"},
+    1: {"dst_forward": "k_dst_lines_fwd", "thomas": "k_thomas_reg", "dst_inverse": "k_dst_lines_inv"},
+    2: {"dst_forward": "k_dense_forward", "thomas": "k_thomas_reg", "dst_inverse": "k_dense_inverse"},
     3: {"fast_solve_fused": "k_fast_solve_fused"},
     4: {},
 }

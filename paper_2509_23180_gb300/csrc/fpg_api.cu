@@ -240,14 +240,15 @@ double cos_pi_frac(long long num, long long den) {
 // Reciprocal Thomas pivots for tridiag(delta, d_k, delta) of length ns, all modes:
 // r[s][k-1], d_k = -4 delta + 2 delta cos(k pi/(n+1)) + kappa.
 void fill_pivots(int n, int ns, double delta, double kappa, std::vector<double>& r) {
-  r.resize((size_t)ns * n);
+  r.resize((size_t)ns * n);  // [k][s], s fastest (one contiguous column per mode)
   for (int k = 1; k <= n; ++k) {
     const double d = -4.0 * delta + 2.0 * delta * cos_pi_frac(k, n + 1) + kappa;
+    double* rk = r.data() + (size_t)(k - 1) * ns;
     double rp = 1.0 / d;
-    r[(size_t)k - 1] = rp;
+    rk[0] = rp;
     for (int s = 1; s < ns; ++s) {
       rp = 1.0 / (d - delta * delta * rp);
-      r[(size_t)s * n + k - 1] = rp;
+      rk[s] = rp;
     }
   }
 }
@@ -258,7 +259,7 @@ void fill_ctab(int n, double delta, const std::vector<double>& rpivA, std::vecto
   const int N = n + 1;
   c.resize(2 * n + 2);
   std::vector<double> g(n);
-  for (int k = 1; k <= n; ++k) g[k - 1] = rpivA[(size_t)(N - 1) * n + k - 1];
+  for (int k = 1; k <= n; ++k) g[k - 1] = rpivA[(size_t)(k - 1) * N + N - 1];
   for (int m = 0; m < 2 * n + 2; ++m) {
     // compensated (Kahan) FP64 summation: exact to ~1 ulp of the sum
     double acc = 0.0, comp = 0.0;
@@ -1272,11 +1273,11 @@ fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out) {
     cudaEventElapsedTime(&ms, e0, e1);
     return ms / reps;
   };
-  // a1: line pairs per CTA x modes per CTA
+  // a1: line pairs per CTA (generic engine) x warps per CTA of the Thomas kernel
   int best_q = 0, best_mt = 0;
   float best = 1e30f;
   static const int qs[] = {0, 1, 2, 4, 8};  // 0: size-specialised kernels where compiled, else built-in Q
-  static const int mts[] = {1, 2, 4, 8, 16};
+  static const int mts[] = {4, 8, 16};
   for (int q : qs) {
     for (int mt : mts) {
       tb.q = q;

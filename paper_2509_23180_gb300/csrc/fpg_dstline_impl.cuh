@@ -40,6 +40,7 @@ struct LineShape {
   static constexpr bool rader = C::rader;
   static constexpr int N = A * B;             // DFT length run by the two passes
   static constexpr int YB = (B % 2 == 0) ? B + 1 : B;  // odd pitch: pass-2 reads hit distinct banks
+  static constexpr int LP = n + 1;            // line pitch in shared memory (odd: column walks hit distinct banks)
   static constexpr int K = (P + 1) / 2;       // unpack terms
   static constexpr int CK = (K + 31) / 32;    // unpack terms per lane
   static_assert(N == (rader ? P - 1 : P), "plan shape");
@@ -51,7 +52,7 @@ struct LineShape {
   static constexpr size_t o_pout = align16(o_pin + (rader ? sizeof(int) * N : 0));
   static constexpr size_t o_dc = align16(o_pout + (rader ? sizeof(int) * N : 0));
   static constexpr size_t o_lines = align16(o_dc + sizeof(C2<T>) * Q);
-  static constexpr size_t o_y = align16(o_lines + sizeof(T) * 2 * Q * n);
+  static constexpr size_t o_y = align16(o_lines + sizeof(T) * 2 * Q * LP);
   static constexpr size_t o_x = align16(o_y + sizeof(C2<T>) * Q * A * YB);
   static constexpr size_t bytes = align16(o_x + sizeof(C2<T>) * Q * P);
 };
@@ -65,7 +66,7 @@ struct LineSmem {
   int* pin;
   int* pout;
   C2<T>* dc;
-  T* lines;  // [2Q][n] real lines (input, then output)
+  T* lines;  // [2Q][LP] real lines (input, then output)
   C2<T>* y;  // [Q][A][YB]
   C2<T>* x;  // [Q][P]
   __device__ __forceinline__ explicit LineSmem(unsigned char* base) {
@@ -105,9 +106,9 @@ __device__ __forceinline__ void load_tables(DstPlan pl, LineSmem<T, P>& s) {
 // for the two lines, packed as real and imaginary part.
 template <typename T, int P>
 __device__ __forceinline__ C2<T> pack(const LineSmem<T, P>& s, int q, int j) {
-  constexpr int n = P - 1;
-  const T* la = s.lines + (2 * q) * n;
-  const T* lb = la + n;
+  constexpr int LP = LineShape<T, P>::LP;
+  const T* la = s.lines + (2 * q) * LP;
+  const T* lb = la + LP;
   const T a1 = la[j - 1], a2 = la[P - j - 1], b1 = lb[j - 1], b2 = lb[P - j - 1];
   const T sj = s.sinp[j];
   return C2<T>{fma(sj, a1 + a2, T(0.5) * (a1 - a2)), fma(sj, b1 + b2, T(0.5) * (b1 - b2))};
@@ -195,8 +196,8 @@ __device__ __forceinline__ void unpack(LineSmem<T, P>& s) {
   constexpr int NW = S::NT / 32;
   for (int q = wid; q < S::Q; q += NW) {
     const C2<T>* Z = s.x + q * P;
-    T* ya = s.lines + (2 * q) * n;
-    T* yb = ya + n;
+    T* ya = s.lines + (2 * q) * S::LP;
+    T* yb = ya + S::LP;
     const int k0 = lane * CK;
     T ra[CK], rb[CK], oa[CK], ob[CK];
     T sa = T(0), sb = T(0);
@@ -258,8 +259,8 @@ __device__ __forceinline__ long long boff(const BatchDesc& d, int b) {
   return (long long)(b / d.nper) * d.rhs_stride + o;
 }
 
-// Forward: 2Q lines (t along the line) of block b -> DST -> scratch[b][s][k]
-// (k fastest), in the compute precision, scaled by 2.
+// Forward: 2Q lines (t along the line) of block b -> DST -> scratch[b][k][s]
+// (s fastest), in the compute precision, scaled by 2.
 template <typename T, int P>
 __global__ void __launch_bounds__(LineShape<T, P>::NT)
 k_dst_lines_fwd(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPlan pl, T* __restrict__ scratch,
@@ -274,38 +275,35 @@ k_dst_lines_fwd(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPl
   const int nl = min(2 * Q, L.ns - s0);
   load_tables<T, P>(pl, s);
   const double* src = in + boff(ib, b);
+  constexpr int LP = S::LP;
   if (vec) {  // rows contiguous (st == 1) and 16-byte aligned: two values per load
     for (int i = threadIdx.x; i < Q * n; i += NT) {
       const int l = i / (n / 2), t2 = i - l * (n / 2);
       double2 v = make_double2(0.0, 0.0);
       if (l < nl) v = *reinterpret_cast<const double2*>(src + (long long)(s0 + l) * L.ss + 2 * t2);
-      s.lines[l * n + 2 * t2] = convert<T>(v.x);
-      s.lines[l * n + 2 * t2 + 1] = convert<T>(v.y);
+      s.lines[l * LP + 2 * t2] = convert<T>(v.x);
+      s.lines[l * LP + 2 * t2 + 1] = convert<T>(v.y);
     }
   } else {
     for (int i = threadIdx.x; i < 2 * Q * n; i += NT) {
       const int l = i / n, t = i - l * n;
       const double v = l < nl ? src[(long long)t * L.st + (long long)(s0 + l) * L.ss] : 0.0;
-      s.lines[i] = convert<T>(v);
+      s.lines[l * LP + t] = convert<T>(v);
     }
   }
   __syncthreads();
   dft_p<T, P>(s);
   unpack<T, P>(s);
   __syncthreads();
-  T* dst = scratch + ((long long)b * L.ns + s0) * n;
-  if constexpr (sizeof(T) == 4) {
-    const float4* y4 = reinterpret_cast<const float4*>(s.lines);
-    float4* d4 = reinterpret_cast<float4*>(dst);
-    for (int i = threadIdx.x; i < nl * n / 4; i += NT) d4[i] = y4[i];
-  } else {
-    const double2* y2 = reinterpret_cast<const double2*>(s.lines);
-    double2* d2 = reinterpret_cast<double2*>(dst);
-    for (int i = threadIdx.x; i < nl * n / 2; i += NT) d2[i] = y2[i];
+  // scratch[b][k][s]: rows l fastest, a warp writes runs of nl consecutive rows
+  T* dst = scratch + (long long)b * n * L.ns + s0;
+  for (int i = threadIdx.x; i < nl * n; i += NT) {
+    const int k = i / nl, l = i - k * nl;
+    dst[(long long)k * L.ns + l] = s.lines[l * LP + k];
   }
 }
 
-// Inverse: scratch[b][s][k] -> DST -> out block (To), times `scale`.
+// Inverse: scratch[b][k][s] -> DST -> out block (To), times `scale`.
 template <typename T, typename To, int P>
 __global__ void __launch_bounds__(LineShape<T, P>::NT)
 k_dst_lines_inv(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc ob, LineLayout L, DstPlan pl, T scale,
@@ -319,16 +317,11 @@ k_dst_lines_inv(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc o
   const int s0 = blockIdx.x * 2 * Q;
   const int nl = min(2 * Q, L.ns - s0);
   load_tables<T, P>(pl, s);
-  const T* src = scratch + ((long long)b * L.ns + s0) * n;
-  if constexpr (sizeof(T) == 4) {
-    const float4* s4 = reinterpret_cast<const float4*>(src);
-    float4* l4 = reinterpret_cast<float4*>(s.lines);
-    for (int i = threadIdx.x; i < 2 * Q * n / 4; i += NT)
-      l4[i] = i < nl * n / 4 ? s4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-  } else {
-    const double2* s2 = reinterpret_cast<const double2*>(src);
-    double2* l2 = reinterpret_cast<double2*>(s.lines);
-    for (int i = threadIdx.x; i < 2 * Q * n / 2; i += NT) l2[i] = i < nl * n / 2 ? s2[i] : make_double2(0.0, 0.0);
+  constexpr int LP = S::LP;
+  const T* src = scratch + (long long)b * n * L.ns + s0;  // [b][k][s]
+  for (int i = threadIdx.x; i < 2 * Q * n; i += NT) {
+    const int k = i / (2 * Q), l = i - k * (2 * Q);
+    s.lines[l * LP + k] = l < nl ? src[(long long)k * L.ns + l] : T(0);
   }
   __syncthreads();
   dft_p<T, P>(s);
@@ -338,8 +331,8 @@ k_dst_lines_inv(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc o
   if (vec) {  // rows contiguous and aligned for two-element stores
     for (int i = threadIdx.x; i < nl * (n / 2); i += NT) {
       const int l = i / (n / 2), t2 = i - l * (n / 2);
-      const To a = convert<To>(s.lines[l * n + 2 * t2] * scale);
-      const To c = convert<To>(s.lines[l * n + 2 * t2 + 1] * scale);
+      const To a = convert<To>(s.lines[l * LP + 2 * t2] * scale);
+      const To c = convert<To>(s.lines[l * LP + 2 * t2 + 1] * scale);
       To* d = dst + (long long)(s0 + l) * L.ss + 2 * t2;
       if constexpr (sizeof(To) == 8) {
         *reinterpret_cast<double2*>(d) = make_double2(a, c);
@@ -350,7 +343,7 @@ k_dst_lines_inv(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc o
   } else {
     for (int i = threadIdx.x; i < nl * n; i += NT) {
       const int l = i / n, k = i - l * n;
-      dst[(long long)k * L.st + (long long)(s0 + l) * L.ss] = convert<To>(s.lines[i] * scale);
+      dst[(long long)k * L.st + (long long)(s0 + l) * L.ss] = convert<To>(s.lines[l * LP + k] * scale);
     }
   }
 }

@@ -9,7 +9,7 @@
 // dx = dy).  So  z = (2/(n+1)) S T^{-1} S v  with S the unnormalised DST-I.
 //
 // Three launches per batch: forward DST of every line into a scratch array laid
-// out [block][s][k] (k fastest), one Thomas solve per (block, mode), inverse DST
+// out [block][k][s] (s fastest), one Thomas solve per (block, mode), inverse DST
 // back into the block layout.  Compute precision T is double or float; inputs
 // are always FP64, the output is written as To.
 #include <cuda_runtime.h>
@@ -97,174 +97,251 @@ k_dense_forward(const double* __restrict__ in, BatchDesc ib, LineLayout L, int n
     }
   }
   __syncthreads();
-  T* dst = scratch + ((long long)b * L.ns + s0) * n;
-  dst_dense_lines<T>(lines, nl, n, pitch, sintab, true,
-                     [&](int l, int k, T v) { dst[(long long)l * n + k] = v; });
+  // scratch[b][k][s]: walk l fastest so that a warp writes runs of nl rows
+  T* dst = scratch + (long long)b * n * L.ns + s0;
+  dst_dense_lines<T>(lines, nl, n, pitch, sintab, false,
+                     [&](int l, int k, T v) { dst[(long long)k * L.ns + l] = v; });
 }
 
-// One Thomas solve per (block, mode k) on scratch[b][s][k] in place.
-// Forward: y_0 = f_0 r_0, y_s = (f_s - delta y_{s-1}) r_s; backward:
-// x_{N-1} = y_{N-1}, x_s = y_s - delta r_s x_{s+1}; r_s are the reciprocal pivots.
-template <typename T>
-__global__ void k_thomas(T* __restrict__ scratch, int n, int ns, T delta, const T* __restrict__ rpiv,
-                         const int* __restrict__ active, int nper_active) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = blockIdx.y;
-  if (k >= n) return;
-  if (active != nullptr && !active[b / nper_active]) return;
-  T* col = scratch + (long long)b * ns * n + k;
-  const T* r = rpiv + k;
-  T y = col[0] * r[0];
-  col[0] = y;
-  for (int s = 1; s < ns; ++s) {
-    y = (col[(long long)s * n] - delta * y) * r[(long long)s * n];
-    col[(long long)s * n] = y;
-  }
-  T x = y;
-  for (int s = ns - 2; s >= 0; --s) {
-    x = col[(long long)s * n] - delta * r[(long long)s * n] * x;
-    col[(long long)s * n] = x;
-  }
-}
+// One Thomas solve per (block b, mode k) on scratch[b][k][s] (s fastest), in
+// place: forward y_s = r_s f_s + m_s y_{s-1}, back substitution
+// x_s = y_s + m_s x_{s+1}, with r_s the reciprocal pivots of Eq. "trans_subeq"'s
+// tridiagonal system and m_s = -delta r_s (tables laid out [k][s] as well).
+// Both are first-order linear recurrences: a warp takes one mode, lane l holds
+// rows [l C, l C + C) in registers, runs the recurrence on them with a zero
+// carry, a warp scan of the (chunk result, chunk multiplier) pairs gives each
+// lane its carry, and a fix-up adds carry x running product of m.  Same
+// operations as the sequential sweep up to the association of the carries.
+// The column moves between HBM and the registers through a per-warp shared
+// buffer (coalesced row-interleaved global access, chunk-per-lane registers);
+// r_s f_s is formed during the load, so only it and m_s are staged.
+template <int C>
+__host__ __device__ constexpr int thomas_pitch() { return C % 2 == 0 ? C + 1 : C + 2; }  // odd
 
-// The same Thomas recurrences, evaluated in parallel along the sweep: with
-// m_s = -delta r_s, the forward pass is y_s = r_s f_s + m_s y_{s-1} and the back
-// substitution x_s = y_s + m_s x_{s+1}.  Both are first-order linear recurrences,
-// so each warp takes one mode, its 32 lanes take contiguous chunks of rows, a
-// lane scan of the (chunk result, chunk multiplier) pairs supplies the carries
-// and a fix-up pass adds them.  Same operations as the sequential sweep up to
-// the association of the carries.  A CTA owns MT modes of one block, staged in
-// shared memory together with their r and m columns.
-template <typename T, int MT>
+template <typename T, int C>
 __global__ void __launch_bounds__(256)
-k_thomas_scan(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv, const T* __restrict__ mneg,
-              const int* __restrict__ active, int nper_active) {
+k_thomas_reg(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv, const T* __restrict__ mneg,
+             int nblk, const int* __restrict__ active, int nper_active) {
+  constexpr int PC = thomas_pitch<C>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int b = blockIdx.y;
+  const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // = b * n + k
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  if (wg >= (long long)nblk * n) return;  // whole warps
+  const int b = (int)(wg / n), k = (int)(wg - (long long)b * n);
   if (active != nullptr && !active[b / nper_active]) return;
-  constexpr int P = MT + 1;
-  const int k0 = blockIdx.x * MT;
-  const int mt = min(MT, n - k0);
-  const int c = (ns + 31) / 32;  // rows per lane
-  // element (s, k) at s*P + k + s/c: the one-word skew per lane chunk makes the
-  // lane-to-lane stride c*P + 1 odd, so the 32 lanes hit 32 different banks
-  const size_t span = (size_t)ns * P + 32;
-  T* xs = reinterpret_cast<T*>(smem_raw);
-  T* rs = xs + span;
-  T* ms = rs + span;
-#define FPG_SK(s, k) ((s) * P + (k) + (s) / c)
-  T* col = scratch + (long long)b * ns * n + k0;
-  for (int idx = threadIdx.x; idx < ns * MT; idx += blockDim.x) {
-    const int s = idx / MT, k = idx - s * MT;
-    if (k < mt) {
-      const long long g = (long long)s * n + k;
-      xs[FPG_SK(s, k)] = col[g];
-      rs[FPG_SK(s, k)] = rpiv[g + k0];
-      ms[FPG_SK(s, k)] = mneg[g + k0];
-    }
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int s0 = min(ns, lane * c), s1 = min(ns, s0 + c);
-  for (int k = warp; k < mt; k += nw) {
-    // forward: y_s = r_s f_s + m_s y_{s-1}
-    T acc = T(0), pr = T(1);
-    for (int s = s0; s < s1; ++s) {
-      const T m = ms[FPG_SK(s, k)];
-      acc = fma(m, acc, rs[FPG_SK(s, k)] * xs[FPG_SK(s, k)]);
-      pr *= m;
-      xs[FPG_SK(s, k)] = acc;
-    }
-    T Y = acc, Pp = pr;
+  T* bf = reinterpret_cast<T*>(smem_raw) + (size_t)wl * 2 * 32 * PC;  // [rf | m], each [32][PC]
+  T* bm = bf + 32 * PC;
+  T* col = scratch + wg * ns;
+  const T* rc = rpiv + (long long)k * ns;
+  const T* mc = mneg + (long long)k * ns;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const T Yo = __shfl_up_sync(0xffffffffu, Y, o), Po = __shfl_up_sync(0xffffffffu, Pp, o);
-      if (lane >= o) {
-        Y = fma(Pp, Yo, Y);
-        Pp *= Po;
-      }
-    }
-    T cin = __shfl_up_sync(0xffffffffu, Y, 1);
-    if (lane == 0) cin = T(0);
-    if (cin != T(0)) {
-      T q = T(1);
-      for (int s = s0; s < s1; ++s) {
-        q *= ms[FPG_SK(s, k)];
-        xs[FPG_SK(s, k)] = fma(q, cin, xs[FPG_SK(s, k)]);
-      }
-    }
-    // backward: x_s = y_s + m_s x_{s+1}
-    acc = T(0);
-    pr = T(1);
-    for (int s = s1 - 1; s >= s0; --s) {
-      const T m = ms[FPG_SK(s, k)];
-      acc = fma(m, acc, xs[FPG_SK(s, k)]);
-      pr *= m;
-      xs[FPG_SK(s, k)] = acc;
-    }
-    Y = acc;
-    Pp = pr;
+  for (int e = 0; e < C; ++e) {
+    const int s = e * 32 + lane;
+    const int at = (s / C) * PC + (s % C);
+    const bool ok = s < ns;
+    bf[at] = ok ? rc[s] * col[s] : T(0);
+    bm[at] = ok ? mc[s] : T(0);
+  }
+  __syncwarp();
+  const int s0 = lane * C;
+  // m stays in registers while they suffice (FP64 with C >= 24 would spill);
+  // otherwise it is re-read from the staging buffer
+  constexpr bool kMreg = sizeof(T) * C <= 128;
+  T x[C], mr[kMreg ? C : 1];
+  const T* ml = bm + lane * PC;
+  auto M = [&](int e) -> T {
+    if constexpr (kMreg)
+      return mr[e];
+    else
+      return ml[e];
+  };
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const T Yo = __shfl_down_sync(0xffffffffu, Y, o), Po = __shfl_down_sync(0xffffffffu, Pp, o);
-      if (lane + o < 32) {
-        Y = fma(Pp, Yo, Y);
-        Pp *= Po;
-      }
+  for (int e = 0; e < C; ++e) {
+    x[e] = bf[lane * PC + e];
+    if constexpr (kMreg) mr[e] = ml[e];
+  }
+  // forward, zero carry
+  T acc = T(0), pr = T(1);
+#pragma unroll
+  for (int e = 0; e < C; ++e) {
+    if (s0 + e < ns) {
+      acc = fma(M(e), acc, x[e]);
+      pr *= M(e);
+      x[e] = acc;
     }
-    T cdn = __shfl_down_sync(0xffffffffu, Y, 1);
-    if (lane == 31) cdn = T(0);
-    if (cdn != T(0)) {
-      T q = T(1);
-      for (int s = s1 - 1; s >= s0; --s) {
-        q *= ms[FPG_SK(s, k)];
-        xs[FPG_SK(s, k)] = fma(q, cdn, xs[FPG_SK(s, k)]);
+  }
+  T Y = acc, P = pr;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T Yo = __shfl_up_sync(0xffffffffu, Y, o), Po = __shfl_up_sync(0xffffffffu, P, o);
+    if (lane >= o) {
+      Y = fma(P, Yo, Y);
+      P *= Po;
+    }
+  }
+  T cin = __shfl_up_sync(0xffffffffu, Y, 1);
+  if (lane == 0) cin = T(0);
+  if (cin != T(0)) {
+    T q = T(1);
+#pragma unroll
+    for (int e = 0; e < C; ++e) {
+      if (s0 + e < ns) {
+        q *= M(e);
+        x[e] = fma(q, cin, x[e]);
       }
     }
   }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < ns * MT; idx += blockDim.x) {
-    const int s = idx / MT, k = idx - s * MT;
-    if (k < mt) col[(long long)s * n + k] = xs[FPG_SK(s, k)];
+  // back substitution, zero carry from above
+  acc = T(0);
+  pr = T(1);
+#pragma unroll
+  for (int e = C - 1; e >= 0; --e) {
+    if (s0 + e < ns) {
+      acc = fma(M(e), acc, x[e]);
+      pr *= M(e);
+      x[e] = acc;
+    }
   }
-#undef FPG_SK
+  Y = acc;
+  P = pr;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T Yo = __shfl_down_sync(0xffffffffu, Y, o), Po = __shfl_down_sync(0xffffffffu, P, o);
+    if (lane + o < 32) {
+      Y = fma(P, Yo, Y);
+      P *= Po;
+    }
+  }
+  T cdn = __shfl_down_sync(0xffffffffu, Y, 1);
+  if (lane == 31) cdn = T(0);
+  if (cdn != T(0)) {
+    T q = T(1);
+#pragma unroll
+    for (int e = C - 1; e >= 0; --e) {
+      if (s0 + e < ns) {
+        q *= M(e);
+        x[e] = fma(q, cdn, x[e]);
+      }
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < C; ++e) bf[lane * PC + e] = x[e];
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < C; ++e) {
+    const int s = e * 32 + lane;
+    if (s < ns) col[s] = bf[(s / C) * PC + (s % C)];
+  }
 }
 
-template <typename T, int MT>
-size_t thomas_smem(int ns) {
-  return 3 * sizeof(T) * ((size_t)ns * (MT + 1) + 32);
-}
-
-// Launch the scanned Thomas solve with the widest mode tile that fits 64 KB.
+// The same for sweeps longer than 32 * 33 rows: each lane streams its chunk
+// through global memory (the scratch column holds the intermediate values).
 template <typename T>
-cudaError_t launch_thomas_scan(T* scratch, int n, int ns, const T* rpiv, const T* mneg, int nblk,
-                               const int* active, int nper_active, cudaStream_t st, int mt_force) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_thomas_scan<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_thomas_scan<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_thomas_scan<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_thomas_scan<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_thomas_scan<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
+__global__ void __launch_bounds__(256)
+k_thomas_long(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv, const T* __restrict__ mneg,
+              int nblk, const int* __restrict__ active, int nper_active) {
+  const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wg >= (long long)nblk * n) return;
+  const int b = (int)(wg / n), k = (int)(wg - (long long)b * n);
+  if (active != nullptr && !active[b / nper_active]) return;
+  T* col = scratch + wg * ns;
+  const T* rc = rpiv + (long long)k * ns;
+  const T* mc = mneg + (long long)k * ns;
+  const int c = (ns + 31) / 32;
+  const int s0 = min(ns, lane * c), s1 = min(ns, s0 + c);
+  T acc = T(0), pr = T(1);
+  for (int s = s0; s < s1; ++s) {
+    acc = fma(mc[s], acc, rc[s] * col[s]);
+    pr *= mc[s];
+    col[s] = acc;
   }
-  const size_t budget = 64 * 1024;
-#define FPG_THOMAS_TRY(MTV)                                                                              \
-  if ((mt_force > 0 ? (mt_force == MTV && thomas_smem<T, MTV>(ns) <= 200 * 1024)                         \
-                    : thomas_smem<T, MTV>(ns) <= budget) || MTV == 1) {                                  \
-    dim3 grid((n + MTV - 1) / MTV, nblk);                                                               \
-    const int threads = 32 * (MTV < 8 ? MTV : 8);                                                       \
-    k_thomas_scan<T, MTV><<<grid, threads, thomas_smem<T, MTV>(ns), st>>>(scratch, n, ns, rpiv, mneg,  \
-                                                                         active, nper_active);          \
-    return cudaGetLastError();                                                                          \
+  T Y = acc, P = pr;
+  for (int o = 1; o < 32; o <<= 1) {
+    const T Yo = __shfl_up_sync(0xffffffffu, Y, o), Po = __shfl_up_sync(0xffffffffu, P, o);
+    if (lane >= o) {
+      Y = fma(P, Yo, Y);
+      P *= Po;
+    }
   }
-  FPG_THOMAS_TRY(16)
-  FPG_THOMAS_TRY(8)
-  FPG_THOMAS_TRY(4)
-  FPG_THOMAS_TRY(2)
-  FPG_THOMAS_TRY(1)
-#undef FPG_THOMAS_TRY
-  return cudaErrorInvalidValue;
+  T cin = __shfl_up_sync(0xffffffffu, Y, 1);
+  if (lane == 0) cin = T(0);
+  if (cin != T(0)) {
+    T q = T(1);
+    for (int s = s0; s < s1; ++s) {
+      q *= mc[s];
+      col[s] = fma(q, cin, col[s]);
+    }
+  }
+  acc = T(0);
+  pr = T(1);
+  for (int s = s1 - 1; s >= s0; --s) {
+    acc = fma(mc[s], acc, col[s]);
+    pr *= mc[s];
+    col[s] = acc;
+  }
+  Y = acc;
+  P = pr;
+  for (int o = 1; o < 32; o <<= 1) {
+    const T Yo = __shfl_down_sync(0xffffffffu, Y, o), Po = __shfl_down_sync(0xffffffffu, P, o);
+    if (lane + o < 32) {
+      Y = fma(P, Yo, Y);
+      P *= Po;
+    }
+  }
+  T cdn = __shfl_down_sync(0xffffffffu, Y, 1);
+  if (lane == 31) cdn = T(0);
+  if (cdn != T(0)) {
+    T q = T(1);
+    for (int s = s1 - 1; s >= s0; --s) {
+      q *= mc[s];
+      col[s] = fma(q, cdn, col[s]);
+    }
+  }
+}
+
+// Launch the Thomas solves: one warp per (block, mode), wpb warps per CTA
+// (0: 8, fewer when the per-warp staging buffers would pass 96 KB), rows per
+// lane C = the smallest compiled value covering ns / 32.
+template <typename T>
+cudaError_t launch_thomas(T* scratch, int n, int ns, const T* rpiv, const T* mneg, int nblk, const int* active,
+                          int nper_active, cudaStream_t st, int wpb) {
+  if (wpb <= 0) wpb = 8;
+  const long long warps = (long long)nblk * n;
+  const int need = (ns + 31) / 32;
+#define FPG_THOMAS_C(CV)                                                                                    \
+  if (need <= CV) {                                                                                         \
+    static bool attr = false;                                                                               \
+    if (!attr) {                                                                                            \
+      cudaFuncSetAttribute(k_thomas_reg<T, CV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);   \
+      attr = true;                                                                                          \
+    }                                                                                                       \
+    const size_t per = sizeof(T) * 2 * 32 * thomas_pitch<CV>();                                             \
+    int w = wpb;                                                                                            \
+    while (w > 1 && per * w > 96 * 1024) w /= 2;                                                            \
+    const dim3 grid((unsigned)((warps + w - 1) / w));                                                       \
+    k_thomas_reg<T, CV><<<grid, 32 * w, per * w, st>>>(scratch, n, ns, rpiv, mneg, nblk, active, nper_active); \
+    return cudaGetLastError();                                                                              \
+  }
+  FPG_THOMAS_C(1)
+  FPG_THOMAS_C(2)
+  FPG_THOMAS_C(3)
+  FPG_THOMAS_C(4)
+  FPG_THOMAS_C(5)
+  FPG_THOMAS_C(8)
+  FPG_THOMAS_C(9)
+  FPG_THOMAS_C(12)
+  FPG_THOMAS_C(16)
+  FPG_THOMAS_C(17)
+  FPG_THOMAS_C(24)
+  FPG_THOMAS_C(32)
+  FPG_THOMAS_C(33)
+#undef FPG_THOMAS_C
+  const dim3 grid((unsigned)((warps + wpb - 1) / wpb));
+  const int threads = 32 * wpb;
+  k_thomas_long<T><<<grid, threads, 0, st>>>(scratch, n, ns, rpiv, mneg, nblk, active, nper_active);
+  return cudaGetLastError();
 }
 
 template <typename T, typename To>
@@ -281,10 +358,10 @@ k_dense_inverse(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc o
   const int s0 = blockIdx.x * lpb;
   const int nl = min(lpb, L.ns - s0);
   for (int i = threadIdx.x; i < p2; i += blockDim.x) sintab[i] = sintab_g[i];
-  const T* src = scratch + ((long long)b * L.ns + s0) * n;
+  const T* src = scratch + (long long)b * n * L.ns + s0;  // [b][k][s]
   for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-    const int l = idx / n, t = idx - l * n;
-    lines[l * pitch + t] = src[(long long)l * n + t];
+    const int t = idx / nl, l = idx - t * nl;
+    lines[l * pitch + t] = src[(long long)t * L.ns + l];
   }
   __syncthreads();
   To* dst = batch_ptr_out(out, ob, b);
@@ -413,8 +490,7 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
     dim3 grid((L.ns + lpb - 1) / lpb, nblk);
     k_dense_forward<T><<<grid, kFsThreads, smem, st>>>(in, ib, L, n, (const T*)pl.dense, scratch, lpb, active,
                                                       nper_active);
-    launch_thomas_scan<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st,
-                          tb.mt);
+    launch_thomas<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st, tb.mt);
     k_dense_inverse<T, To><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, n, (const T*)pl.dense, lpb,
                                                           active, nper_active);
     return cudaGetLastError();
@@ -426,8 +502,7 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
     if (e != cudaSuccess) return e;
     if (ev) record_event(ev[1], st);
     if (ev) record_event(ev[2], st);
-    launch_thomas_scan<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st,
-                          tb.mt);
+    launch_thomas<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st, tb.mt);
     if (ev) record_event(ev[3], st);
     if (ev) record_event(ev[4], st);
     e = lines_inv<T, To>(pl, scratch, out, ob, L, nblk, active, nper_active, st);
@@ -452,8 +527,7 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
   if (e != cudaSuccess) return e;
   if (ev) record_event(ev[1], st);
   if (ev) record_event(ev[2], st);
-  launch_thomas_scan<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st,
-                          tb.mt);
+  launch_thomas<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st, tb.mt);
   if (ev) record_event(ev[3], st);
   if (ev) record_event(ev[4], st);
   const int oprec = sizeof(To) == 8 ? 64 : 32;
@@ -474,8 +548,8 @@ cudaError_t launch_fast_solve_fused(int prec, int out_prec, const FastSolveTable
                                     const int* active, int nper_active, cudaStream_t st);
 
 // Which kernels the fast solve of this block kind runs: 0 generic FFT engine
-// (k_fft_forward / k_thomas_scan / k_fft_inverse), 1 size-specialised
-// (k_dst_lines_fwd / k_thomas_scan / k_dst_lines_inv), 2 dense DST, 3 the fused
+// (k_fft_forward / k_thomas_reg / k_fft_inverse), 1 size-specialised
+// (k_dst_lines_fwd / k_thomas_reg / k_dst_lines_inv), 2 dense DST, 3 the fused
 // one-pass cluster kernel.
 bool fast_solve_fused_fits(int prec, const FastSolveTables& tb, LineLayout L);
 int fast_solve_path(int prec, const FastSolveTables& tb, LineLayout L, int nblk) {

@@ -50,8 +50,12 @@ k_fft_forward(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPlan
   }
   __syncthreads();
   const T* y = dst_lines<T, MAXR>(pl, sm, Q);
-  T* dst = scratch + ((long long)b * L.ns + s0) * n;
-  for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) dst[idx] = y[idx];
+  // scratch[b][k][s]: l fastest, so a warp writes runs of nl consecutive rows
+  T* dst = scratch + (long long)b * n * L.ns + s0;
+  for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+    const int k = idx / nl, l = idx - k * nl;
+    dst[(long long)k * L.ns + l] = y[l * n + k];
+  }
 }
 
 template <typename T, typename To, int MAXR>
@@ -67,8 +71,11 @@ k_fft_inverse(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc ob,
   const int nl = min(lpb, L.ns - s0);
   DstSmem<T> sm = dst_smem_carve<T>(smem_raw, pl, Q);
   dst_load_tables<T>(pl, sm);
-  const T* src = scratch + ((long long)b * L.ns + s0) * n;
-  for (int idx = threadIdx.x; idx < lpb * n; idx += blockDim.x) sm.xin[idx] = idx < nl * n ? src[idx] : T(0);
+  const T* src = scratch + (long long)b * n * L.ns + s0;  // [b][k][s]
+  for (int idx = threadIdx.x; idx < lpb * n; idx += blockDim.x) {
+    const int k = idx / lpb, l = idx - k * lpb;
+    sm.xin[l * n + k] = l < nl ? src[(long long)k * L.ns + l] : T(0);
+  }
   __syncthreads();
   const T* y = dst_lines<T, MAXR>(pl, sm, Q);
   To* dst = fft_batch_ptr_out(out, ob, b);

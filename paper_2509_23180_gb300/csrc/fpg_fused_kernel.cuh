@@ -82,7 +82,7 @@ k_fast_solve_fused(const double* __restrict__ in, BatchDesc ib, To* __restrict__
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     T acc = T(0), pr = T(1);
     for (int s = s0; s < s1; ++s) {
-      const long long g = (long long)s * n + k;
+      const long long g = (long long)k * ns + s;  // tables [k][s]
       const T m = mneg[g];
       T& c = coef[(size_t)(s - s0) * n + k];
       acc = fma(m, acc, rpiv[g] * c);
@@ -103,14 +103,14 @@ k_fast_solve_fused(const double* __restrict__ in, BatchDesc ib, To* __restrict__
     if (cin != T(0)) {
       T qq = T(1);
       for (int s = s0; s < s1; ++s) {
-        qq *= mneg[(long long)s * n + k];
+        qq *= mneg[(long long)k * ns + s];
         T& c = coef[(size_t)(s - s0) * n + k];
         c = fma(qq, cin, c);
       }
     }
     T acc = T(0), pr = T(1);
     for (int s = s1 - 1; s >= s0; --s) {
-      const T m = mneg[(long long)s * n + k];
+      const T m = mneg[(long long)k * ns + s];
       T& c = coef[(size_t)(s - s0) * n + k];
       acc = fma(m, acc, c);
       pr *= m;
@@ -130,7 +130,7 @@ k_fast_solve_fused(const double* __restrict__ in, BatchDesc ib, To* __restrict__
     if (cdn != T(0)) {
       T qq = T(1);
       for (int s = s1 - 1; s >= s0; --s) {
-        qq *= mneg[(long long)s * n + k];
+        qq *= mneg[(long long)k * ns + s];
         T& c = coef[(size_t)(s - s0) * n + k];
         c = fma(qq, cdn, c);
       }

@@ -34,10 +34,10 @@ struct FastSolveTables {
   int ns;             // sweep length
   double delta;       // 1/h^2
   DstPlan plan;       // DST-I plan and tables in the compute precision
-  const void* rpiv;   // Thomas reciprocal pivots r_s, [ns][n], compute precision
-  const void* mneg;   // -delta r_s, [ns][n], compute precision
+  const void* rpiv;   // Thomas reciprocal pivots r_s, [n][ns] (s fastest), compute precision
+  const void* mneg;   // -delta r_s, [n][ns], compute precision
   int q = 0;          // line pairs per CTA in the DST kernels (0: built-in choice)
-  int mt = 0;         // modes per CTA in the Thomas kernel (0: built-in choice)
+  int mt = 0;         // warps (= modes) per CTA in the Thomas kernel (0: 8)
   int fused = 0;      // 1: one-pass cluster kernel when the block fits
   int generic = 0;    // DST engine: 0 auto, 1 generic FFT engine, 2 size-specialised where compiled
 };

@@ -348,7 +348,7 @@ __device__ __forceinline__ double cluster_reduce(double acc, int k, const Cluste
 __host__ __device__ constexpr int reg_max_threads(int ept) { return ept >= 16 ? 256 : kRegMaxThreads; }
 
 template <typename Tz, int EPT>
-__global__ void __launch_bounds__(reg_max_threads(EPT))
+__global__ void __launch_bounds__(reg_max_threads(EPT), EPT >= 16 ? 2 : 1)
 k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const double* __restrict__ w,
                       const Tz* __restrict__ z, const double* __restrict__ corr, int n, double delta, double kappa,
                       int armmask, double* __restrict__ vout, long long len, int j, double* __restrict__ H,
@@ -366,30 +366,28 @@ k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const dou
   __shared__ double hval;
   const ClusterReduce R{red, slots, &hval};
   if (active != nullptr && !active[r]) return;  // uniform over the cluster
-  const long long chunk = (len + csz - 1) / csz;
-  const long long lo = (long long)rank * chunk;
-  const long long hi = lo + chunk < len ? lo + chunk : len;
+  // slice of this CTA: [lo, hi); thread elements lo + tid + e * nb, e < nval
+  const int chunk = (int)((len + csz - 1) / csz);
+  const int lo = rank * chunk;
+  const int hi = (int)(lo + chunk < len ? lo + chunk : len);
+  const int nb = blockDim.x, t0 = lo + threadIdx.x;
+  const int nval = t0 < hi ? (hi - t0 + nb - 1) / nb : 0;  // valid elements of this thread (<= EPT)
   const long long base = (long long)r * len;
+  const double* vt = V + base + t0;  // this thread's first element of v_0
   double wv[EPT], vc[EPT], vn[EPT];
-  {
-    const double* v0 = V + base;
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      const long long idx = lo + threadIdx.x + (long long)e * blockDim.x;
-      vc[e] = idx < hi ? v0[idx] : 0.0;
-    }
-  }
+  for (int e = 0; e < EPT; ++e) vc[e] = e < nval ? vt[e * nb] : 0.0;
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
-    const long long idx = lo + threadIdx.x + (long long)e * blockDim.x;
+    const int idx = t0 + e * nb;
     double x = 0.0;
-    if (idx < hi) {
+    if (e < nval) {
       if (z == nullptr) {
         x = w[base + idx];
       } else {
         const Tz* zr = z + base;
         const double* cr = corr + (long long)r * 4 * n;
-        const int jj = (int)(idx / n), ii = (int)(idx - (long long)jj * n);
+        const int jj = idx / n, ii = idx - jj * n;
         const double zc = ld(zr, idx);
         const double sacc = stencil_sum(zc, ii > 0 ? ld(zr, idx - 1) : 0.0, ii < n - 1 ? ld(zr, idx + 1) : 0.0,
                                         jj > 0 ? ld(zr, idx - n) : 0.0, jj < n - 1 ? ld(zr, idx + n) : 0.0);
@@ -405,12 +403,9 @@ k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const dou
   double* hcol = H + (long long)r * hrhs_stride + (long long)j * hcol_stride;
   for (int k = 0; k <= j; ++k) {
     if (k < j) {  // prefetch v_{k+1}; consumed after this step's reduction
-      const double* vk1 = V + (long long)(k + 1) * vstride + base;
+      const double* vk1 = vt + (long long)(k + 1) * vstride;
 #pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        const long long idx = lo + threadIdx.x + (long long)e * blockDim.x;
-        vn[e] = idx < hi ? vk1[idx] : 0.0;
-      }
+      for (int e = 0; e < EPT; ++e) vn[e] = e < nval ? vk1[e * nb] : 0.0;
     }
     double acc = 0.0;
 #pragma unroll
@@ -428,12 +423,10 @@ k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const dou
   for (int e = 0; e < EPT; ++e) acc = fma(wv[e], wv[e], acc);
   const double hn = sqrt(cluster_reduce(acc, j + 1, R, csz, rank));
   const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
-  double* vr = vout + base;
+  double* vr = vout + base + t0;
 #pragma unroll
-  for (int e = 0; e < EPT; ++e) {
-    const long long idx = lo + threadIdx.x + (long long)e * blockDim.x;
-    if (idx < hi) vr[idx] = wv[e] * inv;
-  }
+  for (int e = 0; e < EPT; ++e)
+    if (e < nval) vr[e * nb] = wv[e] * inv;
   if (rank == 0 && threadIdx.x == 0) {
     double* h = hcol;
     h[j + 1] = hn;

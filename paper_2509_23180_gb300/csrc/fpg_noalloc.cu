@@ -151,11 +151,11 @@ cudaError_t upload_tables(DeviceState& st, int n, double kappa, cudaStream_t str
   }
   for (int k = 1; k <= n; ++k) {
     const double d = -4.0 * delta + 2.0 * delta * cospi_frac(k, p) + kappa;
-    double rp = 1.0 / d;
-    h_rpiv[k - 1] = rp;
+    double rp = 1.0 / d;  // [k][s] layout, s fastest
+    h_rpiv[(size_t)(k - 1) * n] = rp;
     for (int s = 1; s < n; ++s) {
       rp = 1.0 / (d - delta * delta * rp);
-      h_rpiv[(size_t)s * n + k - 1] = rp;
+      h_rpiv[(size_t)(k - 1) * n + s] = rp;
     }
   }
   for (long long i = 0; i < (long long)n * n; ++i) h_mneg[i] = -delta * h_rpiv[i];
