@@ -726,6 +726,7 @@ def run_extra(args):
                                  "budget_gb": args.budget_gb, "max_inflight": 8, "restart": 40, "rtol": args.rtol},
                       "latency_ms": summ["latency_ms"], "requests": summ["requests"], "solves": summ["solves"],
                       "wall_s": wall, "residual_max": summ["residual_max"], "all_converged": summ["all_converged"],
+                      "failures": summ["failures"], "requests_coalesced": srv.coalesced,
                       "domains_created": srv.created, "domains_evicted": srv.evicted,
                       "peak_gb": srv.peak_bytes / 1e9})
         srv.close()

@@ -251,8 +251,22 @@ typedef enum {
    * where one is compiled for the length and pays off (see
    * fpg_fast_solve_path), 1 always the generic FFT engine, 2 the specialised
    * kernels wherever one is compiled. */
-  FPG_OPT_DST_ENGINE = 7
+  FPG_OPT_DST_ENGINE = 7,
+  /* Reduced Schur term (FPG_SCHUR_REDUCED): 0 (default) as the O(n^2)
+   * Toeplitz-minus-Hankel sum c(|i-j|) - c(i+j+2), one thread per output;
+   * 1 as delta^2 Q diag(g_k) Q with two DST-I per interface line where the
+   * size-specialised DST is compiled (n = 64, 256, 512) -- fewer operations, but
+   * only (lines / line batch) CTAs, slower at the batch sizes measured so far.
+   * Same operator. */
+  FPG_OPT_SCHUR_TRANSFORM = 8
 } fpg_option;
+
+/* Move a domain to another CUDA stream (a cudaStream_t; NULL = the default
+ * stream) for its later calls, e.g. a serving worker that reuses resident
+ * domains on its own stream.  The caller orders the switch: work the domain
+ * issued on its previous stream must be complete or ordered before the next
+ * call.  A domain must never be used from two streams at once. */
+fpg_status fpg_set_stream(fpg_domain* d, void* stream);
 
 /* Set an option on a domain (affects later calls).  FPG_EINVAL if unknown. */
 fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value);

@@ -26,6 +26,7 @@ OPT_FUSED_FASTSOLVE = 4
 OPT_ARNOLDI_CSZ = 5
 OPT_ARNOLDI_THREADS = 6
 OPT_DST_ENGINE = 7
+OPT_SCHUR_TRANSFORM = 8
 PRECOND = {"fft": 0, "none": 1, "jacobi": 2}
 PHASES = ("precond", "schur", "arnoldi", "givens", "cycle_end", "setup_finish", "residual",
           "dst_forward", "thomas", "dst_inverse", "fast_solve_fused")
@@ -89,6 +90,7 @@ _SIGS = {
     "fpg_global_residual": ([_P, _P, _P, _P, _I32], _I32),
     "fpg_apply_global": ([_P, _P, _P, _I32], _I32),
     "fpg_set_option": ([_P, _I32, _I32], _I32),
+    "fpg_set_stream": ([_P, _P], _I32),
     "fpg_autotune": ([_P, _P], _I32),
     "fpg_set_profiling": ([_P, _I32], _I32),
     "fpg_phase_stats": ([_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D)], _I32),
@@ -251,6 +253,11 @@ class Domain:
         r = TuneResult()
         _check(self.lib.fpg_autotune(self.handle, ctypes.byref(r)), "fpg_autotune")
         return {"q": r.q, "mt": r.mt, "cluster": r.cluster, "threads": r.threads, "precond_ms": r.precond_ms, "arnoldi_ms": r.arnoldi_ms}
+
+    def set_stream(self, stream):
+        """fpg_set_stream: later calls run on this torch stream."""
+        self.stream = stream
+        _check(self.lib.fpg_set_stream(self.handle, stream.cuda_stream), "fpg_set_stream")
 
     def set_option(self, option: int, value: int):
         _check(self.lib.fpg_set_option(self.handle, option, value), "fpg_set_option")

@@ -17,6 +17,9 @@ namespace fpg {
 cudaError_t launch_fast_solve(int prec, int out_prec, const FastSolveTables& tb, LineLayout L, const double* in,
                               BatchDesc ib, void* out, BatchDesc ob, int nblk, void* scratch, const int* active,
                               int nper_active, cudaStream_t st, int* launches, cudaEvent_t* ev = nullptr);
+bool schur_dst_supported(int n);
+cudaError_t launch_schur_dst(const void* z, int zprec, long long zstride, int n, const DstPlan& pl, const double* gsc,
+                             const int* arms, int narms, double* corr, const int* active, int nrhs, cudaStream_t st);
 cudaError_t launch_schur_reduced(const void* z, int zprec, long long zstride, int n, const double* ctab,
                                  const int* arms_dev, int narms, double* corr, const int* active, int nrhs,
                                  cudaStream_t st);
@@ -184,6 +187,8 @@ struct fpg_domain {
   BatchDesc we, sn;  // arm groups inside full vectors
   FastSolveTables tC64, tC32, tA64, tA32;
   double* ctab;
+  double* gsc;           // [n] g_k delta^2 / (2 (n+1)), the transform form of the reduced Schur term
+  int schur_transform = 0;  // 1: reduced Schur term by two DST-I per line where compiled (else the table sum)
   int* arms_dev;
   double *f, *tmp, *tmp2, *pbuf, *lit_in, *lit_out, *corr, *gres, *fnorm;
   int* resume_dev = nullptr;
@@ -432,6 +437,7 @@ void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostP
   p = c.take(sizeof(double) * L.na);          if (D) D->tA64.mneg = p;
   p = c.take(sizeof(float) * L.na);           if (D) D->tA32.mneg = p;
   p = c.take(sizeof(double) * (2 * n + 2));   if (D) D->ctab = (double*)p;
+  p = c.take(sizeof(double) * n);             if (D) D->gsc = (double*)p;
   p = c.take(sizeof(int) * 4);                if (D) D->arms_dev = (int*)p;
   p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->f = (double*)p;
   p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->tmp = (double*)p;
@@ -603,8 +609,12 @@ fpg_status arm_solves_refined(fpg_domain* D, const double* in, double* out, doub
 fpg_status schur_corr(fpg_domain* D, const void* z, int zprec, int nvec, const int* active) {
   const Layout& L = D->L;
   if (D->desc.schur_mode == FPG_SCHUR_REDUCED) {
-    FPG_CUDA_TRY(launch_schur_reduced(z, zprec, L.nc, L.n, D->ctab, D->arms_dev, L.narms, D->corr, active, nvec,
-                                      D->st));
+    if (D->schur_transform && schur_dst_supported(L.n))
+      FPG_CUDA_TRY(launch_schur_dst(z, zprec, L.nc, L.n, D->tC64.plan, D->gsc, D->arms_dev, L.narms, D->corr, active,
+                                    nvec, D->st));
+    else
+      FPG_CUDA_TRY(launch_schur_reduced(z, zprec, L.nc, L.n, D->ctab, D->arms_dev, L.narms, D->corr, active, nvec,
+                                        D->st));
     count(D, 1, 1);
   } else {
     FPG_CUDA_TRY(launch_literal_inject(z, zprec, L.nc, L.n, D->delta, D->lit_in, L.ntot, L.ao, active, nvec,
@@ -806,13 +816,17 @@ fpg_status stage_cycle(fpg_domain* D) {
       D->phase_launches[i] = ph_before[i];
     }
     D->graph_profiled = D->profiling;
-    if (st != FPG_OK) {
+    if (st != FPG_OK || ce != cudaSuccess) {
+      // Nothing of a failed capture ran.  A capture can be invalidated from
+      // outside (work another thread put on the same stream, a device-wide
+      // synchronisation): clear the error, give up graphs on this domain and
+      // issue the cycle directly.
       if (graph) cudaGraphDestroy(graph);
-      return st;
-    }
-    if (ce != cudaSuccess) {
-      record_cuda_error(ce, "cudaStreamEndCapture");
-      return FPG_ECUDA;
+      cudaGetLastError();
+      D->launches = before;
+      D->use_graphs = false;
+      if (st != FPG_OK && st != FPG_ECUDA) return st;
+      return issue_cycle(D);
     }
     const cudaError_t ie = cudaGraphInstantiate(&D->cycle_exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -1003,6 +1017,8 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   fill_pivots(n, n, D->delta, desc->kappa, pc);
   fill_pivots(n, n + 1, D->delta, desc->kappa, pa);
   fill_ctab(n, D->delta, pa, ct);
+  std::vector<double> gs(n);
+  for (int k = 1; k <= n; ++k) gs[k - 1] = pa[(size_t)(k - 1) * (n + 1) + n] * D->delta * D->delta / (2.0 * (n + 1));
   std::vector<float> pc32(pc.begin(), pc.end()), pa32(pa.begin(), pa.end());
   std::vector<double> mc(pc.size()), ma(pa.size());
   for (size_t i = 0; i < pc.size(); ++i) mc[i] = -D->delta * pc[i];
@@ -1043,6 +1059,7 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   if (!err) err = cp(D->tA64.mneg, ma.data(), sizeof(double) * ma.size());
   if (!err) err = cp(D->tA32.mneg, ma32.data(), sizeof(float) * ma32.size());
   if (!err) err = cp(D->ctab, ct.data(), sizeof(double) * ct.size());
+  if (!err) err = cp(D->gsc, gs.data(), sizeof(double) * gs.size());
   if (!err) err = cp(D->arms_dev, arms, sizeof(arms));
   if (!err) err = cudaMemsetAsync(D->f, 0, sizeof(double) * nrhs * L.ntot, D->st);
   if (!err) err = cudaStreamSynchronize(D->st);
@@ -1356,6 +1373,11 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
       for (auto* t : {&d->tC64, &d->tC32, &d->tA64, &d->tA32}) t->generic = value;
       drop_graph(d);
       return FPG_OK;
+    case FPG_OPT_SCHUR_TRANSFORM:
+      if (value < 0 || value > 1) return FPG_EINVAL;
+      d->schur_transform = value;
+      drop_graph(d);
+      return FPG_OK;
     case FPG_OPT_ARNOLDI_CSZ:
       if (value < 0 || value > 16) return FPG_EINVAL;
       d->tune_csz = value;
@@ -1389,6 +1411,12 @@ fpg_status fpg_phase_stats(fpg_domain* d, int32_t phase, int64_t* launches, doub
   ev_collect(d);  // events of operator calls made since the last solve
   if (launches) *launches = d->phase_launches[phase];
   if (ms) *ms = d->phase_ms[phase];
+  return FPG_OK;
+}
+
+fpg_status fpg_set_stream(fpg_domain* d, void* stream) {
+  if (!d) return FPG_EINVAL;
+  d->st = (cudaStream_t)stream;  // an instantiated cycle graph launches on any stream
   return FPG_OK;
 }
 

@@ -26,7 +26,7 @@ FPG_LINECFG(float, 257, 16, 16, true, 16, 256)
 FPG_LINECFG(float, 513, 27, 19, false, 8, 256)
 FPG_LINECFG(float, 1025, 25, 41, false, 4, 192)
 FPG_LINECFG(double, 65, 13, 5, false, 16, 256)
-FPG_LINECFG(double, 257, 16, 16, true, 8, 128)
+FPG_LINECFG(double, 257, 16, 16, true, 4, 64)
 FPG_LINECFG(double, 513, 27, 19, false, 4, 128)
 #undef FPG_LINECFG
 
@@ -54,7 +54,11 @@ struct LineShape {
   static constexpr size_t o_lines = align16(o_dc + sizeof(C2<T>) * Q);
   static constexpr size_t o_y = align16(o_lines + sizeof(T) * 2 * Q * LP);
   static constexpr size_t o_x = align16(o_y + sizeof(C2<T>) * Q * A * YB);
-  static constexpr size_t bytes = align16(o_x + sizeof(C2<T>) * Q * P);
+  // x: the spectra [Q][P] (Stockham), or FFT2's pass-1 output [Q][A][YB] (Rader;
+  // the final spectra then go back into y, pitch ZP)
+  static constexpr int XP = (rader && A * YB > P) ? A * YB : P;
+  static constexpr int ZP = rader ? A * YB : P;  // pitch of the spectra handed to unpack
+  static constexpr size_t bytes = align16(o_x + sizeof(C2<T>) * Q * XP);
 };
 
 template <typename T, int P>
@@ -68,7 +72,7 @@ struct LineSmem {
   C2<T>* dc;
   T* lines;  // [2Q][LP] real lines (input, then output)
   C2<T>* y;  // [Q][A][YB]
-  C2<T>* x;  // [Q][P]
+  C2<T>* x;  // [Q][XP]
   __device__ __forceinline__ explicit LineSmem(unsigned char* base) {
     sinp = reinterpret_cast<T*>(base + S::o_sinp);
     tw = reinterpret_cast<C2<T>*>(base + S::o_tw);
@@ -151,51 +155,85 @@ __device__ __forceinline__ void pass2(LineSmem<T, P>& s, Out out) {
   }
 }
 
-// DFT of length p of every packed line pair; result in s.x[q][k].
+// DFT of length p of every packed line pair; returns the spectra, pair q at
+// [q * ZP + k].
 template <typename T, int P>
-__device__ __forceinline__ void dft_p(LineSmem<T, P>& s) {
+__device__ __forceinline__ const C2<T>* dft_p(LineSmem<T, P>& s) {
   using S = LineShape<T, P>;
   if constexpr (!S::rader) {
     pass1<T, P>(s, [&](int q, int j) { return j == 0 ? C2<T>{T(0), T(0)} : pack<T, P>(s, q, j); });
     __syncthreads();
     pass2<T, P>(s, [&](int q, int k, C2<T> v) { s.x[q * P + k] = v; });
     __syncthreads();
+    return s.x;
   } else {
     // Rader: with g a generator mod p, A_b = z_{g^b}; X_{g^{-a}} = (A (*) w)[a],
-    // w_c = w_p^{g^{-c}}, a cyclic convolution of length N = p - 1; X_0 = sum_b A_b
-    // (z_0 = 0 because x_0 = x_p = 0).
-    constexpr int N = S::N;
+    // w_c = w_p^{g^{-c}}, a cyclic convolution of length N = p - 1 done as
+    // conj(DFT(conj(DFT(A) . B))) with B = DFT(w)/N; X_0 = sum_b A_b (z_0 = 0
+    // because x_0 = x_p = 0).  N = A * A: the thread that finishes the first
+    // DFT's outputs k = ka + A kb (all kb) holds exactly the inputs of the
+    // second DFT's first pass for jb = ka, so the two meet in registers.
+    constexpr int A = S::A, B = S::B, N = S::N, YB = S::YB;
+    static_assert(A == B && N == P - 1, "Rader length A * A");
     pass1<T, P>(s, [&](int q, int b) { return pack<T, P>(s, q, s.pin[b]); });
     __syncthreads();
-    pass2<T, P>(s, [&](int q, int k, C2<T> v) {
-      if (k == 0) s.dc[q] = v;
-      const C2<T> m = c_mul(v, s.bhat[k]);  // bhat carries the 1/N of the inverse DFT
-      s.x[q * P + k] = C2<T>{m.x, -m.y};    // conj: the inverse DFT as a forward one
-    });
+    for (int t = threadIdx.x; t < S::Q * A; t += S::NT) {
+      const int q = t / A, ka = t - q * A;
+      C2<T> v[B];
+      const C2<T>* yq = s.y + q * (A * YB) + ka * YB;
+      static_for<B>([&](auto jb) { v[decltype(jb)::value] = yq[decltype(jb)::value]; });
+      dft<B, T>(v);  // first DFT, outputs k = ka + A kb
+      if (ka == 0) s.dc[q] = v[0];
+      static_for<B>([&](auto kbi) {
+        constexpr int kb = decltype(kbi)::value;
+        const C2<T> m = c_mul(v[kb], s.bhat[ka + A * kb]);  // bhat carries the 1/N
+        v[kb] = C2<T>{m.x, -m.y};  // conj: the inverse DFT as a forward one
+      });
+      // second DFT, pass 1 for jb' = ka: inputs ja' = kb are v[kb]
+      dft<A, T>(v);
+      C2<T>* xq = s.x + q * (A * YB) + ka;
+      const C2<T>* tw = s.tw + ka;
+      xq[0] = v[0];
+      static_for<A - 1>([&](auto kai) {
+        constexpr int kk = decltype(kai)::value + 1;
+        xq[kk * YB] = c_mul(v[kk], tw[kk * B]);
+      });
+    }
     __syncthreads();
-    pass1<T, P>(s, [&](int q, int j) { return s.x[q * P + j]; });
+    // second DFT, pass 2, from x into y; scatter X_{g^{-a}} = conj(C_a)
+    for (int t = threadIdx.x; t < S::Q * A; t += S::NT) {
+      const int q = t / A, ka = t - q * A;
+      C2<T> v[B];
+      const C2<T>* xq = s.x + q * (A * YB) + ka * YB;
+      static_for<B>([&](auto jb) { v[decltype(jb)::value] = xq[decltype(jb)::value]; });
+      dft<B, T>(v);
+      C2<T>* zq = s.y + q * S::ZP;
+      static_for<B>([&](auto kbi) {
+        constexpr int kb = decltype(kbi)::value;
+        const C2<T> c = v[kb];
+        zq[s.pout[ka + A * kb]] = C2<T>{c.x, -c.y};
+      });
+    }
+    for (int q = threadIdx.x; q < S::Q; q += S::NT) s.y[q * S::ZP] = s.dc[q];
     __syncthreads();
-    pass2<T, P>(s, [&](int q, int a, C2<T> v) { s.x[q * P + s.pout[a]] = C2<T>{v.x, -v.y}; });
-    for (int q = threadIdx.x; q < S::Q; q += S::NT) s.x[q * P] = s.dc[q];
-    static_assert(N == P - 1, "Rader length");
-    __syncthreads();
+    return s.y;
   }
 }
 
-// Unpack the spectra of s.x into the 2Q real output lines (in s.lines), scaled
+// Unpack the spectra into the 2Q real output lines (in s.lines), scaled
 // by 2 (the 1/2 factors are left out): for each pair, with U = (Z_k + conj Z_{p-k})/2
 // (line a) and (Z_k - conj Z_{p-k})/(2i) (line b),
 //   y_{2k} = -Im U_k,  y_1 = Re U_0 / 2,  y_{2k+1} = y_{2k-1} + Re U_k,
 // one warp per pair, each lane a contiguous run of CK terms, a warp scan for
 // the prefix sum.
 template <typename T, int P>
-__device__ __forceinline__ void unpack(LineSmem<T, P>& s) {
+__device__ __forceinline__ void unpack(LineSmem<T, P>& s, const C2<T>* spectra) {
   using S = LineShape<T, P>;
   constexpr int n = S::n, K = S::K, CK = S::CK;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int NW = S::NT / 32;
   for (int q = wid; q < S::Q; q += NW) {
-    const C2<T>* Z = s.x + q * P;
+    const C2<T>* Z = spectra + q * S::ZP;
     T* ya = s.lines + (2 * q) * S::LP;
     T* yb = ya + S::LP;
     const int k0 = lane * CK;
@@ -292,8 +330,7 @@ k_dst_lines_fwd(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPl
     }
   }
   __syncthreads();
-  dft_p<T, P>(s);
-  unpack<T, P>(s);
+  unpack<T, P>(s, dft_p<T, P>(s));
   __syncthreads();
   // scratch[b][k][s]: rows l fastest, a warp writes runs of nl consecutive rows
   T* dst = scratch + (long long)b * n * L.ns + s0;
@@ -324,8 +361,7 @@ k_dst_lines_inv(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc o
     s.lines[l * LP + k] = l < nl ? src[(long long)k * L.ns + l] : T(0);
   }
   __syncthreads();
-  dft_p<T, P>(s);
-  unpack<T, P>(s);
+  unpack<T, P>(s, dft_p<T, P>(s));
   __syncthreads();
   To* dst = out + boff(ob, b);
   if (vec) {  // rows contiguous and aligned for two-element stores

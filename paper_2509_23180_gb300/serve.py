@@ -4,13 +4,20 @@ and size, admitted against an HBM budget.
 Requests (geometry, n, kappa, 1..slot_rhs right-hand sides) arrive over time.
 The server keeps device-resident domains -- workspaces with the tables, Krylov
 basis and Hessenberg state of Alg. "fft_dd_solver" -- keyed by (geometry, n,
-kappa), each with `slot_rhs` right-hand-side slots and its own CUDA stream.  A
-request is admitted as soon as a worker is free and the bytes of all live
-domains fit the budget (idle domains of other keys are evicted, least recently
-used first, to make room).  Up to `max_inflight` requests run at once, each on
-its domain's stream from its own host thread (the library call releases the
-GIL), so the kernels of different requests overlap on the device while new
-requests keep arriving.  Unused slots of a domain carry a zero right-hand side,
+kappa), each with `slot_rhs` right-hand-side slots.  A request is admitted as
+soon as a worker is free and the bytes of all live domains fit the budget (idle
+domains of other keys are evicted, least recently used first, to make room).
+Up to `max_inflight` workers run at once, each from its own host thread (the
+library call releases the GIL) on that worker's own CUDA stream -- the domain
+is moved onto it with fpg_set_stream -- so the kernels of different requests
+overlap on the device while new requests keep arriving.  A free worker takes
+the oldest pending request together with later pending requests of the same
+key whose right-hand sides still fit the domain's slots, and solves them in
+one batch (each right-hand side is solved independently, so a result does not
+depend on its slot or its batch mates).  Streams belong to
+workers, not domains: torch hands out pooled streams, and a domain created per
+stream would, after enough creations, share a stream with a domain that is
+running in another thread.  Unused slots of a domain carry a zero right-hand side,
 which the solver marks converged before the first Arnoldi step.
 
 Everything on the device goes through the C ABI (paper_2509_23180_gb300.binding);
@@ -21,7 +28,6 @@ from __future__ import annotations
 import threading
 import time
 from collections import OrderedDict
-from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 from . import binding as B
@@ -38,6 +44,7 @@ class Result:
     residuals: list = field(default_factory=list)
     status: int = 0
     solution: object = None  # host tensor (nrhs, unknowns) when keep_solutions
+    key: tuple = ()          # (geometry, n, kappa)
 
     @property
     def latency_s(self) -> float:
@@ -58,7 +65,11 @@ class Server:
         self.keep = keep_solutions
         self.device = device
         self._lock = threading.Condition()
-        self._idle = OrderedDict()   # key -> list of idle (Domain, stream, p-buffer)
+        # one stream per worker thread, created up front (distinct pooled streams)
+        self._streams = [torch.cuda.Stream(device=device) for _ in range(max_inflight)]
+        self._next_stream = 0
+        self._tls = threading.local()
+        self._idle = OrderedDict()   # key -> list of idle (Domain, None, p-buffer)
         self._bytes = 0.0            # workspace bytes of all live domains
         self._live = 0
         self.created = 0
@@ -106,12 +117,21 @@ class Server:
                     break
                 self._lock.wait()  # every other domain is busy: wait for a release
         torch = self.torch
-        stream = torch.cuda.Stream(device=self.device)
+        stream = self._worker_stream()
         with torch.cuda.stream(stream):
             dom = B.Domain(self._desc(key), stream=stream, device=self.device)
             p = torch.zeros((self.slot_rhs, dom.N), dtype=torch.float64, device=self.device)
         self.created += 1
-        return dom, stream, p
+        return dom, None, p
+
+    def _worker_stream(self):
+        s = getattr(self._tls, "stream", None)
+        if s is None:
+            with self._lock:
+                s = self._streams[self._next_stream % len(self._streams)]
+                self._next_stream += 1
+            self._tls.stream = s
+        return s
 
     def _release(self, key, entry):
         with self._lock:
@@ -119,55 +139,127 @@ class Server:
             self._idle.move_to_end(key)
             self._lock.notify_all()
 
-    # -- one request -----------------------------------------------------
-    def solve_request(self, req: dict, t0: float, arrival_s: float | None = None) -> Result:
-        """Solve one request (on the calling thread); times are seconds after t0;
-        arrival_s overrides the request's own arrival time."""
+    # -- one solve: one or more requests of the same key --------------------
+    def solve_batch(self, reqs, t0: float, arrival_override: float | None = None):
+        """Solve requests of one key together on one domain (their right-hand
+        sides fill consecutive slots; on the calling thread); times are seconds
+        after t0.  Returns one Result per request."""
         import workloads as W
         torch = self.torch
-        key = (req["geometry"], int(req["n"]), float(req["kappa"]))
-        nr = int(req["nrhs"])
-        if nr < 1 or nr > self.slot_rhs:
-            raise ValueError(f"request {req['id']}: nrhs {nr} outside 1..{self.slot_rhs}")
+        key = (reqs[0]["geometry"], int(reqs[0]["n"]), float(reqs[0]["kappa"]))
+        nrs = [int(r["nrhs"]) for r in reqs]
+        for r, nr in zip(reqs, nrs):
+            if nr < 1 or nr > self.slot_rhs:
+                raise ValueError(f"request {r['id']}: nrhs {nr} outside 1..{self.slot_rhs}")
+            if (r["geometry"], int(r["n"]), float(r["kappa"])) != key:
+                raise ValueError("solve_batch: requests of different keys")
+        if sum(nrs) > self.slot_rhs:
+            raise ValueError("solve_batch: more right-hand sides than slots")
         entry = self._acquire(key)
-        dom, stream, p = entry
+        dom, _, p = entry
+        stream = self._worker_stream()
+        if dom.stream is not stream:
+            dom.set_stream(stream)  # the previous user's work finished before its release
         start = time.perf_counter() - t0
         try:
             with torch.cuda.stream(stream):
                 f = torch.zeros((self.slot_rhs, dom.N), dtype=torch.float64, device=self.device)
-                for r in range(nr):
-                    f[r] = W.fourier_rhs_torch(key[0], key[1], int(req["seed"]) * 16 + r, device=self.device)
+                slot = 0
+                for r, nr in zip(reqs, nrs):
+                    for i in range(nr):
+                        f[slot] = W.fourier_rhs_torch(key[0], key[1], int(r["seed"]) * 16 + i, device=self.device)
+                        slot += 1
                 dom.set_rhs(f)
                 st, info = dom.solve(p, check=False)
-                sol = p[:nr].to("cpu", non_blocking=False) if self.keep else None
+                sol = p[:slot].to("cpu", non_blocking=False) if self.keep else None
             end = time.perf_counter() - t0
         finally:
             self._release(key, entry)
-        arr = float(req["arrival_s"]) if arrival_s is None else arrival_s
-        return Result(id=int(req["id"]), arrival_s=arr, start_s=start, end_s=end, nrhs=nr,
-                      iterations=[i["iterations"] for i in info[:nr]],
-                      residuals=[i["residual"] for i in info[:nr]],
-                      status=max([i["status"] for i in info[:nr]] or [0]), solution=sol)
+        out, s0 = [], 0
+        for r, nr in zip(reqs, nrs):
+            arr = float(r["arrival_s"]) if arrival_override is None else arrival_override
+            inf = info[s0:s0 + nr]
+            out.append(Result(id=int(r["id"]), arrival_s=arr, start_s=start, end_s=end, nrhs=nr,
+                              iterations=[i["iterations"] for i in inf], residuals=[i["residual"] for i in inf],
+                              status=max([i["status"] for i in inf] or [0]),
+                              solution=sol[s0:s0 + nr] if sol is not None else None, key=key))
+            s0 += nr
+        return out
+
+    def solve_request(self, req: dict, t0: float, arrival_s: float | None = None) -> Result:
+        """Solve one request alone (on the calling thread)."""
+        return self.solve_batch([req], t0, arrival_s)[0]
 
     # -- a stream of requests ---------------------------------------------
     def serve(self, requests, realtime: bool = True):
-        """Run a request stream: each request is submitted at its arrival time
-        (realtime=True), or all of them at time 0 (realtime=False, latencies then
-        count from the start of the run); returns the results in request order."""
-        pool = ThreadPoolExecutor(max_workers=self.max_inflight)
+        """Run a request stream with continuous batching: requests enter a
+        pending queue at their arrival time (realtime=True; else all at time 0,
+        latencies then count from the start of the run).  Each of max_inflight
+        workers takes the oldest pending request plus the next pending requests
+        of the same (geometry, n, kappa) while their right-hand sides fit the
+        domain's slots, and solves them together; requests that arrive while
+        others are on the GPU join the queue and go out with the next free
+        worker.  Returns the results in request order."""
         t0 = time.perf_counter()
-        futs = []
+        pending = []              # arrived, not yet taken (FIFO)
+        cv = threading.Condition()
+        state = {"closed": False, "error": None}
+        results = {}
+        self.coalesced = 0
+
+        def key_of(r):
+            return (r["geometry"], int(r["n"]), float(r["kappa"]))
+
+        def worker():
+            while True:
+                with cv:
+                    while not pending and not state["closed"] and state["error"] is None:
+                        cv.wait()
+                    if state["error"] is not None or (not pending and state["closed"]):
+                        return
+                    head = pending.pop(0)
+                    batch, room, k = [head], self.slot_rhs - int(head["nrhs"]), key_of(head)
+                    i = 0
+                    while i < len(pending) and room > 0:
+                        r = pending[i]
+                        if key_of(r) == k and int(r["nrhs"]) <= room:
+                            batch.append(pending.pop(i))
+                            room -= int(r["nrhs"])
+                        else:
+                            i += 1
+                    self.coalesced += len(batch) - 1
+                try:
+                    res = self.solve_batch(batch, t0, None if realtime else 0.0)
+                except BaseException as e:  # stop the stream; re-raised below
+                    with cv:
+                        state["error"] = e
+                        cv.notify_all()
+                    return
+                with cv:
+                    for r in res:
+                        results[r.id] = r
+
+        threads = [threading.Thread(target=worker, daemon=True) for _ in range(self.max_inflight)]
+        for th in threads:
+            th.start()
         for req in requests:
+            if state["error"] is not None:
+                break
             if realtime:
                 delay = float(req["arrival_s"]) - (time.perf_counter() - t0)
                 if delay > 0:
                     time.sleep(delay)
-                futs.append(pool.submit(self.solve_request, req, t0))
-            else:
-                futs.append(pool.submit(self.solve_request, req, t0, 0.0))
-        results = [f.result() for f in futs]
-        pool.shutdown()
-        return results
+            with cv:
+                pending.append(req)
+                cv.notify()
+        with cv:
+            state["closed"] = True
+            cv.notify_all()
+        for th in threads:
+            th.join()
+        if state["error"] is not None:
+            raise state["error"]
+        return [results[int(r["id"])] for r in requests]
 
     def close(self):
         with self._lock:
@@ -189,4 +281,7 @@ def summarize(results, wall_s: float) -> dict:
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
             "residual_max": max(res) if res else None,
-            "all_converged": all(r.status == B.FPG_OK for r in results)}
+            "all_converged": all(r.status == B.FPG_OK for r in results),
+            "failures": [{"id": r.id, "key": list(r.key), "nrhs": r.nrhs, "status": r.status,
+                          "iterations": r.iterations, "residuals": r.residuals}
+                         for r in results if r.status != B.FPG_OK][:12]}

@@ -111,11 +111,11 @@ def test_line_dst_vs_oracle_n256(lib, prec, tol):
 
 def test_line_dst_engine_choice(lib):
     """Default choice: FP32 always specialised where compiled; FP64 only when the
-    batch fills the GPU (10 x 256^2 stays on the generic engine)."""
+    batch gives enough threads (10 x 256^2 does, one 64^2 block does not)."""
     from paper_2509_23180_gb300 import binding as B
-    for prec, nrhs, want in ((32, 2, 1), (64, 10, 0), (64, 64, 1)):
-        d = B.Domain(B.make_desc("cross", 256, 0.0, nrhs=nrhs, restart=2, precond_precision=prec))
-        assert d.fast_solve_path() == want, (prec, nrhs)
+    for prec, n, nrhs, want in ((32, 256, 2, 1), (64, 256, 10, 1), (64, 256, 64, 1), (64, 64, 1, 0)):
+        d = B.Domain(B.make_desc("cross", n, 0.0, nrhs=nrhs, restart=2, precond_precision=prec))
+        assert d.fast_solve_path() == want, (prec, n, nrhs)
         d.close()
 
 
@@ -193,3 +193,32 @@ def test_convert_f32_to_f64_exact(lib):
     B.convert(sd, os_)
     g2 = host(os_)
     assert np.all(g2 == 0.0) and np.array_equal(np.signbit(g2), [False, True])
+
+
+@pytest.mark.parametrize("geom,n,kappa", [("cross", 64, 0.0), ("T", 64, -10.0), ("L", 256, 0.0),
+                                          ("cross", 256, -10.0)])
+def test_schur_transform_form_vs_oracle(lib, geom, n, kappa):
+    """a2 with the reduced interface term applied as delta^2 Q diag(g_k) Q by two
+    DST-I per line: equal to the oracle's Schur matvec (exact arm solves) and to
+    the O(n^2) Toeplitz-minus-Hankel sum, for FP64 and FP32 z."""
+    from paper_2509_23180_gb300 import binding as B
+    bs = S.BlockSystem(O.assemble(geom, n, kappa), geom, n)
+    d = B.Domain(B.make_desc(geom, n, kappa, nrhs=3))
+    d.set_option(B.OPT_SCHUR_TRANSFORM, 1)
+    zv = W.random_block_vectors(3, n * n, seed=n + 1)
+    w = torch.zeros((3, n * n), dtype=torch.float64, device="cuda")
+    d.apply_schur(dev(zv), 64, w, 3)
+    got = host(w)
+    want = np.stack([bs.schur_apply(zi) for zi in zv])
+    assert rel(got, want) < 1e-11
+    d.set_option(B.OPT_SCHUR_TRANSFORM, 0)  # the O(n^2) table sum
+    wd = torch.zeros_like(w)
+    d.apply_schur(dev(zv), 64, wd, 3)
+    assert rel(host(wd), want) < 1e-11
+    assert rel(got, host(wd)) < 1e-13
+    d.set_option(B.OPT_SCHUR_TRANSFORM, 1)
+    z32 = torch.as_tensor(zv, dtype=torch.float32, device="cuda")
+    d.apply_schur(z32, 32, w, 3)
+    want32 = np.stack([bs.schur_apply(zi) for zi in zv.astype(np.float32).astype(np.float64)])
+    d.close()
+    assert rel(host(w), want32) < 1e-11

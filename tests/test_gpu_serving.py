@@ -72,3 +72,49 @@ def test_request_over_budget_is_refused(lib):
         s.serve([{"id": 0, "arrival_s": 0.0, "geometry": "cross", "n": 64, "nrhs": 1, "kappa": 0.0, "seed": 1}],
                 realtime=False)
     assert e.value.status == B.FPG_EBUDGET
+
+
+def test_many_domain_creations_with_graphs(lib):
+    """More domain creations than torch's pool of streams (32), under a budget
+    that forces eviction, with graph capture on and 8 concurrent workers: every
+    request converges and matches its result alone (workers own the streams, so
+    a capture never shares its stream with another running domain)."""
+    from paper_2509_23180_gb300 import serve
+    rng = np.random.default_rng(5)
+    geoms = ("L", "T", "cross")
+    reqs = [{"id": i, "arrival_s": 0.0, "geometry": geoms[i % 3], "n": int(rng.choice([8, 12, 16, 20])),
+             "nrhs": int(rng.integers(1, 3)), "kappa": (0.0, -10.0)[(i // 3) % 2], "seed": 300 + i}
+            for i in range(72)]
+    probe = serve.Server(slot_rhs=2, restart=20)
+    need = max(probe.domain_bytes((r["geometry"], r["n"], r["kappa"])) for r in reqs)
+    s = serve.Server(budget_bytes=9 * need, max_inflight=8, slot_rhs=2, restart=20, rtol=1e-11,
+                     precond_precision=64, keep_solutions=True)
+    res = s.serve(reqs, realtime=False)
+    created = s.created
+    s.close()
+    assert created > 24
+    assert all(r.status == 0 for r in res)
+    for req, r in list(zip(reqs, res))[::9]:
+        alone = serve.Server(budget_bytes=4e9, max_inflight=1, slot_rhs=2, restart=20, rtol=1e-11,
+                             precond_precision=64, keep_solutions=True)
+        a = alone.serve([req], realtime=False)[0]
+        alone.close()
+        assert np.array_equal(r.solution.numpy(), a.solution.numpy()), req
+
+
+def test_set_stream_keeps_the_answer(lib):
+    from paper_2509_23180_gb300 import binding as B
+    n = 24
+    f = torch.as_tensor(W.rhs_batch("cross", n, [0, 1], kind="fourier"), device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    d = B.Domain(B.make_desc("cross", n, 0.0, nrhs=2, restart=10, rtol=1e-11), stream=s1)
+    p1 = torch.zeros_like(f)
+    d.set_rhs(f)
+    assert d.solve(p1)[0] == B.FPG_OK
+    d.set_stream(s2)
+    p2 = torch.zeros_like(f)
+    d.set_rhs(f)
+    assert d.solve(p2)[0] == B.FPG_OK
+    d.close()
+    torch.cuda.synchronize()
+    assert torch.equal(p1, p2)
