@@ -45,8 +45,8 @@ struct LineShape {
   static constexpr int CK = (K + 31) / 32;    // unpack terms per lane
   static_assert(N == (rader ? P - 1 : P), "plan shape");
   // shared memory, in bytes, 16-byte aligned pieces
-  static constexpr size_t o_sinp = 0;
-  static constexpr size_t o_tw = align16(o_sinp + sizeof(T) * P);
+  static constexpr size_t o_sinp = 0;  // [2][P]: sin(pi j/p) + 1/2, sin(pi j/p) - 1/2
+  static constexpr size_t o_tw = align16(o_sinp + sizeof(T) * 2 * P);
   static constexpr size_t o_bhat = align16(o_tw + sizeof(C2<T>) * N);
   static constexpr size_t o_pin = align16(o_bhat + (rader ? sizeof(C2<T>) * N : 0));
   static constexpr size_t o_pout = align16(o_pin + (rader ? sizeof(int) * N : 0));
@@ -64,7 +64,8 @@ struct LineShape {
 template <typename T, int P>
 struct LineSmem {
   using S = LineShape<T, P>;
-  T* sinp;
+  T* spl;      // sin(pi j/p) + 1/2
+  T* smi;      // sin(pi j/p) - 1/2
   C2<T>* tw;    // [ka][jb] = w_N^{ka jb}
   C2<T>* bhat;  // Rader kernel spectrum
   int* pin;
@@ -74,7 +75,8 @@ struct LineSmem {
   C2<T>* y;  // [Q][A][YB]
   C2<T>* x;  // [Q][XP]
   __device__ __forceinline__ explicit LineSmem(unsigned char* base) {
-    sinp = reinterpret_cast<T*>(base + S::o_sinp);
+    spl = reinterpret_cast<T*>(base + S::o_sinp);
+    smi = spl + P;
     tw = reinterpret_cast<C2<T>*>(base + S::o_tw);
     bhat = reinterpret_cast<C2<T>*>(base + S::o_bhat);
     pin = reinterpret_cast<int*>(base + S::o_pin);
@@ -91,7 +93,10 @@ __device__ __forceinline__ void load_tables(DstPlan pl, LineSmem<T, P>& s) {
   using S = LineShape<T, P>;
   const C2<T>* W = reinterpret_cast<const C2<T>*>(pl.W);  // w_N^m, m < N
   const T* sp = reinterpret_cast<const T*>(pl.sinp);
-  for (int i = threadIdx.x; i < P; i += S::NT) s.sinp[i] = sp[i];
+  for (int i = threadIdx.x; i < P; i += S::NT) {
+    s.spl[i] = sp[i] + T(0.5);
+    s.smi[i] = sp[i] - T(0.5);
+  }
   for (int i = threadIdx.x; i < S::N; i += S::NT) {
     const int ka = i / S::B, jb = i - ka * S::B;
     s.tw[i] = W[ka * jb];  // ka * jb < N
@@ -107,15 +112,16 @@ __device__ __forceinline__ void load_tables(DstPlan pl, LineSmem<T, P>& s) {
 }
 
 // z_j of line pair q (j in 1..p-1): u_j = sin(pi j/p)(x_j + x_{p-j}) + (x_j - x_{p-j})/2
-// for the two lines, packed as real and imaginary part.
+// = (sin(pi j/p) + 1/2) x_j + (sin(pi j/p) - 1/2) x_{p-j} for the two lines,
+// packed as real and imaginary part (two operations per value instead of four).
 template <typename T, int P>
 __device__ __forceinline__ C2<T> pack(const LineSmem<T, P>& s, int q, int j) {
   constexpr int LP = LineShape<T, P>::LP;
   const T* la = s.lines + (2 * q) * LP;
   const T* lb = la + LP;
   const T a1 = la[j - 1], a2 = la[P - j - 1], b1 = lb[j - 1], b2 = lb[P - j - 1];
-  const T sj = s.sinp[j];
-  return C2<T>{fma(sj, a1 + a2, T(0.5) * (a1 - a2)), fma(sj, b1 + b2, T(0.5) * (b1 - b2))};
+  const T cp = s.spl[j], cm = s.smi[j];
+  return C2<T>{fma(cp, a1, cm * a2), fma(cp, b1, cm * b2)};
 }
 
 // Pass 1 of the two-pass DFT: per (pair q, jb) a DFT of length A over ja of

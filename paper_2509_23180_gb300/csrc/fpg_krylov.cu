@@ -40,28 +40,44 @@ __device__ __forceinline__ double c_line(const Tz* z, int n, int a, int q) {
 // delta^2 Q diag(g_k) Q applied to C's line next to arm a (the exact interface
 // response R_ca A_a^{-1} R_ac restricted to that line).
 template <typename Tz>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
 k_schur_lines(const Tz* __restrict__ z, long long zstride, int n, const double* __restrict__ ctab,
               const int* __restrict__ arms, int narms, double* __restrict__ corr,
               const int* __restrict__ active) {
+  // CTA: 32 outputs i (threadIdx.x) x 8 column groups (threadIdx.y), each
+  // thread one contiguous eighth of the j range (eight short independent FMA
+  // chains instead of one long one); the group partials are summed in group
+  // order.
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* line = reinterpret_cast<double*>(smem_raw);
   double* c = line + n;
+  double* part = c + 2 * n + 2;  // [8][32]
   const int r = blockIdx.y / narms;
   const int a = arms[blockIdx.y % narms];
   if (active != nullptr && !active[r]) return;
   const Tz* zr = z + (long long)r * zstride;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) line[q] = c_line(zr, n, a, q);
-  for (int q = threadIdx.x; q < 2 * n + 2; q += blockDim.x) c[q] = ctab[q];
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int q = tid; q < n; q += 256) line[q] = c_line(zr, n, a, q);
+  for (int q = tid; q < 2 * n + 2; q += 256) c[q] = ctab[q];
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int per = (n + 7) / 8;
+  const int j0 = threadIdx.y * per, j1 = min(n, j0 + per);
   double acc = 0.0;
-  for (int j = 0; j < n; ++j) {
-    const int d = i > j ? i - j : j - i;
-    acc = fma(c[d] - c[i + j + 2], line[j], acc);
+  if (i < n) {
+    for (int j = j0; j < j1; ++j) {
+      const int d = i > j ? i - j : j - i;
+      acc = fma(c[d] - c[i + j + 2], line[j], acc);
+    }
   }
-  corr[((long long)r * 4 + a) * n + i] = acc;
+  part[threadIdx.y * 32 + threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && i < n) {
+    double s = part[threadIdx.x];
+#pragma unroll
+    for (int g = 1; g < 8; ++g) s += part[g * 32 + threadIdx.x];
+    corr[((long long)r * 4 + a) * n + i] = s;
+  }
 }
 
 // a2, stencil part fused with the interface corrections:
@@ -858,8 +874,8 @@ __global__ void k_tighten(const double* __restrict__ gres, double rtol, double f
 cudaError_t launch_schur_reduced(const void* z, int zprec, long long zstride, int n, const double* ctab,
                                  const int* arms_dev, int narms, double* corr, const int* active, int nrhs,
                                  cudaStream_t st) {
-  dim3 grid((n + 127) / 128, nrhs * narms);
-  const size_t smem = sizeof(double) * (3 * n + 2);
+  dim3 grid((n + 31) / 32, nrhs * narms);
+  const size_t smem = sizeof(double) * (3 * n + 2 + 256);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_schur_lines<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -867,11 +883,11 @@ cudaError_t launch_schur_reduced(const void* z, int zprec, long long zstride, in
     attr_set = true;
   }
   if (zprec == 64)
-    k_schur_lines<double><<<grid, 128, smem, st>>>((const double*)z, zstride, n, ctab, arms_dev, narms, corr,
-                                                    active);
+    k_schur_lines<double><<<grid, dim3(32, 8), smem, st>>>((const double*)z, zstride, n, ctab, arms_dev, narms,
+                                                            corr, active);
   else
-    k_schur_lines<float><<<grid, 128, smem, st>>>((const float*)z, zstride, n, ctab, arms_dev, narms, corr,
-                                                   active);
+    k_schur_lines<float><<<grid, dim3(32, 8), smem, st>>>((const float*)z, zstride, n, ctab, arms_dev, narms,
+                                                           corr, active);
   return cudaGetLastError();
 }
 
