@@ -258,7 +258,11 @@ typedef enum {
    * size-specialised DST is compiled (n = 64, 256, 512) -- fewer operations, but
    * only (lines / line batch) CTAs, slower at the batch sizes measured so far.
    * Same operator. */
-  FPG_OPT_SCHUR_TRANSFORM = 8
+  FPG_OPT_SCHUR_TRANSFORM = 8,
+  /* Iterative-refinement steps (0..4, default 1) of every arm solve in the
+   * setup (q_a = A_a^{-1} f_a) and the finish (p_a = A_a^{-1}(f_a - R_ac p_c)):
+   * each step is out += A_a^{-1}(in - A_a out) in FP64. */
+  FPG_OPT_ARM_REFINE = 9
 } fpg_option;
 
 /* Move a domain to another CUDA stream (a cudaStream_t; NULL = the default

@@ -52,8 +52,10 @@ cudaError_t launch_global_apply(const double* p, double* y, const double* f, lon
                                 double* rel_out, double* fnorm_out, double rtol, double* tolabs,
                                 cudaStream_t st);
 cudaError_t launch_fma_probe(int prec, int blocks, int iters, cudaStream_t st);
-cudaError_t launch_tighten(const double* gres, double rtol, double factor, double* tolabs, int* done, int nrhs,
-                           int* resume_count, cudaStream_t st);
+cudaError_t launch_refine_rhs(const double* f, double* r, const double* gres, double rtol, long long ntot, int nrhs,
+                              int* resume_count, int gx, cudaStream_t st);
+cudaError_t launch_add_vec(double* p, const double* q, long long total, cudaStream_t st);
+cudaError_t launch_refine_tol(double* tolabs, const double* fnorm0, double scale, int nrhs, cudaStream_t st);
 cudaError_t launch_precond_simple(const double* v, void* z, int zprec, long long len, int n, double delta,
                                   double kappa, const double* ctab, int armmask, int jacobi, const int* active,
                                   int nrhs, int gx, cudaStream_t st);
@@ -189,8 +191,12 @@ struct fpg_domain {
   double* ctab;
   double* gsc;           // [n] g_k delta^2 / (2 (n+1)), the transform form of the reduced Schur term
   int schur_transform = 0;  // 1: reduced Schur term by two DST-I per line where compiled (else the table sum)
+  int arm_refine = 1;       // FP64 refinement steps of every arm solve (setup and finish)
   int* arms_dev;
   double *f, *tmp, *tmp2, *pbuf, *lit_in, *lit_out, *corr, *gres, *fnorm;
+  double *rbuf, *psave, *fnorm0;  // global refinement: residual RHS, saved iterate, ||f||
+  double* f_orig = nullptr;       // the caller's RHS while a refinement solve runs on rbuf
+  bool refining = false;
   int* resume_dev = nullptr;
   void* scratch;
   KrylovState ks;
@@ -443,6 +449,9 @@ void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostP
   p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->tmp = (double*)p;
   p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->tmp2 = (double*)p;
   p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->pbuf = (double*)p;
+  p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->rbuf = (double*)p;
+  p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->psave = (double*)p;
+  p = c.take(sizeof(double) * nrhs);          if (D) D->fnorm0 = (double*)p;
   if (d->schur_mode == FPG_SCHUR_LITERAL) {
     p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->lit_in = (double*)p;
     p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->lit_out = (double*)p;
@@ -598,10 +607,12 @@ fpg_status arm_solves(fpg_domain* D, const double* in, double* out, int nvec, in
 fpg_status arm_solves_refined(fpg_domain* D, const double* in, double* out, double* work, int nvec, int phase) {
   const Layout& L = D->L;
   FPG_TRY(arm_solves(D, in, out, nvec, phase));
-  FPG_CUDA_TRY(launch_arm_residual(in, out, work, L.ntot, L.n, D->delta, D->desc.kappa, L.ao, nvec, D->gxf, D->st));
-  FPG_TRY(arm_solves(D, work, work, nvec, phase));
-  FPG_CUDA_TRY(launch_arm_add(out, work, L.ntot, L.n, L.ao, nvec, D->gxf, D->st));
-  count(D, phase, 2);
+  for (int it = 0; it < D->arm_refine; ++it) {  // out += A_a^{-1} (in - A_a out)
+    FPG_CUDA_TRY(launch_arm_residual(in, out, work, L.ntot, L.n, D->delta, D->desc.kappa, L.ao, nvec, D->gxf, D->st));
+    FPG_TRY(arm_solves(D, work, work, nvec, phase));
+    FPG_CUDA_TRY(launch_arm_add(out, work, L.ntot, L.n, L.ao, nvec, D->gxf, D->st));
+    count(D, phase, 2);
+  }
   return FPG_OK;
 }
 
@@ -660,14 +671,27 @@ fpg_status check_launch() {
 // for that read), cycle (m Arnoldi steps and the cycle end), finish (Alg. 1
 // steps 5-7 and the acceptance residual).  The only host synchronisation is
 // the poll, once per restart cycle.
+// Setup on D->f into p (Alg. 1 steps 1-3); keep_iters: a refinement solve
+// continues the iteration counts of the solve it corrects.
+fpg_status setup_common(fpg_domain* D, double* p, bool keep_iters);
+
 fpg_status stage_setup(fpg_domain* D, double* p) {
+  D->cycles_run = 0;
+  D->accept_rounds = 0;
+  D->refining = false;
+  D->p_cur = p;
+  FPG_TRY(setup_common(D, p, false));
+  // ||f|| of the caller's right-hand sides, the scale of every later acceptance test
+  FPG_CUDA_TRY(cudaMemcpyAsync(D->fnorm0, D->ks.fnorm, sizeof(double) * D->desc.nrhs, cudaMemcpyDeviceToDevice,
+                               D->st));
+  return FPG_OK;
+}
+
+fpg_status setup_common(fpg_domain* D, double* p, bool keep_iters) {
   const Layout& L = D->L;
   KrylovState& k = D->ks;
   const int nrhs = D->desc.nrhs;
-  D->cycles_run = 0;
-  D->accept_rounds = 0;
   D->first_cycle = true;
-  D->p_cur = p;
   // ||f|| per RHS and the absolute tolerance
   int e = ev_begin(D, 5);
   FPG_CUDA_TRY(launch_global_apply(D->f, nullptr, D->f, L.ntot, L.n, D->delta, D->desc.kappa, L.ao, k.part, kGmax,
@@ -679,7 +703,7 @@ fpg_status stage_setup(fpg_domain* D, double* p) {
   count(D, 5, 1);
   FPG_CUDA_TRY(cudaMemsetAsync(k.u, 0, sizeof(double) * nrhs * L.nc, D->st));
   FPG_CUDA_TRY(cudaMemsetAsync(k.done, 0, sizeof(int) * nrhs, D->st));
-  FPG_CUDA_TRY(cudaMemsetAsync(k.iters, 0, sizeof(int) * nrhs, D->st));
+  if (!keep_iters) FPG_CUDA_TRY(cudaMemsetAsync(k.iters, 0, sizeof(int) * nrhs, D->st));
   FPG_CUDA_TRY(cudaMemsetAsync(k.w, 0, sizeof(double) * nrhs * L.nc, D->st));
   ev_end(D, e);
   return FPG_OK;
@@ -855,30 +879,55 @@ fpg_status stage_finish(fpg_domain* D) {
   count(D, 5, 1);
   FPG_TRY(arm_solves_refined(D, D->tmp, p, D->tmp2, nrhs, 5));
   ev_end(D, e);
-  // a7: global relative residual
+  // a7: global relative residual, always against the caller's f
   e = ev_begin(D, 6);
-  FPG_CUDA_TRY(launch_global_apply(p, nullptr, D->f, L.ntot, L.n, D->delta, D->desc.kappa, L.ao, k.part, kGmax, nrhs,
-                                   D->gxf, D->gres, nullptr, 0.0, nullptr, D->st));
+  if (D->refining) {  // p held the correction: p = saved iterate + correction
+    FPG_CUDA_TRY(launch_add_vec(p, D->psave, (long long)nrhs * L.ntot, D->st));
+    D->f = D->f_orig;
+    D->refining = false;
+    count(D, 6, 1);
+  }
+  const bool check = D->accept_rounds < kAcceptRounds;
+  // with a check to follow, K p goes to rbuf (the next refinement's residual)
+  FPG_CUDA_TRY(launch_global_apply(p, check ? D->rbuf : nullptr, D->f, L.ntot, L.n, D->delta, D->desc.kappa, L.ao,
+                                   k.part, kGmax, nrhs, D->gxf, D->gres, nullptr, 0.0, nullptr, D->st));
   count(D, 6, 2);
-  ev_end(D, e);
-  // acceptance check: right-hand sides above rtol resume with a tighter Schur target
+  // acceptance check: right-hand sides still above rtol get r = f - K p for a
+  // correction solve (global iterative refinement); the others get r = 0
   D->accept_rounds++;
-  if (D->accept_rounds <= kAcceptRounds) {
+  if (check) {
     FPG_CUDA_TRY(cudaMemsetAsync(D->resume_dev, 0, sizeof(int), D->st));
-    FPG_CUDA_TRY(launch_tighten(D->gres, D->desc.rtol, 0.25, k.tolabs, k.done, nrhs, D->resume_dev, D->st));
+    FPG_CUDA_TRY(launch_refine_rhs(D->f, D->rbuf, D->gres, D->desc.rtol, L.ntot, nrhs, D->resume_dev, D->gxf, D->st));
     count(D, 6, 1);
     FPG_CUDA_TRY(cudaMemcpyAsync(D->h_done_pinned + nrhs, D->resume_dev, sizeof(int), cudaMemcpyDeviceToHost, D->st));
   }
+  ev_end(D, e);
   FPG_CUDA_TRY(cudaEventRecord(D->ev_flags, D->st));
   return check_launch();
 }
 
 // After stage_finish: does any right-hand side resume (waits for the check)?
+// A resume is one step of global iterative refinement: the same Alg. 1 run on
+// r = f - K p (setup, FGMRES cycles, finish) gives a correction that the next
+// stage_finish adds to the saved iterate.  Its Krylov target is absolute,
+// 0.45 rtol ||f|| with the caller's f, so the correction needs only a few
+// iterations; it also corrects the setup's f'_c, whose rounding sets a floor
+// that a tighter Schur target alone does not move (seen at n = 1024).
 fpg_status stage_resume(fpg_domain* D, bool* resume) {
   *resume = false;
   if (D->accept_rounds > kAcceptRounds) return FPG_OK;
   FPG_CUDA_TRY(cudaEventSynchronize(D->ev_flags));
   *resume = D->h_done_pinned[D->desc.nrhs] > 0;
+  if (!*resume) return FPG_OK;
+  const int nrhs = D->desc.nrhs;
+  double* p = D->p_cur;
+  FPG_CUDA_TRY(cudaMemcpyAsync(D->psave, p, sizeof(double) * nrhs * D->L.ntot, cudaMemcpyDeviceToDevice, D->st));
+  D->f_orig = D->f;
+  D->f = D->rbuf;
+  D->refining = true;
+  FPG_TRY(setup_common(D, p, true));
+  FPG_CUDA_TRY(launch_refine_tol(D->ks.tolabs, D->fnorm0, 0.5 * kInnerMargin * D->desc.rtol, nrhs, D->st));
+  count(D, 5, 1);
   return FPG_OK;
 }
 
@@ -1371,6 +1420,11 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
     case FPG_OPT_DST_ENGINE:
       if (value < 0 || value > 2) return FPG_EINVAL;
       for (auto* t : {&d->tC64, &d->tC32, &d->tA64, &d->tA32}) t->generic = value;
+      drop_graph(d);
+      return FPG_OK;
+    case FPG_OPT_ARM_REFINE:
+      if (value < 0 || value > 4) return FPG_EINVAL;
+      d->arm_refine = value;
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_SCHUR_TRANSFORM:

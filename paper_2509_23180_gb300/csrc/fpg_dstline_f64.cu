@@ -5,8 +5,8 @@ namespace fpg {
 
 bool dst_lines_supported_f64(int p) { return p == 65 || p == 257 || p == 513; }
 
-// The specialised kernels run one thread per sub-DFT, (lines / 2) * max(A, B)
-// threads per pass.  FP64 needs enough of them to keep the FP64 pipe busy: 10
+// The specialised kernels run one thread (p = 257 in FP64: one quad of four)
+// per sub-DFT, (lines / 2) * A threads per pass.  FP64 needs enough of them to keep the FP64 pipe busy: 10
 // blocks of 256^2 (20480 threads) are already faster than the generic engine
 // (84 / 74 us against 91 / 88 us per forward / inverse launch); a single 64^2
 // block (416 threads) stays on the generic engine.
@@ -14,7 +14,7 @@ bool dst_lines_profitable_f64(int p, int nblk, int ns) {
   int ab = 0;
   switch (p) {
     case 65: ab = dl::LineCfg<double, 65>::A; break;
-    case 257: ab = dl::LineCfg<double, 257>::A; break;
+    case 257: ab = dl::LineCfg<double, 257>::A * (dl::LineQuad<double, 257>::value ? 4 : 1); break;
     case 513: ab = dl::LineCfg<double, 513>::A; break;
     default: return false;
   }

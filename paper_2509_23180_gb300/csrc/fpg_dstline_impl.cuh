@@ -22,13 +22,25 @@ struct LineCfg;
     static constexpr bool rader = RD;              \
   };
 FPG_LINECFG(float, 65, 13, 5, false, 16, 256)
-FPG_LINECFG(float, 257, 16, 16, true, 16, 256)
+FPG_LINECFG(float, 257, 16, 16, true, 12, 192)
 FPG_LINECFG(float, 513, 27, 19, false, 8, 256)
 FPG_LINECFG(float, 1025, 25, 41, false, 4, 192)
 FPG_LINECFG(double, 65, 13, 5, false, 16, 256)
-FPG_LINECFG(double, 257, 16, 16, true, 4, 64)
+FPG_LINECFG(double, 257, 16, 16, true, 4, 256)
 FPG_LINECFG(double, 513, 27, 19, false, 4, 128)
 #undef FPG_LINECFG
+
+// Quad form of the Rader 16 x 16 passes: each sub-DFT of length 16 is spread
+// over the four lanes of a quad (4x more threads), for FP64 batches that would
+// otherwise run a handful of warps per SM.
+template <typename T, int P>
+struct LineQuad {
+  static constexpr bool value = false;
+};
+template <>
+struct LineQuad<double, 257> {
+  static constexpr bool value = true;
+};
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
 
@@ -51,14 +63,19 @@ struct LineShape {
   static constexpr size_t o_pin = align16(o_bhat + (rader ? sizeof(C2<T>) * N : 0));
   static constexpr size_t o_pout = align16(o_pin + (rader ? sizeof(int) * N : 0));
   static constexpr size_t o_dc = align16(o_pout + (rader ? sizeof(int) * N : 0));
-  static constexpr size_t o_lines = align16(o_dc + sizeof(C2<T>) * Q);
-  static constexpr size_t o_y = align16(o_lines + sizeof(T) * 2 * Q * LP);
-  static constexpr size_t o_x = align16(o_y + sizeof(C2<T>) * Q * A * YB);
   // x: the spectra [Q][P] (Stockham), or FFT2's pass-1 output [Q][A][YB] (Rader;
   // the final spectra then go back into y, pitch ZP)
   static constexpr int XP = (rader && A * YB > P) ? A * YB : P;
   static constexpr int ZP = rader ? A * YB : P;  // pitch of the spectra handed to unpack
-  static constexpr size_t bytes = align16(o_x + sizeof(C2<T>) * Q * XP);
+  // The real lines and x share one region: the lines are dead once pass 1 has
+  // packed them, and x is dead once its spectra are unpacked (non-Rader: pair q's
+  // spectrum overlays pair q's two lines exactly, P = LP).  y follows.
+  static constexpr size_t lines_bytes = sizeof(T) * 2 * Q * LP;
+  static constexpr size_t x_bytes = sizeof(C2<T>) * Q * XP;
+  static constexpr size_t o_lines = align16(o_dc + sizeof(C2<T>) * Q);
+  static constexpr size_t o_x = o_lines;
+  static constexpr size_t o_y = align16(o_lines + (lines_bytes > x_bytes ? lines_bytes : x_bytes));
+  static constexpr size_t bytes = align16(o_y + sizeof(C2<T>) * Q * A * YB);
 };
 
 template <typename T, int P>
@@ -161,6 +178,48 @@ __device__ __forceinline__ void pass2(LineSmem<T, P>& s, Out out) {
   }
 }
 
+template <typename T>
+__device__ __forceinline__ C2<T> sel4(int i, C2<T> a0, C2<T> a1, C2<T> a2, C2<T> a3) {
+  const C2<T> lo = (i & 1) ? a1 : a0, hi = (i & 1) ? a3 : a2;
+  return (i & 2) ? hi : lo;
+}
+template <typename T>
+__device__ __forceinline__ C2<T> shfl_xor_c(C2<T> v, int d) {
+  return C2<T>{__shfl_xor_sync(0xffffffffu, v.x, d), __shfl_xor_sync(0xffffffffu, v.y, d)};
+}
+// DFT of length 16 over the four lanes of a quad, s = lane & 3: lane s holds
+// x[s + 4i] in v[i] on entry and X[s + 4k] in v[k] on exit.  With j = s + 4i and
+// k = k1 + 4 k2: each lane takes the DFT of length 4 over i, twiddles by
+// w_16^{s k1}, the quad transposes (lane t gathers Y_s[t] from every lane s with
+// three xor shuffles) and each lane takes the DFT of length 4 over s.
+template <typename T>
+__device__ __forceinline__ void dft16_quad(C2<T> (&v)[4], int s) {
+  dft<4, T>(v);
+  constexpr T c1 = (T)turn_sincos(1, 16, false), s1 = (T)turn_sincos(1, 16, true);
+  constexpr T c2 = (T)turn_sincos(2, 16, false), s2 = (T)turn_sincos(2, 16, true);
+  constexpr T c3 = (T)turn_sincos(3, 16, false), s3 = (T)turn_sincos(3, 16, true);
+  constexpr T c6 = (T)turn_sincos(6, 16, false), s6 = (T)turn_sincos(6, 16, true);
+  constexpr T c9 = (T)turn_sincos(9, 16, false), s9 = (T)turn_sincos(9, 16, true);
+  const C2<T> one{T(1), T(0)};
+  // w_16^{s k1} = (cos, -sin)(2 pi s k1 / 16)
+  const C2<T> w1 = sel4(s, one, C2<T>{c1, -s1}, C2<T>{c2, -s2}, C2<T>{c3, -s3});
+  const C2<T> w2 = sel4(s, one, C2<T>{c2, -s2}, C2<T>{T(0), T(-1)}, C2<T>{c6, -s6});
+  const C2<T> w3 = sel4(s, one, C2<T>{c3, -s3}, C2<T>{c6, -s6}, C2<T>{c9, -s9});
+  v[1] = c_mul(v[1], w1);
+  v[2] = c_mul(v[2], w2);
+  v[3] = c_mul(v[3], w3);
+  const C2<T> r0 = sel4(s, v[0], v[1], v[2], v[3]);
+  const C2<T> r1 = shfl_xor_c(sel4(s ^ 1, v[0], v[1], v[2], v[3]), 1);
+  const C2<T> r2 = shfl_xor_c(sel4(s ^ 2, v[0], v[1], v[2], v[3]), 2);
+  const C2<T> r3 = shfl_xor_c(sel4(s ^ 3, v[0], v[1], v[2], v[3]), 3);
+  // u[p] = Y_p[s] came from lane p = s ^ d as r_d
+  v[0] = sel4(s, r0, r1, r2, r3);
+  v[1] = sel4(s ^ 1, r0, r1, r2, r3);
+  v[2] = sel4(s ^ 2, r0, r1, r2, r3);
+  v[3] = sel4(s ^ 3, r0, r1, r2, r3);
+  dft<4, T>(v);
+}
+
 // DFT of length p of every packed line pair; returns the spectra, pair q at
 // [q * ZP + k].
 template <typename T, int P>
@@ -181,6 +240,59 @@ __device__ __forceinline__ const C2<T>* dft_p(LineSmem<T, P>& s) {
     // second DFT's first pass for jb = ka, so the two meet in registers.
     constexpr int A = S::A, B = S::B, N = S::N, YB = S::YB;
     static_assert(A == B && N == P - 1, "Rader length A * A");
+    if constexpr (LineQuad<T, P>::value) {
+      static_assert(A == 16 && S::NT == S::Q * 16 * 4, "quad form: one quad per (pair, index)");
+      const int sq = threadIdx.x & 3, qt = threadIdx.x >> 2;
+      const int q = qt / A, g = qt - q * A;  // pass task: jb (first pass) or ka (others)
+      C2<T> v[4];
+      // first DFT, pass 1 (jb = g): inputs ja = sq + 4i, outputs ka = sq + 4k
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] = pack<T, P>(s, q, s.pin[B * (sq + 4 * i) + g]);
+      dft16_quad<T>(v, sq);
+      {
+        C2<T>* yq = s.y + q * (A * YB) + g;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int ka = sq + 4 * k;
+          yq[ka * YB] = c_mul(v[k], s.tw[ka * B + g]);
+        }
+      }
+      __syncthreads();
+      // first DFT pass 2 (ka = g), product with B^, second DFT pass 1 (jb' = g)
+      {
+        const C2<T>* yq = s.y + q * (A * YB) + g * YB;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = yq[sq + 4 * i];
+        dft16_quad<T>(v, sq);  // outputs k = g + A kb, kb = sq + 4k
+        if (g == 0 && sq == 0) s.dc[q] = v[0];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const C2<T> m = c_mul(v[k], s.bhat[g + A * (sq + 4 * k)]);
+          v[k] = C2<T>{m.x, -m.y};
+        }
+        dft16_quad<T>(v, sq);  // inputs ja' = kb, outputs ka' = sq + 4k
+        C2<T>* xq = s.x + q * (A * YB) + g;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int ka = sq + 4 * k;
+          xq[ka * YB] = c_mul(v[k], s.tw[ka * B + g]);
+        }
+      }
+      __syncthreads();
+      // second DFT, pass 2 (ka = g); scatter X_{g^{-a}} = conj(C_a)
+      {
+        const C2<T>* xq = s.x + q * (A * YB) + g * YB;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = xq[sq + 4 * i];
+        dft16_quad<T>(v, sq);
+        C2<T>* zq = s.y + q * S::ZP;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) zq[s.pout[g + A * (sq + 4 * k)]] = C2<T>{v[k].x, -v[k].y};
+      }
+      for (int qq = threadIdx.x; qq < S::Q; qq += S::NT) s.y[qq * S::ZP] = s.dc[qq];
+      __syncthreads();
+      return s.y;
+    }
     pass1<T, P>(s, [&](int q, int b) { return pack<T, P>(s, q, s.pin[b]); });
     __syncthreads();
     for (int t = threadIdx.x; t < S::Q * A; t += S::NT) {
@@ -276,6 +388,7 @@ __device__ __forceinline__ void unpack(LineSmem<T, P>& s, const C2<T>* spectra) 
     }
     T acca = __shfl_up_sync(0xffffffffu, ia, 1), accb = __shfl_up_sync(0xffffffffu, ib, 1);
     if (lane == 0) acca = accb = T(0);
+    __syncwarp();  // the spectrum may share storage with the lines written below
     static_for<CK>([&](auto ii) {
       constexpr int i = decltype(ii)::value;
       const int k = k0 + i;

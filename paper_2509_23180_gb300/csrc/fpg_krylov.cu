@@ -520,20 +520,36 @@ __global__ void k_givens(double* __restrict__ H, int hcol_stride, int hrhs_strid
 }
 
 // a5: y = R^{-1} g over the kcyc[r] steps of this cycle (one thread per RHS).
-__global__ void k_backsolve(const double* __restrict__ H, int hcol_stride, int hrhs_stride,
-                            const double* __restrict__ g, double* __restrict__ y, int m, int nrhs,
-                            const int* __restrict__ kcyc) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32)
+k_backsolve(const double* __restrict__ H, int hcol_stride, int hrhs_stride, const double* __restrict__ g,
+            double* __restrict__ y, int m, int nrhs, const int* __restrict__ kcyc, int h_in_smem) {
+  // One warp per right-hand side.  The triangle is staged in shared memory
+  // (one coalesced copy) when it fits; each row's dot product is spread over
+  // the lanes and reduced in a fixed butterfly, so the chain of k dependent
+  // steps costs one reduction each instead of k sequential loads.
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* ys = reinterpret_cast<double*>(smem_raw);  // [m]
+  double* hs = ys + m;                                  // [hrhs_stride] when staged
+  const int r = blockIdx.x, lane = threadIdx.x;
   if (r >= nrhs) return;
   const int k = kcyc[r];
-  const double* h = H + (long long)r * hrhs_stride;
-  const double* gr = g + (long long)r * (m + 1);
-  double* yr = y + (long long)r * m;
-  for (int i = k - 1; i >= 0; --i) {
-    double s = gr[i];
-    for (int l = i + 1; l < k; ++l) s -= h[(long long)l * hcol_stride + i] * yr[l];
-    yr[i] = s / h[(long long)i * hcol_stride + i];
+  const double* hg = H + (long long)r * hrhs_stride;
+  const double* h = hg;
+  if (h_in_smem) {
+    for (int i = lane; i < hrhs_stride; i += 32) hs[i] = hg[i];
+    h = hs;
   }
+  const double* gr = g + (long long)r * (m + 1);
+  __syncwarp();
+  for (int i = k - 1; i >= 0; --i) {
+    double s = 0.0;
+    for (int l = i + 1 + lane; l < k; l += 32) s = fma(h[(long long)l * hcol_stride + i], ys[l], s);
+    s = warp_sum(s);
+    if (lane == 0) ys[i] = (gr[i] - s) / h[(long long)i * hcol_stride + i];
+    __syncwarp();
+  }
+  double* yr = y + (long long)r * m;
+  for (int i = lane; i < k; i += 32) yr[i] = ys[i];
 }
 
 // a5: u += Z y (k = kcyc[r] columns).
@@ -858,15 +874,32 @@ k_precond_simple(const double* __restrict__ v, To* __restrict__ z, long long len
 // Acceptance check (P8 reading): a right-hand side whose global residual is above
 // rtol after back substitution goes back into the iteration with its Schur
 // tolerance scaled by `factor`; its iterate u is kept.  Flags how many resume.
-__global__ void k_tighten(const double* __restrict__ gres, double rtol, double factor, double* __restrict__ tolabs,
-                          int* __restrict__ done, int nrhs, int* __restrict__ resume_count) {
+
+// Global iterative refinement (acceptance, a7): r = f - K p for the right-hand
+// sides whose global relative residual is above rtol, 0 for the others (those
+// then converge at once and their correction is exactly zero).  On entry r
+// holds K p.
+__global__ void __launch_bounds__(kThreads)
+k_refine_rhs(const double* __restrict__ f, double* __restrict__ r, const double* __restrict__ gres, double rtol,
+             long long ntot, int* __restrict__ resume_count) {
+  const int rr = blockIdx.y;
+  const bool refine = gres[rr] > rtol;
+  if (refine && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(resume_count, 1);
+  const double* fr = f + (long long)rr * ntot;
+  double* xr = r + (long long)rr * ntot;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ntot; i += (long long)gridDim.x * blockDim.x)
+    xr[i] = refine ? fr[i] - xr[i] : 0.0;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_add_vec(double* __restrict__ p, const double* __restrict__ q, long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+    p[i] += q[i];
+}
+
+__global__ void k_refine_tol(double* __restrict__ tolabs, const double* __restrict__ fnorm0, double scale, int nrhs) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrhs) return;
-  if (gres[r] > rtol) {
-    tolabs[r] *= factor;
-    done[r] = 0;
-    atomicAdd(resume_count, 1);
-  }
+  if (r < nrhs) tolabs[r] = scale * fnorm0[r];
 }
 
 // ---------------------------------------------------------------------------
@@ -904,11 +937,23 @@ cudaError_t launch_precond_simple(const double* v, void* z, int zprec, long long
   return cudaGetLastError();
 }
 
-cudaError_t launch_tighten(const double* gres, double rtol, double factor, double* tolabs, int* done, int nrhs,
-                           int* resume_count, cudaStream_t st) {
-  k_tighten<<<(nrhs + 127) / 128, 128, 0, st>>>(gres, rtol, factor, tolabs, done, nrhs, resume_count);
+cudaError_t launch_refine_rhs(const double* f, double* r, const double* gres, double rtol, long long ntot, int nrhs,
+                              int* resume_count, int gx, cudaStream_t st) {
+  k_refine_rhs<<<dim3(gx, nrhs), kThreads, 0, st>>>(f, r, gres, rtol, ntot, resume_count);
   return cudaGetLastError();
 }
+
+cudaError_t launch_add_vec(double* p, const double* q, long long total, cudaStream_t st) {
+  const long long blocks = (total + kThreads - 1) / kThreads;
+  k_add_vec<<<(int)(blocks < 152 * 16 ? blocks : 152 * 16), kThreads, 0, st>>>(p, q, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_tol(double* tolabs, const double* fnorm0, double scale, int nrhs, cudaStream_t st) {
+  k_refine_tol<<<(nrhs + 127) / 128, 128, 0, st>>>(tolabs, fnorm0, scale, nrhs);
+  return cudaGetLastError();
+}
+
 
 cudaError_t launch_stencil_c(const void* z, int zprec, long long zstride, double* w, long long wstride, int n,
                              double delta, double kappa, const double* corr, int armmask, const int* active,
@@ -1086,7 +1131,10 @@ cudaError_t launch_givens(double* H, int hcol_stride, int hrhs_stride, double* c
 cudaError_t launch_cycle_end(const double* H, int hcol_stride, int hrhs_stride, const double* g, double* y,
                              int m, int nrhs, const int* kcyc, double* u, const void* Z, int zprec,
                              long long zvstride, long long len, int gx, cudaStream_t st) {
-  k_backsolve<<<(nrhs + 63) / 64, 64, 0, st>>>(H, hcol_stride, hrhs_stride, g, y, m, nrhs, kcyc);
+  const size_t hbytes = sizeof(double) * (size_t)hrhs_stride;
+  const int staged = sizeof(double) * (size_t)m + hbytes <= 48 * 1024 ? 1 : 0;
+  k_backsolve<<<nrhs, 32, sizeof(double) * (size_t)m + (staged ? hbytes : 0), st>>>(H, hcol_stride, hrhs_stride, g,
+                                                                                   y, m, nrhs, kcyc, staged);
   dim3 grid(gx, nrhs);
   if (zprec == 64)
     k_update_u<double><<<grid, kThreads, 0, st>>>(u, (const double*)Z, zvstride, len, y, m, kcyc);
