@@ -262,7 +262,12 @@ typedef enum {
   /* Iterative-refinement steps (0..4, default 1) of every arm solve in the
    * setup (q_a = A_a^{-1} f_a) and the finish (p_a = A_a^{-1}(f_a - R_ac p_c)):
    * each step is out += A_a^{-1}(in - A_a out) in FP64. */
-  FPG_OPT_ARM_REFINE = 9
+  FPG_OPT_ARM_REFINE = 9,
+  /* 1: the FP32 forward DST of the size-specialised path runs as a persistent
+   * kernel that fetches the next line tile with a bulk asynchronous copy
+   * (cp.async.bulk on an mbarrier) while it transforms the current one (blocks
+   * with contiguous, 16-byte aligned rows); 0 (default): one CTA per tile. */
+  FPG_OPT_DST_BULK = 10
 } fpg_option;
 
 /* Move a domain to another CUDA stream (a cudaStream_t; NULL = the default

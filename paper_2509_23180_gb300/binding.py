@@ -28,6 +28,7 @@ OPT_ARNOLDI_THREADS = 6
 OPT_DST_ENGINE = 7
 OPT_SCHUR_TRANSFORM = 8
 OPT_ARM_REFINE = 9
+OPT_DST_BULK = 10
 PRECOND = {"fft": 0, "none": 1, "jacobi": 2}
 PHASES = ("precond", "schur", "arnoldi", "givens", "cycle_end", "setup_finish", "residual",
           "dst_forward", "thomas", "dst_inverse", "fast_solve_fused")

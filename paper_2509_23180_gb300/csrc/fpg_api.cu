@@ -1422,6 +1422,11 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
       for (auto* t : {&d->tC64, &d->tC32, &d->tA64, &d->tA32}) t->generic = value;
       drop_graph(d);
       return FPG_OK;
+    case FPG_OPT_DST_BULK:
+      if (value < 0 || value > 1) return FPG_EINVAL;
+      for (auto* tt : {&d->tC64, &d->tC32, &d->tA64, &d->tA32}) tt->bulk = value;
+      drop_graph(d);
+      return FPG_OK;
     case FPG_OPT_ARM_REFINE:
       if (value < 0 || value > 4) return FPG_EINVAL;
       d->arm_refine = value;

@@ -459,6 +459,114 @@ k_dst_lines_fwd(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPl
   }
 }
 
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (cp.async.bulk, completion counted on an mbarrier).
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* mbar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One arrival that also announces `bytes` of asynchronous transfer, then the copy
+// of `bytes` (a multiple of 16, both addresses 16-byte aligned) from global memory.
+__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, unsigned bytes, unsigned long long* mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(sdst)),
+               "l"(gsrc), "r"(bytes), "r"(smem_addr(mbar))
+               : "memory");
+}
+
+// Wait for phase `parity` of the barrier; false after `limit` unsuccessful tries.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* mbar, unsigned parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+template <typename T, int P>
+struct BulkShape {
+  using S = LineShape<T, P>;
+  static constexpr size_t o_stage = align16(S::bytes);
+  static constexpr size_t o_mbar = align16(o_stage + sizeof(double) * 2 * S::Q * S::n);
+  static constexpr size_t bytes = o_mbar + 16;
+};
+
+// Persistent form of the forward DST for blocks whose lines are contiguous rows
+// (st == 1, ss == n, 16-byte aligned): each CTA walks the tiles (2Q lines of one
+// block) blockIdx.x, blockIdx.x + gridDim.x, ...; thread 0 fetches the next
+// tile's FP64 rows with one bulk copy into a staging buffer as soon as the
+// current tile has been converted out of it, so the load overlaps the current
+// tile's transform.  A wait that runs out sets *err and ends the CTA.
+template <typename T, int P>
+__global__ void __launch_bounds__(LineShape<T, P>::NT)
+k_dst_lines_fwd_bulk(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPlan pl, T* __restrict__ scratch,
+                     const int* __restrict__ active, int nper_active, int nblk, int* __restrict__ err) {
+  using S = LineShape<T, P>;
+  using BS = BulkShape<T, P>;
+  constexpr int n = S::n, Q = S::Q, NT = S::NT, LP = S::LP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LineSmem<T, P> s(smem_raw);
+  double* stage = reinterpret_cast<double*>(smem_raw + BS::o_stage);
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem_raw + BS::o_mbar);
+  const int tpb = (L.ns + 2 * Q - 1) / (2 * Q);
+  const int total = nblk * tpb;
+  auto live = [&](int tile) { return active == nullptr || active[(tile / tpb) / nper_active]; };
+  auto next_of = [&](int tile) {
+    do tile += gridDim.x;
+    while (tile < total && !live(tile));
+    return tile;
+  };
+  auto issue = [&](int tile) {
+    const int b = tile / tpb, s0 = (tile - b * tpb) * 2 * Q;
+    const int nl = min(2 * Q, L.ns - s0);
+    bulk_load(stage, in + boff(ib, b) + (long long)s0 * n, (unsigned)(nl * n * sizeof(double)), mbar);
+  };
+  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  load_tables<T, P>(pl, s);
+  __syncthreads();
+  int tile = blockIdx.x;
+  if (tile < total && !live(tile)) tile = next_of(tile);
+  if (threadIdx.x == 0 && tile < total) issue(tile);
+  unsigned parity = 0;
+  while (tile < total) {
+    const int b = tile / tpb, s0 = (tile - b * tpb) * 2 * Q;
+    const int nl = min(2 * Q, L.ns - s0);
+    if (!mbar_wait(mbar, parity, 1 << 22)) {
+      if (threadIdx.x == 0) atomicExch(err, 1);
+      mbar_wait(mbar, parity, 1 << 20);  // give the copy in flight a last chance to land
+      return;
+    }
+    parity ^= 1u;
+    for (int i = threadIdx.x; i < 2 * Q * n; i += NT) {
+      const int l = i / n, tt = i - l * n;
+      s.lines[l * LP + tt] = l < nl ? convert<T>(stage[i]) : T(0);
+    }
+    __syncthreads();  // the staging buffer is free
+    const int next = next_of(tile);
+    if (threadIdx.x == 0 && next < total) issue(next);
+    unpack<T, P>(s, dft_p<T, P>(s));
+    __syncthreads();
+    T* dst = scratch + (long long)b * n * L.ns + s0;
+    for (int i = threadIdx.x; i < nl * n; i += NT) {
+      const int k = i / nl, l = i - k * nl;
+      dst[(long long)k * L.ns + l] = s.lines[l * LP + k];
+    }
+    __syncthreads();  // lines are rewritten by the next tile's conversion
+    tile = next;
+  }
+}
+
 // Inverse: scratch[b][k][s] -> DST -> out block (To), times `scale`.
 template <typename T, typename To, int P>
 __global__ void __launch_bounds__(LineShape<T, P>::NT)
@@ -516,6 +624,27 @@ cudaError_t fwd_one(const double* in, BatchDesc ib, LineLayout L, const DstPlan&
   }
   dim3 grid((L.ns + 2 * S::Q - 1) / (2 * S::Q), nblk);
   k_dst_lines_fwd<T, P><<<grid, S::NT, S::bytes, st>>>(in, ib, L, pl, scratch, active, nper_active, vec);
+  return cudaGetLastError();
+}
+
+template <typename T, int P>
+cudaError_t fwd_bulk_one(const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl, T* scratch, int nblk,
+                         const int* active, int nper_active, int* err, cudaStream_t st) {
+  using S = LineShape<T, P>;
+  using BS = BulkShape<T, P>;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaFuncSetAttribute(k_dst_lines_fwd_bulk<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BS::bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dst_lines_fwd_bulk<T, P>, S::NT, BS::bytes);
+    if (per_sm < 1) per_sm = 1;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tpb = (L.ns + 2 * S::Q - 1) / (2 * S::Q);
+  const long long total = (long long)nblk * tpb;
+  const int grid = (int)(total < (long long)per_sm * sms ? total : (long long)per_sm * sms);
+  k_dst_lines_fwd_bulk<T, P><<<grid, S::NT, BS::bytes, st>>>(in, ib, L, pl, scratch, active, nper_active, nblk, err);
   return cudaGetLastError();
 }
 

@@ -420,6 +420,8 @@ bool dst_lines_supported_f64(int p);
 bool dst_lines_profitable_f64(int p, int nblk, int ns);
 cudaError_t dst_lines_fwd_f32(int p, const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl, float* scratch,
                               int nblk, const int* active, int nper_active, int vec, cudaStream_t st);
+cudaError_t dst_lines_fwd_bulk_f32(int p, const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl,
+                                   float* scratch, int nblk, const int* active, int nper_active, cudaStream_t st);
 cudaError_t dst_lines_inv_f32(int p, const float* scratch, void* out, int out_prec, BatchDesc ob, LineLayout L,
                               const DstPlan& pl, int nblk, const int* active, int nper_active, int vec,
                               cudaStream_t st);
@@ -453,8 +455,13 @@ bool lines_engine(int p, int nblk, int ns, int engine) {
 
 template <typename T, typename To>
 cudaError_t lines_fwd(const DstPlan& pl, const double* in, BatchDesc ib, LineLayout L, T* scratch, int nblk,
-                      const int* active, int nper_active, cudaStream_t st) {
+                      const int* active, int nper_active, cudaStream_t st, int bulk) {
   const int vec = pairs_aligned(in, 8, ib, L) ? 1 : 0;
+  if constexpr (sizeof(T) == 4) {
+    // persistent form with bulk copies: contiguous rows, 16-byte aligned blocks
+    if (bulk && vec && L.ss == L.nt) return dst_lines_fwd_bulk_f32(pl.p, in, ib, L, pl, scratch, nblk, active,
+                                                                   nper_active, st);
+  }
   if constexpr (sizeof(T) == 8)
     return dst_lines_fwd_f64(pl.p, in, ib, L, pl, scratch, nblk, active, nper_active, vec, st);
   else
@@ -498,7 +505,7 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
   if (tb.q == 0 && lines_engine<T>(pl.p, nblk, L.ns, tb.generic)) {
     // size-specialised kernels: forward DST, Thomas, inverse DST
     if (ev) record_event(ev[0], st);
-    cudaError_t e = lines_fwd<T, To>(pl, in, ib, L, scratch, nblk, active, nper_active, st);
+    cudaError_t e = lines_fwd<T, To>(pl, in, ib, L, scratch, nblk, active, nper_active, st, tb.bulk);
     if (e != cudaSuccess) return e;
     if (ev) record_event(ev[1], st);
     if (ev) record_event(ev[2], st);

@@ -40,6 +40,7 @@ struct FastSolveTables {
   int mt = 0;         // warps (= modes) per CTA in the Thomas kernel (0: 8)
   int fused = 0;      // 1: one-pass cluster kernel when the block fits
   int generic = 0;    // DST engine: 0 auto, 1 generic FFT engine, 2 size-specialised where compiled
+  int bulk = 0;       // 1: FP32 forward DST as the persistent kernel with bulk asynchronous row copies
 };
 
 // Offsets of the arm blocks W, E, S, N inside one full vector (-1 = absent).

@@ -222,3 +222,31 @@ def test_schur_transform_form_vs_oracle(lib, geom, n, kappa):
     want32 = np.stack([bs.schur_apply(zi) for zi in zv.astype(np.float32).astype(np.float64)])
     d.close()
     assert rel(host(w), want32) < 1e-11
+
+
+@pytest.mark.parametrize("n", [64, 256, 512, 1024])
+def test_bulk_copy_forward_dst_is_bit_identical(lib, n):
+    """The persistent forward DST with bulk asynchronous row copies computes
+    exactly what the one-CTA-per-tile kernel does (FP32 preconditioner, and a
+    whole FP32-preconditioned solve with right-hand sides dropping out)."""
+    from paper_2509_23180_gb300 import binding as B
+    d = B.Domain(B.make_desc("cross", n, -10.0, nrhs=3, restart=20, rtol=1e-10, precond_precision=32))
+    v = dev(W.random_block_vectors(3, n * n, seed=n + 5))
+    outs = []
+    for bulk in (0, 1):
+        d.set_option(B.OPT_DST_BULK, bulk)
+        z = torch.zeros((3, n * n), dtype=torch.float32, device="cuda")
+        d.apply_precond(v, z, 3)
+        outs.append(host(z))
+    assert np.array_equal(outs[0], outs[1])
+    if n <= 256:
+        f = dev(W.rhs_batch("cross", n, [1, 2, 3], kind="fourier"))
+        sols = []
+        for bulk in (0, 1):
+            d.set_option(B.OPT_DST_BULK, bulk)
+            d.set_rhs(f)
+            p = torch.zeros_like(f)
+            assert d.solve(p)[0] == B.FPG_OK
+            sols.append(host(p))
+        assert np.array_equal(sols[0], sols[1])
+    d.close()
