@@ -480,18 +480,34 @@ def roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, nrhs, fs_path=0):
     return out
 
 
-def traffic_for(kernel, args):
-    """DRAM bytes per launch from the committed ncu summary, when it was taken on
-    this workload and the kernel sources have not changed since."""
+# Source files that define each kernel whose DRAM traffic may be quoted from the
+# committed ncu capture (profiles/traffic.txt); a line is used only while the
+# hash of these files still matches the one recorded with the capture.
+TRAFFIC_SOURCES = {
+    "k_arnoldi_cluster_reg": ["fpg_krylov.cu"],
+    "k_dst_lines_fwd": ["fpg_dstline.cuh", "fpg_dstline_impl.cuh"],
+    "k_dst_lines_inv": ["fpg_dstline.cuh", "fpg_dstline_impl.cuh"],
+    "k_thomas_reg": ["fpg_fastsolve.cu"],
+    "k_fft_forward": ["fpg_fft_kernels.cuh", "fpg_dst.cuh"],
+    "k_fft_inverse": ["fpg_fft_kernels.cuh", "fpg_dst.cuh"],
+}
+
+
+def source_hash(kernel):
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
-    srcs = ["paper_2509_23180_gb300/csrc/fpg_fastsolve.cu", "paper_2509_23180_gb300/csrc/fpg_dst.cuh",
-            "paper_2509_23180_gb300/csrc/fpg_krylov.cu", "paper_2509_23180_gb300/csrc/fpg_dstline.cuh",
-            "paper_2509_23180_gb300/csrc/fpg_dstline_impl.cuh"]
     h = hashlib.sha1()
-    for s in srcs:
-        h.update(open(os.path.join(ROOT, s), "rb").read())
-    sha = h.hexdigest()[:12]
+    for s in TRAFFIC_SOURCES.get(kernel, []):
+        h.update(open(os.path.join(ROOT, "paper_2509_23180_gb300", "csrc", s), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def traffic_for(kernel, args):
+    """DRAM bytes per launch (read + write) from the committed ncu summary, when it
+    was taken on this workload and the kernel's sources have not changed since."""
+    if kernel not in TRAFFIC_SOURCES:
+        return None
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    sha = source_hash(kernel)
     try:
         for line in open(path):
             if line.startswith("#") or not line.strip():

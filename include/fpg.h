@@ -313,6 +313,24 @@ fpg_status fpg_phase_stats(fpg_domain* d, int32_t phase, int64_t* launches, doub
 /* Total kernel launches issued by the library on this domain so far. */
 fpg_status fpg_launch_count(fpg_domain* d, int64_t* launches);
 
+/* ---- Neumann rectangles (Sec. 2.2, Eq. "submat_Neumann") --------------------
+ * z = A_N^{-1} v for nvec rectangles of n_t x n_s points (row-major, t fastest,
+ * FP64, device pointers): zero normal derivative on the two edges across t
+ * (the first and last rows of the t-line operator lose one delta: a ghost node
+ * equal to its neighbour, cell-centred points), homogeneous Dirichlet on the
+ * edges across s, spacing h both ways (delta = 1/h^2), kappa <= 0 on the
+ * diagonal.  Computed as a DCT-II along t (the eigenbasis cos(k pi (j-1/2)/n_t),
+ * eigenvalues -4 delta sin^2(k pi/(2 n_t))), one Thomas solve per mode along s
+ * and the inverse DCT.  n_t even, prime factors of n_t at most 13,
+ * 2 <= n_t, n_s <= 4096.  The caller owns `workspace` (device, >=
+ * fpg_neumann_workspace_bytes); the tables are rebuilt on the host and copied
+ * in on every call.  Runs on `stream` (a cudaStream_t, NULL = default).
+ * Errors: FPG_EINVAL (arguments), FPG_ENOMEM (workspace too small),
+ * FPG_EUNSUPPORTED (n_t has a larger prime factor), FPG_ECUDA. */
+fpg_status fpg_neumann_workspace_bytes(int32_t nt, int32_t ns, int32_t nvec, size_t* bytes);
+fpg_status fpg_neumann_solve(int32_t nt, int32_t ns, double h, double kappa, const double* v, double* z,
+                             int32_t nvec, void* workspace, size_t bytes, void* stream);
+
 /* Element-wise conversion between FP64 and FP32 on the device, done with the
  * integer-pipe routines of the mixed-precision path (GB300 runs the hardware
  * conversion on its FP64 pipe).  (in_prec, out_prec) is (64, 32): round to

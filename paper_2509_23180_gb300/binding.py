@@ -18,7 +18,7 @@ SCHUR = {"reduced": 0, "literal": 1}
 STATUS = {0: "FPG_OK", 1: "FPG_EINVAL", 2: "FPG_ENOMEM", 3: "FPG_ECUDA", 4: "FPG_ENOCONV",
           5: "FPG_ETIMEOUT", 6: "FPG_EUNSUPPORTED", 7: "FPG_EBUDGET"}
 FPG_OK, FPG_EINVAL, FPG_ENOMEM, FPG_ECUDA, FPG_ENOCONV = 0, 1, 2, 3, 4
-FPG_EBUDGET = 7
+FPG_ETIMEOUT, FPG_EUNSUPPORTED, FPG_EBUDGET = 5, 6, 7
 OPT_ARNOLDI_CLUSTER = 1
 OPT_CUDA_GRAPHS = 2
 OPT_PRECOND = 3
@@ -99,6 +99,8 @@ _SIGS = {
     "fpg_launch_count": ([_P, ctypes.POINTER(_I64)], _I32),
     "fpg_fast_solve_path": ([_P, ctypes.POINTER(_I32)], _I32),
     "fpg_convert": ([_P, _I32, _P, _I32, _I64, _P], _I32),
+    "fpg_neumann_workspace_bytes": ([_I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)], _I32),
+    "fpg_neumann_solve": ([_I32, _I32, _D, _D, _P, _P, _I32, _P, ctypes.c_size_t, _P], _I32),
     "fpg_probe_fma_peak": ([_I32, ctypes.POINTER(_D)], _I32),
     "fpg_fast_solve_noalloc": ([_I32, _D, _P, _P, _I32, _P], _I32),
 }
@@ -297,6 +299,21 @@ def convert(src, dst, stream=None):
     st = stream if stream is not None else torch.cuda.current_stream(src.device)
     _check(lib.fpg_convert(_ptr(src), prec[src.dtype], _ptr(dst), prec[dst.dtype], src.numel(), st.cuda_stream),
            "fpg_convert")
+
+
+def neumann_solve(v, z, nt: int, ns: int, h: float, kappa: float, stream=None):
+    """fpg_neumann_solve on nvec = v.shape[0] Neumann rectangles (CUDA float64
+    tensors of shape (nvec, nt * ns)); the workspace is a torch uint8 tensor."""
+    import torch
+    lib = load()
+    nvec = v.shape[0]
+    nb = ctypes.c_size_t()
+    _check(lib.fpg_neumann_workspace_bytes(nt, ns, nvec, ctypes.byref(nb)), "fpg_neumann_workspace_bytes")
+    ws = torch.empty(nb.value, dtype=torch.uint8, device=v.device)
+    st = stream if stream is not None else torch.cuda.current_stream(v.device)
+    _check(lib.fpg_neumann_solve(nt, ns, h, kappa, _ptr(v), _ptr(z), nvec, _ptr(ws), nb.value, st.cuda_stream),
+           "fpg_neumann_solve")
+    return ws
 
 
 def solve_many(domains, ps):

@@ -554,6 +554,17 @@ cudaError_t launch_fast_solve_fused(int prec, int out_prec, const FastSolveTable
                                     const double* in, BatchDesc ib, void* out, BatchDesc ob, int nblk,
                                     const int* active, int nper_active, cudaStream_t st);
 
+// The Thomas kernels for other line transforms (the Neumann rectangles): scratch
+// [nblk][n][ns] in place, pivot tables [n][ns].
+cudaError_t launch_thomas_any(int prec, void* scratch, int n, int ns, const void* rpiv, const void* mneg, int nblk,
+                              cudaStream_t st) {
+  if (prec == 64)
+    return launch_thomas<double>((double*)scratch, n, ns, (const double*)rpiv, (const double*)mneg, nblk, nullptr, 1,
+                                 st, 0);
+  return launch_thomas<float>((float*)scratch, n, ns, (const float*)rpiv, (const float*)mneg, nblk, nullptr, 1, st,
+                              0);
+}
+
 // Which kernels the fast solve of this block kind runs: 0 generic FFT engine
 // (k_fft_forward / k_thomas_reg / k_fft_inverse), 1 size-specialised
 // (k_dst_lines_fwd / k_thomas_reg / k_dst_lines_inv), 2 dense DST, 3 the fused
