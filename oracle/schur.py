@@ -28,11 +28,13 @@ from .krylov import gmres
 class BlockSystem:
     """The block pieces of K for one domain."""
 
-    def __init__(self, K: sp.spmatrix, domain: str, n: int):
+    def __init__(self, K: sp.spmatrix, domain: str, n: int, blocks=None):
+        """blocks: (name, I0, J0, nx, ny, offset, size) per block in I/O order;
+        default: the vertex-centred layout of `domain`."""
         self.K = sp.csr_matrix(K)
         self.domain = domain
         self.n = n
-        self.blocks = block_ranges(domain, n)
+        self.blocks = blocks if blocks is not None else block_ranges(domain, n)
         self.names = [b[0] for b in self.blocks]
         self.sl = {b[0]: slice(b[5], b[5] + b[6]) for b in self.blocks}
         self.arms = [b for b in self.names if b != "C"]
