@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--schedule", default="concurrent", choices=["sequential", "concurrent"],
                     help="solve the two kappa domains one after the other, or concurrently on two streams")
     ap.add_argument("--config", default="default",
-                    choices=["default", "small", "precision", "batching", "serving", "fastsolve", "study"],
+                    choices=["default", "small", "precision", "batching", "serving", "fastsolve", "study",
+                             "neumann", "ncross"],
                     help="default: the 256^2 cross workload; the others run the other workloads as extra lines")
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
@@ -583,6 +584,89 @@ def run_extra(args):
                 lines[-1]["vs_plain_fp64"] = lines[-1]["value"] / line["value"]
             lines.append(line)
             d.close()
+    elif args.config == "neumann":
+        # Sec. 2.2: the Neumann-rectangle fast solve on nvec rectangles of n x n
+        # (default 64 x 512^2: 128 MB in, 128 MB out; FP64 throughout)
+        n, nv = args.n, args.seeds
+        h, kappa = 1.0 / n, -10.0
+        v = torch.as_tensor(W.random_block_vectors(nv, n * n, 9), device="cuda")
+        z = torch.zeros_like(v)
+        for _ in range(args.warmup):
+            B.neumann_solve(v, z, n, n, h, kappa)
+        tot = 0.0
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            ms, _, _ = _timed(lambda: B.neumann_solve(v, z, n, n, h, kappa))
+            tot += ms
+        ms = tot / args.steps
+        pts = nv * n * n
+        peaks = measured_peaks()
+        fp64 = B.probe_fma_peak(64)
+        dct_flops = 2 * 2.5 * np.log2(n) * pts + 5.0 * pts  # two transforms + Thomas
+        lines.append({"metric": "Neumann fast solves/s", "value": nv / (ms * 1e-3), "unit": "rectangles/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": f"Neumann rectangle solve on {nv} x {n}^2 (Neumann across t, Dirichlet "
+                                             f"across s), kappa -10, tables rebuilt per call",
+                                 "l2": "flushed before every step"},
+                      "algorithmic_bytes": 16 * pts, "hbm_gbs": 16 * pts / (ms * 1e-3) / 1e9,
+                      "hbm_frac": 16 * pts / (ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0),
+                      "fp64_frac": dct_flops / (ms * 1e-3) / fp64})
+    elif args.config == "ncross":
+        # Sec. 3.1 boundary pattern on the cross (Neumann arm sides, Dirichlet far
+        # ends, cell-centred grid): (i) throughput on the bench shape, n^2 per
+        # block, kappa in {0, -10}, `seeds` fourier RHS each, FGMRES(m);
+        # (ii) the validation case: error to the analytic solution over n (rtol 1e-12).
+        n, m = args.n, args.restart
+        doms = []
+        for kappa in (0.0, -10.0):
+            f = torch.as_tensor(np.stack([W.ncross_fourier_rhs(n, s) for s in range(args.seeds)]), device="cuda")
+            d = B.Domain(B.make_desc("cross", n, kappa, nrhs=args.seeds, restart=m, rtol=args.rtol,
+                                     boundary="neumann_sides"))
+            doms.append((d, f, torch.zeros_like(f)))
+        times, infos = [], []
+        for s in range(args.warmup + args.steps):
+            flush.fill_(float(s))
+            for d, f, p in doms:
+                d.set_rhs(f)
+            ms, _, out = _timed(lambda: [d.solve(p, check=False) for d, f, p in doms])
+            if s >= args.warmup:
+                times.append(ms)
+                for stt, info in out:
+                    infos += info
+        ms = sum(times) / len(times)
+        d0 = doms[0][0]
+        d0.set_profiling(True)
+        d0.set_rhs(doms[0][1])
+        d0.solve(doms[0][2], check=False)
+        phases = d0.phase_stats()
+        d0.set_profiling(False)
+        for d, _, _ in doms:
+            d.close()
+        errs = {}
+        for nv in (64, 128, 256, 512):
+            f = torch.as_tensor(W.ncross_validation_rhs(nv, 0.0)[None, :], device="cuda")
+            d = B.Domain(B.make_desc("cross", nv, 0.0, nrhs=1, restart=m, rtol=1e-12, boundary="neumann_sides"))
+            d.set_rhs(f)
+            p = torch.zeros_like(f)
+            stt, info = d.solve(p, check=False)
+            err = float((p[0].cpu() - torch.as_tensor(W.ncross_validation_solution(nv))).abs().max())
+            errs[nv] = {"max_error": err, "iterations": info[0]["iterations"], "residual": info[0]["residual"]}
+            d.close()
+        ns_ = sorted(errs)
+        order = {f"{a}->{b}": float(np.log2(errs[a]["max_error"] / errs[b]["max_error"])) for a, b in zip(ns_, ns_[1:])}
+        nsolve = 2 * args.seeds
+        lines.append({"metric": METRIC, "value": nsolve / (ms * 1e-3), "unit": "solves/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": f"Neumann-sided cross (Sec. 3.1 boundary pattern, cell-centred) "
+                                             f"{n}^2 per block, kappa 0 and -10, {args.seeds} fourier RHS each",
+                                 "n": n, "restart": m, "rtol": args.rtol, "l2": "flushed before every step"},
+                      "iterations_mean": float(np.mean([i["iterations"] for i in infos])),
+                      "residual_max": max(i["residual"] for i in infos),
+                      "all_converged": all(i["status"] == B.FPG_OK for i in infos),
+                      "phases_kappa0": phases,
+                      "validation": {"max_error": errs, "observed_order": order}})
     elif args.config == "study":
         # Sec. 3.2-3.3 on the GPU: (i) GMRES iterations with P = A_c^{-1} (the fast
         # solve), Jacobi and none, over n; (ii) iterations and solve time of the

@@ -22,6 +22,16 @@
  *   hold n x (n+1).  Inside a block: row-major, x fastest.  Several right-hand
  *   sides are stored one full vector after another.
  *
+ * Neumann-sided cross (boundary = FPG_BC_NEUMANN_SIDES; the boundary pattern
+ * of the paper's precision validation, Sec. 3.1 Eq. "cross_equation"): zero
+ * Dirichlet at the four far ends of the arms, zero normal derivative on the
+ * arms' sides.  The grid is cell-centred, h = 1/n, an unknown at every cell
+ * centre ((I + 1/2) h, (J + 1/2) h); every block, arms included, is n x n, in
+ * the same block order.  The Neumann faces use the matrix of Eq.
+ * "submat_Neumann" (the row loses one delta); a Dirichlet face half a cell away
+ * makes the row gain -delta.  The arms' fast solves run DCT-II lines along
+ * their interface (Sec. 2.2) instead of DST-I; the centre keeps DST-I.
+ *
  * Memory: the library never allocates device memory on the solve path.  The
  * caller passes one device workspace (size from fpg_workspace_bytes) at
  * creation and owns it; the handle itself is host memory owned by the library.
@@ -55,6 +65,12 @@ typedef enum {
 typedef enum { FPG_GEOM_L = 0, FPG_GEOM_T = 1, FPG_GEOM_CROSS = 2 } fpg_geometry;
 
 typedef enum {
+  FPG_BC_DIRICHLET = 0,     /* every outer edge Dirichlet; vertex-centred grid, h = 1/(n+1) */
+  FPG_BC_NEUMANN_SIDES = 1  /* cross only: Neumann arm sides, Dirichlet far ends; cell-centred, h = 1/n;
+                               n even with prime factors <= 13, n <= 2048 (else FPG_EUNSUPPORTED) */
+} fpg_boundary;
+
+typedef enum {
   FPG_SCHUR_REDUCED = 0, /* arm response by its exact interface table (DST, x g_k, DST) */
   FPG_SCHUR_LITERAL = 1  /* arm response by a full fast solve of every arm (Eq. "precond_basis_equ") */
 } fpg_schur_mode;
@@ -69,7 +85,7 @@ typedef struct {
   int32_t max_iters;         /* cap on total GMRES steps per right-hand side */
   int32_t precond_precision; /* 64: FP64 fast solve; 32: FP32 fast solve (FP64 outer loop) */
   int32_t schur_mode;        /* fpg_schur_mode */
-  int32_t reserved;          /* must be 0 */
+  int32_t boundary;          /* fpg_boundary (0 = all Dirichlet) */
 } fpg_domain_desc;
 
 typedef struct {
@@ -90,7 +106,8 @@ const char* fpg_last_cuda_error(void);
 /* Library version string. */
 const char* fpg_version(void);
 
-/* Number of unknowns of one right-hand side: n^2 + arms * n (n+1). */
+/* Number of unknowns of one right-hand side: n^2 + arms * n (n+1); 5 n^2 for
+ * the Neumann-sided cross. */
 fpg_status fpg_unknowns(const fpg_domain_desc* desc, int64_t* count);
 
 /* Device workspace needed by fpg_create_domain for this descriptor (bytes).
@@ -322,7 +339,7 @@ fpg_status fpg_launch_count(fpg_domain* d, int64_t* launches);
  * diagonal.  Computed as a DCT-II along t (the eigenbasis cos(k pi (j-1/2)/n_t),
  * eigenvalues -4 delta sin^2(k pi/(2 n_t))), one Thomas solve per mode along s
  * and the inverse DCT.  n_t even, prime factors of n_t at most 13,
- * 2 <= n_t, n_s <= 4096.  The caller owns `workspace` (device, >=
+ * 2 <= n_t <= 2048 (the shared-memory line batch), 1 <= n_s <= 4096.  The caller owns `workspace` (device, >=
  * fpg_neumann_workspace_bytes); the tables are rebuilt on the host and copied
  * in on every call.  Runs on `stream` (a cudaStream_t, NULL = default).
  * Errors: FPG_EINVAL (arguments), FPG_ENOMEM (workspace too small),

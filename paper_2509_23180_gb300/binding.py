@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfpg.so")
 
 GEOMETRY = {"L": 0, "T": 1, "cross": 2}
+BOUNDARY = {"dirichlet": 0, "neumann_sides": 1}
 SCHUR = {"reduced": 0, "literal": 1}
 STATUS = {0: "FPG_OK", 1: "FPG_EINVAL", 2: "FPG_ENOMEM", 3: "FPG_ECUDA", 4: "FPG_ENOCONV",
           5: "FPG_ETIMEOUT", 6: "FPG_EUNSUPPORTED", 7: "FPG_EBUDGET"}
@@ -46,7 +47,7 @@ class DomainDesc(ctypes.Structure):
     _fields_ = [("geometry", ctypes.c_int32), ("n", ctypes.c_int32), ("kappa", ctypes.c_double),
                 ("nrhs", ctypes.c_int32), ("restart", ctypes.c_int32), ("rtol", ctypes.c_double),
                 ("max_iters", ctypes.c_int32), ("precond_precision", ctypes.c_int32),
-                ("schur_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("schur_mode", ctypes.c_int32), ("boundary", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -134,12 +135,13 @@ def _check(status: int, where: str) -> int:
 
 
 def make_desc(geometry="cross", n=64, kappa=0.0, nrhs=1, restart=30, rtol=1e-10, max_iters=None,
-              precond_precision=64, schur_mode="reduced") -> DomainDesc:
+              precond_precision=64, schur_mode="reduced", boundary="dirichlet") -> DomainDesc:
     if max_iters is None:
         max_iters = 50 * restart
     return DomainDesc(GEOMETRY[geometry] if isinstance(geometry, str) else int(geometry), int(n), float(kappa),
                       int(nrhs), int(restart), float(rtol), int(max_iters), int(precond_precision),
-                      SCHUR[schur_mode] if isinstance(schur_mode, str) else int(schur_mode), 0)
+                      SCHUR[schur_mode] if isinstance(schur_mode, str) else int(schur_mode),
+                      BOUNDARY[boundary] if isinstance(boundary, str) else int(boundary))
 
 
 def unknowns(desc: DomainDesc) -> int:

@@ -61,6 +61,10 @@ cudaError_t launch_precond_simple(const double* v, void* z, int zprec, long long
                                   int nrhs, int gx, cudaStream_t st);
 int arnoldi_cluster_size(long long len);
 int fast_solve_path(int prec, const FastSolveTables& tb, LineLayout L, int nblk);
+bool dct_plan_shape(int n, DstPlan* pl);
+void dct_tables(int n, std::vector<double>& W, std::vector<double>& post);
+void dct_pivots(int nt, int ns, double delta, double kappa, double end_extra, int end, std::vector<double>& r,
+                std::vector<double>& m);
 int arnoldi_reg_ept(long long len, int csz, int ntcap);
 cudaError_t launch_arnoldi_reg(int csz, int ntcap, const double* V, long long vstride, const double* w,
                                const void* z, int zprec, const double* corr, int n, double delta, double kappa, int armmask,
@@ -126,9 +130,12 @@ struct Layout {
 
 bool make_layout(const fpg_domain_desc* d, Layout* L) {
   const int n = d->n;
+  const int as = d->boundary == FPG_BC_NEUMANN_SIDES ? n : n + 1;
   L->n = n;
   L->nc = (long long)n * n;
-  L->na = (long long)n * (n + 1);
+  L->na = (long long)n * as;
+  L->ao.as = as;
+  L->ao.bc = d->boundary == FPG_BC_NEUMANN_SIDES ? 1 : 0;
   static const int slots_cross[] = {0, 1, 2, 3};
   static const int slots_t[] = {0, 1, 2};
   static const int slots_l[] = {1, 3};
@@ -165,7 +172,12 @@ fpg_status validate(const fpg_domain_desc* d) {
   if (d->max_iters < 1) return FPG_EINVAL;
   if (d->precond_precision != 64 && d->precond_precision != 32) return FPG_EINVAL;
   if (d->schur_mode != FPG_SCHUR_REDUCED && d->schur_mode != FPG_SCHUR_LITERAL) return FPG_EINVAL;
-  if (d->reserved != 0) return FPG_EINVAL;
+  if (d->boundary != FPG_BC_DIRICHLET && d->boundary != FPG_BC_NEUMANN_SIDES) return FPG_EINVAL;
+  if (d->boundary == FPG_BC_NEUMANN_SIDES) {
+    // the arms' DCT-II lines: cross only, n even with prime factors <= 13, n <= 2048
+    DstPlan dp;
+    if (d->geometry != FPG_GEOM_CROSS || !dct_plan_shape(d->n, &dp)) return FPG_EUNSUPPORTED;
+  }
   return FPG_OK;
 }
 
@@ -188,6 +200,7 @@ struct fpg_domain {
   LineLayout LC, LWE, LSN;
   BatchDesc we, sn;  // arm groups inside full vectors
   FastSolveTables tC64, tC32, tA64, tA32;
+  FastSolveTables tA64e;  // Neumann-sided arms whose far end is row ns-1 (E, N); tA64 serves W, S
   double* ctab;
   double* gsc;           // [n] g_k delta^2 / (2 (n+1)), the transform form of the reduced Schur term
   int schur_transform = 0;  // 1: reduced Schur term by two DST-I per line where compiled (else the table sum)
@@ -282,6 +295,30 @@ void fill_ctab(int n, double delta, const std::vector<double>& rpivA, std::vecto
     }
     c[m] = acc * delta * delta / (double)(n + 1);
   }
+  c.resize(4 * n + 2);
+  for (int m = 0; m < 2 * n; ++m) c[2 * n + 2 + m] = c[m + 2];  // H(m) = T(m + 2)
+}
+
+// The same table for arms with Neumann sides (cell-centred, DCT-II basis
+// u_k(j) = a_k cos(k pi (j + 1/2)/n), a_0^2 = 1/n, a_k^2 = 2/n): with g_k the
+// interface entry of T_k^{-1} (the last reciprocal pivot when the far end is
+// row 0), G_ij = sum_k g_k u_k(i) u_k(j) = T(|i-j|) + T(i+j+1),
+// T(m) = delta^2/n (g_0/2 + sum_{k>=1} g_k cos(pi k m/n)); stored H(m) = -T(m+1).
+void fill_ctab_dct(int n, double delta, const std::vector<double>& rpivA, std::vector<double>& c) {
+  c.assign(4 * n + 2, 0.0);
+  std::vector<double> g(n);
+  for (int k = 0; k < n; ++k) g[k] = rpivA[(size_t)k * n + n - 1];
+  for (int m = 0; m < 2 * n + 2; ++m) {
+    double acc = 0.5 * g[0], comp = 0.0;
+    for (int k = 1; k < n; ++k) {
+      const double term = g[k] * cos_pi_frac((long long)k * m, n) - comp;
+      const double t = acc + term;
+      comp = (t - acc) - term;
+      acc = t;
+    }
+    c[m] = acc * delta * delta / (double)n;
+  }
+  for (int m = 0; m < 2 * n; ++m) c[2 * n + 2 + m] = -c[m + 1];
 }
 
 // DST plan for transform length n: radices of the Stockham FFT (4s, then a 2,
@@ -442,7 +479,25 @@ void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostP
   p = c.take(sizeof(float) * L.nc);           if (D) D->tC32.mneg = p;
   p = c.take(sizeof(double) * L.na);          if (D) D->tA64.mneg = p;
   p = c.take(sizeof(float) * L.na);           if (D) D->tA32.mneg = p;
-  p = c.take(sizeof(double) * (2 * n + 2));   if (D) D->ctab = (double*)p;
+  if (d->boundary == FPG_BC_NEUMANN_SIDES) {
+    // arms: DCT-II lines along t, pivots with the far-end row first (W, S) or last (E, N)
+    DstPlan dp;
+    dct_plan_shape(n, &dp);
+    dp.W = c.take(sizeof(double) * 2 * n);
+    const void* post = c.take(sizeof(double) * 2 * n);
+    const void* r2 = c.take(sizeof(double) * L.na);
+    const void* m2 = c.take(sizeof(double) * L.na);
+    if (D) {
+      for (FastSolveTables* tb : {&D->tA64, &D->tA64e}) {
+        tb->plan = dp;
+        tb->post = post;
+        tb->kind = 1;
+      }
+      D->tA64e.rpiv = r2;
+      D->tA64e.mneg = m2;
+    }
+  }
+  p = c.take(sizeof(double) * (4 * n + 2));   if (D) D->ctab = (double*)p;
   p = c.take(sizeof(double) * n);             if (D) D->gsc = (double*)p;
   p = c.take(sizeof(int) * 4);                if (D) D->arms_dev = (int*)p;
   p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->f = (double*)p;
@@ -586,15 +641,38 @@ fpg_status precond(fpg_domain* D, const double* v, void* z, int nvec, const int*
   return FPG_OK;
 }
 
+// FP64 fast solves on the arm blocks of nvec full vectors (in -> out), with the
+// per-RHS flags `active` (may be null).  Vertex-centred arms: W and E in one
+// batch, S and N in another (their sweeps are symmetric).  Neumann-sided arms:
+// one batch per arm, since the far-end row is first in W and S and last in E
+// and N, and the pivot tables differ.
+cudaError_t arm_fast_solves(fpg_domain* D, const double* in, double* out, int nvec, const int* active, int* nl) {
+  if (D->L.ao.bc == 0) {
+    if (D->we.nper > 0) {
+      const cudaError_t e = launch_fast_solve(64, 64, D->tA64, D->LWE, in, D->we, out, D->we, nvec * D->we.nper,
+                                              D->scratch, active, D->we.nper, D->st, nl);
+      if (e != cudaSuccess) return e;
+    }
+    if (D->sn.nper > 0)
+      return launch_fast_solve(64, 64, D->tA64, D->LSN, in, D->sn, out, D->sn, nvec * D->sn.nper, D->scratch,
+                               active, D->sn.nper, D->st, nl);
+    return cudaSuccess;
+  }
+  for (int a = 0; a < 4; ++a) {
+    if (D->L.ao.off[a] < 0) continue;
+    const BatchDesc bd{D->L.ntot, {D->L.ao.off[a], 0, 0, 0}, 1};
+    const FastSolveTables& tb = (a == 0 || a == 2) ? D->tA64 : D->tA64e;
+    const cudaError_t e = launch_fast_solve(64, 64, tb, a < 2 ? D->LWE : D->LSN, in, bd, out, bd, nvec, D->scratch,
+                                            active, 1, D->st, nl);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Fast solves on the arms of nvec full vectors (FP64): in -> out (arm blocks only).
 fpg_status arm_solves(fpg_domain* D, const double* in, double* out, int nvec, int phase) {
   int nl = 0;
-  if (D->we.nper > 0)
-    FPG_CUDA_TRY(launch_fast_solve(64, 64, D->tA64, D->LWE, in, D->we, out, D->we, nvec * D->we.nper, D->scratch,
-                                   nullptr, 1, D->st, &nl));
-  if (D->sn.nper > 0)
-    FPG_CUDA_TRY(launch_fast_solve(64, 64, D->tA64, D->LSN, in, D->sn, out, D->sn, nvec * D->sn.nper, D->scratch,
-                                   nullptr, 1, D->st, &nl));
+  FPG_CUDA_TRY(arm_fast_solves(D, in, out, nvec, nullptr, &nl));
   count(D, phase, nl);
   return FPG_OK;
 }
@@ -620,7 +698,7 @@ fpg_status arm_solves_refined(fpg_domain* D, const double* in, double* out, doub
 fpg_status schur_corr(fpg_domain* D, const void* z, int zprec, int nvec, const int* active) {
   const Layout& L = D->L;
   if (D->desc.schur_mode == FPG_SCHUR_REDUCED) {
-    if (D->schur_transform && schur_dst_supported(L.n))
+    if (D->schur_transform && L.ao.bc == 0 && schur_dst_supported(L.n))
       FPG_CUDA_TRY(launch_schur_dst(z, zprec, L.nc, L.n, D->tC64.plan, D->gsc, D->arms_dev, L.narms, D->corr, active,
                                     nvec, D->st));
     else
@@ -632,12 +710,7 @@ fpg_status schur_corr(fpg_domain* D, const void* z, int zprec, int nvec, const i
                                        D->gxf, D->st));
     count(D, 1, 1);
     int nl = 0;
-    if (D->we.nper > 0)
-      FPG_CUDA_TRY(launch_fast_solve(64, 64, D->tA64, D->LWE, D->lit_in, D->we, D->lit_out, D->we,
-                                     nvec * D->we.nper, D->scratch, active, D->we.nper, D->st, &nl));
-    if (D->sn.nper > 0)
-      FPG_CUDA_TRY(launch_fast_solve(64, 64, D->tA64, D->LSN, D->lit_in, D->sn, D->lit_out, D->sn,
-                                     nvec * D->sn.nper, D->scratch, active, D->sn.nper, D->st, &nl));
+    FPG_CUDA_TRY(arm_fast_solves(D, D->lit_in, D->lit_out, nvec, active, &nl));
     count(D, 1, nl);
     FPG_CUDA_TRY(launch_literal_extract(D->lit_out, L.ntot, L.ao, L.n, D->delta, D->corr, active, nvec, D->st));
     count(D, 1, 1);
@@ -1035,11 +1108,13 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   const Layout& L = D->L;
   const int n = desc->n;
   D->st = (cudaStream_t)stream;
-  D->delta = (double)(n + 1) * (double)(n + 1);
+  const int as = L.ao.as;  // arm sweep length: n + 1 (vertex-centred) or n (cell-centred)
+  const bool nside = L.ao.bc == 1;
+  D->delta = nside ? (double)n * (double)n : (double)(n + 1) * (double)(n + 1);
   D->prec = desc->precond_precision;
   D->LC = LineLayout{n, n, 1, n};
-  D->LWE = LineLayout{n, n + 1, n + 1, 1};
-  D->LSN = LineLayout{n, n + 1, 1, n};
+  D->LWE = LineLayout{n, as, as, 1};
+  D->LSN = LineLayout{n, as, 1, n};
   D->we = BatchDesc{L.ntot, {0, 0, 0, 0}, 0};
   D->sn = BatchDesc{L.ntot, {0, 0, 0, 0}, 0};
   for (int a = 0; a < 4; ++a) {
@@ -1048,7 +1123,7 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
     g.off[g.nper++] = L.ao.off[a];
   }
   for (auto* t : {&D->tC64, &D->tC32}) { t->n = n; t->ns = n; t->delta = D->delta; }
-  for (auto* t : {&D->tA64, &D->tA32}) { t->n = n; t->ns = n + 1; t->delta = D->delta; }
+  for (auto* t : {&D->tA64, &D->tA32, &D->tA64e}) { t->n = n; t->ns = as; t->delta = D->delta; }
   HostPlan hp = build_plan(n);
   Carver c(ws);
   carve(D, desc, L, &hp, c);
@@ -1062,16 +1137,25 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   D->ks.gx = D->gx;
   D->h_done.assign(nrhs, 0);
   // host tables
-  std::vector<double> pc, pa, ct;
+  std::vector<double> pc, pa, ct, ma, pae, mae, Wd, postd;
+  std::vector<double> gs(n, 0.0);
   fill_pivots(n, n, D->delta, desc->kappa, pc);
-  fill_pivots(n, n + 1, D->delta, desc->kappa, pa);
-  fill_ctab(n, D->delta, pa, ct);
-  std::vector<double> gs(n);
-  for (int k = 1; k <= n; ++k) gs[k - 1] = pa[(size_t)(k - 1) * (n + 1) + n] * D->delta * D->delta / (2.0 * (n + 1));
+  if (!nside) {
+    fill_pivots(n, n + 1, D->delta, desc->kappa, pa);
+    fill_ctab(n, D->delta, pa, ct);
+    for (int k = 1; k <= n; ++k) gs[k - 1] = pa[(size_t)(k - 1) * (n + 1) + n] * D->delta * D->delta / (2.0 * (n + 1));
+    ma.resize(pa.size());
+    for (size_t i = 0; i < pa.size(); ++i) ma[i] = -D->delta * pa[i];
+  } else {
+    // the far end is a Dirichlet face half a cell beyond row 0 (W, S) or row n-1 (E, N)
+    dct_pivots(n, n, D->delta, desc->kappa, -D->delta, 0, pa, ma);
+    dct_pivots(n, n, D->delta, desc->kappa, -D->delta, 1, pae, mae);
+    dct_tables(n, Wd, postd);
+    fill_ctab_dct(n, D->delta, pa, ct);
+  }
   std::vector<float> pc32(pc.begin(), pc.end()), pa32(pa.begin(), pa.end());
-  std::vector<double> mc(pc.size()), ma(pa.size());
+  std::vector<double> mc(pc.size());
   for (size_t i = 0; i < pc.size(); ++i) mc[i] = -D->delta * pc[i];
-  for (size_t i = 0; i < pa.size(); ++i) ma[i] = -D->delta * pa[i];
   std::vector<float> mc32(mc.begin(), mc.end()), ma32(ma.begin(), ma.end());
   std::vector<float> W32(hp.W.begin(), hp.W.end()), s32(hp.sinp.begin(), hp.sinp.end()),
       B32(hp.Bhat.begin(), hp.Bhat.end()), d32(hp.dense.begin(), hp.dense.end());
@@ -1107,6 +1191,12 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   if (!err) err = cp(D->tC32.mneg, mc32.data(), sizeof(float) * mc32.size());
   if (!err) err = cp(D->tA64.mneg, ma.data(), sizeof(double) * ma.size());
   if (!err) err = cp(D->tA32.mneg, ma32.data(), sizeof(float) * ma32.size());
+  if (nside) {
+    if (!err) err = cp(D->tA64e.rpiv, pae.data(), sizeof(double) * pae.size());
+    if (!err) err = cp(D->tA64e.mneg, mae.data(), sizeof(double) * mae.size());
+    if (!err) err = cp(D->tA64.plan.W, Wd.data(), sizeof(double) * Wd.size());
+    if (!err) err = cp(D->tA64.post, postd.data(), sizeof(double) * postd.size());
+  }
   if (!err) err = cp(D->ctab, ct.data(), sizeof(double) * ct.size());
   if (!err) err = cp(D->gsc, gs.data(), sizeof(double) * gs.size());
   if (!err) err = cp(D->arms_dev, arms, sizeof(arms));
@@ -1233,7 +1323,7 @@ fpg_status fpg_block_solve(fpg_domain* d, int32_t block, const double* v, double
   if (block > 0 && L.ao.off[block - 1] < 0) return FPG_EINVAL;
   const long long len = block == 0 ? L.nc : L.na;
   const LineLayout& LL = block == 0 ? d->LC : (block <= 2 ? d->LWE : d->LSN);
-  const FastSolveTables& tb = block == 0 ? d->tC64 : d->tA64;
+  const FastSolveTables& tb = block == 0 ? d->tC64 : ((L.ao.bc == 1 && (block == 2 || block == 4)) ? d->tA64e : d->tA64);
   const int cap = (int)std::max(1LL, ((long long)d->desc.nrhs * std::max(L.nc, 2 * L.na)) / len);
   for (int s = 0; s < nvec; s += cap) {
     const int c = std::min(cap, nvec - s);
@@ -1409,7 +1499,7 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_FUSED_FASTSOLVE:
-      for (auto* t : {&d->tC64, &d->tC32, &d->tA64, &d->tA32}) t->fused = value != 0;
+      for (auto* t : {&d->tC64, &d->tC32, &d->tA64, &d->tA32, &d->tA64e}) t->fused = value != 0;
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_PRECOND:
@@ -1419,12 +1509,12 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
       return FPG_OK;
     case FPG_OPT_DST_ENGINE:
       if (value < 0 || value > 2) return FPG_EINVAL;
-      for (auto* t : {&d->tC64, &d->tC32, &d->tA64, &d->tA32}) t->generic = value;
+      for (auto* t : {&d->tC64, &d->tC32, &d->tA64, &d->tA32, &d->tA64e}) t->generic = value;
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_DST_BULK:
       if (value < 0 || value > 1) return FPG_EINVAL;
-      for (auto* tt : {&d->tC64, &d->tC32, &d->tA64, &d->tA32}) tt->bulk = value;
+      for (auto* tt : {&d->tC64, &d->tC32, &d->tA64, &d->tA32, &d->tA64e}) tt->bulk = value;
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_ARM_REFINE:

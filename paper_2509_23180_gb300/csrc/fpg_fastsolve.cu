@@ -554,23 +554,29 @@ cudaError_t launch_fast_solve_fused(int prec, int out_prec, const FastSolveTable
                                     const double* in, BatchDesc ib, void* out, BatchDesc ob, int nblk,
                                     const int* active, int nper_active, cudaStream_t st);
 
-// The Thomas kernels for other line transforms (the Neumann rectangles): scratch
-// [nblk][n][ns] in place, pivot tables [n][ns].
+// The Thomas kernels for other line transforms (the Neumann DCT-II lines):
+// scratch [nblk][n][ns] in place, pivot tables [n][ns].
 cudaError_t launch_thomas_any(int prec, void* scratch, int n, int ns, const void* rpiv, const void* mneg, int nblk,
-                              cudaStream_t st) {
+                              const int* active, int nper_active, cudaStream_t st, int wpb) {
   if (prec == 64)
-    return launch_thomas<double>((double*)scratch, n, ns, (const double*)rpiv, (const double*)mneg, nblk, nullptr, 1,
-                                 st, 0);
-  return launch_thomas<float>((float*)scratch, n, ns, (const float*)rpiv, (const float*)mneg, nblk, nullptr, 1, st,
-                              0);
+    return launch_thomas<double>((double*)scratch, n, ns, (const double*)rpiv, (const double*)mneg, nblk, active,
+                                 nper_active, st, wpb);
+  return launch_thomas<float>((float*)scratch, n, ns, (const float*)rpiv, (const float*)mneg, nblk, active,
+                              nper_active, st, wpb);
 }
+
+cudaError_t launch_fast_solve_dct(const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib,
+                                  double* out, BatchDesc ob, int nblk, double* scratch, const int* active,
+                                  int nper_active, cudaStream_t st);
 
 // Which kernels the fast solve of this block kind runs: 0 generic FFT engine
 // (k_fft_forward / k_thomas_reg / k_fft_inverse), 1 size-specialised
 // (k_dst_lines_fwd / k_thomas_reg / k_dst_lines_inv), 2 dense DST, 3 the fused
-// one-pass cluster kernel.
+// one-pass cluster kernel, 4 the DCT-II lines of a Neumann-sided block
+// (k_dct_fwd / k_thomas_reg / k_dct_inv).
 bool fast_solve_fused_fits(int prec, const FastSolveTables& tb, LineLayout L);
 int fast_solve_path(int prec, const FastSolveTables& tb, LineLayout L, int nblk) {
+  if (tb.kind == 1) return 4;
   if (tb.fused && fast_solve_fused_fits(prec, tb, L)) return 3;
   if (tb.plan.mode == DST_DENSE) return 2;
   const bool special = prec == 64 ? lines_engine<double>(tb.plan.p, nblk, L.ns, tb.generic)
@@ -588,6 +594,11 @@ cudaError_t launch_fast_solve(int prec, int out_prec, const FastSolveTables& tb,
                               void* scratch, const int* active, int nper_active, cudaStream_t st,
                               int* launches, cudaEvent_t* ev) {
   if (nblk <= 0) return cudaSuccess;
+  if (tb.kind == 1) {  // DCT-II along t (Neumann ends): FP64 only
+    if (prec != 64 || out_prec != 64) return cudaErrorNotSupported;
+    if (launches) *launches += 3;
+    return launch_fast_solve_dct(tb, L, in, ib, (double*)out, ob, nblk, (double*)scratch, active, nper_active, st);
+  }
   if (tb.fused) {
     if (ev) record_event(ev[6], st);
     const cudaError_t e = launch_fast_solve_fused(prec, out_prec, tb, L, in, ib, out, ob, nblk, active, nper_active, st);

@@ -41,16 +41,27 @@ struct FastSolveTables {
   int fused = 0;      // 1: one-pass cluster kernel when the block fits
   int generic = 0;    // DST engine: 0 auto, 1 generic FFT engine, 2 size-specialised where compiled
   int bulk = 0;       // 1: FP32 forward DST as the persistent kernel with bulk asynchronous row copies
+  int kind = 0;       // transform along t: 0 DST-I (Dirichlet ends), 1 DCT-II (Neumann ends, FP64 only)
+  const void* post = nullptr;  // DCT-II: e^{-i pi k/(2n)}, k < n (complex, FP64)
 };
 
-// Offsets of the arm blocks W, E, S, N inside one full vector (-1 = absent).
+// Offsets of the arm blocks W, E, S, N inside one full vector (-1 = absent),
+// and the arm shape: every arm is n lines across (along its interface) by `as`
+// lines along its sweep (n + 1 on the vertex-centred grid, whose arms own the
+// line they share with the centre; n on the cell-centred grid).  bc = 0: every
+// edge Dirichlet (zero neighbour); bc = 1: cell-centred, the arms' sides are
+// Neumann faces (ghost = the cell's value) and their far ends Dirichlet faces
+// (ghost = minus the cell's value).
 struct ArmOffsets {
   long long off[4];
+  int as = 0;
+  int bc = 0;
 };
 
 // Tables for the interface (Schur) correction, reduced form:
-// G_a = delta^2 Q diag(g_k) Q = Toeplitz-minus-Hankel with entries
-// c(|i-j|) - c(i+j+2) (0-based i, j), c(m) for m = 0..2n+1.
+// G_a = delta^2 Q diag(g_k) Q^T = Toeplitz-plus-Hankel with entries
+// T(|i-j|) - H(i+j) (0-based i, j), stored as T[0..2n+1] followed by H[0..2n-1]:
+// DST-I arms H(m) = T(m+2); DCT-II arms H(m) = -T(m+1).
 struct SchurTables {
   const double* ctab;
 };

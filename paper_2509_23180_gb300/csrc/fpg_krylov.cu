@@ -36,9 +36,9 @@ __device__ __forceinline__ double c_line(const Tz* z, int n, int a, int q) {
 }
 
 // ---------------------------------------------------------------------------
-// a2, reduced form: corr[r][a][i] = sum_j (c(|i-j|) - c(i+j+2)) line_a[j], i.e.
-// delta^2 Q diag(g_k) Q applied to C's line next to arm a (the exact interface
-// response R_ca A_a^{-1} R_ac restricted to that line).
+// a2, reduced form: corr[r][a][i] = sum_j (T(|i-j|) - H(i+j)) line_a[j], i.e.
+// delta^2 Q diag(g_k) Q^T applied to C's line next to arm a (the exact interface
+// response R_ca A_a^{-1} R_ac restricted to that line; ctab = T[2n+2] then H[2n]).
 template <typename Tz>
 __global__ void __launch_bounds__(256)
 k_schur_lines(const Tz* __restrict__ z, long long zstride, int n, const double* __restrict__ ctab,
@@ -51,14 +51,15 @@ k_schur_lines(const Tz* __restrict__ z, long long zstride, int n, const double* 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* line = reinterpret_cast<double*>(smem_raw);
   double* c = line + n;
-  double* part = c + 2 * n + 2;  // [8][32]
+  double* hk = c + 2 * n + 2;
+  double* part = hk + 2 * n;  // [8][32]
   const int r = blockIdx.y / narms;
   const int a = arms[blockIdx.y % narms];
   if (active != nullptr && !active[r]) return;
   const Tz* zr = z + (long long)r * zstride;
   const int tid = threadIdx.y * 32 + threadIdx.x;
   for (int q = tid; q < n; q += 256) line[q] = c_line(zr, n, a, q);
-  for (int q = tid; q < 2 * n + 2; q += 256) c[q] = ctab[q];
+  for (int q = tid; q < 4 * n + 2; q += 256) c[q] = ctab[q];
   __syncthreads();
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int per = (n + 7) / 8;
@@ -67,7 +68,7 @@ k_schur_lines(const Tz* __restrict__ z, long long zstride, int n, const double* 
   if (i < n) {
     for (int j = j0; j < j1; ++j) {
       const int d = i > j ? i - j : j - i;
-      acc = fma(c[d] - c[i + j + 2], line[j], acc);
+      acc = fma(c[d] - hk[i + j], line[j], acc);
     }
   }
   part[threadIdx.y * 32 + threadIdx.x] = acc;
@@ -117,20 +118,21 @@ __global__ void k_literal_inject(const Tz* __restrict__ z, long long zstride, in
   const int r = blockIdx.y;
   if (active != nullptr && !active[r]) return;
   const Tz* zr = z + (long long)r * zstride;
-  const long long na = (long long)n * (n + 1);
+  const int as = ao.as;
+  const long long na = (long long)n * as;
   for (int a = 0; a < 4; ++a) {
     if (ao.off[a] < 0) continue;
     double* ab = armbuf + (long long)r * rhs_stride + ao.off[a];
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < na;
          idx += (long long)gridDim.x * blockDim.x) {
       double v = 0.0;
-      if (a < 2) {  // W/E: (n+1) x n, x fastest
-        const int j = (int)(idx / (n + 1)), i = (int)(idx - (long long)j * (n + 1));
-        const int iface = (a == 0) ? n : 0;
+      if (a < 2) {  // W/E: as x n, x fastest
+        const int j = (int)(idx / as), i = (int)(idx - (long long)j * as);
+        const int iface = (a == 0) ? as - 1 : 0;
         if (i == iface) v = delta * c_line(zr, n, a, j);
-      } else {      // S/N: n x (n+1)
+      } else {      // S/N: n x as
         const int j = (int)(idx / n), i = (int)(idx - (long long)j * n);
-        const int iface = (a == 2) ? n : 0;
+        const int iface = (a == 2) ? as - 1 : 0;
         if (j == iface) v = delta * c_line(zr, n, a, i);
       }
       ab[idx] = v;
@@ -149,10 +151,11 @@ __global__ void k_literal_extract(const double* __restrict__ armsol, long long r
   for (int a = 0; a < 4; ++a) {
     if (ao.off[a] < 0) continue;
     const double* s = armsol + (long long)r * rhs_stride + ao.off[a];
+    const int as = ao.as;
     double v;
-    if (a == 0) v = s[(long long)q * (n + 1) + n];
-    else if (a == 1) v = s[(long long)q * (n + 1)];
-    else if (a == 2) v = s[(long long)n * n + q];
+    if (a == 0) v = s[(long long)q * as + as - 1];
+    else if (a == 1) v = s[(long long)q * as];
+    else if (a == 2) v = s[(long long)(as - 1) * n + q];
     else v = s[q];
     corr[((long long)r * 4 + a) * n + q] = delta * v;
   }
@@ -653,9 +656,10 @@ k_reduce_rhs(const double* __restrict__ f, const double* __restrict__ q, long lo
        idx += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(idx / n), i = (int)(idx - (long long)j * n);
     double v = fr[idx];
-    if (i == 0 && ao.off[0] >= 0) v -= delta * qr[ao.off[0] + (long long)j * (n + 1) + n];
-    if (i == n - 1 && ao.off[1] >= 0) v -= delta * qr[ao.off[1] + (long long)j * (n + 1)];
-    if (j == 0 && ao.off[2] >= 0) v -= delta * qr[ao.off[2] + (long long)n * n + i];
+    const int as = ao.as;
+    if (i == 0 && ao.off[0] >= 0) v -= delta * qr[ao.off[0] + (long long)j * as + as - 1];
+    if (i == n - 1 && ao.off[1] >= 0) v -= delta * qr[ao.off[1] + (long long)j * as];
+    if (j == 0 && ao.off[2] >= 0) v -= delta * qr[ao.off[2] + (long long)(as - 1) * n + i];
     if (j == n - 1 && ao.off[3] >= 0) v -= delta * qr[ao.off[3] + i];
     out[idx] = v;
   }
@@ -679,22 +683,32 @@ k_arm_rhs(const double* __restrict__ f, const double* __restrict__ u, long long 
       continue;
     }
     double v = fr[idx];
+    const int as = ao.as;
     for (int a = 0; a < 4; ++a) {
       const long long off = ao.off[a];
-      if (off < 0 || idx < off || idx >= off + (long long)n * (n + 1)) continue;
+      if (off < 0 || idx < off || idx >= off + (long long)n * as) continue;
       const long long li = idx - off;
       if (a < 2) {
-        const int j = (int)(li / (n + 1)), i = (int)(li - (long long)j * (n + 1));
-        if (a == 0 && i == n) v -= delta * ur[(long long)j * n];
+        const int j = (int)(li / as), i = (int)(li - (long long)j * as);
+        if (a == 0 && i == as - 1) v -= delta * ur[(long long)j * n];
         if (a == 1 && i == 0) v -= delta * ur[(long long)j * n + n - 1];
       } else {
         const int j = (int)(li / n), i = (int)(li - (long long)j * n);
-        if (a == 2 && j == n) v -= delta * ur[i];
+        if (a == 2 && j == as - 1) v -= delta * ur[i];
         if (a == 3 && j == 0) v -= delta * ur[(long long)(n - 1) * n + i];
       }
     }
     o[idx] = v;
   }
+}
+
+// Ghost value beyond an arm's own edge (the arm seen alone, its interface line
+// treated as Dirichlet): 0 on the vertex-centred grid; on the cell-centred grid
+// (bc = 1) 0 across the interface, xc across a side (Neumann face), -xc across
+// the far end (Dirichlet face).  side: 0 = interface, 1 = side, 2 = far end.
+__device__ __forceinline__ double arm_ghost(int bc, int side, double xc) {
+  if (bc == 0 || side == 0) return 0.0;
+  return side == 1 ? xc : -xc;
 }
 
 // a6 refinement: out_a = rhs_a - A_a x_a on every arm block (A_a: the arm's own
@@ -703,11 +717,15 @@ __global__ void __launch_bounds__(kThreads)
 k_arm_residual(const double* __restrict__ rhs, const double* __restrict__ x, double* __restrict__ out,
                long long ntot, int n, double delta, double kappa, ArmOffsets ao) {
   const int r = blockIdx.y;
-  const long long na = (long long)n * (n + 1);
+  const int as = ao.as, bc = ao.bc;
+  const long long na = (long long)n * as;
   for (int a = 0; a < 4; ++a) {
     const long long off = ao.off[a];
     if (off < 0) continue;
-    const int nx = a < 2 ? n + 1 : n, ny = a < 2 ? n : n + 1;
+    const int nx = a < 2 ? as : n, ny = a < 2 ? n : as;
+    // which edge lies beyond i = -1, i = nx, j = -1, j = ny
+    const int eL = a == 0 ? 2 : (a == 1 ? 0 : 1), eR = a == 0 ? 0 : (a == 1 ? 2 : 1);
+    const int eD = a == 2 ? 2 : (a == 3 ? 0 : 1), eU = a == 2 ? 0 : (a == 3 ? 2 : 1);
     const double* xr = x + (long long)r * ntot + off;
     const double* fr = rhs + (long long)r * ntot + off;
     double* o = out + (long long)r * ntot + off;
@@ -715,8 +733,10 @@ k_arm_residual(const double* __restrict__ rhs, const double* __restrict__ x, dou
          idx += (long long)gridDim.x * blockDim.x) {
       const int j = (int)(idx / nx), i = (int)(idx - (long long)j * nx);
       const double xc = xr[idx];
-      const double s = stencil_sum(xc, i > 0 ? xr[idx - 1] : 0.0, i < nx - 1 ? xr[idx + 1] : 0.0,
-                                   j > 0 ? xr[idx - nx] : 0.0, j < ny - 1 ? xr[idx + nx] : 0.0);
+      const double s = stencil_sum(xc, i > 0 ? xr[idx - 1] : arm_ghost(bc, eL, xc),
+                                   i < nx - 1 ? xr[idx + 1] : arm_ghost(bc, eR, xc),
+                                   j > 0 ? xr[idx - nx] : arm_ghost(bc, eD, xc),
+                                   j < ny - 1 ? xr[idx + nx] : arm_ghost(bc, eU, xc));
       o[idx] = fr[idx] - fma(delta, s, kappa * xc);
     }
   }
@@ -726,7 +746,7 @@ k_arm_residual(const double* __restrict__ rhs, const double* __restrict__ x, dou
 __global__ void __launch_bounds__(kThreads)
 k_arm_add(double* __restrict__ x, const double* __restrict__ e, long long ntot, int n, ArmOffsets ao) {
   const int r = blockIdx.y;
-  const long long na = (long long)n * (n + 1);
+  const long long na = (long long)n * ao.as;
   for (int a = 0; a < 4; ++a) {
     const long long off = ao.off[a];
     if (off < 0) continue;
@@ -740,31 +760,35 @@ k_arm_add(double* __restrict__ x, const double* __restrict__ e, long long ntot, 
 
 // ---------------------------------------------------------------------------
 // Global operator K (a7): value of the neighbour (di, dj) of local node (i, j)
-// of block `blk` (0 = C, 1..4 = W, E, S, N); zero on the domain's edge.
+// of block `blk` (0 = C, 1..4 = W, E, S, N) whose own value is pc.  Beyond the
+// domain's edge: zero on the vertex-centred grid; on the cell-centred grid
+// (bc = 1) pc across an arm's side (Neumann face) and -pc across its far end
+// (Dirichlet face).
 __device__ __forceinline__ double nb_value(const double* pr, int n, const ArmOffsets& ao, int blk, int i,
-                                           int j, int di, int dj) {
+                                           int j, int di, int dj, double pc) {
   const int ni = i + di, nj = j + dj;
-  const long long nc = (long long)n * n;
+  const int as = ao.as;
   if (blk == 0) {
     if (ni >= 0 && ni < n && nj >= 0 && nj < n) return pr[(long long)nj * n + ni];
-    if (ni < 0) return ao.off[0] >= 0 ? pr[ao.off[0] + (long long)nj * (n + 1) + n] : 0.0;
-    if (ni >= n) return ao.off[1] >= 0 ? pr[ao.off[1] + (long long)nj * (n + 1)] : 0.0;
-    if (nj < 0) return ao.off[2] >= 0 ? pr[ao.off[2] + (long long)n * n + ni] : 0.0;
+    if (ni < 0) return ao.off[0] >= 0 ? pr[ao.off[0] + (long long)nj * as + as - 1] : 0.0;
+    if (ni >= n) return ao.off[1] >= 0 ? pr[ao.off[1] + (long long)nj * as] : 0.0;
+    if (nj < 0) return ao.off[2] >= 0 ? pr[ao.off[2] + (long long)(as - 1) * n + ni] : 0.0;
     return ao.off[3] >= 0 ? pr[ao.off[3] + ni] : 0.0;
   }
   const int a = blk - 1;
   const long long off = ao.off[a];
-  if (a < 2) {  // (n+1) x n
-    if (ni >= 0 && ni <= n && nj >= 0 && nj < n) return pr[off + (long long)nj * (n + 1) + ni];
-    if (a == 0 && ni == n + 1) return pr[(long long)nj * n];          // W -> C column 0
+  if (a < 2) {  // as x n
+    if (ni >= 0 && ni < as && nj >= 0 && nj < n) return pr[off + (long long)nj * as + ni];
+    if (a == 0 && ni == as) return pr[(long long)nj * n];             // W -> C column 0
     if (a == 1 && ni == -1) return pr[(long long)nj * n + n - 1];     // E -> C column n-1
-    return 0.0;
+    if (ao.bc == 0) return 0.0;
+    return (nj < 0 || nj >= n) ? pc : -pc;                            // side : far end
   }
-  if (ni >= 0 && ni < n && nj >= 0 && nj <= n) return pr[off + (long long)nj * n + ni];
-  if (a == 2 && nj == n + 1) return pr[ni];                           // S -> C row 0
+  if (ni >= 0 && ni < n && nj >= 0 && nj < as) return pr[off + (long long)nj * n + ni];
+  if (a == 2 && nj == as) return pr[ni];                              // S -> C row 0
   if (a == 3 && nj == -1) return pr[(long long)(n - 1) * n + ni];     // N -> C row n-1
-  (void)nc;
-  return 0.0;
+  if (ao.bc == 0) return 0.0;
+  return (ni < 0 || ni >= n) ? pc : -pc;                              // side : far end
 }
 
 __device__ __forceinline__ void locate(long long idx, int n, const ArmOffsets& ao, int* blk, int* i, int* j) {
@@ -777,10 +801,10 @@ __device__ __forceinline__ void locate(long long idx, int n, const ArmOffsets& a
   }
   for (int a = 0; a < 4; ++a) {
     const long long off = ao.off[a];
-    if (off < 0 || idx < off || idx >= off + (long long)n * (n + 1)) continue;
+    if (off < 0 || idx < off || idx >= off + (long long)n * ao.as) continue;
     const long long li = idx - off;
     *blk = a + 1;
-    const int nx = (a < 2) ? n + 1 : n;
+    const int nx = (a < 2) ? ao.as : n;
     *j = (int)(li / nx);
     *i = (int)(li - (long long)(*j) * nx);
     return;
@@ -803,8 +827,8 @@ k_global_apply(const double* __restrict__ p, double* __restrict__ y, const doubl
     int blk, i, j;
     locate(idx, n, ao, &blk, &i, &j);
     const double pc = pr[idx];
-    const double s = stencil_sum(pc, nb_value(pr, n, ao, blk, i, j, -1, 0), nb_value(pr, n, ao, blk, i, j, 1, 0),
-                                 nb_value(pr, n, ao, blk, i, j, 0, -1), nb_value(pr, n, ao, blk, i, j, 0, 1));
+    const double s = stencil_sum(pc, nb_value(pr, n, ao, blk, i, j, -1, 0, pc), nb_value(pr, n, ao, blk, i, j, 1, 0, pc),
+                                 nb_value(pr, n, ao, blk, i, j, 0, -1, pc), nb_value(pr, n, ao, blk, i, j, 0, 1, pc));
     const double kp = fma(delta, s, kappa * pc);
     if (y) y[(long long)r * ntot + idx] = kp;
     if (f) {
@@ -845,8 +869,8 @@ __global__ void k_residual_finalize(const double* __restrict__ part, int gmax, i
 // ---------------------------------------------------------------------------
 // Comparison preconditioners of Sec. 3.2 (P = I and the Jacobi P = D_2).
 // Jacobi: z = v / diag(L_c) with diag(L_c) = -4 delta + kappa on C, minus, on the
-// line next to arm a, the diagonal of delta^2 Q diag(g) Q, which is c(0) - c(2q+2)
-// at position q of that line (the Toeplitz-minus-Hankel form of the interface table).
+// line next to arm a, the diagonal of delta^2 Q diag(g) Q^T, which is T(0) - H(2q)
+// at position q of that line (the Toeplitz-plus-Hankel form of the interface table).
 template <typename To>
 __global__ void __launch_bounds__(kThreads)
 k_precond_simple(const double* __restrict__ v, To* __restrict__ z, long long len, int n, double delta, double kappa,
@@ -860,11 +884,12 @@ k_precond_simple(const double* __restrict__ v, To* __restrict__ z, long long len
     double x = vr[idx];
     if (jacobi) {
       const int j = (int)(idx / n), i = (int)(idx - (long long)j * n);
+      const double* hk = ctab + 2 * n + 2;
       double d = -4.0 * delta + kappa;
-      if (i == 0 && (armmask & 1)) d -= ctab[0] - ctab[2 * j + 2];
-      if (i == n - 1 && (armmask & 2)) d -= ctab[0] - ctab[2 * j + 2];
-      if (j == 0 && (armmask & 4)) d -= ctab[0] - ctab[2 * i + 2];
-      if (j == n - 1 && (armmask & 8)) d -= ctab[0] - ctab[2 * i + 2];
+      if (i == 0 && (armmask & 1)) d -= ctab[0] - hk[2 * j];
+      if (i == n - 1 && (armmask & 2)) d -= ctab[0] - hk[2 * j];
+      if (j == 0 && (armmask & 4)) d -= ctab[0] - hk[2 * i];
+      if (j == n - 1 && (armmask & 8)) d -= ctab[0] - hk[2 * i];
       x /= d;
     }
     zr[idx] = (To)x;
@@ -908,7 +933,7 @@ cudaError_t launch_schur_reduced(const void* z, int zprec, long long zstride, in
                                  const int* arms_dev, int narms, double* corr, const int* active, int nrhs,
                                  cudaStream_t st) {
   dim3 grid((n + 31) / 32, nrhs * narms);
-  const size_t smem = sizeof(double) * (3 * n + 2 + 256);
+  const size_t smem = sizeof(double) * (5 * n + 2 + 256);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_schur_lines<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -24,7 +24,7 @@ namespace fpg {
 
 void record_message(const char* msg);
 cudaError_t launch_thomas_any(int prec, void* scratch, int n, int ns, const void* rpiv, const void* mneg, int nblk,
-                              cudaStream_t st);
+                              const int* active, int nper_active, cudaStream_t st, int wpb);
 
 namespace {
 
@@ -70,29 +70,46 @@ int nm_pairs(int nt) {
 
 size_t nm_smem(int nt, int Q) { return sizeof(C2<double>) * ((size_t)2 * Q * nt + 2 * nt); }
 
+__device__ __forceinline__ int makhoul_slot(int t, int nt) {
+  // position of x_t in the reordered sequence v: v_m = x_{2m}, v_{n-1-m} = x_{2m+1}
+  return (t & 1) == 0 ? t >> 1 : nt - 1 - (t >> 1);
+}
+
+// Forward DCT-II of the lines of a batch of blocks: element (t, s) of block b
+// at in + (b / nper) rhs_stride + off[b % nper] + t st + s ss; 2Q lines per CTA,
+// result X_k of line s at scratch[b][k][s].
 template <int MAXR>
 __global__ void __launch_bounds__(kNmThreads)
-k_dct_fwd(const double* __restrict__ v, double* __restrict__ scratch, int nt, int ns, DstPlan pl,
-          const C2<double>* __restrict__ Wg, const C2<double>* __restrict__ postg, int Q) {
+k_dct_fwd(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPlan pl, const C2<double>* __restrict__ Wg,
+          const C2<double>* __restrict__ postg, double* __restrict__ scratch, int Q, const int* __restrict__ active,
+          int nper_active) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.y;
+  if (active != nullptr && !active[b / nper_active]) return;
+  const int nt = L.nt, ns = L.ns;
   C2<double>* b0 = reinterpret_cast<C2<double>*>(smem_raw);
   C2<double>* b1 = b0 + (size_t)Q * nt;
   C2<double>* W = b1 + (size_t)Q * nt;
   C2<double>* post = W + nt;
-  const int b = blockIdx.y, s0 = blockIdx.x * 2 * Q, nl = min(2 * Q, ns - s0);
-  const int half = nt / 2;
+  double* b0d = reinterpret_cast<double*>(b0);
+  const int s0 = blockIdx.x * 2 * Q, nl = min(2 * Q, ns - s0);
   for (int i = threadIdx.x; i < nt; i += blockDim.x) {
     W[i] = Wg[i];
     post[i] = postg[i];
   }
-  const double* src = v + (long long)b * nt * ns;
-  for (int i = threadIdx.x; i < Q * nt; i += blockDim.x) {
-    const int q = i / nt, m = i - q * nt;
-    const int t = m < half ? 2 * m : 2 * (nt - 1 - m) + 1;  // Makhoul reordering
-    const int la = 2 * q, lb = la + 1;
-    const double a = la < nl ? src[(long long)(s0 + la) * nt + t] : 0.0;
-    const double c = lb < nl ? src[(long long)(s0 + lb) * nt + t] : 0.0;
-    b0[i] = C2<double>{a, c};
+  const double* src = in + (long long)(b / ib.nper) * ib.rhs_stride + ib.off[b % ib.nper];
+  // line l = 2q + c goes to component c of packed sequence q, in Makhoul order
+  if (L.st == 1) {
+    for (int i = threadIdx.x; i < 2 * Q * nt; i += blockDim.x) {
+      const int l = i / nt, t = i - l * nt;
+      b0d[2 * ((l >> 1) * nt + makhoul_slot(t, nt)) + (l & 1)] = l < nl ? src[t + (long long)(s0 + l) * L.ss] : 0.0;
+    }
+  } else {
+    for (int i = threadIdx.x; i < 2 * Q * nt; i += blockDim.x) {
+      const int t = i / (2 * Q), l = i - t * (2 * Q);
+      b0d[2 * ((l >> 1) * nt + makhoul_slot(t, nt)) + (l & 1)] =
+          l < nl ? src[(long long)t * L.st + (long long)(s0 + l) * L.ss] : 0.0;
+    }
   }
   __syncthreads();
   const C2<double>* Z = stockham_fft<double, MAXR>(pl, b0, b1, Q, nt, W);
@@ -110,17 +127,23 @@ k_dct_fwd(const double* __restrict__ v, double* __restrict__ scratch, int nt, in
   }
 }
 
+// Inverse of k_dct_fwd (x = DCT-II^{-1} X, i.e. X_0/n + (2/n) sum_k X_k cos(...)),
+// written into the batch layout of `out`.
 template <int MAXR>
 __global__ void __launch_bounds__(kNmThreads)
-k_dct_inv(const double* __restrict__ scratch, double* __restrict__ z, int nt, int ns, DstPlan pl,
-          const C2<double>* __restrict__ Wg, const C2<double>* __restrict__ postg, int Q) {
+k_dct_inv(const double* __restrict__ scratch, double* __restrict__ out, BatchDesc ob, LineLayout L, DstPlan pl,
+          const C2<double>* __restrict__ Wg, const C2<double>* __restrict__ postg, int Q,
+          const int* __restrict__ active, int nper_active) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.y;
+  if (active != nullptr && !active[b / nper_active]) return;
+  const int nt = L.nt, ns = L.ns;
   C2<double>* b0 = reinterpret_cast<C2<double>*>(smem_raw);
   C2<double>* b1 = b0 + (size_t)Q * nt;
   C2<double>* W = b1 + (size_t)Q * nt;
   C2<double>* post = W + nt;
   double* X = reinterpret_cast<double*>(b1);  // [2Q][nt] spectra, staged
-  const int b = blockIdx.y, s0 = blockIdx.x * 2 * Q, nl = min(2 * Q, ns - s0);
+  const int s0 = blockIdx.x * 2 * Q, nl = min(2 * Q, ns - s0);
   for (int i = threadIdx.x; i < nt; i += blockDim.x) {
     W[i] = Wg[i];
     post[i] = postg[i];
@@ -146,21 +169,29 @@ k_dct_inv(const double* __restrict__ scratch, double* __restrict__ z, int nt, in
   __syncthreads();
   const C2<double>* Z = stockham_fft<double, MAXR>(pl, b0, b1, Q, nt, W);
   const double inv = 1.0 / nt;
-  double* dst = z + (long long)b * nt * ns;
-  for (int i = threadIdx.x; i < 2 * Q * nt; i += blockDim.x) {
-    const int l = i / nt, t = i - l * nt;
-    if (l >= nl) continue;
-    const int m = (t & 1) == 0 ? t / 2 : nt - 1 - (t - 1) / 2;
-    const C2<double> zm = Z[(l >> 1) * nt + m];
-    // v = conj(Z) / n: line a is the real part, line b the imaginary part
-    dst[(long long)(s0 + l) * nt + t] = (l & 1) == 0 ? zm.x * inv : -zm.y * inv;
+  double* dst = out + (long long)(b / ob.nper) * ob.rhs_stride + ob.off[b % ob.nper];
+  // v = conj(Z) / n: line 2q is the real part, line 2q + 1 the imaginary part
+  if (L.st == 1) {
+    for (int i = threadIdx.x; i < 2 * Q * nt; i += blockDim.x) {
+      const int l = i / nt, t = i - l * nt;
+      if (l >= nl) continue;
+      const C2<double> zm = Z[(l >> 1) * nt + makhoul_slot(t, nt)];
+      dst[t + (long long)(s0 + l) * L.ss] = (l & 1) == 0 ? zm.x * inv : -zm.y * inv;
+    }
+  } else {
+    for (int i = threadIdx.x; i < 2 * Q * nt; i += blockDim.x) {
+      const int t = i / (2 * Q), l = i - t * (2 * Q);
+      if (l >= nl) continue;
+      const C2<double> zm = Z[(l >> 1) * nt + makhoul_slot(t, nt)];
+      dst[(long long)t * L.st + (long long)(s0 + l) * L.ss] = (l & 1) == 0 ? zm.x * inv : -zm.y * inv;
+    }
   }
 }
 
 template <int MAXR>
-cudaError_t nm_launch(const double* v, double* z, double* scratch, int nt, int ns, const DstPlan& pl,
-                      const C2<double>* W, const C2<double>* post, const double* rpiv, const double* mneg, int nvec,
-                      cudaStream_t st) {
+cudaError_t nm_launch(const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib, double* out,
+                      BatchDesc ob, int nblk, double* scratch, const int* active, int nper_active, cudaStream_t st) {
+  const int nt = L.nt;
   const int Q = nm_pairs(nt);
   const size_t smem = nm_smem(nt, Q);
   static bool attr = false;
@@ -169,21 +200,86 @@ cudaError_t nm_launch(const double* v, double* z, double* scratch, int nt, int n
     cudaFuncSetAttribute(k_dct_inv<MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  const dim3 grid((ns + 2 * Q - 1) / (2 * Q), nvec);
-  k_dct_fwd<MAXR><<<grid, kNmThreads, smem, st>>>(v, scratch, nt, ns, pl, W, post, Q);
+  const C2<double>* W = reinterpret_cast<const C2<double>*>(tb.plan.W);
+  const C2<double>* post = reinterpret_cast<const C2<double>*>(tb.post);
+  const dim3 grid((L.ns + 2 * Q - 1) / (2 * Q), nblk);
+  k_dct_fwd<MAXR><<<grid, kNmThreads, smem, st>>>(in, ib, L, tb.plan, W, post, scratch, Q, active, nper_active);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_thomas_any(64, scratch, nt, ns, rpiv, mneg, nvec, st);
+  e = launch_thomas_any(64, scratch, nt, L.ns, tb.rpiv, tb.mneg, nblk, active, nper_active, st, tb.mt);
   if (e != cudaSuccess) return e;
-  k_dct_inv<MAXR><<<grid, kNmThreads, smem, st>>>(scratch, z, nt, ns, pl, W, post, Q);
+  k_dct_inv<MAXR><<<grid, kNmThreads, smem, st>>>(scratch, out, ob, L, tb.plan, W, post, Q, active, nper_active);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+// DCT-II plan of length n (Stockham, radices 4, 2 and odd primes to 13); false
+// when n is odd or has another prime factor.  Tables are not touched.
+bool dct_plan_shape(int n, DstPlan* pl) {
+  *pl = DstPlan{};
+  if (n < 2 || (n & 1) || n > 2048) return false;
+  pl->n = n;
+  pl->p = n;
+  pl->mode = DST_STOCKHAM;
+  pl->N = n;
+  return dct_radices(n, pl->rad, &pl->nrad) && plan_maxr(*pl) <= 13;
+}
+
+// Host tables of the DCT-II lines: W[m] = e^{-2 pi i m/n}, post[k] = e^{-i pi k/(2n)}
+// (interleaved re, im; n entries each).
+void dct_tables(int n, std::vector<double>& W, std::vector<double>& post) {
+  const double pi = 3.14159265358979323846;
+  W.resize(2 * n);
+  post.resize(2 * n);
+  for (int i = 0; i < n; ++i) {
+    const double a = 2.0 * pi * (double)i / n;
+    W[2 * i] = std::cos(a);
+    W[2 * i + 1] = -std::sin(a);
+    const double b = pi * (double)i / (2.0 * n);
+    post[2 * i] = std::cos(b);
+    post[2 * i + 1] = -std::sin(b);
+  }
+}
+
+// Reciprocal Thomas pivots r[k][s] and m = -delta r of the mode-k sweeps along
+// s of a block with Neumann ends along t:  tridiag(delta, -2 delta + mu_k + kappa,
+// delta), mu_k = -4 delta sin^2(k pi/(2n)), with `end_extra` added to the
+// diagonal of row 0 (end = 0) or of row ns-1 (end = 1) -- -delta for a
+// Dirichlet face half a cell beyond that row, 0 for a vertex-centred end.
+void dct_pivots(int nt, int ns, double delta, double kappa, double end_extra, int end, std::vector<double>& r,
+                std::vector<double>& m) {
+  const double pi = 3.14159265358979323846;
+  r.resize((size_t)nt * ns);
+  m.resize((size_t)nt * ns);
+  for (int k = 0; k < nt; ++k) {
+    const double sk = std::sin(pi * (double)k / (2.0 * nt));
+    const double d = -2.0 * delta - 4.0 * delta * sk * sk + kappa;
+    double* rk = r.data() + (size_t)k * ns;
+    double* mk = m.data() + (size_t)k * ns;
+    double rp = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      double ds = d;
+      if ((end == 0 && s == 0) || (end == 1 && s == ns - 1)) ds += end_extra;
+      rp = s == 0 ? 1.0 / ds : 1.0 / (ds - delta * delta * rp);
+      rk[s] = rp;
+      mk[s] = -delta * rp;
+    }
+  }
+}
+
+cudaError_t launch_fast_solve_dct(const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib,
+                                  double* out, BatchDesc ob, int nblk, double* scratch, const int* active,
+                                  int nper_active, cudaStream_t st) {
+  if (nblk <= 0) return cudaSuccess;
+  return plan_maxr(tb.plan) <= 5 ? nm_launch<5>(tb, L, in, ib, out, ob, nblk, scratch, active, nper_active, st)
+                                 : nm_launch<13>(tb, L, in, ib, out, ob, nblk, scratch, active, nper_active, st);
+}
+
 }  // namespace fpg
 
 extern "C" fpg_status fpg_neumann_workspace_bytes(int32_t nt, int32_t ns, int32_t nvec, size_t* bytes) {
-  if (!bytes || nt < 2 || (nt & 1) || ns < 1 || nvec < 1 || nt > 4096 || ns > 4096) return FPG_EINVAL;
+  if (!bytes || nt < 2 || (nt & 1) || ns < 1 || nvec < 1 || nt > 2048 || ns > 4096) return FPG_EINVAL;
   *bytes = fpg::nm_layout(nt, ns, nvec).total;
   return FPG_OK;
 }
@@ -191,49 +287,25 @@ extern "C" fpg_status fpg_neumann_workspace_bytes(int32_t nt, int32_t ns, int32_
 extern "C" fpg_status fpg_neumann_solve(int32_t nt, int32_t ns, double h, double kappa, const double* v, double* z,
                                         int32_t nvec, void* workspace, size_t bytes, void* stream) {
   using namespace fpg;
-  if (!v || !z || !workspace || nt < 2 || (nt & 1) || ns < 1 || nvec < 1 || nt > 4096 || ns > 4096 ||
+  if (!v || !z || !workspace || nt < 2 || (nt & 1) || ns < 1 || nvec < 1 || nt > 2048 || ns > 4096 ||
       !(h > 0.0) || !(kappa <= 0.0)) {
-    record_message("fpg_neumann_solve: bad argument (n_t even >= 2, n_s >= 1, h > 0, kappa <= 0, pointers)");
+    record_message("fpg_neumann_solve: bad argument (2 <= n_t <= 2048 even, 1 <= n_s <= 4096, h > 0, kappa <= 0)");
     return FPG_EINVAL;
   }
   const NmLayout L = nm_layout(nt, ns, nvec);
   if (bytes < L.total) return FPG_ENOMEM;
-  DstPlan pl{};
-  pl.n = nt;
-  pl.p = nt;
-  pl.mode = DST_STOCKHAM;
-  pl.N = nt;
-  if (!dct_radices(nt, pl.rad, &pl.nrad) || plan_maxr(pl) > 13) {
+  FastSolveTables tb{};
+  if (!dct_plan_shape(nt, &tb.plan)) {
     record_message("fpg_neumann_solve: n_t has a prime factor above 13");
     return FPG_EUNSUPPORTED;
   }
-  // tables: w_n^m, e^{-i pi k/(2n)}, and the reciprocal Thomas pivots of
-  // tridiag(delta, -2 delta + mu_k + kappa, delta) along s, laid out [k][s]
-  const double delta = 1.0 / (h * h);
-  const double pi = 3.14159265358979323846;
-  std::vector<double> W(2 * nt), post(2 * nt), r((size_t)nt * ns), m((size_t)nt * ns);
-  for (int i = 0; i < nt; ++i) {
-    const double a = 2.0 * pi * (double)i / nt;
-    W[2 * i] = std::cos(a);
-    W[2 * i + 1] = -std::sin(a);
-    const double b = pi * (double)i / (2.0 * nt);
-    post[2 * i] = std::cos(b);
-    post[2 * i + 1] = -std::sin(b);
-  }
-  for (int k = 0; k < nt; ++k) {
-    const double sk = std::sin(pi * (double)k / (2.0 * nt));
-    const double d = -2.0 * delta - 4.0 * delta * sk * sk + kappa;
-    double rp = 1.0 / d;
-    double* rk = r.data() + (size_t)k * ns;
-    double* mk = m.data() + (size_t)k * ns;
-    rk[0] = rp;
-    mk[0] = -delta * rp;
-    for (int s = 1; s < ns; ++s) {
-      rp = 1.0 / (d - delta * delta * rp);
-      rk[s] = rp;
-      mk[s] = -delta * rp;
-    }
-  }
+  tb.kind = 1;
+  tb.n = nt;
+  tb.ns = ns;
+  tb.delta = 1.0 / (h * h);
+  std::vector<double> W, post, r, m;
+  dct_tables(nt, W, post);
+  dct_pivots(nt, ns, tb.delta, kappa, 0.0, 0, r, m);
   cudaStream_t st = (cudaStream_t)stream;
   unsigned char* base = static_cast<unsigned char*>(workspace);
   // pageable sources: each copy has finished reading its host buffer on return
@@ -245,14 +317,14 @@ extern "C" fpg_status fpg_neumann_solve(int32_t nt, int32_t ns, double h, double
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(base + L.mneg, m.data(), sizeof(double) * m.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
-    pl.W = base + L.W;
-    const C2<double>* Wd = reinterpret_cast<const C2<double>*>(base + L.W);
-    const C2<double>* Pd = reinterpret_cast<const C2<double>*>(base + L.post);
-    double* scratch = reinterpret_cast<double*>(base + L.scratch);
-    const double* rd = reinterpret_cast<const double*>(base + L.rpiv);
-    const double* md = reinterpret_cast<const double*>(base + L.mneg);
-    e = plan_maxr(pl) <= 5 ? nm_launch<5>(v, z, scratch, nt, ns, pl, Wd, Pd, rd, md, nvec, st)
-                           : nm_launch<13>(v, z, scratch, nt, ns, pl, Wd, Pd, rd, md, nvec, st);
+    tb.plan.W = base + L.W;
+    tb.post = base + L.post;
+    tb.rpiv = base + L.rpiv;
+    tb.mneg = base + L.mneg;
+    const LineLayout LL{nt, ns, 1, nt};
+    const BatchDesc bd{(long long)nt * ns, {0, 0, 0, 0}, 1};
+    e = launch_fast_solve_dct(tb, LL, v, bd, z, bd, nvec, reinterpret_cast<double*>(base + L.scratch), nullptr, 1,
+                              st);
   }
   if (e != cudaSuccess) {
     record_cuda_error(e, "fpg_neumann_solve");

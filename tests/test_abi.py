@@ -49,7 +49,7 @@ def test_unknowns_and_workspace(lib, geom, arms):
 @pytest.mark.parametrize("field,value", [("n", 1), ("n", 5000), ("kappa", 1.0), ("nrhs", 0), ("restart", 0),
                                          ("restart", 500), ("rtol", 0.0), ("rtol", 1.0),
                                          ("precond_precision", 16), ("schur_mode", 7), ("geometry", 3),
-                                         ("max_iters", 0), ("reserved", 1)])
+                                         ("max_iters", 0), ("boundary", 2), ("boundary", -1)])
 def test_invalid_descriptors_rejected(lib, field, value):
     d = B.make_desc("cross", 16)
     setattr(d, field, value)
@@ -65,3 +65,16 @@ def test_create_rejects_small_workspace_without_touching_gpu(lib):
     # a dummy non-null address: the size check fails before any CUDA call
     st = lib.fpg_create_domain(ctypes.byref(d), 0x1000, 16, None, ctypes.byref(h))
     assert st == B.FPG_ENOMEM and not h.value
+
+
+def test_neumann_sided_cross_descriptor(lib):
+    """Sec. 3.1 boundary pattern: 5 n^2 unknowns on the cell-centred cross; other
+    geometries and lengths without a DCT-II plan are refused as unsupported."""
+    d = B.make_desc("cross", 64, -10.0, nrhs=2, boundary="neumann_sides")
+    assert B.unknowns(d) == 5 * 64 * 64
+    assert B.workspace_bytes(d) > 8 * 2 * (31 * 64 * 64 + 2 * B.unknowns(d))
+    for geom, n in (("T", 64), ("L", 64), ("cross", 63), ("cross", 34), ("cross", 4096)):
+        bad = B.make_desc(geom, n, boundary="neumann_sides")
+        with pytest.raises(B.FpgError) as e:
+            B.workspace_bytes(bad)
+        assert e.value.status == B.FPG_EUNSUPPORTED, (geom, n)

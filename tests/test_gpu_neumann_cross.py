@@ -1,0 +1,151 @@
+"""GPU parity of the Neumann-sided cross (Sec. 3.1 boundary pattern; Sec. 2.2
+DCT-II arm transform) against the oracle assembled from cell membership and
+face positions: the global operator, the arm fast solves, the Schur matvec in
+both forms, whole solves against K^{-1} f, the preconditioner's FP32 variant,
+and second-order convergence to the analytic solution.  Tolerances as in the
+Dirichlet parity tests."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import workloads as W
+from oracle import neumann_cross as X
+from oracle.schur import BlockSystem
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+BLOCKS = ["C", "W", "E", "S", "N"]
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def domain(B, n, kappa, **kw):
+    return B.Domain(B.make_desc("cross", n, kappa, boundary="neumann_sides", **kw))
+
+
+@pytest.mark.parametrize("n", [2, 8, 30, 64])
+def test_global_operator(lib, n):
+    from paper_2509_23180_gb300 import binding as B
+    K = X.assemble(n, -10.0)
+    d = domain(B, n, -10.0, nrhs=2)
+    p = W.random_block_vectors(2, K.shape[0], seed=n)
+    y = torch.zeros_like(dev(p))
+    d.apply_global(dev(p), y, 2)
+    assert rel(host(y), np.stack([K @ pi for pi in p])) < 1e-13
+
+
+@pytest.mark.parametrize("n,kappa", [(2, 0.0), (6, -10.0), (30, -3.0), (64, 0.0), (256, -10.0)])
+def test_arm_block_solves(lib, n, kappa):
+    """A_a^{-1} v on every arm (DCT-II lines, far end first in W and S and last in
+    E and N) and A_c^{-1} v on the centre, against sparse direct solves."""
+    from paper_2509_23180_gb300 import binding as B
+    K = X.assemble(n, kappa)
+    bs = BlockSystem(K, "cross", n, blocks=X.block_ranges(n))
+    d = domain(B, n, kappa, nrhs=2)
+    for blk, name in enumerate(BLOCKS):
+        v = W.random_block_vectors(3, n * n, seed=blk + 7 * n)
+        z = torch.zeros_like(dev(v))
+        d.block_solve(blk, dev(v), z, 3)
+        want = np.stack([bs.block_solve(name, vi) for vi in v])
+        assert rel(host(z), want) < 1e-11, name
+
+
+@pytest.mark.parametrize("mode", ["reduced", "literal"])
+@pytest.mark.parametrize("n,kappa", [(4, 0.0), (30, -10.0), (64, -3.0)])
+def test_schur_matvec(lib, mode, n, kappa):
+    """a2: the interface response of Neumann-sided arms (Toeplitz-plus-Hankel
+    table, or a literal DCT-II arm solve) against R_ca A_a^{-1} R_ac by sparse solves."""
+    from paper_2509_23180_gb300 import binding as B
+    K = X.assemble(n, kappa)
+    bs = BlockSystem(K, "cross", n, blocks=X.block_ranges(n))
+    d = domain(B, n, kappa, nrhs=3, schur_mode=mode)
+    zv = W.random_block_vectors(4, n * n, seed=5 * n)
+    w = torch.zeros((4, n * n), dtype=torch.float64, device="cuda")
+    d.apply_schur(dev(zv), 64, w, 4)
+    assert rel(host(w), np.stack([bs.schur_apply(zi) for zi in zv])) < 1e-11
+
+
+@pytest.mark.parametrize("mode", ["reduced", "literal"])
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("n,kappa", [(8, 0.0), (30, -10.0), (64, -10.0)])
+def test_solve_vs_direct(lib, mode, prec, n, kappa):
+    """Alg. 1 on the Neumann-sided cross reproduces K^{-1} f (rtol 1e-12)."""
+    from paper_2509_23180_gb300 import binding as B
+    K = X.assemble(n, kappa)
+    f = np.stack([W.ncross_fourier_rhs(n, s) for s in (0, 1)] + [W.ncross_validation_rhs(n, kappa)])
+    lu = spla.splu(K.tocsc())
+    d = domain(B, n, kappa, nrhs=3, rtol=1e-12, precond_precision=prec, schur_mode=mode)
+    d.set_rhs(dev(f))
+    p = torch.zeros_like(dev(f))
+    st, info = d.solve(p)
+    assert st == B.FPG_OK, info
+    P = host(p)
+    for r in range(3):
+        assert rel(P[r], lu.solve(f[r])) < 1e-9
+        assert info[r]["residual"] <= 1e-12
+        assert np.linalg.norm(f[r] - K @ P[r]) / np.linalg.norm(f[r]) <= 1.01e-12
+
+
+def test_iterations_match_oracle_algorithm1(lib):
+    """The GPU's FGMRES(m) takes the oracle's number of iterations (+-1) on the
+    Neumann-sided cross, n = 16."""
+    from oracle.schur import algorithm1
+    from paper_2509_23180_gb300 import binding as B
+    n, kappa = 16, 0.0
+    K = X.assemble(n, kappa)
+    f = W.ncross_validation_rhs(n, kappa)
+    bs = BlockSystem(K, "cross", n, blocks=X.block_ranges(n))
+    _, oinfo = algorithm1(bs, f, m=30, rtol=1e-10)
+    d = domain(B, n, kappa, nrhs=1, rtol=1e-10, restart=30)
+    d.set_rhs(dev(f[None, :]))
+    p = torch.zeros_like(dev(f[None, :]))
+    st, info = d.solve(p)
+    assert st == B.FPG_OK
+    assert abs(info[0]["iterations"] - oinfo["iterations"]) <= 1, (info[0], oinfo)
+
+
+def test_validation_case_second_order(lib):
+    """Sec. 3.1: the discrete solution converges to the analytic one like h^2
+    (n = 64, 128, 256, rtol 1e-12)."""
+    from paper_2509_23180_gb300 import binding as B
+    errs = []
+    for n in (64, 128, 256):
+        f = W.ncross_validation_rhs(n, 0.0)[None, :]
+        d = domain(B, n, 0.0, nrhs=1, rtol=1e-12)
+        d.set_rhs(dev(f))
+        p = torch.zeros_like(dev(f))
+        st, info = d.solve(p)
+        assert st == B.FPG_OK and info[0]["residual"] <= 1e-12
+        errs.append(np.abs(host(p)[0] - W.ncross_validation_solution(n)).max())
+    assert 3.9 < errs[0] / errs[1] < 4.1 and 3.9 < errs[1] / errs[2] < 4.1, errs
+
+
+def test_batch_and_graph_invariance(lib):
+    """A right-hand side gives the same answer alone and in a batch, with and
+    without CUDA graphs."""
+    from paper_2509_23180_gb300 import binding as B
+    n = 32
+    f = np.stack([W.ncross_fourier_rhs(n, s) for s in (3, 4, 5)])
+    d3 = domain(B, n, -10.0, nrhs=3, rtol=1e-12)
+    d3.set_rhs(dev(f))
+    p3 = torch.zeros_like(dev(f))
+    d3.solve(p3)
+    d1 = domain(B, n, -10.0, nrhs=1, rtol=1e-12)
+    d1.set_option(B.OPT_CUDA_GRAPHS, 0)
+    for r in range(3):
+        d1.set_rhs(dev(f[r:r + 1]))
+        p1 = torch.zeros_like(dev(f[r:r + 1]))
+        d1.solve(p1)
+        assert rel(host(p1)[0], host(p3)[r]) < 1e-11

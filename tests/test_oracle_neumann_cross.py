@@ -127,3 +127,13 @@ def test_algorithm1_on_the_neumann_cross():
     p, info = algorithm1(bs, f, m=20, rtol=1e-12)
     want = spla.spsolve(K.tocsc(), f)
     assert np.linalg.norm(p - want) / np.linalg.norm(want) < 1e-10
+
+
+def test_workload_generator_agrees_with_oracle():
+    """The input generator's restatement of the validation solution and source
+    (monomial form) equals the oracle's (Newton form) at every cell centre."""
+    import workloads as W
+    for n, kappa in ((6, 0.0), (16, -3.0)):
+        p, f = X.manufactured(n, kappa)
+        assert np.allclose(W.ncross_validation_rhs(n, kappa), f, rtol=1e-13, atol=1e-12)
+        assert np.allclose(W.ncross_validation_solution(n), p, rtol=1e-13, atol=1e-14)

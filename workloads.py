@@ -189,3 +189,68 @@ def fourier_rhs_torch(geometry: str, n: int, seed: int, device="cuda", modes: in
         w = torch.as_tensor(c / (kx ** 2 + ky ** 2), dtype=torch.float64, device=device)
         parts.append(torch.einsum("q,qy,qx->yx", w, sy, sx).reshape(-1))
     return torch.cat(parts)
+
+
+# ---- the Neumann-sided cross (cell-centred grid) -------------------------------
+# Boundary pattern of the paper's precision validation (Sec. 3.1): zero Dirichlet
+# at the far ends of the four arms (x = -1, x = 2, y = -1, y = 2), zero normal
+# derivative on the arms' sides.  Cell-centred grid, h = 1/n: every block holds
+# n x n cell centres, block order C, W, E, S, N, x fastest; block b covers the
+# unit square with lower-left corner NCROSS_CORNER[b].
+
+NCROSS_CORNER = {"C": (0, 0), "W": (-1, 0), "E": (1, 0), "S": (0, -1), "N": (0, 1)}
+
+
+def ncross_block_coords(name: str, n: int) -> tuple[np.ndarray, np.ndarray]:
+    """Cell centres x, y of one block of the Neumann-sided cross, shaped (n, n)."""
+    x0, y0 = NCROSS_CORNER[name]
+    c = (np.arange(n) + 0.5) / n
+    return np.meshgrid(x0 + c, y0 + c)
+
+
+def _ncross_psi(t):
+    """The cubic through (-1, 0), (0, pi/2), (1, 3 pi/2), (2, 2 pi) and its first
+    two derivatives (coefficients written out in powers of t)."""
+    a0, a1, a2, a3 = math.pi / 2, 11 * math.pi / 12, math.pi / 4, -math.pi / 6
+    return (a0 + t * (a1 + t * (a2 + t * a3)), a1 + t * (2 * a2 + 3 * a3 * t), 2 * a2 + 6 * a3 * t)
+
+
+def ncross_validation_solution(n: int) -> np.ndarray:
+    """p = sin(psi(x)) sin(psi(y)) at every cell centre, block order."""
+    parts = []
+    for b in ("C", "W", "E", "S", "N"):
+        x, y = ncross_block_coords(b, n)
+        parts.append((np.sin(_ncross_psi(x)[0]) * np.sin(_ncross_psi(y)[0])).ravel())
+    return np.concatenate(parts)
+
+
+def ncross_validation_rhs(n: int, kappa: float = 0.0) -> np.ndarray:
+    """f = lap(p) + kappa p of the validation solution, block order."""
+    parts = []
+    for b in ("C", "W", "E", "S", "N"):
+        x, y = ncross_block_coords(b, n)
+        px, dx, ddx = _ncross_psi(x)
+        py, dy, ddy = _ncross_psi(y)
+        sx, sy = np.sin(px), np.sin(py)
+        sxx = -sx * dx * dx + np.cos(px) * ddx
+        syy = -sy * dy * dy + np.cos(py) * ddy
+        parts.append((sxx * sy + sx * syy + kappa * sx * sy).ravel())
+    return np.concatenate(parts)
+
+
+def ncross_fourier_rhs(n: int, seed: int, modes: int = 16, kmax: int = 8) -> np.ndarray:
+    """The "fourier" workload on the cell-centred blocks (same draws per block)."""
+    parts = []
+    for b in ("C", "W", "E", "S", "N"):
+        rng = np.random.default_rng(seed * 1000 + BLOCK_ID[b])
+        kx = rng.integers(1, kmax + 1, size=modes)
+        ky = rng.integers(1, kmax + 1, size=modes)
+        c = rng.standard_normal(modes)
+        x, y = ncross_block_coords(b, n)
+        x0, y0 = NCROSS_CORNER[b]
+        xi, eta = x - x0, y - y0
+        f = np.zeros_like(x)
+        for q in range(modes):
+            f += c[q] * np.sin(kx[q] * math.pi * xi) * np.sin(ky[q] * math.pi * eta) / (kx[q] ** 2 + ky[q] ** 2)
+        parts.append(f.ravel())
+    return np.concatenate(parts)
