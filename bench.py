@@ -585,38 +585,54 @@ def run_extra(args):
             lines.append(line)
             d.close()
     elif args.config == "neumann":
-        # Sec. 2.2: the Neumann-rectangle fast solve on nvec rectangles of n x n
-        # (default 64 x 512^2: 128 MB in, 128 MB out; FP64 throughout)
-        n, nv = args.n, args.seeds
+        # Sec. 2.2: the DCT-II fast solve of Neumann-sided blocks, nvec = 2 * seeds
+        # blocks of n x n per call (default 20 x 256^2), FP64 throughout:
+        # (i) through a Neumann-sided cross domain's arm solve (tables built once;
+        #     S arm: lines contiguous along t, W arm: strided along t);
+        # (ii) the standalone fpg_neumann_solve (host tables rebuilt every call).
+        n, nv = args.n, 2 * args.seeds
         h, kappa = 1.0 / n, -10.0
         v = torch.as_tensor(W.random_block_vectors(nv, n * n, 9), device="cuda")
         z = torch.zeros_like(v)
-        for _ in range(args.warmup):
-            B.neumann_solve(v, z, n, n, h, kappa)
-        tot = 0.0
-        for s in range(args.steps):
-            flush.fill_(float(s))
-            ms, _, _ = _timed(lambda: B.neumann_solve(v, z, n, n, h, kappa))
-            tot += ms
-        ms = tot / args.steps
+        d = B.Domain(B.make_desc("cross", n, kappa, nrhs=args.seeds, restart=2, boundary="neumann_sides"))
         pts = nv * n * n
         peaks = measured_peaks()
         fp64 = B.probe_fma_peak(64)
-        dct_flops = 2 * 2.5 * np.log2(n) * pts + 5.0 * pts  # two transforms + Thomas
-        lines.append({"metric": "Neumann fast solves/s", "value": nv / (ms * 1e-3), "unit": "rectangles/s",
-                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        flops = 2 * 2.5 * np.log2(n) * pts + 5.0 * pts  # two transforms + Thomas
+        calls = {"arm_S_contiguous": lambda: d.block_solve(3, v, z, nv),
+                 "arm_W_strided": lambda: d.block_solve(1, v, z, nv),
+                 "standalone_tables_per_call": lambda: B.neumann_solve(v, z, n, n, h, kappa)}
+        res = {}
+        for name, fn in calls.items():
+            for _ in range(args.warmup):
+                fn()
+            tot = 0.0
+            for s in range(args.steps):
+                flush.fill_(float(s))
+                ms, _, _ = _timed(fn)
+                tot += ms
+            ms = tot / args.steps
+            res[name] = {"ms": ms, "blocks_per_s": nv / (ms * 1e-3), "fp64_frac": flops / (ms * 1e-3) / fp64,
+                         "hbm_gbs_algorithmic": 64 * pts / (ms * 1e-3) / 1e9}
+        d.close()
+        best = res["arm_S_contiguous"]
+        lines.append({"metric": "Neumann fast solves/s", "value": best["blocks_per_s"], "unit": "blocks/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms"],
                       "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-                      "config": {"workload": f"Neumann rectangle solve on {nv} x {n}^2 (Neumann across t, Dirichlet "
-                                             f"across s), kappa -10, tables rebuilt per call",
+                      "config": {"workload": f"DCT-II fast solve of {nv} Neumann-sided blocks of {n}^2 "
+                                             f"(k_dct_fwd, k_thomas_reg, k_dct_inv), kappa -10",
                                  "l2": "flushed before every step"},
-                      "algorithmic_bytes": 16 * pts, "hbm_gbs": 16 * pts / (ms * 1e-3) / 1e9,
-                      "hbm_frac": 16 * pts / (ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0),
-                      "fp64_frac": dct_flops / (ms * 1e-3) / fp64})
+                      "roofline": {"bound": "alu", "achieved": flops / (best["ms"] * 1e-3) / 1e12,
+                                   "peak": fp64 / 1e12, "unit": "TFLOP/s",
+                                   "frac": flops / (best["ms"] * 1e-3) / fp64,
+                                   "peak_source": "measured: library FP64 FMA probe on this GPU"},
+                      "algorithmic_bytes": 64 * pts, "hbm_peak_gbs": peaks.get("hbm_gbs"), "calls": res})
     elif args.config == "ncross":
         # Sec. 3.1 boundary pattern on the cross (Neumann arm sides, Dirichlet far
         # ends, cell-centred grid): (i) throughput on the bench shape, n^2 per
         # block, kappa in {0, -10}, `seeds` fourier RHS each, FGMRES(m);
-        # (ii) the validation case: error to the analytic solution over n (rtol 1e-12).
+        # (ii) the validation case: error to the analytic solution over n (rtol 1e-11,
+        #      so that the residual's share of the error stays below 1% of O(h^2)).
         n, m = args.n, args.restart
         doms = []
         for kappa in (0.0, -10.0):
@@ -646,7 +662,7 @@ def run_extra(args):
         errs = {}
         for nv in (64, 128, 256, 512):
             f = torch.as_tensor(W.ncross_validation_rhs(nv, 0.0)[None, :], device="cuda")
-            d = B.Domain(B.make_desc("cross", nv, 0.0, nrhs=1, restart=m, rtol=1e-12, boundary="neumann_sides"))
+            d = B.Domain(B.make_desc("cross", nv, 0.0, nrhs=1, restart=m, rtol=1e-11, boundary="neumann_sides"))
             d.set_rhs(f)
             p = torch.zeros_like(f)
             stt, info = d.solve(p, check=False)

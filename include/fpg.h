@@ -348,6 +348,23 @@ fpg_status fpg_neumann_workspace_bytes(int32_t nt, int32_t ns, int32_t nvec, siz
 fpg_status fpg_neumann_solve(int32_t nt, int32_t ns, double h, double kappa, const double* v, double* z,
                              int32_t nvec, void* workspace, size_t bytes, void* stream);
 
+/* Fast solve on periodic rectangles (Sec. 2.2, Eq. "submat_Periodic"):
+ * z = A_P^{-1} v, A_P = I (x) A_t^P + T_s (x) I + kappa I on an n_t x n_s grid
+ * (row-major, t fastest) with spacing h both ways: periodic along t
+ * (A_t^P = delta circ(-2, 1, 0, ..., 0, 1), delta = 1/h^2), Dirichlet ends along s.
+ * The real eigen-coordinates along t are the real and imaginary parts of each
+ * line's DFT (mode m: Re X_m for 2m <= n_t, Im X_m otherwise; eigenvalue
+ * -4 delta sin^2(pi m/n_t)), two lines per complex FFT; Thomas per mode along s;
+ * inverse.  FP64.  n_t with prime factors <= 13, 2 <= n_t <= 2048, 1 <= n_s <= 4096.
+ * v, z: device pointers to nvec blocks of n_t * n_s doubles (may not alias);
+ * workspace: device, >= fpg_periodic_workspace_bytes(n_t, n_s, nvec) bytes,
+ * caller-owned; tables are rebuilt on the host at every call.
+ * Errors: FPG_EINVAL (sizes, h <= 0, kappa > 0, null pointers), FPG_ENOMEM
+ * (workspace short), FPG_EUNSUPPORTED (n_t has a prime factor above 13), FPG_ECUDA. */
+fpg_status fpg_periodic_workspace_bytes(int32_t nt, int32_t ns, int32_t nvec, size_t* bytes);
+fpg_status fpg_periodic_solve(int32_t nt, int32_t ns, double h, double kappa, const double* v, double* z,
+                              int32_t nvec, void* workspace, size_t bytes, void* stream);
+
 /* Element-wise conversion between FP64 and FP32 on the device, done with the
  * integer-pipe routines of the mixed-precision path (GB300 runs the hardware
  * conversion on its FP64 pipe).  (in_prec, out_prec) is (64, 32): round to

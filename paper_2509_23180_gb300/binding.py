@@ -102,6 +102,8 @@ _SIGS = {
     "fpg_convert": ([_P, _I32, _P, _I32, _I64, _P], _I32),
     "fpg_neumann_workspace_bytes": ([_I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)], _I32),
     "fpg_neumann_solve": ([_I32, _I32, _D, _D, _P, _P, _I32, _P, ctypes.c_size_t, _P], _I32),
+    "fpg_periodic_workspace_bytes": ([_I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)], _I32),
+    "fpg_periodic_solve": ([_I32, _I32, _D, _D, _P, _P, _I32, _P, ctypes.c_size_t, _P], _I32),
     "fpg_probe_fma_peak": ([_I32, ctypes.POINTER(_D)], _I32),
     "fpg_fast_solve_noalloc": ([_I32, _D, _P, _P, _I32, _P], _I32),
 }
@@ -338,3 +340,18 @@ def probe_fma_peak(precision: int = 64) -> float:
     out = _D()
     _check(load().fpg_probe_fma_peak(precision, ctypes.byref(out)), "fpg_probe_fma_peak")
     return float(out.value)
+
+
+def periodic_solve(v, z, nt: int, ns: int, h: float, kappa: float, stream=None):
+    """fpg_periodic_solve on nvec = v.shape[0] periodic rectangles (CUDA float64
+    tensors of shape (nvec, nt * ns)); the workspace is a torch uint8 tensor."""
+    import torch
+    lib = load()
+    nvec = v.shape[0]
+    nb = ctypes.c_size_t()
+    _check(lib.fpg_periodic_workspace_bytes(nt, ns, nvec, ctypes.byref(nb)), "fpg_periodic_workspace_bytes")
+    ws = torch.empty(nb.value, dtype=torch.uint8, device=v.device)
+    st = stream if stream is not None else torch.cuda.current_stream(v.device)
+    _check(lib.fpg_periodic_solve(nt, ns, h, kappa, _ptr(v), _ptr(z), nvec, _ptr(ws), nb.value, st.cuda_stream),
+           "fpg_periodic_solve")
+    return ws

@@ -568,15 +568,20 @@ cudaError_t launch_thomas_any(int prec, void* scratch, int n, int ns, const void
 cudaError_t launch_fast_solve_dct(const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib,
                                   double* out, BatchDesc ob, int nblk, double* scratch, const int* active,
                                   int nper_active, cudaStream_t st);
+cudaError_t launch_fast_solve_rdft(const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib,
+                                   double* out, BatchDesc ob, int nblk, double* scratch, const int* active,
+                                   int nper_active, cudaStream_t st);
 
 // Which kernels the fast solve of this block kind runs: 0 generic FFT engine
 // (k_fft_forward / k_thomas_reg / k_fft_inverse), 1 size-specialised
 // (k_dst_lines_fwd / k_thomas_reg / k_dst_lines_inv), 2 dense DST, 3 the fused
 // one-pass cluster kernel, 4 the DCT-II lines of a Neumann-sided block
-// (k_dct_fwd / k_thomas_reg / k_dct_inv).
+// (k_dct_fwd / k_thomas_reg / k_dct_inv), 5 the real-DFT lines of a periodic
+// block (k_rdft_fwd / k_thomas_reg / k_rdft_inv).
 bool fast_solve_fused_fits(int prec, const FastSolveTables& tb, LineLayout L);
 int fast_solve_path(int prec, const FastSolveTables& tb, LineLayout L, int nblk) {
   if (tb.kind == 1) return 4;
+  if (tb.kind == 2) return 5;
   if (tb.fused && fast_solve_fused_fits(prec, tb, L)) return 3;
   if (tb.plan.mode == DST_DENSE) return 2;
   const bool special = prec == 64 ? lines_engine<double>(tb.plan.p, nblk, L.ns, tb.generic)
@@ -594,10 +599,14 @@ cudaError_t launch_fast_solve(int prec, int out_prec, const FastSolveTables& tb,
                               void* scratch, const int* active, int nper_active, cudaStream_t st,
                               int* launches, cudaEvent_t* ev) {
   if (nblk <= 0) return cudaSuccess;
-  if (tb.kind == 1) {  // DCT-II along t (Neumann ends): FP64 only
+  if (tb.kind == 1 || tb.kind == 2) {  // DCT-II (Neumann ends) or real DFT (periodic) along t: FP64 only
     if (prec != 64 || out_prec != 64) return cudaErrorNotSupported;
     if (launches) *launches += 3;
-    return launch_fast_solve_dct(tb, L, in, ib, (double*)out, ob, nblk, (double*)scratch, active, nper_active, st);
+    return tb.kind == 1
+               ? launch_fast_solve_dct(tb, L, in, ib, (double*)out, ob, nblk, (double*)scratch, active, nper_active,
+                                       st)
+               : launch_fast_solve_rdft(tb, L, in, ib, (double*)out, ob, nblk, (double*)scratch, active, nper_active,
+                                        st);
   }
   if (tb.fused) {
     if (ev) record_event(ev[6], st);

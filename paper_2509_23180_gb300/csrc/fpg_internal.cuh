@@ -41,7 +41,8 @@ struct FastSolveTables {
   int fused = 0;      // 1: one-pass cluster kernel when the block fits
   int generic = 0;    // DST engine: 0 auto, 1 generic FFT engine, 2 size-specialised where compiled
   int bulk = 0;       // 1: FP32 forward DST as the persistent kernel with bulk asynchronous row copies
-  int kind = 0;       // transform along t: 0 DST-I (Dirichlet ends), 1 DCT-II (Neumann ends, FP64 only)
+  int kind = 0;       // transform along t: 0 DST-I (Dirichlet ends), 1 DCT-II (Neumann ends), 2 real DFT
+                      // (periodic); 1 and 2 FP64 only
   const void* post = nullptr;  // DCT-II: e^{-i pi k/(2n)}, k < n (complex, FP64)
 };
 

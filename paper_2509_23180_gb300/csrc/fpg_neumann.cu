@@ -13,6 +13,16 @@
 //     delta) along s (k_thomas_reg of the Dirichlet path, its own pivot tables);
 //   * the inverse: V_k = e^{i pi k/(2n)} (X_k - i X_{n-k}) (X_n = 0), v = IDFT(V),
 //     x_{2m} = v_m, x_{2m+1} = v_{n-1-m} -- the exact inverse of the forward map.
+//
+// Periodic rectangles (Sec. 2.2, Eq. "submat_Periodic"): periodic along t,
+// Dirichlet across s.  The circulant line operator has mu_k = -4 delta sin^2(pi k/n_t)
+// with mu_k = mu_{n-k}; the real eigenbasis pairs frequencies k and n-k (the
+// paper's Q_P, a Hartley-type basis).  Here the same real modes are the real and
+// imaginary parts of the line's DFT: mode m holds Re X_m for 2m <= n_t and
+// Im X_m otherwise, each a real eigen-coordinate with eigenvalue mu_m.  Two real
+// lines share one complex FFT forward and one inverse, with the Thomas solves of
+// the DCT-II path in between.
+
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -188,6 +198,129 @@ k_dct_inv(const double* __restrict__ scratch, double* __restrict__ out, BatchDes
   }
 }
 
+// Forward real DFT of the lines of a batch of blocks (periodic along t): mode m
+// of line s gets Re X_m (2m <= n) or Im X_m (2m > n), X = DFT_n(x), written to
+// scratch[b][m][s].
+template <int MAXR>
+__global__ void __launch_bounds__(kNmThreads)
+k_rdft_fwd(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPlan pl, const C2<double>* __restrict__ Wg,
+           double* __restrict__ scratch, int Q, const int* __restrict__ active, int nper_active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.y;
+  if (active != nullptr && !active[b / nper_active]) return;
+  const int nt = L.nt, ns = L.ns;
+  C2<double>* b0 = reinterpret_cast<C2<double>*>(smem_raw);
+  C2<double>* b1 = b0 + (size_t)Q * nt;
+  C2<double>* W = b1 + (size_t)Q * nt;
+  double* b0d = reinterpret_cast<double*>(b0);
+  const int s0 = blockIdx.x * 2 * Q, nl = min(2 * Q, ns - s0);
+  for (int i = threadIdx.x; i < nt; i += blockDim.x) W[i] = Wg[i];
+  const double* src = in + (long long)(b / ib.nper) * ib.rhs_stride + ib.off[b % ib.nper];
+  if (L.st == 1) {
+    for (int i = threadIdx.x; i < 2 * Q * nt; i += blockDim.x) {
+      const int l = i / nt, t = i - l * nt;
+      b0d[2 * ((l >> 1) * nt + t) + (l & 1)] = l < nl ? src[t + (long long)(s0 + l) * L.ss] : 0.0;
+    }
+  } else {
+    for (int i = threadIdx.x; i < 2 * Q * nt; i += blockDim.x) {
+      const int t = i / (2 * Q), l = i - t * (2 * Q);
+      b0d[2 * ((l >> 1) * nt + t) + (l & 1)] = l < nl ? src[(long long)t * L.st + (long long)(s0 + l) * L.ss] : 0.0;
+    }
+  }
+  __syncthreads();
+  const C2<double>* Z = stockham_fft<double, MAXR>(pl, b0, b1, Q, nt, W);
+  double* dst = scratch + (long long)b * nt * ns + s0;
+  for (int i = threadIdx.x; i < Q * nt; i += blockDim.x) {
+    const int k = i / Q, q = i - k * Q;
+    const C2<double> zk = Z[q * nt + k], zc = Z[q * nt + (k == 0 ? 0 : nt - k)];
+    const C2<double> va{0.5 * (zk.x + zc.x), 0.5 * (zk.y - zc.y)};   // DFT of line 2q at k
+    const C2<double> vb{0.5 * (zk.y + zc.y), -0.5 * (zk.x - zc.x)};  // DFT of line 2q+1 at k
+    const bool re = 2 * k <= nt;
+    const int la = 2 * q;
+    if (la < nl) dst[(long long)k * ns + la] = re ? va.x : va.y;
+    if (la + 1 < nl) dst[(long long)k * ns + la + 1] = re ? vb.x : vb.y;
+  }
+}
+
+// Inverse of k_rdft_fwd: rebuild each line's Hermitian spectrum from its real
+// modes (Re X_k = Y_min(k,n-k); Im X_k = Y_k for 2k > n, -Y_{n-k} for 0 < 2k < n,
+// 0 for k = 0 and 2k = n), x = IDFT(X), written into the batch layout of `out`.
+template <int MAXR>
+__global__ void __launch_bounds__(kNmThreads)
+k_rdft_inv(const double* __restrict__ scratch, double* __restrict__ out, BatchDesc ob, LineLayout L, DstPlan pl,
+           const C2<double>* __restrict__ Wg, int Q, const int* __restrict__ active, int nper_active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.y;
+  if (active != nullptr && !active[b / nper_active]) return;
+  const int nt = L.nt, ns = L.ns;
+  C2<double>* b0 = reinterpret_cast<C2<double>*>(smem_raw);
+  C2<double>* b1 = b0 + (size_t)Q * nt;
+  C2<double>* W = b1 + (size_t)Q * nt;
+  double* X = reinterpret_cast<double*>(b1);  // [2Q][nt] real modes, staged
+  const int s0 = blockIdx.x * 2 * Q, nl = min(2 * Q, ns - s0);
+  for (int i = threadIdx.x; i < nt; i += blockDim.x) W[i] = Wg[i];
+  const double* src = scratch + (long long)b * nt * ns + s0;
+  for (int i = threadIdx.x; i < 2 * Q * nt; i += blockDim.x) {
+    const int k = i / (2 * Q), l = i - k * (2 * Q);
+    X[l * nt + k] = l < nl ? src[(long long)k * ns + l] : 0.0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < Q * nt; i += blockDim.x) {
+    const int q = i / nt, k = i - q * nt;
+    const double* ya = X + (2 * q) * nt;
+    const double* yb = ya + nt;
+    const int kr = 2 * k <= nt ? k : nt - k;
+    const bool zero_im = k == 0 || 2 * k == nt;
+    const double ra = ya[kr], rb = yb[kr];
+    const double ia = zero_im ? 0.0 : (2 * k > nt ? ya[k] : -ya[nt - k]);
+    const double ib = zero_im ? 0.0 : (2 * k > nt ? yb[k] : -yb[nt - k]);
+    // packed spectrum A + i B, conjugated: the inverse DFT as a forward one
+    b0[i] = C2<double>{ra - ib, -(ia + rb)};
+  }
+  __syncthreads();
+  const C2<double>* Z = stockham_fft<double, MAXR>(pl, b0, b1, Q, nt, W);
+  const double inv = 1.0 / nt;
+  double* dst = out + (long long)(b / ob.nper) * ob.rhs_stride + ob.off[b % ob.nper];
+  if (L.st == 1) {
+    for (int i = threadIdx.x; i < 2 * Q * nt; i += blockDim.x) {
+      const int l = i / nt, t = i - l * nt;
+      if (l >= nl) continue;
+      const C2<double> zm = Z[(l >> 1) * nt + t];
+      dst[t + (long long)(s0 + l) * L.ss] = (l & 1) == 0 ? zm.x * inv : -zm.y * inv;
+    }
+  } else {
+    for (int i = threadIdx.x; i < 2 * Q * nt; i += blockDim.x) {
+      const int t = i / (2 * Q), l = i - t * (2 * Q);
+      if (l >= nl) continue;
+      const C2<double> zm = Z[(l >> 1) * nt + t];
+      dst[(long long)t * L.st + (long long)(s0 + l) * L.ss] = (l & 1) == 0 ? zm.x * inv : -zm.y * inv;
+    }
+  }
+}
+
+template <int MAXR>
+cudaError_t pd_launch(const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib, double* out,
+                      BatchDesc ob, int nblk, double* scratch, const int* active, int nper_active, cudaStream_t st) {
+  const int nt = L.nt;
+  const int Q = nm_pairs(nt);
+  const size_t smem = nm_smem(nt, Q);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_rdft_fwd<MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_rdft_inv<MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  const C2<double>* W = reinterpret_cast<const C2<double>*>(tb.plan.W);
+  const dim3 grid((L.ns + 2 * Q - 1) / (2 * Q), nblk);
+  k_rdft_fwd<MAXR><<<grid, kNmThreads, smem, st>>>(in, ib, L, tb.plan, W, scratch, Q, active, nper_active);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_thomas_any(64, scratch, nt, L.ns, tb.rpiv, tb.mneg, nblk, active, nper_active, st, tb.mt);
+  if (e != cudaSuccess) return e;
+  k_rdft_inv<MAXR><<<grid, kNmThreads, smem, st>>>(scratch, out, ob, L, tb.plan, W, Q, active, nper_active);
+  return cudaGetLastError();
+}
+
 template <int MAXR>
 cudaError_t nm_launch(const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib, double* out,
                       BatchDesc ob, int nblk, double* scratch, const int* active, int nper_active, cudaStream_t st) {
@@ -226,6 +359,26 @@ bool dct_plan_shape(int n, DstPlan* pl) {
   return dct_radices(n, pl->rad, &pl->nrad) && plan_maxr(*pl) <= 13;
 }
 
+// Real-DFT plan of length n (periodic lines): any n >= 2 whose prime factors are
+// at most 13, n <= 2048.
+bool rdft_plan_shape(int n, DstPlan* pl) {
+  *pl = DstPlan{};
+  if (n < 2 || n > 2048) return false;
+  pl->n = n;
+  pl->p = n;
+  pl->mode = DST_STOCKHAM;
+  pl->N = n;
+  return dct_radices(n, pl->rad, &pl->nrad) && plan_maxr(*pl) <= 13;
+}
+
+cudaError_t launch_fast_solve_rdft(const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib,
+                                   double* out, BatchDesc ob, int nblk, double* scratch, const int* active,
+                                   int nper_active, cudaStream_t st) {
+  if (nblk <= 0) return cudaSuccess;
+  return plan_maxr(tb.plan) <= 5 ? pd_launch<5>(tb, L, in, ib, out, ob, nblk, scratch, active, nper_active, st)
+                                 : pd_launch<13>(tb, L, in, ib, out, ob, nblk, scratch, active, nper_active, st);
+}
+
 // Host tables of the DCT-II lines: W[m] = e^{-2 pi i m/n}, post[k] = e^{-i pi k/(2n)}
 // (interleaved re, im; n entries each).
 void dct_tables(int n, std::vector<double>& W, std::vector<double>& post) {
@@ -262,6 +415,26 @@ void dct_pivots(int nt, int ns, double delta, double kappa, double end_extra, in
       double ds = d;
       if ((end == 0 && s == 0) || (end == 1 && s == ns - 1)) ds += end_extra;
       rp = s == 0 ? 1.0 / ds : 1.0 / (ds - delta * delta * rp);
+      rk[s] = rp;
+      mk[s] = -delta * rp;
+    }
+  }
+}
+
+// Pivots of the periodic lines: mode m has mu_m = -4 delta sin^2(pi m/n), plain
+// Dirichlet ends along s.
+void rdft_pivots(int nt, int ns, double delta, double kappa, std::vector<double>& r, std::vector<double>& m) {
+  const double pi = 3.14159265358979323846;
+  r.resize((size_t)nt * ns);
+  m.resize((size_t)nt * ns);
+  for (int k = 0; k < nt; ++k) {
+    const double sk = std::sin(pi * (double)k / nt);
+    const double d = -2.0 * delta - 4.0 * delta * sk * sk + kappa;
+    double* rk = r.data() + (size_t)k * ns;
+    double* mk = m.data() + (size_t)k * ns;
+    double rp = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      rp = s == 0 ? 1.0 / d : 1.0 / (d - delta * delta * rp);
       rk[s] = rp;
       mk[s] = -delta * rp;
     }
@@ -328,6 +501,57 @@ extern "C" fpg_status fpg_neumann_solve(int32_t nt, int32_t ns, double h, double
   }
   if (e != cudaSuccess) {
     record_cuda_error(e, "fpg_neumann_solve");
+    return FPG_ECUDA;
+  }
+  return FPG_OK;
+}
+
+extern "C" fpg_status fpg_periodic_workspace_bytes(int32_t nt, int32_t ns, int32_t nvec, size_t* bytes) {
+  if (!bytes || nt < 2 || ns < 1 || nvec < 1 || nt > 2048 || ns > 4096) return FPG_EINVAL;
+  *bytes = fpg::nm_layout(nt, ns, nvec).total;
+  return FPG_OK;
+}
+
+extern "C" fpg_status fpg_periodic_solve(int32_t nt, int32_t ns, double h, double kappa, const double* v, double* z,
+                                         int32_t nvec, void* workspace, size_t bytes, void* stream) {
+  using namespace fpg;
+  if (!v || !z || !workspace || nt < 2 || ns < 1 || nvec < 1 || nt > 2048 || ns > 4096 || !(h > 0.0) ||
+      !(kappa <= 0.0)) {
+    record_message("fpg_periodic_solve: bad argument (2 <= n_t <= 2048, 1 <= n_s <= 4096, h > 0, kappa <= 0)");
+    return FPG_EINVAL;
+  }
+  const NmLayout L = nm_layout(nt, ns, nvec);
+  if (bytes < L.total) return FPG_ENOMEM;
+  FastSolveTables tb{};
+  if (!rdft_plan_shape(nt, &tb.plan)) {
+    record_message("fpg_periodic_solve: n_t has a prime factor above 13");
+    return FPG_EUNSUPPORTED;
+  }
+  tb.kind = 2;
+  tb.n = nt;
+  tb.ns = ns;
+  tb.delta = 1.0 / (h * h);
+  std::vector<double> W, post, r, m;
+  dct_tables(nt, W, post);
+  rdft_pivots(nt, ns, tb.delta, kappa, r, m);
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* base = static_cast<unsigned char*>(workspace);
+  cudaError_t e = cudaMemcpyAsync(base + L.W, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + L.rpiv, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + L.mneg, m.data(), sizeof(double) * m.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    tb.plan.W = base + L.W;
+    tb.rpiv = base + L.rpiv;
+    tb.mneg = base + L.mneg;
+    const LineLayout LL{nt, ns, 1, nt};
+    const BatchDesc bd{(long long)nt * ns, {0, 0, 0, 0}, 1};
+    e = launch_fast_solve_rdft(tb, LL, v, bd, z, bd, nvec, reinterpret_cast<double*>(base + L.scratch), nullptr, 1,
+                               st);
+  }
+  if (e != cudaSuccess) {
+    record_cuda_error(e, "fpg_periodic_solve");
     return FPG_ECUDA;
   }
   return FPG_OK;
