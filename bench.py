@@ -47,7 +47,7 @@ def parse():
                     help="solve the two kappa domains one after the other, or concurrently on two streams")
     ap.add_argument("--config", default="default",
                     choices=["default", "small", "precision", "batching", "serving", "fastsolve", "study",
-                             "neumann", "ncross"],
+                             "neumann", "ncross", "rect"],
                     help="default: the 256^2 cross workload; the others run the other workloads as extra lines")
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
@@ -627,6 +627,35 @@ def run_extra(args):
                                    "frac": flops / (best["ms"] * 1e-3) / fp64,
                                    "peak_source": "measured: library FP64 FMA probe on this GPU"},
                       "algorithmic_bytes": 64 * pts, "hbm_peak_gbs": peaks.get("hbm_gbs"), "calls": res})
+    elif args.config == "rect":
+        # Sec. 2.1-2.2: rectangle fast-solve plans for the three line transforms
+        # (DST-I Dirichlet, DCT-II Neumann, real DFT periodic), 2 * seeds blocks of
+        # n x n per call (default 20 x 256^2), tables built once per plan, FP64.
+        n, nv = args.n, 2 * args.seeds
+        v = torch.as_tensor(W.random_block_vectors(nv, n * n, 5), device="cuda")
+        z = torch.zeros_like(v)
+        fp64 = B.probe_fma_peak(64)
+        pts = nv * n * n
+        flops = 2 * 2.5 * np.log2(n) * pts + 5.0 * pts
+        for kind in ("dirichlet", "neumann", "periodic"):
+            plan = B.RectPlan(kind, n, n, 1.0 / n, -10.0, nv)
+            for _ in range(args.warmup):
+                plan.solve(v, z, nv)
+            tot = 0.0
+            for s in range(args.steps):
+                flush.fill_(float(s))
+                ms, _, _ = _timed(lambda: plan.solve(v, z, nv))
+                tot += ms
+            plan.close()
+            ms = tot / args.steps
+            lines.append({"metric": "rectangle fast solves/s", "value": nv / (ms * 1e-3), "unit": "blocks/s",
+                          "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                          "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": f"{kind} rectangle fast solve, {nv} blocks of {n}^2, kappa -10",
+                                     "kind": kind, "l2": "flushed before every step"},
+                          "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp64 / 1e12,
+                                       "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / fp64,
+                                       "peak_source": "measured: library FP64 FMA probe on this GPU"}})
     elif args.config == "ncross":
         # Sec. 3.1 boundary pattern on the cross (Neumann arm sides, Dirichlet far
         # ends, cell-centred grid): (i) throughput on the bench shape, n^2 per

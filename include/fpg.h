@@ -330,37 +330,65 @@ fpg_status fpg_phase_stats(fpg_domain* d, int32_t phase, int64_t* launches, doub
 /* Total kernel launches issued by the library on this domain so far. */
 fpg_status fpg_launch_count(fpg_domain* d, int64_t* launches);
 
-/* ---- Neumann rectangles (Sec. 2.2, Eq. "submat_Neumann") --------------------
- * z = A_N^{-1} v for nvec rectangles of n_t x n_s points (row-major, t fastest,
- * FP64, device pointers): zero normal derivative on the two edges across t
- * (the first and last rows of the t-line operator lose one delta: a ghost node
- * equal to its neighbour, cell-centred points), homogeneous Dirichlet on the
- * edges across s, spacing h both ways (delta = 1/h^2), kappa <= 0 on the
- * diagonal.  Computed as a DCT-II along t (the eigenbasis cos(k pi (j-1/2)/n_t),
- * eigenvalues -4 delta sin^2(k pi/(2 n_t))), one Thomas solve per mode along s
- * and the inverse DCT.  n_t even, prime factors of n_t at most 13,
- * 2 <= n_t <= 2048 (the shared-memory line batch), 1 <= n_s <= 4096.  The caller owns `workspace` (device, >=
- * fpg_neumann_workspace_bytes); the tables are rebuilt on the host and copied
- * in on every call.  Runs on `stream` (a cudaStream_t, NULL = default).
- * Errors: FPG_EINVAL (arguments), FPG_ENOMEM (workspace too small),
- * FPG_EUNSUPPORTED (n_t has a larger prime factor), FPG_ECUDA. */
+/* ---- rectangle fast solves (Sec. 2.1-2.2) ----------------------------------
+ * z = A^{-1} v for nvec rectangles of n_t x n_s points (row-major, t fastest,
+ * FP64, device pointers; v and z may not alias), spacing h both ways
+ * (delta = 1/h^2), kappa <= 0 on the diagonal, homogeneous Dirichlet ends along
+ * s (vertex-centred: the zero neighbours sit one step beyond rows 0 and n_s-1).
+ * Along t, by kind:
+ *   FPG_RECT_DIRICHLET: zero neighbours one step beyond both ends; DST-I
+ *     (Eq. "Dirichlet_mat_decomp"), eigenvalues -4 delta sin^2(k pi/(2(n_t+1))),
+ *     k = 1..n_t; 2 <= n_t <= 4096 (the solver's own engine: any length).
+ *   FPG_RECT_NEUMANN (Eq. "submat_Neumann"): zero normal derivative half a step
+ *     beyond both ends (the first and last rows lose one delta: cell-centred
+ *     points); DCT-II, basis cos(k pi (j-1/2)/n_t), eigenvalues
+ *     -4 delta sin^2(k pi/(2 n_t)), k = 0..n_t-1; n_t even, 2 <= n_t <= 2048.
+ *   FPG_RECT_PERIODIC (Eq. "submat_Periodic"): t wraps around (circulant);
+ *     real modes = Re and Im of each line's DFT (mode m: Re X_m for 2m <= n_t,
+ *     Im X_m otherwise), eigenvalues -4 delta sin^2(pi m/n_t); 2 <= n_t <= 2048.
+ *   Neumann and periodic need n_t with prime factors <= 13 (FPG_EUNSUPPORTED).
+ * Each solve is the transform along t (two real lines per complex FFT), one
+ * Thomas solve per mode along s, and the inverse transform; 1 <= n_s <= 4096.
+ *
+ * A plan holds the tables (built on the host in FP64 and copied once) and the
+ * scratch for up to nvec rectangles in the caller's device workspace (>=
+ * fpg_rect_plan_bytes; owned by the caller, valid until the plan is destroyed);
+ * the plan handle is host memory.  fpg_rect_plan_create synchronises `stream`
+ * once; fpg_rect_solve only enqueues on it (a cudaStream_t, NULL = default).
+ * Errors: FPG_EINVAL (kind, sizes, h <= 0, kappa > 0, null pointers, nvec above
+ * the plan's), FPG_ENOMEM (workspace short), FPG_EUNSUPPORTED, FPG_ECUDA. */
+typedef enum { FPG_RECT_DIRICHLET = 0, FPG_RECT_NEUMANN = 1, FPG_RECT_PERIODIC = 2 } fpg_rect_kind;
+typedef struct fpg_rect_plan fpg_rect_plan;
+fpg_status fpg_rect_plan_bytes(int32_t kind, int32_t nt, int32_t ns, int32_t nvec, size_t* bytes);
+fpg_status fpg_rect_plan_create(int32_t kind, int32_t nt, int32_t ns, double h, double kappa, int32_t nvec,
+                                void* workspace, size_t bytes, void* stream, fpg_rect_plan** out);
+fpg_status fpg_rect_solve(fpg_rect_plan* plan, const double* v, double* z, int32_t nvec);
+void fpg_rect_plan_destroy(fpg_rect_plan* plan);
+
+/* ---- 3-D box fast solve (the 3-D extension named after Sec. 2.1) -----------
+ * z = A^{-1} v for nvec boxes of nx x ny x nz points (x fastest, then y, then z;
+ * FP64, device pointers, v and z may not alias): the 7-point stencil with
+ * spacing h in all directions (delta = 1/h^2), kappa <= 0 on the diagonal,
+ * zero Dirichlet data one step beyond every face.  One more transform turns the
+ * 3-D equation into independent 2-D ones: DST-I along x, DST-I along y (the a1
+ * engines), one Thomas solve along z per mode pair (kx, ky) with diagonal
+ * -6 delta + 2 delta cos(kx pi/(nx+1)) + 2 delta cos(ky pi/(ny+1)) + kappa, and the
+ * two inverse transforms.  2 <= nx, ny <= 4096, 1 <= nz <= 4096, nvec * nx <= 65535.
+ * Plan, workspace, stream and error rules as for the rectangle plans. */
+typedef struct fpg_box_plan fpg_box_plan;
+fpg_status fpg_box_plan_bytes(int32_t nx, int32_t ny, int32_t nz, int32_t nvec, size_t* bytes);
+fpg_status fpg_box_plan_create(int32_t nx, int32_t ny, int32_t nz, double h, double kappa, int32_t nvec,
+                               void* workspace, size_t bytes, void* stream, fpg_box_plan** out);
+fpg_status fpg_box_solve(fpg_box_plan* plan, const double* v, double* z, int32_t nvec);
+void fpg_box_plan_destroy(fpg_box_plan* plan);
+
+/* One-call forms (plan, solve, release; the tables are rebuilt at every call):
+ * Neumann rectangles (Sec. 2.2, Eq. "submat_Neumann") and periodic rectangles
+ * (Eq. "submat_Periodic") as described above; workspace >= the matching
+ * *_workspace_bytes (= fpg_rect_plan_bytes of that kind).  Same errors. */
 fpg_status fpg_neumann_workspace_bytes(int32_t nt, int32_t ns, int32_t nvec, size_t* bytes);
 fpg_status fpg_neumann_solve(int32_t nt, int32_t ns, double h, double kappa, const double* v, double* z,
                              int32_t nvec, void* workspace, size_t bytes, void* stream);
-
-/* Fast solve on periodic rectangles (Sec. 2.2, Eq. "submat_Periodic"):
- * z = A_P^{-1} v, A_P = I (x) A_t^P + T_s (x) I + kappa I on an n_t x n_s grid
- * (row-major, t fastest) with spacing h both ways: periodic along t
- * (A_t^P = delta circ(-2, 1, 0, ..., 0, 1), delta = 1/h^2), Dirichlet ends along s.
- * The real eigen-coordinates along t are the real and imaginary parts of each
- * line's DFT (mode m: Re X_m for 2m <= n_t, Im X_m otherwise; eigenvalue
- * -4 delta sin^2(pi m/n_t)), two lines per complex FFT; Thomas per mode along s;
- * inverse.  FP64.  n_t with prime factors <= 13, 2 <= n_t <= 2048, 1 <= n_s <= 4096.
- * v, z: device pointers to nvec blocks of n_t * n_s doubles (may not alias);
- * workspace: device, >= fpg_periodic_workspace_bytes(n_t, n_s, nvec) bytes,
- * caller-owned; tables are rebuilt on the host at every call.
- * Errors: FPG_EINVAL (sizes, h <= 0, kappa > 0, null pointers), FPG_ENOMEM
- * (workspace short), FPG_EUNSUPPORTED (n_t has a prime factor above 13), FPG_ECUDA. */
 fpg_status fpg_periodic_workspace_bytes(int32_t nt, int32_t ns, int32_t nvec, size_t* bytes);
 fpg_status fpg_periodic_solve(int32_t nt, int32_t ns, double h, double kappa, const double* v, double* z,
                               int32_t nvec, void* workspace, size_t bytes, void* stream);

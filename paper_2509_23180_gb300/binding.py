@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libfpg.so")
 
 GEOMETRY = {"L": 0, "T": 1, "cross": 2}
 BOUNDARY = {"dirichlet": 0, "neumann_sides": 1}
+RECT = {"dirichlet": 0, "neumann": 1, "periodic": 2}
 SCHUR = {"reduced": 0, "literal": 1}
 STATUS = {0: "FPG_OK", 1: "FPG_EINVAL", 2: "FPG_ENOMEM", 3: "FPG_ECUDA", 4: "FPG_ENOCONV",
           5: "FPG_ETIMEOUT", 6: "FPG_EUNSUPPORTED", 7: "FPG_EBUDGET"}
@@ -102,6 +103,14 @@ _SIGS = {
     "fpg_convert": ([_P, _I32, _P, _I32, _I64, _P], _I32),
     "fpg_neumann_workspace_bytes": ([_I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)], _I32),
     "fpg_neumann_solve": ([_I32, _I32, _D, _D, _P, _P, _I32, _P, ctypes.c_size_t, _P], _I32),
+    "fpg_rect_plan_bytes": ([_I32, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)], _I32),
+    "fpg_rect_plan_create": ([_I32, _I32, _I32, _D, _D, _I32, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)], _I32),
+    "fpg_rect_solve": ([_P, _P, _P, _I32], _I32),
+    "fpg_rect_plan_destroy": ([_P], None),
+    "fpg_box_plan_bytes": ([_I32, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)], _I32),
+    "fpg_box_plan_create": ([_I32, _I32, _I32, _D, _D, _I32, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)], _I32),
+    "fpg_box_solve": ([_P, _P, _P, _I32], _I32),
+    "fpg_box_plan_destroy": ([_P], None),
     "fpg_periodic_workspace_bytes": ([_I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)], _I32),
     "fpg_periodic_solve": ([_I32, _I32, _D, _D, _P, _P, _I32, _P, ctypes.c_size_t, _P], _I32),
     "fpg_probe_fma_peak": ([_I32, ctypes.POINTER(_D)], _I32),
@@ -355,3 +364,58 @@ def periodic_solve(v, z, nt: int, ns: int, h: float, kappa: float, stream=None):
     _check(lib.fpg_periodic_solve(nt, ns, h, kappa, _ptr(v), _ptr(z), nvec, _ptr(ws), nb.value, st.cuda_stream),
            "fpg_periodic_solve")
     return ws
+
+
+class RectPlan:
+    """A rectangle fast-solve plan (fpg_rect_plan_*) with its device workspace."""
+
+    def __init__(self, kind, nt: int, ns: int, h: float, kappa: float, nvec: int, stream=None, device="cuda"):
+        import torch
+        self.lib = load()
+        self.kind = RECT[kind] if isinstance(kind, str) else int(kind)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        nb = ctypes.c_size_t()
+        _check(self.lib.fpg_rect_plan_bytes(self.kind, nt, ns, nvec, ctypes.byref(nb)), "fpg_rect_plan_bytes")
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=device)
+        h_ = _P()
+        _check(self.lib.fpg_rect_plan_create(self.kind, nt, ns, h, kappa, nvec, _ptr(self.workspace), nb.value,
+                                             self.stream.cuda_stream, ctypes.byref(h_)), "fpg_rect_plan_create")
+        self.handle = h_
+
+    def solve(self, v, z, nvec: int):
+        _check(self.lib.fpg_rect_solve(self.handle, _ptr(v), _ptr(z), nvec), "fpg_rect_solve")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.fpg_rect_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+class BoxPlan:
+    """A 3-D box fast-solve plan (fpg_box_plan_*) with its device workspace."""
+
+    def __init__(self, nx: int, ny: int, nz: int, h: float, kappa: float, nvec: int, stream=None, device="cuda"):
+        import torch
+        self.lib = load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        nb = ctypes.c_size_t()
+        _check(self.lib.fpg_box_plan_bytes(nx, ny, nz, nvec, ctypes.byref(nb)), "fpg_box_plan_bytes")
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=device)
+        h_ = _P()
+        _check(self.lib.fpg_box_plan_create(nx, ny, nz, h, kappa, nvec, _ptr(self.workspace), nb.value,
+                                            self.stream.cuda_stream, ctypes.byref(h_)), "fpg_box_plan_create")
+        self.handle = h_
+
+    def solve(self, v, z, nvec: int):
+        _check(self.lib.fpg_box_solve(self.handle, _ptr(v), _ptr(z), nvec), "fpg_box_solve")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.fpg_box_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()

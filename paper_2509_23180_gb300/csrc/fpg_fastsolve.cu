@@ -550,6 +550,57 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
 
 }  // namespace
 
+// One DST-I pass of the FP64 fast solve on its own (the 3-D box solve chains
+// them): forward, in (layout ib, L) -> scratch[b][k][s]; or inverse,
+// scratch -> out (layout ob, L), scaled by 2/(n+1).  The engine is chosen as
+// in the full fast solve (dense, size-specialised where compiled and
+// profitable, else the generic FFT engine).
+cudaError_t launch_dst_pass(bool forward, const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib,
+                            double* scratch, double* out, BatchDesc ob, int nblk, cudaStream_t st) {
+  if (nblk <= 0) return cudaSuccess;
+  const int n = tb.n;
+  const DstPlan& pl = tb.plan;
+  if (pl.mode == DST_DENSE) {
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(k_dense_forward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(k_dense_inverse<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           200 * 1024);
+      attr_set = true;
+    }
+    const int lpb = lines_per_block<double>(n);
+    const size_t smem = fs_smem_bytes<double>(n, lpb);
+    dim3 grid((L.ns + lpb - 1) / lpb, nblk);
+    if (forward)
+      k_dense_forward<double><<<grid, kFsThreads, smem, st>>>(in, ib, L, n, (const double*)pl.dense, scratch, lpb,
+                                                              nullptr, 1);
+    else
+      k_dense_inverse<double, double><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, n,
+                                                                      (const double*)pl.dense, lpb, nullptr, 1);
+    return cudaGetLastError();
+  }
+  if (tb.q == 0 && lines_engine<double>(pl.p, nblk, L.ns, tb.generic))
+    return forward ? lines_fwd<double, double>(pl, in, ib, L, scratch, nblk, nullptr, 1, st, 0)
+                   : lines_inv<double, double>(pl, scratch, out, ob, L, nblk, nullptr, 1, st);
+  const int Q = pairs_per_block<double>(pl, L.ns, nblk);
+  const size_t smem = dst_smem_bytes<double>(pl.p, pl.N, Q, pl.mode);
+  dim3 grid((L.ns + 2 * Q - 1) / (2 * Q), nblk);
+  if (forward) {
+    switch (plan_maxr(pl)) {
+      case 5: return fft_family_fwd_5(64, grid, smem, st, in, ib, L, pl, scratch, Q, nullptr, 1);
+      case 13: return fft_family_fwd_13(64, grid, smem, st, in, ib, L, pl, scratch, Q, nullptr, 1);
+      case 19: return fft_family_fwd_19(64, grid, smem, st, in, ib, L, pl, scratch, Q, nullptr, 1);
+      default: return fft_family_fwd_43(64, grid, smem, st, in, ib, L, pl, scratch, Q, nullptr, 1);
+    }
+  }
+  switch (plan_maxr(pl)) {
+    case 5: return fft_family_inv_5(64, 64, grid, smem, st, scratch, out, ob, L, pl, Q, nullptr, 1);
+    case 13: return fft_family_inv_13(64, 64, grid, smem, st, scratch, out, ob, L, pl, Q, nullptr, 1);
+    case 19: return fft_family_inv_19(64, 64, grid, smem, st, scratch, out, ob, L, pl, Q, nullptr, 1);
+    default: return fft_family_inv_43(64, 64, grid, smem, st, scratch, out, ob, L, pl, Q, nullptr, 1);
+  }
+}
+
 cudaError_t launch_fast_solve_fused(int prec, int out_prec, const FastSolveTables& tb, LineLayout L,
                                     const double* in, BatchDesc ib, void* out, BatchDesc ob, int nblk,
                                     const int* active, int nper_active, cudaStream_t st);

@@ -32,7 +32,6 @@
 
 namespace fpg {
 
-void record_message(const char* msg);
 cudaError_t launch_thomas_any(int prec, void* scratch, int n, int ns, const void* rpiv, const void* mneg, int nblk,
                               const int* active, int nper_active, cudaStream_t st, int wpb);
 
@@ -51,23 +50,6 @@ bool dct_radices(int N, int* rad, int* nrad) {
     while (m % q == 0) { if (cnt >= kMaxRadices) return false; rad[cnt++] = q; m /= q; }
   *nrad = cnt;
   return m == 1 && cnt > 0;
-}
-
-struct NmLayout {  // byte offsets in the caller's workspace
-  size_t W, post, rpiv, mneg, scratch, total;
-};
-
-NmLayout nm_layout(int nt, int ns, int nvec) {
-  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-  NmLayout L{};
-  size_t o = 0;
-  L.W = o;       o = al(o + sizeof(double) * 2 * nt);
-  L.post = o;    o = al(o + sizeof(double) * 2 * nt);
-  L.rpiv = o;    o = al(o + sizeof(double) * (size_t)nt * ns);
-  L.mneg = o;    o = al(o + sizeof(double) * (size_t)nt * ns);
-  L.scratch = o; o = al(o + sizeof(double) * (size_t)nvec * nt * ns);
-  L.total = o;
-  return L;
 }
 
 int nm_pairs(int nt) {
@@ -450,109 +432,3 @@ cudaError_t launch_fast_solve_dct(const FastSolveTables& tb, LineLayout L, const
 }
 
 }  // namespace fpg
-
-extern "C" fpg_status fpg_neumann_workspace_bytes(int32_t nt, int32_t ns, int32_t nvec, size_t* bytes) {
-  if (!bytes || nt < 2 || (nt & 1) || ns < 1 || nvec < 1 || nt > 2048 || ns > 4096) return FPG_EINVAL;
-  *bytes = fpg::nm_layout(nt, ns, nvec).total;
-  return FPG_OK;
-}
-
-extern "C" fpg_status fpg_neumann_solve(int32_t nt, int32_t ns, double h, double kappa, const double* v, double* z,
-                                        int32_t nvec, void* workspace, size_t bytes, void* stream) {
-  using namespace fpg;
-  if (!v || !z || !workspace || nt < 2 || (nt & 1) || ns < 1 || nvec < 1 || nt > 2048 || ns > 4096 ||
-      !(h > 0.0) || !(kappa <= 0.0)) {
-    record_message("fpg_neumann_solve: bad argument (2 <= n_t <= 2048 even, 1 <= n_s <= 4096, h > 0, kappa <= 0)");
-    return FPG_EINVAL;
-  }
-  const NmLayout L = nm_layout(nt, ns, nvec);
-  if (bytes < L.total) return FPG_ENOMEM;
-  FastSolveTables tb{};
-  if (!dct_plan_shape(nt, &tb.plan)) {
-    record_message("fpg_neumann_solve: n_t has a prime factor above 13");
-    return FPG_EUNSUPPORTED;
-  }
-  tb.kind = 1;
-  tb.n = nt;
-  tb.ns = ns;
-  tb.delta = 1.0 / (h * h);
-  std::vector<double> W, post, r, m;
-  dct_tables(nt, W, post);
-  dct_pivots(nt, ns, tb.delta, kappa, 0.0, 0, r, m);
-  cudaStream_t st = (cudaStream_t)stream;
-  unsigned char* base = static_cast<unsigned char*>(workspace);
-  // pageable sources: each copy has finished reading its host buffer on return
-  cudaError_t e = cudaMemcpyAsync(base + L.W, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(base + L.post, post.data(), sizeof(double) * post.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(base + L.rpiv, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(base + L.mneg, m.data(), sizeof(double) * m.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) {
-    tb.plan.W = base + L.W;
-    tb.post = base + L.post;
-    tb.rpiv = base + L.rpiv;
-    tb.mneg = base + L.mneg;
-    const LineLayout LL{nt, ns, 1, nt};
-    const BatchDesc bd{(long long)nt * ns, {0, 0, 0, 0}, 1};
-    e = launch_fast_solve_dct(tb, LL, v, bd, z, bd, nvec, reinterpret_cast<double*>(base + L.scratch), nullptr, 1,
-                              st);
-  }
-  if (e != cudaSuccess) {
-    record_cuda_error(e, "fpg_neumann_solve");
-    return FPG_ECUDA;
-  }
-  return FPG_OK;
-}
-
-extern "C" fpg_status fpg_periodic_workspace_bytes(int32_t nt, int32_t ns, int32_t nvec, size_t* bytes) {
-  if (!bytes || nt < 2 || ns < 1 || nvec < 1 || nt > 2048 || ns > 4096) return FPG_EINVAL;
-  *bytes = fpg::nm_layout(nt, ns, nvec).total;
-  return FPG_OK;
-}
-
-extern "C" fpg_status fpg_periodic_solve(int32_t nt, int32_t ns, double h, double kappa, const double* v, double* z,
-                                         int32_t nvec, void* workspace, size_t bytes, void* stream) {
-  using namespace fpg;
-  if (!v || !z || !workspace || nt < 2 || ns < 1 || nvec < 1 || nt > 2048 || ns > 4096 || !(h > 0.0) ||
-      !(kappa <= 0.0)) {
-    record_message("fpg_periodic_solve: bad argument (2 <= n_t <= 2048, 1 <= n_s <= 4096, h > 0, kappa <= 0)");
-    return FPG_EINVAL;
-  }
-  const NmLayout L = nm_layout(nt, ns, nvec);
-  if (bytes < L.total) return FPG_ENOMEM;
-  FastSolveTables tb{};
-  if (!rdft_plan_shape(nt, &tb.plan)) {
-    record_message("fpg_periodic_solve: n_t has a prime factor above 13");
-    return FPG_EUNSUPPORTED;
-  }
-  tb.kind = 2;
-  tb.n = nt;
-  tb.ns = ns;
-  tb.delta = 1.0 / (h * h);
-  std::vector<double> W, post, r, m;
-  dct_tables(nt, W, post);
-  rdft_pivots(nt, ns, tb.delta, kappa, r, m);
-  cudaStream_t st = (cudaStream_t)stream;
-  unsigned char* base = static_cast<unsigned char*>(workspace);
-  cudaError_t e = cudaMemcpyAsync(base + L.W, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(base + L.rpiv, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(base + L.mneg, m.data(), sizeof(double) * m.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) {
-    tb.plan.W = base + L.W;
-    tb.rpiv = base + L.rpiv;
-    tb.mneg = base + L.mneg;
-    const LineLayout LL{nt, ns, 1, nt};
-    const BatchDesc bd{(long long)nt * ns, {0, 0, 0, 0}, 1};
-    e = launch_fast_solve_rdft(tb, LL, v, bd, z, bd, nvec, reinterpret_cast<double*>(base + L.scratch), nullptr, 1,
-                               st);
-  }
-  if (e != cudaSuccess) {
-    record_cuda_error(e, "fpg_periodic_solve");
-    return FPG_ECUDA;
-  }
-  return FPG_OK;
-}

@@ -1,5 +1,6 @@
 """The C-ABI library builds, loads and exports every entry point include/fpg.h
 declares; descriptor validation and workspace sizing need no GPU (CPU only)."""
+import ctypes
 import os
 import re
 
@@ -78,3 +79,15 @@ def test_neumann_sided_cross_descriptor(lib):
         with pytest.raises(B.FpgError) as e:
             B.workspace_bytes(bad)
         assert e.value.status == B.FPG_EUNSUPPORTED, (geom, n)
+
+
+@pytest.mark.parametrize("kind,nt,ns,want", [(0, 64, 40, "OK"), (0, 4097, 8, "EINVAL"), (1, 64, 8, "OK"),
+                                             (1, 63, 8, "EINVAL"), (1, 34, 8, "EUNSUPPORTED"),
+                                             (1, 4096, 8, "EINVAL"), (2, 45, 8, "OK"), (2, 17, 8, "EUNSUPPORTED"),
+                                             (2, 1, 8, "EINVAL"), (3, 64, 8, "EINVAL"), (0, 64, 0, "EINVAL")])
+def test_rect_plan_bytes(lib, kind, nt, ns, want):
+    nb = ctypes.c_size_t()
+    st = lib.fpg_rect_plan_bytes(kind, nt, ns, 2, ctypes.byref(nb))
+    assert st == getattr(B, "FPG_" + want)
+    if want == "OK":
+        assert nb.value >= 2 * 8 * nt * ns + 2 * 8 * nt * ns  # pivots + scratch of two rectangles

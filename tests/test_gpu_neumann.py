@@ -74,16 +74,19 @@ def test_neumann_second_order(lib):
 def test_neumann_errors(lib):
     from paper_2509_23180_gb300 import binding as B
     nb = ctypes.c_size_t()
-    assert lib.fpg_neumann_workspace_bytes(7, 4, 1, ctypes.byref(nb)) == B.FPG_EINVAL  # odd n_t
-    assert lib.fpg_neumann_workspace_bytes(34, 4, 1, ctypes.byref(nb)) == B.FPG_OK
-    v = torch.zeros((1, 34 * 4), dtype=torch.float64, device="cuda")
+    assert lib.fpg_neumann_workspace_bytes(7, 4, 1, ctypes.byref(nb)) == B.FPG_EINVAL
+    # 34 has a prime factor above 13: no FFT plan
+    assert lib.fpg_neumann_workspace_bytes(34, 4, 1, ctypes.byref(nb)) == B.FPG_EUNSUPPORTED
+    assert lib.fpg_neumann_workspace_bytes(36, 4, 1, ctypes.byref(nb)) == B.FPG_OK
+    v = torch.zeros((1, 36 * 4), dtype=torch.float64, device="cuda")
     z = torch.zeros_like(v)
     ws = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
     st = torch.cuda.current_stream().cuda_stream
-    # 34 = 2 * 17: no FFT plan with radices up to 13
     assert lib.fpg_neumann_solve(34, 4, 0.1, 0.0, v.data_ptr(), z.data_ptr(), 1, ws.data_ptr(), nb.value,
                                  st) == B.FPG_EUNSUPPORTED
-    assert lib.fpg_neumann_solve(34, 4, 0.1, 0.0, v.data_ptr(), z.data_ptr(), 1, ws.data_ptr(), nb.value - 256,
+    assert lib.fpg_neumann_solve(36, 4, 0.1, 0.0, v.data_ptr(), z.data_ptr(), 1, ws.data_ptr(), nb.value - 256,
                                  st) == B.FPG_ENOMEM
-    assert lib.fpg_neumann_solve(34, 4, 0.1, 1.0, v.data_ptr(), z.data_ptr(), 1, ws.data_ptr(), nb.value,
+    assert lib.fpg_neumann_solve(36, 4, 0.1, 1.0, v.data_ptr(), z.data_ptr(), 1, ws.data_ptr(), nb.value,
                                  st) == B.FPG_EINVAL  # kappa > 0
+    assert lib.fpg_neumann_solve(36, 4, 0.1, 0.0, v.data_ptr(), z.data_ptr(), 2, ws.data_ptr(), nb.value,
+                                 st) == B.FPG_ENOMEM  # workspace sized for one rectangle

@@ -74,14 +74,18 @@ def test_periodic_errors(lib):
     from paper_2509_23180_gb300 import binding as B
     nb = ctypes.c_size_t()
     assert lib.fpg_periodic_workspace_bytes(1, 4, 1, ctypes.byref(nb)) == B.FPG_EINVAL
-    assert lib.fpg_periodic_workspace_bytes(17, 4, 1, ctypes.byref(nb)) == B.FPG_OK
-    v = torch.zeros((1, 17 * 4), dtype=torch.float64, device="cuda")
+    # 17 has a prime factor above 13: no FFT plan
+    assert lib.fpg_periodic_workspace_bytes(17, 4, 1, ctypes.byref(nb)) == B.FPG_EUNSUPPORTED
+    assert lib.fpg_periodic_workspace_bytes(18, 4, 1, ctypes.byref(nb)) == B.FPG_OK
+    v = torch.zeros((1, 18 * 4), dtype=torch.float64, device="cuda")
     z = torch.zeros_like(v)
     ws = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
     st = torch.cuda.current_stream().cuda_stream
     assert lib.fpg_periodic_solve(17, 4, 0.1, 0.0, v.data_ptr(), z.data_ptr(), 1, ws.data_ptr(), nb.value,
-                                  st) == B.FPG_EUNSUPPORTED
-    assert lib.fpg_periodic_solve(17, 4, 0.1, 0.0, v.data_ptr(), z.data_ptr(), 1, ws.data_ptr(), nb.value - 256,
-                                  st) == B.FPG_ENOMEM
-    assert lib.fpg_periodic_solve(17, 4, 0.1, 1.0, v.data_ptr(), z.data_ptr(), 1, ws.data_ptr(), nb.value,
-                                  st) == B.FPG_EINVAL
+                                 st) == B.FPG_EUNSUPPORTED
+    assert lib.fpg_periodic_solve(18, 4, 0.1, 0.0, v.data_ptr(), z.data_ptr(), 1, ws.data_ptr(), nb.value - 256,
+                                 st) == B.FPG_ENOMEM
+    assert lib.fpg_periodic_solve(18, 4, 0.1, 1.0, v.data_ptr(), z.data_ptr(), 1, ws.data_ptr(), nb.value,
+                                 st) == B.FPG_EINVAL  # kappa > 0
+    assert lib.fpg_periodic_solve(18, 4, 0.1, 0.0, v.data_ptr(), z.data_ptr(), 2, ws.data_ptr(), nb.value,
+                                 st) == B.FPG_ENOMEM  # workspace sized for one rectangle
