@@ -78,15 +78,26 @@ class BlockSystem:
 
 
 def algorithm1(bs: BlockSystem, f: np.ndarray, m: int = 30, rtol: float = 1e-10,
-               max_iters: int = 3000, precond: str = "A_c"):
+               max_iters: int = 3000, precond: str = "A_c", centre_parts=None):
     """Alg. "fft_dd_solver": Schur reduction, preconditioned GMRES on the centre
     block, back substitution.  precond: "A_c" (the paper's A_2^{-1}, applied on
-    the right; flexible GMRES), "jacobi" (inverse diagonal of L_c) or "none".
+    the right; flexible GMRES), "block_diag" (several coupled blocks stored as
+    one centre vector: the exact inverse of each part's own operator, parts given
+    as index arrays in `centre_parts`), "jacobi" (inverse diagonal of L_c) or "none".
     The stopping test is taken against ||f||_2 of the whole domain.
     Returns (p, info)."""
     fc, _ = bs.reduced_rhs(f)
     if precond == "A_c":
         M = lambda v: bs.block_solve("C", v)
+    elif precond == "block_diag":
+        Ac = sp.csc_matrix(bs.A["C"])
+        lus = [(ix, spla.splu(sp.csc_matrix(Ac[ix][:, ix]))) for ix in centre_parts]
+
+        def M(v):
+            z = np.empty_like(v)
+            for ix, lu in lus:
+                z[ix] = lu.solve(v[ix])
+            return z
     elif precond == "jacobi":
         diag = np.array([bs.schur_apply(e)[i] for i, e in enumerate(np.eye(bs.n * bs.n))]) \
             if bs.n <= 24 else _schur_diagonal(bs)

@@ -254,3 +254,82 @@ def ncross_fourier_rhs(n: int, seed: int, modes: int = 16, kmax: int = 8) -> np.
             f += c[q] * np.sin(kx[q] * math.pi * xi) * np.sin(ky[q] * math.pi * eta) / (kx[q] ** 2 + ky[q] ** 2)
         parts.append(f.ravel())
     return np.concatenate(parts)
+
+
+# ---- the chain of K crosses (several coupled blocks; vertex-centred, h = 1/(n+1)) ----
+# 2K - 1 unit squares in a row along x (centres at even q, links at odd q), arms W
+# and E at the ends and S_i, N_i below and above centre i (at q = 2(i-1)).  Block
+# order: the coupled row as one rectangle ((2K-1)(n+1) - 1 columns, n rows), W, E
+# ((n+1) x n), S_1..S_K, N_1..N_K (n x (n+1)); the arms own the line they share
+# with the row.
+
+def strip_block_boxes(K: int, n: int):
+    """(name, first x node, first y node, nx, ny, unit-square corner) per block;
+    node coordinates in units of h."""
+    m = n + 1
+    q = 2 * K - 1
+    out = [("C", 1, 1, q * m - 1, n, None), ("W", -m + 1, 1, m, n, (-1, 0)), ("E", q * m, 1, m, n, (q, 0))]
+    out += [(f"S{i}", 2 * (i - 1) * m + 1, -m + 1, n, m, (2 * (i - 1), -1)) for i in range(1, K + 1)]
+    out += [(f"N{i}", 2 * (i - 1) * m + 1, m, n, m, (2 * (i - 1), 1)) for i in range(1, K + 1)]
+    return out
+
+
+def strip_total_unknowns(K: int, n: int) -> int:
+    return ((2 * K - 1) * (n + 1) - 1) * n + (2 * K + 2) * n * (n + 1)
+
+
+def strip_manufactured_rhs(K: int, n: int, kappa: float = 0.0) -> np.ndarray:
+    """f = lap(p) + kappa p for p = sin(pi x) sin(pi y) exp(0.3 x) (zero on every
+    integer line, so on the strip's edge), block order."""
+    h = 1.0 / (n + 1)
+    parts = []
+    for _, i0, j0, nx, ny, _ in strip_block_boxes(K, n):
+        x, y = np.meshgrid((i0 + np.arange(nx)) * h, (j0 + np.arange(ny)) * h)
+        e = np.exp(0.3 * x)
+        p = np.sin(math.pi * x) * np.sin(math.pi * y) * e
+        lap = e * np.sin(math.pi * y) * ((0.09 - 2 * math.pi ** 2) * np.sin(math.pi * x)
+                                          + 0.6 * math.pi * np.cos(math.pi * x))
+        parts.append((lap + kappa * p).ravel())
+    return np.concatenate(parts)
+
+
+def strip_manufactured_solution(K: int, n: int) -> np.ndarray:
+    h = 1.0 / (n + 1)
+    parts = []
+    for _, i0, j0, nx, ny, _ in strip_block_boxes(K, n):
+        x, y = np.meshgrid((i0 + np.arange(nx)) * h, (j0 + np.arange(ny)) * h)
+        parts.append((np.sin(math.pi * x) * np.sin(math.pi * y) * np.exp(0.3 * x)).ravel())
+    return np.concatenate(parts)
+
+
+def strip_fourier_rhs(K: int, n: int, seed: int, modes: int = 16, kmax: int = 8) -> np.ndarray:
+    """The "fourier" workload per unit square of the chain (the coupled row takes
+    square q's draws on its part x in [q, q+1]), block order."""
+    h = 1.0 / (n + 1)
+    parts = []
+    for name, i0, j0, nx, ny, corner in strip_block_boxes(K, n):
+        x, y = np.meshgrid((i0 + np.arange(nx)) * h, (j0 + np.arange(ny)) * h)
+        f = np.zeros_like(x)
+        if corner is None:
+            sq = np.minimum(np.floor(x).astype(int), 2 * K - 2)  # square index of each column
+            for i in range(2 * K - 1):
+                f += np.where(sq == i, _square_modes(seed, 100 + i, x - i, y, modes, kmax), 0.0)
+        else:
+            block_id = _STRIP_ID[name[0]] * 16 + int(name[1:] or 0)
+            f = _square_modes(seed, block_id, x - corner[0], y - corner[1], modes, kmax)
+        parts.append(f.ravel())
+    return np.concatenate(parts)
+
+
+_STRIP_ID = {"W": 1, "E": 2, "S": 3, "N": 4}
+
+
+def _square_modes(seed, block_id, xi, eta, modes, kmax):
+    rng = np.random.default_rng(seed * 1000 + block_id)
+    kx = rng.integers(1, kmax + 1, size=modes)
+    ky = rng.integers(1, kmax + 1, size=modes)
+    c = rng.standard_normal(modes)
+    f = np.zeros_like(xi)
+    for q in range(modes):
+        f += c[q] * np.sin(kx[q] * math.pi * xi) * np.sin(ky[q] * math.pi * eta) / (kx[q] ** 2 + ky[q] ** 2)
+    return f
