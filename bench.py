@@ -47,7 +47,7 @@ def parse():
                     help="solve the two kappa domains one after the other, or concurrently on two streams")
     ap.add_argument("--config", default="default",
                     choices=["default", "small", "precision", "batching", "serving", "fastsolve", "study",
-                             "neumann", "ncross", "rect"],
+                             "neumann", "ncross", "rect", "box"],
                     help="default: the 256^2 cross workload; the others run the other workloads as extra lines")
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
@@ -656,6 +656,36 @@ def run_extra(args):
                           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp64 / 1e12,
                                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / fp64,
                                        "peak_source": "measured: library FP64 FMA probe on this GPU"}})
+    elif args.config == "box":
+        # the 3-D extension after Sec. 2.1: fast solve on boxes of n^3 (default 4 x 255^3
+        # -- p = 256 per transform -- and 4 x 256^3, p = 257 by Rader), FP64
+        fp64 = B.probe_fma_peak(64)
+        nv = 4
+        for n in (255, 256):
+            v = torch.as_tensor(W.random_block_vectors(nv, n ** 3, 3), device="cuda")
+            z = torch.zeros_like(v)
+            plan = B.BoxPlan(n, n, n, 1.0 / (n + 1), -10.0, nv)
+            for _ in range(args.warmup):
+                plan.solve(v, z, nv)
+            tot = 0.0
+            for s in range(args.steps):
+                flush.fill_(float(s))
+                ms, _, _ = _timed(lambda: plan.solve(v, z, nv))
+                tot += ms
+            plan.close()
+            ms = tot / args.steps
+            pts = nv * n ** 3
+            flops = 2 * 2 * 2.5 * np.log2(n + 1) * pts + 5.0 * pts  # two transforms each along x and y + Thomas
+            lines.append({"metric": "3-D box fast solves/s", "value": nv / (ms * 1e-3), "unit": "boxes/s",
+                          "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                          "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": f"3-D box fast solve (DST-I x, DST-I y, Thomas z), {nv} boxes "
+                                                 f"of {n}^3, kappa -10", "l2": "inputs larger than L2"},
+                          "algorithmic_bytes": 5 * 16 * pts,
+                          "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp64 / 1e12,
+                                       "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / fp64,
+                                       "peak_source": "measured: library FP64 FMA probe on this GPU"}})
+            del v, z
     elif args.config == "ncross":
         # Sec. 3.1 boundary pattern on the cross (Neumann arm sides, Dirichlet far
         # ends, cell-centred grid): (i) throughput on the bench shape, n^2 per

@@ -22,6 +22,18 @@
  *   hold n x (n+1).  Inside a block: row-major, x fastest.  Several right-hand
  *   sides are stored one full vector after another.
  *
+ * Chain of K crosses (geometry = FPG_GEOM_CHAIN, desc.chain = K, 2 <= K <= 5;
+ * several coupled blocks, Sec. 2.3-2.4): 2K - 1 unit squares in a row along x
+ * (centres at even positions, links between them) are the coupled set, solved
+ * together by flexible GMRES with the block-diagonal preconditioner of its
+ * squares (one fast solve each); arms W and E at the row's ends and S_i, N_i
+ * below and above centre i are eliminated exactly.  Vector layout: the row as
+ * one rectangle of nx_c = (2K-1)(n+1) - 1 columns by n rows (x fastest; each
+ * square owns the line it shares with the next), then W, E ((n+1) x n), S_1..S_K,
+ * N_1..N_K (n x (n+1)); centre i's columns start at 2 i (n+1).  Reduced Schur
+ * form, Dirichlet edges, A_c^{-1} or identity preconditioner only (else
+ * FPG_EUNSUPPORTED); fpg_block_solve and fpg_autotune are not offered.
+ *
  * Neumann-sided cross (boundary = FPG_BC_NEUMANN_SIDES; the boundary pattern
  * of the paper's precision validation, Sec. 3.1 Eq. "cross_equation"): zero
  * Dirichlet at the four far ends of the arms, zero normal derivative on the
@@ -62,7 +74,7 @@ typedef enum {
   FPG_EBUDGET = 7       /* admission refused: over the memory budget */
 } fpg_status;
 
-typedef enum { FPG_GEOM_L = 0, FPG_GEOM_T = 1, FPG_GEOM_CROSS = 2 } fpg_geometry;
+typedef enum { FPG_GEOM_L = 0, FPG_GEOM_T = 1, FPG_GEOM_CROSS = 2, FPG_GEOM_CHAIN = 3 } fpg_geometry;
 
 typedef enum {
   FPG_BC_DIRICHLET = 0,     /* every outer edge Dirichlet; vertex-centred grid, h = 1/(n+1) */
@@ -86,6 +98,7 @@ typedef struct {
   int32_t precond_precision; /* 64: FP64 fast solve; 32: FP32 fast solve (FP64 outer loop) */
   int32_t schur_mode;        /* fpg_schur_mode */
   int32_t boundary;          /* fpg_boundary (0 = all Dirichlet) */
+  int32_t chain;             /* FPG_GEOM_CHAIN: number of crosses K, 2..5; other geometries: 0 */
 } fpg_domain_desc;
 
 typedef struct {
@@ -107,7 +120,7 @@ const char* fpg_last_cuda_error(void);
 const char* fpg_version(void);
 
 /* Number of unknowns of one right-hand side: n^2 + arms * n (n+1); 5 n^2 for
- * the Neumann-sided cross. */
+ * the Neumann-sided cross; nx_c n + (2K + 2) n (n+1) for a chain. */
 fpg_status fpg_unknowns(const fpg_domain_desc* desc, int64_t* count);
 
 /* Device workspace needed by fpg_create_domain for this descriptor (bytes).

@@ -63,6 +63,19 @@ int arnoldi_cluster_size(long long len);
 int fast_solve_path(int prec, const FastSolveTables& tb, LineLayout L, int nblk);
 bool dct_plan_shape(int n, DstPlan* pl);
 bool rdft_plan_shape(int n, DstPlan* pl);
+cudaError_t launch_chain_schur(const void* z, int zprec, long long zstride, const ChainGeom& G, const double* ctab,
+                               double* corr, const int* active, int nrhs, cudaStream_t st);
+cudaError_t launch_chain_stencil(const void* z, int zprec, long long zstride, double* w, long long wstride,
+                                 const ChainGeom& G, double delta, double kappa, const double* corr,
+                                 const int* active, int nrhs, int gx, cudaStream_t st);
+cudaError_t launch_chain_reduce_rhs(const double* f, const double* q, long long ntot, const ChainGeom& G,
+                                    double delta, double* fc, int nrhs, int gx, cudaStream_t st);
+cudaError_t launch_chain_arm_rhs(const double* f, const double* u, long long ntot, const ChainGeom& G, double delta,
+                                 double* out, double* p, int nrhs, int gx, cudaStream_t st);
+cudaError_t launch_chain_global_apply(const double* p, double* y, const double* f, long long ntot, const ChainGeom& G,
+                                      double delta, double kappa, double* part, int gmax, int nrhs, int gx,
+                                      double* rel_out, double* fnorm_out, double rtol, double* tolabs,
+                                      cudaStream_t st);
 cudaError_t launch_dst_pass(bool forward, const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib,
                             double* scratch, double* out, BatchDesc ob, int nblk, cudaStream_t st);
 cudaError_t launch_thomas_any(int prec, void* scratch, int n, int ns, const void* rpiv, const void* mneg, int nblk,
@@ -132,6 +145,8 @@ struct Layout {
   long long nc, na, ntot;
   ArmOffsets ao;
   int arm_slots[4];
+  int chain = 0;  // K of a chain of crosses (0: L, T or cross)
+  ChainGeom cg;   // the chain's row width and arm offsets
 };
 
 bool make_layout(const fpg_domain_desc* d, Layout* L) {
@@ -142,6 +157,25 @@ bool make_layout(const fpg_domain_desc* d, Layout* L) {
   L->na = (long long)n * as;
   L->ao.as = as;
   L->ao.bc = d->boundary == FPG_BC_NEUMANN_SIDES ? 1 : 0;
+  if (d->geometry == FPG_GEOM_CHAIN) {
+    const int K = d->chain;
+    L->chain = K;
+    L->cg.K = K;
+    L->cg.n = n;
+    L->cg.nxc = (2 * K - 1) * (n + 1) - 1;
+    L->nc = (long long)L->cg.nxc * n;
+    L->narms = 2 * K + 2;
+    L->armmask = 0;
+    for (int s = 0; s < L->narms; ++s) L->cg.off[s] = L->nc + (long long)s * L->na;
+    // ao: the first group (W, E, S_1, N_1) for the arm kernels; the rest go group by group
+    L->ao.off[0] = L->cg.off[0];
+    L->ao.off[1] = L->cg.off[1];
+    L->ao.off[2] = L->cg.off[2];
+    L->ao.off[3] = L->cg.off[2 + K];
+    for (int i = 0; i < 4; ++i) L->arm_slots[i] = i;
+    L->ntot = L->nc + (long long)L->narms * L->na;
+    return true;
+  }
   static const int slots_cross[] = {0, 1, 2, 3};
   static const int slots_t[] = {0, 1, 2};
   static const int slots_l[] = {1, 3};
@@ -169,7 +203,13 @@ bool make_layout(const fpg_domain_desc* d, Layout* L) {
 
 fpg_status validate(const fpg_domain_desc* d) {
   if (!d) return FPG_EINVAL;
-  if (d->geometry < 0 || d->geometry > 2) return FPG_EINVAL;
+  if (d->geometry < 0 || d->geometry > 3) return FPG_EINVAL;
+  if (d->geometry == FPG_GEOM_CHAIN) {
+    if (d->chain < 2 || d->chain > 5) return FPG_EINVAL;
+    if (d->boundary != FPG_BC_DIRICHLET || d->schur_mode != FPG_SCHUR_REDUCED) return FPG_EUNSUPPORTED;
+  } else if (d->chain != 0) {
+    return FPG_EINVAL;
+  }
   if (d->n < 2 || d->n > 4096) return FPG_EINVAL;
   if (!(d->kappa <= 0.0) || !std::isfinite(d->kappa)) return FPG_EINVAL;
   if (d->nrhs < 1 || d->nrhs > 4096) return FPG_EINVAL;
@@ -205,6 +245,9 @@ struct fpg_domain {
   int prec;
   LineLayout LC, LWE, LSN;
   BatchDesc we, sn;  // arm groups inside full vectors
+  BatchDesc sn2;     // chain: the N arms (sn holds the S arms)
+  BatchDesc cb1, cb2;      // chain: the row's squares with n + 1 columns, and the last square
+  LineLayout LC1, LC2;     // chain: their line layouts (transform along y, sweep along x)
   FastSolveTables tC64, tC32, tA64, tA32;
   FastSolveTables tA64e;  // Neumann-sided arms whose far end is row ns-1 (E, N); tA64 serves W, S
   double* ctab;
@@ -505,7 +548,7 @@ void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostP
   }
   p = c.take(sizeof(double) * (4 * n + 2));   if (D) D->ctab = (double*)p;
   p = c.take(sizeof(double) * n);             if (D) D->gsc = (double*)p;
-  p = c.take(sizeof(int) * 4);                if (D) D->arms_dev = (int*)p;
+  p = c.take(sizeof(int) * 12);               if (D) D->arms_dev = (int*)p;
   p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->f = (double*)p;
   p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->tmp = (double*)p;
   p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->tmp2 = (double*)p;
@@ -519,7 +562,7 @@ void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostP
   } else if (D) {
     D->lit_in = D->lit_out = nullptr;
   }
-  p = c.take(sizeof(double) * nrhs * 4 * n); if (D) D->corr = (double*)p;
+  p = c.take(sizeof(double) * nrhs * std::max(4, L.narms) * n); if (D) D->corr = (double*)p;
   const long long sc = (long long)nrhs * std::max(L.nc, 2 * L.na);
   p = c.take(sizeof(double) * sc);            if (D) D->scratch = p;
   p = c.take(sizeof(double) * nrhs);          if (D) D->gres = (double*)p;
@@ -618,8 +661,19 @@ fpg_status precond(fpg_domain* D, const double* v, void* z, int nvec, const int*
     count(D, 0, 1);
     return FPG_OK;
   }
-  BatchDesc ib{L.nc, {0, 0, 0, 0}, 1};
   int nl = 0;
+  if (L.chain) {
+    // block-diagonal over the row's squares: 2K - 2 squares of n + 1 columns, then the last
+    const FastSolveTables& ta = D->prec == 64 ? D->tA64 : D->tA32;
+    const FastSolveTables& tc = D->prec == 64 ? D->tC64 : D->tC32;
+    FPG_CUDA_TRY(launch_fast_solve(D->prec, D->prec, ta, D->LC1, v, D->cb1, z, D->cb1, nvec * D->cb1.nper,
+                                   D->scratch, active, D->cb1.nper, D->st, &nl));
+    FPG_CUDA_TRY(launch_fast_solve(D->prec, D->prec, tc, D->LC2, v, D->cb2, z, D->cb2, nvec, D->scratch, active, 1,
+                                   D->st, &nl));
+    count(D, 0, nl);
+    return FPG_OK;
+  }
+  BatchDesc ib{L.nc, {0, 0, 0, 0}, 1};
   const FastSolveTables& tb = D->prec == 64 ? D->tC64 : D->tC32;
   cudaEvent_t* evp = nullptr;
   const int i = ev_take(D, 8);
@@ -659,9 +713,12 @@ cudaError_t arm_fast_solves(fpg_domain* D, const double* in, double* out, int nv
                                               D->scratch, active, D->we.nper, D->st, nl);
       if (e != cudaSuccess) return e;
     }
-    if (D->sn.nper > 0)
-      return launch_fast_solve(64, 64, D->tA64, D->LSN, in, D->sn, out, D->sn, nvec * D->sn.nper, D->scratch,
-                               active, D->sn.nper, D->st, nl);
+    for (const BatchDesc* g : {&D->sn, &D->sn2}) {  // sn2: a chain's N arms
+      if (g->nper == 0) continue;
+      const cudaError_t e = launch_fast_solve(64, 64, D->tA64, D->LSN, in, *g, out, *g, nvec * g->nper, D->scratch,
+                                              active, g->nper, D->st, nl);
+      if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
   }
   for (int a = 0; a < 4; ++a) {
@@ -691,11 +748,22 @@ fpg_status arm_solves(fpg_domain* D, const double* in, double* out, int nvec, in
 fpg_status arm_solves_refined(fpg_domain* D, const double* in, double* out, double* work, int nvec, int phase) {
   const Layout& L = D->L;
   FPG_TRY(arm_solves(D, in, out, nvec, phase));
+  // the arm kernels take up to four arms (W, E, S, N slots) per launch: a chain's
+  // arms go in K groups (W, E, S_1, N_1), (-, -, S_2, N_2), ...
+  const int groups = L.chain ? L.chain : 1;
   for (int it = 0; it < D->arm_refine; ++it) {  // out += A_a^{-1} (in - A_a out)
-    FPG_CUDA_TRY(launch_arm_residual(in, out, work, L.ntot, L.n, D->delta, D->desc.kappa, L.ao, nvec, D->gxf, D->st));
+    for (int g = 0; g < groups; ++g) {
+      ArmOffsets ao = L.ao;
+      if (L.chain && g > 0) ao.off[0] = ao.off[1] = -1, ao.off[2] = L.cg.off[2 + g], ao.off[3] = L.cg.off[2 + L.chain + g];
+      FPG_CUDA_TRY(launch_arm_residual(in, out, work, L.ntot, L.n, D->delta, D->desc.kappa, ao, nvec, D->gxf, D->st));
+    }
     FPG_TRY(arm_solves(D, work, work, nvec, phase));
-    FPG_CUDA_TRY(launch_arm_add(out, work, L.ntot, L.n, L.ao, nvec, D->gxf, D->st));
-    count(D, phase, 2);
+    for (int g = 0; g < groups; ++g) {
+      ArmOffsets ao = L.ao;
+      if (L.chain && g > 0) ao.off[0] = ao.off[1] = -1, ao.off[2] = L.cg.off[2 + g], ao.off[3] = L.cg.off[2 + L.chain + g];
+      FPG_CUDA_TRY(launch_arm_add(out, work, L.ntot, L.n, ao, nvec, D->gxf, D->st));
+    }
+    count(D, phase, 2 * groups);
   }
   return FPG_OK;
 }
@@ -703,6 +771,11 @@ fpg_status arm_solves_refined(fpg_domain* D, const double* in, double* out, doub
 // a2, interface part: corr[r][a][:] = R_ca A_a^{-1} R_ac z on C's line next to arm a.
 fpg_status schur_corr(fpg_domain* D, const void* z, int zprec, int nvec, const int* active) {
   const Layout& L = D->L;
+  if (L.chain) {
+    FPG_CUDA_TRY(launch_chain_schur(z, zprec, L.nc, L.cg, D->ctab, D->corr, active, nvec, D->st));
+    count(D, 1, 1);
+    return FPG_OK;
+  }
   if (D->desc.schur_mode == FPG_SCHUR_REDUCED) {
     if (D->schur_transform && L.ao.bc == 0 && schur_dst_supported(L.n))
       FPG_CUDA_TRY(launch_schur_dst(z, zprec, L.nc, L.n, D->tC64.plan, D->gsc, D->arms_dev, L.narms, D->corr, active,
@@ -728,10 +801,25 @@ fpg_status schur_corr(fpg_domain* D, const void* z, int zprec, int nvec, const i
 fpg_status schur(fpg_domain* D, const void* z, int zprec, double* w, int nvec, const int* active) {
   const Layout& L = D->L;
   FPG_TRY(schur_corr(D, z, zprec, nvec, active));
-  FPG_CUDA_TRY(launch_stencil_c(z, zprec, L.nc, w, L.nc, L.n, D->delta, D->desc.kappa, D->corr, L.armmask, active,
-                                nvec, D->gx, D->st));
+  if (L.chain)
+    FPG_CUDA_TRY(launch_chain_stencil(z, zprec, L.nc, w, L.nc, L.cg, D->delta, D->desc.kappa, D->corr, active, nvec,
+                                      D->gx, D->st));
+  else
+    FPG_CUDA_TRY(launch_stencil_c(z, zprec, L.nc, w, L.nc, L.n, D->delta, D->desc.kappa, D->corr, L.armmask,
+                                  active, nvec, D->gx, D->st));
   count(D, 1, 1);
   return FPG_OK;
+}
+
+// a7: y = K p (y may be null) and, with f, the relative residuals ||f - K p||/||f||.
+cudaError_t global_apply(fpg_domain* D, const double* p, double* y, const double* f, int nvec, double* rel_out,
+                         double* fnorm_out, double rtol, double* tolabs) {
+  const Layout& L = D->L;
+  if (L.chain)
+    return launch_chain_global_apply(p, y, f, L.ntot, L.cg, D->delta, D->desc.kappa, D->ks.part, kGmax, nvec, D->gxf,
+                                     rel_out, fnorm_out, rtol, tolabs, D->st);
+  return launch_global_apply(p, y, f, L.ntot, L.n, D->delta, D->desc.kappa, L.ao, D->ks.part, kGmax, nvec, D->gxf,
+                             rel_out, fnorm_out, rtol, tolabs, D->st);
 }
 
 fpg_status check_launch() {
@@ -773,12 +861,14 @@ fpg_status setup_common(fpg_domain* D, double* p, bool keep_iters) {
   D->first_cycle = true;
   // ||f|| per RHS and the absolute tolerance
   int e = ev_begin(D, 5);
-  FPG_CUDA_TRY(launch_global_apply(D->f, nullptr, D->f, L.ntot, L.n, D->delta, D->desc.kappa, L.ao, k.part, kGmax,
-                                   nrhs, D->gxf, nullptr, k.fnorm, kInnerMargin * D->desc.rtol, k.tolabs, D->st));
+  FPG_CUDA_TRY(global_apply(D, D->f, nullptr, D->f, nrhs, nullptr, k.fnorm, kInnerMargin * D->desc.rtol, k.tolabs));
   count(D, 5, 2);
   // Alg. 1 steps 1-3: q_a = A_a^{-1} f_a (into p's arm blocks), f'_c = f_c - sum R_ca q_a
   FPG_TRY(arm_solves_refined(D, D->f, p, D->tmp2, nrhs, 5));
-  FPG_CUDA_TRY(launch_reduce_rhs(D->f, p, L.ntot, L.n, D->delta, L.ao, k.fc, nrhs, D->gx, D->st));
+  if (L.chain)
+    FPG_CUDA_TRY(launch_chain_reduce_rhs(D->f, p, L.ntot, L.cg, D->delta, k.fc, nrhs, D->gx, D->st));
+  else
+    FPG_CUDA_TRY(launch_reduce_rhs(D->f, p, L.ntot, L.n, D->delta, L.ao, k.fc, nrhs, D->gx, D->st));
   count(D, 5, 1);
   FPG_CUDA_TRY(cudaMemsetAsync(k.u, 0, sizeof(double) * nrhs * L.nc, D->st));
   FPG_CUDA_TRY(cudaMemsetAsync(k.done, 0, sizeof(int) * nrhs, D->st));
@@ -830,7 +920,8 @@ fpg_status issue_cycle(fpg_domain* D) {
     FPG_TRY(precond(D, vj, zj, nrhs, k.active));
     ev_end(D, e);
     const int csz = D->use_cluster ? (D->tune_csz > 0 && L.nc <= 262144 ? D->tune_csz : arnoldi_cluster_size(L.nc)) : 0;
-    const int ept = (csz > 0 && D->arnoldi_mode == 1) ? arnoldi_reg_ept(L.nc, csz, D->tune_nt) : 0;
+    // the register-resident step fuses the cross's stencil: chains take the global-w step
+    const int ept = (csz > 0 && D->arnoldi_mode == 1 && !L.chain) ? arnoldi_reg_ept(L.nc, csz, D->tune_nt) : 0;
     if (ept > 0) {
       // a2's interface part, then one launch for a2's stencil + a3 + a4
       e = ev_begin(D, 1);
@@ -954,7 +1045,10 @@ fpg_status stage_finish(fpg_domain* D) {
   double* p = D->p_cur;
   // Alg. 1 steps 5-7: f'_a = f_a - R_ac p_c, p_a = A_a^{-1} f'_a, p_c = u
   int e = ev_begin(D, 5);
-  FPG_CUDA_TRY(launch_arm_rhs(D->f, k.u, L.ntot, L.n, D->delta, L.ao, D->tmp, p, nrhs, D->gxf, D->st));
+  if (L.chain)
+    FPG_CUDA_TRY(launch_chain_arm_rhs(D->f, k.u, L.ntot, L.cg, D->delta, D->tmp, p, nrhs, D->gxf, D->st));
+  else
+    FPG_CUDA_TRY(launch_arm_rhs(D->f, k.u, L.ntot, L.n, D->delta, L.ao, D->tmp, p, nrhs, D->gxf, D->st));
   count(D, 5, 1);
   FPG_TRY(arm_solves_refined(D, D->tmp, p, D->tmp2, nrhs, 5));
   ev_end(D, e);
@@ -968,8 +1062,7 @@ fpg_status stage_finish(fpg_domain* D) {
   }
   const bool check = D->accept_rounds < kAcceptRounds;
   // with a check to follow, K p goes to rbuf (the next refinement's residual)
-  FPG_CUDA_TRY(launch_global_apply(p, check ? D->rbuf : nullptr, D->f, L.ntot, L.n, D->delta, D->desc.kappa, L.ao,
-                                   k.part, kGmax, nrhs, D->gxf, D->gres, nullptr, 0.0, nullptr, D->st));
+  FPG_CUDA_TRY(global_apply(D, p, check ? D->rbuf : nullptr, D->f, nrhs, D->gres, nullptr, 0.0, nullptr));
   count(D, 6, 2);
   // acceptance check: right-hand sides still above rtol get r = f - K p for a
   // correction solve (global iterative refinement); the others get r = 0
@@ -1428,10 +1521,27 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   D->LSN = LineLayout{n, as, 1, n};
   D->we = BatchDesc{L.ntot, {0, 0, 0, 0}, 0};
   D->sn = BatchDesc{L.ntot, {0, 0, 0, 0}, 0};
-  for (int a = 0; a < 4; ++a) {
-    if (L.ao.off[a] < 0) continue;
-    BatchDesc& g = a < 2 ? D->we : D->sn;
-    g.off[g.nper++] = L.ao.off[a];
+  D->sn2 = BatchDesc{L.ntot, {0, 0, 0, 0}, 0};
+  if (L.chain) {
+    const int K = L.chain, nxc = L.cg.nxc;
+    D->we.off[D->we.nper++] = L.cg.off[0];
+    D->we.off[D->we.nper++] = L.cg.off[1];
+    for (int i = 0; i < K; ++i) {
+      D->sn.off[D->sn.nper++] = L.cg.off[2 + i];
+      D->sn2.off[D->sn2.nper++] = L.cg.off[2 + K + i];
+    }
+    // the row's squares: transform along y (stride nxc), sweep along x
+    D->LC1 = LineLayout{n, n + 1, nxc, 1};
+    D->LC2 = LineLayout{n, n, nxc, 1};
+    D->cb1 = BatchDesc{L.nc, {0, 0, 0, 0}, 0};
+    for (int q = 0; q < 2 * K - 2; ++q) D->cb1.off[D->cb1.nper++] = (long long)q * (n + 1);
+    D->cb2 = BatchDesc{L.nc, {(long long)(2 * K - 2) * (n + 1), 0, 0, 0}, 1};
+  } else {
+    for (int a = 0; a < 4; ++a) {
+      if (L.ao.off[a] < 0) continue;
+      BatchDesc& g = a < 2 ? D->we : D->sn;
+      g.off[g.nper++] = L.ao.off[a];
+    }
   }
   for (auto* t : {&D->tC64, &D->tC32}) { t->n = n; t->ns = n; t->delta = D->delta; }
   for (auto* t : {&D->tA64, &D->tA32, &D->tA64e}) { t->n = n; t->ns = as; t->delta = D->delta; }
@@ -1470,8 +1580,8 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   std::vector<float> mc32(mc.begin(), mc.end()), ma32(ma.begin(), ma.end());
   std::vector<float> W32(hp.W.begin(), hp.W.end()), s32(hp.sinp.begin(), hp.sinp.end()),
       B32(hp.Bhat.begin(), hp.Bhat.end()), d32(hp.dense.begin(), hp.dense.end());
-  int arms[4] = {0, 0, 0, 0};
-  for (int i = 0; i < L.narms; ++i) arms[i] = L.arm_slots[i];
+  int arms[12] = {0};
+  for (int i = 0; i < L.narms; ++i) arms[i] = L.chain ? i : L.arm_slots[i];
   auto cp = [&](const void* dst, const void* src, size_t b) {
     return cudaMemcpyAsync(const_cast<void*>(dst), src, b, cudaMemcpyHostToDevice, D->st);
   };
@@ -1631,6 +1741,7 @@ fpg_status fpg_apply_precond(fpg_domain* d, const double* v, void* z, int32_t nv
 fpg_status fpg_block_solve(fpg_domain* d, int32_t block, const double* v, double* z, int32_t nvec) {
   if (!d || !v || !z || nvec < 0 || block < 0 || block > 4) return FPG_EINVAL;
   const Layout& L = d->L;
+  if (L.chain) return FPG_EUNSUPPORTED;
   if (block > 0 && L.ao.off[block - 1] < 0) return FPG_EINVAL;
   const long long len = block == 0 ? L.nc : L.na;
   const LineLayout& LL = block == 0 ? d->LC : (block <= 2 ? d->LWE : d->LSN);
@@ -1697,9 +1808,8 @@ fpg_status fpg_global_residual(fpg_domain* d, const double* f, const double* p, 
   const Layout& L = d->L;
   for (int s = 0; s < nvec; s += d->desc.nrhs) {
     const int c = std::min(d->desc.nrhs, nvec - s);
-    FPG_CUDA_TRY(launch_global_apply(p + (size_t)s * L.ntot, nullptr, f + (size_t)s * L.ntot, L.ntot, L.n, d->delta,
-                                     d->desc.kappa, L.ao, d->ks.part, kGmax, c, d->gxf, d->gres, nullptr, 0.0,
-                                     nullptr, d->st));
+    FPG_CUDA_TRY(global_apply(d, p + (size_t)s * L.ntot, nullptr, f + (size_t)s * L.ntot, c, d->gres, nullptr, 0.0,
+                              nullptr));
     d->launches += 2;
     FPG_CUDA_TRY(cudaMemcpyAsync(out_host + s, d->gres, sizeof(double) * c, cudaMemcpyDeviceToHost, d->st));
     FPG_CUDA_TRY(cudaStreamSynchronize(d->st));
@@ -1710,14 +1820,14 @@ fpg_status fpg_global_residual(fpg_domain* d, const double* f, const double* p, 
 fpg_status fpg_apply_global(fpg_domain* d, const double* p, double* y, int32_t nvec) {
   if (!d || !p || !y || nvec <= 0) return FPG_EINVAL;
   const Layout& L = d->L;
-  FPG_CUDA_TRY(launch_global_apply(p, y, nullptr, L.ntot, L.n, d->delta, d->desc.kappa, L.ao, d->ks.part, kGmax,
-                                   nvec, d->gxf, nullptr, nullptr, 0.0, nullptr, d->st));
+  FPG_CUDA_TRY(global_apply(d, p, y, nullptr, nvec, nullptr, nullptr, 0.0, nullptr));
   d->launches += 1;
   return check_launch();
 }
 
 fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out) {
   if (!d) return FPG_EINVAL;
+  if (d->L.chain) return FPG_EUNSUPPORTED;
   drop_graph(d);
   const Layout& L = d->L;
   KrylovState& k = d->ks;
@@ -1810,11 +1920,13 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_FUSED_FASTSOLVE:
+      if (d->L.chain && value) return FPG_EUNSUPPORTED;  // the one-pass kernel takes whole square blocks
       for (auto* t : {&d->tC64, &d->tC32, &d->tA64, &d->tA32, &d->tA64e}) t->fused = value != 0;
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_PRECOND:
       if (value < 0 || value > 2) return FPG_EINVAL;
+      if (d->L.chain && value == 2) return FPG_EUNSUPPORTED;  // the Jacobi diagonal is written for the cross
       d->precond_kind = value;
       drop_graph(d);
       return FPG_OK;

@@ -12,11 +12,11 @@ namespace fpg {
 
 // ---------------------------------------------------------------------------
 // Batch of blocks of one shape inside larger vectors.  Block b of a launch lives
-// at base + (b / nper) * rhs_stride + off[b % nper]: nper blocks per right-hand
-// side (e.g. the two arms W and E), one right-hand side after another.
+// at base + (b / nper) * rhs_stride + off[b % nper]: nper <= 8 blocks per
+// right-hand side (e.g. the two arms W and E), one right-hand side after another.
 struct BatchDesc {
   long long rhs_stride;
-  long long off[4];
+  long long off[8];
   int nper;
 };
 
@@ -57,6 +57,14 @@ struct ArmOffsets {
   long long off[4];
   int as = 0;
   int bc = 0;
+};
+
+// The chain of K crosses (2 <= K <= 5): the coupled row is nxc = (2K-1)(n+1) - 1
+// columns by n rows; its arms, in slot order W, E, S_1..S_K, N_1..N_K, start at
+// off[slot] inside one full vector (W and E (n+1) x n, S and N n x (n+1)).
+struct ChainGeom {
+  int K = 0, n = 0, nxc = 0;
+  long long off[12];
 };
 
 // Tables for the interface (Schur) correction, reduced form:

@@ -1206,6 +1206,12 @@ cudaError_t launch_arm_add(double* x, const double* e, long long ntot, int n, Ar
   return cudaGetLastError();
 }
 
+cudaError_t launch_residual_finalize(const double* part, int gmax, int cnt, int nrhs, double* out, double* fnorm_out,
+                                     double rtol, double* tolabs, cudaStream_t st) {
+  k_residual_finalize<<<nrhs, 32, 0, st>>>(part, gmax, cnt, nrhs, out, fnorm_out, rtol, tolabs);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_global_apply(const double* p, double* y, const double* f, long long ntot, int n, double delta,
                                 double kappa, ArmOffsets ao, double* part, int gmax, int nrhs, int gx,
                                 double* rel_out, double* fnorm_out, double rtol, double* tolabs,

@@ -91,3 +91,22 @@ def test_rect_plan_bytes(lib, kind, nt, ns, want):
     assert st == getattr(B, "FPG_" + want)
     if want == "OK":
         assert nb.value >= 2 * 8 * nt * ns + 2 * 8 * nt * ns  # pivots + scratch of two rectangles
+
+
+def test_chain_descriptor(lib):
+    """Several coupled blocks: a chain of K crosses has (2K-1)(n+1)-1 by n row
+    unknowns plus 2K + 2 arms; K outside 2..5, a chain count on another geometry,
+    and the literal Schur form or Neumann sides on a chain are refused."""
+    n = 16
+    for K in (2, 3, 5):
+        d = B.make_desc("chain", n, 0.0, chain=K)
+        assert B.unknowns(d) == ((2 * K - 1) * (n + 1) - 1) * n + (2 * K + 2) * n * (n + 1)
+    for kw, want in (({"chain": 1}, B.FPG_EINVAL), ({"chain": 6}, B.FPG_EINVAL),
+                     ({"chain": 2, "schur_mode": "literal"}, B.FPG_EUNSUPPORTED),
+                     ({"chain": 2, "boundary": "neumann_sides"}, B.FPG_EUNSUPPORTED)):
+        with pytest.raises(B.FpgError) as e:
+            B.workspace_bytes(B.make_desc("chain", n, 0.0, **kw))
+        assert e.value.status == want, kw
+    with pytest.raises(B.FpgError) as e:
+        B.workspace_bytes(B.make_desc("cross", n, 0.0, chain=2))
+    assert e.value.status == B.FPG_EINVAL
