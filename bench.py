@@ -47,7 +47,7 @@ def parse():
                     help="solve the two kappa domains one after the other, or concurrently on two streams")
     ap.add_argument("--config", default="default",
                     choices=["default", "small", "precision", "batching", "serving", "fastsolve", "study",
-                             "neumann", "ncross", "rect", "box"],
+                             "neumann", "ncross", "rect", "box", "chain"],
                     help="default: the 256^2 cross workload; the others run the other workloads as extra lines")
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
@@ -656,6 +656,45 @@ def run_extra(args):
                           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp64 / 1e12,
                                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / fp64,
                                        "peak_source": "measured: library FP64 FMA probe on this GPU"}})
+    elif args.config == "chain":
+        # several coupled blocks (Sec. 2.3-2.4): a chain of K = 3 crosses, n^2 per
+        # square, kappa in {0, -10}, `seeds` fourier RHS each, FGMRES(m) with the
+        # block-diagonal fast-solve preconditioner of the 5 coupled squares
+        n, m, K = args.n, args.restart, 3
+        doms = []
+        for kappa in (0.0, -10.0):
+            f = torch.as_tensor(np.stack([W.strip_fourier_rhs(K, n, s) for s in range(args.seeds)]), device="cuda")
+            d = B.Domain(B.make_desc("chain", n, kappa, nrhs=args.seeds, restart=m, rtol=args.rtol, chain=K))
+            doms.append((d, f, torch.zeros_like(f)))
+        times, infos = [], []
+        for s in range(args.warmup + args.steps):
+            flush.fill_(float(s))
+            for d, f, p in doms:
+                d.set_rhs(f)
+            ms, _, out = _timed(lambda: [d.solve(p, check=False) for d, f, p in doms])
+            if s >= args.warmup:
+                times.append(ms)
+                for stt, info in out:
+                    infos += info
+        ms = sum(times) / len(times)
+        d0 = doms[0][0]
+        d0.set_profiling(True)
+        d0.set_rhs(doms[0][1])
+        d0.solve(doms[0][2], check=False)
+        phases = d0.phase_stats()
+        d0.set_profiling(False)
+        for d, _, _ in doms:
+            d.close()
+        lines.append({"metric": METRIC, "value": 2 * args.seeds / (ms * 1e-3), "unit": "solves/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": f"chain of {K} crosses ({2 * K - 1} coupled squares, {2 * K + 2} arms), "
+                                             f"{n}^2 per square, kappa 0 and -10, {args.seeds} fourier RHS each",
+                                 "n": n, "restart": m, "rtol": args.rtol, "l2": "flushed before every step"},
+                      "unknowns_per_rhs": W.strip_total_unknowns(K, n),
+                      "iterations_mean": float(np.mean([i["iterations"] for i in infos])),
+                      "residual_max": max(i["residual"] for i in infos),
+                      "all_converged": all(i["status"] == B.FPG_OK for i in infos), "phases_kappa0": phases})
     elif args.config == "box":
         # the 3-D extension after Sec. 2.1: fast solve on boxes of n^3 (default 4 x 255^3
         # -- p = 256 per transform -- and 4 x 256^3, p = 257 by Rader), FP64
