@@ -665,6 +665,7 @@ def run_extra(args):
         for kappa in (0.0, -10.0):
             f = torch.as_tensor(np.stack([W.strip_fourier_rhs(K, n, s) for s in range(args.seeds)]), device="cuda")
             d = B.Domain(B.make_desc("chain", n, kappa, nrhs=args.seeds, restart=m, rtol=args.rtol, chain=K))
+            apply_options(d, args)
             doms.append((d, f, torch.zeros_like(f)))
         times, infos = [], []
         for s in range(args.warmup + args.steps):
@@ -690,7 +691,8 @@ def run_extra(args):
                       "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                       "config": {"workload": f"chain of {K} crosses ({2 * K - 1} coupled squares, {2 * K + 2} arms), "
                                              f"{n}^2 per square, kappa 0 and -10, {args.seeds} fourier RHS each",
-                                 "n": n, "restart": m, "rtol": args.rtol, "l2": "flushed before every step"},
+                                 "n": n, "restart": m, "rtol": args.rtol, "l2": "flushed before every step",
+                                 "options": args.option},
                       "unknowns_per_rhs": W.strip_total_unknowns(K, n),
                       "iterations_mean": float(np.mean([i["iterations"] for i in infos])),
                       "residual_max": max(i["residual"] for i in infos),
@@ -737,6 +739,7 @@ def run_extra(args):
             f = torch.as_tensor(np.stack([W.ncross_fourier_rhs(n, s) for s in range(args.seeds)]), device="cuda")
             d = B.Domain(B.make_desc("cross", n, kappa, nrhs=args.seeds, restart=m, rtol=args.rtol,
                                      boundary="neumann_sides"))
+            apply_options(d, args)
             doms.append((d, f, torch.zeros_like(f)))
         times, infos = [], []
         for s in range(args.warmup + args.steps):

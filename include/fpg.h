@@ -271,8 +271,9 @@ typedef enum {
    * inverse DST) through a scratch array. */
   FPG_OPT_FUSED_FASTSOLVE = 4,
   /* CTAs per right-hand side of the fused Arnoldi step, 1..16 (0: built-in
-   * choice or the autotuner's).  Only used for centre vectors of at most
-   * 262144 points. */
+   * choice or the autotuner's).  The built-in choice for centre vectors of more
+   * than 262144 points is the multi-launch MGS; a value here runs the cluster
+   * kernel (w in HBM) for them instead. */
   FPG_OPT_ARNOLDI_CSZ = 5,
   /* Thread cap per CTA of the register-resident Arnoldi kernel: 256 or 512
    * (0: 256 when the centre slice of one CTA fits, else 512). */

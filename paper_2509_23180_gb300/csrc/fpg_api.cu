@@ -919,7 +919,7 @@ fpg_status issue_cycle(fpg_domain* D) {
     e = ev_begin(D, 0);
     FPG_TRY(precond(D, vj, zj, nrhs, k.active));
     ev_end(D, e);
-    const int csz = D->use_cluster ? (D->tune_csz > 0 && L.nc <= 262144 ? D->tune_csz : arnoldi_cluster_size(L.nc)) : 0;
+    const int csz = D->use_cluster ? (D->tune_csz > 0 ? D->tune_csz : arnoldi_cluster_size(L.nc)) : 0;
     // the register-resident step fuses the cross's stencil: chains take the global-w step
     const int ept = (csz > 0 && D->arnoldi_mode == 1 && !L.chain) ? arnoldi_reg_ept(L.nc, csz, D->tune_nt) : 0;
     if (ept > 0) {
