@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: HBM admission budget")
+    ap.add_argument("--server", default="native", choices=["native", "threads"],
+                    help="serving: the library's batch runtime driven by one host thread, or the threaded "
+                         "Python server")
     ap.add_argument("--option", action="append", default=[], metavar="NAME=VALUE",
                     help="fpg_set_option on every domain, e.g. DST_ENGINE=1, FUSED_FASTSOLVE=1, ARNOLDI_THREADS=512")
     ap.add_argument("--no-variants", action="store_true")
@@ -928,25 +931,34 @@ def run_extra(args):
     elif args.config == "serving":
         from paper_2509_23180_gb300 import serve
         reqs = W.serving_requests(args.requests, args.rate, seed=0)
-        srv = serve.Server(budget_bytes=args.budget_gb * 1e9, max_inflight=8, slot_rhs=8, restart=40,
-                           rtol=args.rtol, precond_precision=32)
-        # warm: one request of every n so that domain creation is not the first arrivals' latency
-        srv.serve([dict(r, arrival_s=0.0) for r in reqs[:0]], realtime=False)
-        t0 = time.perf_counter()
-        res = srv.serve(reqs, realtime=True)
-        wall = time.perf_counter() - t0
+        extra = {}
+        if args.server == "native":
+            t0 = time.perf_counter()
+            res, st = serve.serve_native(reqs, pool_bytes=args.budget_gb * 1e9, slot_rhs=8, restart=40,
+                                         rtol=args.rtol, precond_precision=32)
+            wall = time.perf_counter() - t0
+            extra = {"server": "fpg_batch runtime, one host thread", "domains_created": st["created"],
+                     "domains_evicted": st["evicted"]}
+        else:
+            srv = serve.Server(budget_bytes=args.budget_gb * 1e9, max_inflight=8, slot_rhs=8, restart=40,
+                               rtol=args.rtol, precond_precision=32)
+            t0 = time.perf_counter()
+            res = srv.serve(reqs, realtime=True)
+            wall = time.perf_counter() - t0
+            extra = {"server": "threaded Python server, 8 workers", "requests_coalesced": srv.coalesced,
+                     "domains_created": srv.created, "domains_evicted": srv.evicted,
+                     "peak_gb": srv.peak_bytes / 1e9}
+            srv.close()
         summ = serve.summarize(res, wall)
         lines.append({"metric": METRIC, "value": summ["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
                       "higher_is_better": True, "scaling": "weak", "dtype": "f64+f32precond", "data": "synthetic",
                       "config": {"workload": f"serving: {args.requests} Poisson requests at {args.rate}/s, "
                                              "geometry L/T/cross, n 64..1024, 1-8 RHS, kappa 0/-10",
-                                 "budget_gb": args.budget_gb, "max_inflight": 8, "restart": 40, "rtol": args.rtol},
+                                 "budget_gb": args.budget_gb, "restart": 40, "rtol": args.rtol,
+                                 "server": args.server},
                       "latency_ms": summ["latency_ms"], "requests": summ["requests"], "solves": summ["solves"],
                       "wall_s": wall, "residual_max": summ["residual_max"], "all_converged": summ["all_converged"],
-                      "failures": summ["failures"], "requests_coalesced": srv.coalesced,
-                      "domains_created": srv.created, "domains_evicted": srv.evicted,
-                      "peak_gb": srv.peak_bytes / 1e9})
-        srv.close()
+                      "failures": summ["failures"], **extra})
     for line in lines:
         print(json.dumps(line), flush=True)
 

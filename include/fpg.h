@@ -176,6 +176,57 @@ void fpg_destroy_domain(fpg_domain* d);
 fpg_status fpg_solve_many(fpg_domain* const* doms, int32_t count, double* const* p_dev,
                           fpg_solve_info* const* infos);
 
+/* ---- batch runtime: continuous batching of requests (serving) --------------
+ * A batch holds resident domains carved from one caller-owned device pool.  A
+ * request is a domain descriptor whose nrhs (1..slots) counts the request's
+ * right-hand sides, plus device pointers to them (f, block order, nrhs full
+ * vectors) and to its solution buffer (p, same shape).  Requests with equal
+ * descriptors apart from nrhs share one resident domain of `slots` right-hand
+ * sides: an idle domain takes its oldest pending requests whose right-hand
+ * sides fit and solves them as one batch (unused slots carry zero); requests
+ * arriving meanwhile join that domain's next batch.  Every resident domain
+ * runs on its own CUDA stream created by the library, so batches of different
+ * descriptors overlap on the device.  When a new descriptor does not fit the
+ * pool (workspace + solution buffer, fpg_workspace_bytes + 8 slots unknowns
+ * bytes) or max_domains is reached, idle domains without pending requests are
+ * evicted least recently used first; a request that still does not fit is
+ * refused with FPG_EBUDGET and nothing is queued.
+ * fpg_batch_step never waits on the device: it advances every domain whose
+ * last enqueued stage finished (restart flags, acceptance check, copy-out) and
+ * starts idle domains; *completed = tickets finished in this step.  The caller
+ * drives admit / step / poll from one host thread.  f must hold its values
+ * before fpg_batch_admit returns (synchronise the producing stream); f and p
+ * stay owned by the caller and must stay valid until fpg_batch_poll reports
+ * the ticket done (done = 1 also releases the ticket; info, if not NULL,
+ * receives nrhs entries).  fpg_batch_destroy waits for the device and frees
+ * every resident domain; the pool itself stays the caller's.
+ * Errors: FPG_EINVAL (arguments, descriptor, unknown ticket), FPG_EBUDGET,
+ * FPG_EUNSUPPORTED (descriptor), FPG_ENOMEM, FPG_ECUDA. */
+typedef struct {
+  int32_t slots;       /* right-hand sides per resident domain, 1..64 */
+  int32_t max_domains; /* resident domains at most, 1..256 */
+  int32_t reserved[2]; /* 0 */
+} fpg_batch_desc;
+
+typedef struct {
+  int32_t resident;     /* resident domains */
+  int32_t busy;         /* of them solving or copying out */
+  int32_t queued;       /* requests waiting for their domain's next batch */
+  int32_t open_tickets; /* admitted requests not yet finished */
+  int64_t pool_used;    /* pool bytes held by resident domains */
+  int64_t created;      /* domains created so far */
+  int64_t evicted;      /* domains evicted so far */
+} fpg_batch_stats_t;
+
+typedef struct fpg_batch fpg_batch;
+fpg_status fpg_batch_create(const fpg_batch_desc* desc, void* dev_pool, size_t pool_bytes, fpg_batch** out);
+fpg_status fpg_batch_admit(fpg_batch* b, const fpg_domain_desc* request, const double* f_dev, double* p_dev,
+                           int64_t* ticket);
+fpg_status fpg_batch_step(fpg_batch* b, int32_t* completed);
+fpg_status fpg_batch_poll(fpg_batch* b, int64_t ticket, int32_t* done, fpg_solve_info* info);
+fpg_status fpg_batch_stats(fpg_batch* b, fpg_batch_stats_t* out);
+void fpg_batch_destroy(fpg_batch* b);
+
 /* ---- operator entry points: each hot-path step on its own ------------------ */
 
 /* a1: preconditioner apply z = A_c^{-1} v for nvec centre-block vectors

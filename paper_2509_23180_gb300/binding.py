@@ -56,6 +56,16 @@ class SolveInfo(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("residual", ctypes.c_double), ("schur_residual", ctypes.c_double)]
 
 
+class BatchDescC(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_domains", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("resident", ctypes.c_int32), ("busy", ctypes.c_int32), ("queued", ctypes.c_int32),
+                ("open_tickets", ctypes.c_int32), ("pool_used", ctypes.c_int64), ("created", ctypes.c_int64),
+                ("evicted", ctypes.c_int64)]
+
+
 class TuneResult(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int32), ("mt", ctypes.c_int32), ("cluster", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("precond_ms", ctypes.c_double), ("arnoldi_ms", ctypes.c_double)]
@@ -107,6 +117,12 @@ _SIGS = {
     "fpg_rect_plan_create": ([_I32, _I32, _I32, _D, _D, _I32, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)], _I32),
     "fpg_rect_solve": ([_P, _P, _P, _I32], _I32),
     "fpg_rect_plan_destroy": ([_P], None),
+    "fpg_batch_create": ([_P, _P, ctypes.c_size_t, ctypes.POINTER(_P)], _I32),
+    "fpg_batch_admit": ([_P, _P, _P, _P, ctypes.POINTER(_I64)], _I32),
+    "fpg_batch_step": ([_P, ctypes.POINTER(_I32)], _I32),
+    "fpg_batch_poll": ([_P, _I64, ctypes.POINTER(_I32), _P], _I32),
+    "fpg_batch_stats": ([_P, _P], _I32),
+    "fpg_batch_destroy": ([_P], None),
     "fpg_box_plan_bytes": ([_I32, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)], _I32),
     "fpg_box_plan_create": ([_I32, _I32, _I32, _D, _D, _I32, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)], _I32),
     "fpg_box_solve": ([_P, _P, _P, _I32], _I32),
@@ -415,6 +431,58 @@ class BoxPlan:
     def close(self):
         if getattr(self, "handle", None):
             self.lib.fpg_box_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+class Batch:
+    """The library's batch runtime (fpg_batch_*): continuous batching of requests
+    over resident domains carved from one device pool (a torch uint8 tensor)."""
+
+    def __init__(self, pool_bytes: int, slots: int = 8, max_domains: int = 64, device="cuda"):
+        import torch
+        self.lib = load()
+        self.slots = slots
+        self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=device)
+        d = BatchDescC(slots, max_domains, (ctypes.c_int32 * 2)(0, 0))
+        h = _P()
+        _check(self.lib.fpg_batch_create(ctypes.byref(d), _ptr(self.pool), int(pool_bytes), ctypes.byref(h)),
+               "fpg_batch_create")
+        self.handle = h
+
+    def admit(self, desc: DomainDesc, f, p) -> int:
+        """f, p: CUDA float64 tensors (desc.nrhs, unknowns); f must be final (the
+        caller synchronises the stream that produced it); both stay referenced by
+        the caller until poll() reports the ticket done."""
+        t = _I64()
+        _check(self.lib.fpg_batch_admit(self.handle, ctypes.byref(desc), _ptr(f), _ptr(p), ctypes.byref(t)),
+               "fpg_batch_admit")
+        return int(t.value)
+
+    def step(self) -> int:
+        c = _I32()
+        _check(self.lib.fpg_batch_step(self.handle, ctypes.byref(c)), "fpg_batch_step")
+        return int(c.value)
+
+    def poll(self, ticket: int, nrhs: int):
+        """None while running; else the list of per-RHS info dicts (the ticket is released)."""
+        done = _I32()
+        arr = (SolveInfo * max(1, nrhs))()
+        _check(self.lib.fpg_batch_poll(self.handle, ticket, ctypes.byref(done), arr), "fpg_batch_poll")
+        if not done.value:
+            return None
+        return Domain._info_list(arr[:nrhs])
+
+    def stats(self) -> dict:
+        s = BatchStats()
+        _check(self.lib.fpg_batch_stats(self.handle, ctypes.byref(s)), "fpg_batch_stats")
+        return {k: getattr(s, k) for k, _ in BatchStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.fpg_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

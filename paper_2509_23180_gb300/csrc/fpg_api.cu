@@ -295,6 +295,7 @@ struct fpg_domain {
   double* p_cur = nullptr;
   int* h_done_pinned = nullptr;  // pinned host copy of the done flags
   cudaEvent_t ev_flags = nullptr;
+  int bphase = 0;  // non-blocking staged solve: 0 idle, 1 restart issued, 2 finish issued
 };
 
 namespace {
@@ -1151,6 +1152,60 @@ fpg_status collect_info(fpg_domain* D, fpg_solve_info* info) {
 }
 
 }  // namespace
+
+// ---- the staged solve without host waits (used by the batch runtime) --------
+namespace fpg {
+
+// Start a solve of the domain's right-hand sides into p (setup and the first
+// restart are issued on the domain's stream).
+fpg_status batch_start(fpg_domain* D, double* p) {
+  FPG_TRY(stage_setup(D, p));
+  FPG_TRY(stage_restart(D));
+  D->bphase = 1;
+  return FPG_OK;
+}
+
+// Has the work the host waits for next (restart flags or acceptance check) finished?
+bool batch_ready(fpg_domain* D) { return cudaEventQuery(D->ev_flags) == cudaSuccess; }
+
+// Advance a ready domain by one stage; *finished when its results are final.
+fpg_status batch_advance(fpg_domain* D, bool* finished) {
+  *finished = false;
+  if (D->bphase == 1) {
+    bool done = false;
+    FPG_TRY(stage_poll(D, &done));
+    if (done) {
+      FPG_TRY(stage_finish(D));
+      D->bphase = 2;
+    } else {
+      FPG_TRY(stage_cycle(D));
+      FPG_TRY(stage_restart(D));
+    }
+  } else if (D->bphase == 2) {
+    bool resume = false;
+    FPG_TRY(stage_resume(D, &resume));
+    if (resume) {
+      FPG_TRY(stage_restart(D));
+      D->bphase = 1;
+    } else {
+      D->bphase = 0;
+      *finished = true;
+    }
+  }
+  return FPG_OK;
+}
+
+fpg_status batch_info(fpg_domain* D, fpg_solve_info* info) { return collect_info(D, info); }
+
+// Zero right-hand-side slots first..nrhs-1 (they converge before the first Arnoldi step).
+fpg_status batch_zero_rhs(fpg_domain* D, int first) {
+  if (first >= D->desc.nrhs) return FPG_OK;
+  const size_t one = sizeof(double) * D->L.ntot;
+  FPG_CUDA_TRY(cudaMemsetAsync(D->f + (size_t)first * D->L.ntot, 0, one * (D->desc.nrhs - first), D->st));
+  return FPG_OK;
+}
+
+}  // namespace fpg
 
 // ============================================================================
 // ---- rectangle fast-solve plans (Sec. 2.1-2.2) --------------------------------

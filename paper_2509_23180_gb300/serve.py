@@ -270,6 +270,85 @@ class Server:
             self._bytes = 0.0
 
 
+def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart: int = 40, rtol: float = 1e-10,
+                 precond_precision: int = 32, max_domains: int = 64, realtime: bool = True, device: str = "cuda"):
+    """The same request stream through the library's batch runtime (fpg_batch_*):
+    one host thread admits every request at its arrival time into the resident
+    domain of its (geometry, n, kappa) -- the runtime coalesces the pending
+    requests of a key into that domain's next batch and evicts idle domains when
+    the pool is short -- steps the runtime (which never waits on the device) and
+    polls the tickets.  Right-hand sides are generated on the device as in
+    Server.solve_batch.  Returns (results in request order, runtime stats)."""
+    from collections import deque
+
+    import torch
+
+    import workloads as W
+    batch = B.Batch(int(pool_bytes), slots=slot_rhs, max_domains=max_domains, device=device)
+    order = sorted(range(len(requests)), key=lambda i: float(requests[i]["arrival_s"]))
+    live = {}          # ticket -> (request, f, p, admit time)
+    waiting = deque()  # arrived, refused for now: every domain that could make room is busy
+    results = {}
+    t0 = time.perf_counter()
+    nxt = 0
+
+    def key_bytes(desc):
+        full = B.make_desc(desc.geometry, desc.n, desc.kappa, nrhs=slot_rhs, restart=restart, rtol=rtol,
+                           precond_precision=precond_precision)
+        return B.workspace_bytes(full) + 8 * slot_rhs * B.unknowns(full)
+
+    def prepare(r):
+        geom, n, kappa, nr = r["geometry"], int(r["n"]), float(r["kappa"]), int(r["nrhs"])
+        desc = B.make_desc(geom, n, kappa, nrhs=nr, restart=restart, rtol=rtol, precond_precision=precond_precision)
+        f = torch.stack([W.fourier_rhs_torch(geom, n, int(r["seed"]) * 16 + i, device=device) for i in range(nr)])
+        torch.cuda.current_stream(device).synchronize()  # f final before the runtime copies it
+        return r, desc, f, torch.empty_like(f)
+
+    def try_admit(entry, now):
+        r, desc, f, p = entry
+        try:
+            live[batch.admit(desc, f, p)] = (r, f, p, now)
+            return True
+        except B.FpgError as e:
+            if e.status != B.FPG_EBUDGET or key_bytes(desc) > pool_bytes:
+                raise
+            return False
+
+    try:
+        while nxt < len(order) or live or waiting:
+            now = time.perf_counter() - t0
+            while waiting and try_admit(waiting[0], now):
+                waiting.popleft()
+            while nxt < len(order) and (not realtime or float(requests[order[nxt]]["arrival_s"]) <= now):
+                entry = prepare(requests[order[nxt]])
+                nxt += 1
+                if waiting or not try_admit(entry, now):
+                    waiting.append(entry)  # first come, first admitted
+            progressed = batch.step() > 0
+            for t in list(live):
+                r, f, p, t_adm = live[t]
+                info = batch.poll(t, int(r["nrhs"]))
+                if info is None:
+                    continue
+                end = time.perf_counter() - t0
+                arr = float(r["arrival_s"]) if realtime else 0.0
+                results[int(r["id"])] = Result(
+                    id=int(r["id"]), arrival_s=arr, start_s=t_adm, end_s=end, nrhs=int(r["nrhs"]),
+                    iterations=[i["iterations"] for i in info], residuals=[i["residual"] for i in info],
+                    status=max([i["status"] for i in info] or [0]),
+                    key=(r["geometry"], int(r["n"]), float(r["kappa"])))
+                del live[t]
+                progressed = True
+            if not progressed and nxt < len(order) and realtime and not waiting:
+                wait = float(requests[order[nxt]]["arrival_s"]) - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 2e-4))
+        stats = batch.stats()
+    finally:
+        batch.close()
+    return [results[int(r["id"])] for r in requests], stats
+
+
 def summarize(results, wall_s: float) -> dict:
     """Throughput and latency of a served stream."""
     import numpy as np

@@ -110,3 +110,11 @@ def test_chain_descriptor(lib):
     with pytest.raises(B.FpgError) as e:
         B.workspace_bytes(B.make_desc("cross", n, 0.0, chain=2))
     assert e.value.status == B.FPG_EINVAL
+
+
+def test_batch_create_arguments(lib):
+    """The batch runtime's descriptor checks need no device."""
+    h = ctypes.c_void_p()
+    for slots, maxd in ((0, 4), (65, 4), (8, 0), (8, 257)):
+        d = B.BatchDescC(slots, maxd, (ctypes.c_int32 * 2)(0, 0))
+        assert lib.fpg_batch_create(ctypes.byref(d), ctypes.c_void_p(4096), 1 << 20, ctypes.byref(h)) == B.FPG_EINVAL
