@@ -181,16 +181,18 @@ fpg_status fpg_solve_many(fpg_domain* const* doms, int32_t count, double* const*
  * request is a domain descriptor whose nrhs (1..slots) counts the request's
  * right-hand sides, plus device pointers to them (f, block order, nrhs full
  * vectors) and to its solution buffer (p, same shape).  Requests with equal
- * descriptors apart from nrhs share one resident domain of `slots` right-hand
- * sides: an idle domain takes its oldest pending requests whose right-hand
- * sides fit and solves them as one batch (unused slots carry zero); requests
- * arriving meanwhile join that domain's next batch.  Every resident domain
- * runs on its own CUDA stream created by the library, so batches of different
- * descriptors overlap on the device.  When a new descriptor does not fit the
- * pool (workspace + solution buffer, fpg_workspace_bytes + 8 slots unknowns
- * bytes) or max_domains is reached, idle domains without pending requests are
- * evicted least recently used first; a request that still does not fit is
- * refused with FPG_EBUDGET and nothing is queued.
+ * descriptors apart from nrhs form one queue, served by resident domains of
+ * that descriptor with `slots` right-hand sides each: an idle domain takes the
+ * oldest queued requests whose right-hand sides fit and solves them as one
+ * batch (unused slots carry zero); while all of a descriptor's domains are
+ * busy and requests wait, another domain of it is created if the pool has
+ * room (up to max_per_key).  Every resident domain runs on its own CUDA stream
+ * created by the library, so batches overlap on the device.  Admission needs
+ * one domain of the descriptor (workspace + solution buffer,
+ * fpg_workspace_bytes + 8 slots unknowns bytes); when the pool or max_domains
+ * is short, idle domains of descriptors with empty queues are evicted least
+ * recently used first, and a request that still finds no domain is refused
+ * with FPG_EBUDGET and nothing is queued.
  * fpg_batch_step never waits on the device: it advances every domain whose
  * last enqueued stage finished (restart flags, acceptance check, copy-out) and
  * starts idle domains; *completed = tickets finished in this step.  The caller
@@ -205,7 +207,8 @@ fpg_status fpg_solve_many(fpg_domain* const* doms, int32_t count, double* const*
 typedef struct {
   int32_t slots;       /* right-hand sides per resident domain, 1..64 */
   int32_t max_domains; /* resident domains at most, 1..256 */
-  int32_t reserved[2]; /* 0 */
+  int32_t max_per_key; /* resident domains per descriptor, 1..16 (0: 4) */
+  int32_t reserved;    /* 0 */
 } fpg_batch_desc;
 
 typedef struct {

@@ -4,12 +4,14 @@
 //
 // A request is a domain descriptor (its nrhs = the request's right-hand
 // sides), a device pointer to those right-hand sides and one for the
-// solutions.  Requests with the same descriptor (apart from nrhs) share a
-// resident domain of `slots` right-hand sides: a domain that is idle takes its
-// oldest pending requests whose right-hand sides fit its slots and solves them
-// in one batch (unused slots carry zero and converge at once), and requests that
-// arrive meanwhile wait for the next batch of that domain.  Each domain has its
-// own CUDA stream, so the batches of different keys overlap on the device.
+// solutions.  Requests with the same descriptor (apart from nrhs) form one
+// queue and are served by resident domains of that descriptor with `slots`
+// right-hand sides each: an idle domain takes the oldest queued requests whose
+// right-hand sides fit its slots and solves them in one batch (unused slots
+// carry zero and converge at once).  While every domain of a busy descriptor is
+// solving and its queue is not empty, another domain of it is created if the
+// pool has room (up to max_per_key).  Each domain has its own CUDA stream, so
+// batches overlap on the device.
 // fpg_batch_step never waits for the device: it advances every domain whose
 // last enqueued stage has finished (CUDA event query) and starts idle domains.
 // Domain workspaces and solution buffers are carved first-fit from the pool;
@@ -45,8 +47,15 @@ struct Request {
 
 enum class DomState { Idle, Running, Copying };
 
+struct KeyQueue {
+  fpg_domain_desc key;  // nrhs = slots
+  std::deque<Request> pending;
+  int residents = 0;
+};
+
 struct Resident {
   fpg_domain_desc key;  // nrhs = slots
+  KeyQueue* kq = nullptr;
   fpg_domain* d = nullptr;
   cudaStream_t st = nullptr;
   cudaEvent_t copied = nullptr;
@@ -54,7 +63,6 @@ struct Resident {
   double* pbuf = nullptr;
   long long ntot = 0;
   DomState state = DomState::Idle;
-  std::deque<Request> pending;
   std::vector<Request> running;
   std::vector<fpg_solve_info> infos;  // one per slot, from the last finished batch
   uint64_t last_used = 0;
@@ -77,7 +85,8 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 }  // namespace fpg
 
 struct fpg_batch {
-  int slots = 0, max_domains = 0;
+  int slots = 0, max_domains = 0, max_per_key = 0;
+  std::vector<fpg::KeyQueue*> keys;
   char* pool = nullptr;
   size_t pool_bytes = 0;
   std::vector<std::pair<size_t, size_t>> free_list;  // (offset, bytes), sorted, coalesced
@@ -123,6 +132,7 @@ void pool_give(fpg_batch* b, size_t off, size_t bytes) {
 
 void drop_resident(fpg_batch* b, size_t idx) {
   Resident* R = b->doms[idx];
+  R->kq->residents--;
   cudaStreamSynchronize(R->st);
   fpg_destroy_domain(R->d);
   cudaEventDestroy(R->copied);
@@ -137,7 +147,7 @@ bool evict_one(fpg_batch* b) {
   size_t best = b->doms.size();
   for (size_t i = 0; i < b->doms.size(); ++i) {
     const Resident* R = b->doms[i];
-    if (R->state != DomState::Idle || !R->pending.empty()) continue;
+    if (R->state != DomState::Idle || !R->kq->pending.empty()) continue;
     if (best == b->doms.size() || R->last_used < b->doms[best]->last_used) best = i;
   }
   if (best == b->doms.size()) return false;
@@ -146,7 +156,8 @@ bool evict_one(fpg_batch* b) {
   return true;
 }
 
-fpg_status make_resident(fpg_batch* b, const fpg_domain_desc& key, Resident** out) {
+fpg_status make_resident(fpg_batch* b, KeyQueue* kq, Resident** out) {
+  const fpg_domain_desc& key = kq->key;
   size_t ws = 0;
   FPG_TRY(fpg_workspace_bytes(&key, &ws));
   int64_t ntot = 0;
@@ -165,6 +176,7 @@ fpg_status make_resident(fpg_batch* b, const fpg_domain_desc& key, Resident** ou
     return FPG_ENOMEM;
   }
   R->key = key;
+  R->kq = kq;
   R->off = off;
   R->bytes = need;
   R->ntot = ntot;
@@ -182,18 +194,20 @@ fpg_status make_resident(fpg_batch* b, const fpg_domain_desc& key, Resident** ou
     return s;
   }
   b->doms.push_back(R);
+  kq->residents++;
   b->created++;
   *out = R;
   return FPG_OK;
 }
 
-// An idle domain takes its oldest pending requests that fit its slots and starts.
+// An idle domain takes the oldest queued requests of its key that fit its slots and starts.
 fpg_status start_batch(fpg_batch* b, Resident* R) {
   int used = 0;
-  while (!R->pending.empty() && used + R->pending.front().nrhs <= R->key.nrhs) {
-    R->running.push_back(R->pending.front());
-    used += R->pending.front().nrhs;
-    R->pending.pop_front();
+  std::deque<Request>& q = R->kq->pending;
+  while (!q.empty() && used + q.front().nrhs <= R->key.nrhs) {
+    R->running.push_back(q.front());
+    used += q.front().nrhs;
+    q.pop_front();
   }
   if (R->running.empty()) return FPG_OK;
   int slot = 0;
@@ -217,12 +231,13 @@ extern "C" {
 
 fpg_status fpg_batch_create(const fpg_batch_desc* desc, void* pool, size_t pool_bytes, fpg_batch** out) {
   if (!desc || !pool || !out || desc->slots < 1 || desc->slots > 64 || desc->max_domains < 1 ||
-      desc->max_domains > 256)
+      desc->max_domains > 256 || desc->max_per_key < 0 || desc->max_per_key > 16 || desc->reserved != 0)
     return FPG_EINVAL;
   fpg_batch* b = new (std::nothrow) fpg_batch();
   if (!b) return FPG_ENOMEM;
   b->slots = desc->slots;
   b->max_domains = desc->max_domains;
+  b->max_per_key = desc->max_per_key > 0 ? desc->max_per_key : 4;
   // the pool starts at a 256-byte boundary
   const uintptr_t base = reinterpret_cast<uintptr_t>(pool);
   const size_t skip = (256 - base % 256) % 256;
@@ -242,16 +257,26 @@ fpg_status fpg_batch_admit(fpg_batch* b, const fpg_domain_desc* req, const doubl
   if (!b || !req || !f_dev || !p_dev || !ticket || req->nrhs < 1 || req->nrhs > b->slots) return FPG_EINVAL;
   fpg_domain_desc key = *req;
   key.nrhs = b->slots;
-  Resident* R = nullptr;
-  for (Resident* x : b->doms)
+  size_t ws = 0;
+  FPG_TRY(fpg_workspace_bytes(&key, &ws));  // descriptor errors before anything is queued
+  KeyQueue* kq = nullptr;
+  for (KeyQueue* x : b->keys)
     if (same_key(x->key, key)) {
-      R = x;
+      kq = x;
       break;
     }
-  if (!R) FPG_TRY(make_resident(b, key, &R));
+  if (!kq) {
+    kq = new (std::nothrow) KeyQueue();
+    if (!kq) return FPG_ENOMEM;
+    kq->key = key;
+    b->keys.push_back(kq);
+  }
+  if (kq->residents == 0) {  // the key needs one domain to make progress
+    Resident* R = nullptr;
+    FPG_TRY(make_resident(b, kq, &R));
+  }
   const int64_t t = b->next_ticket++;
-  R->pending.push_back(Request{t, f_dev, p_dev, req->nrhs});
-  R->last_used = ++b->clock;
+  kq->pending.push_back(Request{t, f_dev, p_dev, req->nrhs});
   b->tickets[t] = TicketState{};
   *ticket = t;
   return FPG_OK;
@@ -289,7 +314,14 @@ fpg_status fpg_batch_step(fpg_batch* b, int32_t* completed) {
       R->running.clear();
       R->state = DomState::Idle;
     }
-    if (R->state == DomState::Idle && !R->pending.empty()) FPG_TRY(start_batch(b, R));
+    if (R->state == DomState::Idle && !R->kq->pending.empty()) FPG_TRY(start_batch(b, R));
+  }
+  // a key whose domains are all busy while requests wait gets one more domain,
+  // if the pool has room (idle domains of keys with empty queues may be evicted)
+  for (KeyQueue* kq : b->keys) {
+    if (kq->pending.empty() || kq->residents >= b->max_per_key) continue;
+    Resident* R = nullptr;
+    if (make_resident(b, kq, &R) == FPG_OK) FPG_TRY(start_batch(b, R));
   }
   if (completed) *completed = done;
   return FPG_OK;
@@ -314,8 +346,8 @@ fpg_status fpg_batch_stats(fpg_batch* b, fpg_batch_stats_t* out) {
   for (const Resident* R : b->doms) {
     out->pool_used += (int64_t)R->bytes;
     if (R->state != DomState::Idle) out->busy++;
-    out->queued += (int32_t)R->pending.size();
   }
+  for (const KeyQueue* kq : b->keys) out->queued += (int32_t)kq->pending.size();
   for (const auto& kv : b->tickets) out->open_tickets += kv.second.done ? 0 : 1;
   out->created = b->created;
   out->evicted = b->evicted;
@@ -324,9 +356,8 @@ fpg_status fpg_batch_stats(fpg_batch* b, fpg_batch_stats_t* out) {
 
 void fpg_batch_destroy(fpg_batch* b) {
   if (!b) return;
-  while (!b->doms.empty()) {
-    drop_resident(b, b->doms.size() - 1);
-  }
+  while (!b->doms.empty()) drop_resident(b, b->doms.size() - 1);
+  for (KeyQueue* kq : b->keys) delete kq;
   delete b;
 }
 

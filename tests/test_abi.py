@@ -115,6 +115,6 @@ def test_chain_descriptor(lib):
 def test_batch_create_arguments(lib):
     """The batch runtime's descriptor checks need no device."""
     h = ctypes.c_void_p()
-    for slots, maxd in ((0, 4), (65, 4), (8, 0), (8, 257)):
-        d = B.BatchDescC(slots, maxd, (ctypes.c_int32 * 2)(0, 0))
+    for slots, maxd, per in ((0, 4, 0), (65, 4, 0), (8, 0, 0), (8, 257, 0), (8, 4, 17), (8, 4, -1)):
+        d = B.BatchDescC(slots, maxd, per, 0)
         assert lib.fpg_batch_create(ctypes.byref(d), ctypes.c_void_p(4096), 1 << 20, ctypes.byref(h)) == B.FPG_EINVAL
