@@ -186,7 +186,7 @@ fpg_status fpg_solve_many(fpg_domain* const* doms, int32_t count, double* const*
  * oldest queued requests whose right-hand sides fit and solves them as one
  * batch (unused slots carry zero); while all of a descriptor's domains are
  * busy and requests wait, another domain of it is created if the pool has
- * room (up to max_per_key).  Every resident domain runs on its own CUDA stream
+ * room without evicting (up to max_per_key).  Every resident domain runs on its own CUDA stream
  * created by the library, so batches overlap on the device.  Admission needs
  * one domain of the descriptor (workspace + solution buffer,
  * fpg_workspace_bytes + 8 slots unknowns bytes); when the pool or max_domains
@@ -195,7 +195,9 @@ fpg_status fpg_solve_many(fpg_domain* const* doms, int32_t count, double* const*
  * with FPG_EBUDGET and nothing is queued.
  * fpg_batch_step never waits on the device: it advances every domain whose
  * last enqueued stage finished (restart flags, acceptance check, copy-out) and
- * starts idle domains; *completed = tickets finished in this step.  The caller
+ * starts idle domains; *completed = tickets finished in this step, the first
+ * min(*completed, cap) of them written to finished_tickets (host array, may be
+ * NULL when cap = 0; the others stay pollable).  The caller
  * drives admit / step / poll from one host thread.  f must hold its values
  * before fpg_batch_admit returns (synchronise the producing stream); f and p
  * stay owned by the caller and must stay valid until fpg_batch_poll reports
@@ -225,7 +227,7 @@ typedef struct fpg_batch fpg_batch;
 fpg_status fpg_batch_create(const fpg_batch_desc* desc, void* dev_pool, size_t pool_bytes, fpg_batch** out);
 fpg_status fpg_batch_admit(fpg_batch* b, const fpg_domain_desc* request, const double* f_dev, double* p_dev,
                            int64_t* ticket);
-fpg_status fpg_batch_step(fpg_batch* b, int32_t* completed);
+fpg_status fpg_batch_step(fpg_batch* b, int64_t* finished_tickets, int32_t cap, int32_t* completed);
 fpg_status fpg_batch_poll(fpg_batch* b, int64_t ticket, int32_t* done, fpg_solve_info* info);
 fpg_status fpg_batch_stats(fpg_batch* b, fpg_batch_stats_t* out);
 void fpg_batch_destroy(fpg_batch* b);

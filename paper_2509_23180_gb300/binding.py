@@ -120,7 +120,7 @@ _SIGS = {
     "fpg_rect_plan_destroy": ([_P], None),
     "fpg_batch_create": ([_P, _P, ctypes.c_size_t, ctypes.POINTER(_P)], _I32),
     "fpg_batch_admit": ([_P, _P, _P, _P, ctypes.POINTER(_I64)], _I32),
-    "fpg_batch_step": ([_P, ctypes.POINTER(_I32)], _I32),
+    "fpg_batch_step": ([_P, _P, _I32, ctypes.POINTER(_I32)], _I32),
     "fpg_batch_poll": ([_P, _I64, ctypes.POINTER(_I32), _P], _I32),
     "fpg_batch_stats": ([_P, _P], _I32),
     "fpg_batch_destroy": ([_P], None),
@@ -442,7 +442,7 @@ class Batch:
     """The library's batch runtime (fpg_batch_*): continuous batching of requests
     over resident domains carved from one device pool (a torch uint8 tensor)."""
 
-    def __init__(self, pool_bytes: int, slots: int = 8, max_domains: int = 64, max_per_key: int = 4, device="cuda"):
+    def __init__(self, pool_bytes: int, slots: int = 8, max_domains: int = 64, max_per_key: int = 2, device="cuda"):
         import torch
         self.lib = load()
         self.slots = slots
@@ -462,10 +462,13 @@ class Batch:
                "fpg_batch_admit")
         return int(t.value)
 
-    def step(self) -> int:
+    def step(self) -> list:
+        """Advance the runtime; returns the tickets that finished in this step."""
+        cap = 256
+        buf = (_I64 * cap)()
         c = _I32()
-        _check(self.lib.fpg_batch_step(self.handle, ctypes.byref(c)), "fpg_batch_step")
-        return int(c.value)
+        _check(self.lib.fpg_batch_step(self.handle, buf, cap, ctypes.byref(c)), "fpg_batch_step")
+        return list(buf[:min(cap, c.value)])
 
     def poll(self, ticket: int, nrhs: int):
         """None while running; else the list of per-RHS info dicts (the ticket is released)."""

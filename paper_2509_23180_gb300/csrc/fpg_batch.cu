@@ -156,7 +156,7 @@ bool evict_one(fpg_batch* b) {
   return true;
 }
 
-fpg_status make_resident(fpg_batch* b, KeyQueue* kq, Resident** out) {
+fpg_status make_resident(fpg_batch* b, KeyQueue* kq, bool may_evict, Resident** out) {
   const fpg_domain_desc& key = kq->key;
   size_t ws = 0;
   FPG_TRY(fpg_workspace_bytes(&key, &ws));
@@ -168,7 +168,7 @@ fpg_status make_resident(fpg_batch* b, KeyQueue* kq, Resident** out) {
   size_t off = 0;
   for (;;) {
     if ((int)b->doms.size() < b->max_domains && pool_take(b, need, &off)) break;
-    if (!evict_one(b)) return FPG_EBUDGET;
+    if (!may_evict || !evict_one(b)) return FPG_EBUDGET;
   }
   Resident* R = new (std::nothrow) Resident();
   if (!R) {
@@ -273,7 +273,7 @@ fpg_status fpg_batch_admit(fpg_batch* b, const fpg_domain_desc* req, const doubl
   }
   if (kq->residents == 0) {  // the key needs one domain to make progress
     Resident* R = nullptr;
-    FPG_TRY(make_resident(b, kq, &R));
+    FPG_TRY(make_resident(b, kq, true, &R));
   }
   const int64_t t = b->next_ticket++;
   kq->pending.push_back(Request{t, f_dev, p_dev, req->nrhs});
@@ -282,8 +282,8 @@ fpg_status fpg_batch_admit(fpg_batch* b, const fpg_domain_desc* req, const doubl
   return FPG_OK;
 }
 
-fpg_status fpg_batch_step(fpg_batch* b, int32_t* completed) {
-  if (!b) return FPG_EINVAL;
+fpg_status fpg_batch_step(fpg_batch* b, int64_t* finished_tickets, int32_t cap, int32_t* completed) {
+  if (!b || cap < 0 || (cap > 0 && !finished_tickets)) return FPG_EINVAL;
   int done = 0;
   for (Resident* R : b->doms) {
     if (R->state == DomState::Running && batch_ready(R->d)) {
@@ -309,6 +309,7 @@ fpg_status fpg_batch_step(fpg_batch* b, int32_t* completed) {
         ts.info.assign(R->infos.begin() + slot, R->infos.begin() + slot + q.nrhs);
         ts.done = true;
         slot += q.nrhs;
+        if (done < cap) finished_tickets[done] = q.ticket;
         ++done;
       }
       R->running.clear();
@@ -316,12 +317,13 @@ fpg_status fpg_batch_step(fpg_batch* b, int32_t* completed) {
     }
     if (R->state == DomState::Idle && !R->kq->pending.empty()) FPG_TRY(start_batch(b, R));
   }
-  // a key whose domains are all busy while requests wait gets one more domain,
-  // if the pool has room (idle domains of keys with empty queues may be evicted)
+  // a key whose domains are all busy while requests wait gets one more domain
+  // from free pool space (no eviction: that would trade one key's domain for
+  // another's creation)
   for (KeyQueue* kq : b->keys) {
     if (kq->pending.empty() || kq->residents >= b->max_per_key) continue;
     Resident* R = nullptr;
-    if (make_resident(b, kq, &R) == FPG_OK) FPG_TRY(start_batch(b, R));
+    if (make_resident(b, kq, false, &R) == FPG_OK) FPG_TRY(start_batch(b, R));
   }
   if (completed) *completed = done;
   return FPG_OK;

@@ -83,32 +83,30 @@ k_chain_schur_lines(const Tz* __restrict__ z, long long zstride, ChainGeom G, co
 }
 
 // a2 stencil part: w = A_row z - the interface terms on the lines next to the arms.
+// One CTA per (row j, right-hand side), threads along the row: no index division.
 template <typename Tz>
 __global__ void __launch_bounds__(kChainThreads)
 k_chain_stencil(const Tz* __restrict__ z, long long zstride, double* __restrict__ w, long long wstride, ChainGeom G,
                 double delta, double kappa, const double* __restrict__ corr, const int* __restrict__ active) {
-  const int r = blockIdx.y;
+  const int r = blockIdx.y, j = blockIdx.x;
   if (active != nullptr && !active[r]) return;
   const int n = G.n, nxc = G.nxc, K = G.K, nslots = 2 * K + 2;
-  const Tz* zr = z + (long long)r * zstride;
-  double* wr = w + (long long)r * wstride;
+  const Tz* zr = z + (long long)r * zstride + (long long)j * nxc;
+  double* wr = w + (long long)r * wstride + (long long)j * nxc;
   const double* cr = corr + (long long)r * nslots * n;
-  const long long nc = (long long)nxc * n;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nc;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(idx / nxc), i = (int)(idx - (long long)j * nxc);
-    const double zc = cld(zr, idx);
-    const double s = stencil_sum(zc, i > 0 ? cld(zr, idx - 1) : 0.0, i < nxc - 1 ? cld(zr, idx + 1) : 0.0,
-                                 j > 0 ? cld(zr, idx - nxc) : 0.0, j < n - 1 ? cld(zr, idx + nxc) : 0.0);
+  const int period = 2 * (n + 1);
+  for (int i = threadIdx.x; i < nxc; i += blockDim.x) {
+    const double zc = cld(zr, i);
+    const double s = stencil_sum(zc, i > 0 ? cld(zr, i - 1) : 0.0, i < nxc - 1 ? cld(zr, i + 1) : 0.0,
+                                 j > 0 ? cld(zr, i - nxc) : 0.0, j < n - 1 ? cld(zr, i + nxc) : 0.0);
     double v = fma(delta, s, kappa * zc);
     if (i == 0) v -= cr[0 * n + j];
     if (i == nxc - 1) v -= cr[1 * n + j];
-    const int a = i / (2 * (n + 1)), q = i - chain_x0(G, a);
-    if (q < n) {  // column under / over centre a
-      if (j == 0) v -= cr[(2 + a) * n + q];
-      if (j == n - 1) v -= cr[(2 + K + a) * n + q];
+    if (j == 0 || j == n - 1) {
+      const int a = i / period, q = i - a * period;
+      if (q < n) v -= j == 0 ? cr[(2 + a) * n + q] : cr[(2 + K + a) * n + q];  // column under / over centre a (n >= 2)
     }
-    wr[idx] = v;
+    wr[i] = v;
   }
 }
 
@@ -269,7 +267,8 @@ cudaError_t launch_chain_schur(const void* z, int zprec, long long zstride, cons
 cudaError_t launch_chain_stencil(const void* z, int zprec, long long zstride, double* w, long long wstride,
                                  const ChainGeom& G, double delta, double kappa, const double* corr,
                                  const int* active, int nrhs, int gx, cudaStream_t st) {
-  dim3 grid(gx, nrhs);
+  (void)gx;
+  dim3 grid(G.n, nrhs);
   if (zprec == 64)
     k_chain_stencil<double><<<grid, kChainThreads, 0, st>>>((const double*)z, zstride, w, wstride, G, delta, kappa,
                                                             corr, active);

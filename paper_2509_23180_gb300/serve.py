@@ -271,80 +271,116 @@ class Server:
 
 
 def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart: int = 40, rtol: float = 1e-10,
-                 precond_precision: int = 32, max_domains: int = 64, realtime: bool = True, device: str = "cuda"):
-    """The same request stream through the library's batch runtime (fpg_batch_*):
-    one host thread admits every request at its arrival time into the resident
-    domain of its (geometry, n, kappa) -- the runtime coalesces the pending
-    requests of a key into that domain's next batch and evicts idle domains when
-    the pool is short -- steps the runtime (which never waits on the device) and
-    polls the tickets.  Right-hand sides are generated on the device as in
-    Server.solve_batch.  Returns (results in request order, runtime stats)."""
+                 precond_precision: int = 32, max_domains: int = 64, max_per_key: int = 2, realtime: bool = True,
+                 device: str = "cuda"):
+    """The same request stream through the library's batch runtime (fpg_batch_*).
+    A producer thread plays the clients: at each request's arrival time it
+    builds the right-hand sides on the device (its own stream) and hands the
+    request over.  The driver thread admits it into the runtime -- which queues
+    it with the other requests of its (geometry, n, kappa) for the next batch of
+    a resident domain and evicts idle domains when the pool is short -- steps the
+    runtime, which never waits on the device, and collects the tickets it
+    reports finished.  A request refused for lack of idle room waits and is
+    admitted first when room frees.  Returns (results in request order, stats)."""
+    import queue
     from collections import deque
 
     import torch
 
     import workloads as W
-    batch = B.Batch(int(pool_bytes), slots=slot_rhs, max_domains=max_domains, device=device)
+    batch = B.Batch(int(pool_bytes), slots=slot_rhs, max_domains=max_domains, max_per_key=max_per_key,
+                    device=device)
     order = sorted(range(len(requests)), key=lambda i: float(requests[i]["arrival_s"]))
+    ready = queue.Queue()
     live = {}          # ticket -> (request, f, p, admit time)
-    waiting = deque()  # arrived, refused for now: every domain that could make room is busy
+    waiting = deque()  # prepared, refused for now
     results = {}
     t0 = time.perf_counter()
-    nxt = 0
+    stop = threading.Event()
+
+    def producer():
+        stream = torch.cuda.Stream(device=device)
+        try:
+            for i in order:
+                if stop.is_set():
+                    return
+                r = requests[i]
+                if realtime:
+                    delay = float(r["arrival_s"]) - (time.perf_counter() - t0)
+                    if delay > 0:
+                        time.sleep(delay)
+                geom, n, kappa, nr = r["geometry"], int(r["n"]), float(r["kappa"]), int(r["nrhs"])
+                with torch.cuda.stream(stream):
+                    f = torch.stack([W.fourier_rhs_torch(geom, n, int(r["seed"]) * 16 + j, device=device)
+                                     for j in range(nr)])
+                    p = torch.empty_like(f)
+                stream.synchronize()  # f final before the runtime copies it
+                desc = B.make_desc(geom, n, kappa, nrhs=nr, restart=restart, rtol=rtol,
+                                   precond_precision=precond_precision)
+                ready.put((r, desc, f, p))
+        finally:
+            ready.put(None)
 
     def key_bytes(desc):
         full = B.make_desc(desc.geometry, desc.n, desc.kappa, nrhs=slot_rhs, restart=restart, rtol=rtol,
                            precond_precision=precond_precision)
         return B.workspace_bytes(full) + 8 * slot_rhs * B.unknowns(full)
 
-    def prepare(r):
-        geom, n, kappa, nr = r["geometry"], int(r["n"]), float(r["kappa"]), int(r["nrhs"])
-        desc = B.make_desc(geom, n, kappa, nrhs=nr, restart=restart, rtol=rtol, precond_precision=precond_precision)
-        f = torch.stack([W.fourier_rhs_torch(geom, n, int(r["seed"]) * 16 + i, device=device) for i in range(nr)])
-        torch.cuda.current_stream(device).synchronize()  # f final before the runtime copies it
-        return r, desc, f, torch.empty_like(f)
-
-    def try_admit(entry, now):
+    def try_admit(entry):
         r, desc, f, p = entry
         try:
-            live[batch.admit(desc, f, p)] = (r, f, p, now)
+            live[batch.admit(desc, f, p)] = (r, f, p, time.perf_counter() - t0)
             return True
         except B.FpgError as e:
             if e.status != B.FPG_EBUDGET or key_bytes(desc) > pool_bytes:
                 raise
             return False
 
+    def collect(t):
+        r, f, p, t_adm = live[t]
+        info = batch.poll(t, int(r["nrhs"]))
+        if info is None:
+            return False
+        results[int(r["id"])] = Result(
+            id=int(r["id"]), arrival_s=float(r["arrival_s"]) if realtime else 0.0, start_s=t_adm,
+            end_s=time.perf_counter() - t0, nrhs=int(r["nrhs"]),
+            iterations=[i["iterations"] for i in info], residuals=[i["residual"] for i in info],
+            status=max([i["status"] for i in info] or [0]), key=(r["geometry"], int(r["n"]), float(r["kappa"])))
+        del live[t]
+        return True
+
+    th = threading.Thread(target=producer, daemon=True)
+    th.start()
+    produced_all = False
     try:
-        while nxt < len(order) or live or waiting:
-            now = time.perf_counter() - t0
-            while waiting and try_admit(waiting[0], now):
+        while not produced_all or live or waiting:
+            progressed = False
+            while waiting and try_admit(waiting[0]):
                 waiting.popleft()
-            while nxt < len(order) and (not realtime or float(requests[order[nxt]]["arrival_s"]) <= now):
-                entry = prepare(requests[order[nxt]])
-                nxt += 1
-                if waiting or not try_admit(entry, now):
-                    waiting.append(entry)  # first come, first admitted
-            progressed = batch.step() > 0
-            for t in list(live):
-                r, f, p, t_adm = live[t]
-                info = batch.poll(t, int(r["nrhs"]))
-                if info is None:
-                    continue
-                end = time.perf_counter() - t0
-                arr = float(r["arrival_s"]) if realtime else 0.0
-                results[int(r["id"])] = Result(
-                    id=int(r["id"]), arrival_s=arr, start_s=t_adm, end_s=end, nrhs=int(r["nrhs"]),
-                    iterations=[i["iterations"] for i in info], residuals=[i["residual"] for i in info],
-                    status=max([i["status"] for i in info] or [0]),
-                    key=(r["geometry"], int(r["n"]), float(r["kappa"])))
-                del live[t]
                 progressed = True
-            if not progressed and nxt < len(order) and realtime and not waiting:
-                wait = float(requests[order[nxt]]["arrival_s"]) - (time.perf_counter() - t0)
-                if wait > 0:
-                    time.sleep(min(wait, 2e-4))
+            while True:
+                try:
+                    entry = ready.get_nowait()
+                except queue.Empty:
+                    break
+                if entry is None:
+                    produced_all = True
+                    break
+                if waiting or not try_admit(entry):
+                    waiting.append(entry)  # first come, first admitted
+                progressed = True
+            finished = batch.step()
+            for t in finished:
+                progressed |= collect(t)
+            if len(finished) >= 256:  # more finished than reported: poll the rest
+                for t in list(live):
+                    collect(t)
+            if not progressed:
+                time.sleep(5e-5)
         stats = batch.stats()
     finally:
+        stop.set()
+        th.join()
         batch.close()
     return [results[int(r["id"])] for r in requests], stats
 

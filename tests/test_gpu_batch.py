@@ -33,9 +33,10 @@ def run(batch, live, limit=200000):
     """Step until every ticket of `live` is done; returns {ticket: info}."""
     out = {}
     for _ in range(limit):
-        batch.step()
+        finished = set(batch.step())
         for t, nr in list(live.items()):
             info = batch.poll(t, nr)
+            assert (info is not None) == (t in finished)  # step reports exactly the tickets it finished
             if info is not None:
                 out[t] = info
                 del live[t]
