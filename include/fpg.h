@@ -210,7 +210,7 @@ typedef struct {
   int32_t slots;       /* right-hand sides per resident domain, 1..64 */
   int32_t max_domains; /* resident domains at most, 1..256 */
   int32_t max_per_key; /* resident domains per descriptor, 1..16 (0: 4) */
-  int32_t reserved;    /* 0 */
+  int32_t max_busy;    /* domains solving at once, >= 1 (0: no limit); batches start oldest request first */
 } fpg_batch_desc;
 
 typedef struct {

@@ -58,7 +58,7 @@ class SolveInfo(ctypes.Structure):
 
 class BatchDescC(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("max_domains", ctypes.c_int32), ("max_per_key", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("max_busy", ctypes.c_int32)]
 
 
 class BatchStats(ctypes.Structure):
@@ -442,12 +442,13 @@ class Batch:
     """The library's batch runtime (fpg_batch_*): continuous batching of requests
     over resident domains carved from one device pool (a torch uint8 tensor)."""
 
-    def __init__(self, pool_bytes: int, slots: int = 8, max_domains: int = 64, max_per_key: int = 2, device="cuda"):
+    def __init__(self, pool_bytes: int, slots: int = 8, max_domains: int = 64, max_per_key: int = 2, max_busy: int = 0,
+                 device="cuda"):
         import torch
         self.lib = load()
         self.slots = slots
         self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=device)
-        d = BatchDescC(slots, max_domains, max_per_key, 0)
+        d = BatchDescC(slots, max_domains, max_per_key, max_busy)
         h = _P()
         _check(self.lib.fpg_batch_create(ctypes.byref(d), _ptr(self.pool), int(pool_bytes), ctypes.byref(h)),
                "fpg_batch_create")

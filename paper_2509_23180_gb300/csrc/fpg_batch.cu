@@ -85,7 +85,7 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 }  // namespace fpg
 
 struct fpg_batch {
-  int slots = 0, max_domains = 0, max_per_key = 0;
+  int slots = 0, max_domains = 0, max_per_key = 0, max_busy = 0;
   std::vector<fpg::KeyQueue*> keys;
   char* pool = nullptr;
   size_t pool_bytes = 0;
@@ -231,13 +231,14 @@ extern "C" {
 
 fpg_status fpg_batch_create(const fpg_batch_desc* desc, void* pool, size_t pool_bytes, fpg_batch** out) {
   if (!desc || !pool || !out || desc->slots < 1 || desc->slots > 64 || desc->max_domains < 1 ||
-      desc->max_domains > 256 || desc->max_per_key < 0 || desc->max_per_key > 16 || desc->reserved != 0)
+      desc->max_domains > 256 || desc->max_per_key < 0 || desc->max_per_key > 16 || desc->max_busy < 0)
     return FPG_EINVAL;
   fpg_batch* b = new (std::nothrow) fpg_batch();
   if (!b) return FPG_ENOMEM;
   b->slots = desc->slots;
   b->max_domains = desc->max_domains;
   b->max_per_key = desc->max_per_key > 0 ? desc->max_per_key : 4;
+  b->max_busy = desc->max_busy > 0 ? desc->max_busy : 1 << 30;
   // the pool starts at a 256-byte boundary
   const uintptr_t base = reinterpret_cast<uintptr_t>(pool);
   const size_t skip = (256 - base % 256) % 256;
@@ -315,15 +316,30 @@ fpg_status fpg_batch_step(fpg_batch* b, int64_t* finished_tickets, int32_t cap, 
       R->running.clear();
       R->state = DomState::Idle;
     }
-    if (R->state == DomState::Idle && !R->kq->pending.empty()) FPG_TRY(start_batch(b, R));
   }
-  // a key whose domains are all busy while requests wait gets one more domain
+  // start batches, oldest queued request first, while fewer than max_busy
+  // domains are solving; a key whose domains are all busy gets one more domain
   // from free pool space (no eviction: that would trade one key's domain for
   // another's creation)
-  for (KeyQueue* kq : b->keys) {
-    if (kq->pending.empty() || kq->residents >= b->max_per_key) continue;
-    Resident* R = nullptr;
-    if (make_resident(b, kq, false, &R) == FPG_OK) FPG_TRY(start_batch(b, R));
+  int busy = 0;
+  for (const Resident* R : b->doms) busy += R->state != DomState::Idle;
+  std::vector<KeyQueue*> order;
+  for (KeyQueue* kq : b->keys)
+    if (!kq->pending.empty()) order.push_back(kq);
+  std::sort(order.begin(), order.end(),
+            [](const KeyQueue* x, const KeyQueue* y) { return x->pending.front().ticket < y->pending.front().ticket; });
+  for (KeyQueue* kq : order) {
+    while (busy < b->max_busy && !kq->pending.empty()) {
+      Resident* R = nullptr;
+      for (Resident* x : b->doms)
+        if (x->kq == kq && x->state == DomState::Idle) {
+          R = x;
+          break;
+        }
+      if (!R && (kq->residents >= b->max_per_key || make_resident(b, kq, false, &R) != FPG_OK)) break;
+      FPG_TRY(start_batch(b, R));
+      ++busy;
+    }
   }
   if (completed) *completed = done;
   return FPG_OK;

@@ -271,8 +271,8 @@ class Server:
 
 
 def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart: int = 40, rtol: float = 1e-10,
-                 precond_precision: int = 32, max_domains: int = 64, max_per_key: int = 2, realtime: bool = True,
-                 device: str = "cuda"):
+                 precond_precision: int = 32, max_domains: int = 64, max_per_key: int = 2, max_busy: int = 8,
+                 realtime: bool = True, device: str = "cuda"):
     """The same request stream through the library's batch runtime (fpg_batch_*).
     A producer thread plays the clients: at each request's arrival time it
     builds the right-hand sides on the device (its own stream) and hands the
@@ -289,7 +289,7 @@ def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart
 
     import workloads as W
     batch = B.Batch(int(pool_bytes), slots=slot_rhs, max_domains=max_domains, max_per_key=max_per_key,
-                    device=device)
+                    max_busy=max_busy, device=device)
     order = sorted(range(len(requests)), key=lambda i: float(requests[i]["arrival_s"]))
     ready = queue.Queue()
     live = {}          # ticket -> (request, f, p, admit time)

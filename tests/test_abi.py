@@ -115,6 +115,7 @@ def test_chain_descriptor(lib):
 def test_batch_create_arguments(lib):
     """The batch runtime's descriptor checks need no device."""
     h = ctypes.c_void_p()
-    for slots, maxd, per in ((0, 4, 0), (65, 4, 0), (8, 0, 0), (8, 257, 0), (8, 4, 17), (8, 4, -1)):
-        d = B.BatchDescC(slots, maxd, per, 0)
+    for slots, maxd, per, busy in ((0, 4, 0, 0), (65, 4, 0, 0), (8, 0, 0, 0), (8, 257, 0, 0), (8, 4, 17, 0),
+                                   (8, 4, -1, 0), (8, 4, 0, -1)):
+        d = B.BatchDescC(slots, maxd, per, busy)
         assert lib.fpg_batch_create(ctypes.byref(d), ctypes.c_void_p(4096), 1 << 20, ctypes.byref(h)) == B.FPG_EINVAL
