@@ -25,7 +25,8 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("nx,ny,nz", [(2, 3, 1), (8, 6, 5), (16, 16, 16), (64, 40, 9)])
+@pytest.mark.parametrize("nx,ny,nz", [(2, 3, 1), (2, 2, 1), (8, 6, 5), (16, 16, 16), (64, 40, 9), (4096, 3, 2),
+                                      (5, 4096, 2)])
 def test_box_modes(lib, nx, ny, nz):
     from paper_2509_23180_gb300 import binding as B
     h, kappa = 1.0 / (nx + 1), -10.0

@@ -60,3 +60,36 @@ def test_rect_plan_limits(lib):
         plan.solve(v, torch.zeros_like(v), 3)  # more rectangles than the plan holds
     assert e.value.status == B.FPG_EINVAL
     plan.close()
+
+
+@pytest.mark.parametrize("kind,nt,ns", [("neumann", 2048, 4096), ("periodic", 2048, 300), ("dirichlet", 4096, 64),
+                                        ("neumann", 2, 1), ("periodic", 2, 1), ("dirichlet", 2, 1)])
+def test_rect_plan_extreme_sizes(lib, kind, nt, ns):
+    """The largest and smallest accepted shapes, checked on closed-form modes
+    (the oracle's sparse solve of 8.4M unknowns would not finish in seconds)."""
+    from paper_2509_23180_gb300 import binding as B
+    h, kappa = 1.0 / nt, -3.0
+    if kind == "neumann":
+        mode, lam = NM.rectangle_neumann_mode, NM.rectangle_neumann_eigenvalue
+        ks = [0, nt - 1, nt // 2]
+    elif kind == "periodic":
+        mode, lam = PD.rectangle_periodic_mode, PD.rectangle_periodic_eigenvalue
+        ks = [0, nt - 1, nt // 2]
+    else:
+        from oracle import transforms as T
+        mode = lambda k, l, a, b: T.rectangle_mode(k, l, a, b)
+        lam = lambda k, l, a, b, hh, kk: T.rectangle_eigenvalue(k, l, a, b, hh, kk)
+        ks = [1, nt, nt // 2]
+    v = np.zeros(nt * ns)
+    want = np.zeros(nt * ns)
+    for i, k in enumerate(ks):
+        l = [1, ns, (ns + 1) // 2][i]
+        q = mode(k, l, nt, ns)
+        v += (i + 1) * q
+        want += (i + 1) / lam(k, l, nt, ns, h, kappa) * q
+    plan = B.RectPlan(kind, nt, ns, h, kappa, nvec=1)
+    z = torch.zeros((1, nt * ns), dtype=torch.float64, device="cuda")
+    plan.solve(dev(v[None, :]), z, 1)
+    assert rel(host(z)[0], want) < 1e-10
+    plan.solve(dev(v[None, :]), z, 0)  # an empty batch launches nothing
+    plan.close()
