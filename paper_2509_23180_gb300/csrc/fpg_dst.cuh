@@ -125,11 +125,21 @@ __device__ __forceinline__ void stockham_stage(const C2<T>* __restrict__ in, C2<
   }
 }
 
+// Power-of-two stages (radices 2, 4, 8, 16) with compile-time register DFTs;
+// defined with the register DFTs (fpg_dstline.cuh), used by the MAXR = 16 family.
+template <typename T>
+__device__ void stockham_pow2(int R, const C2<T>* in, C2<T>* out, int Q, int N, int Ns, int pitch, const C2<T>* W);
+
 // MAXR bounds the radices compiled into one kernel: a kernel built for small
-// radices does not carry the register footprint of the large ones.
+// radices does not carry the register footprint of the large ones.  MAXR = 16
+// is the power-of-two family (radices 2, 4, 8, 16 only).
 template <typename T, int MAXR>
 __device__ __forceinline__ void stockham_dispatch(int R, const C2<T>* in, C2<T>* out, int Q, int N, int Ns,
                                                   int pitch, const C2<T>* W) {
+  if constexpr (MAXR == 16) {
+    stockham_pow2<T>(R, in, out, Q, N, Ns, pitch, W);
+    return;
+  }
   switch (R) {
     case 2: stockham_stage<2, T>(in, out, Q, N, Ns, pitch, W); break;
     case 3: stockham_stage<3, T>(in, out, Q, N, Ns, pitch, W); break;
@@ -165,10 +175,16 @@ __device__ __forceinline__ void stockham_dispatch(int R, const C2<T>* in, C2<T>*
   }
 }
 
-// Largest radix family a plan needs: 5, 13, 19 or 43.
+// Radix family a plan needs: 16 for plans of radices 2, 4, 8, 16 with an 8 or a
+// 16 among them, else the largest radix rounded up to 5, 13, 19 or 43.
 __host__ __device__ inline int plan_maxr(const DstPlan& pl) {
   int mx = 2;
-  for (int i = 0; i < pl.nrad; ++i) mx = pl.rad[i] > mx ? pl.rad[i] : mx;
+  bool pow2 = true;
+  for (int i = 0; i < pl.nrad; ++i) {
+    mx = pl.rad[i] > mx ? pl.rad[i] : mx;
+    pow2 = pow2 && (pl.rad[i] == 2 || pl.rad[i] == 4 || pl.rad[i] == 8 || pl.rad[i] == 16);
+  }
+  if (pow2 && mx >= 8) return 16;
   return mx <= 5 ? 5 : (mx <= 13 ? 13 : (mx <= 19 ? 19 : 43));
 }
 

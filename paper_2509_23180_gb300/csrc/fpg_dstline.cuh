@@ -266,4 +266,41 @@ __device__ __forceinline__ To convert(From v) {
 }
 
 }  // namespace dl
+
+// One Stockham stage of radix R in {2, 4, 8, 16} with the register DFT of
+// length R (constants folded at compile time); otherwise as stockham_stage.
+template <int R, typename T>
+__device__ __forceinline__ void stockham_stage_pow2(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, int Q,
+                                                    int N, int Ns, int pitch, const C2<T>* __restrict__ W) {
+  const int nb = N / R;
+  const int tstep = N / (Ns * R);
+  for (int idx = threadIdx.x; idx < Q * nb; idx += blockDim.x) {
+    const int q = idx / nb, j = idx - q * nb;
+    const C2<T>* a = in + q * pitch;
+    const int jm = j % Ns;
+    C2<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = a[j + r * nb];
+    if (jm != 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], W[jm * r * tstep]);
+    }
+    dl::dft<R, T>(v);
+    C2<T>* o = out + q * pitch + (j - jm) * R + jm;
+#pragma unroll
+    for (int k = 0; k < R; ++k) o[k * Ns] = v[k];
+  }
+}
+
+template <typename T>
+__device__ void stockham_pow2(int R, const C2<T>* in, C2<T>* out, int Q, int N, int Ns, int pitch,
+                              const C2<T>* W) {
+  switch (R) {
+    case 2: stockham_stage_pow2<2, T>(in, out, Q, N, Ns, pitch, W); break;
+    case 4: stockham_stage_pow2<4, T>(in, out, Q, N, Ns, pitch, W); break;
+    case 8: stockham_stage_pow2<8, T>(in, out, Q, N, Ns, pitch, W); break;
+    default: stockham_stage_pow2<16, T>(in, out, Q, N, Ns, pitch, W); break;  // plans hold 2, 4, 8, 16 only
+  }
+}
+
 }  // namespace fpg

@@ -28,6 +28,7 @@
 #include <cmath>
 #include <vector>
 
+#include "fpg_dstline.cuh"
 #include "fpg_internal.cuh"
 
 namespace fpg {
@@ -39,11 +40,19 @@ namespace {
 
 constexpr int kNmThreads = 256;
 
-// Radices of the Stockham plan for length N (4, 2 and odd primes to 13); false
-// when N has another factor.
+// Radices of the Stockham plan for length N: powers of two as 16s, then one 8,
+// 4 or 2 (the power-of-two family); any other N as 4s, a 2 and odd primes to
+// 13.  False when N has a prime factor above 13.
 bool dct_radices(int N, int* rad, int* nrad) {
   static const int odd[] = {3, 5, 7, 11, 13};
   int m = N, cnt = 0;
+  if (N >= 8 && (N & (N - 1)) == 0) {
+    while (m % 16 == 0 && m > 16) { if (cnt >= kMaxRadices) return false; rad[cnt++] = 16; m /= 16; }
+    if (cnt >= kMaxRadices) return false;
+    rad[cnt++] = m;  // 16, 8, 4 or 2 -- the last, largest-stride stage
+    *nrad = cnt;
+    return true;
+  }
   while (m % 4 == 0) { if (cnt >= kMaxRadices) return false; rad[cnt++] = 4; m /= 4; }
   if (m % 2 == 0) { if (cnt >= kMaxRadices) return false; rad[cnt++] = 2; m /= 2; }
   for (int q : odd)
@@ -338,7 +347,7 @@ bool dct_plan_shape(int n, DstPlan* pl) {
   pl->p = n;
   pl->mode = DST_STOCKHAM;
   pl->N = n;
-  return dct_radices(n, pl->rad, &pl->nrad) && plan_maxr(*pl) <= 13;
+  return dct_radices(n, pl->rad, &pl->nrad);
 }
 
 // Real-DFT plan of length n (periodic lines): any n >= 2 whose prime factors are
@@ -350,15 +359,18 @@ bool rdft_plan_shape(int n, DstPlan* pl) {
   pl->p = n;
   pl->mode = DST_STOCKHAM;
   pl->N = n;
-  return dct_radices(n, pl->rad, &pl->nrad) && plan_maxr(*pl) <= 13;
+  return dct_radices(n, pl->rad, &pl->nrad);
 }
 
 cudaError_t launch_fast_solve_rdft(const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib,
                                    double* out, BatchDesc ob, int nblk, double* scratch, const int* active,
                                    int nper_active, cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;
-  return plan_maxr(tb.plan) <= 5 ? pd_launch<5>(tb, L, in, ib, out, ob, nblk, scratch, active, nper_active, st)
-                                 : pd_launch<13>(tb, L, in, ib, out, ob, nblk, scratch, active, nper_active, st);
+  switch (plan_maxr(tb.plan)) {
+    case 16: return pd_launch<16>(tb, L, in, ib, out, ob, nblk, scratch, active, nper_active, st);
+    case 5: return pd_launch<5>(tb, L, in, ib, out, ob, nblk, scratch, active, nper_active, st);
+    default: return pd_launch<13>(tb, L, in, ib, out, ob, nblk, scratch, active, nper_active, st);
+  }
 }
 
 // Host tables of the DCT-II lines: W[m] = e^{-2 pi i m/n}, post[k] = e^{-i pi k/(2n)}
@@ -427,8 +439,11 @@ cudaError_t launch_fast_solve_dct(const FastSolveTables& tb, LineLayout L, const
                                   double* out, BatchDesc ob, int nblk, double* scratch, const int* active,
                                   int nper_active, cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;
-  return plan_maxr(tb.plan) <= 5 ? nm_launch<5>(tb, L, in, ib, out, ob, nblk, scratch, active, nper_active, st)
-                                 : nm_launch<13>(tb, L, in, ib, out, ob, nblk, scratch, active, nper_active, st);
+  switch (plan_maxr(tb.plan)) {
+    case 16: return nm_launch<16>(tb, L, in, ib, out, ob, nblk, scratch, active, nper_active, st);
+    case 5: return nm_launch<5>(tb, L, in, ib, out, ob, nblk, scratch, active, nper_active, st);
+    default: return nm_launch<13>(tb, L, in, ib, out, ob, nblk, scratch, active, nper_active, st);
+  }
 }
 
 }  // namespace fpg
