@@ -162,3 +162,24 @@ def test_options_a_chain_does_not_take(lib):
         d.set_option(B.OPT_PRECOND, 2)
     assert e.value.status == B.FPG_EUNSUPPORTED
     d.set_option(B.OPT_PRECOND, 1)  # the identity works on any length
+
+
+def test_bench_configuration_residual(lib):
+    """The bench's chain (K = 3, 256^2 per square, FGMRES(30), rtol 1e-10) with its
+    launch configuration: the oracle's K, assembled independently, confirms the
+    residual of every right-hand side (855,040 unknowns each)."""
+    from paper_2509_23180_gb300 import binding as B
+    K, n = 3, 256
+    A = X.assemble(K, n, -10.0)
+    f = np.stack([W.strip_fourier_rhs(K, n, s) for s in range(3)])
+    d = domain(B, K, n, -10.0, nrhs=3, rtol=1e-10, restart=30)
+    d.set_rhs(dev(f))
+    p = torch.zeros_like(dev(f))
+    st, info = d.solve(p)
+    assert st == B.FPG_OK
+    P = host(p)
+    for r in range(3):
+        res = np.linalg.norm(f[r] - A @ P[r]) / np.linalg.norm(f[r])
+        # the oracle's plain sparse product rounds ~1e-12 worse than the library's
+        # difference-form stencil at this size, hence the margins
+        assert res <= 1.1e-10 and abs(res - info[r]["residual"]) <= 1e-11
