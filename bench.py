@@ -157,6 +157,25 @@ def cpu_baseline(args, f_by_kappa, max_seconds=30.0):
                       f"{dt:.1f} s (SuperLU and the assembly run single-threaded)"}
 
 
+def cpu_baseline_of(assemble, f, label, max_seconds=30.0):
+    """The oracle on a widening workload: assemble K, SuperLU factor, then direct
+    solves of the rows of f until the time bound (one host core)."""
+    from oracle import direct
+    t0 = time.perf_counter()
+    K = assemble()
+    F = direct.Factor(K)
+    cnt = 0
+    for r in range(f.shape[0]):
+        F.solve(f[r])
+        cnt += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": cnt / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{label}: assemble + SuperLU factor of K ({K.shape[0]} unknowns) + {cnt} direct solves, "
+                      f"{dt:.1f} s (single-threaded)"}
+
+
 def run_reference(args, rank, world):
     import numpy as np
     import workloads as W
@@ -699,7 +718,11 @@ def run_extra(args):
                       "unknowns_per_rhs": W.strip_total_unknowns(K, n),
                       "iterations_mean": float(np.mean([i["iterations"] for i in infos])),
                       "residual_max": max(i["residual"] for i in infos),
-                      "all_converged": all(i["status"] == B.FPG_OK for i in infos), "phases_kappa0": phases})
+                      "all_converged": all(i["status"] == B.FPG_OK for i in infos), "phases_kappa0": phases,
+                      "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline_of(
+                          lambda: __import__("oracle.strip", fromlist=["x"]).assemble(K, n, 0.0),
+                          np.stack([W.strip_fourier_rhs(K, n, s) for s in range(2)]),
+                          f"chain of {K} crosses, kappa 0")})
     elif args.config == "box":
         # the 3-D extension after Sec. 2.1: fast solve on boxes of n^3 (default 4 x 255^3
         # -- p = 256 per transform -- and 4 x 256^3, p = 257 by Rader), FP64
@@ -786,7 +809,11 @@ def run_extra(args):
                       "residual_max": max(i["residual"] for i in infos),
                       "all_converged": all(i["status"] == B.FPG_OK for i in infos),
                       "phases_kappa0": phases,
-                      "validation": {"max_error": errs, "observed_order": order}})
+                      "validation": {"max_error": errs, "observed_order": order},
+                      "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline_of(
+                          lambda: __import__("oracle.neumann_cross", fromlist=["x"]).assemble(n, 0.0),
+                          np.stack([W.ncross_fourier_rhs(n, s) for s in range(args.seeds)]),
+                          "Neumann-sided cross, kappa 0")})
     elif args.config == "study":
         # Sec. 3.2-3.3 on the GPU: (i) GMRES iterations with P = A_c^{-1} (the fast
         # solve), Jacobi and none, over n; (ii) iterations and solve time of the
