@@ -19,6 +19,14 @@ What it computes, each piece by its plain definition:
                (Eqs. "block_global", "Schur_subeq", Alg. "fft_dd_solver")
   krylov    -- restarted GMRES / flexible GMRES with modified Gram-Schmidt
                Arnoldi and Givens least squares (Sec. 2.4)
+  neumann   -- the Neumann line operator, its DCT-II eigenbasis and the Neumann
+               rectangle (Sec. 2.2, Eq. "submat_Neumann")
+  neumann_cross -- the cross with Neumann arm sides and its analytic solution
+               (Sec. 3.1, Eqs. "cross_equation"-"cross_ana_sol_psi")
+  periodic  -- the circulant line operator, its real (Hartley) eigenbasis and
+               the periodic rectangle (Sec. 2.2, Eq. "submat_Periodic")
+  box       -- the 7-point operator of a 3-D box (the 3-D extension after Sec. 2.1)
+  strip     -- the chain of crosses, several coupled blocks (Sec. 2.3-2.4)
 
 Parity status: every function above is pinned by `tests/test_oracle_*.py`
 (closed forms, brute force on tiny grids, second-order convergence, library
