@@ -314,8 +314,11 @@ typedef enum {
    * domain was created on the legacy default stream. */
   FPG_OPT_CUDA_GRAPHS = 2,
   /* Right preconditioner of the Schur iteration (Sec. 3.2):
-   * 0 (default): A_c^{-1}, the paper's FFT preconditioner (a1);
-   * 1: none (P = I);  2: Jacobi, the inverse diagonal of L_c.
+   * 0 (default): A_c^{-1}, the paper's FFT preconditioner (a1); on a chain the
+   *    block diagonal of the coupled squares' own operators;
+   * 1: none (P = I);  2: Jacobi, the inverse diagonal of L_c (not on chains);
+   * 3: chains only -- the coupled row's own operator, couplings between its
+   *    squares included, inverted by one fast solve of the whole row.
    * With 1 or 2 the flexible basis is still stored in the domain's
    * precond_precision. */
   FPG_OPT_PRECOND = 3,

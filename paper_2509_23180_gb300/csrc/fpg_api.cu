@@ -250,6 +250,8 @@ struct fpg_domain {
   LineLayout LC1, LC2;     // chain: their line layouts (transform along y, sweep along x)
   FastSolveTables tC64, tC32, tA64, tA32;
   FastSolveTables tA64e;  // Neumann-sided arms whose far end is row ns-1 (E, N); tA64 serves W, S
+  FastSolveTables tR64, tR32;  // chain: the whole coupled row as one block (FPG_OPT_PRECOND = 3)
+  LineLayout LR;
   double* ctab;
   double* gsc;           // [n] g_k delta^2 / (2 (n+1)), the transform form of the reduced Schur term
   int schur_transform = 0;  // 1: reduced Schur term by two DST-I per line where compiled (else the table sum)
@@ -279,7 +281,7 @@ struct fpg_domain {
   int tune_csz = 0;      // Arnoldi cluster size chosen by fpg_autotune (0: built-in choice)
   int tune_nt = 0;       // thread cap per CTA of the register Arnoldi kernel (0: 256, else 512)
   bool use_graphs = true;
-  int precond_kind = 0;  // 0: A_c^{-1} (the paper's), 1: identity, 2: Jacobi
+  int precond_kind = 0;  // 0: A_c^{-1} (the paper's), 1: identity, 2: Jacobi, 3: chain row as one block
   int accept_rounds = 0;  // acceptance checks done in the current solve
   cudaGraphExec_t cycle_exec = nullptr;
   long long cycle_kernels = 0;
@@ -547,6 +549,13 @@ void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostP
       D->tA64e.mneg = m2;
     }
   }
+  if (L.chain) {  // the coupled row's own sweeps: n modes of nxc rows
+    const size_t rows = (size_t)n * L.cg.nxc;
+    p = c.take(sizeof(double) * rows); if (D) D->tR64.rpiv = p;
+    p = c.take(sizeof(double) * rows); if (D) D->tR64.mneg = p;
+    p = c.take(sizeof(float) * rows);  if (D) D->tR32.rpiv = p;
+    p = c.take(sizeof(float) * rows);  if (D) D->tR32.mneg = p;
+  }
   p = c.take(sizeof(double) * (4 * n + 2));   if (D) D->ctab = (double*)p;
   p = c.take(sizeof(double) * n);             if (D) D->gsc = (double*)p;
   p = c.take(sizeof(int) * 12);               if (D) D->arms_dev = (int*)p;
@@ -656,6 +665,14 @@ inline void count(fpg_domain* D, int phase, int n) {
 // a1 on nvec centre vectors (nvec <= nrhs): v (FP64, stride nc) -> z (prec).
 fpg_status precond(fpg_domain* D, const double* v, void* z, int nvec, const int* active) {
   const Layout& L = D->L;
+  if (D->precond_kind == 3) {  // a chain's coupled row as one block: A_row^{-1} by one fast solve
+    int nl3 = 0;
+    const BatchDesc rb{L.nc, {0, 0, 0, 0}, 1};
+    FPG_CUDA_TRY(launch_fast_solve(D->prec, D->prec, D->prec == 64 ? D->tR64 : D->tR32, D->LR, v, rb, z, rb, nvec,
+                                   D->scratch, active, 1, D->st, &nl3));
+    count(D, 0, nl3);
+    return FPG_OK;
+  }
   if (D->precond_kind != 0) {  // Sec. 3.2 comparison preconditioners: identity, Jacobi
     FPG_CUDA_TRY(launch_precond_simple(v, z, D->prec, L.nc, L.n, D->delta, D->desc.kappa, D->ctab, L.armmask,
                                        D->precond_kind == 2, active, nvec, D->gx, D->st));
@@ -1591,6 +1608,7 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
     D->cb1 = BatchDesc{L.nc, {0, 0, 0, 0}, 0};
     for (int q = 0; q < 2 * K - 2; ++q) D->cb1.off[D->cb1.nper++] = (long long)q * (n + 1);
     D->cb2 = BatchDesc{L.nc, {(long long)(2 * K - 2) * (n + 1), 0, 0, 0}, 1};
+    D->LR = LineLayout{n, nxc, nxc, 1};
   } else {
     for (int a = 0; a < 4; ++a) {
       if (L.ao.off[a] < 0) continue;
@@ -1600,6 +1618,7 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   }
   for (auto* t : {&D->tC64, &D->tC32}) { t->n = n; t->ns = n; t->delta = D->delta; }
   for (auto* t : {&D->tA64, &D->tA32, &D->tA64e}) { t->n = n; t->ns = as; t->delta = D->delta; }
+  for (auto* t : {&D->tR64, &D->tR32}) { t->n = n; t->ns = L.chain ? L.cg.nxc : 0; t->delta = D->delta; }
   HostPlan hp = build_plan(n);
   Carver c(ws);
   carve(D, desc, L, &hp, c);
@@ -1667,6 +1686,20 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   if (!err) err = cp(D->tC32.mneg, mc32.data(), sizeof(float) * mc32.size());
   if (!err) err = cp(D->tA64.mneg, ma.data(), sizeof(double) * ma.size());
   if (!err) err = cp(D->tA32.mneg, ma32.data(), sizeof(float) * ma32.size());
+  if (L.chain) {  // pivots of the row's sweeps (length nxc); the DST-I tables are the centre's
+    D->tR64.plan = D->tC64.plan;
+    D->tR32.plan = D->tC32.plan;
+    std::vector<double> pr, mr;
+    fill_pivots(n, L.cg.nxc, D->delta, desc->kappa, pr);
+    mr.resize(pr.size());
+    for (size_t i = 0; i < pr.size(); ++i) mr[i] = -D->delta * pr[i];
+    std::vector<float> pr32(pr.begin(), pr.end()), mr32(mr.begin(), mr.end());
+    if (!err) err = cp(D->tR64.rpiv, pr.data(), sizeof(double) * pr.size());
+    if (!err) err = cp(D->tR64.mneg, mr.data(), sizeof(double) * mr.size());
+    if (!err) err = cp(D->tR32.rpiv, pr32.data(), sizeof(float) * pr32.size());
+    if (!err) err = cp(D->tR32.mneg, mr32.data(), sizeof(float) * mr32.size());
+    if (!err) err = cudaStreamSynchronize(D->st);  // the host vectors end with this block
+  }
   if (nside) {
     if (!err) err = cp(D->tA64e.rpiv, pae.data(), sizeof(double) * pae.size());
     if (!err) err = cp(D->tA64e.mneg, mae.data(), sizeof(double) * mae.size());
@@ -1980,8 +2013,9 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_PRECOND:
-      if (value < 0 || value > 2) return FPG_EINVAL;
+      if (value < 0 || value > 3) return FPG_EINVAL;
       if (d->L.chain && value == 2) return FPG_EUNSUPPORTED;  // the Jacobi diagonal is written for the cross
+      if (!d->L.chain && value == 3) return FPG_EUNSUPPORTED;  // the coupled row exists on chains only
       d->precond_kind = value;
       drop_graph(d);
       return FPG_OK;
@@ -2049,6 +2083,10 @@ fpg_status fpg_set_stream(fpg_domain* d, void* stream) {
 
 fpg_status fpg_fast_solve_path(fpg_domain* d, int32_t* path) {
   if (!d || !path) return FPG_EINVAL;
+  if (d->precond_kind == 3) {
+    *path = fast_solve_path(d->prec, d->prec == 64 ? d->tR64 : d->tR32, d->LR, d->desc.nrhs);
+    return FPG_OK;
+  }
   if (d->precond_kind != 0) {
     *path = 4;
     return FPG_OK;

@@ -626,13 +626,14 @@ cudaError_t launch_fast_solve_rdft(const FastSolveTables& tb, LineLayout L, cons
 // Which kernels the fast solve of this block kind runs: 0 generic FFT engine
 // (k_fft_forward / k_thomas_reg / k_fft_inverse), 1 size-specialised
 // (k_dst_lines_fwd / k_thomas_reg / k_dst_lines_inv), 2 dense DST, 3 the fused
-// one-pass cluster kernel, 4 the DCT-II lines of a Neumann-sided block
-// (k_dct_fwd / k_thomas_reg / k_dct_inv), 5 the real-DFT lines of a periodic
-// block (k_rdft_fwd / k_thomas_reg / k_rdft_inv).
+// one-pass cluster kernel, 5 the DCT-II lines of a Neumann-sided block
+// (k_dct_fwd / k_thomas_reg / k_dct_inv), 6 the real-DFT lines of a periodic
+// block (k_rdft_fwd / k_thomas_reg / k_rdft_inv).  (4 is the public code for a
+// centre without fast solve.)
 bool fast_solve_fused_fits(int prec, const FastSolveTables& tb, LineLayout L);
 int fast_solve_path(int prec, const FastSolveTables& tb, LineLayout L, int nblk) {
-  if (tb.kind == 1) return 4;
-  if (tb.kind == 2) return 5;
+  if (tb.kind == 1) return 5;
+  if (tb.kind == 2) return 6;
   if (tb.fused && fast_solve_fused_fits(prec, tb, L)) return 3;
   if (tb.plan.mode == DST_DENSE) return 2;
   const bool special = prec == 64 ? lines_engine<double>(tb.plan.p, nblk, L.ns, tb.generic)

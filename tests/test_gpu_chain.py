@@ -183,3 +183,37 @@ def test_bench_configuration_residual(lib):
         # the oracle's plain sparse product rounds ~1e-12 worse than the library's
         # difference-form stencil at this size, hence the margins
         assert res <= 1.1e-10 and abs(res - info[r]["residual"]) <= 1e-11
+
+
+@pytest.mark.parametrize("prec,tol", [(64, 1e-11), (32, 2e-5)])
+def test_row_preconditioner(lib, prec, tol):
+    """FPG_OPT_PRECOND = 3: the coupled row's own operator (couplings between its
+    squares included) inverted by one fast solve of the whole row, against the
+    oracle's sparse solve with A_C; then whole solves reach K^{-1} f with the
+    oracle's FGMRES iteration count for that preconditioner (+-1)."""
+    from paper_2509_23180_gb300 import binding as B
+    K, n = 3, 16
+    A = X.assemble(K, n, -10.0)
+    bs = BlockSystem(A, "chain", n, blocks=X.block_ranges(K, n))
+    nc = bs.A["C"].shape[0]
+    d = domain(B, K, n, -10.0, nrhs=2, precond_precision=prec, rtol=1e-10)
+    d.set_option(B.OPT_PRECOND, 3)
+    v = W.random_block_vectors(2, nc, seed=9)
+    z = torch.zeros((2, nc), dtype=torch.float64 if prec == 64 else torch.float32, device="cuda")
+    d.apply_precond(dev(v), z, 2)
+    assert rel(host(z).astype(np.float64), np.stack([bs.block_solve("C", vi) for vi in v])) < tol
+    f = np.stack([W.strip_fourier_rhs(K, n, s) for s in (1, 2)])
+    d.set_rhs(dev(f))
+    p = torch.zeros_like(dev(f))
+    st, info = d.solve(p)
+    assert st == B.FPG_OK
+    lu = spla.splu(A.tocsc())
+    for r in range(2):
+        assert rel(host(p)[r], lu.solve(f[r])) < 1e-8
+        if prec == 64:
+            _, oinfo = algorithm1(bs, f[r], m=30, rtol=1e-10, precond="A_c")
+            assert abs(info[r]["iterations"] - oinfo["iterations"]) <= 1, (info[r], oinfo["iterations"])
+    cross = B.Domain(B.make_desc("cross", 8, 0.0))
+    with pytest.raises(B.FpgError) as e:
+        cross.set_option(B.OPT_PRECOND, 3)
+    assert e.value.status == B.FPG_EUNSUPPORTED
