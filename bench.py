@@ -680,9 +680,9 @@ def run_extra(args):
                                        "peak_source": "measured: library FP64 FMA probe on this GPU"}})
     elif args.config == "chain":
         # several coupled blocks (Sec. 2.3-2.4): a chain of K = 3 crosses, n^2 per
-        # square, kappa in {0, -10}, `seeds` fourier RHS each, FGMRES(m) with the
-        # block-diagonal fast-solve preconditioner of the 5 coupled squares
-        # (--option PRECOND=3: the whole coupled row as one fast solve)
+        # square, kappa in {0, -10}, `seeds` fourier RHS each, FGMRES(m)
+        # preconditioned by one fast solve of the whole coupled row
+        # (--option PRECOND=3: the block diagonal of its 5 squares)
         n, m, K = args.n, args.restart, 3
         doms = []
         for kappa in (0.0, -10.0):

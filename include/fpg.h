@@ -25,8 +25,9 @@
  * Chain of K crosses (geometry = FPG_GEOM_CHAIN, desc.chain = K, 2 <= K <= 5;
  * several coupled blocks, Sec. 2.3-2.4): 2K - 1 unit squares in a row along x
  * (centres at even positions, links between them) are the coupled set, solved
- * together by flexible GMRES with the block-diagonal preconditioner of its
- * squares (one fast solve each); arms W and E at the row's ends and S_i, N_i
+ * together by flexible GMRES preconditioned with the row's own operator (one
+ * fast solve of the whole row; FPG_OPT_PRECOND = 3: the block diagonal of its
+ * squares, one fast solve each); arms W and E at the row's ends and S_i, N_i
  * below and above centre i are eliminated exactly.  Vector layout: the row as
  * one rectangle of nx_c = (2K-1)(n+1) - 1 columns by n rows (x fastest; each
  * square owns the line it shares with the next), then W, E ((n+1) x n), S_1..S_K,
@@ -315,10 +316,11 @@ typedef enum {
   FPG_OPT_CUDA_GRAPHS = 2,
   /* Right preconditioner of the Schur iteration (Sec. 3.2):
    * 0 (default): A_c^{-1}, the paper's FFT preconditioner (a1); on a chain the
-   *    block diagonal of the coupled squares' own operators;
+   *    coupled row's own operator (couplings between its squares included),
+   *    inverted by one fast solve of the whole row;
    * 1: none (P = I);  2: Jacobi, the inverse diagonal of L_c (not on chains);
-   * 3: chains only -- the coupled row's own operator, couplings between its
-   *    squares included, inverted by one fast solve of the whole row.
+   * 3: chains only -- the block diagonal of the coupled squares' own
+   *    operators, one fast solve per square.
    * With 1 or 2 the flexible basis is still stored in the domain's
    * precond_precision. */
   FPG_OPT_PRECOND = 3,

@@ -250,7 +250,7 @@ struct fpg_domain {
   LineLayout LC1, LC2;     // chain: their line layouts (transform along y, sweep along x)
   FastSolveTables tC64, tC32, tA64, tA32;
   FastSolveTables tA64e;  // Neumann-sided arms whose far end is row ns-1 (E, N); tA64 serves W, S
-  FastSolveTables tR64, tR32;  // chain: the whole coupled row as one block (FPG_OPT_PRECOND = 3)
+  FastSolveTables tR64, tR32;  // chain: the whole coupled row as one block (its A_c)
   LineLayout LR;
   double* ctab;
   double* gsc;           // [n] g_k delta^2 / (2 (n+1)), the transform form of the reduced Schur term
@@ -281,7 +281,7 @@ struct fpg_domain {
   int tune_csz = 0;      // Arnoldi cluster size chosen by fpg_autotune (0: built-in choice)
   int tune_nt = 0;       // thread cap per CTA of the register Arnoldi kernel (0: 256, else 512)
   bool use_graphs = true;
-  int precond_kind = 0;  // 0: A_c^{-1} (the paper's), 1: identity, 2: Jacobi, 3: chain row as one block
+  int precond_kind = 0;  // 0: A_c^{-1} (the paper's), 1: identity, 2: Jacobi, 3: chain, block diagonal
   int accept_rounds = 0;  // acceptance checks done in the current solve
   cudaGraphExec_t cycle_exec = nullptr;
   long long cycle_kernels = 0;
@@ -665,7 +665,7 @@ inline void count(fpg_domain* D, int phase, int n) {
 // a1 on nvec centre vectors (nvec <= nrhs): v (FP64, stride nc) -> z (prec).
 fpg_status precond(fpg_domain* D, const double* v, void* z, int nvec, const int* active) {
   const Layout& L = D->L;
-  if (D->precond_kind == 3) {  // a chain's coupled row as one block: A_row^{-1} by one fast solve
+  if (L.chain && D->precond_kind == 0) {  // a chain's A_c: the coupled row's own operator, one fast solve
     int nl3 = 0;
     const BatchDesc rb{L.nc, {0, 0, 0, 0}, 1};
     FPG_CUDA_TRY(launch_fast_solve(D->prec, D->prec, D->prec == 64 ? D->tR64 : D->tR32, D->LR, v, rb, z, rb, nvec,
@@ -673,14 +673,14 @@ fpg_status precond(fpg_domain* D, const double* v, void* z, int nvec, const int*
     count(D, 0, nl3);
     return FPG_OK;
   }
-  if (D->precond_kind != 0) {  // Sec. 3.2 comparison preconditioners: identity, Jacobi
+  if (D->precond_kind == 1 || D->precond_kind == 2) {  // Sec. 3.2 comparison preconditioners: identity, Jacobi
     FPG_CUDA_TRY(launch_precond_simple(v, z, D->prec, L.nc, L.n, D->delta, D->desc.kappa, D->ctab, L.armmask,
                                        D->precond_kind == 2, active, nvec, D->gx, D->st));
     count(D, 0, 1);
     return FPG_OK;
   }
   int nl = 0;
-  if (L.chain) {
+  if (L.chain) {  // FPG_OPT_PRECOND = 3
     // block-diagonal over the row's squares: 2K - 2 squares of n + 1 columns, then the last
     const FastSolveTables& ta = D->prec == 64 ? D->tA64 : D->tA32;
     const FastSolveTables& tc = D->prec == 64 ? D->tC64 : D->tC32;
@@ -2015,7 +2015,7 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
     case FPG_OPT_PRECOND:
       if (value < 0 || value > 3) return FPG_EINVAL;
       if (d->L.chain && value == 2) return FPG_EUNSUPPORTED;  // the Jacobi diagonal is written for the cross
-      if (!d->L.chain && value == 3) return FPG_EUNSUPPORTED;  // the coupled row exists on chains only
+      if (!d->L.chain && value == 3) return FPG_EUNSUPPORTED;  // the squares of a coupled row: chains only
       d->precond_kind = value;
       drop_graph(d);
       return FPG_OK;
@@ -2083,8 +2083,9 @@ fpg_status fpg_set_stream(fpg_domain* d, void* stream) {
 
 fpg_status fpg_fast_solve_path(fpg_domain* d, int32_t* path) {
   if (!d || !path) return FPG_EINVAL;
-  if (d->precond_kind == 3) {
-    *path = fast_solve_path(d->prec, d->prec == 64 ? d->tR64 : d->tR32, d->LR, d->desc.nrhs);
+  if (d->L.chain && d->precond_kind != 1) {  // the row solve, or the squares (same engine choice)
+    *path = d->precond_kind == 0 ? fast_solve_path(d->prec, d->prec == 64 ? d->tR64 : d->tR32, d->LR, d->desc.nrhs)
+                                 : fast_solve_path(d->prec, d->prec == 64 ? d->tA64 : d->tA32, d->LC1, d->desc.nrhs);
     return FPG_OK;
   }
   if (d->precond_kind != 0) {

@@ -53,13 +53,15 @@ def test_global_operator(lib, K, n):
 @pytest.mark.parametrize("prec,tol", [(64, 1e-11), (32, 2e-5)])
 @pytest.mark.parametrize("K,n", [(2, 8), (3, 64), (5, 16)])
 def test_block_diagonal_preconditioner(lib, prec, tol, K, n):
-    """a1 on the row: the exact inverse of each square's own operator."""
+    """a1 on the row with FPG_OPT_PRECOND = 3: the exact inverse of each square's
+    own operator."""
     from paper_2509_23180_gb300 import binding as B
     A = X.assemble(K, n, -10.0)
     bs = BlockSystem(A, "chain", n, blocks=X.block_ranges(K, n))
     Ac = bs.A["C"].tocsc()
     nc = Ac.shape[0]
     d = domain(B, K, n, -10.0, nrhs=3, precond_precision=prec)
+    d.set_option(B.OPT_PRECOND, 3)
     v = W.random_block_vectors(3, nc, seed=n + K)
     z = torch.zeros((3, nc), dtype=torch.float64 if prec == 64 else torch.float32, device="cuda")
     d.apply_precond(dev(v), z, 3)
@@ -102,7 +104,7 @@ def test_solve_vs_direct(lib, prec, K, n, kappa):
         assert np.linalg.norm(f[r] - A @ P[r]) / np.linalg.norm(f[r]) <= 1.01e-12
 
 
-def test_iterations_match_oracle(lib):
+def test_iterations_match_oracle_block_diagonal(lib):
     from paper_2509_23180_gb300 import binding as B
     K, n = 3, 16
     A = X.assemble(K, n, 0.0)
@@ -110,6 +112,7 @@ def test_iterations_match_oracle(lib):
     bs = BlockSystem(A, "chain", n, blocks=X.block_ranges(K, n))
     _, oinfo = algorithm1(bs, f, m=30, rtol=1e-10, precond="block_diag", centre_parts=parts(K, n))
     d = domain(B, K, n, 0.0, nrhs=1, rtol=1e-10, restart=30)
+    d.set_option(B.OPT_PRECOND, 3)
     d.set_rhs(dev(f[None, :]))
     p = torch.zeros_like(dev(f[None, :]))
     st, info = d.solve(p)
@@ -187,17 +190,16 @@ def test_bench_configuration_residual(lib):
 
 @pytest.mark.parametrize("prec,tol", [(64, 1e-11), (32, 2e-5)])
 def test_row_preconditioner(lib, prec, tol):
-    """FPG_OPT_PRECOND = 3: the coupled row's own operator (couplings between its
-    squares included) inverted by one fast solve of the whole row, against the
-    oracle's sparse solve with A_C; then whole solves reach K^{-1} f with the
-    oracle's FGMRES iteration count for that preconditioner (+-1)."""
+    """The default chain preconditioner: the coupled row's own operator (couplings
+    between its squares included) inverted by one fast solve of the whole row,
+    against the oracle's sparse solve with A_C; then whole solves reach K^{-1} f
+    with the oracle's FGMRES iteration count for that preconditioner (+-1)."""
     from paper_2509_23180_gb300 import binding as B
     K, n = 3, 16
     A = X.assemble(K, n, -10.0)
     bs = BlockSystem(A, "chain", n, blocks=X.block_ranges(K, n))
     nc = bs.A["C"].shape[0]
     d = domain(B, K, n, -10.0, nrhs=2, precond_precision=prec, rtol=1e-10)
-    d.set_option(B.OPT_PRECOND, 3)
     v = W.random_block_vectors(2, nc, seed=9)
     z = torch.zeros((2, nc), dtype=torch.float64 if prec == 64 else torch.float32, device="cuda")
     d.apply_precond(dev(v), z, 2)
