@@ -13,6 +13,8 @@
 // back into the block layout.  Compute precision T is double or float; inputs
 // are always FP64, the output is written as To.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "fpg_dstline.cuh"
@@ -301,6 +303,86 @@ k_thomas_long(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv
   }
 }
 
+// The same two-scan Thomas solve for sweeps longer than the register kernel
+// takes: the warp stages its column and the mode's pivot tables in its own
+// shared-memory slice with coalesced loads, runs the chunked scans there and
+// writes the column back coalesced.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_thomas_long_smem(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv, const T* __restrict__ mneg,
+                   int nblk, const int* __restrict__ active, int nper_active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (wg >= (long long)nblk * n) return;  // uniform per warp; only warp-level syncs follow
+  const int b = (int)(wg / n), k = (int)(wg - (long long)b * n);
+  if (active != nullptr && !active[b / nper_active]) return;
+  T* sc = reinterpret_cast<T*>(smem_raw) + (size_t)wib * 3 * ns;
+  T* sr = sc + ns;
+  T* sm = sr + ns;
+  T* col = scratch + wg * ns;
+  const T* rg = rpiv + (long long)k * ns;
+  const T* mg = mneg + (long long)k * ns;
+  for (int s = lane; s < ns; s += 32) {
+    sc[s] = col[s];
+    sr[s] = rg[s];
+    sm[s] = mg[s];
+  }
+  __syncwarp();
+  const int c = (ns + 31) / 32;
+  const int s0 = min(ns, lane * c), s1 = min(ns, s0 + c);
+  T acc = T(0), pr = T(1);
+  for (int s = s0; s < s1; ++s) {
+    acc = fma(sm[s], acc, sr[s] * sc[s]);
+    pr *= sm[s];
+    sc[s] = acc;
+  }
+  T Y = acc, P = pr;
+  for (int o = 1; o < 32; o <<= 1) {
+    const T Yo = __shfl_up_sync(0xffffffffu, Y, o), Po = __shfl_up_sync(0xffffffffu, P, o);
+    if (lane >= o) {
+      Y = fma(P, Yo, Y);
+      P *= Po;
+    }
+  }
+  T cin = __shfl_up_sync(0xffffffffu, Y, 1);
+  if (lane == 0) cin = T(0);
+  if (cin != T(0)) {
+    T q = T(1);
+    for (int s = s0; s < s1; ++s) {
+      q *= sm[s];
+      sc[s] = fma(q, cin, sc[s]);
+    }
+  }
+  acc = T(0);
+  pr = T(1);
+  for (int s = s1 - 1; s >= s0; --s) {
+    acc = fma(sm[s], acc, sc[s]);
+    pr *= sm[s];
+    sc[s] = acc;
+  }
+  Y = acc;
+  P = pr;
+  for (int o = 1; o < 32; o <<= 1) {
+    const T Yo = __shfl_down_sync(0xffffffffu, Y, o), Po = __shfl_down_sync(0xffffffffu, P, o);
+    if (lane + o < 32) {
+      Y = fma(P, Yo, Y);
+      P *= Po;
+    }
+  }
+  T cdn = __shfl_down_sync(0xffffffffu, Y, 1);
+  if (lane == 31) cdn = T(0);
+  if (cdn != T(0)) {
+    T q = T(1);
+    for (int s = s1 - 1; s >= s0; --s) {
+      q *= sm[s];
+      sc[s] = fma(q, cdn, sc[s]);
+    }
+  }
+  __syncwarp();
+  for (int s = lane; s < ns; s += 32) col[s] = sc[s];
+}
+
 // Launch the Thomas solves: one warp per (block, mode), wpb warps per CTA
 // (0: 8, fewer when the per-warp staging buffers would pass 96 KB), rows per
 // lane C = the smallest compiled value covering ns / 32.
@@ -338,6 +420,20 @@ cudaError_t launch_thomas(T* scratch, int n, int ns, const T* rpiv, const T* mne
   FPG_THOMAS_C(32)
   FPG_THOMAS_C(33)
 #undef FPG_THOMAS_C
+  // longer sweeps: the column and the pivot tables staged in shared memory
+  // (3 ns values per warp), else straight from global memory
+  const size_t per = sizeof(T) * 3 * (size_t)ns;
+  const int wl = (int)std::min<size_t>(8, (size_t)(200 * 1024) / per);
+  if (wl >= 1) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_thomas_long_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr = true;
+    }
+    const dim3 grid((unsigned)((warps + wl - 1) / wl));
+    k_thomas_long_smem<T><<<grid, 32 * wl, per * wl, st>>>(scratch, n, ns, rpiv, mneg, nblk, active, nper_active);
+    return cudaGetLastError();
+  }
   const dim3 grid((unsigned)((warps + wpb - 1) / wpb));
   const int threads = 32 * wpb;
   k_thomas_long<T><<<grid, threads, 0, st>>>(scratch, n, ns, rpiv, mneg, nblk, active, nper_active);

@@ -39,7 +39,9 @@ def oracle_solve(kind, nt, ns, h, kappa, v):
 
 @pytest.mark.parametrize("kind,nt,ns", [("dirichlet", 64, 40), ("dirichlet", 93, 17), ("dirichlet", 256, 257),
                                         ("neumann", 64, 40), ("neumann", 90, 33), ("periodic", 64, 40),
-                                        ("periodic", 45, 70), ("periodic", 512, 64)])
+                                        ("periodic", 45, 70), ("periodic", 512, 64),
+                                        # sweeps longer than the register Thomas kernel holds
+                                        ("dirichlet", 64, 2000), ("neumann", 32, 1500), ("periodic", 24, 3001)])
 def test_rect_plan_vs_oracle(lib, kind, nt, ns):
     from paper_2509_23180_gb300 import binding as B
     h, kappa = 1.0 / nt, -5.0
