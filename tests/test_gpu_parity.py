@@ -219,6 +219,26 @@ def test_solve_matches_golden(lib, fname, geom, n, kappa, kind, seed):
     assert rel(host(p)[0], load_golden(fname)) < 1e-10
 
 
+@pytest.mark.parametrize("fname,geometry,n,kappa,extra",
+                         __import__("tests.golden.make_golden", fromlist=["EXTRA_CASES"]).EXTRA_CASES)
+def test_widening_solve_matches_golden(lib, fname, geometry, n, kappa, extra):
+    """The Neumann-sided cross and a chain of crosses against their stored oracle solutions."""
+    from paper_2509_23180_gb300 import binding as B
+    from tests.golden.make_golden import expected_extra
+    from tests.test_oracle_golden import load_golden
+    f, _ = expected_extra(geometry, n, kappa, extra)
+    if geometry == "ncross":
+        desc = B.make_desc("cross", n, kappa, nrhs=1, rtol=1e-13, boundary="neumann_sides")
+    else:
+        desc = B.make_desc("chain", n, kappa, nrhs=1, rtol=1e-13, chain=extra)
+    d = B.Domain(desc)
+    d.set_rhs(dev(f[None, :]))
+    p = torch.zeros_like(dev(f[None, :]))
+    st, info = d.solve(p)
+    assert st == B.FPG_OK
+    assert rel(host(p)[0], load_golden(fname)) < 1e-10
+
+
 def test_manufactured_config_n64(lib):
     """The 64^2-per-block cross with the manufactured solution, m = 30, rtol
     1e-10: residual met, error to the direct solve within 1e-9 relative, and the
