@@ -820,9 +820,10 @@ def run_extra(args):
         # solve), Jacobi and none, over n; (ii) iterations and solve time of the
         # FFT-preconditioned solve against the Krylov dimension m (the paper finds
         # an optimum near m = 80).  Cross, kappa 0, random Fourier RHS seed 0.
-        def solve_once(n, m, precond, max_iters):
+        def solve_once(n, m, precond, max_iters, rtol=None):
             f = torch.as_tensor(W.rhs_batch("cross", n, [0], kind="fourier"), device="cuda")
-            d = B.Domain(B.make_desc("cross", n, 0.0, nrhs=1, restart=m, rtol=args.rtol, max_iters=max_iters))
+            d = B.Domain(B.make_desc("cross", n, 0.0, nrhs=1, restart=m, rtol=rtol or args.rtol,
+                                     max_iters=max_iters))
             d.set_option(B.OPT_PRECOND, B.PRECOND[precond])
             p = torch.zeros_like(f)
             res = []
@@ -845,12 +846,21 @@ def run_extra(args):
         best_m = min(msweep, key=lambda m: msweep[m]["ms"])
         ratio = {n: {pc: v["iterations"] / max(1, pre[n]["fft"]["iterations"]) for pc, v in r.items() if pc != "fft"}
                  for n, r in pre.items()}
+        # Sec. 3.3: iterations against k_n at the tolerances 1e-7 and 1e-10, and the
+        # exponent of a least-squares power-law fit (the paper reports about 1/2)
+        ns_ = (16, 32, 64, 128, 256, 512)
+        vs_n, fit = {}, {}
+        for tol in (1e-7, 1e-10):
+            its = [solve_once(n, 30, "fft", 20000, rtol=tol)["iterations"] for n in ns_]
+            vs_n[str(tol)] = dict(zip(ns_, its))
+            fit[str(tol)] = float(np.polyfit(np.log(ns_), np.log(its), 1)[0])
         lines.append({"metric": "GMRES iterations and solve time vs preconditioner and Krylov dimension",
                       "value": msweep[best_m]["ms"], "unit": "ms", "n_gpus": 1, "higher_is_better": False,
                       "dtype": "f64", "data": "synthetic",
                       "config": {"workload": "cross, kappa 0, fourier RHS seed 0, rtol %g" % args.rtol,
                                  "precond_study_m": 30, "m_sweep_n": 256},
                       "precond_iterations": pre, "iterations_ratio_vs_fft": ratio,
+                      "iterations_vs_n": vs_n, "iterations_exponent": fit,
                       "m_sweep": msweep, "best_m": best_m})
     elif args.config == "batching":
         # (i) 64 RHS in one domain on the 512^2 cross, FP32 fast solve, FP64 FGMRES(40)
