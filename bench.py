@@ -848,6 +848,22 @@ def run_extra(args):
                  for n, r in pre.items()}
         # Sec. 3.3: iterations against k_n at the tolerances 1e-7 and 1e-10, and the
         # exponent of a least-squares power-law fit (the paper reports about 1/2)
+        # Sec. 3.2: residual histories (relative GMRES estimate after every step) for
+        # six (n, m) combinations
+        histories = {}
+        for n in (64, 256):
+            for m in (10, 30, 80):
+                f = torch.as_tensor(W.rhs_batch("cross", n, [0], kind="fourier"), device="cuda")
+                d = B.Domain(B.make_desc("cross", n, 0.0, nrhs=1, restart=m, rtol=args.rtol))
+                hb = torch.zeros((1, 2000), dtype=torch.float64, device="cuda")
+                d.set_history(hb)
+                d.set_rhs(f)
+                p = torch.zeros_like(f)
+                _, info = d.solve(p, check=False)
+                its = info[0]["iterations"]
+                fn = float(torch.linalg.norm(f))
+                histories[f"n={n},m={m}"] = [float(x) / fn for x in hb[0, :its].cpu()]
+                d.close()
         ns_ = (16, 32, 64, 128, 256, 512)
         vs_n, fit = {}, {}
         for tol in (1e-7, 1e-10):
@@ -860,7 +876,7 @@ def run_extra(args):
                       "config": {"workload": "cross, kappa 0, fourier RHS seed 0, rtol %g" % args.rtol,
                                  "precond_study_m": 30, "m_sweep_n": 256},
                       "precond_iterations": pre, "iterations_ratio_vs_fft": ratio,
-                      "iterations_vs_n": vs_n, "iterations_exponent": fit,
+                      "iterations_vs_n": vs_n, "iterations_exponent": fit, "residual_histories": histories,
                       "m_sweep": msweep, "best_m": best_m})
     elif args.config == "batching":
         # (i) 64 RHS in one domain on the 512^2 cross, FP32 fast solve, FP64 FGMRES(40)

@@ -393,6 +393,15 @@ fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out);
 
 /* ---- measurement ----------------------------------------------------------- */
 
+/* Residual history (the residual curves of the GMRES study, Sec. 3.2): with a
+ * caller-owned device buffer of nrhs x len doubles, every Arnoldi step of later
+ * solves writes the GMRES residual estimate |g_{j+1}| of the Schur system of each
+ * right-hand side to buf[r * len + i], i = that right-hand side's step count - 1
+ * (i < len; relative values: divide by ||f||_2).  Entries past the last step are
+ * left untouched.  len = 0 (buf may be NULL) stops recording.  One small extra
+ * launch per Arnoldi step while recording.  Errors: FPG_EINVAL. */
+fpg_status fpg_set_history(fpg_domain* d, double* dev_buf, int32_t len);
+
 /* Kernel-level timing of the last fpg_solve on this domain: launches issued and
  * the device time (ms, CUDA events on the domain stream) of each phase.
  * phase: 0 = preconditioner (a1), 1 = Schur matvec (a2), 2 = Arnoldi (a3),

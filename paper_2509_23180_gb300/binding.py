@@ -124,6 +124,7 @@ _SIGS = {
     "fpg_batch_poll": ([_P, _I64, ctypes.POINTER(_I32), _P], _I32),
     "fpg_batch_stats": ([_P, _P], _I32),
     "fpg_batch_destroy": ([_P], None),
+    "fpg_set_history": ([_P, _P, _I32], _I32),
     "fpg_box_plan_bytes": ([_I32, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)], _I32),
     "fpg_box_plan_create": ([_I32, _I32, _I32, _D, _D, _I32, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)], _I32),
     "fpg_box_solve": ([_P, _P, _P, _I32], _I32),
@@ -307,6 +308,14 @@ class Domain:
             _check(self.lib.fpg_phase_stats(self.handle, i, ctypes.byref(ln), ctypes.byref(ms)), "fpg_phase_stats")
             out[name] = {"launches": int(ln.value), "ms": float(ms.value)}
         return out
+
+    def set_history(self, buf):
+        """fpg_set_history: buf a CUDA float64 tensor (nrhs, len), or None to stop."""
+        if buf is None:
+            _check(self.lib.fpg_set_history(self.handle, None, 0), "fpg_set_history")
+        else:
+            _check(self.lib.fpg_set_history(self.handle, _ptr(buf), buf.shape[-1]), "fpg_set_history")
+        self._hist = buf  # keep the buffer alive while the library writes it
 
     def fast_solve_path(self) -> int:
         """fpg_fast_solve_path: which kernels the preconditioner runs (see FAST_SOLVE_KERNELS)."""

@@ -63,6 +63,8 @@ int arnoldi_cluster_size(long long len);
 int fast_solve_path(int prec, const FastSolveTables& tb, LineLayout L, int nblk);
 bool dct_plan_shape(int n, DstPlan* pl);
 bool rdft_plan_shape(int n, DstPlan* pl);
+cudaError_t launch_record_history(const double* res, const int* iters, double* hist, int len, int nrhs,
+                                  cudaStream_t st);
 cudaError_t launch_chain_schur(const void* z, int zprec, long long zstride, const ChainGeom& G, const double* ctab,
                                double* corr, const int* active, int nrhs, cudaStream_t st);
 cudaError_t launch_chain_stencil(const void* z, int zprec, long long zstride, double* w, long long wstride,
@@ -298,6 +300,8 @@ struct fpg_domain {
   int* h_done_pinned = nullptr;  // pinned host copy of the done flags
   cudaEvent_t ev_flags = nullptr;
   int bphase = 0;  // non-blocking staged solve: 0 idle, 1 restart issued, 2 finish issued
+  double* hist = nullptr;  // caller's residual-history buffer [nrhs][hist_len] (fpg_set_history)
+  int hist_len = 0;
 };
 
 namespace {
@@ -952,6 +956,10 @@ fpg_status issue_cycle(fpg_domain* D) {
                                       k.iters, D->desc.max_iters, 1, D->st));
       count(D, 2, 1);
       ev_end(D, e);
+      if (D->hist) {
+        FPG_CUDA_TRY(launch_record_history(k.res, k.iters, D->hist, D->hist_len, nrhs, D->st));
+        count(D, 3, 1);
+      }
       continue;
     }
     e = ev_begin(D, 1);
@@ -976,6 +984,10 @@ fpg_status issue_cycle(fpg_domain* D) {
                                  k.iters, D->desc.max_iters, D->st));
       count(D, 3, 1);
       ev_end(D, e);
+    }
+    if (D->hist) {
+      FPG_CUDA_TRY(launch_record_history(k.res, k.iters, D->hist, D->hist_len, nrhs, D->st));
+      count(D, 3, 1);
     }
   }
   e = ev_begin(D, 4);
@@ -2072,6 +2084,14 @@ fpg_status fpg_phase_stats(fpg_domain* d, int32_t phase, int64_t* launches, doub
   ev_collect(d);  // events of operator calls made since the last solve
   if (launches) *launches = d->phase_launches[phase];
   if (ms) *ms = d->phase_ms[phase];
+  return FPG_OK;
+}
+
+fpg_status fpg_set_history(fpg_domain* d, double* dev_buf, int32_t len) {
+  if (!d || len < 0 || (len > 0 && !dev_buf)) return FPG_EINVAL;
+  d->hist = len > 0 ? dev_buf : nullptr;
+  d->hist_len = len;
+  drop_graph(d);  // the recording launches join or leave the captured cycle
   return FPG_OK;
 }
 

@@ -546,3 +546,36 @@ def test_global_refinement_reaches_rtol_at_n1024(lib):
         assert d.solve(p1)[0] == B.FPG_OK
         assert torch.equal(p1[ok], p[ok])
         d.close()
+
+
+def test_residual_history_matches_oracle(lib):
+    """fpg_set_history: the GMRES residual estimate after every step (across
+    restarts) follows the oracle's FGMRES history (Sec. 3.2 residual curves)."""
+    from paper_2509_23180_gb300 import binding as B
+    n, m = 16, 10
+    K = O.assemble("cross", n, 0.0)
+    bs = S.BlockSystem(K, "cross", n)
+    f = W.rhs_batch("cross", n, [0], kind="fourier")
+    _, oinfo = S.algorithm1(bs, f[0], m=m, rtol=1e-10)
+    hist, steps, i, total = oinfo["history"], [], 0, oinfo["iterations"]
+    while len(steps) < total and i < len(hist):  # drop each cycle's starting residual
+        take = min(m, total - len(steps))
+        steps += hist[i + 1:i + 1 + take]
+        i += 1 + take
+    d = domain(B, "cross", n, 0.0, nrhs=1, restart=m, rtol=1e-10)
+    buf = torch.full((1, 400), -1.0, dtype=torch.float64, device="cuda")
+    d.set_history(buf)
+    d.set_rhs(dev(f))
+    p = torch.zeros_like(dev(f))
+    st, info = d.solve(p)
+    assert st == B.FPG_OK
+    gh = host(buf)[0]
+    its = info[0]["iterations"]
+    assert (gh[:its] > 0).all() and (gh[its:] == -1.0).all()
+    fn = np.linalg.norm(f[0])
+    cnt = min(its, len(steps))
+    assert cnt >= 20
+    for a, b in zip(gh[:cnt], steps[:cnt]):
+        if b > 1e-8 * fn:
+            assert abs(a - b) <= 1e-6 * b, (a, b)
+    d.set_history(None)
