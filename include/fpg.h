@@ -398,7 +398,8 @@ fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out);
  * solves writes the GMRES residual estimate |g_{j+1}| of the Schur system of each
  * right-hand side to buf[r * len + i], i = that right-hand side's step count - 1
  * (i < len; relative values: divide by ||f||_2).  Entries past the last step are
- * left untouched.  len = 0 (buf may be NULL) stops recording.  One small extra
+ * left untouched.  len = 0 (buf may be NULL) stops recording; the buffer must
+ * stay valid until then or until the domain is destroyed.  One small extra
  * launch per Arnoldi step while recording.  Errors: FPG_EINVAL. */
 fpg_status fpg_set_history(fpg_domain* d, double* dev_buf, int32_t len);
 
