@@ -1,6 +1,14 @@
 """Request serving on one GPU: continuous batching of solves of mixed geometry
 and size, admitted against an HBM budget.
 
+Two request loops share the Result type and summarize():
+  serve_native()  -- the library's batch runtime (fpg_batch_*: queues per
+                     descriptor, resident domains on their own streams, pool
+                     allocator with eviction) driven from one host thread, with a
+                     producer thread playing the clients;
+  Server.serve()  -- worker threads that each run whole solves on domains they
+                     take from a Python-side pool (described below).
+
 Requests (geometry, n, kappa, 1..slot_rhs right-hand sides) arrive over time.
 The server keeps device-resident domains -- workspaces with the tables, Krylov
 basis and Hessenberg state of Alg. "fft_dd_solver" -- keyed by (geometry, n,
