@@ -61,3 +61,20 @@ def test_algorithm1_block_diagonal(K):
     want = spla.spsolve(A.tocsc(), f)
     assert np.linalg.norm(p - want) / np.linalg.norm(want) < 1e-10
     assert info["converged"]
+
+
+def test_arms_are_independent_blocks():
+    """Sec. 2.4's rule: every arm touches one block only (the coupled row), along
+    exactly n of its unknowns (its interface line), and no two arms touch."""
+    K, n = 3, 5
+    A = X.assemble(K, n, 0.0).tocsr()
+    blocks = X.block_ranges(K, n)
+    sl = {b[0]: slice(b[5], b[5] + b[6]) for b in blocks}
+    arms = [b[0] for b in blocks if b[0] != "C"]
+    for a in arms:
+        for b in arms:
+            if a != b:
+                assert A[sl[a], sl[b]].nnz == 0, (a, b)
+        coupling = A[sl[a], sl["C"]]
+        assert coupling.nnz == n                      # one neighbour per interface node
+        assert len(set(coupling.nonzero()[0])) == n   # on n distinct arm unknowns
