@@ -137,3 +137,16 @@ def test_workload_generator_agrees_with_oracle():
         p, f = X.manufactured(n, kappa)
         assert np.allclose(W.ncross_validation_rhs(n, kappa), f, rtol=1e-13, atol=1e-12)
         assert np.allclose(W.ncross_validation_solution(n), p, rtol=1e-13, atol=1e-14)
+
+
+def test_arms_couple_to_the_centre_only():
+    """Each n x n arm touches the centre along one face of n cells and no other arm
+    (the reentrant corners carry no unknown on the cell-centred grid)."""
+    n = 6
+    A = X.assemble(n, 0.0).tocsr()
+    sl = {b[0]: slice(b[5], b[5] + b[6]) for b in X.block_ranges(n)}
+    for a in ("W", "E", "S", "N"):
+        for b in ("W", "E", "S", "N"):
+            if a != b:
+                assert A[sl[a], sl[b]].nnz == 0
+        assert A[sl[a], sl["C"]].nnz == n
