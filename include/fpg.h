@@ -159,6 +159,16 @@ fpg_status fpg_solve(fpg_domain* d, double* p_dev, fpg_solve_info* info_host);
 fpg_status fpg_solve_async(fpg_domain* d, double* p_dev);
 fpg_status fpg_solve_finish(fpg_domain* d, fpg_solve_info* info_host);
 
+/* Checkpoint / resume: solve the domain's right-hand sides starting from the
+ * iterates already in p_dev (same layout as fpg_solve's output, e.g. the p of a
+ * solve that stopped with FPG_ENOCONV at max_iters, copied out and back).  The
+ * residual r = f - K p is formed on the device, the same algorithm runs on r
+ * (a right-hand side already at or below rtol gets r = 0 and keeps its p), and
+ * the correction is added to p; the acceptance loop then runs as in fpg_solve.
+ * info counts the iterations of this call only.  A right-hand side f = 0 with a
+ * nonzero p runs to max_iters (its rtol ||f|| is 0).  Same errors as fpg_solve. */
+fpg_status fpg_solve_resume(fpg_domain* d, double* p_dev, fpg_solve_info* info_host);
+
 /* End-to-end convenience: host f -> device -> solve -> host p (both pinned for
  * best speed), all on the domain's stream. */
 fpg_status fpg_solve_host(fpg_domain* d, const double* f_host, double* p_host,

@@ -92,6 +92,7 @@ _SIGS = {
     "fpg_set_rhs": ([_P, _P, _I32], _I32),
     "fpg_set_rhs_host": ([_P, _P, _I32], _I32),
     "fpg_solve": ([_P, _P, _P], _I32),
+    "fpg_solve_resume": ([_P, _P, _P], _I32),
     "fpg_solve_async": ([_P, _P], _I32),
     "fpg_solve_finish": ([_P, _P], _I32),
     "fpg_solve_host": ([_P, _P, _P, _P], _I32),
@@ -238,6 +239,14 @@ class Domain:
         st = self.lib.fpg_solve(self.handle, _ptr(p), infos)
         if check and st != FPG_ENOCONV:
             _check(st, "fpg_solve")
+        return st, self._info_list(infos)
+
+    def solve_resume(self, p, check: bool = True):
+        """fpg_solve_resume: continue from the iterates already in p (checkpoint / resume)."""
+        infos = self._infos()
+        st = self.lib.fpg_solve_resume(self.handle, _ptr(p), infos)
+        if check and st not in (FPG_OK, FPG_ENOCONV):
+            _check(st, "fpg_solve_resume")
         return st, self._info_list(infos)
 
     def solve_async(self, p):

@@ -971,8 +971,36 @@ fpg_status stage_resume(fpg_domain* D, bool* resume) {
 
 // One domain, start to finish (the host waits once per restart cycle, and once
 // per acceptance check).
-fpg_status solve_launch(fpg_domain* D, double* p) {
-  FPG_TRY(stage_setup(D, p));
+// Setup of a solve that starts from the iterate held in p (checkpoint / resume):
+// r = f - K p for the right-hand sides whose relative residual is above rtol
+// (0 for the others), then the same algorithm on r, whose result is added to
+// the saved iterate at finish -- the machinery of the acceptance loop's global
+// refinement, with the Krylov target 0.9 rtol ||f||.
+fpg_status stage_setup_from(fpg_domain* D, double* p) {
+  const Layout& L = D->L;
+  const int nrhs = D->desc.nrhs;
+  D->cycles_run = 0;
+  D->accept_rounds = 0;
+  D->refining = false;
+  D->p_cur = p;
+  int e = ev_begin(D, 6);
+  FPG_CUDA_TRY(global_apply(D, p, D->rbuf, D->f, nrhs, D->gres, D->fnorm0, 0.0, nullptr));
+  FPG_CUDA_TRY(cudaMemsetAsync(D->resume_dev, 0, sizeof(int), D->st));
+  FPG_CUDA_TRY(launch_refine_rhs(D->f, D->rbuf, D->gres, D->desc.rtol, L.ntot, nrhs, D->resume_dev, D->gxf, D->st));
+  FPG_CUDA_TRY(cudaMemcpyAsync(D->psave, p, sizeof(double) * nrhs * L.ntot, cudaMemcpyDeviceToDevice, D->st));
+  count(D, 6, 3);
+  ev_end(D, e);
+  D->f_orig = D->f;
+  D->f = D->rbuf;
+  D->refining = true;
+  FPG_TRY(setup_common(D, p, false));
+  FPG_CUDA_TRY(launch_refine_tol(D->ks.tolabs, D->fnorm0, kInnerMargin * D->desc.rtol, nrhs, D->st));
+  count(D, 5, 1);
+  return FPG_OK;
+}
+
+fpg_status solve_launch(fpg_domain* D, double* p, bool from_p = false) {
+  FPG_TRY(from_p ? stage_setup_from(D, p) : stage_setup(D, p));
   for (;;) {
     for (;;) {
       FPG_TRY(stage_restart(D));
@@ -1334,6 +1362,12 @@ fpg_status fpg_set_rhs_host(fpg_domain* d, const double* f_host, int32_t rhs_ind
 fpg_status fpg_solve(fpg_domain* d, double* p_dev, fpg_solve_info* info) {
   if (!d || !p_dev) return FPG_EINVAL;
   FPG_TRY(solve_launch(d, p_dev));
+  return collect_info(d, info);
+}
+
+fpg_status fpg_solve_resume(fpg_domain* d, double* p_dev, fpg_solve_info* info) {
+  if (!d || !p_dev) return FPG_EINVAL;
+  FPG_TRY(solve_launch(d, p_dev, true));
   return collect_info(d, info);
 }
 

@@ -579,3 +579,44 @@ def test_residual_history_matches_oracle(lib):
         if b > 1e-8 * fn:
             assert abs(a - b) <= 1e-6 * b, (a, b)
     d.set_history(None)
+
+
+def test_checkpoint_and_resume(lib):
+    """fpg_solve_resume: a solve paused at max_iters (FPG_ENOCONV, the iterate copied
+    out) and resumed on another domain reaches K^{-1} f; resuming from zero repeats
+    the plain solve bit for bit; resuming from the exact solution takes no step."""
+    from paper_2509_23180_gb300 import binding as B
+    n, kappa = 24, -10.0
+    K = O.assemble("cross", n, kappa)
+    f = W.rhs_batch("cross", n, [3, 4], kind="fourier")
+    ref = D.Factor(K).solve(f)
+    plain = domain(B, "cross", n, kappa, nrhs=2, restart=10, rtol=1e-10)
+    plain.set_rhs(dev(f))
+    p_plain = torch.zeros_like(dev(f))
+    st, info_plain = plain.solve(p_plain)
+    assert st == B.FPG_OK
+    paused = domain(B, "cross", n, kappa, nrhs=2, restart=10, rtol=1e-10, max_iters=12)
+    paused.set_rhs(dev(f))
+    p = torch.zeros_like(dev(f))
+    st, info_a = paused.solve(p, check=False)
+    assert st == B.FPG_ENOCONV and all(i["iterations"] == 12 for i in info_a)
+    checkpoint = p.cpu()  # the iterate leaves the device and comes back
+    resumed = domain(B, "cross", n, kappa, nrhs=2, restart=10, rtol=1e-10)
+    resumed.set_rhs(dev(f))
+    p2 = checkpoint.to("cuda")
+    st, info_b = resumed.solve_resume(p2)
+    assert st == B.FPG_OK
+    P = host(p2)
+    for r in range(2):
+        assert info_b[r]["residual"] <= 1e-10 and rel(P[r], ref[r]) < 1e-9
+        assert info_a[r]["iterations"] + info_b[r]["iterations"] <= info_plain[r]["iterations"] + 10
+    # from zero: the plain solve, bit for bit
+    p0 = torch.zeros_like(dev(f))
+    st, info0 = resumed.solve_resume(p0)
+    assert st == B.FPG_OK and torch.equal(p0, p_plain)
+    assert [i["iterations"] for i in info0] == [i["iterations"] for i in info_plain]
+    # from the exact solution: nothing to do
+    pe = dev(ref)
+    st, infoe = resumed.solve_resume(pe)
+    assert st == B.FPG_OK and all(i["iterations"] == 0 for i in infoe)
+    assert torch.equal(pe, dev(ref))
