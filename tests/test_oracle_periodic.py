@@ -69,3 +69,24 @@ def test_second_order_convergence():
         z = spla.spsolve(P.rectangle_periodic_t(nt, ns, h).tocsc(), f)
         errs.append(np.abs(z - p).max())
     assert 3.8 < errs[0] / errs[1] < 4.2 and 3.8 < errs[1] / errs[2] < 4.2, errs
+
+
+def test_direct_solve_equals_fft_banded_solve():
+    """An independent route: numpy's FFT along t, one banded (tridiagonal) solve per
+    Fourier mode along s with scipy, inverse FFT -- equal to the sparse LU solve."""
+    from scipy.linalg import solve_banded
+    nt, ns, h, kappa = 12, 9, 0.1, -2.0
+    d = 1.0 / h ** 2
+    v = np.random.default_rng(5).standard_normal((ns, nt))
+    V = np.fft.fft(v, axis=1)
+    Z = np.empty_like(V)
+    for k in range(nt):
+        diag = -2 * d - 4 * d * np.sin(np.pi * k / nt) ** 2 + kappa
+        ab = np.zeros((3, ns), dtype=complex)
+        ab[0, 1:] = d
+        ab[1, :] = diag
+        ab[2, :-1] = d
+        Z[:, k] = solve_banded((1, 1), ab, V[:, k])
+    z = np.fft.ifft(Z, axis=1).real
+    want = P.solve_periodic_rectangle(nt, ns, h, kappa, v.ravel()[None, :])[0]
+    assert np.allclose(z.ravel(), want, rtol=1e-11, atol=1e-13)
