@@ -460,6 +460,8 @@ class Batch:
     """The library's batch runtime (fpg_batch_*): continuous batching of requests
     over resident domains carved from one device pool (a torch uint8 tensor)."""
 
+    report_cap = 256  # finished tickets one step() reports; poll() finds any beyond them
+
     def __init__(self, pool_bytes: int, slots: int = 8, max_domains: int = 64, max_per_key: int = 2, max_busy: int = 0,
                  device="cuda"):
         import torch
@@ -483,7 +485,7 @@ class Batch:
 
     def step(self) -> list:
         """Advance the runtime; returns the tickets that finished in this step."""
-        cap = 256
+        cap = self.report_cap
         buf = (_I64 * cap)()
         c = _I32()
         _check(self.lib.fpg_batch_step(self.handle, buf, cap, ctypes.byref(c)), "fpg_batch_step")

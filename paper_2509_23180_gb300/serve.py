@@ -380,7 +380,7 @@ def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart
             finished = batch.step()
             for t in finished:
                 progressed |= collect(t)
-            if len(finished) >= 256:  # more finished than reported: poll the rest
+            if len(finished) >= batch.report_cap:  # more finished than reported: poll the rest
                 for t in list(live):
                     collect(t)
             if not progressed:
