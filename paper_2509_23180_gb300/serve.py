@@ -305,10 +305,11 @@ def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart
     results = {}
     t0 = time.perf_counter()
     stop = threading.Event()
+    failed = []        # the producer's exception, re-raised by the driver thread
 
     def producer():
-        stream = torch.cuda.Stream(device=device)
         try:
+            stream = torch.cuda.Stream(device=device)
             for i in order:
                 if stop.is_set():
                     return
@@ -326,6 +327,8 @@ def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart
                 desc = B.make_desc(geom, n, kappa, nrhs=nr, restart=restart, rtol=rtol,
                                    precond_precision=precond_precision)
                 ready.put((r, desc, f, p))
+        except BaseException as e:
+            failed.append(e)
         finally:
             ready.put(None)
 
@@ -372,6 +375,8 @@ def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart
                 except queue.Empty:
                     break
                 if entry is None:
+                    if failed:
+                        raise RuntimeError("request producer failed") from failed[0]
                     produced_all = True
                     break
                 if waiting or not try_admit(entry):

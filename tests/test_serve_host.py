@@ -8,7 +8,9 @@ What the loop must guarantee whatever the device does:
   * a request refused for lack of room waits and is admitted before any later
     arrival (first come, first admitted), once room frees;
   * a request that could never fit the pool is an error, not an endless wait;
-  * more finished tickets than one step reports are still all collected.
+  * more finished tickets than one step reports are still all collected;
+  * a failure while preparing a request ends the loop with that error (and the
+    runtime is closed), instead of a missing result.
 """
 import contextlib
 
@@ -93,7 +95,7 @@ class FakeBatch:
         return {"created": 0, "evicted": 0, "steps": self.steps}
 
     def close(self):
-        assert not self.running and not self.done, "tickets left behind"
+        self.left = len(self.running) + len(self.done)  # tickets neither finished nor collected
 
 
 class _Stream:
@@ -133,6 +135,7 @@ def test_every_request_gets_one_result_in_order(fake):
     assert all(r.nrhs == q["nrhs"] and len(r.residuals) == q["nrhs"] for r, q in zip(res, reqs))
     assert all(r.status == B.FPG_OK for r in res)
     assert [a[0] for a in FakeBatch.log.admitted] == sorted(a[0] for a in FakeBatch.log.admitted)
+    assert FakeBatch.log.left == 0
 
 
 def test_refused_requests_wait_and_keep_arrival_order(fake):
@@ -144,7 +147,7 @@ def test_refused_requests_wait_and_keep_arrival_order(fake):
     assert [r.id for r in res] == [q["id"] for q in reqs]
     by_arrival = sorted(reqs, key=lambda q: q["arrival_s"])
     assert [(a[1], a[2]) for a in FakeBatch.log.admitted] == [(q["n"], q["nrhs"]) for q in by_arrival]
-    assert FakeBatch.log.refused >= 10 and FakeBatch.log.used == 0
+    assert FakeBatch.log.refused >= 10 and FakeBatch.log.used == 0 and FakeBatch.log.left == 0
 
 
 def test_request_larger_than_the_pool_is_an_error(fake):
@@ -161,4 +164,21 @@ def test_more_finished_than_one_step_reports(fake):
     reqs = _requests(25)
     res, _ = S.serve_native(reqs, pool_bytes=1 << 40, realtime=False, device="cpu")
     assert len(res) == 25 and all(len(r.iterations) == r.nrhs for r in res)
-    assert FakeBatch.log.truncated >= 1
+    assert FakeBatch.log.truncated >= 1 and FakeBatch.log.left == 0
+
+
+def test_a_failing_producer_fails_the_loop(fake, monkeypatch):
+    fake(latency=5)
+    calls = []
+
+    def rhs(g, n, seed, device=None):
+        calls.append(seed)
+        if len(calls) > 12:
+            raise ValueError("rhs generation failed")
+        return torch.zeros(W.total_unknowns(g, n), dtype=torch.float64)
+
+    monkeypatch.setattr(W, "fourier_rhs_torch", rhs)
+    with pytest.raises(RuntimeError) as e:
+        S.serve_native(_requests(20), pool_bytes=1 << 40, realtime=False, device="cpu")
+    assert isinstance(e.value.__cause__, ValueError)
+    assert hasattr(FakeBatch.log, "left")  # the runtime was still closed
