@@ -60,3 +60,30 @@ def test_gmres_exact_in_N_steps_and_restarted():
     x3, info3 = Kr.gmres(lambda v: A @ v, b, m=10, atol=1e-12 * np.linalg.norm(b),
                          right_precond=lambda v: M @ v)
     assert np.allclose(x3, x_ref, rtol=1e-9) and info3["iterations"] < info2["iterations"]
+
+
+def test_gmres_history_is_the_minimal_residual_over_the_krylov_space():
+    """The GMRES residual after k steps is min ||b - A x|| over x in K_k(A, b)
+    (the defining property), found here by least squares over the explicit
+    Krylov power basis; with a fixed right preconditioner M it is the same over
+    x in M K_k(A M, b)."""
+    rng = np.random.default_rng(7)
+    N = 40
+    A = rng.standard_normal((N, N)) / np.sqrt(N) + 2.0 * np.eye(N)
+    b = rng.standard_normal(N)
+    M = np.linalg.inv(A + 0.3 * rng.standard_normal((N, N)) / np.sqrt(N))
+    for precond in (None, M):
+        Aop = A if precond is None else A @ precond
+        _, info = Kr.gmres(lambda v: A @ v, b, m=12, atol=0.0, max_iters=8,
+                           right_precond=None if precond is None else (lambda v: precond @ v))
+        hist = info["history"]
+        P = np.zeros((N, 8))
+        v = b.copy()
+        for k in range(8):
+            P[:, k] = v / np.linalg.norm(v)
+            v = Aop @ P[:, k]
+        for k in range(1, 9):
+            Q, _ = np.linalg.qr(P[:, :k])          # an orthonormal basis of K_k
+            y, *_ = np.linalg.lstsq(Aop @ Q, b, rcond=None)
+            best = np.linalg.norm(b - Aop @ Q @ y)
+            assert abs(hist[k] - best) <= 1e-10 * np.linalg.norm(b), (precond is None, k, hist[k], best)
