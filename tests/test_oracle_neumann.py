@@ -1,6 +1,7 @@
 """Pins of the Neumann oracle (Sec. 2.2, Eq. "submat_Neumann"): eigenpairs in
 closed form, the transform against a library DCT, an independently built dense
-stencil, and second-order convergence on a manufactured solution."""
+stencil, second-order convergence on a manufactured solution, and the rectangle
+solve by an independent route (library DCT-II plus banded solves)."""
 import numpy as np
 import pytest
 
@@ -83,3 +84,25 @@ def test_second_order_on_the_manufactured_solution():
         errs.append(np.max(np.abs(z - p)))
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 3.6 < r1 < 4.4 and 3.8 < r2 < 4.2, errs
+
+
+def test_direct_solve_equals_dct_banded_solve():
+    """An independent route: scipy's orthonormal DCT-II along t, one banded
+    (tridiagonal) solve per cosine mode along s, inverse DCT-II -- equal to the
+    sparse LU solve of the Neumann rectangle."""
+    from scipy.fft import dct, idct
+    from scipy.linalg import solve_banded
+    nt, ns, h, kappa = 11, 8, 1.0 / 11, -3.0
+    d = 1.0 / h ** 2
+    v = np.random.default_rng(6).standard_normal((ns, nt))
+    V = dct(v, type=2, norm="ortho", axis=1)
+    Z = np.empty_like(V)
+    for k in range(nt):
+        ab = np.zeros((3, ns))
+        ab[0, 1:] = d
+        ab[1, :] = -2 * d - 4 * d * np.sin(np.pi * k / (2 * nt)) ** 2 + kappa
+        ab[2, :-1] = d
+        Z[:, k] = solve_banded((1, 1), ab, V[:, k])
+    z = idct(Z, type=2, norm="ortho", axis=1)
+    want = N.solve_neumann_rectangle(nt, ns, h, kappa, v.ravel()[None, :])[0]
+    assert np.allclose(z.ravel(), want, rtol=1e-11, atol=1e-13)
