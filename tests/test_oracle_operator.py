@@ -94,3 +94,35 @@ def test_direct_batch_of_rhs_dense_and_sparse():
         X = F.solve(b)
         for r in range(3):
             assert np.allclose(X[r], F.solve(b[r]), rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("case", ["cross64", "T40", "L30", "chain2_12", "ncross24", "periodic", "box"])
+def test_library_direct_solve_equals_conjugate_gradient(case):
+    """The library direct solves the oracle uses (dense LU, SuperLU) against a
+    second route written from the textbook definition: CG on -K to a relative
+    residual of 1e-12 (the rounding floor of the recurrence at n = 64 is ~5e-13)."""
+    from oracle import box as Xb
+    from oracle import neumann_cross as NC
+    from oracle import periodic as P
+    from oracle import strip as S
+    rng = np.random.default_rng(11)
+    if case == "cross64":
+        K, b = O.assemble("cross", 64, 0.0), W.fourier_rhs("cross", 64, 1)
+    elif case == "T40":
+        K, b = O.assemble("T", 40, -10.0), W.fourier_rhs("T", 40, 2)
+    elif case == "L30":
+        K, b = O.assemble("L", 30, -3.0), W.fourier_rhs("L", 30, 3)
+    elif case == "chain2_12":
+        K, b = S.assemble(2, 12, -10.0), W.strip_fourier_rhs(2, 12, 4)
+    elif case == "ncross24":
+        K, b = NC.assemble(24, 0.0), W.ncross_fourier_rhs(24, 5)
+    elif case == "periodic":
+        K = P.rectangle_periodic_t(24, 17, 1 / 24, -1.0)
+        b = rng.standard_normal(K.shape[0])
+    else:
+        K = Xb.box_operator(9, 8, 7, 0.1, -2.0)
+        b = rng.standard_normal(K.shape[0])
+    x_cg, steps = D.conjugate_gradient(K, b, rtol=1e-12)
+    x = D.solve(K, b)
+    assert np.linalg.norm(b - K @ x_cg) <= 1.5e-12 * np.linalg.norm(b), steps
+    assert np.abs(x - x_cg).max() <= 1e-10 * np.abs(x).max()
