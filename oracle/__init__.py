@@ -11,7 +11,8 @@ What it computes, each piece by its plain definition:
                union of the blocks (Sec. 2.3, Fig. "concat"; the cross of Sec. 3)
   operator  -- the global 5-point matrix K of  lap p + kappa p = f  (Eq. 1,
                Eq. "Poisson_central", Eq. "mat_Poisson") with zero Dirichlet data
-  direct    -- p = K^{-1} b (dense LU for tiny grids, sparse LU otherwise)
+  direct    -- p = K^{-1} b (dense LU for tiny grids, sparse LU otherwise), and
+               conjugate gradients on -K as a second, hand-written route
   transforms-- the DST-I matrix and the closed-form eigenvalues (Eqs.
                "Poisson_spectral_eigen", "eigvector_Diri")
   schur     -- the block pieces A_i, R_ij read off K, the Schur complement
@@ -30,6 +31,7 @@ What it computes, each piece by its plain definition:
 
 Parity status: every function above is pinned by `tests/test_oracle_*.py`
 (closed forms, brute force on tiny grids, second-order convergence, library
-routines).  Iteration counts are "parity unpinned": the paper's plots of them
+routines, an independent second route: library transforms with banded solves,
+conjugate gradients, least squares over the explicit Krylov space).  Iteration counts are "parity unpinned": the paper's plots of them
 are lost, only their trend is stated.
 """
