@@ -1,6 +1,7 @@
 """bench.py's host-side pieces (CPU only): the reference arm's JSON line on a small
-workload, the committed DRAM-traffic lookup and its invalidation, and the oracle
-baseline helper of the widening lines."""
+workload, the committed DRAM-traffic lookup and its invalidation, the oracle
+baseline helper of the widening lines, the algorithmic work behind the roofline,
+the choice of the dominant kernel and its peak, and the clock-sample summary."""
 import json
 import os
 import subprocess
@@ -52,3 +53,49 @@ def test_cpu_baseline_helper():
     out = bench.cpu_baseline_of(lambda: strip.assemble(2, 4, 0.0),
                                 np.stack([W.strip_fourier_rhs(2, 4, s) for s in range(2)]), "tiny chain")
     assert out["kind"] == "oracle" and out["value"] > 0 and out["cores"] == 1 and "tiny chain" in out["sample"]
+
+
+def test_arnoldi_algorithmic_work_per_point():
+    """The roofline's algorithmic work of one Arnoldi step per centre point:
+    8(j+1)+16 bytes and 4(j+1)+12 flops at the cycle's mean index j = m/2, i.e.
+    144 B and 76 flops for m = 30 (94.4 MB and 49.8 MFLOP per launch of 10
+    right-hand sides of 256^2)."""
+    import bench
+    c = bench.algorithmic_costs(256, 76.6, 30)
+    nc = 256 * 256
+    assert c["arnoldi_bytes"] == 144.0 * nc and c["arnoldi_flops"] == 76.0 * nc
+    assert c["arnoldi_bytes"] * 10 == 94371840.0 and c["arnoldi_flops"] * 10 == 49807360.0
+    short = bench.algorithmic_costs(64, 9.0, 30)      # fewer steps than m: j averages over them
+    assert short["arnoldi_flops"] == (4.0 * (4.5 + 1) + 12.0) * 64 * 64
+
+
+def test_roofline_picks_the_dominant_kernel_and_divides_by_its_peak():
+    import bench
+    args = SimpleNamespace(n=256, precision=64, seeds=10)
+    costs = bench.algorithmic_costs(256, 76.6, 30)
+    phases = {"arnoldi": {"ms": 17.2, "launches": 180}, "dst_forward": {"ms": 9.8, "launches": 90},
+              "thomas": {"ms": 3.6, "launches": 90}, "dst_inverse": {"ms": 10.0, "launches": 90}}
+    r = bench.roofline(phases, costs, args, {"hbm_gbs": 6774.0}, 1.05e12, 75e12, 10)
+    assert r["phase"] == "arnoldi" and r["kernel"] == "k_arnoldi_cluster_reg" and r["bound"] == "alu"
+    t = 17.2e-3 / 180
+    assert abs(r["achieved"] - 49807360.0 / t / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 1.05) < 1e-12 and r["unit"] == "TFLOP/s"
+    # FP32 fast solve dominating: HBM-bound line against the measured copy bandwidth
+    args32 = SimpleNamespace(n=256, precision=32, seeds=10)
+    phases32 = {"arnoldi": {"ms": 1.0, "launches": 10}, "dst_forward": {"ms": 5.0, "launches": 10}}
+    r32 = bench.roofline(phases32, costs, args32, {"hbm_gbs": 6774.0}, 1.05e12, 75e12, 10)
+    assert r32["bound"] == "hbm" and r32["unit"] == "GB/s" and r32["peak"] == 6774.0
+    assert abs(r32["achieved"] - 12 * 256 * 256 * 10 / 5e-4 / 1e9) < 1e-9
+
+
+def test_clock_summary_reads_reasons_and_median(tmp_path):
+    import bench
+    csv = tmp_path / "clocks.csv"
+    csv.write_text("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                   "0, 1980, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active\n"
+                   "0, 2040, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                   "garbage line\n")
+    s = bench.ClockSampler(0)
+    s.proc, s.path = object(), str(csv)
+    out = s.summary()
+    assert out == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "samples": 3, "reasons": ["sw_power_cap"]}
