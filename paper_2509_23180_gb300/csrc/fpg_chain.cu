@@ -2,8 +2,10 @@
 // squares in a row along x form the coupled set -- centres at even positions,
 // links between them -- with arms W and E at the row's ends and S_i, N_i below
 // and above centre i; every arm touches one block and is eliminated exactly,
-// the row is solved by flexible GMRES with the block-diagonal preconditioner
-// of its squares (one fast solve per square, run by the a1 kernels).
+// and the row is solved by flexible GMRES.  Its preconditioner is the row's own
+// operator, one fast solve of the whole rectangle (transforms along y, sweeps of
+// nxc rows along x), or on request the block diagonal of its squares (one fast
+// solve per square); both run on the a1 kernels.
 //
 // Layout of one full vector (vertex-centred grid, h = 1/(n+1)): the coupled row
 // as one rectangle of nxc = (2K-1)(n+1) - 1 columns by n rows (x fastest; each
