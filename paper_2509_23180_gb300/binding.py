@@ -492,9 +492,11 @@ class Batch:
         return list(buf[:min(cap, c.value)])
 
     def poll(self, ticket: int, nrhs: int):
-        """None while running; else the list of per-RHS info dicts (the ticket is released)."""
+        """None while running; else the list of per-RHS info dicts (the ticket is released).
+        The library writes one entry per right-hand side of the request, at most
+        `slots`, so the array is sized by slots whatever nrhs the caller names."""
         done = _I32()
-        arr = (SolveInfo * max(1, nrhs))()
+        arr = (SolveInfo * max(1, self.slots, nrhs))()
         _check(self.lib.fpg_batch_poll(self.handle, ticket, ctypes.byref(done), arr), "fpg_batch_poll")
         if not done.value:
             return None
