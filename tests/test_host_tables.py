@@ -1,0 +1,199 @@
+"""The library's host-side tables (CPU only; needs nvcc): the DST-I plan of a
+line length, Rader's permutations and kernel, the sine table, and the Thomas
+pivots of every mode.  A small host program built from the library's own header
+(fpg_host_tables.h) prints them, and each is checked by an independent route:
+  * the plan's radices multiply to its FFT length, the mode follows from p = n + 1
+    (Stockham when p factors into 4, 2 and odd primes to 43, Rader for such a p - 1
+    with p prime, the dense DST otherwise);
+  * Rader: pin[b] = g^b mod p with g of order p - 1 (so pin is a permutation of
+    1..p-1), pout = its inverse powers, and Bhat = DFT(B)/N (numpy FFT), which
+    makes the Rader convolution reproduce numpy's DFT of length p;
+  * sinp[j] = sin(pi j / p) within 3e-16 of 40-digit values (an absolute bound:
+    the table is computed as cos(pi/2 - pi j/p), so small entries carry a large
+    relative error, which the DST packing does not see);
+  * a Thomas sweep with the printed reciprocal pivots solves tridiag(delta,
+    d_k, delta) x = f as LAPACK's banded solver does (scipy), with
+    d_k = -4 delta + 2 delta cos(k pi/(n+1)) + kappa (Sec. 2.1, Eq. "trans_subeq").
+"""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+mpmath = pytest.importorskip("mpmath")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2509_23180_gb300", "csrc")
+SIZES = [2, 7, 16, 33, 64, 88, 93, 100, 256, 512, 1024]
+PIVOTS = [(8, 5, 81.0, 0.0), (64, 64, 4225.0, -10.0), (256, 257, 66049.0, -3.0)]
+
+PROGRAM = r"""
+#include <cstdio>
+#include <vector>
+#include "fpg_host_tables.h"
+using namespace fpg;
+int main() {
+  const int sizes[] = {%(sizes)s};
+  for (int n : sizes) {
+    HostPlan P = build_plan(n);
+    std::printf("PLAN %%d %%d %%d %%d", n, P.mode, P.N, P.nrad);
+    for (int i = 0; i < P.nrad; ++i) std::printf(" %%d", P.rad[i]);
+    std::printf("\nSINP %%d", n);
+    for (double v : P.sinp) std::printf(" %%a", v);
+    std::printf("\n");
+    if (P.mode == DST_RADER) {
+      std::printf("PIN %%d", n);
+      for (int v : P.pin) std::printf(" %%d", v);
+      std::printf("\nPOUT %%d", n);
+      for (int v : P.pout) std::printf(" %%d", v);
+      std::printf("\nBHAT %%d", n);
+      for (double v : P.Bhat) std::printf(" %%a", v);
+      std::printf("\n");
+    }
+  }
+  struct Pv { int n, ns; double delta, kappa; };
+  const Pv pv[] = {%(pivots)s};
+  for (const Pv& q : pv) {
+    std::vector<double> r;
+    fill_pivots(q.n, q.ns, q.delta, q.kappa, r);
+    std::printf("PIV %%d %%d", q.n, q.ns);
+    for (double v : r) std::printf(" %%a", v);
+    std::printf("\n");
+  }
+  return 0;
+}
+"""
+
+@pytest.fixture(scope="module")
+def tables(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    d = tmp_path_factory.mktemp("tables")
+    pv = ", ".join(f"{{{n}, {ns}, {delta!r}, {kappa!r}}}" for n, ns, delta, kappa in PIVOTS)
+    src = d / "tables.cu"
+    src.write_text(PROGRAM % {"sizes": ", ".join(map(str, SIZES)), "pivots": pv})
+    probe = d / "modes.cu"
+    probe.write_text('#include <cstdio>\n#include "fpg_dst.cuh"\n'
+                     'int main() { std::printf("%d %d %d\\n", fpg::DST_DENSE, fpg::DST_STOCKHAM, fpg::DST_RADER); }\n')
+    flags = ["-std=c++17", "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
+             "-gencode", "arch=compute_103a,code=sm_103a"]
+    out = {}
+    for name in ("tables", "modes"):
+        exe = d / name
+        subprocess.run([nvcc, *flags, str(d / f"{name}.cu"), "-o", str(exe)], check=True, capture_output=True,
+                       timeout=300)
+        out[name] = subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=60).stdout
+    modes = dict(zip(("dense", "stockham", "rader"), map(int, out["modes"].split())))
+    rec = {}
+    for line in out["tables"].splitlines():
+        tag, key, *vals = line.split()
+        rec[(tag, int(key))] = vals
+    return modes, rec
+
+
+def _hex(vals):
+    return np.array([float.fromhex(v) for v in vals])
+
+
+def _factors_ok(p):
+    m = p
+    while m % 2 == 0:
+        m //= 2
+    for q in (3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43):
+        while m % q == 0:
+            m //= q
+    return m == 1
+
+
+def _is_prime(p):
+    return p > 1 and all(p % d for d in range(2, int(p ** 0.5) + 1))
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_plan_mode_and_radices(tables, n):
+    modes, rec = tables
+    mode, N, nrad, *rad = map(int, rec[("PLAN", n)])
+    p = n + 1
+    if p > 1 and _factors_ok(p):
+        assert mode == modes["stockham"] and N == p
+    elif _is_prime(p) and _factors_ok(p - 1):
+        assert mode == modes["rader"] and N == p - 1
+    else:
+        assert mode == modes["dense"] and nrad == 0
+        return
+    assert len(rad) == nrad and int(np.prod(rad)) == N
+    assert all(r in (2, 3, 4, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43) for r in rad)
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_sine_table(tables, n):
+    _, rec = tables
+    p = n + 1
+    s = _hex(rec[("SINP", n)])
+    assert len(s) == p
+    mpmath.mp.dps = 40
+    worst = max(abs(float(mpmath.mpf(s[j]) - mpmath.sin(mpmath.pi * j / p))) for j in range(p))
+    # absolute accuracy (what the packing u_j = sin(pi j/p)(x_j + x_{p-j}) + (x_j - x_{p-j})/2
+    # needs): the table is cos(pi q/den) after exact folding, and the rounding of the
+    # argument pi q/den (up to ~3e-16 near pi/2) carries over; measured worst 2.58e-16,
+    # with j = 0 holding cos(pi/2) = 6.1e-17 in place of 0
+    assert worst <= 3e-16, worst
+
+
+def test_rader_tables_reproduce_the_dft(tables):
+    modes, rec = tables
+    rader = [n for n in SIZES if int(rec[("PLAN", n)][0]) == modes["rader"]]
+    assert rader, "no Rader length among the sizes"
+    rng = np.random.default_rng(9)
+    for n in rader:
+        p, N = n + 1, n
+        pin = np.array(list(map(int, rec[("PIN", n)])))
+        pout = np.array(list(map(int, rec[("POUT", n)])))
+        g = int(pin[1])
+        assert pin[0] == 1 and sorted(pin) == list(range(1, p))
+        assert all(pow(g, (p - 1) // q, p) != 1 for q in range(2, p) if (p - 1) % q == 0 and _is_prime(q))
+        assert all(pin[b] == pow(g, b, p) and (pout[b] * pin[b]) % p == 1 for b in range(N))
+        bh = _hex(rec[("BHAT", n)])
+        Bhat = bh[0::2] + 1j * bh[1::2]
+        B = np.exp(-2j * np.pi * pout / p)
+        assert np.allclose(Bhat, np.fft.fft(B) / N, rtol=0, atol=1e-15)
+        # Rader: X_{g^{-c}} = x_0 + sum_b x_{g^b} B_{c-b}, computed as a circular
+        # convolution through the length-N DFT with the printed kernel
+        x = rng.standard_normal(p) + 1j * rng.standard_normal(p)
+        a = x[pin]
+        conv = np.fft.ifft(np.fft.fft(a) * Bhat * N)
+        X = np.empty(p, dtype=complex)
+        X[0] = x.sum()
+        X[pout] = x[0] + conv
+        assert np.allclose(X, np.fft.fft(x), rtol=0, atol=1e-12 * np.abs(x).sum())
+
+
+@pytest.mark.parametrize("n,ns,delta,kappa", PIVOTS)
+def test_thomas_pivots_solve_the_mode_systems(tables, n, ns, delta, kappa):
+    from scipy.linalg import solve_banded
+    _, rec = tables
+    vals = rec[("PIV", n)]
+    assert int(vals[0]) == ns
+    r = _hex(vals[1:]).reshape(n, ns)
+    rng = np.random.default_rng(n)
+    for k in (1, 2, n // 2 + 1, n):
+        d = -4 * delta + 2 * delta * np.cos(k * np.pi / (n + 1)) + kappa
+        f = rng.standard_normal(ns)
+        rk = r[k - 1]
+        y = np.empty(ns)
+        y[0] = rk[0] * f[0]
+        for s in range(1, ns):
+            y[s] = rk[s] * (f[s] - delta * y[s - 1])
+        x = np.empty(ns)
+        x[-1] = y[-1]
+        for s in range(ns - 2, -1, -1):
+            x[s] = y[s] - delta * rk[s] * x[s + 1]
+        ab = np.zeros((3, ns))
+        ab[0, 1:] = delta
+        ab[1, :] = d
+        ab[2, :-1] = delta
+        want = solve_banded((1, 1), ab, f)
+        assert np.allclose(x, want, rtol=1e-12, atol=1e-14 * np.abs(want).max()), (n, k)
