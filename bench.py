@@ -52,13 +52,14 @@ def parse():
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: HBM admission budget")
-    ap.add_argument("--server", default="native", choices=["native", "threads"],
-                    help="serving: the library's batch runtime driven by one host thread, or the threaded "
-                         "Python server")
     ap.add_argument("--option", action="append", default=[], metavar="NAME=VALUE",
                     help="fpg_set_option on every domain, e.g. DST_ENGINE=1, FUSED_FASTSOLVE=1, ARNOLDI_THREADS=512")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default run: leave out the precision, batching and serving workloads")
+    ap.add_argument("--serving-prefix", type=int, default=1000,
+                    help="serving: requests of the stream's prefix served both batched and one at a time")
     return ap.parse_args()
 
 
@@ -124,37 +125,92 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle arm
-def oracle_step(args, f_by_kappa):
-    """The FP64 oracle on the same workload: sparse LU of K, then the solves."""
-    from oracle import direct, operator
-    t0 = time.perf_counter()
-    out = {}
-    for kappa, f in f_by_kappa.items():
-        K = operator.assemble("cross", args.n, kappa)
-        out[kappa] = direct.Factor(K).solve(f)
-    return time.perf_counter() - t0, out
+# The oracle runs on the host cores through a process pool started with `spawn`
+# (the parent may already hold a CUDA context).  Its unit of work is one
+# independent piece of the workload: assemble K, factor it (SuperLU, one thread),
+# solve the right-hand sides handed to that piece.  The workload's right-hand
+# sides per kappa are split over the workers, so every worker that gets a piece
+# factors K itself: the pool measures the oracle as it stands, run on all cores.
+def _oracle_warm(_):
+    import scipy.sparse.linalg  # noqa: F401
+    from oracle import direct, operator  # noqa: F401
+    return os.getpid()
 
 
-def cpu_baseline(args, f_by_kappa, max_seconds=30.0):
-    """Oracle timed on the host cores on a bounded sample: the factorisation and
-    the solves of the first kappa's right-hand sides (the sample shrinks when a
-    solve would exceed the time bound)."""
+def _oracle_task(task):
+    geom, n, kappa, f = task
     from oracle import direct, operator
-    kappa = 0.0
-    f = f_by_kappa[kappa]
     t0 = time.perf_counter()
-    K = operator.assemble("cross", args.n, kappa)
-    F = direct.Factor(K)
-    cnt = 0
-    for r in range(f.shape[0]):
-        F.solve(f[r])
-        cnt += 1
-        if time.perf_counter() - t0 > max_seconds:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": cnt / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"kappa=0: assemble + SuperLU factor of K ({K.shape[0]} unknowns) + {cnt} direct solves, "
-                      f"{dt:.1f} s (SuperLU and the assembly run single-threaded)"}
+    K = operator.assemble_grid(geom, n, kappa)
+    P = direct.Factor(K).solve(f)
+    return time.perf_counter() - t0, P
+
+
+class OraclePool:
+    """Worker processes for the oracle, one per host core (or `workers`), each
+    single-threaded (BLAS threads pinned to 1 in the children)."""
+
+    def __init__(self, workers: int | None = None):
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        self.workers = max(1, workers or os.cpu_count() or 1)
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            self.ex = ProcessPoolExecutor(max_workers=self.workers, mp_context=mp.get_context("spawn"))
+            list(self.ex.map(_oracle_warm, range(self.workers)))  # start and import before any timing
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def split(self, geom, n, f_by_kappa, pieces: int | None = None):
+        """Tasks covering every right-hand side: per kappa, up to workers / #kappa pieces."""
+        per = max(1, (pieces or self.workers) // max(1, len(f_by_kappa)))
+        tasks = []
+        for kappa, f in f_by_kappa.items():
+            import numpy as np
+            for idx in np.array_split(np.arange(f.shape[0]), min(per, f.shape[0])):
+                tasks.append((geom, n, kappa, f[idx]))
+        return tasks
+
+    def run(self, tasks):
+        """Wall seconds for all tasks (in parallel) and their solutions in task order."""
+        t0 = time.perf_counter()
+        out = list(self.ex.map(_oracle_task, tasks))
+        return time.perf_counter() - t0, [P for _, P in out]
+
+    def close(self):
+        self.ex.shutdown()
+
+
+def oracle_step(args, pool, f_by_kappa):
+    """One step of the headline workload on the oracle: every kappa's RHS, all cores."""
+    tasks = pool.split("cross", args.n, f_by_kappa)
+    dt, _ = pool.run(tasks)
+    return dt, min(len(tasks), pool.workers)
+
+
+def cpu_baseline(args, f_by_kappa, pool=None):
+    """The oracle timed on the host cores: one full step of the headline workload
+    (every kappa's factorisation and all right-hand sides), split over the cores."""
+    own = pool is None
+    pool = pool or OraclePool()
+    try:
+        dt, used = oracle_step(args, pool, f_by_kappa)
+    finally:
+        if own:
+            pool.close()
+    nsolve = sum(f.shape[0] for f in f_by_kappa.values())
+    return {"value": nsolve / dt, "unit": "solves/s", "cores": used, "kind": "oracle",
+            "sample": f"one full step: {nsolve} direct solves of the cross {args.n}^2 per block "
+                      f"({args.n ** 2 + 4 * args.n * (args.n + 1)} unknowns), kappa in "
+                      f"{sorted(f_by_kappa)}; {used} worker processes on {os.cpu_count()} host cores, each "
+                      f"assembling K and factoring it (SuperLU, single-threaded) for its share of the RHS; "
+                      f"{dt:.1f} s wall"}
 
 
 def cpu_baseline_of(assemble, f, label, max_seconds=30.0):
@@ -176,25 +232,49 @@ def cpu_baseline_of(assemble, f, label, max_seconds=30.0):
                       f"{dt:.1f} s (single-threaded)"}
 
 
-def run_reference(args, rank, world):
+def error_stats(P, R, geom, n):
+    """Error of a GPU solution P against the oracle's R (one vector each): the 2-norm
+    relative error, max|P - R| / max|R|, and the worst block's max-abs relative error."""
     import numpy as np
+    import workloads as W
+    P = np.asarray(P, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64)
+    out = {"rel_2norm": float(np.linalg.norm(P - R) / np.linalg.norm(R)),
+           "maxabs_rel": float(np.abs(P - R).max() / np.abs(R).max())}
+    off, worst = 0, (None, 0.0)
+    for name in W.GEOMETRY_BLOCKS[geom]:
+        nx, ny = W.block_shape(name, n)
+        sl = slice(off, off + nx * ny)
+        off += nx * ny
+        e = float(np.abs(P[sl] - R[sl]).max() / max(np.abs(R[sl]).max(), 1e-300))
+        if e >= worst[1]:
+            worst = (name, e)
+    out["worst_block"] = {"block": worst[0], "maxabs_rel": worst[1]}
+    return out
+
+
+def run_reference(args, rank, world):
     import workloads as W
     if rank != 0:
         return
     seeds = list(range(args.seeds))
     f_by_kappa = {k: W.rhs_batch("cross", args.n, seeds, kind="fourier") for k in (0.0, -10.0)}
-    times = []
+    pool = OraclePool()
+    times, used = [], 1
     for s in range(args.warmup + args.steps):
-        dt, _ = oracle_step(args, f_by_kappa)
+        dt, used = oracle_step(args, pool, f_by_kappa)
         if s >= args.warmup:
             times.append(dt)
+    pool.close()
     ms = 1e3 * sum(times) / len(times)
     val = 2 * args.seeds / (ms * 1e-3)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload(args),
-            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": "full step: SuperLU factor of K per kappa + all direct solves, single thread"},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": used, "kind": "oracle",
+                             "sample": f"every step in full: SuperLU factor of K per kappa and all direct solves, "
+                                       f"split over {used} worker processes ({os.cpu_count()} host cores), each "
+                                       f"factoring K for its share of the right-hand sides"},
             "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -400,8 +480,20 @@ def run_ours(args, rank, world):
     run.close()
     if rank == 0 and not args.no_variants:
         line["variants"] = variants(args, f_host, flush)
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args, f_host)
+    pool = OraclePool() if rank == 0 and world == 1 and not (args.no_cpu_baseline and args.no_configs) else None
+    if pool is not None and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, f_host, pool)
+    if pool is not None and not args.no_configs:
+        # the patterns of the method, each against plain FP64 on the same inputs
+        t0 = time.perf_counter()
+        cfg = {}
+        cfg["precision"] = config_precision(args, flush, pool)
+        cfg["batching"] = config_batching(args, flush, pool)
+        cfg["serving"] = config_serving(args)
+        cfg["seconds"] = time.perf_counter() - t0
+        line["configs"] = cfg
+    if pool is not None:
+        pool.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -558,6 +650,244 @@ def _timed(fn, stream_sync=True):
     return a.elapsed_time(b), (time.perf_counter() - t0) * 1e3, out
 
 
+# ------------------------------------------------------------------ pattern workloads
+# The three patterns on top of the plain method, each against the plain FP64 GPU
+# method on the same inputs at the same 1e-10 residual.  The default run puts all
+# three under "configs" in its JSON line; --config precision|batching|serving
+# prints each as its own line.  Errors against the oracle come from the CPU leg
+# (`pool`, the oracle on the host cores).
+
+def _solve_timed(d, f, p, flush, steps, warmup=1):
+    """Device-timed solves of one domain: L2 flushed before each, the first `warmup` untimed."""
+    times, infos = [], []
+    for s in range(warmup + steps):
+        flush.fill_(float(s))
+        d.set_rhs(f)
+        ms, _, (stt, info) = _timed(lambda: d.solve(p, check=False))
+        if s >= warmup:
+            times.append(ms)
+            infos += info
+    return sum(times) / len(times), infos
+
+
+def _form_summary(ms, nsolve, infos, B):
+    import numpy as np
+    return {"solves_per_s": nsolve * 1e3 / ms, "ms_per_step": ms,
+            "iterations_mean": float(np.mean([i["iterations"] for i in infos])),
+            "residual_max": max(i["residual"] for i in infos),
+            "all_converged": all(i["status"] == B.FPG_OK for i in infos)}
+
+
+def config_precision(args, flush, pool):
+    """The precision workload: cross 1024^2 per block (5,246,976 unknowns),
+    kappa 0, one fourier RHS (seed 0), FP32 DST/Thomas inside FP64 FGMRES(40)
+    against the plain FP64 path, both at rtol 1e-10, each solution's error
+    against the oracle's direct solve."""
+    import torch
+    import workloads as W
+    from paper_2509_23180_gb300 import binding as B
+    n, m, kappa = 1024, 40, 0.0
+    f = W.rhs_batch("cross", n, [0], kind="fourier")
+    fd = torch.as_tensor(f, device="cuda")
+    forms, sols = {}, {}
+    for name, prec in (("fp32_precond", 32), ("fp64_plain", 64)):
+        st = torch.cuda.Stream()
+        d = B.Domain(B.make_desc("cross", n, kappa, nrhs=1, restart=m, rtol=args.rtol, precond_precision=prec),
+                     stream=st)
+        p = torch.zeros_like(fd)
+        ms, infos = _solve_timed(d, fd, p, flush, steps=max(1, min(args.steps, 3)))
+        forms[name] = _form_summary(ms, 1, infos, B)
+        sols[name] = p.cpu().numpy()[0]
+        d.close()
+        del p
+    dt, (R,) = pool.run([("cross", n, kappa, f)])
+    for name in forms:
+        forms[name]["error_vs_oracle"] = error_stats(sols[name], R[0], "cross", n)
+    return {"workload": f"cross {n}^2 per block ({W.total_unknowns('cross', n)} unknowns), kappa 0, 1 fourier RHS "
+                        f"(seed 0), FGMRES({m}), rtol {args.rtol:g}; L2 flushed before every solve",
+            "forms": forms, "fp32_precond_over_fp64_plain": forms["fp32_precond"]["solves_per_s"] /
+            forms["fp64_plain"]["solves_per_s"],
+            "oracle": {"what": "SuperLU direct solve of K (grid assembly), the same RHS", "seconds": dt}}
+
+
+def config_batching(args, flush, pool):
+    """The batching workload.  (i) 64 RHS in one domain on the 512^2 cross
+    (kappa 0, FGMRES(40)), FP32 preconditioner against plain FP64; the oracle
+    checks two of the 64 solutions of each form.  (ii) a mixed batch of L, T and
+    cross instances (n drawn from {128, 256, 512, 1024}, kappa 0 / -10, 2 RHS
+    each, per-instance seeds) through fpg_solve_many: FP32 preconditioner with
+    the launch shapes fpg_autotune picks for each domain, against plain FP64
+    with the built-in shapes; the oracle checks the instances with n <= 512."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2509_23180_gb300 import binding as B
+    out = {}
+    n, m, nr = 512, 40, 64
+    f = torch.stack([W.fourier_rhs_torch("cross", n, s) for s in range(nr)])
+    f_check = f[:2].cpu().numpy()
+    forms, sols = {}, {}
+    for name, prec in (("fp32_precond", 32), ("fp64_plain", 64)):
+        d = B.Domain(B.make_desc("cross", n, 0.0, nrhs=nr, restart=m, rtol=args.rtol, precond_precision=prec))
+        p = torch.zeros_like(f)
+        ms, infos = _solve_timed(d, f, p, flush, steps=max(1, min(args.steps, 2)))
+        forms[name] = _form_summary(ms, nr, infos, B)
+        sols[name] = p[:2].cpu().numpy()
+        d.close()
+        del p
+    del f
+    torch.cuda.empty_cache()
+    dt, (R,) = pool.run([("cross", n, 0.0, f_check)])
+    for name in forms:
+        forms[name]["error_vs_oracle"] = {f"rhs {r}": error_stats(sols[name][r], R[r], "cross", n) for r in range(2)}
+    out["rhs64_512"] = {"workload": f"cross {n}^2 per block, {nr} fourier RHS (seeds 0..{nr - 1}) in one domain, "
+                                    f"kappa 0, FGMRES({m}), rtol {args.rtol:g}",
+                        "forms": forms, "fp32_precond_over_fp64_plain": forms["fp32_precond"]["solves_per_s"] /
+                        forms["fp64_plain"]["solves_per_s"], "oracle_seconds": dt}
+    # (ii) the mixed batch
+    rng = np.random.default_rng(3)
+    inst = []
+    for i, geom in enumerate(["L", "T", "cross"] * 4):
+        inst.append((geom, int(rng.choice([128, 256, 512, 1024])), (0.0, -10.0)[i % 2], 2))
+    fs = [torch.stack([W.fourier_rhs_torch(g, nn, 1000 + 10 * i + r) for r in range(nr_)])
+          for i, (g, nn, _, nr_) in enumerate(inst)]
+    forms, sols, tuned = {}, {}, []
+    for name, prec, tune in (("fp32_precond_autotuned", 32, True), ("fp64_plain", 64, False)):
+        doms, ps = [], []
+        for (geom, nn, kappa, nr_), ff in zip(inst, fs):
+            st = torch.cuda.Stream()
+            dd = B.Domain(B.make_desc(geom, nn, kappa, nrhs=nr_, restart=m, rtol=args.rtol, precond_precision=prec),
+                          stream=st)
+            if tune:
+                tuned.append(dd.autotune())
+            torch.cuda.synchronize()
+            doms.append(dd)
+            ps.append(torch.zeros_like(ff))
+        times, infos = [], []
+        for rep in range(1 + max(1, min(args.steps, 2))):
+            for dd, ff in zip(doms, fs):
+                dd.set_rhs(ff)
+            torch.cuda.synchronize()
+            flush.fill_(float(rep))
+            ms, _, (stt, inf) = _timed(lambda: B.solve_many(doms, ps))
+            if rep >= 1:
+                times.append(ms)
+                infos += [i for x in inf for i in x]
+        ms = sum(times) / len(times)
+        forms[name] = _form_summary(ms, sum(x[3] for x in inst), infos, B)
+        sols[name] = [p.cpu().numpy() for p in ps]
+        for dd in doms:
+            dd.close()
+    check = [i for i, x in enumerate(inst) if x[1] <= 512]
+    tasks = [(inst[i][0], inst[i][1], inst[i][2], fs[i].cpu().numpy()) for i in check]
+    dt, Rs = pool.run(tasks)
+    for name in forms:
+        worst = {"rel_2norm": 0.0, "maxabs_rel": 0.0}
+        for i, R in zip(check, Rs):
+            for r in range(R.shape[0]):
+                e = error_stats(sols[name][i][r], R[r], inst[i][0], inst[i][1])
+                worst = {k: max(worst[k], e[k]) for k in worst}
+        forms[name]["error_vs_oracle"] = dict(worst, instances_checked=[f"{inst[i][0]}{inst[i][1]}" for i in check])
+    out["mixed"] = {"workload": "mixed batch via fpg_solve_many: " +
+                                ", ".join(f"{g}{nn}k{int(k)}x{r}" for g, nn, k, r in inst) +
+                                f"; FGMRES({m}), rtol {args.rtol:g}",
+                    "forms": forms, "autotuned_shapes": tuned,
+                    "fp32_autotuned_over_fp64_plain": forms["fp32_precond_autotuned"]["solves_per_s"] /
+                    forms["fp64_plain"]["solves_per_s"], "oracle_seconds": dt}
+    return out
+
+
+def serve_plain(requests, restart, rtol, precond_precision, budget_bytes, slot_rhs=8):
+    """The baseline of the serving comparison: the plain method, one request at a
+    time in arrival order (a request waits until the previous one is solved), on
+    a resident domain of its (geometry, n, kappa) with `slot_rhs` slots (unused
+    slots carry a zero RHS), least recently used domains evicted to stay in the
+    budget.  Returns serve.Result objects in request order."""
+    from collections import OrderedDict
+
+    import torch
+    import workloads as W
+    from paper_2509_23180_gb300 import binding as B
+    from paper_2509_23180_gb300.serve import Result
+    doms, used = OrderedDict(), 0
+    order = sorted(range(len(requests)), key=lambda i: float(requests[i]["arrival_s"]))
+    out = {}
+    t0 = time.perf_counter()
+    for i in order:
+        r = requests[i]
+        delay = float(r["arrival_s"]) - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        start = time.perf_counter() - t0
+        geom, n, kappa, nr = r["geometry"], int(r["n"]), float(r["kappa"]), int(r["nrhs"])
+        key = (geom, n, kappa)
+        if key not in doms:
+            desc = B.make_desc(geom, n, kappa, nrhs=slot_rhs, restart=restart, rtol=rtol,
+                               precond_precision=precond_precision)
+            need = B.workspace_bytes(desc) + 16 * slot_rhs * B.unknowns(desc)
+            while doms and used + need > budget_bytes:
+                _, (dd, nb) = doms.popitem(last=False)
+                dd.close()
+                used -= nb
+            doms[key] = (B.Domain(desc), need)
+            used += need
+        doms.move_to_end(key)
+        d = doms[key][0]
+        f = torch.zeros((slot_rhs, B.unknowns(d.desc)), dtype=torch.float64, device="cuda")
+        for j in range(nr):
+            f[j] = W.fourier_rhs_torch(geom, n, int(r["seed"]) * 16 + j)
+        p = torch.zeros_like(f)
+        d.set_rhs(f)
+        st, info = d.solve(p, check=False)
+        end = time.perf_counter() - t0
+        out[int(r["id"])] = Result(id=int(r["id"]), arrival_s=float(r["arrival_s"]), start_s=start, end_s=end,
+                                   nrhs=nr, iterations=[x["iterations"] for x in info[:nr]],
+                                   residuals=[x["residual"] for x in info[:nr]],
+                                   status=max(x["status"] for x in info[:nr]), key=key)
+    wall = time.perf_counter() - t0
+    for dd, _ in doms.values():
+        dd.close()
+    return [out[int(r["id"])] for r in requests], wall
+
+
+def config_serving(args):
+    """The serving workload: `args.requests` Poisson requests at `args.rate`/s
+    (L/T/cross, n in 64..1024, 1-8 RHS, kappa 0/-10, seeded RHS) through the
+    library's batch runtime (continuous batching, FP32 preconditioner, 120 GB
+    admission budget); and, on the first `args.serving_prefix` requests of the
+    same stream, the batch runtime against the plain FP64 method serving one
+    request at a time."""
+    import workloads as W
+    from paper_2509_23180_gb300 import serve
+    reqs = W.serving_requests(args.requests, args.rate, seed=0)
+    budget = args.budget_gb * 1e9
+
+    def native(rs):
+        t0 = time.perf_counter()
+        res, st = serve.serve_native(rs, pool_bytes=budget, slot_rhs=8, restart=40, rtol=args.rtol,
+                                     precond_precision=32)
+        return res, time.perf_counter() - t0, st
+
+    res, wall, st = native(reqs)
+    full = serve.summarize(res, wall)
+    full.pop("failures", None) if full["all_converged"] else None
+    full.update({"domains_created": st["created"], "domains_evicted": st["evicted"]})
+    pre = reqs[:min(args.serving_prefix, len(reqs))]
+    res_b, wall_b, _ = native(pre)
+    res_p, wall_p = serve_plain(pre, restart=40, rtol=args.rtol, precond_precision=64, budget_bytes=budget)
+    sb, sp = serve.summarize(res_b, wall_b), serve.summarize(res_p, wall_p)
+    for x in (sb, sp):
+        if x["all_converged"]:
+            x.pop("failures", None)
+    return {"workload": f"serving: {len(reqs)} Poisson requests at {args.rate:g}/s, geometry L/T/cross, "
+                        f"n 64..1024, 1-8 RHS, kappa 0/-10; batch runtime (fpg_batch_*), FP32 preconditioner, "
+                        f"FGMRES(40), rtol {args.rtol:g}, {args.budget_gb:g} GB budget",
+            "served": full,
+            "prefix_comparison": {"requests": len(pre), "served_fp32_batched": sb,
+                                  "plain_fp64_one_at_a_time": sp,
+                                  "served_over_plain": sb["solves_per_s"] / sp["solves_per_s"]}}
+
+
 def run_extra(args):
     """Extra lines for the other workloads; each line carries its own config."""
     import numpy as np
@@ -571,41 +901,31 @@ def run_extra(args):
     B.load()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     lines = []
-    if args.config in ("small", "precision"):
-        # small: the manufactured 64^2 cross, m = 30; precision: 1024^2 cross, kappa 0,
-        # FP32 fast solve inside FP64 FGMRES(40) against the plain FP64 path
-        if args.config == "small":
-            n, m, kinds = 64, 30, [("fp64", 64)]
-            f = W.manufactured_rhs("cross", n, 0.0)[None, :]
-        else:
-            n, m, kinds = 1024, 40, [("fp32_precond", 32), ("fp64_plain", 64)]
-            f = W.rhs_batch("cross", n, [0], kind="fourier")
+    if args.config == "precision":
+        pool = OraclePool(1)
+        r = config_precision(args, flush, pool)
+        pool.close()
+        f32 = r["forms"]["fp32_precond"]
+        lines.append({"metric": METRIC, "value": f32["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": 1, "ms_per_step": f32["ms_per_step"], "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32precond", "data": "synthetic",
+                      "config": {"workload": r["workload"]}, **r})
+    elif args.config == "small":
+        # the manufactured 64^2 cross, m = 30
+        n, m = 64, 30
+        f = W.manufactured_rhs("cross", n, 0.0)[None, :]
         fd = torch.as_tensor(f, device="cuda")
-        for name, prec in kinds:
-            st = torch.cuda.Stream()
-            d = B.Domain(B.make_desc("cross", n, 0.0, nrhs=1, restart=m, rtol=args.rtol, precond_precision=prec),
-                         stream=st)
-            p = torch.zeros_like(fd)
-            times, infos = [], []
-            for s in range(args.warmup + args.steps):
-                flush.fill_(float(s))
-                d.set_rhs(fd)
-                ms, _, (stt, info) = _timed(lambda: d.solve(p, check=False))
-                if s >= args.warmup:
-                    times.append(ms)
-                    infos += info
-            ms = sum(times) / len(times)
-            line = {"metric": METRIC, "value": 1e3 / ms, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
-                    "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                    "vs_baseline": None, "dtype": "f64+f32precond" if prec == 32 else "f64", "data": "synthetic",
-                    "config": {"workload": f"cross {n}^2 per block, kappa 0, 1 RHS ({name})", "n": n, "restart": m,
-                               "rtol": args.rtol, "l2": "flushed before every solve"},
-                    "iterations": infos[0]["iterations"], "residual": max(i["residual"] for i in infos),
-                    "solution_checksum": float(p.abs().sum())}
-            if name == "fp64_plain" and lines:
-                lines[-1]["vs_plain_fp64"] = lines[-1]["value"] / line["value"]
-            lines.append(line)
-            d.close()
+        st = torch.cuda.Stream()
+        d = B.Domain(B.make_desc("cross", n, 0.0, nrhs=1, restart=m, rtol=args.rtol), stream=st)
+        p = torch.zeros_like(fd)
+        ms, infos = _solve_timed(d, fd, p, flush, steps=args.steps, warmup=args.warmup)
+        d.close()
+        lines.append({"metric": METRIC, "value": 1e3 / ms, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": f"cross {n}^2 per block, kappa 0, manufactured RHS, 1 RHS", "n": n,
+                                 "restart": m, "rtol": args.rtol, "l2": "flushed before every solve"},
+                      "iterations": infos[0]["iterations"], "residual": max(i["residual"] for i in infos)})
     elif args.config == "neumann":
         # Sec. 2.2: the DCT-II fast solve of Neumann-sided blocks, nvec = 2 * seeds
         # blocks of n x n per call (default 20 x 256^2), FP64 throughout:
@@ -886,64 +1206,15 @@ def run_extra(args):
                       "solve_ms_exponent_n_ge_128": t_fit, "residual_histories": histories,
                       "m_sweep": msweep, "best_m": best_m})
     elif args.config == "batching":
-        # (i) 64 RHS in one domain on the 512^2 cross, FP32 fast solve, FP64 FGMRES(40)
-        n, m, nr = 512, 40, 64
-        f = torch.stack([W.fourier_rhs_torch("cross", n, s) for s in range(nr)])
-        for prec in (32, 64):
-            d = B.Domain(B.make_desc("cross", n, 0.0, nrhs=nr, restart=m, rtol=args.rtol, precond_precision=prec))
-            p = torch.zeros_like(f)
-            times, infos = [], []
-            for s in range(1 + max(1, args.steps // 2)):
-                flush.fill_(float(s))
-                d.set_rhs(f)
-                ms, _, (stt, info) = _timed(lambda: d.solve(p, check=False))
-                if s >= 1:
-                    times.append(ms)
-                    infos += info
-            ms = sum(times) / len(times)
-            lines.append({"metric": METRIC, "value": nr * 1e3 / ms, "unit": "solves/s", "n_gpus": 1,
-                          "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                          "dtype": "f64+f32precond" if prec == 32 else "f64", "data": "synthetic",
-                          "config": {"workload": f"cross 512^2 per block, {nr} RHS in one launch sequence",
-                                     "precond_precision": prec, "restart": m, "rtol": args.rtol},
-                          "iterations_mean": float(np.mean([i["iterations"] for i in infos])),
-                          "residual_max": max(i["residual"] for i in infos),
-                          "all_converged": all(i["status"] == 0 for i in infos)})
-            d.close()
-            del p
-        del f
-        torch.cuda.empty_cache()
-        # (ii) mixed batch: L, T and cross, n in {128, 256, 512, 1024}, per-instance seeds, fpg_solve_many
-        rng = np.random.default_rng(3)
-        inst = []
-        for i, geom in enumerate(["L", "T", "cross"] * 4):
-            nn = int(rng.choice([128, 256, 512, 1024]))
-            inst.append((geom, nn, (0.0, -10.0)[i % 2], 2))
-        doms, ps, fs = [], [], []
-        for i, (geom, nn, kappa, nr) in enumerate(inst):
-            st = torch.cuda.Stream()
-            dd = B.Domain(B.make_desc(geom, nn, kappa, nrhs=nr, restart=m, rtol=args.rtol, precond_precision=32),
-                          stream=st)
-            ff = torch.stack([W.fourier_rhs_torch(geom, nn, 1000 + 10 * i + r) for r in range(nr)])
-            torch.cuda.synchronize()
-            dd.set_rhs(ff)
-            doms.append(dd); fs.append(ff); ps.append(torch.zeros_like(ff))
-        for rep in range(2):
-            for dd, ff in zip(doms, fs):
-                dd.set_rhs(ff)
-            flush.fill_(float(rep))
-            ms, wall, (stt, infos) = _timed(lambda: B.solve_many(doms, ps))
-        solves = sum(x[3] for x in inst)
-        lines.append({"metric": METRIC, "value": solves * 1e3 / ms, "unit": "solves/s", "n_gpus": 1,
-                      "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "dtype": "f64+f32precond",
-                      "data": "synthetic",
-                      "config": {"workload": "mixed batch via fpg_solve_many: " +
-                                 ", ".join(f"{g}{nn}k{int(k)}" for g, nn, k, _ in inst),
-                                 "restart": m, "rtol": args.rtol},
-                      "residual_max": max(i["residual"] for inf in infos for i in inf),
-                      "all_converged": stt == B.FPG_OK})
-        for dd in doms:
-            dd.close()
+        pool = OraclePool()
+        r = config_batching(args, flush, pool)
+        pool.close()
+        for key, part in r.items():
+            best = max(part["forms"].values(), key=lambda x: x["solves_per_s"])
+            lines.append({"metric": METRIC, "value": best["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+                          "ms_per_step": best["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                          "dtype": "f64+f32precond", "data": "synthetic",
+                          "config": {"workload": part["workload"], "part": key}, **part})
     elif args.config == "fastsolve":
         # a1 on its own: the preconditioner applied to a batch of centre vectors
         # that does not fit in L2 (default 64 x 512^2: 128 MB in, 64 MB out in FP32)
@@ -990,36 +1261,11 @@ def run_extra(args):
                       "peak_gbs": hbm})
         d.close()
     elif args.config == "serving":
-        from paper_2509_23180_gb300 import serve
-        reqs = W.serving_requests(args.requests, args.rate, seed=0)
-        extra = {}
-        if args.server == "native":
-            t0 = time.perf_counter()
-            res, st = serve.serve_native(reqs, pool_bytes=args.budget_gb * 1e9, slot_rhs=8, restart=40,
-                                         rtol=args.rtol, precond_precision=32)
-            wall = time.perf_counter() - t0
-            extra = {"server": "fpg_batch runtime, one host thread", "domains_created": st["created"],
-                     "domains_evicted": st["evicted"]}
-        else:
-            srv = serve.Server(budget_bytes=args.budget_gb * 1e9, max_inflight=8, slot_rhs=8, restart=40,
-                               rtol=args.rtol, precond_precision=32)
-            t0 = time.perf_counter()
-            res = srv.serve(reqs, realtime=True)
-            wall = time.perf_counter() - t0
-            extra = {"server": "threaded Python server, 8 workers", "requests_coalesced": srv.coalesced,
-                     "domains_created": srv.created, "domains_evicted": srv.evicted,
-                     "peak_gb": srv.peak_bytes / 1e9}
-            srv.close()
-        summ = serve.summarize(res, wall)
-        lines.append({"metric": METRIC, "value": summ["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+        r = config_serving(args)
+        lines.append({"metric": METRIC, "value": r["served"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
                       "higher_is_better": True, "scaling": "weak", "dtype": "f64+f32precond", "data": "synthetic",
-                      "config": {"workload": f"serving: {args.requests} Poisson requests at {args.rate}/s, "
-                                             "geometry L/T/cross, n 64..1024, 1-8 RHS, kappa 0/-10",
-                                 "budget_gb": args.budget_gb, "restart": 40, "rtol": args.rtol,
-                                 "server": args.server},
-                      "latency_ms": summ["latency_ms"], "requests": summ["requests"], "solves": summ["solves"],
-                      "wall_s": wall, "residual_max": summ["residual_max"], "all_converged": summ["all_converged"],
-                      "failures": summ["failures"], **extra})
+                      "config": {"workload": r["workload"], "budget_gb": args.budget_gb},
+                      "latency_ms": r["served"]["latency_ms"], **r})
     for line in lines:
         print(json.dumps(line), flush=True)
 

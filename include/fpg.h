@@ -52,7 +52,8 @@
  * return host results synchronise that stream.
  *
  * Errors: every call returns an fpg_status; no C++ exception crosses the ABI.
- * Device waits are bounded: a wait that gives up sets FPG_ETIMEOUT.
+ * Device waits are bounded (FPG_OPT_WAIT_LIMIT): a wait that gives up makes the
+ * solve return FPG_ETIMEOUT, and the stream and context stay usable.
  */
 #ifndef FPG_H
 #define FPG_H
@@ -294,9 +295,9 @@ fpg_status fpg_apply_global(fpg_domain* d, const double* p_dev, double* y_dev, i
  * Its scratch (spectral coefficients and the DST / Thomas tables) is one
  * file-scope device array of about 20 MiB that every GPU loading the library
  * holds until the process exits; no device or host memory is allocated.
- *   - Limits: 2 <= n <= FPG_NOALLOC_MAX_N, nvec * n * n <= FPG_NOALLOC_MAX_POINTS,
- *     kappa <= 0.  Anything beyond returns FPG_EINVAL, the reason readable
- *     from fpg_last_cuda_error().
+ *   - Limits: 2 <= n <= FPG_NOALLOC_MAX_N, 1 <= nvec <= FPG_NOALLOC_MAX_NVEC,
+ *     nvec * n * n <= FPG_NOALLOC_MAX_POINTS, kappa <= 0.  Anything beyond
+ *     returns FPG_EINVAL, the reason readable from fpg_last_cuda_error().
  *   - The first call on a device performs that device's set-up (it looks up
  *     the array's device address); make that first call before any stream
  *     capture.  A call whose (n, kappa) differs from the previous call's
@@ -307,6 +308,7 @@ fpg_status fpg_apply_global(fpg_domain* d, const double* p_dev, double* y_dev, i
  * v_dev, z_dev: device pointers owned by the caller; stream: a cudaStream_t. */
 #define FPG_NOALLOC_MAX_N 512
 #define FPG_NOALLOC_MAX_POINTS (1LL << 21)
+#define FPG_NOALLOC_MAX_NVEC 4096
 fpg_status fpg_fast_solve_noalloc(int32_t n, double kappa, const double* v_dev, double* z_dev,
                                   int32_t nvec, void* stream);
 
@@ -369,7 +371,22 @@ typedef enum {
    * kernel that fetches the next line tile with a bulk asynchronous copy
    * (cp.async.bulk on an mbarrier) while it transforms the current one (blocks
    * with contiguous, 16-byte aligned rows); 0 (default): one CTA per tile. */
-  FPG_OPT_DST_BULK = 10
+  FPG_OPT_DST_BULK = 10,
+  /* Tries of every bounded device wait (default 2^22, each try a
+   * hardware-suspended mbarrier test; 0: give up at once).  A wait that runs
+   * out records it in the domain's status word, the kernel that waited lets its
+   * copy in flight land and returns, and the solve reports FPG_ETIMEOUT for
+   * every right-hand side.  The one wait of this kind today is the bulk-copy
+   * wait of FPG_OPT_DST_BULK's persistent kernel. */
+  FPG_OPT_WAIT_LIMIT = 11,
+  /* 1: the FP32 preconditioner (a1 with precond_precision = 32) of centre
+   * blocks with n = 64 or 512 runs as one kernel per batch: one thread-block
+   * cluster per block (n / 32 CTAs of 32 lines each), the block's spectral
+   * coefficients kept in the cluster's shared memory, the tridiagonal sweeps
+   * carried across the CTAs through distributed shared memory, v read once
+   * and z written once.  0: the three-kernel path.  Other lengths, FP64 and
+   * blocks that are not 16-byte aligned always take the other paths. */
+  FPG_OPT_CLUSTER_FASTSOLVE = 12
 } fpg_option;
 
 /* Move a domain to another CUDA stream (a cudaStream_t; NULL = the default

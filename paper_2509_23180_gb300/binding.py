@@ -31,6 +31,8 @@ OPT_DST_ENGINE = 7
 OPT_SCHUR_TRANSFORM = 8
 OPT_ARM_REFINE = 9
 OPT_DST_BULK = 10
+OPT_WAIT_LIMIT = 11
+OPT_CLUSTER_FASTSOLVE = 12
 PRECOND = {"fft": 0, "none": 1, "jacobi": 2}
 PHASES = ("precond", "schur", "arnoldi", "givens", "cycle_end", "setup_finish", "residual",
           "dst_forward", "thomas", "dst_inverse", "fast_solve_fused")
@@ -41,6 +43,7 @@ FAST_SOLVE_KERNELS = {
     2: {"dst_forward": "k_dense_forward", "thomas": "k_thomas_reg", "dst_inverse": "k_dense_inverse"},
     3: {"fast_solve_fused": "k_fast_solve_fused"},
     4: {},
+    7: {"fast_solve_fused": "k_fast_solve_cluster"},
 }
 
 

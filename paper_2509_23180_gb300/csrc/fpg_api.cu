@@ -19,6 +19,8 @@ cudaError_t launch_fast_solve(int prec, int out_prec, const FastSolveTables& tb,
                               BatchDesc ib, void* out, BatchDesc ob, int nblk, void* scratch, const int* active,
                               int nper_active, cudaStream_t st, int* launches, cudaEvent_t* ev = nullptr);
 bool schur_dst_supported(int n);
+bool fast_solve_cluster_tables(int n, double delta, double kappa, std::vector<float>& sigma,
+                               std::vector<float>& wseed);
 cudaError_t launch_schur_dst(const void* z, int zprec, long long zstride, int n, const DstPlan& pl, const double* gsc,
                              const int* arms, int narms, double* corr, const int* active, int nrhs, cudaStream_t st);
 cudaError_t launch_schur_reduced(const void* z, int zprec, long long zstride, int n, const double* ctab,
@@ -252,6 +254,7 @@ struct fpg_domain {
   double* f_orig = nullptr;       // the caller's RHS while a refinement solve runs on rbuf
   bool refining = false;
   int* resume_dev = nullptr;
+  int* err_dev = nullptr;   // status word of the bounded device waits (1: a wait gave up)
   void* scratch;
   KrylovState ks;
   int gx, gxf;
@@ -417,6 +420,7 @@ void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostP
   p = c.take(sizeof(double) * sc);            if (D) D->scratch = p;
   p = c.take(sizeof(double) * nrhs);          if (D) D->gres = (double*)p;
   p = c.take(sizeof(int) * 4);                if (D) D->resume_dev = (int*)p;
+  p = c.take(sizeof(int) * 4);                if (D) D->err_dev = (int*)p;
   KrylovState* k = D ? &D->ks : nullptr;
   p = c.take(sizeof(double) * (size_t)(m + 1) * nrhs * L.nc); if (k) k->V = (double*)p;
   p = c.take(zel * (size_t)m * nrhs * L.nc);                  if (k) k->Z = p;
@@ -437,6 +441,12 @@ void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostP
   p = c.take(sizeof(int) * nrhs);             if (k) k->done = (int*)p;
   p = c.take(sizeof(int) * nrhs);             if (k) k->kcyc = (int*)p;
   p = c.take(sizeof(int) * nrhs);             if (k) k->iters = (int*)p;
+  // the one-pass FP32 cluster fast solve of the centre: sigma_k and the pivot at each strip start
+  p = c.take(sizeof(float) * 17 * (size_t)n);
+  if (D) {
+    D->tC32.cl_sigma = p;
+    D->tC32.cl_wseed = (const float*)p + n;
+  }
 }
 
 // Phase timing helpers (only when profiling is on).  Events come from the
@@ -701,6 +711,7 @@ fpg_status check_launch() {
 fpg_status setup_common(fpg_domain* D, double* p, bool keep_iters);
 
 fpg_status stage_setup(fpg_domain* D, double* p) {
+  FPG_CUDA_TRY(cudaMemsetAsync(D->err_dev, 0, sizeof(int), D->st));
   D->cycles_run = 0;
   D->accept_rounds = 0;
   D->refining = false;
@@ -979,6 +990,7 @@ fpg_status stage_resume(fpg_domain* D, bool* resume) {
 fpg_status stage_setup_from(fpg_domain* D, double* p) {
   const Layout& L = D->L;
   const int nrhs = D->desc.nrhs;
+  FPG_CUDA_TRY(cudaMemsetAsync(D->err_dev, 0, sizeof(int), D->st));
   D->cycles_run = 0;
   D->accept_rounds = 0;
   D->refining = false;
@@ -1025,13 +1037,17 @@ fpg_status collect_info(fpg_domain* D, fpg_solve_info* info) {
   FPG_CUDA_TRY(cudaMemcpyAsync(rn.data(), k.rnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, D->st));
   FPG_CUDA_TRY(cudaMemcpyAsync(fn.data(), k.fnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, D->st));
   FPG_CUDA_TRY(cudaMemcpyAsync(iters.data(), k.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, D->st));
+  int waited_out = 0;
+  FPG_CUDA_TRY(cudaMemcpyAsync(&waited_out, D->err_dev, sizeof(int), cudaMemcpyDeviceToHost, D->st));
   FPG_CUDA_TRY(cudaStreamSynchronize(D->st));
   ev_collect(D);
-  fpg_status all = FPG_OK;
+  fpg_status all = waited_out ? FPG_ETIMEOUT : FPG_OK;
   for (int r = 0; r < nrhs; ++r) {
     const bool ok = gres[r] <= D->desc.rtol;
-    const fpg_status s = ok ? FPG_OK : FPG_ENOCONV;
-    if (s != FPG_OK) all = FPG_ENOCONV;
+    // a device wait that gave up left part of a fast solve undone: every
+    // right-hand side of the solve reports it, whatever its residual
+    const fpg_status s = waited_out ? FPG_ETIMEOUT : ok ? FPG_OK : FPG_ENOCONV;
+    if (s == FPG_ENOCONV && all == FPG_OK) all = FPG_ENOCONV;
     if (info) {
       info[r].iterations = iters[r];
       info[r].restarts = D->cycles_run;
@@ -1192,6 +1208,7 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   HostPlan hp = build_plan(n);
   Carver c(ws);
   carve(D, desc, L, &hp, c);
+  for (auto* t : {&D->tC64, &D->tC32, &D->tA64, &D->tA32, &D->tA64e, &D->tR64, &D->tR32}) t->err = D->err_dev;
   const int nrhs = desc->nrhs;
   D->gx = pick_gx(L.nc, nrhs);
   D->gxf = pick_gx(L.ntot, nrhs);
@@ -1203,6 +1220,7 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   D->h_done.assign(nrhs, 0);
   // host tables
   std::vector<double> pc, pa, ct, ma, pae, mae, Wd, postd;
+  std::vector<float> cl_sigma, cl_wseed;
   std::vector<double> gs(n, 0.0);
   fill_pivots(n, n, D->delta, desc->kappa, pc);
   if (!nside) {
@@ -1275,6 +1293,12 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
     if (!err) err = cp(D->tA64e.mneg, mae.data(), sizeof(double) * mae.size());
     if (!err) err = cp(D->tA64.plan.W, Wd.data(), sizeof(double) * Wd.size());
     if (!err) err = cp(D->tA64.post, postd.data(), sizeof(double) * postd.size());
+  }
+  if (!L.chain && fast_solve_cluster_tables(n, D->delta, desc->kappa, cl_sigma, cl_wseed)) {
+    if (!err) err = cp(D->tC32.cl_sigma, cl_sigma.data(), sizeof(float) * cl_sigma.size());
+    if (!err) err = cp(D->tC32.cl_wseed, cl_wseed.data(), sizeof(float) * cl_wseed.size());
+  } else {
+    D->tC32.cl_sigma = D->tC32.cl_wseed = nullptr;  // the kernel does not take this length
   }
   if (!err) err = cp(D->ctab, ct.data(), sizeof(double) * ct.size());
   if (!err) err = cp(D->gsc, gs.data(), sizeof(double) * gs.size());
@@ -1603,6 +1627,16 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
     case FPG_OPT_DST_BULK:
       if (value < 0 || value > 1) return FPG_EINVAL;
       for (auto* tt : {&d->tC64, &d->tC32, &d->tA64, &d->tA32, &d->tA64e}) tt->bulk = value;
+      drop_graph(d);
+      return FPG_OK;
+    case FPG_OPT_CLUSTER_FASTSOLVE:
+      if (value < 0 || value > 1) return FPG_EINVAL;
+      d->tC32.cluster = value;
+      drop_graph(d);
+      return FPG_OK;
+    case FPG_OPT_WAIT_LIMIT:
+      if (value < 0) return FPG_EINVAL;
+      for (auto* tt : {&d->tC64, &d->tC32, &d->tA64, &d->tA32, &d->tA64e, &d->tR64, &d->tR32}) tt->wait_limit = value;
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_ARM_REFINE:

@@ -253,11 +253,10 @@ cudaError_t launch_chain_schur(const void* z, int zprec, long long zstride, cons
   const int n = G.n;
   dim3 grid((n + 31) / 32, nrhs * (2 * G.K + 2));
   const size_t smem = sizeof(double) * (5 * n + 2 + 256);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static PerDeviceOnce attr_set;
+  if (attr_set.first()) {
     cudaFuncSetAttribute(k_chain_schur_lines<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_chain_schur_lines<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
   }
   if (zprec == 64)
     k_chain_schur_lines<double><<<grid, dim3(32, 8), smem, st>>>((const double*)z, zstride, G, ctab, corr, active);

@@ -5,19 +5,24 @@ namespace fpg {
 
 bool dst_lines_supported_f32(int p) { return p == 65 || p == 257 || p == 513 || p == 1025; }
 
-// Set by the persistent forward kernel when a bulk-copy wait runs out (its CTA
-// then stops; the solve that used it does not converge and reports so).
+// Status word of callers that pass none: set by the persistent forward kernel
+// when a bulk-copy wait runs out.  A domain passes its own word instead, and
+// its solve then returns FPG_ETIMEOUT.
 __device__ int g_dst_bulk_timeout_f32 = 0;
 
 cudaError_t dst_lines_fwd_bulk_f32(int p, const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl,
-                                   float* scratch, int nblk, const int* active, int nper_active, cudaStream_t st) {
-  int* err = nullptr;
-  cudaGetSymbolAddress((void**)&err, g_dst_bulk_timeout_f32);
+                                   float* scratch, int nblk, const int* active, int nper_active, int* err,
+                                   int wait_limit, cudaStream_t st) {
+  if (err == nullptr) {
+    cudaError_t e = cudaGetSymbolAddress((void**)&err, g_dst_bulk_timeout_f32);
+    if (e != cudaSuccess) return e;
+  }
   switch (p) {
-    case 65: return dl::fwd_bulk_one<float, 65>(in, ib, L, pl, scratch, nblk, active, nper_active, err, st);
-    case 257: return dl::fwd_bulk_one<float, 257>(in, ib, L, pl, scratch, nblk, active, nper_active, err, st);
-    case 513: return dl::fwd_bulk_one<float, 513>(in, ib, L, pl, scratch, nblk, active, nper_active, err, st);
-    case 1025: return dl::fwd_bulk_one<float, 1025>(in, ib, L, pl, scratch, nblk, active, nper_active, err, st);
+    case 65: return dl::fwd_bulk_one<float, 65>(in, ib, L, pl, scratch, nblk, active, nper_active, err, wait_limit, st);
+    case 257: return dl::fwd_bulk_one<float, 257>(in, ib, L, pl, scratch, nblk, active, nper_active, err, wait_limit, st);
+    case 513: return dl::fwd_bulk_one<float, 513>(in, ib, L, pl, scratch, nblk, active, nper_active, err, wait_limit, st);
+    case 1025:
+      return dl::fwd_bulk_one<float, 1025>(in, ib, L, pl, scratch, nblk, active, nper_active, err, wait_limit, st);
     default: return cudaErrorNotSupported;
   }
 }

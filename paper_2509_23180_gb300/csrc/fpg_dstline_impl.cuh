@@ -507,11 +507,16 @@ struct BulkShape {
 // block) blockIdx.x, blockIdx.x + gridDim.x, ...; thread 0 fetches the next
 // tile's FP64 rows with one bulk copy into a staging buffer as soon as the
 // current tile has been converted out of it, so the load overlaps the current
-// tile's transform.  A wait that runs out sets *err and ends the CTA.
+// tile's transform.  Thread 0 waits for each copy, at most `wait_limit` tries
+// (0: gives up at once), and tells the CTA through shared memory, so every
+// thread takes the same branch.  A wait that runs out sets *err = 1; thread 0
+// then waits (again bounded) for the copy in flight to land, and the whole CTA
+// returns: no trap, nothing left writing into freed shared memory.
 template <typename T, int P>
 __global__ void __launch_bounds__(LineShape<T, P>::NT)
 k_dst_lines_fwd_bulk(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPlan pl, T* __restrict__ scratch,
-                     const int* __restrict__ active, int nper_active, int nblk, int* __restrict__ err) {
+                     const int* __restrict__ active, int nper_active, int nblk, int* __restrict__ err,
+                     int wait_limit) {
   using S = LineShape<T, P>;
   using BS = BulkShape<T, P>;
   constexpr int n = S::n, Q = S::Q, NT = S::NT, LP = S::LP;
@@ -519,6 +524,7 @@ k_dst_lines_fwd_bulk(const double* __restrict__ in, BatchDesc ib, LineLayout L, 
   LineSmem<T, P> s(smem_raw);
   double* stage = reinterpret_cast<double*>(smem_raw + BS::o_stage);
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem_raw + BS::o_mbar);
+  __shared__ int s_landed;
   const int tpb = (L.ns + 2 * Q - 1) / (2 * Q);
   const int total = nblk * tpb;
   auto live = [&](int tile) { return active == nullptr || active[(tile / tpb) / nper_active]; };
@@ -542,11 +548,16 @@ k_dst_lines_fwd_bulk(const double* __restrict__ in, BatchDesc ib, LineLayout L, 
   while (tile < total) {
     const int b = tile / tpb, s0 = (tile - b * tpb) * 2 * Q;
     const int nl = min(2 * Q, L.ns - s0);
-    if (!mbar_wait(mbar, parity, 1 << 22)) {
-      if (threadIdx.x == 0) atomicExch(err, 1);
-      mbar_wait(mbar, parity, 1 << 20);  // give the copy in flight a last chance to land
+    if (threadIdx.x == 0) s_landed = mbar_wait(mbar, parity, wait_limit) ? 1 : 0;
+    __syncthreads();
+    if (!s_landed) {  // the same value in every thread
+      if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        mbar_wait(mbar, parity, 1 << 20);  // the copy in flight lands before the CTA leaves
+      }
       return;
     }
+    mbar_wait(mbar, parity, 1 << 22);  // phase complete: returns at once, and orders the copied data
     parity ^= 1u;
     for (int i = threadIdx.x; i < 2 * Q * n; i += NT) {
       const int l = i / n, tt = i - l * n;
@@ -617,10 +628,9 @@ template <typename T, int P>
 cudaError_t fwd_one(const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl, T* scratch, int nblk,
                     const int* active, int nper_active, int vec, cudaStream_t st) {
   using S = LineShape<T, P>;
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  if (attr.first()) {
     cudaFuncSetAttribute(k_dst_lines_fwd<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
-    attr = true;
   }
   dim3 grid((L.ns + 2 * S::Q - 1) / (2 * S::Q), nblk);
   k_dst_lines_fwd<T, P><<<grid, S::NT, S::bytes, st>>>(in, ib, L, pl, scratch, active, nper_active, vec);
@@ -629,22 +639,26 @@ cudaError_t fwd_one(const double* in, BatchDesc ib, LineLayout L, const DstPlan&
 
 template <typename T, int P>
 cudaError_t fwd_bulk_one(const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl, T* scratch, int nblk,
-                         const int* active, int nper_active, int* err, cudaStream_t st) {
+                         const int* active, int nper_active, int* err, int wait_limit, cudaStream_t st) {
   using S = LineShape<T, P>;
   using BS = BulkShape<T, P>;
-  static int per_sm = 0;
-  if (per_sm == 0) {
+  static PerDeviceOnce attr;
+  static int per_sm_of[64] = {};
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  int per_sm = (dev >= 0 && dev < 64) ? per_sm_of[dev] : 0;
+  if (attr.first() || per_sm == 0) {
     cudaFuncSetAttribute(k_dst_lines_fwd_bulk<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BS::bytes);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dst_lines_fwd_bulk<T, P>, S::NT, BS::bytes);
     if (per_sm < 1) per_sm = 1;
+    if (dev >= 0 && dev < 64) per_sm_of[dev] = per_sm;
   }
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int tpb = (L.ns + 2 * S::Q - 1) / (2 * S::Q);
   const long long total = (long long)nblk * tpb;
   const int grid = (int)(total < (long long)per_sm * sms ? total : (long long)per_sm * sms);
-  k_dst_lines_fwd_bulk<T, P><<<grid, S::NT, BS::bytes, st>>>(in, ib, L, pl, scratch, active, nper_active, nblk, err);
+  k_dst_lines_fwd_bulk<T, P><<<grid, S::NT, BS::bytes, st>>>(in, ib, L, pl, scratch, active, nper_active, nblk, err,
+                                                              wait_limit);
   return cudaGetLastError();
 }
 
@@ -652,10 +666,9 @@ template <typename T, typename To, int P>
 cudaError_t inv_one(const T* scratch, To* out, BatchDesc ob, LineLayout L, const DstPlan& pl, int nblk,
                     const int* active, int nper_active, int vec, cudaStream_t st) {
   using S = LineShape<T, P>;
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  if (attr.first()) {
     cudaFuncSetAttribute(k_dst_lines_inv<T, To, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
-    attr = true;
   }
   // 2/p for the normalisation, 1/4 for the two left-out factors 1/2 (exact)
   const T scale = (T(2) / T(P)) * T(0.25);

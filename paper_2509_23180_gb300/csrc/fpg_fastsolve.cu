@@ -394,10 +394,9 @@ cudaError_t launch_thomas(T* scratch, int n, int ns, const T* rpiv, const T* mne
   const int need = (ns + 31) / 32;
 #define FPG_THOMAS_C(CV)                                                                                    \
   if (need <= CV) {                                                                                         \
-    static bool attr = false;                                                                               \
-    if (!attr) {                                                                                            \
+    static PerDeviceOnce attr;                                                                               \
+    if (attr.first()) {                                                                                            \
       cudaFuncSetAttribute(k_thomas_reg<T, CV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);   \
-      attr = true;                                                                                          \
     }                                                                                                       \
     const size_t per = sizeof(T) * 2 * 32 * thomas_pitch<CV>();                                             \
     int w = wpb;                                                                                            \
@@ -425,10 +424,9 @@ cudaError_t launch_thomas(T* scratch, int n, int ns, const T* rpiv, const T* mne
   const size_t per = sizeof(T) * 3 * (size_t)ns;
   const int wl = (int)std::min<size_t>(8, (size_t)(200 * 1024) / per);
   if (wl >= 1) {
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce attr;
+    if (attr.first()) {
       cudaFuncSetAttribute(k_thomas_long_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr = true;
     }
     const dim3 grid((unsigned)((warps + wl - 1) / wl));
     k_thomas_long_smem<T><<<grid, 32 * wl, per * wl, st>>>(scratch, n, ns, rpiv, mneg, nblk, active, nper_active);
@@ -517,7 +515,8 @@ bool dst_lines_profitable_f64(int p, int nblk, int ns);
 cudaError_t dst_lines_fwd_f32(int p, const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl, float* scratch,
                               int nblk, const int* active, int nper_active, int vec, cudaStream_t st);
 cudaError_t dst_lines_fwd_bulk_f32(int p, const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl,
-                                   float* scratch, int nblk, const int* active, int nper_active, cudaStream_t st);
+                                   float* scratch, int nblk, const int* active, int nper_active, int* err,
+                                   int wait_limit, cudaStream_t st);
 cudaError_t dst_lines_inv_f32(int p, const float* scratch, void* out, int out_prec, BatchDesc ob, LineLayout L,
                               const DstPlan& pl, int nblk, const int* active, int nper_active, int vec,
                               cudaStream_t st);
@@ -551,12 +550,13 @@ bool lines_engine(int p, int nblk, int ns, int engine) {
 
 template <typename T, typename To>
 cudaError_t lines_fwd(const DstPlan& pl, const double* in, BatchDesc ib, LineLayout L, T* scratch, int nblk,
-                      const int* active, int nper_active, cudaStream_t st, int bulk) {
+                      const int* active, int nper_active, cudaStream_t st, int bulk, int* err = nullptr,
+                      int wait_limit = 1 << 22) {
   const int vec = pairs_aligned(in, 8, ib, L) ? 1 : 0;
   if constexpr (sizeof(T) == 4) {
     // persistent form with bulk copies: contiguous rows, 16-byte aligned blocks
     if (bulk && vec && L.ss == L.nt) return dst_lines_fwd_bulk_f32(pl.p, in, ib, L, pl, scratch, nblk, active,
-                                                                   nper_active, st);
+                                                                   nper_active, err, wait_limit, st);
   }
   if constexpr (sizeof(T) == 8)
     return dst_lines_fwd_f64(pl.p, in, ib, L, pl, scratch, nblk, active, nper_active, vec, st);
@@ -580,11 +580,10 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
                             To* out, BatchDesc ob, int nblk, T* scratch, const int* active,
                             int nper_active, cudaStream_t st, cudaEvent_t* ev) {
   const int n = tb.n;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static PerDeviceOnce attr_set;
+  if (attr_set.first()) {
     cudaFuncSetAttribute(k_dense_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dense_inverse<T, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
   }
   const DstPlan& pl = tb.plan;
   if (pl.mode == DST_DENSE) {
@@ -601,7 +600,8 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
   if (tb.q == 0 && lines_engine<T>(pl.p, nblk, L.ns, tb.generic)) {
     // size-specialised kernels: forward DST, Thomas, inverse DST
     if (ev) record_event(ev[0], st);
-    cudaError_t e = lines_fwd<T, To>(pl, in, ib, L, scratch, nblk, active, nper_active, st, tb.bulk);
+    cudaError_t e = lines_fwd<T, To>(pl, in, ib, L, scratch, nblk, active, nper_active, st, tb.bulk, tb.err,
+                                     tb.wait_limit);
     if (e != cudaSuccess) return e;
     if (ev) record_event(ev[1], st);
     if (ev) record_event(ev[2], st);
@@ -657,12 +657,11 @@ cudaError_t launch_dst_pass(bool forward, const FastSolveTables& tb, LineLayout 
   const int n = tb.n;
   const DstPlan& pl = tb.plan;
   if (pl.mode == DST_DENSE) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static PerDeviceOnce attr_set;
+    if (attr_set.first()) {
       cudaFuncSetAttribute(k_dense_forward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(k_dense_inverse<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            200 * 1024);
-      attr_set = true;
     }
     const int lpb = lines_per_block<double>(n);
     const size_t smem = fs_smem_bytes<double>(n, lpb);
@@ -727,9 +726,14 @@ cudaError_t launch_fast_solve_rdft(const FastSolveTables& tb, LineLayout L, cons
 // block (k_rdft_fwd / k_thomas_reg / k_rdft_inv).  (4 is the public code for a
 // centre without fast solve.)
 bool fast_solve_fused_fits(int prec, const FastSolveTables& tb, LineLayout L);
+bool fast_solve_cluster_fits(const FastSolveTables& tb, LineLayout L);
+cudaError_t launch_fast_solve_cluster(int out_prec, const FastSolveTables& tb, LineLayout L, const double* in,
+                                      BatchDesc ib, void* out, BatchDesc ob, int nblk, const int* active,
+                                      int nper_active, cudaStream_t st);
 int fast_solve_path(int prec, const FastSolveTables& tb, LineLayout L, int nblk) {
   if (tb.kind == 1) return 5;
   if (tb.kind == 2) return 6;
+  if (prec == 32 && tb.cluster && fast_solve_cluster_fits(tb, L)) return 7;
   if (tb.fused && fast_solve_fused_fits(prec, tb, L)) return 3;
   if (tb.plan.mode == DST_DENSE) return 2;
   const bool special = prec == 64 ? lines_engine<double>(tb.plan.p, nblk, L.ns, tb.generic)
@@ -755,6 +759,21 @@ cudaError_t launch_fast_solve(int prec, int out_prec, const FastSolveTables& tb,
                                        st)
                : launch_fast_solve_rdft(tb, L, in, ib, (double*)out, ob, nblk, (double*)scratch, active, nper_active,
                                         st);
+  }
+  if (prec == 32 && tb.cluster && fast_solve_cluster_fits(tb, L)) {
+    // one pass, one cluster per block (FP32 only); the profiled slot is the fused one
+    if (ev) record_event(ev[6], st);
+    const cudaError_t e = launch_fast_solve_cluster(out_prec, tb, L, in, ib, out, ob, nblk, active, nper_active, st);
+    if (e == cudaSuccess) {
+      if (ev) {
+        record_event(ev[7], st);
+        for (int i = 0; i < 6; ++i) record_event(ev[i], st);
+      }
+      if (launches) *launches += 1;
+      return cudaSuccess;
+    }
+    if (e != cudaErrorNotSupported) return e;
+    cudaGetLastError();  // unaligned blocks or no resident cluster: the other paths
   }
   if (tb.fused) {
     if (ev) record_event(ev[6], st);

@@ -97,10 +97,9 @@ k_fft_inverse(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc ob,
 template <typename T, int MAXR>
 cudaError_t fft_fwd_launch(dim3 grid, size_t smem, cudaStream_t st, const double* in, BatchDesc ib, LineLayout L,
                            const DstPlan& pl, T* scratch, int Q, const int* active, int nper_active) {
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  if (attr.first()) {
     cudaFuncSetAttribute(k_fft_forward<T, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
   }
   k_fft_forward<T, MAXR><<<grid, kFftThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
   return cudaGetLastError();
@@ -109,10 +108,9 @@ cudaError_t fft_fwd_launch(dim3 grid, size_t smem, cudaStream_t st, const double
 template <typename T, typename To, int MAXR>
 cudaError_t fft_inv_launch(dim3 grid, size_t smem, cudaStream_t st, const T* scratch, To* out, BatchDesc ob,
                            LineLayout L, const DstPlan& pl, int Q, const int* active, int nper_active) {
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  if (attr.first()) {
     cudaFuncSetAttribute(k_fft_inverse<T, To, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
   }
   k_fft_inverse<T, To, MAXR><<<grid, kFftThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);
   return cudaGetLastError();

@@ -209,11 +209,10 @@ template <typename T, typename To, int MAXR>
 cudaError_t launch_fused_impl(int csz, int R, int Q, const FastSolveTables& tb, LineLayout L, const double* in,
                               BatchDesc ib, To* out, BatchDesc ob, int nblk, const int* active, int nper_active,
                               cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  if (attr.first()) {
     cudaFuncSetAttribute(k_fast_solve_fused<T, To, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_fast_solve_fused<T, To, MAXR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    attr = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(csz, nblk, 1);

@@ -37,13 +37,13 @@ inline double cos_pi_frac(long long num, long long den) {
   return sign * std::cos(M_PI * (double)q / (double)den);
 }
 
-// Reciprocal Thomas pivots for tridiag(delta, d_k, delta) of length ns, all modes:
-// r[s][k-1], d_k = -4 delta + 2 delta cos(k pi/(n+1)) + kappa.
-inline void fill_pivots(int n, int ns, double delta, double kappa, std::vector<double>& r) {
-  r.resize((size_t)ns * n);  // [k][s], s fastest (one contiguous column per mode)
+// Reciprocal Thomas pivots for tridiag(delta, d_k, delta) of length ns, all modes,
+// into caller storage of n * ns doubles laid out [k][s], s fastest (one
+// contiguous column per mode); d_k = -4 delta + 2 delta cos(k pi/(n+1)) + kappa.
+inline void fill_pivots_into(int n, int ns, double delta, double kappa, double* r) {
   for (int k = 1; k <= n; ++k) {
     const double d = -4.0 * delta + 2.0 * delta * cos_pi_frac(k, n + 1) + kappa;
-    double* rk = r.data() + (size_t)(k - 1) * ns;
+    double* rk = r + (size_t)(k - 1) * ns;
     double rp = 1.0 / d;
     rk[0] = rp;
     for (int s = 1; s < ns; ++s) {
@@ -51,6 +51,11 @@ inline void fill_pivots(int n, int ns, double delta, double kappa, std::vector<d
       rk[s] = rp;
     }
   }
+}
+
+inline void fill_pivots(int n, int ns, double delta, double kappa, std::vector<double>& r) {
+  r.resize((size_t)ns * n);
+  fill_pivots_into(n, ns, delta, kappa, r.data());
 }
 
 
@@ -83,16 +88,18 @@ inline bool is_prime(int p) {
 }
 
 inline int primitive_root(int p) {
-  std::vector<int> fs;
+  // distinct prime factors of p - 1 (a 32-bit p - 1 has at most 9 of them);
+  // fixed arrays, no heap, so the no-allocation entry point can call it
+  int fs[32], nf = 0;
   int m = p - 1;
   for (int d = 2; (long long)d * d <= m; ++d) {
-    if (m % d == 0) { fs.push_back(d); while (m % d == 0) m /= d; }
+    if (m % d == 0) { fs[nf++] = d; while (m % d == 0) m /= d; }
   }
-  if (m > 1) fs.push_back(m);
+  if (m > 1) fs[nf++] = m;
   for (int g = 2; g < p; ++g) {
     bool ok = true;
-    for (int q : fs) {
-      long long r = 1, b = g, e = (p - 1) / q;
+    for (int i = 0; i < nf; ++i) {
+      long long r = 1, b = g, e = (p - 1) / fs[i];
       while (e) { if (e & 1) r = r * b % p; b = b * b % p; e >>= 1; }
       if (r == 1) { ok = false; break; }
     }
@@ -106,6 +113,38 @@ inline void cexp_neg(long long num, long long den, double* re, double* im) {
   *re = cos_pi_frac(2 * num, den);
   // sin(2 pi num/den) = cos(pi (4 num - den) / (2 den))
   *im = -cos_pi_frac(4 * num - den, 2 * den);
+}
+
+// Rader's tables for a prime p (N = p - 1), into caller storage: the input and
+// output permutations pin[b] = g^b mod p and pout[b] = g^-b mod p for a
+// primitive root g, and Bhat = DFT_N(B) / N (N complex values, re/im
+// interleaved) with B_c = exp(-2 pi i g^-c / p).  No heap.
+inline void rader_tables(int p, int* pin, int* pout, double* Bhat) {
+  const int N = p - 1, g = primitive_root(p);
+  long long ginv = 1;
+  {  // g^{p-2} mod p
+    long long b = g, e = p - 2;
+    while (e) { if (e & 1) ginv = ginv * b % p; b = b * b % p; e >>= 1; }
+  }
+  long long a = 1, c = 1;
+  for (int b = 0; b < N; ++b) {
+    pin[b] = (int)a;
+    pout[b] = (int)c;
+    a = a * g % p;
+    c = c * ginv % p;
+  }
+  for (int k = 0; k < N; ++k) {
+    long double sr = 0, si = 0;
+    for (int q = 0; q < N; ++q) {
+      double br, bi, wr, wi;
+      cexp_neg(pout[q], p, &br, &bi);
+      cexp_neg((long long)q * k % N, N, &wr, &wi);
+      sr += (long double)br * wr - (long double)bi * wi;
+      si += (long double)br * wi + (long double)bi * wr;
+    }
+    Bhat[2 * k] = (double)(sr / N);
+    Bhat[2 * k + 1] = (double)(si / N);
+  }
 }
 
 inline HostPlan build_plan(int n) {
@@ -132,36 +171,10 @@ inline HostPlan build_plan(int n) {
   P.W.resize(2 * P.N);
   for (int m = 0; m < P.N; ++m) cexp_neg(m, P.N, &P.W[2 * m], &P.W[2 * m + 1]);
   if (P.mode == DST_RADER) {
-    const int N = P.N, g = primitive_root(p);
-    long long ginv = 1;
-    {  // g^{p-2} mod p
-      long long b = g, e = p - 2;
-      while (e) { if (e & 1) ginv = ginv * b % p; b = b * b % p; e >>= 1; }
-    }
-    P.pin.resize(N);
-    P.pout.resize(N);
-    long long a = 1, c = 1;
-    for (int b = 0; b < N; ++b) {
-      P.pin[b] = (int)a;
-      P.pout[b] = (int)c;
-      a = a * g % p;
-      c = c * ginv % p;
-    }
-    // Bhat = DFT_N(B) / N with B_c = exp(-2 pi i g^{-c} / p)
-    std::vector<double> Br(N), Bi(N);
-    for (int q = 0; q < N; ++q) cexp_neg(P.pout[q], p, &Br[q], &Bi[q]);
-    P.Bhat.resize(2 * N);
-    for (int k = 0; k < N; ++k) {
-      long double sr = 0, si = 0;
-      for (int q = 0; q < N; ++q) {
-        double wr, wi;
-        cexp_neg((long long)q * k % N, N, &wr, &wi);
-        sr += (long double)Br[q] * wr - (long double)Bi[q] * wi;
-        si += (long double)Br[q] * wi + (long double)Bi[q] * wr;
-      }
-      P.Bhat[2 * k] = (double)(sr / N);
-      P.Bhat[2 * k + 1] = (double)(si / N);
-    }
+    P.pin.resize(P.N);
+    P.pout.resize(P.N);
+    P.Bhat.resize(2 * P.N);
+    rader_tables(p, P.pin.data(), P.pout.data(), P.Bhat.data());
   }
   return P;
 }

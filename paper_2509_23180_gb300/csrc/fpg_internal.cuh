@@ -10,6 +10,20 @@
 
 namespace fpg {
 
+// Function attributes (cudaFuncSetAttribute) apply to the current device only, so
+// a kernel's attributes are set once per device.  `first()` is true the first time
+// it is asked on the current device (and always for device ordinals past 63).
+struct PerDeviceOnce {
+  bool done[64] = {};
+  bool first() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+    if (done[dev]) return false;
+    done[dev] = true;
+    return true;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Batch of blocks of one shape inside larger vectors.  Block b of a launch lives
 // at base + (b / nper) * rhs_stride + off[b % nper]: nper <= 8 blocks per
@@ -41,6 +55,11 @@ struct FastSolveTables {
   int fused = 0;      // 1: one-pass cluster kernel when the block fits
   int generic = 0;    // DST engine: 0 auto, 1 generic FFT engine, 2 size-specialised where compiled
   int bulk = 0;       // 1: FP32 forward DST as the persistent kernel with bulk asynchronous row copies
+  int cluster = 0;             // 1: FP32 one-pass cluster kernel where it fits (fpg_cluster_fs.cu)
+  const void* cl_sigma = nullptr;  // its tables (FP32): sigma_k and the scaled pivot at each strip start
+  const void* cl_wseed = nullptr;
+  int* err = nullptr;          // device status word: a bounded wait that gave up writes 1 (null: none)
+  int wait_limit = 1 << 22;    // tries of every bounded device wait (0: give up at once)
   int kind = 0;       // transform along t: 0 DST-I (Dirichlet ends), 1 DCT-II (Neumann ends), 2 real DFT
                       // (periodic); 1 and 2 FP64 only
   const void* post = nullptr;  // DCT-II: e^{-i pi k/(2n)}, k < n (complex, FP64)

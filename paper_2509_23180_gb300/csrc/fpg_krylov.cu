@@ -934,11 +934,10 @@ cudaError_t launch_schur_reduced(const void* z, int zprec, long long zstride, in
                                  cudaStream_t st) {
   dim3 grid((n + 31) / 32, nrhs * narms);
   const size_t smem = sizeof(double) * (5 * n + 2 + 256);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static PerDeviceOnce attr_set;
+  if (attr_set.first()) {
     cudaFuncSetAttribute(k_schur_lines<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_schur_lines<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
   }
   if (zprec == 64)
     k_schur_lines<double><<<grid, dim3(32, 8), smem, st>>>((const double*)z, zstride, n, ctab, arms_dev, narms,
@@ -1042,10 +1041,9 @@ cudaError_t launch_arnoldi_cluster(int csz, const double* V, long long vstride, 
                                    double* cs, double* sn, double* g, double* res, int m, const double* tolabs,
                                    int* active, int* kcyc, int* iters, int max_iters, int do_givens,
                                    cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  if (attr.first()) {
     cudaFuncSetAttribute(k_arnoldi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    attr = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(csz * nrhs, 1, 1);
@@ -1097,10 +1095,9 @@ cudaError_t launch_reg_impl(int csz, const double* V, long long vstride, const d
                             long long len, int j, int nrhs, double* H, int hcol_stride, int hrhs_stride, double* cs,
                             double* sn, double* g, double* res, int m, const double* tolabs, int* active, int* kcyc,
                             int* iters, int max_iters, int do_givens, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  if (attr.first()) {
     cudaFuncSetAttribute(k_arnoldi_cluster_reg<Tz, EPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    attr = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(csz * nrhs, 1, 1);

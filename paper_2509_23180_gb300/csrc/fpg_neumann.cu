@@ -295,11 +295,10 @@ cudaError_t pd_launch(const FastSolveTables& tb, LineLayout L, const double* in,
   const int nt = L.nt;
   const int Q = nm_pairs(nt);
   const size_t smem = nm_smem(nt, Q);
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  if (attr.first()) {
     cudaFuncSetAttribute(k_rdft_fwd<MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_rdft_inv<MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
   }
   const C2<double>* W = reinterpret_cast<const C2<double>*>(tb.plan.W);
   const dim3 grid((L.ns + 2 * Q - 1) / (2 * Q), nblk);
@@ -318,11 +317,10 @@ cudaError_t nm_launch(const FastSolveTables& tb, LineLayout L, const double* in,
   const int nt = L.nt;
   const int Q = nm_pairs(nt);
   const size_t smem = nm_smem(nt, Q);
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  if (attr.first()) {
     cudaFuncSetAttribute(k_dct_fwd<MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dct_inv<MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
   }
   const C2<double>* W = reinterpret_cast<const C2<double>*>(tb.plan.W);
   const C2<double>* post = reinterpret_cast<const C2<double>*>(tb.post);

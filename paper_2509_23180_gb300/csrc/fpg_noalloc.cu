@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <mutex>
 
+#include "fpg_host_tables.h"
 #include "fpg_internal.cuh"
 
 namespace fpg {
@@ -58,55 +59,6 @@ constexpr int kMaxDevices = 64;
 static DeviceState g_dev[kMaxDevices];
 static std::mutex g_mutex;
 
-double cospi_frac(long long num, long long den) {
-  long long q = num % (2 * den);
-  if (q < 0) q += 2 * den;
-  if (q > den) q = 2 * den - q;
-  double sign = 1.0;
-  if (2 * q > den) { q = den - q; sign = -1.0; }
-  return sign * std::cos(M_PI * (double)q / (double)den);
-}
-
-bool radix_list(int N, int* rad, int* nrad) {
-  static const int odd[] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43};
-  int m = N, twos = 0, cnt = 0;
-  while (m % 2 == 0) { m /= 2; ++twos; }
-  while (twos >= 2) { if (cnt >= kMaxRadices) return false; rad[cnt++] = 4; twos -= 2; }
-  if (twos == 1) { if (cnt >= kMaxRadices) return false; rad[cnt++] = 2; }
-  for (int q : odd)
-    while (m % q == 0) { if (cnt >= kMaxRadices) return false; rad[cnt++] = q; m /= q; }
-  *nrad = cnt;
-  return m == 1 && cnt > 0;
-}
-
-bool prime(int p) {
-  if (p < 2) return false;
-  for (int d = 2; d * d <= p; ++d) if (p % d == 0) return false;
-  return true;
-}
-
-int prim_root(int p) {
-  int fs[32], nf = 0, m = p - 1;
-  for (int d = 2; d * d <= m; ++d)
-    if (m % d == 0) { fs[nf++] = d; while (m % d == 0) m /= d; }
-  if (m > 1) fs[nf++] = m;
-  for (int g = 2; g < p; ++g) {
-    bool ok = true;
-    for (int i = 0; i < nf && ok; ++i) {
-      long long r = 1, b = g, e = (p - 1) / fs[i];
-      while (e) { if (e & 1) r = r * b % p; b = b * b % p; e >>= 1; }
-      ok = r != 1;
-    }
-    if (ok) return g;
-  }
-  return -1;
-}
-
-void cexp_minus(long long num, long long den, double* re, double* im) {
-  *re = cospi_frac(2 * num, den);
-  *im = -cospi_frac(4 * num - den, 2 * den);
-}
-
 // Build the tables of (n, kappa) in the host staging arrays and copy them into
 // the table region of the device array; fills st.plan.  Synchronises `stream`.
 cudaError_t upload_tables(DeviceState& st, int n, double kappa, cudaStream_t stream) {
@@ -115,49 +67,19 @@ cudaError_t upload_tables(DeviceState& st, int n, double kappa, cudaStream_t str
   DstPlan dp{};
   dp.n = n;
   dp.p = p;
-  int rad[kMaxRadices], nrad = 0;
-  if (radix_list(p, rad, &nrad)) { dp.mode = DST_STOCKHAM; dp.N = p; }
-  else if (prime(p) && radix_list(p - 1, rad, &nrad)) { dp.mode = DST_RADER; dp.N = p - 1; }
-  else { dp.mode = DST_DENSE; dp.N = 1; nrad = 0; }
-  dp.nrad = nrad;
-  for (int i = 0; i < nrad; ++i) dp.rad[i] = rad[i];
+  // the plan and tables come from the library's host-table helpers (the same
+  // functions the domain API uses), in their heap-free forms
+  const HostPlan shape = plan_shape(n);
+  dp.mode = shape.mode;
+  dp.N = shape.N;
+  dp.nrad = shape.nrad;
+  for (int i = 0; i < shape.nrad; ++i) dp.rad[i] = shape.rad[i];
   const int N = dp.N;
-  for (int j = 0; j < p; ++j) h_sinp[j] = cospi_frac(2 * j - p, 2 * p);
-  for (int m = 0; m < 2 * p; ++m) h_dense[m] = cospi_frac(2 * m - p, 2 * p);
-  for (int m = 0; m < N; ++m) cexp_minus(m, N, &h_W[2 * m], &h_W[2 * m + 1]);
-  if (dp.mode == DST_RADER) {
-    const int g = prim_root(p);
-    long long ginv = 1, b = g, e = p - 2;
-    while (e) { if (e & 1) ginv = ginv * b % p; b = b * b % p; e >>= 1; }
-    long long a = 1, c = 1;
-    for (int q = 0; q < N; ++q) {
-      h_pin[q] = (int)a;
-      h_pout[q] = (int)c;
-      a = a * g % p;
-      c = c * ginv % p;
-    }
-    for (int k = 0; k < N; ++k) {
-      long double sr = 0, si = 0;
-      for (int q = 0; q < N; ++q) {
-        double br, bi, wr, wi;
-        cexp_minus(h_pout[q], p, &br, &bi);
-        cexp_minus((long long)q * k % N, N, &wr, &wi);
-        sr += (long double)br * wr - (long double)bi * wi;
-        si += (long double)br * wi + (long double)bi * wr;
-      }
-      h_Bhat[2 * k] = (double)(sr / N);
-      h_Bhat[2 * k + 1] = (double)(si / N);
-    }
-  }
-  for (int k = 1; k <= n; ++k) {
-    const double d = -4.0 * delta + 2.0 * delta * cospi_frac(k, p) + kappa;
-    double rp = 1.0 / d;  // [k][s] layout, s fastest
-    h_rpiv[(size_t)(k - 1) * n] = rp;
-    for (int s = 1; s < n; ++s) {
-      rp = 1.0 / (d - delta * delta * rp);
-      h_rpiv[(size_t)(k - 1) * n + s] = rp;
-    }
-  }
+  for (int j = 0; j < p; ++j) h_sinp[j] = cos_pi_frac(2 * j - p, 2 * p);  // sin(pi j/p)
+  for (int m = 0; m < 2 * p; ++m) h_dense[m] = cos_pi_frac(2 * m - p, 2 * p);
+  for (int m = 0; m < N; ++m) cexp_neg(m, N, &h_W[2 * m], &h_W[2 * m + 1]);
+  if (dp.mode == DST_RADER) rader_tables(p, h_pin, h_pout, h_Bhat);
+  fill_pivots_into(n, n, delta, kappa, h_rpiv);
   for (long long i = 0; i < (long long)n * n; ++i) h_mneg[i] = -delta * h_rpiv[i];
 
   // table region, after the coefficient area; 256-byte aligned pieces
@@ -217,6 +139,12 @@ extern "C" fpg_status fpg_fast_solve_noalloc(int32_t n, double kappa, const doub
   }
   if (!(kappa <= 0.0) || !std::isfinite(kappa)) {
     record_message("fpg_fast_solve_noalloc: kappa must be finite and <= 0");
+    return FPG_EINVAL;
+  }
+  if (nvec > FPG_NOALLOC_MAX_NVEC) {
+    // the batch is a grid dimension of the fast-solve launches; the cap matches
+    // the domain API's largest right-hand-side count
+    record_message("fpg_fast_solve_noalloc: nvec exceeds FPG_NOALLOC_MAX_NVEC");
     return FPG_EINVAL;
   }
   if ((long long)nvec * n * n > kCoeffDoubles) {

@@ -70,11 +70,10 @@ template <int P>
 cudaError_t schur_dst_one(const void* z, int zprec, long long zstride, const DstPlan& pl, const double* gsc,
                           const int* arms, int narms, double* corr, const int* active, int nrhs, cudaStream_t st) {
   using S = dl::LineShape<double, P>;
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  if (attr.first()) {
     cudaFuncSetAttribute(k_schur_lines_dst<P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
     cudaFuncSetAttribute(k_schur_lines_dst<P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
-    attr = true;
   }
   const int nlines = nrhs * narms;
   const dim3 grid((nlines + 2 * S::Q - 1) / (2 * S::Q));

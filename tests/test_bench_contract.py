@@ -99,3 +99,64 @@ def test_clock_summary_reads_reasons_and_median(tmp_path):
     s.proc, s.path = object(), str(csv)
     out = s.summary()
     assert out == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "samples": 3, "reasons": ["sw_power_cap"]}
+
+
+def test_oracle_pool_splits_the_work_and_matches_the_direct_solve():
+    """The CPU leg on several host cores: the workload's right-hand sides split
+    over spawn-started workers (each factors K for its share) give exactly the
+    oracle's direct solutions, every right-hand side once."""
+    import bench
+    import workloads as W
+    from oracle import direct, operator
+    n = 12
+    f_by_kappa = {k: W.rhs_batch("cross", n, [0, 1, 2], kind="fourier") for k in (0.0, -10.0)}
+    pool = bench.OraclePool(3)
+    try:
+        tasks = pool.split("cross", n, f_by_kappa)
+        assert sum(t[3].shape[0] for t in tasks) == 6 and {t[2] for t in tasks} == {0.0, -10.0}
+        dt, sols = pool.run(tasks)
+        assert dt > 0
+        for (g, nn, kappa, f), P in zip(tasks, sols):
+            want = direct.Factor(operator.assemble(g, nn, kappa)).solve(f)
+            assert np.allclose(P, want, rtol=1e-13, atol=1e-16)
+        out = bench.cpu_baseline(SimpleNamespace(n=n), f_by_kappa, pool)
+        assert out["kind"] == "oracle" and out["value"] > 0 and 1 <= out["cores"] <= 3
+    finally:
+        pool.close()
+
+
+def test_error_stats_sees_one_wrong_block():
+    """The bench's error statement is element-wise: a mistake confined to one arm
+    shows at its own size in max-abs and in the worst block."""
+    import bench
+    import workloads as W
+    n = 10
+    R = W.rhs_batch("cross", n, [4], kind="fourier")[0]
+    P = R.copy()
+    off = n * n  # W arm follows the centre
+    P[off + 3] += 1e-6 * np.abs(R).max()
+    e = bench.error_stats(P, R, "cross", n)
+    assert e["worst_block"]["block"] == "W"
+    assert abs(e["maxabs_rel"] - 1e-6) < 1e-9 and e["rel_2norm"] < e["maxabs_rel"]
+
+
+def test_parity_helper_is_element_wise():
+    """The GPU tests' error measure sees a mistake on one interface line that the
+    2-norm of the whole vector dilutes, and judges near-zero parts at 1% of the
+    solution's scale."""
+    from tests import parity
+    import workloads as W
+    n = 16
+    R = W.rhs_batch("cross", n, [2], kind="fourier")[0]
+    P = R.copy()
+    line = dict(parity.part_slices("cross", n))["W|C"]
+    P[line] += 1e-8 * np.abs(R).max()
+    assert parity.rel(P, R) >= 0.99e-8 and parity.norm_rel(P, R) < 0.5 * parity.rel(P, R)
+    errs = parity.part_errors(P, R, "cross", n)
+    assert errs["W|C"] > 1e-9 and errs["C"] == 0.0 and errs["E|C"] == 0.0
+    # a part of near-zero values: its error is measured against 1% of max|R|
+    Z = R.copy()
+    Z[line] = 1e-14
+    Pz = Z.copy()
+    Pz[line] += 1e-12 * np.abs(Z).max()
+    assert parity.part_errors(Pz, Z, "cross", n)["W|C"] <= 1e-10

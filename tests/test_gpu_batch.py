@@ -8,6 +8,7 @@ import pytest
 import scipy.sparse.linalg as spla
 
 import workloads as W
+from tests.parity import assert_solution, rel  # noqa: F401
 from oracle import neumann_cross as NX
 from oracle import operator as O
 from oracle import strip as SX
@@ -25,8 +26,6 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
 def run(batch, live, limit=200000):

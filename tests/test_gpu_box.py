@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import box as X
+from tests.parity import rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -21,8 +22,6 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
 @pytest.mark.parametrize("nx,ny,nz", [(2, 3, 1), (2, 2, 1), (8, 6, 5), (16, 16, 16), (64, 40, 9), (4096, 3, 2),

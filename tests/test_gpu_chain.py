@@ -9,6 +9,7 @@ import pytest
 import scipy.sparse.linalg as spla
 
 import workloads as W
+from tests.parity import assert_solution, rel  # noqa: F401
 from oracle import strip as X
 from oracle.schur import BlockSystem, algorithm1
 
@@ -25,8 +26,6 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def rel(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
 
 
 def domain(B, K, n, kappa, **kw):

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from tests.parity import assert_solution, rel  # noqa: F401
 from oracle import operator as O
 from oracle import schur as S
 from oracle import transforms as T
@@ -27,8 +28,6 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def rel(a, b):
-    return np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / np.linalg.norm(b)
 
 
 def mode_mix(n, kappa, seed, count=2):

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import neumann as N
+from tests.parity import rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -21,8 +22,6 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
 @pytest.mark.parametrize("nt,ns", [(8, 7), (64, 63), (256, 256), (1024, 100)])

@@ -9,6 +9,7 @@ import pytest
 import scipy.sparse.linalg as spla
 
 import workloads as W
+from tests.parity import assert_solution, rel  # noqa: F401
 from oracle import neumann_cross as X
 from oracle.schur import BlockSystem
 
@@ -27,8 +28,6 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def rel(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
 
 
 def domain(B, n, kappa, **kw):

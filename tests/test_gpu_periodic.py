@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import periodic as P
+from tests.parity import rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -22,8 +23,6 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
 @pytest.mark.parametrize("nt,ns", [(2, 3), (8, 7), (15, 9), (64, 63), (256, 256), (1024, 100)])

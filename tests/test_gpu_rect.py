@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import neumann as NM
+from tests.parity import rel
 from oracle import operator as O
 from oracle import periodic as PD
 
@@ -21,8 +22,6 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
 def oracle_solve(kind, nt, ns, h, kappa, v):

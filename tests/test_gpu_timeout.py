@@ -1,0 +1,57 @@
+"""Bounded device waits: a wait that runs out gives FPG_ETIMEOUT, not a trap or a hang.
+
+The bulk-copy forward DST (FPG_OPT_DST_BULK) waits on an mbarrier for each line
+tile it fetches.  With FPG_OPT_WAIT_LIMIT = 0 every such wait gives up at once:
+the kernel records it in the domain's status word, lets its copy in flight land
+and returns.  The solve must then report FPG_ETIMEOUT for every right-hand side,
+and the same domain, stream and context must solve correctly afterwards with
+the default limit.  Nothing here faults the GPU: the copies are real and in
+bounds, only the waiting is cut short.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import direct as D
+from oracle import operator as O
+from tests.parity import assert_solution
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_wait_that_runs_out_reports_etimeout_and_context_stays_usable(lib):
+    from paper_2509_23180_gb300 import binding as B
+    n, kappa = 64, -10.0
+    f = W.rhs_batch("cross", n, [1, 2], kind="fourier")
+    fd = torch.as_tensor(f, device="cuda")
+    d = B.Domain(B.make_desc("cross", n, kappa, nrhs=2, restart=20, rtol=1e-10, max_iters=200,
+                             precond_precision=32))
+    d.set_option(B.OPT_DST_BULK, 1)
+    assert d.fast_solve_path() == 1  # the size-specialised line DST (p = 65), whose FP32 forward is the bulk kernel
+    d.set_option(B.OPT_WAIT_LIMIT, 0)
+    d.set_rhs(fd)
+    p = torch.zeros_like(fd)
+    st, info = d.solve(p, check=False)
+    torch.cuda.synchronize()  # the device is still answering
+    assert st == B.FPG_ETIMEOUT, (st, info)
+    assert all(i["status"] == B.FPG_ETIMEOUT for i in info)
+    # default limit again: the same domain solves, and the answer is the oracle's
+    d.set_option(B.OPT_WAIT_LIMIT, 1 << 22)
+    d.set_rhs(fd)
+    p.zero_()
+    st, info = d.solve(p, check=False)
+    assert st == B.FPG_OK, info
+    ref = D.Factor(O.assemble("cross", n, kappa)).solve(f)
+    P = p.cpu().numpy()
+    for r in range(2):
+        assert_solution(P[r], ref[r], "cross", n, 1e-9)
+    d.close()
+
+
+def test_wait_limit_option_is_validated(lib):
+    from paper_2509_23180_gb300 import binding as B
+    d = B.Domain(B.make_desc("cross", 16, 0.0, nrhs=1))
+    assert lib.fpg_set_option(d.handle, B.OPT_WAIT_LIMIT, -1) == B.FPG_EINVAL
+    assert lib.fpg_set_option(d.handle, B.OPT_WAIT_LIMIT, 1000) == B.FPG_OK
+    d.close()

@@ -14,6 +14,9 @@ pivots of every mode.  A small host program built from the library's own header
   * a Thomas sweep with the printed reciprocal pivots solves tridiag(delta,
     d_k, delta) x = f as LAPACK's banded solver does (scipy), with
     d_k = -4 delta + 2 delta cos(k pi/(n+1)) + kappa (Sec. 2.1, Eq. "trans_subeq").
+Rader's tables and the pivots are printed from the heap-free forms
+(`rader_tables`, `fill_pivots_into`) that the no-allocation fast solve calls,
+and checked identical to what the domain API's `build_plan` / `fill_pivots` give.
 """
 import os
 import shutil
@@ -44,20 +47,28 @@ int main() {
     for (double v : P.sinp) std::printf(" %%a", v);
     std::printf("\n");
     if (P.mode == DST_RADER) {
+      // the heap-free form the no-allocation entry point calls, into fixed arrays
+      static int pin[4096], pout[4096];
+      static double bhat[8192];
+      rader_tables(n + 1, pin, pout, bhat);
       std::printf("PIN %%d", n);
-      for (int v : P.pin) std::printf(" %%d", v);
+      for (int b = 0; b < P.N; ++b) std::printf(" %%d", pin[b]);
       std::printf("\nPOUT %%d", n);
-      for (int v : P.pout) std::printf(" %%d", v);
+      for (int b = 0; b < P.N; ++b) std::printf(" %%d", pout[b]);
       std::printf("\nBHAT %%d", n);
-      for (double v : P.Bhat) std::printf(" %%a", v);
-      std::printf("\n");
+      for (int b = 0; b < 2 * P.N; ++b) std::printf(" %%a", bhat[b]);
+      std::printf("\nSAME %%d %%d\n", n, (int)(std::vector<int>(pin, pin + P.N) == P.pin &&
+                                              std::vector<int>(pout, pout + P.N) == P.pout &&
+                                              std::vector<double>(bhat, bhat + 2 * P.N) == P.Bhat));
     }
   }
   struct Pv { int n, ns; double delta, kappa; };
   const Pv pv[] = {%(pivots)s};
   for (const Pv& q : pv) {
-    std::vector<double> r;
-    fill_pivots(q.n, q.ns, q.delta, q.kappa, r);
+    std::vector<double> r((size_t)q.n * q.ns), rv;
+    fill_pivots_into(q.n, q.ns, q.delta, q.kappa, r.data());  // heap-free form (caller storage)
+    fill_pivots(q.n, q.ns, q.delta, q.kappa, rv);
+    std::printf("SAME %%d %%d\n", q.n, (int)(r == rv));
     std::printf("PIV %%d %%d", q.n, q.ns);
     for (double v : r) std::printf(" %%a", v);
     std::printf("\n");
@@ -90,8 +101,18 @@ def tables(tmp_path_factory):
     rec = {}
     for line in out["tables"].splitlines():
         tag, key, *vals = line.split()
+        if tag == "SAME":
+            rec.setdefault(("SAME", 0), []).append((int(key), int(vals[0])))
+            continue
         rec[(tag, int(key))] = vals
     return modes, rec
+
+
+def test_heap_free_forms_equal_the_vector_forms(tables):
+    _, rec = tables
+    same = rec[("SAME", 0)]
+    assert len(same) == sum(1 for n in SIZES if rec.get(("PIN", n))) + len(PIVOTS)
+    assert all(ok == 1 for _, ok in same), same
 
 
 def _hex(vals):

@@ -37,6 +37,21 @@ def test_centre_block_is_the_rectangle_operator(nx, ny):
         assert np.allclose(R @ v, lam * v, rtol=1e-12, atol=1e-9)
 
 
+@pytest.mark.parametrize("domain", ["cross", "T", "L"])
+@pytest.mark.parametrize("n", [1, 2, 7, 24])
+def test_grid_assembly_equals_pointwise_assembly(domain, n):
+    """The grid-indexed K (used at n = 512 and 1024) is the point-by-point K:
+    the same pattern and the same values, entry for entry."""
+    A = O.assemble(domain, n, -10.0)
+    B = O.assemble_grid(domain, n, -10.0)
+    assert A.shape == B.shape
+    A.sort_indices()
+    B = B.tocsr()
+    B.sort_indices()
+    assert np.array_equal(A.indptr, B.indptr) and np.array_equal(A.indices, B.indices)
+    assert np.array_equal(A.data, B.data)
+
+
 def test_five_point_stencil_is_exact_on_quadratics():
     """Away from the edge, (K q)_I = lap q + kappa q for any quadratic q
     (the central second difference is exact on quadratics)."""
