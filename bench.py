@@ -487,9 +487,11 @@ def run_ours(args, rank, world):
         # the patterns of the method, each against plain FP64 on the same inputs
         t0 = time.perf_counter()
         cfg = {}
-        cfg["precision"] = config_precision(args, flush, pool)
-        cfg["batching"] = config_batching(args, flush, pool)
-        cfg["serving"] = config_serving(args)
+        for name, fn in (("precision", lambda: config_precision(args, flush, pool)),
+                         ("batching", lambda: config_batching(args, flush, pool)),
+                         ("serving", lambda: config_serving(args))):
+            print(f"bench: config {name} starts at {time.perf_counter() - t0:.0f} s", file=sys.stderr, flush=True)
+            cfg[name] = fn()
         cfg["seconds"] = time.perf_counter() - t0
         line["configs"] = cfg
     if pool is not None:

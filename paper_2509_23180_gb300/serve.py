@@ -280,16 +280,20 @@ class Server:
 
 def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart: int = 40, rtol: float = 1e-10,
                  precond_precision: int = 32, max_domains: int = 64, max_per_key: int = 2, max_busy: int = 8,
-                 realtime: bool = True, device: str = "cuda"):
-    """The same request stream through the library's batch runtime (fpg_batch_*).
-    A producer thread plays the clients: at each request's arrival time it
-    builds the right-hand sides on the device (its own stream) and hands the
-    request over.  The driver thread admits it into the runtime -- which queues
-    it with the other requests of its (geometry, n, kappa) for the next batch of
-    a resident domain and evicts idle domains when the pool is short -- steps the
-    runtime, which never waits on the device, and collects the tickets it
-    reports finished.  A request refused for lack of idle room waits and is
-    admitted first when room frees.  Returns (results in request order, stats)."""
+                 realtime: bool = True, device: str = "cuda", io_bytes: float = 32e9):
+    """The request stream through the library's batch runtime (fpg_batch_*).
+    A producer thread plays the clients: at each request's arrival time it hands
+    the request (its descriptor and seed, host side) to the driver thread.  The
+    driver admits requests in arrival order: it builds a request's right-hand
+    sides and solution buffer on the device only when it admits it, and only
+    while the buffers of admitted, unfinished requests stay within `io_bytes`
+    (a backlog waits on the host, not in HBM).  The runtime queues an admitted
+    request with the other requests of its (geometry, n, kappa) for the next
+    batch of a resident domain and evicts idle domains when the pool is short;
+    the driver steps it -- the runtime never waits on the device -- and collects
+    the tickets it reports finished.  A request refused for lack of idle room
+    keeps its buffers and is admitted first when room frees.  Returns (results
+    in request order, stats)."""
     import queue
     from collections import deque
 
@@ -300,16 +304,18 @@ def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart
                     max_busy=max_busy, device=device)
     order = sorted(range(len(requests)), key=lambda i: float(requests[i]["arrival_s"]))
     ready = queue.Queue()
-    live = {}          # ticket -> (request, f, p, admit time)
-    waiting = deque()  # prepared, refused for now
+    live = {}          # ticket -> (request, f, p, admit time, buffer bytes)
+    pending = deque()  # arrived, not yet built on the device (arrival order)
+    head = None        # built, refused for room: admitted first
     results = {}
+    io_live = 0
+    gen = torch.cuda.Stream(device=device)
     t0 = time.perf_counter()
     stop = threading.Event()
     failed = []        # the producer's exception, re-raised by the driver thread
 
     def producer():
         try:
-            stream = torch.cuda.Stream(device=device)
             for i in order:
                 if stop.is_set():
                     return
@@ -318,19 +324,27 @@ def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart
                     delay = float(r["arrival_s"]) - (time.perf_counter() - t0)
                     if delay > 0:
                         time.sleep(delay)
-                geom, n, kappa, nr = r["geometry"], int(r["n"]), float(r["kappa"]), int(r["nrhs"])
-                with torch.cuda.stream(stream):
-                    f = torch.stack([W.fourier_rhs_torch(geom, n, int(r["seed"]) * 16 + j, device=device)
-                                     for j in range(nr)])
-                    p = torch.empty_like(f)
-                stream.synchronize()  # f final before the runtime copies it
-                desc = B.make_desc(geom, n, kappa, nrhs=nr, restart=restart, rtol=rtol,
-                                   precond_precision=precond_precision)
-                ready.put((r, desc, f, p))
+                ready.put(r)
         except BaseException as e:
             failed.append(e)
         finally:
             ready.put(None)
+
+    def desc_of(r):
+        return B.make_desc(r["geometry"], int(r["n"]), float(r["kappa"]), nrhs=int(r["nrhs"]), restart=restart,
+                           rtol=rtol, precond_precision=precond_precision)
+
+    def buffer_bytes(r):
+        return 2 * 8 * int(r["nrhs"]) * B.unknowns(desc_of(r))
+
+    def build(r):
+        geom, n, nr = r["geometry"], int(r["n"]), int(r["nrhs"])
+        with torch.cuda.stream(gen):
+            f = torch.stack([W.fourier_rhs_torch(geom, n, int(r["seed"]) * 16 + j, device=device)
+                             for j in range(nr)])
+            p = torch.empty_like(f)
+        gen.synchronize()  # f final before the runtime copies it
+        return (r, desc_of(r), f, p, buffer_bytes(r))
 
     def key_bytes(desc):
         full = B.make_desc(desc.geometry, desc.n, desc.kappa, nrhs=slot_rhs, restart=restart, rtol=rtol,
@@ -338,9 +352,9 @@ def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart
         return B.workspace_bytes(full) + 8 * slot_rhs * B.unknowns(full)
 
     def try_admit(entry):
-        r, desc, f, p = entry
+        r, desc, f, p, nb = entry
         try:
-            live[batch.admit(desc, f, p)] = (r, f, p, time.perf_counter() - t0)
+            live[batch.admit(desc, f, p)] = (r, f, p, time.perf_counter() - t0, nb)
             return True
         except B.FpgError as e:
             if e.status != B.FPG_EBUDGET or key_bytes(desc) > pool_bytes:
@@ -348,7 +362,8 @@ def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart
             return False
 
     def collect(t):
-        r, f, p, t_adm = live[t]
+        nonlocal io_live
+        r, f, p, t_adm, nb = live[t]
         info = batch.poll(t, int(r["nrhs"]))
         if info is None:
             return False
@@ -358,30 +373,39 @@ def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart
             iterations=[i["iterations"] for i in info], residuals=[i["residual"] for i in info],
             status=max([i["status"] for i in info] or [0]), key=(r["geometry"], int(r["n"]), float(r["kappa"])))
         del live[t]
+        io_live -= nb
         return True
 
     th = threading.Thread(target=producer, daemon=True)
     th.start()
     produced_all = False
     try:
-        while not produced_all or live or waiting:
+        while not produced_all or live or pending or head is not None:
             progressed = False
-            while waiting and try_admit(waiting[0]):
-                waiting.popleft()
-                progressed = True
-            while True:
+            while True:  # arrivals: host side only
                 try:
-                    entry = ready.get_nowait()
+                    r = ready.get_nowait()
                 except queue.Empty:
                     break
-                if entry is None:
+                if r is None:
                     if failed:
                         raise RuntimeError("request producer failed") from failed[0]
                     produced_all = True
                     break
-                if waiting or not try_admit(entry):
-                    waiting.append(entry)  # first come, first admitted
+                pending.append(r)
                 progressed = True
+            if head is not None and try_admit(head):
+                head = None
+                progressed = True
+            while head is None and pending:
+                nb = buffer_bytes(pending[0])
+                if (live or io_live) and io_live + nb > io_bytes:
+                    break  # request buffers at their cap: the backlog waits on the host
+                entry = build(pending.popleft())
+                io_live += nb
+                progressed = True
+                if not try_admit(entry):
+                    head = entry
             finished = batch.step()
             for t in finished:
                 progressed |= collect(t)

@@ -333,3 +333,110 @@ def _square_modes(seed, block_id, xi, eta, modes, kmax):
     for q in range(modes):
         f += c[q] * np.sin(kx[q] * math.pi * xi) * np.sin(ky[q] * math.pi * eta) / (kx[q] ** 2 + ky[q] ** 2)
     return f
+
+
+# --------------------------------------------------------------------- lattices
+# A general concatenated geometry: any edge-connected set of unit squares
+# [i, i+1] x [j, j+1], 0 <= i, j < 8, given as a 64-bit mask (bit i + 8 j).
+# Block order (the library's I/O convention for FPG_GEOM_LATTICE): coupled
+# squares (two or more edge neighbours; of a lone pair, the first) in bit order,
+# n x n each; the links (grid lines shared by two coupled squares: vertical
+# edges by (j, i) of the left square, then horizontal edges by (j, i) of the
+# lower square), n points each; the junction points (lattice vertices with all
+# four squares around them, by (Y, X)); then the independent squares (one
+# neighbour) in bit order, each with the line it shares with its neighbour,
+# last (neighbour east or north) or first (west or south): (n+1) x n or n x (n+1).
+
+LATTICE_EXAMPLES = {
+    "square2x2": (1 << 0) | (1 << 1) | (1 << 8) | (1 << 9),
+    "L5": (1 << 0) | (1 << 1) | (1 << 2) | (1 << 8) | (1 << 16),          # L-shaped coupled set
+    "T6": (1 << 0) | (1 << 1) | (1 << 2) | (1 << 3) | (1 << 4) | (1 << 10),  # a row with a stem
+    "cross": (1 << 9) | (1 << 8) | (1 << 10) | (1 << 1) | (1 << 17),
+    "domino": (1 << 0) | (1 << 1),
+}
+
+
+def lattice_squares(mask: int):
+    return [(b % 8, b // 8) for b in range(64) if (mask >> b) & 1]
+
+
+def lattice_blocks(mask: int, n: int):
+    """(kind, (i, j) or None, first x node, first y node, nx, ny) per block in block
+    order; kind is 'Q' (coupled square), 'V'/'H' (link), 'P' (junction) or 'A'
+    (independent square); node coordinates in units of h."""
+    m = n + 1
+    have = set(lattice_squares(mask))
+    nb = {s: [d for d in ((1, 0), (-1, 0), (0, 1), (0, -1)) if (s[0] + d[0], s[1] + d[1]) in have]
+          for s in have}
+    order = lattice_squares(mask)
+    coupled = [s for s in order if len(nb[s]) >= 2] or order[:1]
+    cset = set(coupled)
+    out = [("Q", s, s[0] * m + 1, s[1] * m + 1, n, n) for s in coupled]
+    for kind, d in (("V", (1, 0)), ("H", (0, 1))):
+        for j in range(8):
+            for i in range(8):
+                if (i, j) in cset and (i + d[0], j + d[1]) in cset:
+                    if kind == "V":
+                        out.append(("V", (i, j), (i + 1) * m, j * m + 1, 1, n))
+                    else:
+                        out.append(("H", (i, j), i * m + 1, (j + 1) * m, n, 1))
+    for Y in range(1, 8):
+        for X in range(1, 8):
+            if {(X - 1, Y - 1), (X, Y - 1), (X - 1, Y), (X, Y)} <= have:
+                out.append(("P", (X, Y), X * m, Y * m, 1, 1))
+    for s in order:
+        if s in cset:
+            continue
+        d = nb[s][0]
+        i, j = s
+        box = {(1, 0): (i * m + 1, j * m + 1, m, n), (-1, 0): (i * m, j * m + 1, m, n),
+               (0, 1): (i * m + 1, j * m + 1, n, m), (0, -1): (i * m + 1, j * m, n, m)}[d]
+        out.append(("A", s) + box)
+    return out
+
+
+def lattice_total_unknowns(mask: int, n: int) -> int:
+    return sum(b[4] * b[5] for b in lattice_blocks(mask, n))
+
+
+def _lattice_xy(mask: int, n: int):
+    h = 1.0 / (n + 1)
+    xs, ys = [], []
+    for _, _, i0, j0, nx, ny in lattice_blocks(mask, n):
+        x, y = np.meshgrid((i0 + np.arange(nx)) * h, (j0 + np.arange(ny)) * h)
+        xs.append(x.ravel())
+        ys.append(y.ravel())
+    return np.concatenate(xs), np.concatenate(ys)
+
+
+def lattice_manufactured_solution(mask: int, n: int) -> np.ndarray:
+    """p = sin(pi x) sin(pi y) exp(0.3 x) at every unknown (zero on every integer
+    line, so on the union's edge), block order."""
+    x, y = _lattice_xy(mask, n)
+    return np.sin(math.pi * x) * np.sin(math.pi * y) * np.exp(0.3 * x)
+
+
+def lattice_manufactured_rhs(mask: int, n: int, kappa: float = 0.0) -> np.ndarray:
+    x, y = _lattice_xy(mask, n)
+    e = np.exp(0.3 * x)
+    lap = e * np.sin(math.pi * y) * ((0.09 - 2 * math.pi ** 2) * np.sin(math.pi * x)
+                                      + 0.6 * math.pi * np.cos(math.pi * x))
+    return lap + kappa * np.sin(math.pi * x) * np.sin(math.pi * y) * e
+
+
+def lattice_fourier_rhs(mask: int, n: int, seed: int, modes: int = 16, kmax: int = 8) -> np.ndarray:
+    """The "fourier" workload per unit square (seeded by seed * 1000 + 100 + bit),
+    in block order; every point on a grid line between squares gets 0 (each
+    square's modes vanish on its edges)."""
+    m = n + 1
+    h = 1.0 / m
+    parts = []
+    for _, _, i0, j0, nx, ny in lattice_blocks(mask, n):
+        I, J = np.meshgrid(i0 + np.arange(nx), j0 + np.arange(ny))
+        f = np.zeros(I.shape)
+        inside = (I % m != 0) & (J % m != 0)
+        for (si, sj) in set(zip((I[inside] // m).tolist(), (J[inside] // m).tolist())):
+            sel = inside & (I // m == si) & (J // m == sj)
+            f[sel] = _square_modes(seed, 100 + si + 8 * sj, I[sel] * h - si, J[sel] * h - sj, modes, kmax)
+        parts.append(f.ravel())
+    return np.concatenate(parts)
