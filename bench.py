@@ -47,7 +47,7 @@ def parse():
                     help="solve the two kappa domains one after the other, or concurrently on two streams")
     ap.add_argument("--config", default="default",
                     choices=["default", "small", "precision", "batching", "serving", "fastsolve", "study",
-                             "neumann", "ncross", "rect", "box", "chain"],
+                             "neumann", "ncross", "rect", "box", "chain", "lattice"],
                     help="default: the 256^2 cross workload; the others run the other workloads as extra lines")
     ap.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
@@ -1046,6 +1046,62 @@ def run_extra(args):
                           lambda: __import__("oracle.strip", fromlist=["x"]).assemble(K, n, 0.0),
                           np.stack([W.strip_fourier_rhs(K, n, s) for s in range(2)]),
                           f"chain of {K} crosses, kappa 0")})
+    elif args.config == "lattice":
+        # general coupled sets (Sec. 2.3-2.4): a 2 x 2 block of coupled squares (four
+        # squares, four links, one junction) and an L-shaped coupled set with two
+        # independent squares, n^2 per square, kappa in {0, -10}, `seeds` fourier
+        # RHS each, FGMRES(m) with the block-diagonal preconditioner
+        from oracle import lattice as LT
+        n, m = args.n, args.restart
+        for name in ("square2x2", "L5"):
+            mask = W.LATTICE_EXAMPLES[name]
+            doms = []
+            fh = {k: np.stack([W.lattice_fourier_rhs(mask, n, s) for s in range(args.seeds)]) for k in (0.0, -10.0)}
+            for kappa in (0.0, -10.0):
+                f = torch.as_tensor(fh[kappa], device="cuda")
+                d = B.Domain(B.make_desc("lattice", n, kappa, nrhs=args.seeds, restart=m, rtol=args.rtol,
+                                         lattice=mask))
+                apply_options(d, args)
+                doms.append((d, f, torch.zeros_like(f)))
+            times, infos = [], []
+            for s in range(args.warmup + args.steps):
+                flush.fill_(float(s))
+                for d, f, p in doms:
+                    d.set_rhs(f)
+                ms, _, out = _timed(lambda: [d.solve(p, check=False) for d, f, p in doms])
+                if s >= args.warmup:
+                    times.append(ms)
+                    for stt, info in out:
+                        infos += info
+            ms = sum(times) / len(times)
+            sol = doms[0][2][:2].cpu().numpy()
+            for d, _, _ in doms:
+                d.close()
+            base = None
+            err = None
+            if not args.no_cpu_baseline:
+                base = cpu_baseline_of(lambda: LT.assemble_grid(mask, n, 0.0), fh[0.0][:2],
+                                       f"lattice {name}, kappa 0")
+                R = __import__("oracle.direct", fromlist=["x"]).Factor(LT.assemble_grid(mask, n, 0.0)).solve(fh[0.0][:2])
+                err = {f"rhs {r}": {"rel_2norm": float(np.linalg.norm(sol[r] - R[r]) / np.linalg.norm(R[r])),
+                                    "maxabs_rel": float(np.abs(sol[r] - R[r]).max() / np.abs(R[r]).max())}
+                       for r in range(2)}
+            coupled, indep = LT.classify(mask)
+            lines.append({"metric": METRIC, "value": 2 * args.seeds / (ms * 1e-3), "unit": "solves/s",
+                          "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic",
+                          "config": {"workload": f"lattice {name}: {len(coupled)} coupled squares, "
+                                                 f"{len(LT.links(mask))} links, {len(LT.junctions(mask))} junctions, "
+                                                 f"{len(indep)} independent squares; {n}^2 per square, kappa 0 and "
+                                                 f"-10, {args.seeds} fourier RHS each",
+                                     "n": n, "restart": m, "rtol": args.rtol, "l2": "flushed before every step"},
+                          "unknowns_per_rhs": W.lattice_total_unknowns(mask, n),
+                          "coupled_unknowns": LT.coupled_size(mask, n),
+                          "iterations_mean": float(np.mean([i["iterations"] for i in infos])),
+                          "residual_max": max(i["residual"] for i in infos),
+                          "all_converged": all(i["status"] == B.FPG_OK for i in infos),
+                          "error_vs_oracle_kappa0": err, "cpu_baseline": base})
     elif args.config == "box":
         # the 3-D extension after Sec. 2.1: fast solve on boxes of n^3 (default 4 x 255^3
         # -- p = 256 per transform -- and 4 x 256^3, p = 257 by Rader), FP64

@@ -35,6 +35,30 @@
  * form, Dirichlet edges, A_c^{-1} or identity preconditioner only (else
  * FPG_EUNSUPPORTED); fpg_block_solve and fpg_autotune are not offered.
  *
+ * General concatenated geometry (geometry = FPG_GEOM_LATTICE; Sec. 2.3-2.4 and
+ * the rule after Alg. "fft_dd_solver": a sub-domain adjacent to only one other
+ * is independent, the others are coupled): any edge-connected set of 2..64 unit
+ * squares [i, i+1] x [j, j+1], 0 <= i, j < 8, given as desc.lattice with bit
+ * i + 8 j set.  A square with one edge neighbour is independent, eliminated
+ * exactly, and owns the grid line it shares with that neighbour; squares with
+ * two or more neighbours are coupled (of two squares, the first is taken as
+ * coupled).  The coupled set -- the coupled squares' n x n interiors, every grid
+ * line shared by two coupled squares (a link, n points) and every lattice
+ * vertex with four squares around it (a junction, one point) -- is solved by
+ * flexible GMRES preconditioned with the block diagonal of its parts (a fast
+ * solve per coupled square, a tridiagonal solve per link, the diagonal of each
+ * junction).  Vector layout: the coupled set first -- coupled squares in bit
+ * order (n x n), the links across vertical edges then across horizontal edges,
+ * each ordered by (j, i) of the left or lower square (n points along the line),
+ * the junctions ordered by the vertex's (Y, X) -- then the independent squares
+ * in bit order, (n+1) x n when the neighbour is west or east, n x (n+1) when it
+ * is south or north, the shared line first (neighbour west or south) or last
+ * (east or north); x fastest in every block.  At most 8 independent squares
+ * with a west or east neighbour and 8 with a south or north one; reduced Schur
+ * form, Dirichlet edges, block-diagonal or identity preconditioner
+ * (FPG_OPT_PRECOND 0 or 1); fpg_block_solve and fpg_autotune are not offered
+ * (else FPG_EUNSUPPORTED; a mask that is not edge-connected is FPG_EINVAL).
+ *
  * Neumann-sided cross (boundary = FPG_BC_NEUMANN_SIDES; the boundary pattern
  * of the paper's precision validation, Sec. 3.1 Eq. "cross_equation"): zero
  * Dirichlet at the four far ends of the arms, zero normal derivative on the
@@ -76,7 +100,13 @@ typedef enum {
   FPG_EBUDGET = 7       /* admission refused: over the memory budget */
 } fpg_status;
 
-typedef enum { FPG_GEOM_L = 0, FPG_GEOM_T = 1, FPG_GEOM_CROSS = 2, FPG_GEOM_CHAIN = 3 } fpg_geometry;
+typedef enum {
+  FPG_GEOM_L = 0,
+  FPG_GEOM_T = 1,
+  FPG_GEOM_CROSS = 2,
+  FPG_GEOM_CHAIN = 3,
+  FPG_GEOM_LATTICE = 4
+} fpg_geometry;
 
 typedef enum {
   FPG_BC_DIRICHLET = 0,     /* every outer edge Dirichlet; vertex-centred grid, h = 1/(n+1) */
@@ -101,6 +131,7 @@ typedef struct {
   int32_t schur_mode;        /* fpg_schur_mode */
   int32_t boundary;          /* fpg_boundary (0 = all Dirichlet) */
   int32_t chain;             /* FPG_GEOM_CHAIN: number of crosses K, 2..5; other geometries: 0 */
+  uint64_t lattice;          /* FPG_GEOM_LATTICE: the squares, bit i + 8 j; other geometries: 0 */
 } fpg_domain_desc;
 
 typedef struct {
@@ -386,7 +417,13 @@ typedef enum {
    * carried across the CTAs through distributed shared memory, v read once
    * and z written once.  0: the three-kernel path.  Other lengths, FP64 and
    * blocks that are not 16-byte aligned always take the other paths. */
-  FPG_OPT_CLUSTER_FASTSOLVE = 12
+  FPG_OPT_CLUSTER_FASTSOLVE = 12,
+  /* Launch shapes of the centre's fast solve, as fpg_autotune sets them: line
+   * pairs per CTA of the generic FFT engine (0: the size-specialised kernels
+   * where compiled, else the built-in choice; 1, 2, 4 or 8), and warps (modes)
+   * per CTA of the Thomas kernel (0: 8; 4 or 8). */
+  FPG_OPT_DST_PAIRS = 13,
+  FPG_OPT_THOMAS_WARPS = 14
 } fpg_option;
 
 /* Move a domain to another CUDA stream (a cudaStream_t; NULL = the default

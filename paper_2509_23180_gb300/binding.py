@@ -13,7 +13,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfpg.so")
 
-GEOMETRY = {"L": 0, "T": 1, "cross": 2, "chain": 3}
+GEOMETRY = {"L": 0, "T": 1, "cross": 2, "chain": 3, "lattice": 4}
 BOUNDARY = {"dirichlet": 0, "neumann_sides": 1}
 RECT = {"dirichlet": 0, "neumann": 1, "periodic": 2}
 SCHUR = {"reduced": 0, "literal": 1}
@@ -33,6 +33,8 @@ OPT_ARM_REFINE = 9
 OPT_DST_BULK = 10
 OPT_WAIT_LIMIT = 11
 OPT_CLUSTER_FASTSOLVE = 12
+OPT_DST_PAIRS = 13
+OPT_THOMAS_WARPS = 14
 PRECOND = {"fft": 0, "none": 1, "jacobi": 2}
 PHASES = ("precond", "schur", "arnoldi", "givens", "cycle_end", "setup_finish", "residual",
           "dst_forward", "thomas", "dst_inverse", "fast_solve_fused")
@@ -51,7 +53,8 @@ class DomainDesc(ctypes.Structure):
     _fields_ = [("geometry", ctypes.c_int32), ("n", ctypes.c_int32), ("kappa", ctypes.c_double),
                 ("nrhs", ctypes.c_int32), ("restart", ctypes.c_int32), ("rtol", ctypes.c_double),
                 ("max_iters", ctypes.c_int32), ("precond_precision", ctypes.c_int32),
-                ("schur_mode", ctypes.c_int32), ("boundary", ctypes.c_int32), ("chain", ctypes.c_int32)]
+                ("schur_mode", ctypes.c_int32), ("boundary", ctypes.c_int32), ("chain", ctypes.c_int32),
+                ("lattice", ctypes.c_uint64)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -168,13 +171,15 @@ def _check(status: int, where: str) -> int:
 
 
 def make_desc(geometry="cross", n=64, kappa=0.0, nrhs=1, restart=30, rtol=1e-10, max_iters=None,
-              precond_precision=64, schur_mode="reduced", boundary="dirichlet", chain=0) -> DomainDesc:
+              precond_precision=64, schur_mode="reduced", boundary="dirichlet", chain=0,
+              lattice=0) -> DomainDesc:
     if max_iters is None:
         max_iters = 50 * restart
     return DomainDesc(GEOMETRY[geometry] if isinstance(geometry, str) else int(geometry), int(n), float(kappa),
                       int(nrhs), int(restart), float(rtol), int(max_iters), int(precond_precision),
                       SCHUR[schur_mode] if isinstance(schur_mode, str) else int(schur_mode),
-                      BOUNDARY[boundary] if isinstance(boundary, str) else int(boundary), int(chain))
+                      BOUNDARY[boundary] if isinstance(boundary, str) else int(boundary), int(chain),
+                      int(lattice))
 
 
 def unknowns(desc: DomainDesc) -> int:
@@ -205,7 +210,7 @@ class Domain:
         self.nbytes = workspace_bytes(desc)
         self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
         self.N = unknowns(desc)
-        self.nc = desc.n * desc.n if desc.geometry != 3 else ((2 * desc.chain - 1) * (desc.n + 1) - 1) * desc.n
+        self.nc = {3: ((2 * desc.chain - 1) * (desc.n + 1) - 1) * desc.n, 4: None}.get(desc.geometry, desc.n * desc.n)
         h = _P()
         _check(self.lib.fpg_create_domain(ctypes.byref(desc), _ptr(self.workspace), self.nbytes,
                                           self.stream.cuda_stream, ctypes.byref(h)), "fpg_create_domain")

@@ -12,6 +12,7 @@
 
 #include "fpg_host_tables.h"
 #include "fpg_internal.cuh"
+#include "fpg_lattice_host.h"
 
 namespace fpg {
 
@@ -139,6 +140,11 @@ struct Layout {
   int arm_slots[4];
   int chain = 0;  // K of a chain of crosses (0: L, T or cross)
   ChainGeom cg;   // the chain's row width and arm offsets
+  int lattice = 0;  // 1: general concatenated geometry (FPG_GEOM_LATTICE)
+  LatticeGeom lg;
+  // the arm kernels (residual, update) take up to four arms, slots W, E (n+1 wide)
+  // and S, N (n+1 tall); the arms of a chain or a lattice go in several groups
+  std::vector<ArmOffsets> arm_groups;
 };
 
 bool make_layout(const fpg_domain_desc* d, Layout* L) {
@@ -149,6 +155,32 @@ bool make_layout(const fpg_domain_desc* d, Layout* L) {
   L->na = (long long)n * as;
   L->ao.as = as;
   L->ao.bc = d->boundary == FPG_BC_NEUMANN_SIDES ? 1 : 0;
+  L->arm_groups.clear();
+  if (d->geometry == FPG_GEOM_LATTICE) {
+    if (!lattice_shape(d->lattice, n, &L->lg)) return false;
+    const LatticeGeom& g = L->lg;
+    L->lattice = 1;
+    L->nc = g.nc;
+    L->ntot = g.ntot;
+    L->narms = g.nfaces;
+    L->armmask = 0;
+    for (int i = 0; i < 4; ++i) L->arm_slots[i] = i;
+    const int groups = (std::max(g.nwe, g.nsn) + 1) / 2;
+    for (int k = 0; k < groups; ++k) {
+      ArmOffsets ao = L->ao;
+      ao.off[0] = 2 * k < g.nwe ? g.we_off[2 * k] : -1;
+      ao.off[1] = 2 * k + 1 < g.nwe ? g.we_off[2 * k + 1] : -1;
+      ao.off[2] = 2 * k < g.nsn ? g.sn_off[2 * k] : -1;
+      ao.off[3] = 2 * k + 1 < g.nsn ? g.sn_off[2 * k + 1] : -1;
+      L->arm_groups.push_back(ao);
+    }
+    if (L->arm_groups.empty()) {
+      for (int a = 0; a < 4; ++a) L->ao.off[a] = -1;
+    } else {
+      L->ao = L->arm_groups[0];
+    }
+    return true;
+  }
   if (d->geometry == FPG_GEOM_CHAIN) {
     const int K = d->chain;
     L->chain = K;
@@ -166,6 +198,11 @@ bool make_layout(const fpg_domain_desc* d, Layout* L) {
     L->ao.off[3] = L->cg.off[2 + K];
     for (int i = 0; i < 4; ++i) L->arm_slots[i] = i;
     L->ntot = L->nc + (long long)L->narms * L->na;
+    for (int g = 0; g < K; ++g) {  // (W, E, S_1, N_1), (-, -, S_2, N_2), ...
+      ArmOffsets ao = L->ao;
+      if (g > 0) ao.off[0] = ao.off[1] = -1, ao.off[2] = L->cg.off[2 + g], ao.off[3] = L->cg.off[2 + K + g];
+      L->arm_groups.push_back(ao);
+    }
     return true;
   }
   static const int slots_cross[] = {0, 1, 2, 3};
@@ -190,12 +227,22 @@ bool make_layout(const fpg_domain_desc* d, Layout* L) {
     off += L->na;
   }
   L->ntot = off;
+  L->arm_groups.push_back(L->ao);
   return true;
 }
 
 fpg_status validate(const fpg_domain_desc* d) {
   if (!d) return FPG_EINVAL;
-  if (d->geometry < 0 || d->geometry > 3) return FPG_EINVAL;
+  if (d->geometry < 0 || d->geometry > 4) return FPG_EINVAL;
+  if (d->geometry == FPG_GEOM_LATTICE) {
+    LatticeGeom g;
+    if (d->chain != 0 || d->n < 2 || d->n > 4096 || !lattice_shape(d->lattice, d->n, &g)) return FPG_EINVAL;
+    if (g.nwe > 8 || g.nsn > 8) return FPG_EUNSUPPORTED;  // one batch of the arm kernels per shape
+    if (d->boundary != FPG_BC_DIRICHLET || d->schur_mode != FPG_SCHUR_REDUCED) return FPG_EUNSUPPORTED;
+    if (g.ntot > (1LL << 31) - 1) return FPG_EUNSUPPORTED;  // 32-bit neighbour tables
+  } else if (d->lattice != 0) {
+    return FPG_EINVAL;
+  }
   if (d->geometry == FPG_GEOM_CHAIN) {
     if (d->chain < 2 || d->chain > 5) return FPG_EINVAL;
     if (d->boundary != FPG_BC_DIRICHLET || d->schur_mode != FPG_SCHUR_REDUCED) return FPG_EUNSUPPORTED;
@@ -255,6 +302,7 @@ struct fpg_domain {
   bool refining = false;
   int* resume_dev = nullptr;
   int* err_dev = nullptr;   // status word of the bounded device waits (1: a wait gave up)
+  LatticeDev lat;           // FPG_GEOM_LATTICE: neighbour, face and coupling tables
   void* scratch;
   KrylovState ks;
   int gx, gxf;
@@ -416,7 +464,28 @@ void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostP
     D->lit_in = D->lit_out = nullptr;
   }
   p = c.take(sizeof(double) * nrhs * std::max(4, L.narms) * n); if (D) D->corr = (double*)p;
-  const long long sc = (long long)nrhs * std::max(L.nc, 2 * L.na);
+  long long sc = (long long)nrhs * std::max(L.nc, 2 * L.na);
+  if (L.lattice) {
+    // the arm batches hold up to 8 blocks each; the coupled squares go 8 at a time
+    const LatticeGeom& g = L.lg;
+    sc = std::max(sc, (long long)nrhs * L.na * std::max(g.nwe, g.nsn));
+    const long long nc = g.nc, nt = g.ntot;
+    p = c.take(sizeof(int4) * nc);             if (D) D->lat.nbr = (const int4*)p;
+    p = c.take(sizeof(int2) * nc);             if (D) D->lat.cf = (const int2*)p;
+    p = c.take(sizeof(int2) * nc);             if (D) D->lat.anb = (const int2*)p;
+    p = c.take(sizeof(int2) * std::max(1, g.nfaces)); if (D) D->lat.faces = (const int2*)p;
+    p = c.take(sizeof(int4) * nt);             if (D) D->lat.gnbr = (const int4*)p;
+    p = c.take(sizeof(int) * nt);              if (D) D->lat.gcn = (const int*)p;
+    p = c.take(sizeof(double) * n);            if (D) D->lat.lpiv = (const double*)p;
+    if (D) {
+      D->lat.nc = nc;
+      D->lat.link_base = g.link_base;
+      D->lat.junc_base = g.junc_base;
+      D->lat.nfaces = g.nfaces;
+      D->lat.nlinks = g.nlinks;
+      D->lat.njunc = g.njunc;
+    }
+  }
   p = c.take(sizeof(double) * sc);            if (D) D->scratch = p;
   p = c.take(sizeof(double) * nrhs);          if (D) D->gres = (double*)p;
   p = c.take(sizeof(int) * 4);                if (D) D->resume_dev = (int*)p;
@@ -530,6 +599,21 @@ fpg_status precond(fpg_domain* D, const double* v, void* z, int nvec, const int*
     return FPG_OK;
   }
   int nl = 0;
+  if (L.lattice) {
+    // block diagonal of the coupled set: the coupled squares' fast solves, 8 per
+    // launch, then the links' and junctions' own operators
+    const FastSolveTables& tc = D->prec == 64 ? D->tC64 : D->tC32;
+    const LatticeGeom& g = L.lg;
+    for (int k0 = 0; k0 < g.ncsq; k0 += 8) {
+      BatchDesc bd{L.nc, {0, 0, 0, 0}, 0};
+      for (int k = k0; k < g.ncsq && k < k0 + 8; ++k) bd.off[bd.nper++] = g.sq_off[k];
+      FPG_CUDA_TRY(launch_fast_solve(D->prec, D->prec, tc, D->LC, v, bd, z, bd, nvec * bd.nper, D->scratch, active,
+                                     bd.nper, D->st, &nl));
+    }
+    FPG_CUDA_TRY(launch_lattice_skeleton(v, z, D->prec, D->lat, L.n, D->delta, D->desc.kappa, active, nvec, D->st));
+    count(D, 0, nl + 1);
+    return FPG_OK;
+  }
   if (L.chain) {  // FPG_OPT_PRECOND = 3
     // block-diagonal over the row's squares: 2K - 2 squares of n + 1 columns, then the last
     const FastSolveTables& ta = D->prec == 64 ? D->tA64 : D->tA32;
@@ -616,21 +700,15 @@ fpg_status arm_solves(fpg_domain* D, const double* in, double* out, int nvec, in
 fpg_status arm_solves_refined(fpg_domain* D, const double* in, double* out, double* work, int nvec, int phase) {
   const Layout& L = D->L;
   FPG_TRY(arm_solves(D, in, out, nvec, phase));
-  // the arm kernels take up to four arms (W, E, S, N slots) per launch: a chain's
-  // arms go in K groups (W, E, S_1, N_1), (-, -, S_2, N_2), ...
-  const int groups = L.chain ? L.chain : 1;
-  for (int it = 0; it < D->arm_refine; ++it) {  // out += A_a^{-1} (in - A_a out)
-    for (int g = 0; g < groups; ++g) {
-      ArmOffsets ao = L.ao;
-      if (L.chain && g > 0) ao.off[0] = ao.off[1] = -1, ao.off[2] = L.cg.off[2 + g], ao.off[3] = L.cg.off[2 + L.chain + g];
+  // the arm kernels take up to four arms (W, E, S, N slots) per launch: the arms
+  // of a chain or a lattice go group by group
+  const int groups = (int)L.arm_groups.size();
+  for (int it = 0; it < D->arm_refine && groups > 0; ++it) {  // out += A_a^{-1} (in - A_a out)
+    for (const ArmOffsets& ao : L.arm_groups)
       FPG_CUDA_TRY(launch_arm_residual(in, out, work, L.ntot, L.n, D->delta, D->desc.kappa, ao, nvec, D->gxf, D->st));
-    }
     FPG_TRY(arm_solves(D, work, work, nvec, phase));
-    for (int g = 0; g < groups; ++g) {
-      ArmOffsets ao = L.ao;
-      if (L.chain && g > 0) ao.off[0] = ao.off[1] = -1, ao.off[2] = L.cg.off[2 + g], ao.off[3] = L.cg.off[2 + L.chain + g];
+    for (const ArmOffsets& ao : L.arm_groups)
       FPG_CUDA_TRY(launch_arm_add(out, work, L.ntot, L.n, ao, nvec, D->gxf, D->st));
-    }
     count(D, phase, 2 * groups);
   }
   return FPG_OK;
@@ -668,6 +746,12 @@ fpg_status schur_corr(fpg_domain* D, const void* z, int zprec, int nvec, const i
 // a2 on nvec centre vectors (nvec <= nrhs): z (zprec) -> w.
 fpg_status schur(fpg_domain* D, const void* z, int zprec, double* w, int nvec, const int* active) {
   const Layout& L = D->L;
+  if (L.lattice) {
+    FPG_CUDA_TRY(launch_lattice_schur(z, zprec, L.nc, w, L.nc, D->lat, L.n, D->delta, D->desc.kappa, D->ctab,
+                                      D->corr, active, nvec, D->gx, D->st));
+    count(D, 1, D->lat.nfaces > 0 ? 2 : 1);
+    return FPG_OK;
+  }
   FPG_TRY(schur_corr(D, z, zprec, nvec, active));
   if (L.chain)
     FPG_CUDA_TRY(launch_chain_stencil(z, zprec, L.nc, w, L.nc, L.cg, D->delta, D->desc.kappa, D->corr, active, nvec,
@@ -683,6 +767,9 @@ fpg_status schur(fpg_domain* D, const void* z, int zprec, double* w, int nvec, c
 cudaError_t global_apply(fpg_domain* D, const double* p, double* y, const double* f, int nvec, double* rel_out,
                          double* fnorm_out, double rtol, double* tolabs) {
   const Layout& L = D->L;
+  if (L.lattice)
+    return launch_lattice_global_apply(p, y, f, L.ntot, D->lat, D->delta, D->desc.kappa, D->ks.part, kGmax, nvec,
+                                       D->gxf, rel_out, fnorm_out, rtol, tolabs, D->st);
   if (L.chain)
     return launch_chain_global_apply(p, y, f, L.ntot, L.cg, D->delta, D->desc.kappa, D->ks.part, kGmax, nvec, D->gxf,
                                      rel_out, fnorm_out, rtol, tolabs, D->st);
@@ -734,7 +821,9 @@ fpg_status setup_common(fpg_domain* D, double* p, bool keep_iters) {
   count(D, 5, 2);
   // Alg. 1 steps 1-3: q_a = A_a^{-1} f_a (into p's arm blocks), f'_c = f_c - sum R_ca q_a
   FPG_TRY(arm_solves_refined(D, D->f, p, D->tmp2, nrhs, 5));
-  if (L.chain)
+  if (L.lattice)
+    FPG_CUDA_TRY(launch_lattice_reduce_rhs(D->f, p, L.ntot, D->lat, D->delta, k.fc, nrhs, D->gx, D->st));
+  else if (L.chain)
     FPG_CUDA_TRY(launch_chain_reduce_rhs(D->f, p, L.ntot, L.cg, D->delta, k.fc, nrhs, D->gx, D->st));
   else
     FPG_CUDA_TRY(launch_reduce_rhs(D->f, p, L.ntot, L.n, D->delta, L.ao, k.fc, nrhs, D->gx, D->st));
@@ -790,7 +879,8 @@ fpg_status issue_cycle(fpg_domain* D) {
     ev_end(D, e);
     const int csz = D->use_cluster ? (D->tune_csz > 0 ? D->tune_csz : arnoldi_cluster_size(L.nc)) : 0;
     // the register-resident step fuses the cross's stencil: chains take the global-w step
-    const int ept = (csz > 0 && D->arnoldi_mode == 1 && !L.chain) ? arnoldi_reg_ept(L.nc, csz, D->tune_nt) : 0;
+    const int ept = (csz > 0 && D->arnoldi_mode == 1 && !L.chain && !L.lattice)
+                        ? arnoldi_reg_ept(L.nc, csz, D->tune_nt) : 0;
     if (ept > 0) {
       // a2's interface part, then one launch for a2's stencil + a3 + a4
       e = ev_begin(D, 1);
@@ -922,7 +1012,9 @@ fpg_status stage_finish(fpg_domain* D) {
   double* p = D->p_cur;
   // Alg. 1 steps 5-7: f'_a = f_a - R_ac p_c, p_a = A_a^{-1} f'_a, p_c = u
   int e = ev_begin(D, 5);
-  if (L.chain)
+  if (L.lattice)
+    FPG_CUDA_TRY(launch_lattice_arm_rhs(D->f, k.u, L.ntot, D->lat, D->delta, D->tmp, p, nrhs, D->gxf, D->st));
+  else if (L.chain)
     FPG_CUDA_TRY(launch_chain_arm_rhs(D->f, k.u, L.ntot, L.cg, D->delta, D->tmp, p, nrhs, D->gxf, D->st));
   else
     FPG_CUDA_TRY(launch_arm_rhs(D->f, k.u, L.ntot, L.n, D->delta, L.ao, D->tmp, p, nrhs, D->gxf, D->st));
@@ -1195,6 +1287,9 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
     for (int q = 0; q < 2 * K - 2; ++q) D->cb1.off[D->cb1.nper++] = (long long)q * (n + 1);
     D->cb2 = BatchDesc{L.nc, {(long long)(2 * K - 2) * (n + 1), 0, 0, 0}, 1};
     D->LR = LineLayout{n, nxc, nxc, 1};
+  } else if (L.lattice) {
+    for (int k = 0; k < L.lg.nwe; ++k) D->we.off[D->we.nper++] = L.lg.we_off[k];
+    for (int k = 0; k < L.lg.nsn; ++k) D->sn.off[D->sn.nper++] = L.lg.sn_off[k];
   } else {
     for (int a = 0; a < 4; ++a) {
       if (L.ao.off[a] < 0) continue;
@@ -1243,7 +1338,7 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   std::vector<float> W32(hp.W.begin(), hp.W.end()), s32(hp.sinp.begin(), hp.sinp.end()),
       B32(hp.Bhat.begin(), hp.Bhat.end()), d32(hp.dense.begin(), hp.dense.end());
   int arms[12] = {0};
-  for (int i = 0; i < L.narms; ++i) arms[i] = L.chain ? i : L.arm_slots[i];
+  for (int i = 0; i < L.narms && i < 12; ++i) arms[i] = L.chain ? i : L.arm_slots[i % 4];
   auto cp = [&](const void* dst, const void* src, size_t b) {
     return cudaMemcpyAsync(const_cast<void*>(dst), src, b, cudaMemcpyHostToDevice, D->st);
   };
@@ -1299,6 +1394,17 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
     if (!err) err = cp(D->tC32.cl_wseed, cl_wseed.data(), sizeof(float) * cl_wseed.size());
   } else {
     D->tC32.cl_sigma = D->tC32.cl_wseed = nullptr;  // the kernel does not take this length
+  }
+  LatticeHost lh;
+  if (L.lattice) {
+    if (!lattice_tables(desc->lattice, n, D->delta, desc->kappa, &lh)) err = cudaErrorInvalidValue;
+    if (!err) err = cp(D->lat.nbr, lh.nbr.data(), sizeof(int4) * lh.nbr.size());
+    if (!err) err = cp(D->lat.cf, lh.cf.data(), sizeof(int2) * lh.cf.size());
+    if (!err) err = cp(D->lat.anb, lh.anb.data(), sizeof(int2) * lh.anb.size());
+    if (!err && !lh.faces.empty()) err = cp(D->lat.faces, lh.faces.data(), sizeof(int2) * lh.faces.size());
+    if (!err) err = cp(D->lat.gnbr, lh.gnbr.data(), sizeof(int4) * lh.gnbr.size());
+    if (!err) err = cp(D->lat.gcn, lh.gcn.data(), sizeof(int) * lh.gcn.size());
+    if (!err) err = cp(D->lat.lpiv, lh.lpiv.data(), sizeof(double) * lh.lpiv.size());
   }
   if (!err) err = cp(D->ctab, ct.data(), sizeof(double) * ct.size());
   if (!err) err = cp(D->gsc, gs.data(), sizeof(double) * gs.size());
@@ -1429,7 +1535,7 @@ fpg_status fpg_apply_precond(fpg_domain* d, const double* v, void* z, int32_t nv
 fpg_status fpg_block_solve(fpg_domain* d, int32_t block, const double* v, double* z, int32_t nvec) {
   if (!d || !v || !z || nvec < 0 || block < 0 || block > 4) return FPG_EINVAL;
   const Layout& L = d->L;
-  if (L.chain) return FPG_EUNSUPPORTED;
+  if (L.chain || L.lattice) return FPG_EUNSUPPORTED;
   if (block > 0 && L.ao.off[block - 1] < 0) return FPG_EINVAL;
   const long long len = block == 0 ? L.nc : L.na;
   const LineLayout& LL = block == 0 ? d->LC : (block <= 2 ? d->LWE : d->LSN);
@@ -1515,7 +1621,7 @@ fpg_status fpg_apply_global(fpg_domain* d, const double* p, double* y, int32_t n
 
 fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out) {
   if (!d) return FPG_EINVAL;
-  if (d->L.chain) return FPG_EUNSUPPORTED;
+  if (d->L.chain || d->L.lattice) return FPG_EUNSUPPORTED;
   drop_graph(d);
   const Layout& L = d->L;
   KrylovState& k = d->ks;
@@ -1527,9 +1633,11 @@ fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out) {
   // timing inputs: the first two basis vectors and w (contents do not affect the time)
   FPG_CUDA_TRY(cudaMemsetAsync(k.V, 0, sizeof(double) * (size_t)2 * nrhs * L.nc, d->st));
   FPG_CUDA_TRY(cudaMemsetAsync(k.w, 0, sizeof(double) * (size_t)nrhs * L.nc, d->st));
+  // fn returns true when every launch was accepted; a shape whose launch fails
+  // (even one the launch consumes the error of) is never chosen
   auto time_it = [&](auto&& fn, int reps) -> float {
-    fn();  // warm-up (also sets kernel attributes)
-    if (cudaGetLastError() != cudaSuccess) return 1e30f;
+    const bool ok = fn();  // warm-up (also sets kernel attributes)
+    if (!ok || cudaGetLastError() != cudaSuccess) return 1e30f;
     cudaEventRecord(e0, d->st);
     for (int i = 0; i < reps; ++i) fn();
     cudaEventRecord(e1, d->st);
@@ -1542,12 +1650,12 @@ fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out) {
   int best_q = 0, best_mt = 0;
   float best = 1e30f;
   static const int qs[] = {0, 1, 2, 4, 8};  // 0: size-specialised kernels where compiled, else built-in Q
-  static const int mts[] = {4, 8, 16};
+  static const int mts[] = {4, 8};  // the Thomas kernel's launch bound: 8 warps
   for (int q : qs) {
     for (int mt : mts) {
       tb.q = q;
       tb.mt = mt;
-      const float t = time_it([&] { precond(d, k.V, k.Z, nrhs, nullptr); }, 3);
+      const float t = time_it([&] { return precond(d, k.V, k.Z, nrhs, nullptr) == FPG_OK; }, 3);
       if (t < best) { best = t; best_q = q; best_mt = mt; }
     }
   }
@@ -1567,13 +1675,13 @@ fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out) {
         if (d->arnoldi_mode != 1 && nt != nts[0]) continue;
         const float t = time_it([&] {
           if (ept > 0)
-            launch_arnoldi_reg(c, nt, k.V, (long long)nrhs * L.nc, k.w, nullptr, 64, nullptr, 0, 0.0, 0.0, 0,
+            return launch_arnoldi_reg(c, nt, k.V, (long long)nrhs * L.nc, k.w, nullptr, 64, nullptr, 0, 0.0, 0.0, 0,
                                k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j, nrhs, k.H, hcol, hrhs, nullptr, nullptr,
-                               nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0, 0, d->st);
+                               nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0, 0, d->st) == cudaSuccess;
           else
-            launch_arnoldi_cluster(c, k.V, (long long)nrhs * L.nc, k.w, k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc,
+            return launch_arnoldi_cluster(c, k.V, (long long)nrhs * L.nc, k.w, k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc,
                                    j, nrhs, k.H, hcol, hrhs, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
-                                   nullptr, nullptr, 0, 0, d->st);
+                                   nullptr, nullptr, 0, 0, d->st) == cudaSuccess;
         }, 3);
         if (t < best_a) { best_a = t; best_c = c; best_nt = nt; }
       }
@@ -1608,13 +1716,14 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_FUSED_FASTSOLVE:
-      if (d->L.chain && value) return FPG_EUNSUPPORTED;  // the one-pass kernel takes whole square blocks
+      if ((d->L.chain || d->L.lattice) && value) return FPG_EUNSUPPORTED;  // the one-pass kernel takes whole square blocks
       for (auto* t : {&d->tC64, &d->tC32, &d->tA64, &d->tA32, &d->tA64e}) t->fused = value != 0;
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_PRECOND:
       if (value < 0 || value > 3) return FPG_EINVAL;
-      if (d->L.chain && value == 2) return FPG_EUNSUPPORTED;  // the Jacobi diagonal is written for the cross
+      if ((d->L.chain || d->L.lattice) && value == 2) return FPG_EUNSUPPORTED;  // Jacobi: written for the cross
+      if (d->L.lattice && value == 3) return FPG_EUNSUPPORTED;  // a lattice's default is already block diagonal
       if (!d->L.chain && value == 3) return FPG_EUNSUPPORTED;  // the squares of a coupled row: chains only
       d->precond_kind = value;
       drop_graph(d);
@@ -1627,6 +1736,16 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
     case FPG_OPT_DST_BULK:
       if (value < 0 || value > 1) return FPG_EINVAL;
       for (auto* tt : {&d->tC64, &d->tC32, &d->tA64, &d->tA32, &d->tA64e}) tt->bulk = value;
+      drop_graph(d);
+      return FPG_OK;
+    case FPG_OPT_DST_PAIRS:
+      if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8) return FPG_EINVAL;
+      for (auto* t : {&d->tC64, &d->tC32}) t->q = value;
+      drop_graph(d);
+      return FPG_OK;
+    case FPG_OPT_THOMAS_WARPS:
+      if (value != 0 && value != 4 && value != 8) return FPG_EINVAL;
+      for (auto* t : {&d->tC64, &d->tC32}) t->mt = value;
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_CLUSTER_FASTSOLVE:

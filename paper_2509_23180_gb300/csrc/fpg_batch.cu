@@ -76,7 +76,7 @@ struct TicketState {
 bool same_key(const fpg_domain_desc& a, const fpg_domain_desc& b) {
   return a.geometry == b.geometry && a.n == b.n && a.kappa == b.kappa && a.restart == b.restart &&
          a.rtol == b.rtol && a.max_iters == b.max_iters && a.precond_precision == b.precond_precision &&
-         a.schur_mode == b.schur_mode && a.boundary == b.boundary && a.chain == b.chain;
+         a.schur_mode == b.schur_mode && a.boundary == b.boundary && a.chain == b.chain && a.lattice == b.lattice;
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }

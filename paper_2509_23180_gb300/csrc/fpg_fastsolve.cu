@@ -384,12 +384,13 @@ k_thomas_long_smem(T* __restrict__ scratch, int n, int ns, const T* __restrict__
 }
 
 // Launch the Thomas solves: one warp per (block, mode), wpb warps per CTA
-// (0: 8, fewer when the per-warp staging buffers would pass 96 KB), rows per
-// lane C = the smallest compiled value covering ns / 32.
+// (0: 8; at most 8, the register kernel's launch bound of 256 threads; fewer
+// when the per-warp staging buffers would pass 96 KB), rows per lane C = the
+// smallest compiled value covering ns / 32.
 template <typename T>
 cudaError_t launch_thomas(T* scratch, int n, int ns, const T* rpiv, const T* mneg, int nblk, const int* active,
                           int nper_active, cudaStream_t st, int wpb) {
-  if (wpb <= 0) wpb = 8;
+  if (wpb <= 0 || wpb > 8) wpb = 8;
   const long long warps = (long long)nblk * n;
   const int need = (ns + 31) / 32;
 #define FPG_THOMAS_C(CV)                                                                                    \
@@ -592,7 +593,11 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
     dim3 grid((L.ns + lpb - 1) / lpb, nblk);
     k_dense_forward<T><<<grid, kFsThreads, smem, st>>>(in, ib, L, n, (const T*)pl.dense, scratch, lpb, active,
                                                       nper_active);
-    launch_thomas<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st, tb.mt);
+    {
+      const cudaError_t te = launch_thomas<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active,
+                                              nper_active, st, tb.mt);
+      if (te != cudaSuccess) return te;
+    }
     k_dense_inverse<T, To><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, n, (const T*)pl.dense, lpb,
                                                           active, nper_active);
     return cudaGetLastError();
@@ -605,7 +610,11 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
     if (e != cudaSuccess) return e;
     if (ev) record_event(ev[1], st);
     if (ev) record_event(ev[2], st);
-    launch_thomas<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st, tb.mt);
+    {
+      const cudaError_t te = launch_thomas<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active,
+                                              nper_active, st, tb.mt);
+      if (te != cudaSuccess) return te;
+    }
     if (ev) record_event(ev[3], st);
     if (ev) record_event(ev[4], st);
     e = lines_inv<T, To>(pl, scratch, out, ob, L, nblk, active, nper_active, st);
@@ -630,7 +639,8 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
   if (e != cudaSuccess) return e;
   if (ev) record_event(ev[1], st);
   if (ev) record_event(ev[2], st);
-  launch_thomas<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st, tb.mt);
+  e = launch_thomas<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st, tb.mt);
+  if (e != cudaSuccess) return e;
   if (ev) record_event(ev[3], st);
   if (ev) record_event(ev[4], st);
   const int oprec = sizeof(To) == 8 ? 64 : 32;

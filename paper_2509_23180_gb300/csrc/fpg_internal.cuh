@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "fpg.h"
 #include "fpg_dst.cuh"
 
@@ -90,6 +92,63 @@ struct ChainGeom {
 // G_a = delta^2 Q diag(g_k) Q^T = Toeplitz-plus-Hankel with entries
 // T(|i-j|) - H(i+j) (0-based i, j), stored as T[0..2n+1] followed by H[0..2n-1]:
 // DST-I arms H(m) = T(m+2); DCT-II arms H(m) = -T(m+1).
+// A general concatenated geometry (FPG_GEOM_LATTICE, fpg_lattice.cu): counts and
+// block offsets.  The coupled set -- coupled squares (n x n each, offsets sq_off),
+// links (n points each, from link_base) and junctions (one point each, from
+// junc_base) -- is the prefix [0, nc) of a full vector; the independent squares
+// follow, those whose neighbour is west or east ((n+1) x n, we_off) and those
+// whose neighbour is south or north (n x (n+1), sn_off).
+struct LatticeGeom {
+  int n = 0, ncsq = 0, nlinks = 0, njunc = 0, nfaces = 0, nwe = 0, nsn = 0;
+  long long nc = 0, ntot = 0, link_base = 0, junc_base = 0;
+  long long sq_off[64] = {0};
+  long long we_off[8] = {0}, sn_off[8] = {0};
+};
+// lattice_shape() and lattice_tables() (fpg_lattice_host.h) fill it; false: the
+// mask is not an edge-connected set of at least two squares.
+
+// Host tables of a lattice.  Coupled set (length nc): nbr = coupled indices of the
+// W, E, S, N neighbours (-1: not in the coupled set); cf = up to two interface
+// corrections (index face * n + position, -1: none); anb = global indices of up
+// to two neighbouring points of independent squares.  Full vector (length ntot):
+// gnbr = global indices of the four neighbours (-1: outside, zero Dirichlet);
+// gcn = for a point of an independent square, its neighbour in the coupled set
+// (-1: none).  faces = (offset of the coupled square, side 0 W / 1 E / 2 S / 3 N)
+// facing each independent square; lpiv = reciprocal Thomas pivots of a link's
+// own operator tridiag(delta, -4 delta + kappa, delta).
+struct LatticeHost {
+  std::vector<int4> nbr, gnbr;
+  std::vector<int2> cf, anb, faces;
+  std::vector<int> gcn;
+  std::vector<double> lpiv;
+};
+
+// The same tables in the device workspace.
+struct LatticeDev {
+  long long nc = 0, link_base = 0, junc_base = 0;
+  int nfaces = 0, nlinks = 0, njunc = 0;
+  const int4* nbr = nullptr;
+  const int2* cf = nullptr;
+  const int2* anb = nullptr;
+  const int2* faces = nullptr;
+  const int4* gnbr = nullptr;
+  const int* gcn = nullptr;
+  const double* lpiv = nullptr;
+};
+cudaError_t launch_lattice_schur(const void* z, int zprec, long long zstride, double* w, long long wstride,
+                                 const LatticeDev& t, int n, double delta, double kappa, const double* ctab,
+                                 double* corr, const int* active, int nrhs, int gx, cudaStream_t st);
+cudaError_t launch_lattice_skeleton(const double* v, void* z, int zprec, const LatticeDev& t, int n, double delta,
+                                    double kappa, const int* active, int nrhs, cudaStream_t st);
+cudaError_t launch_lattice_reduce_rhs(const double* f, const double* q, long long ntot, const LatticeDev& t,
+                                      double delta, double* fc, int nrhs, int gx, cudaStream_t st);
+cudaError_t launch_lattice_arm_rhs(const double* f, const double* u, long long ntot, const LatticeDev& t,
+                                   double delta, double* out, double* p, int nrhs, int gx, cudaStream_t st);
+cudaError_t launch_lattice_global_apply(const double* p, double* y, const double* f, long long ntot,
+                                        const LatticeDev& t, double delta, double kappa, double* part, int gmax,
+                                        int nrhs, int gx, double* rel_out, double* fnorm_out, double rtol,
+                                        double* tolabs, cudaStream_t st);
+
 struct SchurTables {
   const double* ctab;
 };
