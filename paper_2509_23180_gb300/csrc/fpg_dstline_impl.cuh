@@ -434,12 +434,26 @@ k_dst_lines_fwd(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPl
   const double* src = in + boff(ib, b);
   constexpr int LP = S::LP;
   if (vec) {  // rows contiguous (st == 1) and 16-byte aligned: two values per load
-    for (int i = threadIdx.x; i < Q * n; i += NT) {
-      const int l = i / (n / 2), t2 = i - l * (n / 2);
-      double2 v = make_double2(0.0, 0.0);
-      if (l < nl) v = *reinterpret_cast<const double2*>(src + (long long)(s0 + l) * L.ss + 2 * t2);
-      s.lines[l * LP + 2 * t2] = convert<T>(v.x);
-      s.lines[l * LP + 2 * t2 + 1] = convert<T>(v.y);
+    // U loads in flight per thread before any is converted and stored
+    constexpr int U = 8;
+    for (int i0 = threadIdx.x; i0 < Q * n; i0 += NT * U) {
+      double2 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * NT;
+        const int l = i / (n / 2), t2 = i - l * (n / 2);
+        v[u] = make_double2(0.0, 0.0);
+        if (i < Q * n && l < nl) v[u] = *reinterpret_cast<const double2*>(src + (long long)(s0 + l) * L.ss + 2 * t2);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * NT;
+        if (i < Q * n) {
+          const int l = i / (n / 2), t2 = i - l * (n / 2);
+          s.lines[l * LP + 2 * t2] = convert<T>(v[u].x);
+          s.lines[l * LP + 2 * t2 + 1] = convert<T>(v[u].y);
+        }
+      }
     }
   } else {
     for (int i = threadIdx.x; i < 2 * Q * n; i += NT) {
@@ -594,9 +608,25 @@ k_dst_lines_inv(const T* __restrict__ scratch, To* __restrict__ out, BatchDesc o
   load_tables<T, P>(pl, s);
   constexpr int LP = S::LP;
   const T* src = scratch + (long long)b * n * L.ns + s0;  // [b][k][s]
-  for (int i = threadIdx.x; i < 2 * Q * n; i += NT) {
-    const int k = i / (2 * Q), l = i - k * (2 * Q);
-    s.lines[l * LP + k] = l < nl ? src[(long long)k * L.ns + l] : T(0);
+  {
+    constexpr int U = 8;  // loads in flight per thread
+    for (int i0 = threadIdx.x; i0 < 2 * Q * n; i0 += NT * U) {
+      T v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * NT;
+        const int k = i / (2 * Q), l = i - k * (2 * Q);
+        v[u] = (i < 2 * Q * n && l < nl) ? src[(long long)k * L.ns + l] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * NT;
+        if (i < 2 * Q * n) {
+          const int k = i / (2 * Q), l = i - k * (2 * Q);
+          s.lines[l * LP + k] = v[u];
+        }
+      }
+    }
   }
   __syncthreads();
   unpack<T, P>(s, dft_p<T, P>(s));
