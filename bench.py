@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: HBM admission budget")
     ap.add_argument("--option", action="append", default=[], metavar="NAME=VALUE",
                     help="fpg_set_option on every domain, e.g. DST_ENGINE=1, FUSED_FASTSOLVE=1, ARNOLDI_THREADS=512")
+    ap.add_argument("--split", type=int, default=2,
+                    help="domains per kappa, each on its own stream with seeds / split right-hand sides")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
@@ -69,6 +71,7 @@ def workload(args):
             "kappas": [0.0, -10.0], "rhs_per_kappa": args.seeds, "solves_per_step": 2 * args.seeds,
             "restart": args.restart, "rtol": args.rtol, "precond_precision": args.precision,
             "schur_mode": "reduced", "schedule": args.schedule, "options": list(args.option),
+            "domains_per_kappa": max(1, args.split), "rhs_per_domain": args.seeds // max(1, args.split),
             "l2": "flushed before every step (512 MiB write)"}
 
 
@@ -301,71 +304,79 @@ def algorithmic_costs(n, iters_per_solve, m):
 
 
 class Runner:
-    """The workload on the GPU: one domain per kappa, each with its own stream and
-    host thread (the library call releases the GIL), solved concurrently."""
+    """The workload on the GPU: `split` domains per kappa, each with its own stream
+    and host thread (the library call releases the GIL), solved concurrently;
+    domain (kappa, i) takes the i-th equal share of that kappa's right-hand sides,
+    in chunks of `nrhs`."""
 
-    def __init__(self, args, f_host, precision, nrhs, flush, concurrent=False):
+    def __init__(self, args, f_host, precision, nrhs, flush, concurrent=False, split=1):
         import torch
         from paper_2509_23180_gb300 import binding as B
         self.torch, self.B = torch, B
         self.kappas = tuple(f_host)
+        self.keys = [(k, i) for k in self.kappas for i in range(split)]
         self.nrhs = nrhs
         self.args = args
         self.flush = flush
         self.main = torch.cuda.Stream()
         self.streams, self.doms, self.fdev, self.pdev = {}, {}, {}, {}
         for k in self.kappas:
-            self.streams[k] = torch.cuda.Stream()
-            desc = B.make_desc("cross", args.n, k, nrhs=nrhs, restart=args.restart, rtol=args.rtol,
-                               precond_precision=precision)
-            self.doms[k] = B.Domain(desc, stream=self.streams[k])
-            apply_options(self.doms[k], args)
-            self.fdev[k] = torch.as_tensor(f_host[k], device="cuda")
-            self.pdev[k] = torch.zeros_like(self.fdev[k])
-        self.pool = ThreadPoolExecutor(max_workers=len(self.kappas))
+            total = f_host[k].shape[0]
+            assert total % split == 0 and (total // split) % nrhs == 0, (total, split, nrhs)
+            share = total // split
+            for i in range(split):
+                key = (k, i)
+                self.streams[key] = torch.cuda.Stream()
+                desc = B.make_desc("cross", args.n, k, nrhs=nrhs, restart=args.restart, rtol=args.rtol,
+                                   precond_precision=precision)
+                self.doms[key] = B.Domain(desc, stream=self.streams[key])
+                apply_options(self.doms[key], args)
+                self.fdev[key] = torch.as_tensor(f_host[k][i * share:(i + 1) * share], device="cuda")
+                self.pdev[key] = torch.zeros_like(self.fdev[key])
+        self.pool = ThreadPoolExecutor(max_workers=len(self.keys))
         self.concurrent = concurrent
         torch.cuda.synchronize()
 
-    def _solve_domain(self, k):
+    def _solve_domain(self, key):
         out = []
-        total = self.fdev[k].shape[0]
+        total = self.fdev[key].shape[0]
         for s0 in range(0, total, self.nrhs):
-            self.doms[k].set_rhs(self.fdev[k][s0:s0 + self.nrhs])
-            st, info = self.doms[k].solve(self.pdev[k][s0:s0 + self.nrhs], check=False)
+            self.doms[key].set_rhs(self.fdev[key][s0:s0 + self.nrhs])
+            st, info = self.doms[key].solve(self.pdev[key][s0:s0 + self.nrhs], check=False)
             out += [(st, i) for i in info]
         return out
 
     def timed_step(self, s):
         """Device time of one step: an event on `main` starts it after the L2
-        flush, both domain streams wait on it, `main` waits on both to end it."""
+        flush, every domain stream waits on it, `main` waits on all to end it."""
         torch = self.torch
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(self.main):
             self.flush.fill_(float(s))
             a.record(self.main)
-        for k in self.kappas:
-            self.streams[k].wait_event(a)
+        for key in self.keys:
+            self.streams[key].wait_event(a)
         if self.concurrent:
-            res = list(self.pool.map(self._solve_domain, self.kappas))
+            res = list(self.pool.map(self._solve_domain, self.keys))
         else:
-            res = [self._solve_domain(k) for k in self.kappas]
-        for k in self.kappas:
+            res = [self._solve_domain(key) for key in self.keys]
+        for key in self.keys:
             e = torch.cuda.Event()
-            e.record(self.streams[k])
+            e.record(self.streams[key])
             self.main.wait_event(e)
         b.record(self.main)
         return a, b, [x for r in res for x in r]
 
     def launches(self):
-        return sum(self.doms[k].launch_count() for k in self.kappas)
+        return sum(self.doms[k].launch_count() for k in self.keys)
 
     def set_profiling(self, on):
-        for k in self.kappas:
+        for k in self.keys:
             self.doms[k].set_profiling(on)
 
     def phases(self):
         out = {}
-        for k in self.kappas:
+        for k in self.keys:
             for name, v in self.doms[k].phase_stats().items():
                 ph = out.setdefault(name, {"launches": 0, "ms": 0.0})
                 ph["launches"] += v["launches"]
@@ -373,7 +384,7 @@ class Runner:
         return out
 
     def close(self):
-        for k in self.kappas:
+        for k in self.keys:
             self.doms[k].close()
         self.pool.shutdown()
 
@@ -396,7 +407,9 @@ def run_ours(args, rank, world):
     seeds = replicas.seeds_for_rank(rank, world, args.seeds)  # independent problems per rank
     f_host = {k: W.rhs_batch("cross", args.n, seeds, kind="fourier") for k in (0.0, -10.0)}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    run = Runner(args, f_host, args.precision, args.seeds, flush, args.schedule == "concurrent")
+    split = max(1, args.split)
+    per_domain = args.seeds // split
+    run = Runner(args, f_host, args.precision, per_domain, flush, args.schedule == "concurrent", split=split)
     for s in range(args.warmup):
         run.timed_step(s)
     torch.cuda.synchronize()
@@ -435,28 +448,29 @@ def run_ours(args, rank, world):
     ok = all(st == B.FPG_OK for st, _ in infos)
 
     # e2e: host buffers through fpg_solve_host, copies inside the timed region
-    fpin = {k: torch.as_tensor(f_host[k]).pin_memory() for k in f_host}
-    ppin = {k: torch.empty_like(fpin[k]).pin_memory() for k in f_host}
-    host_solve = lambda k: run.doms[k].solve_host(fpin[k], ppin[k])
-    list(run.pool.map(host_solve, f_host))  # warm the pinned path once
+    fpin = {key: torch.as_tensor(f_host[key[0]][key[1] * per_domain:(key[1] + 1) * per_domain]).pin_memory()
+            for key in run.keys}
+    ppin = {key: torch.empty_like(fpin[key]).pin_memory() for key in run.keys}
+    host_solve = lambda key: run.doms[key].solve_host(fpin[key], ppin[key])
+    list(run.pool.map(host_solve, run.keys))  # warm the pinned path once
     torch.cuda.synchronize()
     e2e_total = 0.0
     for s in range(args.steps):
         flush.fill_(float(s))
         torch.cuda.synchronize()
         ta = time.perf_counter()
-        list(run.pool.map(host_solve, f_host))
+        list(run.pool.map(host_solve, run.keys))
         e2e_total += time.perf_counter() - ta
     e2e_val = world * solves_per_step * args.steps / e2e_total
-    bytes_h2d = sum(fpin[k].numel() * 8 for k in f_host)
+    bytes_h2d = sum(fpin[key].numel() * 8 for key in run.keys)
 
     iters_mean = float(np.mean(iters)) if iters else 0.0
     costs = algorithmic_costs(args.n, iters_mean, args.restart)
     peaks = measured_peaks()
     fp64_peak = B.probe_fma_peak(64)
     fp32_peak = B.probe_fma_peak(32)
-    roof = roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, args.seeds,
-                    run.doms[run.kappas[0]].fast_solve_path())
+    roof = roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, per_domain,
+                    run.doms[run.keys[0]].fast_solve_path())
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -505,13 +519,15 @@ def variants(args, f_host, flush):
     import torch
     from paper_2509_23180_gb300 import binding as B
     other = args.schedule != "concurrent"
-    forms = {"fp32_precond": (32, args.seeds, False), "fp64_single_rhs": (64, 1, False),
-             ("fp64_concurrent" if other else "fp64_sequential"): (64, args.seeds, other)}
+    per = args.seeds // max(1, args.split)
+    conc = not other
+    forms = {"fp32_precond": (32, per, conc), "fp64_single_rhs": (64, 1, False),
+             ("fp64_concurrent" if other else "fp64_sequential"): (64, per, other)}
     if args.precision == 32:
-        forms = {"fp64_plain": (64, args.seeds, False)}
+        forms = {"fp64_plain": (64, per, conc)}
     out = {}
     for name, (prec, nrhs, conc) in forms.items():
-        run = Runner(args, f_host, prec, nrhs, flush, conc)
+        run = Runner(args, f_host, prec, nrhs, flush, conc, split=1 if nrhs == 1 else max(1, args.split))
         run.timed_step(0)
         torch.cuda.synchronize()
         nsteps = max(1, min(args.steps, 3))
@@ -586,7 +602,7 @@ def roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, nrhs, fs_path=0):
            "measured": "CUDA events around every launch of the kernel in one profiled step of the same "
                        "workload (sequential schedule) after the timed steps",
            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
-           "traffic": traffic_for(kname, args)}
+           "traffic": traffic_for(kname, args, nrhs)}
     if fp64_kernel:
         out.update({"bound": "alu", "achieved": ach_alu / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
                     "frac": ach_alu / peak_alu, "hbm_frac": ach_hbm / hbm,
@@ -618,7 +634,7 @@ def source_hash(kernel):
     return h.hexdigest()[:12]
 
 
-def traffic_for(kernel, args):
+def traffic_for(kernel, args, nrhs=None):
     """DRAM bytes per launch (read + write) from the committed ncu summary, when it
     was taken on this workload and the kernel's sources have not changed since."""
     if kernel not in TRAFFIC_SOURCES:
@@ -631,7 +647,7 @@ def traffic_for(kernel, args):
                 continue
             f = dict(kv.split("=", 1) for kv in line.split())
             if (f.get("kernel") == kernel and f.get("n") == str(args.n) and f.get("prec") == str(args.precision)
-                    and f.get("nrhs") == str(args.seeds) and f.get("src") == sha):
+                    and f.get("nrhs") == str(nrhs if nrhs is not None else args.seeds) and f.get("src") == sha):
                 return float(f["dram_bytes"])
     except (OSError, ValueError, KeyError):
         pass
