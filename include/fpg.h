@@ -407,8 +407,12 @@ typedef enum {
    * hardware-suspended mbarrier test; 0: give up at once).  A wait that runs
    * out records it in the domain's status word, the kernel that waited lets its
    * copy in flight land and returns, and the solve reports FPG_ETIMEOUT for
-   * every right-hand side.  The one wait of this kind today is the bulk-copy
-   * wait of FPG_OPT_DST_BULK's persistent kernel. */
+   * every right-hand side.  The waits this option bounds are the bulk-copy
+   * waits of FPG_OPT_DST_BULK's persistent kernel.  The Arnoldi step's
+   * exchange of projection partials between the CTAs of a cluster waits on an
+   * mbarrier too, with a fixed limit of 2^22 tries that only a stopped CTA can
+   * reach (its protocol cannot continue after an early give-up); reaching it
+   * also sets the status word and gives FPG_ETIMEOUT. */
   FPG_OPT_WAIT_LIMIT = 11,
   /* 1: the FP32 preconditioner (a1 with precond_precision = 32) of centre
    * blocks with n = 64 or 512 runs as one kernel per batch: one thread-block

@@ -96,7 +96,7 @@ cudaError_t launch_arnoldi_reg(int csz, int ntcap, const double* V, long long vs
                                double* vout, long long len, int j, int nrhs, double* H, int hcol_stride,
                                int hrhs_stride, double* cs, double* sn, double* g, double* res, int m,
                                const double* tolabs, int* active, int* kcyc, int* iters, int max_iters, int do_givens,
-                               cudaStream_t st);
+                               int* err, cudaStream_t st);
 cudaError_t launch_arnoldi_cluster(int csz, const double* V, long long vstride, double* w, double* vout,
                                    long long len, int j, int nrhs, double* H, int hcol_stride, int hrhs_stride,
                                    double* cs, double* sn, double* g, double* res, int m, const double* tolabs,
@@ -890,7 +890,7 @@ fpg_status issue_cycle(fpg_domain* D) {
       FPG_CUDA_TRY(launch_arnoldi_reg(csz, D->tune_nt, k.V, (long long)nrhs * L.nc, nullptr, zj, zprec, D->corr, L.n, D->delta,
                                       D->desc.kappa, L.armmask, k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j, nrhs,
                                       k.H, hcol, hrhs, k.cs, k.sn, k.g, k.res, m, k.tolabs, k.active, k.kcyc,
-                                      k.iters, D->desc.max_iters, 1, D->st));
+                                      k.iters, D->desc.max_iters, 1, D->err_dev, D->st));
       count(D, 2, 1);
       ev_end(D, e);
       if (D->hist) {
@@ -1572,7 +1572,7 @@ fpg_status fpg_arnoldi_mgs(fpg_domain* d, const double* V, int32_t j, double* w,
   if (ept > 0) {
     FPG_CUDA_TRY(launch_arnoldi_reg(csz, d->tune_nt, V, (long long)nvec * len, w, nullptr, 64, nullptr, 0, 0.0, 0.0, 0, w, len, j,
                                     nvec, h, 0, j + 2, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
-                                    nullptr, nullptr, 0, 0, d->st));
+                                    nullptr, nullptr, 0, 0, d->err_dev, d->st));
     d->launches += 1;
   } else if (csz > 0) {
     FPG_CUDA_TRY(launch_arnoldi_cluster(csz, V, (long long)nvec * len, w, w, len, j, nvec, h, 0, j + 2, nullptr,
@@ -1677,7 +1677,8 @@ fpg_status fpg_autotune(fpg_domain* d, fpg_tune_result* out) {
           if (ept > 0)
             return launch_arnoldi_reg(c, nt, k.V, (long long)nrhs * L.nc, k.w, nullptr, 64, nullptr, 0, 0.0, 0.0, 0,
                                k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc, j, nrhs, k.H, hcol, hrhs, nullptr, nullptr,
-                               nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0, 0, d->st) == cudaSuccess;
+                               nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0, 0, d->err_dev,
+                               d->st) == cudaSuccess;
           else
             return launch_arnoldi_cluster(c, k.V, (long long)nrhs * L.nc, k.w, k.V + (size_t)(j + 1) * nrhs * L.nc, L.nc,
                                    j, nrhs, k.H, hcol, hrhs, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr,

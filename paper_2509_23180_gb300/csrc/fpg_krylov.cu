@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "fpg_dstline.cuh"
+#include "fpg_exactsum.cuh"
 #include "fpg_internal.cuh"
 
 namespace fpg {
@@ -327,36 +328,49 @@ k_arnoldi_cluster(const double* __restrict__ V, long long vstride, double* __res
 // back.  With z != nullptr the kernel first forms w = A_c z - sum_a corr_a (the
 // Schur matvec's stencil, a2) straight into those registers.
 //
-// Reduction of one MGS step (fixed order, identical in every CTA): the thread
-// partials go to shared memory, warp 0 sums them lane-strided and across lanes,
-// pushes the CTA partial into slot [rank] of every CTA of the cluster, and after
-// one cluster barrier each CTA sums the csz slots in lane order.  That costs one
-// block barrier, one cluster barrier and ~17 FP64 warp instructions per CTA
-// (a butterfly in every warp would cost 5 per warp).
+// Reduction of one MGS step: an exact fixed-point sum (fpg_exactsum.cuh) on the
+// integer pipes.  Each warp sums its lanes' partials, warp 0 sums the warps' tuples
+// and pushes the CTA's tuple into slot [rank] of every CTA of the cluster with
+// st.async (completing on that CTA's mbarrier for the step's parity), then sums the
+// csz tuples it received.  Every CTA ends with the same bits; the FP64 pipe, which
+// bounds the step, only runs the dot products and updates.  Slot and mbarrier k & 1
+// are used again at step k + 2, which no CTA can reach before every CTA has read
+// step k's slots (each needs every CTA's step k + 1 tuple first).
 constexpr int kRegMaxThreads = 512;
+// Tries of each exchange wait.  The exchange cannot give up early and continue
+// (the mbarrier phases would fall out of step and late tuples could land in a CTA
+// that has left), so the limit only catches a cluster whose CTAs stopped: long
+// enough never to fire otherwise.
+constexpr int kExchangeTries = 1 << 22;
 
 struct ClusterReduce {
-  double* red;         // [blockDim.x]
-  double (*slots)[16]; // [2][16]
+  int4* wtup;                // [16] per-warp tuples
+  int4 (*slots)[16];         // [2][16] the cluster's CTA tuples, by step parity
+  unsigned long long* mbar;  // [2]
   double* hval;
+  int* ok;                   // 0 once an exchange wait gave up
 };
 
 __device__ __forceinline__ double cluster_reduce(double acc, int k, const ClusterReduce& R, int csz, int rank) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cl = cg::this_cluster();
-  R.red[threadIdx.x] = acc;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int4 wt = xs::warp_sum_exact(acc);
+  if (lane == 0) R.wtup[wid] = wt;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) s += R.red[i];
-    s = warp_sum(s);
-    if ((int)threadIdx.x < csz) *cl.map_shared_rank(&R.slots[k & 1][rank], threadIdx.x) = s;
-  }
-  cl.sync();
-  if (threadIdx.x < 32) {
-    const double q = (int)threadIdx.x < csz ? R.slots[k & 1][threadIdx.x] : 0.0;
-    const double sum = warp_sum(q);
-    if (threadIdx.x == 0) *R.hval = sum;
+  if (wid == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    const int4 ct = xs::warp_sum_tuples(lane < nw ? R.wtup[lane] : make_int4(0, 0, 0, 0), lane < nw);
+    const int b = k & 1;
+    if (lane == 0) xs::mbar_expect(&R.mbar[b], (unsigned)(16 * csz));
+    __syncwarp();
+    if (lane < csz)
+      xs::st_async_tuple(xs::cluster_addr(xs::smem_u32(&R.slots[b][rank]), lane), ct,
+                         xs::cluster_addr(xs::smem_u32(&R.mbar[b]), lane));
+    const bool got = xs::mbar_wait_cluster(&R.mbar[b], (unsigned)((k >> 1) & 1), kExchangeTries);
+    const int4 tt = xs::warp_sum_tuples(lane < csz ? R.slots[b][lane] : make_int4(0, 0, 0, 0), lane < csz);
+    if (lane == 0) {
+      *R.hval = xs::tuple_to_double(tt);
+      if (!got) *R.ok = 0;
+    }
   }
   __syncthreads();
   return *R.hval;
@@ -374,17 +388,27 @@ k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const dou
                       int hcol_stride, int hrhs_stride, double* __restrict__ cs, double* __restrict__ sn,
                       double* __restrict__ g, double* __restrict__ res, int m, const double* __restrict__ tolabs,
                       int* __restrict__ active, int* __restrict__ kcyc, int* __restrict__ iters, int max_iters,
-                      int do_givens) {
+                      int do_givens, int* __restrict__ err) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int csz = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int r = blockIdx.x / csz;
-  __shared__ double red[kRegMaxThreads];
-  __shared__ double slots[2][16];
+  __shared__ int4 wtup[kRegMaxThreads / 32];
+  __shared__ int4 slots[2][16];
+  __shared__ unsigned long long mbar[2];
   __shared__ double hval;
-  const ClusterReduce R{red, slots, &hval};
+  __shared__ int ok;
+  const ClusterReduce R{wtup, slots, mbar, &hval, &ok};
   if (active != nullptr && !active[r]) return;  // uniform over the cluster
+  if (threadIdx.x == 0) {
+    xs::mbar_init_cluster(&mbar[0]);
+    xs::mbar_init_cluster(&mbar[1]);
+    ok = 1;
+  }
+  // Every CTA's mbarriers are initialised before any tuple can reach them: the
+  // wait half of this barrier follows the loads below.
+  xs::cluster_arrive_release();
   // slice of this CTA: [lo, hi); thread elements lo + tid + e * nb, e < nval
   const int chunk = (int)((len + csz - 1) / csz);
   const int lo = rank * chunk;
@@ -419,7 +443,9 @@ k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const dou
     }
     wv[e] = x;
   }
+  xs::cluster_wait_acquire();
   double* hcol = H + (long long)r * hrhs_stride + (long long)j * hcol_stride;
+  int kfail = -1;
   for (int k = 0; k <= j; ++k) {
     if (k < j) {  // prefetch v_{k+1}; consumed after this step's reduction
       const double* vk1 = vt + (long long)(k + 1) * vstride;
@@ -430,6 +456,10 @@ k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const dou
 #pragma unroll
     for (int e = 0; e < EPT; ++e) acc = fma(wv[e], vc[e], acc);
     const double h = cluster_reduce(acc, k, R, csz, rank);
+    if (!ok) {
+      kfail = k;
+      break;
+    }
     if (rank == 0 && threadIdx.x == 0) hcol[k] = h;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
@@ -437,10 +467,21 @@ k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const dou
       vc[e] = vn[e];
     }
   }
-  double acc = 0.0;
+  double hn = 0.0;
+  if (kfail < 0) {
+    double acc = 0.0;
 #pragma unroll
-  for (int e = 0; e < EPT; ++e) acc = fma(wv[e], wv[e], acc);
-  const double hn = sqrt(cluster_reduce(acc, j + 1, R, csz, rank));
+    for (int e = 0; e < EPT; ++e) acc = fma(wv[e], wv[e], acc);
+    hn = sqrt(cluster_reduce(acc, j + 1, R, csz, rank));
+    if (!ok) kfail = j + 1;
+  }
+  if (kfail >= 0) {
+    // An exchange wait gave up (a CTA of the cluster stopped): report it, give the
+    // tuples of that step one more bounded wait to land, and leave without results.
+    if (threadIdx.x == 0 && err != nullptr) *err = 1;
+    if (threadIdx.x < 32) xs::mbar_wait_cluster(&mbar[kfail & 1], (unsigned)((kfail >> 1) & 1), kExchangeTries);
+    return;
+  }
   const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
   double* vr = vout + base + t0;
 #pragma unroll
@@ -478,8 +519,8 @@ k_arnoldi_cluster_reg(const double* __restrict__ V, long long vstride, const dou
       if (rj <= tolabs[r] || b == 0.0 || iters[r] >= max_iters) active[r] = 0;
     }
   }
-  // Every remote store into a CTA's slots precedes a cluster barrier that CTA
-  // also waits on, so no CTA's shared memory is touched after it exits.
+  // Each CTA waited for the csz tuples of every step, the last included, so no
+  // store is in flight towards a CTA when it exits.
 }
 
 // ---------------------------------------------------------------------------
@@ -1094,7 +1135,7 @@ cudaError_t launch_reg_impl(int csz, const double* V, long long vstride, const d
                             const double* corr, int n, double delta, double kappa, int armmask, double* vout,
                             long long len, int j, int nrhs, double* H, int hcol_stride, int hrhs_stride, double* cs,
                             double* sn, double* g, double* res, int m, const double* tolabs, int* active, int* kcyc,
-                            int* iters, int max_iters, int do_givens, cudaStream_t st) {
+                            int* iters, int max_iters, int do_givens, int* err, cudaStream_t st) {
   static PerDeviceOnce attr;
   if (attr.first()) {
     cudaFuncSetAttribute(k_arnoldi_cluster_reg<Tz, EPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1112,7 +1153,7 @@ cudaError_t launch_reg_impl(int csz, const double* V, long long vstride, const d
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_arnoldi_cluster_reg<Tz, EPT>, V, vstride, w, z, corr, n, delta, kappa, armmask,
                             vout, len, j, H, hcol_stride, hrhs_stride, cs, sn, g, res, m, tolabs, active, kcyc,
-                            iters, max_iters, do_givens);
+                            iters, max_iters, do_givens, err);
 }
 
 // z == nullptr: w is read from `w`; otherwise w = A_c z - corr is formed in the kernel (zprec 64 or 32).
@@ -1121,17 +1162,17 @@ cudaError_t launch_arnoldi_reg(int csz, int ntcap, const double* V, long long vs
                                double* vout, long long len, int j, int nrhs, double* H, int hcol_stride,
                                int hrhs_stride, double* cs, double* sn, double* g, double* res, int m,
                                const double* tolabs, int* active, int* kcyc, int* iters, int max_iters, int do_givens,
-                               cudaStream_t st) {
+                               int* err, cudaStream_t st) {
   const int ept = arnoldi_reg_ept(len, csz, ntcap);
 #define FPG_REG_CASE(E)                                                                                            \
   if (ept == E) {                                                                                                  \
     if (z != nullptr && zprec == 32)                                                                               \
       return launch_reg_impl<float, E>(csz, V, vstride, w, (const float*)z, corr, n, delta, kappa, armmask, vout,  \
                                        len, j, nrhs, H, hcol_stride, hrhs_stride, cs, sn, g, res, m, tolabs, active, \
-                                       kcyc, iters, max_iters, do_givens, st);                                     \
+                                       kcyc, iters, max_iters, do_givens, err, st);                                \
     return launch_reg_impl<double, E>(csz, V, vstride, w, (const double*)z, corr, n, delta, kappa, armmask, vout,  \
                                       len, j, nrhs, H, hcol_stride, hrhs_stride, cs, sn, g, res, m, tolabs, active, \
-                                      kcyc, iters, max_iters, do_givens, st);                                      \
+                                      kcyc, iters, max_iters, do_givens, err, st);                                 \
   }
   FPG_REG_CASE(2)
   FPG_REG_CASE(4)
