@@ -398,17 +398,21 @@ typedef enum {
    * setup (q_a = A_a^{-1} f_a) and the finish (p_a = A_a^{-1}(f_a - R_ac p_c)):
    * each step is out += A_a^{-1}(in - A_a out) in FP64. */
   FPG_OPT_ARM_REFINE = 9,
-  /* 1: the FP32 forward DST of the size-specialised path runs as a persistent
-   * kernel that fetches the next line tile with a bulk asynchronous copy
-   * (cp.async.bulk on an mbarrier) while it transforms the current one (blocks
-   * with contiguous, 16-byte aligned rows); 0 (default): one CTA per tile. */
+  /* Form of the FP32 forward DST of the size-specialised path for blocks with
+   * contiguous, 16-byte aligned rows.  0 (default): where n + 1 is 65, 513 or
+   * 1025 and the sweep length is a whole number of tiles, a persistent
+   * streaming kernel (two CTAs per SM; the next tile's FP64 rows arrive by a
+   * bulk asynchronous copy, cp.async.bulk on an mbarrier, while the current one
+   * is transformed in place), else one CTA per tile.  1: a persistent kernel
+   * with one CTA per SM and the per-tile engine's buffers.  2: one CTA per tile.
+   * All three give bit-identical results. */
   FPG_OPT_DST_BULK = 10,
   /* Tries of every bounded device wait (default 2^22, each try a
    * hardware-suspended mbarrier test; 0: give up at once).  A wait that runs
    * out records it in the domain's status word, the kernel that waited lets its
    * copy in flight land and returns, and the solve reports FPG_ETIMEOUT for
    * every right-hand side.  The waits this option bounds are the bulk-copy
-   * waits of FPG_OPT_DST_BULK's persistent kernel.  The Arnoldi step's
+   * waits of FPG_OPT_DST_BULK's persistent kernels (forms 0 and 1).  The Arnoldi step's
    * exchange of projection partials between the CTAs of a cluster waits on an
    * mbarrier too, with a fixed limit of 2^22 tries that only a stopped CTA can
    * reach (its protocol cannot continue after an early give-up); reaching it

@@ -1735,7 +1735,7 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_DST_BULK:
-      if (value < 0 || value > 1) return FPG_EINVAL;
+      if (value < 0 || value > 2) return FPG_EINVAL;
       for (auto* tt : {&d->tC64, &d->tC32, &d->tA64, &d->tA32, &d->tA64e}) tt->bulk = value;
       drop_graph(d);
       return FPG_OK;

@@ -27,6 +27,32 @@ cudaError_t dst_lines_fwd_bulk_f32(int p, const double* in, BatchDesc ib, LineLa
   }
 }
 
+// The streaming forward form (k_dst_lines_fwd_stream) for this p and sweep length:
+// p without Rader, and ns a whole number of tiles of 2Q rows.
+bool dst_lines_stream_ok_f32(int p, int ns) {
+  switch (p) {
+    case 65: return dl::StreamShape<65>::eligible && ns % (2 * dl::LineShape<float, 65>::Q) == 0;
+    case 513: return dl::StreamShape<513>::eligible && ns % (2 * dl::LineShape<float, 513>::Q) == 0;
+    case 1025: return dl::StreamShape<1025>::eligible && ns % (2 * dl::LineShape<float, 1025>::Q) == 0;
+    default: return false;
+  }
+}
+
+cudaError_t dst_lines_fwd_stream_f32(int p, const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl,
+                                     float* scratch, int nblk, const int* active, int nper_active, int* err,
+                                     int wait_limit, cudaStream_t st) {
+  if (err == nullptr) {
+    cudaError_t e = cudaGetSymbolAddress((void**)&err, g_dst_bulk_timeout_f32);
+    if (e != cudaSuccess) return e;
+  }
+  switch (p) {
+    case 65: return dl::fwd_stream_one<65>(in, ib, L, pl, scratch, nblk, active, nper_active, err, wait_limit, st);
+    case 513: return dl::fwd_stream_one<513>(in, ib, L, pl, scratch, nblk, active, nper_active, err, wait_limit, st);
+    case 1025: return dl::fwd_stream_one<1025>(in, ib, L, pl, scratch, nblk, active, nper_active, err, wait_limit, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
 cudaError_t dst_lines_fwd_f32(int p, const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl, float* scratch,
                               int nblk, const int* active, int nper_active, int vec, cudaStream_t st) {
   switch (p) {

@@ -592,6 +592,192 @@ k_dst_lines_fwd_bulk(const double* __restrict__ in, BatchDesc ib, LineLayout L, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Streaming persistent forward DST (FP32 compute; p without Rader; tiles of 2Q
+// contiguous, 16-byte aligned rows, ns a multiple of 2Q).  Same arithmetic in the
+// same order as k_dst_lines_fwd, so the output is bit-identical; what changes is
+// the movement of data:
+//   * each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ... and keeps the
+//     packing and twiddle tables in shared memory for all of them;
+//   * the next tile's FP64 rows arrive by one bulk copy (cp.async.bulk on an
+//     mbarrier) into a staging buffer while the current tile is transformed;
+//   * the packing reads the staging buffer directly: one pair of loads x_{j-1},
+//     x_{p-j-1} gives both u_j and u_{p-j} (sin(pi (p-j)/p) = sin(pi j/p)), so the
+//     real lines never pass through shared memory in FP32;
+//   * both passes of the DFT and the unpacking run in place in one buffer of Q
+//     spectra (each pass reads its inputs into registers, the CTA synchronises, then
+//     writes), which with the staging buffer leaves two CTAs per SM;
+//   * the transposed store to scratch[b][k][s] writes runs of 2Q rows as float4.
+template <int P>
+struct StreamShape {
+  using S = LineShape<float, P>;
+  static constexpr int n = S::n, Q = S::Q;
+  static constexpr size_t o_spl = 0;                                   // [P] sin(pi j/p) + 1/2
+  static constexpr size_t o_smi = align16(o_spl + sizeof(float) * P);  // [P] sin(pi j/p) - 1/2
+  static constexpr size_t o_tw = align16(o_smi + sizeof(float) * P);   // [N] w_p^{ka jb}
+  static constexpr size_t o_z = align16(o_tw + sizeof(C2<float>) * S::N);
+  static constexpr size_t o_stage = align16(o_z + sizeof(C2<float>) * Q * P);
+  static constexpr size_t o_mbar = align16(o_stage + sizeof(double) * 2 * Q * n);
+  static constexpr size_t bytes = o_mbar + 16;
+  static constexpr bool eligible = !S::rader && S::YB == S::B && S::ZP == P && S::LP == P &&
+                                   Q * S::B <= S::NT && Q * S::A <= S::NT && (2 * Q) % 4 == 0;
+};
+
+template <int P>
+__global__ void __launch_bounds__(LineShape<float, P>::NT, 2)
+k_dst_lines_fwd_stream(const double* __restrict__ in, BatchDesc ib, LineLayout L, DstPlan pl,
+                       float* __restrict__ scratch, const int* __restrict__ active, int nper_active, int nblk,
+                       int* __restrict__ err, int wait_limit) {
+  using T = float;
+  using S = LineShape<T, P>;
+  using SS = StreamShape<P>;
+  static_assert(SS::eligible, "streaming forward DST: non-Rader p with in-place passes");
+  constexpr int n = S::n, Q = S::Q, NT = S::NT, A = S::A, B = S::B, YB = S::YB, N = S::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* spl = reinterpret_cast<T*>(smem_raw + SS::o_spl);
+  T* smi = reinterpret_cast<T*>(smem_raw + SS::o_smi);
+  C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw + SS::o_tw);
+  C2<T>* Z = reinterpret_cast<C2<T>*>(smem_raw + SS::o_z);
+  double* stage = reinterpret_cast<double*>(smem_raw + SS::o_stage);
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem_raw + SS::o_mbar);
+  __shared__ int s_landed;
+  // the unpacking writes the 2Q real lines over the Q spectra (pitch LP = P)
+  LineSmem<T, P> ls(smem_raw);
+  ls.lines = reinterpret_cast<T*>(Z);
+  const int tpb = L.ns / (2 * Q);
+  const int total = nblk * tpb;
+  auto live = [&](int tile) { return active == nullptr || active[(tile / tpb) / nper_active]; };
+  auto next_of = [&](int tile) {
+    do tile += gridDim.x;
+    while (tile < total && !live(tile));
+    return tile;
+  };
+  auto issue = [&](int tile) {
+    const int b = tile / tpb, s0 = (tile - b * tpb) * 2 * Q;
+    bulk_load(stage, in + boff(ib, b) + (long long)s0 * n, (unsigned)(2 * Q * n * sizeof(double)), mbar);
+  };
+  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  {
+    const C2<T>* W = reinterpret_cast<const C2<T>*>(pl.W);
+    const T* sp = reinterpret_cast<const T*>(pl.sinp);
+    for (int i = threadIdx.x; i < P; i += NT) {
+      spl[i] = sp[i] + T(0.5);
+      smi[i] = sp[i] - T(0.5);
+    }
+    for (int i = threadIdx.x; i < N; i += NT) {
+      const int ka = i / B, jb = i - ka * B;
+      tw[i] = W[ka * jb];
+    }
+  }
+  __syncthreads();
+  int tile = blockIdx.x;
+  if (tile < total && !live(tile)) tile = next_of(tile);
+  if (threadIdx.x == 0 && tile < total) issue(tile);
+  // this thread's tasks in the two passes, the same for every tile
+  const int t = threadIdx.x;
+  const int q1 = t / B, jb1 = t - q1 * B;  // pass 1 (t < Q B)
+  const int q2 = t / A, ka2 = t - q2 * A;  // pass 2 (t < Q A)
+  unsigned parity = 0;
+  while (tile < total) {
+    const int b = tile / tpb, s0 = (tile - b * tpb) * 2 * Q;
+    if (t == 0) s_landed = mbar_wait(mbar, parity, wait_limit) ? 1 : 0;
+    __syncthreads();
+    if (!s_landed) {  // the same value in every thread
+      if (t == 0) {
+        atomicExch(err, 1);
+        mbar_wait(mbar, parity, 1 << 20);  // the copy in flight lands before the CTA leaves
+      }
+      return;
+    }
+    mbar_wait(mbar, parity, 1 << 22);  // phase complete: returns at once, and orders the copied data
+    parity ^= 1u;
+    // packing straight from the FP64 rows: z_j and z_{p-j} of pair q
+#pragma unroll 2
+    for (int i = t; i < Q * (n / 2); i += NT) {
+      const int q = i / (n / 2), j = i - q * (n / 2) + 1;
+      const double* ra = stage + (2 * q) * n;
+      const double* rb = ra + n;
+      const T a1 = f64_to_f32(ra[j - 1]), a2 = f64_to_f32(ra[P - j - 1]);
+      const T b1 = f64_to_f32(rb[j - 1]), b2 = f64_to_f32(rb[P - j - 1]);
+      const T cp = spl[j], cm = smi[j];
+      Z[q * P + j] = C2<T>{fma(cp, a1, cm * a2), fma(cp, b1, cm * b2)};
+      Z[q * P + P - j] = C2<T>{fma(cp, a2, cm * a1), fma(cp, b2, cm * b1)};
+    }
+    if (t < Q) Z[t * P] = C2<T>{T(0), T(0)};
+    __syncthreads();  // the staging buffer is free
+    const int next = next_of(tile);
+    if (t == 0 && next < total) issue(next);
+    {  // pass 1: per (q, jb) a DFT of length A over ja, times w_p^{jb ka}, in place
+      C2<T> v[A];
+      if (t < Q * B) static_for<A>([&](auto ja) { v[decltype(ja)::value] = Z[q1 * P + B * decltype(ja)::value + jb1]; });
+      __syncthreads();
+      if (t < Q * B) {
+        dft<A, T>(v);
+        C2<T>* yq = Z + q1 * P + jb1;
+        yq[0] = v[0];
+        static_for<A - 1>([&](auto kai) {
+          constexpr int ka = decltype(kai)::value + 1;
+          yq[ka * YB] = c_mul(v[ka], tw[ka * B + jb1]);
+        });
+      }
+      __syncthreads();
+    }
+    {  // pass 2: per (q, ka) a DFT of length B over jb, output k = ka + A kb, in place
+      C2<T> u[B];
+      if (t < Q * A) static_for<B>([&](auto jb) { u[decltype(jb)::value] = Z[q2 * P + ka2 * YB + decltype(jb)::value]; });
+      __syncthreads();
+      if (t < Q * A) {
+        dft<B, T>(u);
+        static_for<B>([&](auto kb) { Z[q2 * P + ka2 + A * decltype(kb)::value] = u[decltype(kb)::value]; });
+      }
+      __syncthreads();
+    }
+    unpack<T, P>(ls, Z);
+    __syncthreads();
+    // scratch[b][k][s]: runs of 2Q rows, four rows per store
+    T* dst = scratch + (long long)b * n * L.ns + s0;
+    constexpr int R4 = 2 * Q / 4;
+#pragma unroll 2
+    for (int i = t; i < n * R4; i += NT) {
+      const int k = i / R4, l = (i - k * R4) * 4;
+      const T* col = ls.lines + k;
+      *reinterpret_cast<float4*>(dst + (long long)k * L.ns + l) =
+          make_float4(col[l * P], col[(l + 1) * P], col[(l + 2) * P], col[(l + 3) * P]);
+    }
+    __syncthreads();  // the spectra buffer is rewritten by the next tile's packing
+    tile = next;
+  }
+}
+
+template <int P>
+cudaError_t fwd_stream_one(const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl, float* scratch, int nblk,
+                           const int* active, int nper_active, int* err, int wait_limit, cudaStream_t st) {
+  if constexpr (!StreamShape<P>::eligible) {
+    return cudaErrorNotSupported;
+  } else {
+    using S = LineShape<float, P>;
+    using SS = StreamShape<P>;
+    static PerDeviceOnce attr;
+    static int per_sm_of[64] = {};
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    int per_sm = (dev >= 0 && dev < 64) ? per_sm_of[dev] : 0;
+    if (attr.first() || per_sm == 0) {
+      cudaFuncSetAttribute(k_dst_lines_fwd_stream<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SS::bytes);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dst_lines_fwd_stream<P>, S::NT, SS::bytes);
+      if (per_sm < 1) per_sm = 1;
+      if (dev >= 0 && dev < 64) per_sm_of[dev] = per_sm;
+    }
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long total = (long long)nblk * (L.ns / (2 * S::Q));
+    const int grid = (int)(total < (long long)per_sm * sms ? total : (long long)per_sm * sms);
+    if (grid <= 0) return cudaSuccess;
+    k_dst_lines_fwd_stream<P><<<grid, S::NT, SS::bytes, st>>>(in, ib, L, pl, scratch, active, nper_active, nblk, err,
+                                                              wait_limit);
+    return cudaGetLastError();
+  }
+}
+
 // Inverse: scratch[b][k][s] -> DST -> out block (To), times `scale`.
 template <typename T, typename To, int P>
 __global__ void __launch_bounds__(LineShape<T, P>::NT)

@@ -518,6 +518,10 @@ cudaError_t dst_lines_fwd_f32(int p, const double* in, BatchDesc ib, LineLayout 
 cudaError_t dst_lines_fwd_bulk_f32(int p, const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl,
                                    float* scratch, int nblk, const int* active, int nper_active, int* err,
                                    int wait_limit, cudaStream_t st);
+bool dst_lines_stream_ok_f32(int p, int ns);
+cudaError_t dst_lines_fwd_stream_f32(int p, const double* in, BatchDesc ib, LineLayout L, const DstPlan& pl,
+                                     float* scratch, int nblk, const int* active, int nper_active, int* err,
+                                     int wait_limit, cudaStream_t st);
 cudaError_t dst_lines_inv_f32(int p, const float* scratch, void* out, int out_prec, BatchDesc ob, LineLayout L,
                               const DstPlan& pl, int nblk, const int* active, int nper_active, int vec,
                               cudaStream_t st);
@@ -555,9 +559,14 @@ cudaError_t lines_fwd(const DstPlan& pl, const double* in, BatchDesc ib, LineLay
                       int wait_limit = 1 << 22) {
   const int vec = pairs_aligned(in, 8, ib, L) ? 1 : 0;
   if constexpr (sizeof(T) == 4) {
-    // persistent form with bulk copies: contiguous rows, 16-byte aligned blocks
-    if (bulk && vec && L.ss == L.nt) return dst_lines_fwd_bulk_f32(pl.p, in, ib, L, pl, scratch, nblk, active,
-                                                                   nper_active, err, wait_limit, st);
+    // persistent forms with bulk copies: contiguous rows, 16-byte aligned blocks.
+    // bulk 0 (default): the streaming kernel where the length and tiles allow it;
+    // 1: the one-CTA-per-SM bulk kernel; 2: one CTA per tile.
+    if (bulk == 1 && vec && L.ss == L.nt)
+      return dst_lines_fwd_bulk_f32(pl.p, in, ib, L, pl, scratch, nblk, active, nper_active, err, wait_limit, st);
+    if (bulk == 0 && vec && L.ss == L.nt && (L.ns & 3) == 0 && ((uintptr_t)scratch & 15) == 0 &&
+        dst_lines_stream_ok_f32(pl.p, L.ns))
+      return dst_lines_fwd_stream_f32(pl.p, in, ib, L, pl, scratch, nblk, active, nper_active, err, wait_limit, st);
   }
   if constexpr (sizeof(T) == 8)
     return dst_lines_fwd_f64(pl.p, in, ib, L, pl, scratch, nblk, active, nper_active, vec, st);

@@ -37,11 +37,13 @@ def test_traffic_lookup_follows_sources_and_workload():
         if line.startswith("kernel=k_arnoldi_cluster_reg "):
             committed = dict(kv.split("=", 1) for kv in line.split())
     assert committed is not None
-    t = bench.traffic_for("k_arnoldi_cluster_reg", args)
+    nrhs = int(committed["nrhs"])  # right-hand sides of one launch (one domain)
+    t = bench.traffic_for("k_arnoldi_cluster_reg", args, nrhs)
     if committed["src"] == bench.source_hash("k_arnoldi_cluster_reg"):
         assert t == float(committed["dram_bytes"])
     else:
         assert t is None
+    assert bench.traffic_for("k_arnoldi_cluster_reg", args, nrhs + 1) is None
     assert bench.traffic_for("k_arnoldi_cluster_reg", SimpleNamespace(n=512, precision=64, seeds=10)) is None
     assert bench.traffic_for("k_not_a_kernel", args) is None
 

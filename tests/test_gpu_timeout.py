@@ -1,7 +1,7 @@
 """Bounded device waits: a wait that runs out gives FPG_ETIMEOUT, not a trap or a hang.
 
-The bulk-copy forward DST (FPG_OPT_DST_BULK) waits on an mbarrier for each line
-tile it fetches.  With FPG_OPT_WAIT_LIMIT = 0 every such wait gives up at once:
+The persistent forward DST kernels (FPG_OPT_DST_BULK forms 0, the default streaming
+kernel, and 1) wait on an mbarrier for each line tile they fetch.  With FPG_OPT_WAIT_LIMIT = 0 every such wait gives up at once:
 the kernel records it in the domain's status word, lets its copy in flight land
 and returns.  The solve must then report FPG_ETIMEOUT for every right-hand side,
 and the same domain, stream and context must solve correctly afterwards with
@@ -20,15 +20,16 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def test_wait_that_runs_out_reports_etimeout_and_context_stays_usable(lib):
+@pytest.mark.parametrize("form", [0, 1])
+def test_wait_that_runs_out_reports_etimeout_and_context_stays_usable(lib, form):
     from paper_2509_23180_gb300 import binding as B
     n, kappa = 64, -10.0
     f = W.rhs_batch("cross", n, [1, 2], kind="fourier")
     fd = torch.as_tensor(f, device="cuda")
     d = B.Domain(B.make_desc("cross", n, kappa, nrhs=2, restart=20, rtol=1e-10, max_iters=200,
                              precond_precision=32))
-    d.set_option(B.OPT_DST_BULK, 1)
-    assert d.fast_solve_path() == 1  # the size-specialised line DST (p = 65), whose FP32 forward is the bulk kernel
+    d.set_option(B.OPT_DST_BULK, form)
+    assert d.fast_solve_path() == 1  # the size-specialised line DST (p = 65), whose FP32 forward is a bulk kernel
     d.set_option(B.OPT_WAIT_LIMIT, 0)
     d.set_rhs(fd)
     p = torch.zeros_like(fd)
