@@ -399,7 +399,7 @@ typedef enum {
    * each step is out += A_a^{-1}(in - A_a out) in FP64. */
   FPG_OPT_ARM_REFINE = 9,
   /* Form of the FP32 forward DST of the size-specialised path for blocks with
-   * contiguous, 16-byte aligned rows.  0 (default): where n + 1 is 65, 513 or
+   * contiguous, 16-byte aligned rows.  0 (default): where n + 1 is 513 or
    * 1025 and the sweep length is a whole number of tiles, a persistent
    * streaming kernel (two CTAs per SM; the next tile's FP64 rows arrive by a
    * bulk asynchronous copy, cp.async.bulk on an mbarrier, while the current one

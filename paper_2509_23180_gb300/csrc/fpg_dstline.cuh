@@ -85,13 +85,43 @@ __host__ __device__ constexpr double turn_sincos(long long m, long long R, bool 
   return want_sin ? sn : cs;
 }
 
+// FP32 complex arithmetic runs on the paired FP32 instructions (FADD2, FMUL2,
+// FFMA2: two lanes of binary32 per instruction, each rounded exactly as the
+// scalar operation).  Every paired form below computes, component by component,
+// the same operations in the same order as the scalar form next to it, so the
+// results are bit-identical; the transforms are issue-bound and the pairing
+// halves their floating-point instruction count.
+__device__ __forceinline__ float2 f2(C2<float> a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ C2<float> c2(float2 a) { return C2<float>{a.x, a.y}; }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 template <typename T>
-__device__ __forceinline__ C2<T> c_add(C2<T> a, C2<T> b) { return C2<T>{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ C2<T> c_add(C2<T> a, C2<T> b) {
+  if constexpr (sizeof(T) == 4) {
+    return c2(add2(f2(a), f2(b)));
+  } else {
+    return C2<T>{a.x + b.x, a.y + b.y};
+  }
+}
 template <typename T>
-__device__ __forceinline__ C2<T> c_sub(C2<T> a, C2<T> b) { return C2<T>{a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ C2<T> c_sub(C2<T> a, C2<T> b) {
+  if constexpr (sizeof(T) == 4) {
+    return c2(add2(f2(a), make_float2(-b.x, -b.y)));  // a + (-b) = a - b exactly
+  } else {
+    return C2<T>{a.x - b.x, a.y - b.y};
+  }
+}
 template <typename T>
 __device__ __forceinline__ C2<T> c_mul(C2<T> a, C2<T> w) {
-  return C2<T>{fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x)};
+  if constexpr (sizeof(T) == 4) {
+    // (fma(a.x, w.x, -(a.y w.y)), fma(a.x, w.y, a.y w.x))
+    const float2 t = mul2(make_float2(a.y, a.y), make_float2(w.y, w.x));
+    return c2(fma2(make_float2(a.x, a.x), make_float2(w.x, w.y), make_float2(-t.x, t.y)));
+  } else {
+    return C2<T>{fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x)};
+  }
 }
 
 // a * w_R^M with w_R = exp(-2 pi i / R), M and R compile-time.
@@ -110,7 +140,13 @@ __device__ __forceinline__ C2<T> c_mul_root(C2<T> a) {
     constexpr T c = (T)turn_sincos(m, R, false);
     constexpr T s = (T)turn_sincos(m, R, true);
     // (a.x + i a.y)(c - i s)
-    return C2<T>{fma(a.x, c, a.y * s), fma(a.y, c, -(a.x * s))};
+    if constexpr (sizeof(T) == 4) {
+      // (fma(a.x, c, a.y s), fma(a.y, c, -(a.x s)))
+      const float2 t = mul2(make_float2(a.y, a.x), make_float2(s, s));
+      return c2(fma2(make_float2(a.x, a.y), make_float2(c, c), make_float2(t.x, -t.y)));
+    } else {
+      return C2<T>{fma(a.x, c, a.y * s), fma(a.y, c, -(a.x * s))};
+    }
   }
 }
 
@@ -148,19 +184,33 @@ __device__ __forceinline__ void dft_odd_prime(C2<T> (&v)[R]) {
   out[0] = x0;
   static_for<H>([&](auto ki) {
     constexpr int k = decltype(ki)::value + 1;
-    C2<T> a = v[0], b{T(0), T(0)};
-    static_for<H>([&](auto qi) {
-      constexpr int q = decltype(qi)::value + 1;
-      constexpr int m = (q * k) % R;
-      constexpr T c = (T)turn_sincos(m, R, false);
-      constexpr T sn = (T)turn_sincos(m, R, true);
-      a.x = fma(s[q - 1].x, c, a.x);
-      a.y = fma(s[q - 1].y, c, a.y);
-      b.x = fma(d[q - 1].x, sn, b.x);
-      b.y = fma(d[q - 1].y, sn, b.y);
-    });
-    out[k] = C2<T>{a.x + b.y, a.y - b.x};      // a - i b
-    out[R - k] = C2<T>{a.x - b.y, a.y + b.x};  // a + i b
+    if constexpr (sizeof(T) == 4) {
+      float2 a2 = f2(v[0]), b2 = make_float2(0.f, 0.f);
+      static_for<H>([&](auto qi) {
+        constexpr int q = decltype(qi)::value + 1;
+        constexpr int m = (q * k) % R;
+        constexpr float c = (float)turn_sincos(m, R, false);
+        constexpr float sn = (float)turn_sincos(m, R, true);
+        a2 = fma2(f2(s[q - 1]), make_float2(c, c), a2);
+        b2 = fma2(f2(d[q - 1]), make_float2(sn, sn), b2);
+      });
+      out[k] = c2(add2(a2, make_float2(b2.y, -b2.x)));      // a - i b
+      out[R - k] = c2(add2(a2, make_float2(-b2.y, b2.x)));  // a + i b
+    } else {
+      C2<T> a = v[0], b{T(0), T(0)};
+      static_for<H>([&](auto qi) {
+        constexpr int q = decltype(qi)::value + 1;
+        constexpr int m = (q * k) % R;
+        constexpr T c = (T)turn_sincos(m, R, false);
+        constexpr T sn = (T)turn_sincos(m, R, true);
+        a.x = fma(s[q - 1].x, c, a.x);
+        a.y = fma(s[q - 1].y, c, a.y);
+        b.x = fma(d[q - 1].x, sn, b.x);
+        b.y = fma(d[q - 1].y, sn, b.y);
+      });
+      out[k] = C2<T>{a.x + b.y, a.y - b.x};      // a - i b
+      out[R - k] = C2<T>{a.x - b.y, a.y + b.x};  // a + i b
+    }
   });
   static_for<R>([&](auto i) { v[decltype(i)::value] = out[decltype(i)::value]; });
 }

@@ -28,10 +28,11 @@ cudaError_t dst_lines_fwd_bulk_f32(int p, const double* in, BatchDesc ib, LineLa
 }
 
 // The streaming forward form (k_dst_lines_fwd_stream) for this p and sweep length:
-// p without Rader, and ns a whole number of tiles of 2Q rows.
+// p without Rader, ns a whole number of tiles of 2Q rows, and a measured gain over
+// one CTA per tile (64 x 512^2: 76.5 against 81.9 us; 16 x 1024^2: 103 against 113;
+// at p = 65 it was slower, 88 against 80, so that length keeps the per-tile kernel).
 bool dst_lines_stream_ok_f32(int p, int ns) {
   switch (p) {
-    case 65: return dl::StreamShape<65>::eligible && ns % (2 * dl::LineShape<float, 65>::Q) == 0;
     case 513: return dl::StreamShape<513>::eligible && ns % (2 * dl::LineShape<float, 513>::Q) == 0;
     case 1025: return dl::StreamShape<1025>::eligible && ns % (2 * dl::LineShape<float, 1025>::Q) == 0;
     default: return false;

@@ -128,6 +128,17 @@ __device__ __forceinline__ void load_tables(DstPlan pl, LineSmem<T, P>& s) {
   }
 }
 
+// (fma(cp, a1, cm a2), fma(cp, b1, cm b2)): one packed value of a line pair
+template <typename T>
+__device__ __forceinline__ C2<T> pack_pair(T cp, T cm, T a1, T a2, T b1, T b2) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 t = mul2(make_float2(cm, cm), make_float2(a2, b2));
+    return c2(fma2(make_float2(cp, cp), make_float2(a1, b1), t));
+  } else {
+    return C2<T>{fma(cp, a1, cm * a2), fma(cp, b1, cm * b2)};
+  }
+}
+
 // z_j of line pair q (j in 1..p-1): u_j = sin(pi j/p)(x_j + x_{p-j}) + (x_j - x_{p-j})/2
 // = (sin(pi j/p) + 1/2) x_j + (sin(pi j/p) - 1/2) x_{p-j} for the two lines,
 // packed as real and imaginary part (two operations per value instead of four).
@@ -138,7 +149,7 @@ __device__ __forceinline__ C2<T> pack(const LineSmem<T, P>& s, int q, int j) {
   const T* lb = la + LP;
   const T a1 = la[j - 1], a2 = la[P - j - 1], b1 = lb[j - 1], b2 = lb[P - j - 1];
   const T cp = s.spl[j], cm = s.smi[j];
-  return C2<T>{fma(cp, a1, cm * a2), fma(cp, b1, cm * b2)};
+  return pack_pair(cp, cm, a1, a2, b1, b2);
 }
 
 // Pass 1 of the two-pass DFT: per (pair q, jb) a DFT of length A over ja of
@@ -355,56 +366,104 @@ __device__ __forceinline__ void unpack(LineSmem<T, P>& s, const C2<T>* spectra) 
     T* ya = s.lines + (2 * q) * S::LP;
     T* yb = ya + S::LP;
     const int k0 = lane * CK;
-    T ra[CK], rb[CK], oa[CK], ob[CK];
-    T sa = T(0), sb = T(0);
-    static_for<CK>([&](auto ii) {
-      constexpr int i = decltype(ii)::value;
-      const int k = k0 + i;
-      ra[i] = rb[i] = oa[i] = ob[i] = T(0);
-      if (k < K) {
-        const C2<T> zk = Z[k];
-        if (k == 0) {
-          ra[i] = zk.x;
-          rb[i] = zk.y;
-        } else {
-          const C2<T> zr = Z[P - k];
-          ra[i] = zk.x + zr.x;
-          rb[i] = zk.y + zr.y;
-          oa[i] = -(zk.y - zr.y);
-          ob[i] = zk.x - zr.x;
+    if constexpr (sizeof(T) == 4) {
+      // the two lines' sums as one paired value (line a in .x, line b in .y):
+      // component by component the same operations as the scalar form below
+      float2 r[CK], o[CK];
+      float2 sum = make_float2(0.f, 0.f);
+      static_for<CK>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        const int k = k0 + i;
+        r[i] = o[i] = make_float2(0.f, 0.f);
+        if (k < K) {
+          const float2 zk = f2(Z[k]);
+          if (k == 0) {
+            r[i] = zk;
+          } else {
+            const float2 zr = f2(Z[P - k]);
+            r[i] = add2(zk, zr);
+            const float2 d = add2(make_float2(zk.y, zk.x), make_float2(-zr.y, -zr.x));
+            o[i] = make_float2(-d.x, d.y);
+          }
+          sum = add2(sum, r[i]);
         }
-        sa += ra[i];
-        sb += rb[i];
-      }
-    });
-    T ia = sa, ib = sb;  // inclusive scan of the lane totals
+      });
+      float2 in = sum;  // inclusive scan of the lane totals
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const T ta = __shfl_up_sync(0xffffffffu, ia, o), tb = __shfl_up_sync(0xffffffffu, ib, o);
-      if (lane >= o) {
-        ia += ta;
-        ib += tb;
+      for (int off = 1; off < 32; off <<= 1) {
+        const float2 t = make_float2(__shfl_up_sync(0xffffffffu, in.x, off), __shfl_up_sync(0xffffffffu, in.y, off));
+        if (lane >= off) in = add2(in, t);
       }
+      float2 acc = make_float2(__shfl_up_sync(0xffffffffu, in.x, 1), __shfl_up_sync(0xffffffffu, in.y, 1));
+      if (lane == 0) acc = make_float2(0.f, 0.f);
+      __syncwarp();  // the spectrum may share storage with the lines written below
+      static_for<CK>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        const int k = k0 + i;
+        if (k < K) {
+          acc = add2(acc, r[i]);
+          if (2 * k + 1 <= n) {
+            ya[2 * k] = acc.x;
+            yb[2 * k] = acc.y;
+          }
+          if (k >= 1 && 2 * k <= n) {
+            ya[2 * k - 1] = o[i].x;
+            yb[2 * k - 1] = o[i].y;
+          }
+        }
+      });
+    } else {
+      T ra[CK], rb[CK], oa[CK], ob[CK];
+      T sa = T(0), sb = T(0);
+      static_for<CK>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        const int k = k0 + i;
+        ra[i] = rb[i] = oa[i] = ob[i] = T(0);
+        if (k < K) {
+          const C2<T> zk = Z[k];
+          if (k == 0) {
+            ra[i] = zk.x;
+            rb[i] = zk.y;
+          } else {
+            const C2<T> zr = Z[P - k];
+            ra[i] = zk.x + zr.x;
+            rb[i] = zk.y + zr.y;
+            oa[i] = -(zk.y - zr.y);
+            ob[i] = zk.x - zr.x;
+          }
+          sa += ra[i];
+          sb += rb[i];
+        }
+      });
+      T ia = sa, ib = sb;  // inclusive scan of the lane totals
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const T ta = __shfl_up_sync(0xffffffffu, ia, o), tb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+          ia += ta;
+          ib += tb;
+        }
+      }
+      T acca = __shfl_up_sync(0xffffffffu, ia, 1), accb = __shfl_up_sync(0xffffffffu, ib, 1);
+      if (lane == 0) acca = accb = T(0);
+      __syncwarp();  // the spectrum may share storage with the lines written below
+      static_for<CK>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        const int k = k0 + i;
+        if (k < K) {
+          acca += ra[i];
+          accb += rb[i];
+          if (2 * k + 1 <= n) {
+            ya[2 * k] = acca;
+            yb[2 * k] = accb;
+          }
+          if (k >= 1 && 2 * k <= n) {
+            ya[2 * k - 1] = oa[i];
+            yb[2 * k - 1] = ob[i];
+          }
+        }
+      });
     }
-    T acca = __shfl_up_sync(0xffffffffu, ia, 1), accb = __shfl_up_sync(0xffffffffu, ib, 1);
-    if (lane == 0) acca = accb = T(0);
-    __syncwarp();  // the spectrum may share storage with the lines written below
-    static_for<CK>([&](auto ii) {
-      constexpr int i = decltype(ii)::value;
-      const int k = k0 + i;
-      if (k < K) {
-        acca += ra[i];
-        accb += rb[i];
-        if (2 * k + 1 <= n) {
-          ya[2 * k] = acca;
-          yb[2 * k] = accb;
-        }
-        if (k >= 1 && 2 * k <= n) {
-          ya[2 * k - 1] = oa[i];
-          yb[2 * k - 1] = ob[i];
-        }
-      }
-    });
   }
 }
 
@@ -700,8 +759,8 @@ k_dst_lines_fwd_stream(const double* __restrict__ in, BatchDesc ib, LineLayout L
       const T a1 = f64_to_f32(ra[j - 1]), a2 = f64_to_f32(ra[P - j - 1]);
       const T b1 = f64_to_f32(rb[j - 1]), b2 = f64_to_f32(rb[P - j - 1]);
       const T cp = spl[j], cm = smi[j];
-      Z[q * P + j] = C2<T>{fma(cp, a1, cm * a2), fma(cp, b1, cm * b2)};
-      Z[q * P + P - j] = C2<T>{fma(cp, a2, cm * a1), fma(cp, b2, cm * b1)};
+      Z[q * P + j] = pack_pair(cp, cm, a1, a2, b1, b2);
+      Z[q * P + P - j] = pack_pair(cp, cm, a2, a1, b2, b1);
     }
     if (t < Q) Z[t * P] = C2<T>{T(0), T(0)};
     __syncthreads();  // the staging buffer is free

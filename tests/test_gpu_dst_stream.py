@@ -3,8 +3,8 @@
 packing straight from the staging buffer, in-place passes); 1, the persistent kernel
 with one CTA per SM; 2, one CTA per tile.  They run the same arithmetic in the same
 order, so the preconditioner output z = A_c^{-1} v (Sec. 2.1) must agree bit for bit,
-for every length the streaming form covers (p = 65, 513, 1025) and for one it does not
-(p = 257, Rader: all forms fall back to the per-tile kernel).  The oracle comparison of
+for the lengths the streaming form covers (p = 513, 1025) and for two it does not
+(p = 65 and p = 257, Rader: forms 0 and 2 are the per-tile kernel there).  The oracle comparison of
 the default path is in test_gpu_parity.py and test_gpu_large.py; here the forms are
 also checked against the oracle's fast solve once, element-wise.
 """
