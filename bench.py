@@ -62,8 +62,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
                     help="default run: leave out the precision, batching and serving workloads")
-    ap.add_argument("--serving-prefix", type=int, default=1000,
+    ap.add_argument("--serving-prefix", type=int, default=200,
                     help="serving: requests of the stream's prefix served both batched and one at a time")
+    ap.add_argument("--configs-budget", type=float, default=720.0,
+                    help="default run: seconds for the precision, batching and serving workloads together; "
+                         "the full serving stream admits no request past it")
     return ap.parse_args()
 
 
@@ -506,7 +509,7 @@ def run_ours(args, rank, world):
         cfg = {}
         for name, fn in (("precision", lambda: config_precision(args, flush, pool)),
                          ("batching", lambda: config_batching(args, flush, pool)),
-                         ("serving", lambda: config_serving(args))):
+                         ("serving", lambda: config_serving(args, args.configs_budget - (time.perf_counter() - t0)))):
             print(f"bench: config {name} starts at {time.perf_counter() - t0:.0f} s", file=sys.stderr, flush=True)
             cfg[name] = fn()
         cfg["seconds"] = time.perf_counter() - t0
@@ -871,28 +874,27 @@ def serve_plain(requests, restart, rtol, precond_precision, budget_bytes, slot_r
     return [out[int(r["id"])] for r in requests], wall
 
 
-def config_serving(args):
-    """The serving workload: `args.requests` Poisson requests at `args.rate`/s
-    (L/T/cross, n in 64..1024, 1-8 RHS, kappa 0/-10, seeded RHS) through the
-    library's batch runtime (continuous batching, FP32 preconditioner, 120 GB
-    admission budget); and, on the first `args.serving_prefix` requests of the
-    same stream, the batch runtime against the plain FP64 method serving one
-    request at a time."""
+def config_serving(args, budget_s=None):
+    """The serving workload: on the first `args.serving_prefix` requests of the
+    stream, the library's batch runtime (continuous batching, FP32
+    preconditioner, 120 GB admission budget) against the plain FP64 method
+    serving one request at a time; then the whole stream, `args.requests`
+    Poisson requests at `args.rate`/s (L/T/cross, n in 64..1024, 1-8 RHS, kappa
+    0/-10, seeded RHS), through the batch runtime.  With `budget_s`, the whole
+    stream admits no request after what is left of that many seconds (at least
+    60) and reports how many it served."""
     import workloads as W
     from paper_2509_23180_gb300 import serve
+    t_start = time.perf_counter()
     reqs = W.serving_requests(args.requests, args.rate, seed=0)
     budget = args.budget_gb * 1e9
 
-    def native(rs):
+    def native(rs, deadline=None):
         t0 = time.perf_counter()
         res, st = serve.serve_native(rs, pool_bytes=budget, slot_rhs=8, restart=40, rtol=args.rtol,
-                                     precond_precision=32)
+                                     precond_precision=32, deadline_s=deadline)
         return res, time.perf_counter() - t0, st
 
-    res, wall, st = native(reqs)
-    full = serve.summarize(res, wall)
-    full.pop("failures", None) if full["all_converged"] else None
-    full.update({"domains_created": st["created"], "domains_evicted": st["evicted"]})
     pre = reqs[:min(args.serving_prefix, len(reqs))]
     res_b, wall_b, _ = native(pre)
     res_p, wall_p = serve_plain(pre, restart=40, rtol=args.rtol, precond_precision=64, budget_bytes=budget)
@@ -900,6 +902,15 @@ def config_serving(args):
     for x in (sb, sp):
         if x["all_converged"]:
             x.pop("failures", None)
+    deadline = None
+    if budget_s is not None:
+        deadline = max(60.0, budget_s - (time.perf_counter() - t_start))
+    res, wall, st = native(reqs, deadline)
+    full = serve.summarize(res, wall)
+    full.pop("failures", None) if full["all_converged"] else None
+    full.update({"requests_in_stream": len(reqs), "unserved_at_deadline": st["unserved"],
+                 "admission_deadline_s": deadline, "domains_created": st["created"],
+                 "domains_evicted": st["evicted"]})
     return {"workload": f"serving: {len(reqs)} Poisson requests at {args.rate:g}/s, geometry L/T/cross, "
                         f"n 64..1024, 1-8 RHS, kappa 0/-10; batch runtime (fpg_batch_*), FP32 preconditioner, "
                         f"FGMRES(40), rtol {args.rtol:g}, {args.budget_gb:g} GB budget",

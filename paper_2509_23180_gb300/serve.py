@@ -39,7 +39,7 @@ class Result:
 def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart: int = 40, rtol: float = 1e-10,
                  precond_precision: int = 32, max_domains: int = 64, max_per_key: int = 2, max_busy: int = 8,
                  realtime: bool = True, device: str = "cuda", io_bytes: float = 32e9,
-                 keep_solutions: bool = False):
+                 keep_solutions: bool = False, deadline_s: float | None = None):
     """The request stream through the library's batch runtime (fpg_batch_*).
     A producer thread plays the clients: at each request's arrival time it hands
     the request (its descriptor and seed, host side) to the driver thread.  The
@@ -52,8 +52,10 @@ def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart
     the driver steps it -- the runtime never waits on the device -- and collects
     the tickets it reports finished.  A request refused for lack of idle room
     keeps its buffers and is admitted first when room frees.  With
-    keep_solutions, each result carries its solution (a host tensor).  Returns
-    (results in request order, stats)."""
+    keep_solutions, each result carries its solution (a host tensor).  With
+    deadline_s, no request is admitted after that many seconds: the ones admitted
+    finish, the rest are left out and counted in stats["unserved"].  Returns
+    (results of the served requests in request order, stats)."""
     import queue
     from collections import deque
 
@@ -140,10 +142,20 @@ def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart
     th = threading.Thread(target=producer, daemon=True)
     th.start()
     produced_all = False
+    past_deadline = False
     try:
         while not produced_all or live or pending or head is not None:
             progressed = False
-            while True:  # arrivals: host side only
+            if deadline_s is not None and not past_deadline and time.perf_counter() - t0 > deadline_s:
+                # admit nothing more: drop the backlog, let the admitted requests finish
+                past_deadline = True
+                stop.set()
+                produced_all = True
+                pending.clear()
+                if head is not None:
+                    io_live -= head[4]
+                    head = None
+            while not past_deadline:  # arrivals: host side only
                 try:
                     r = ready.get_nowait()
                 except queue.Empty:
@@ -180,7 +192,9 @@ def serve_native(requests, pool_bytes: float = 120e9, slot_rhs: int = 8, restart
         stop.set()
         th.join()
         batch.close()
-    return [results[int(r["id"])] for r in requests], stats
+    served = [results[int(r["id"])] for r in requests if int(r["id"]) in results]
+    stats["unserved"] = len(requests) - len(served)
+    return served, stats
 
 
 def summarize(results, wall_s: float) -> dict:

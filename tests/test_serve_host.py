@@ -202,3 +202,23 @@ def test_a_failing_request_build_fails_the_loop(fake, monkeypatch):
     with pytest.raises(ValueError):
         S.serve_native(_requests(20), pool_bytes=1 << 40, realtime=False, device="cpu")
     assert hasattr(FakeBatch.log, "left")  # the runtime was still closed
+
+
+def test_admission_deadline_serves_a_prefix_and_counts_the_rest(fake):
+    """With deadline_s, nothing is admitted once that many seconds have passed:
+    the requests admitted before it finish and are reported in request order, the
+    others are counted as unserved, and the runtime is left empty."""
+    fake(latency=2)
+    reqs = _requests(30)
+    for i, q in enumerate(reqs):  # arrivals 0, 0.01, ... s apart in real time
+        q["arrival_s"] = 0.01 * i
+    res, stats = S.serve_native(reqs, pool_bytes=1 << 40, realtime=True, device="cpu", deadline_s=0.12)
+    served = [r.id for r in res]
+    assert 0 < len(served) < len(reqs)
+    assert served == [q["id"] for q in reqs][:len(served)]  # a prefix, in request order
+    assert stats["unserved"] == len(reqs) - len(served)
+    assert FakeBatch.log.left == 0
+    # no deadline: everything
+    fake(latency=2)
+    res, stats = S.serve_native(reqs, pool_bytes=1 << 40, realtime=False, device="cpu")
+    assert len(res) == len(reqs) and stats["unserved"] == 0
