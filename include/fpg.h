@@ -387,12 +387,14 @@ typedef enum {
    * fpg_fast_solve_path), 1 always the generic FFT engine, 2 the specialised
    * kernels wherever one is compiled. */
   FPG_OPT_DST_ENGINE = 7,
-  /* Reduced Schur term (FPG_SCHUR_REDUCED): 0 (default) as the O(n^2)
-   * Toeplitz-minus-Hankel sum c(|i-j|) - c(i+j+2), one thread per output;
-   * 1 as delta^2 Q diag(g_k) Q with two DST-I per interface line where the
-   * size-specialised DST is compiled (n = 64, 256, 512) -- fewer operations, but
-   * only (lines / line batch) CTAs, slower at the batch sizes measured so far.
-   * Same operator. */
+  /* Reduced Schur term (FPG_SCHUR_REDUCED) of the cross, T and L: 0 (default)
+   * as the product of the interface lines with the stored n x n matrix
+   * G(i, j) = T(|i-j|) - H(i+j) (all arms of a right-hand side per CTA: one
+   * FMA per element of G and arm); 1 as delta^2 Q diag(g_k) Q with two DST-I per
+   * interface line where the size-specialised DST is compiled (n = 64, 256,
+   * 512) -- fewer operations, but only (lines / line batch) CTAs; 2 as the
+   * Toeplitz-minus-Hankel sum c(|i-j|) - c(i+j+2) formed on the fly, one thread
+   * per output and arm.  Same operator; the forms differ only in rounding. */
   FPG_OPT_SCHUR_TRANSFORM = 8,
   /* Iterative-refinement steps (0..4, default 1) of every arm solve in the
    * setup (q_a = A_a^{-1} f_a) and the finish (p_a = A_a^{-1}(f_a - R_ac p_c)):

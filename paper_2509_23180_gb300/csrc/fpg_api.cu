@@ -24,6 +24,8 @@ bool fast_solve_cluster_tables(int n, double delta, double kappa, std::vector<fl
                                std::vector<float>& wseed);
 cudaError_t launch_schur_dst(const void* z, int zprec, long long zstride, int n, const DstPlan& pl, const double* gsc,
                              const int* arms, int narms, double* corr, const int* active, int nrhs, cudaStream_t st);
+cudaError_t launch_schur_gmat(const void* z, int zprec, long long zstride, int n, const double* G, const int* arms_dev,
+                              int narms, double* corr, const int* active, int nrhs, cudaStream_t st);
 cudaError_t launch_schur_reduced(const void* z, int zprec, long long zstride, int n, const double* ctab,
                                  const int* arms_dev, int narms, double* corr, const int* active, int nrhs,
                                  cudaStream_t st);
@@ -292,6 +294,7 @@ struct fpg_domain {
   FastSolveTables tR64, tR32;  // chain: the whole coupled row as one block (its A_c)
   LineLayout LR;
   double* ctab;
+  double* gmat = nullptr;  // reduced Schur form: G(i, j) = T(|i-j|) - H(i+j), n x n (cross, T, L)
   double* gsc;           // [n] g_k delta^2 / (2 (n+1)), the transform form of the reduced Schur term
   int schur_transform = 0;  // 1: reduced Schur term by two DST-I per line where compiled (else the table sum)
   int arm_refine = 1;       // FP64 refinement steps of every arm solve (setup and finish)
@@ -448,6 +451,9 @@ void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostP
     p = c.take(sizeof(float) * rows);  if (D) D->tR32.mneg = p;
   }
   p = c.take(sizeof(double) * (4 * n + 2));   if (D) D->ctab = (double*)p;
+  if (!L.chain && !L.lattice && d->schur_mode == FPG_SCHUR_REDUCED) {
+    p = c.take(sizeof(double) * (size_t)n * n); if (D) D->gmat = (double*)p;
+  }
   p = c.take(sizeof(double) * n);             if (D) D->gsc = (double*)p;
   p = c.take(sizeof(int) * 12);               if (D) D->arms_dev = (int*)p;
   p = c.take(sizeof(double) * nrhs * L.ntot); if (D) D->f = (double*)p;
@@ -723,9 +729,12 @@ fpg_status schur_corr(fpg_domain* D, const void* z, int zprec, int nvec, const i
     return FPG_OK;
   }
   if (D->desc.schur_mode == FPG_SCHUR_REDUCED) {
-    if (D->schur_transform && L.ao.bc == 0 && schur_dst_supported(L.n))
+    if (D->schur_transform == 1 && L.ao.bc == 0 && schur_dst_supported(L.n))
       FPG_CUDA_TRY(launch_schur_dst(z, zprec, L.nc, L.n, D->tC64.plan, D->gsc, D->arms_dev, L.narms, D->corr, active,
                                     nvec, D->st));
+    else if (D->schur_transform == 0 && D->gmat != nullptr)
+      FPG_CUDA_TRY(launch_schur_gmat(z, zprec, L.nc, L.n, D->gmat, D->arms_dev, L.narms, D->corr, active, nvec,
+                                     D->st));
     else
       FPG_CUDA_TRY(launch_schur_reduced(z, zprec, L.nc, L.n, D->ctab, D->arms_dev, L.narms, D->corr, active, nvec,
                                         D->st));
@@ -1407,6 +1416,13 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
     if (!err) err = cp(D->lat.lpiv, lh.lpiv.data(), sizeof(double) * lh.lpiv.size());
   }
   if (!err) err = cp(D->ctab, ct.data(), sizeof(double) * ct.size());
+  if (!err && D->gmat != nullptr) {
+    // G(j, i) = T(|i-j|) - H(i+j): the same values the table form forms on the fly
+    std::vector<double> G((size_t)n * n);
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) G[(size_t)j * n + i] = ct[i > j ? i - j : j - i] - ct[2 * n + 2 + i + j];
+    err = cp(D->gmat, G.data(), sizeof(double) * G.size());
+  }
   if (!err) err = cp(D->gsc, gs.data(), sizeof(double) * gs.size());
   if (!err) err = cp(D->arms_dev, arms, sizeof(arms));
   if (!err) err = cudaMemsetAsync(D->f, 0, sizeof(double) * nrhs * L.ntot, D->st);
@@ -1765,7 +1781,7 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_SCHUR_TRANSFORM:
-      if (value < 0 || value > 1) return FPG_EINVAL;
+      if (value < 0 || value > 2) return FPG_EINVAL;
       d->schur_transform = value;
       drop_graph(d);
       return FPG_OK;

@@ -970,6 +970,91 @@ __global__ void k_refine_tol(double* __restrict__ tolabs, const double* __restri
 
 // ---------------------------------------------------------------------------
 // Launchers (library-internal).
+// a2, reduced form as a matrix product: corr[r][a][i] = sum_j G(j, i) line_a[j] with
+// the interface matrix G(i, j) = T(|i-j|) - H(i+j) of the table above stored whole
+// (n x n, symmetric, built once per domain).  One CTA takes 16 outputs i of every arm
+// line of one right-hand side, the j range split over 16 groups of threads: each
+// element of G (read coalesced from L2) feeds one FMA per arm, where the table form
+// spends a subtraction and an FMA per arm and output.  Group partials are summed in
+// group order (deterministic).
+constexpr int kGTile = 16, kGGroups = 16;
+
+template <typename Tz>
+__global__ void __launch_bounds__(kGTile * kGGroups)
+k_schur_lines_g(const Tz* __restrict__ z, long long zstride, int n, const double* __restrict__ G,
+                const int* __restrict__ arms, int narms, double* __restrict__ corr, const int* __restrict__ active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* line = reinterpret_cast<double*>(smem_raw);  // [narms][n]
+  double* part = line + 4 * n;                         // [kGGroups][4][kGTile]
+  const int r = blockIdx.y;
+  if (active != nullptr && !active[r]) return;
+  const Tz* zr = z + (long long)r * zstride;
+  for (int q = threadIdx.x; q < narms * n; q += kGTile * kGGroups) {
+    const int a = q / n;
+    line[q] = c_line(zr, n, arms[a], q - a * n);
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % kGTile, ty = threadIdx.x / kGTile;
+  const int i = blockIdx.x * kGTile + tx;
+  const int per = (n + kGGroups - 1) / kGGroups;
+  const int j0 = ty * per, j1 = min(n, j0 + per);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < n) {
+    // eight elements of G in flight before their FMAs (the loop is bound by L2 latency)
+    constexpr int U = 8;
+    const double* gp = G + (long long)j0 * n + i;
+    int j = j0;
+    for (; j + U <= j1; j += U, gp += (long long)U * n) {
+      double g[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) g[u] = gp[(long long)u * n];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+          if (a < narms) acc[a] = fma(g[u], line[a * n + j + u], acc[a]);
+      }
+    }
+    for (; j < j1; ++j, gp += n) {
+      const double g = *gp;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        if (a < narms) acc[a] = fma(g, line[a * n + j], acc[a]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) part[(ty * 4 + a) * kGTile + tx] = acc[a];
+  __syncthreads();
+  if (threadIdx.x < 4 * kGTile) {
+    const int a = threadIdx.x / kGTile, t2 = threadIdx.x % kGTile;
+    const int i2 = blockIdx.x * kGTile + t2;
+    if (a < narms && i2 < n) {
+      double sum = part[a * kGTile + t2];
+      for (int g = 1; g < kGGroups; ++g) sum += part[(g * 4 + a) * kGTile + t2];
+      corr[((long long)r * 4 + arms[a]) * n + i2] = sum;
+    }
+  }
+}
+
+cudaError_t launch_schur_gmat(const void* z, int zprec, long long zstride, int n, const double* G, const int* arms_dev,
+                              int narms, double* corr, const int* active, int nrhs, cudaStream_t st) {
+  if (narms < 1 || narms > 4) return cudaErrorInvalidValue;
+  dim3 grid((n + kGTile - 1) / kGTile, nrhs);
+  const size_t smem = sizeof(double) * (4 * (size_t)n + kGGroups * 4 * kGTile);
+  static PerDeviceOnce attr_set;
+  if (attr_set.first()) {
+    cudaFuncSetAttribute(k_schur_lines_g<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_schur_lines_g<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  }
+  if (zprec == 64)
+    k_schur_lines_g<double><<<grid, kGTile * kGGroups, smem, st>>>((const double*)z, zstride, n, G, arms_dev, narms,
+                                                                   corr, active);
+  else
+    k_schur_lines_g<float><<<grid, kGTile * kGGroups, smem, st>>>((const float*)z, zstride, n, G, arms_dev, narms,
+                                                                  corr, active);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_schur_reduced(const void* z, int zprec, long long zstride, int n, const double* ctab,
                                  const int* arms_dev, int narms, double* corr, const int* active, int nrhs,
                                  cudaStream_t st) {

@@ -126,6 +126,43 @@ def test_schur_matvec_vs_oracle(lib, mode, geom, n, kappa):
     assert rel(host(w), want32) < 1e-11
 
 
+@pytest.mark.parametrize("geom,n,kappa,nrhs", [("cross", 64, 0.0, 3), ("T", 40, -10.0, 2), ("L", 256, -10.0, 5),
+                                               ("cross", 512, 0.0, 6)])
+def test_reduced_schur_forms_agree_with_the_oracle(lib, geom, n, kappa, nrhs):
+    """The three forms of the reduced Schur term (FPG_OPT_SCHUR_TRANSFORM: 0 the stored
+    interface matrix G, default; 1 two DST-I per line where compiled; 2 the
+    Toeplitz-minus-Hankel sum) give the same L_c z, element-wise, against each other
+    and -- up to n = 256 -- against the oracle's sparse solves; FP64 and FP32 input."""
+    from paper_2509_23180_gb300 import binding as B
+    zv = W.random_block_vectors(nrhs, n * n, seed=n + nrhs)
+    outs = {}
+    for form in (0, 1, 2):
+        d = domain(B, geom, n, kappa, nrhs=nrhs)
+        d.set_option(B.OPT_SCHUR_TRANSFORM, form)
+        for zp in (64, 32):
+            z = dev(zv) if zp == 64 else torch.as_tensor(zv, dtype=torch.float32, device="cuda")
+            w = torch.zeros((nrhs, n * n), dtype=torch.float64, device="cuda")
+            d.apply_schur(z, zp, w, nrhs)
+            outs[(form, zp)] = host(w)
+        d.close()
+    for zp in (64, 32):
+        for form in (1, 2):
+            assert rel(outs[(form, zp)], outs[(0, zp)]) < 1e-13, (form, zp)
+    if n <= 256:
+        K = O.assemble_grid(geom, n, kappa)
+        bs = S.BlockSystem(K, geom, n)
+        want = np.stack([bs.schur_apply(zi) for zi in zv])
+        assert rel(outs[(0, 64)], want) < 1e-11
+
+
+def test_reduced_schur_form_option_is_validated(lib):
+    from paper_2509_23180_gb300 import binding as B
+    d = domain(B, "cross", 16, 0.0, nrhs=1)
+    assert lib.fpg_set_option(d.handle, B.OPT_SCHUR_TRANSFORM, 3) == B.FPG_EINVAL
+    assert lib.fpg_set_option(d.handle, B.OPT_SCHUR_TRANSFORM, 2) == B.FPG_OK
+    d.close()
+
+
 # ---------------------------------------------------------------- a3 Arnoldi
 # lengths up to 262144 run the cluster kernel, longer ones the multi-launch MGS
 @pytest.mark.parametrize("j,length", [(0, 1000), (3, 4096), (12, 70001), (5, 300007)])
