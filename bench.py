@@ -476,7 +476,7 @@ def run_ours(args, rank, world):
     fp64_peak = B.probe_fma_peak(64)
     fp32_peak = B.probe_fma_peak(32)
     roof = roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, per_domain,
-                    run.doms[run.keys[0]].fast_solve_path())
+                    run.doms[run.keys[0]].fast_solve_path(), run.doms[run.keys[0]].arnoldi_shape())
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -566,7 +566,7 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, nrhs, fs_path=0):
+def roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, nrhs, fs_path=0, arnoldi_shape=None):
     """Roofline of the dominant kernel: its algorithmic work per launch over its
     average device duration.  Durations come from CUDA events the library
     records around each kernel launch when profiling is on (the a1 kernels one
@@ -609,6 +609,11 @@ def roofline(phases, costs, args, peaks, fp64_peak, fp32_peak, nrhs, fs_path=0):
                        "workload (sequential schedule) after the timed steps",
            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
            "traffic": traffic_for(kname, args, nrhs)}
+    if best == "arnoldi" and arnoldi_shape and arnoldi_shape.get("ctas"):
+        import torch
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        # one launch's CTAs against the SMs: a launch of c CTAs keeps at most min(c, SMs) SMs busy
+        out["launch_shape"] = {**arnoldi_shape, "sms": sms, "sm_share_max": min(1.0, arnoldi_shape["ctas"] / sms)}
     if fp64_kernel:
         out.update({"bound": "alu", "achieved": ach_alu / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
                     "frac": ach_alu / peak_alu, "hbm_frac": ach_hbm / hbm,

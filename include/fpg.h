@@ -571,6 +571,15 @@ fpg_status fpg_convert(const void* in, int32_t in_prec, void* out, int32_t out_p
  * (FPG_OPT_FUSED_FASTSOLVE), 4 = no fast solve (identity or Jacobi). */
 fpg_status fpg_fast_solve_path(fpg_domain* d, int32_t* path);
 
+/* Launch shape of the Arnoldi step (a3 + a4) this domain's solve runs with its
+ * current options: *kind 1 = register-resident cluster kernel
+ * (k_arnoldi_cluster_reg, stencil fused), 2 = cluster kernel with w in HBM
+ * (k_arnoldi_cluster), 0 = multi-launch MGS (no cluster); *cluster = CTAs per
+ * right-hand side (0 for kind 0), *threads = threads per CTA, *ctas = CTAs of one
+ * launch over all nrhs right-hand sides.  Any output pointer may be NULL.
+ * FPG_EINVAL on a null handle. */
+fpg_status fpg_arnoldi_shape(fpg_domain* d, int32_t* kind, int32_t* cluster, int32_t* threads, int32_t* ctas);
+
 /* FMA throughput of this GPU measured by a short library kernel (FLOP/s,
  * 2 per FMA): precision 64 or 32.  Used as the ALU roofline. */
 fpg_status fpg_probe_fma_peak(int32_t precision, double* flops_per_s);

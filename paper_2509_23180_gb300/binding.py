@@ -118,6 +118,8 @@ _SIGS = {
     "fpg_phase_stats": ([_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D)], _I32),
     "fpg_launch_count": ([_P, ctypes.POINTER(_I64)], _I32),
     "fpg_fast_solve_path": ([_P, ctypes.POINTER(_I32)], _I32),
+    "fpg_arnoldi_shape": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                           ctypes.POINTER(_I32)], _I32),
     "fpg_convert": ([_P, _I32, _P, _I32, _I64, _P], _I32),
     "fpg_neumann_workspace_bytes": ([_I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)], _I32),
     "fpg_neumann_solve": ([_I32, _I32, _D, _D, _P, _P, _I32, _P, ctypes.c_size_t, _P], _I32),
@@ -339,6 +341,14 @@ class Domain:
         out = _I32()
         _check(self.lib.fpg_fast_solve_path(self.handle, ctypes.byref(out)), "fpg_fast_solve_path")
         return int(out.value)
+
+    def arnoldi_shape(self) -> dict:
+        """fpg_arnoldi_shape: kernel form (1 register cluster, 2 cluster with w in HBM,
+        0 multi-launch MGS), CTAs per right-hand side, threads per CTA, CTAs per launch."""
+        k, c, t, n = _I32(), _I32(), _I32(), _I32()
+        _check(self.lib.fpg_arnoldi_shape(self.handle, ctypes.byref(k), ctypes.byref(c), ctypes.byref(t),
+                                          ctypes.byref(n)), "fpg_arnoldi_shape")
+        return {"kind": int(k.value), "cluster": int(c.value), "threads": int(t.value), "ctas": int(n.value)}
 
     def launch_count(self) -> int:
         out = _I64()

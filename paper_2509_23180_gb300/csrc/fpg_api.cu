@@ -93,6 +93,7 @@ void dct_tables(int n, std::vector<double>& W, std::vector<double>& post);
 void dct_pivots(int nt, int ns, double delta, double kappa, double end_extra, int end, std::vector<double>& r,
                 std::vector<double>& m);
 int arnoldi_reg_ept(long long len, int csz, int ntcap);
+int arnoldi_reg_threads(long long len, int csz, int ept);
 cudaError_t launch_arnoldi_reg(int csz, int ntcap, const double* V, long long vstride, const double* w,
                                const void* z, int zprec, const double* corr, int n, double delta, double kappa, int armmask,
                                double* vout, long long len, int j, int nrhs, double* H, int hcol_stride,
@@ -1832,6 +1833,27 @@ fpg_status fpg_set_history(fpg_domain* d, double* dev_buf, int32_t len) {
 fpg_status fpg_set_stream(fpg_domain* d, void* stream) {
   if (!d) return FPG_EINVAL;
   d->st = (cudaStream_t)stream;  // an instantiated cycle graph launches on any stream
+  return FPG_OK;
+}
+
+fpg_status fpg_arnoldi_shape(fpg_domain* d, int32_t* kind, int32_t* cluster, int32_t* threads, int32_t* ctas) {
+  if (!d) return FPG_EINVAL;
+  const Layout& L = d->L;
+  // the same choice as the solver's Arnoldi step
+  const int csz = d->use_cluster ? (d->tune_csz > 0 ? d->tune_csz : arnoldi_cluster_size(L.nc)) : 0;
+  const int ept = (csz > 0 && d->arnoldi_mode == 1 && !L.chain && !L.lattice) ? arnoldi_reg_ept(L.nc, csz, d->tune_nt)
+                                                                                 : 0;
+  int k = 0, t = 256;
+  if (ept > 0) {
+    k = 1;
+    t = arnoldi_reg_threads(L.nc, csz, ept);
+  } else if (csz > 0) {
+    k = 2;
+  }
+  if (kind) *kind = k;
+  if (cluster) *cluster = k ? csz : 0;
+  if (threads) *threads = t;
+  if (ctas) *ctas = k ? csz * d->desc.nrhs : 0;
   return FPG_OK;
 }
 

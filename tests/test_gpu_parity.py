@@ -698,3 +698,25 @@ def test_checkpoint_and_resume(lib):
     st, infoe = resumed.solve_resume(pe)
     assert st == B.FPG_OK and all(i["iterations"] == 0 for i in infoe)
     assert torch.equal(pe, dev(ref))
+
+
+@pytest.mark.parametrize("n,nrhs,option,kind", [(256, 5, None, 1), (512, 2, None, 2), (1024, 1, None, 0),
+                                                (256, 3, 0, 0), (256, 3, 2, 2)])
+def test_arnoldi_shape_reports_the_step_the_solver_runs(lib, n, nrhs, option, kind):
+    """fpg_arnoldi_shape names the Arnoldi kernel and its launch: the register kernel
+    (one 16-CTA cluster per right-hand side) at 256^2, the HBM-w cluster kernel at
+    512^2, the multi-launch MGS beyond 262144 points, and what FPG_OPT_ARNOLDI_CLUSTER
+    selects."""
+    from paper_2509_23180_gb300 import binding as B
+    d = domain(B, "cross", n, 0.0, nrhs=nrhs)
+    if option is not None:
+        d.set_option(B.OPT_ARNOLDI_CLUSTER, option)
+    sh = d.arnoldi_shape()
+    assert sh["kind"] == kind, sh
+    if kind:
+        assert sh["cluster"] >= 1 and sh["ctas"] == sh["cluster"] * nrhs and sh["threads"] % 32 == 0
+    else:
+        assert sh["cluster"] == 0 and sh["ctas"] == 0
+    if n == 256 and option is None:
+        assert sh["cluster"] == 16 and sh["ctas"] == 80
+    d.close()
