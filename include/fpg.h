@@ -433,7 +433,13 @@ typedef enum {
    * where compiled, else the built-in choice; 1, 2, 4 or 8), and warps (modes)
    * per CTA of the Thomas kernel (0: 8; 4 or 8). */
   FPG_OPT_DST_PAIRS = 13,
-  FPG_OPT_THOMAS_WARPS = 14
+  FPG_OPT_THOMAS_WARPS = 14,
+  /* 1 (default): the FP64 Thomas sweeps of the centre and the Dirichlet arms read
+   * the carries' running products of the multipliers (-delta r_s inside each lane's
+   * chunk of rows) from tables built with the domain, multiplied on the host in the
+   * kernel's own order: four FP64 multiplications per row fewer, bit-identical
+   * results.  0: the kernel forms them itself. */
+  FPG_OPT_THOMAS_PRODUCTS = 15
 } fpg_option;
 
 /* Move a domain to another CUDA stream (a cudaStream_t; NULL = the default

@@ -35,6 +35,7 @@ OPT_WAIT_LIMIT = 11
 OPT_CLUSTER_FASTSOLVE = 12
 OPT_DST_PAIRS = 13
 OPT_THOMAS_WARPS = 14
+OPT_THOMAS_PRODUCTS = 15
 PRECOND = {"fft": 0, "none": 1, "jacobi": 2}
 PHASES = ("precond", "schur", "arnoldi", "givens", "cycle_end", "setup_finish", "residual",
           "dst_forward", "thomas", "dst_inverse", "fast_solve_fused")

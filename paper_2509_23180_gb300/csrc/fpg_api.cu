@@ -393,6 +393,34 @@ void fill_ctab_dct(int n, double delta, const std::vector<double>& rpivA, std::v
   for (int m = 0; m < 2 * n; ++m) c[2 * n + 2 + m] = -c[m + 1];
 }
 
+// The FP64 Thomas kernel's carry products, for each mode k and each chunk of
+// thomas_chunk_rows(ns) rows: pf[k][s] = m_{c0} m_{c0+1} ... m_s (from the chunk's first
+// row c0) and pb[k][s] = m_{c1} m_{c1-1} ... m_s (from its last row c1), multiplied in
+// the kernel's own order so that the kernel's results do not change.
+void thomas_chunk_products(int n, int ns, const std::vector<double>& m, std::vector<double>& pf,
+                           std::vector<double>& pb) {
+  pf.assign((size_t)n * ns, 0.0);
+  pb.assign((size_t)n * ns, 0.0);
+  const int C = thomas_chunk_rows(ns);
+  if (C == 0) return;
+  for (int k = 0; k < n; ++k) {
+    const size_t row = (size_t)k * ns;
+    for (int c0 = 0; c0 < ns; c0 += C) {
+      const int c1 = std::min(ns, c0 + C) - 1;
+      double q = 1.0;
+      for (int s = c0; s <= c1; ++s) {
+        q *= m[row + s];
+        pf[row + s] = q;
+      }
+      q = 1.0;
+      for (int s = c1; s >= c0; --s) {
+        q *= m[row + s];
+        pb[row + s] = q;
+      }
+    }
+  }
+}
+
 // Carves every region; with base == nullptr only sizes are computed.
 void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostPlan* plan, Carver& c) {
   const int n = d->n, nrhs = d->nrhs, m = d->restart;
@@ -426,6 +454,13 @@ void carve(fpg_domain* D, const fpg_domain_desc* d, const Layout& L, const HostP
   p = c.take(sizeof(float) * L.nc);           if (D) D->tC32.mneg = p;
   p = c.take(sizeof(double) * L.na);          if (D) D->tA64.mneg = p;
   p = c.take(sizeof(float) * L.na);           if (D) D->tA32.mneg = p;
+  // FP64 Thomas: in-chunk products of mneg (centre, and Dirichlet arms)
+  p = c.take(sizeof(double) * L.nc);          if (D) D->tC64.pfwd = p;
+  p = c.take(sizeof(double) * L.nc);          if (D) D->tC64.pbwd = p;
+  if (d->boundary != FPG_BC_NEUMANN_SIDES) {
+    p = c.take(sizeof(double) * L.na);        if (D) D->tA64.pfwd = p;
+    p = c.take(sizeof(double) * L.na);        if (D) D->tA64.pbwd = p;
+  }
   if (d->boundary == FPG_BC_NEUMANN_SIDES) {
     // arms: DCT-II lines along t, pivots with the far-end row first (W, S) or last (E, N)
     DstPlan dp;
@@ -1378,6 +1413,17 @@ fpg_status fpg_create_domain(const fpg_domain_desc* desc, void* ws, size_t bytes
   if (!err) err = cp(D->tC64.mneg, mc.data(), sizeof(double) * mc.size());
   if (!err) err = cp(D->tC32.mneg, mc32.data(), sizeof(float) * mc32.size());
   if (!err) err = cp(D->tA64.mneg, ma.data(), sizeof(double) * ma.size());
+  {
+    std::vector<double> pf, pb;
+    thomas_chunk_products(n, n, mc, pf, pb);
+    if (!err) err = cp(D->tC64.pfwd, pf.data(), sizeof(double) * pf.size());
+    if (!err) err = cp(D->tC64.pbwd, pb.data(), sizeof(double) * pb.size());
+    if (D->tA64.pfwd != nullptr) {
+      thomas_chunk_products(n, as, ma, pf, pb);
+      if (!err) err = cp(D->tA64.pfwd, pf.data(), sizeof(double) * pf.size());
+      if (!err) err = cp(D->tA64.pbwd, pb.data(), sizeof(double) * pb.size());
+    }
+  }
   if (!err) err = cp(D->tA32.mneg, ma32.data(), sizeof(float) * ma32.size());
   if (L.chain) {  // pivots of the row's sweeps (length nxc); the DST-I tables are the centre's
     D->tR64.plan = D->tC64.plan;
@@ -1769,6 +1815,11 @@ fpg_status fpg_set_option(fpg_domain* d, int32_t option, int32_t value) {
     case FPG_OPT_CLUSTER_FASTSOLVE:
       if (value < 0 || value > 1) return FPG_EINVAL;
       d->tC32.cluster = value;
+      drop_graph(d);
+      return FPG_OK;
+    case FPG_OPT_THOMAS_PRODUCTS:
+      if (value < 0 || value > 1) return FPG_EINVAL;
+      for (auto* tt : {&d->tC64, &d->tA64}) tt->use_products = value;
       drop_graph(d);
       return FPG_OK;
     case FPG_OPT_WAIT_LIMIT:

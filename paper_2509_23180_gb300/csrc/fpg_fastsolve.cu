@@ -120,10 +120,14 @@ k_dense_forward(const double* __restrict__ in, BatchDesc ib, LineLayout L, int n
 template <int C>
 __host__ __device__ constexpr int thomas_pitch() { return C % 2 == 0 ? C + 1 : C + 2; }  // odd
 
-template <typename T, int C>
+// TAB: the carries' running products of m come from the tables pf / pb (the same
+// products in the same order, computed once on the host), which removes the four
+// multiplications per row that form them here; the results are bit-identical.
+template <typename T, int C, bool TAB>
 __global__ void __launch_bounds__(256)
 k_thomas_reg(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv, const T* __restrict__ mneg,
-             int nblk, const int* __restrict__ active, int nper_active) {
+             const T* __restrict__ pf, const T* __restrict__ pb, int nblk, const int* __restrict__ active,
+             int nper_active) {
   constexpr int PC = thomas_pitch<C>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // = b * n + k
@@ -162,16 +166,21 @@ k_thomas_reg(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv,
     x[e] = bf[lane * PC + e];
     if constexpr (kMreg) mr[e] = ml[e];
   }
+  // this lane's rows of the product tables (TAB)
+  const T* pfl = TAB ? pf + (long long)k * ns + s0 : nullptr;
+  const T* pbl = TAB ? pb + (long long)k * ns + s0 : nullptr;
+  const int nv = ns - s0 < C ? (ns - s0 > 0 ? ns - s0 : 0) : C;  // valid rows of the chunk
   // forward, zero carry
   T acc = T(0), pr = T(1);
 #pragma unroll
   for (int e = 0; e < C; ++e) {
     if (s0 + e < ns) {
       acc = fma(M(e), acc, x[e]);
-      pr *= M(e);
+      if constexpr (!TAB) pr *= M(e);
       x[e] = acc;
     }
   }
+  if constexpr (TAB) pr = nv > 0 ? pfl[nv - 1] : T(1);
   T Y = acc, P = pr;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -188,7 +197,10 @@ k_thomas_reg(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv,
 #pragma unroll
     for (int e = 0; e < C; ++e) {
       if (s0 + e < ns) {
-        q *= M(e);
+        if constexpr (TAB)
+          q = pfl[e];
+        else
+          q *= M(e);
         x[e] = fma(q, cin, x[e]);
       }
     }
@@ -200,10 +212,11 @@ k_thomas_reg(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv,
   for (int e = C - 1; e >= 0; --e) {
     if (s0 + e < ns) {
       acc = fma(M(e), acc, x[e]);
-      pr *= M(e);
+      if constexpr (!TAB) pr *= M(e);
       x[e] = acc;
     }
   }
+  if constexpr (TAB) pr = nv > 0 ? pbl[0] : T(1);
   Y = acc;
   P = pr;
 #pragma unroll
@@ -221,7 +234,10 @@ k_thomas_reg(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv,
 #pragma unroll
     for (int e = C - 1; e >= 0; --e) {
       if (s0 + e < ns) {
-        q *= M(e);
+        if constexpr (TAB)
+          q = pbl[e];
+        else
+          q *= M(e);
         x[e] = fma(q, cdn, x[e]);
       }
     }
@@ -387,23 +403,39 @@ k_thomas_long_smem(T* __restrict__ scratch, int n, int ns, const T* __restrict__
 // (0: 8; at most 8, the register kernel's launch bound of 256 threads; fewer
 // when the per-warp staging buffers would pass 96 KB), rows per lane C = the
 // smallest compiled value covering ns / 32.
+// A block kind's Thomas product table, when it was built for this sweep (its own
+// n and ns); null otherwise (the kernel then forms the products itself).
+template <typename T>
+const T* thomas_tab(const FastSolveTables& tb, int n, int ns, const void* table) {
+  return (table != nullptr && tb.use_products && tb.n == n && tb.ns == ns) ? (const T*)table : nullptr;
+}
+
+// pf / pb (optional, FP64): the in-chunk products of mneg for chunks of
+// thomas_chunk_rows(ns) rows (FastSolveTables::pfwd / pbwd); bit-identical results.
 template <typename T>
 cudaError_t launch_thomas(T* scratch, int n, int ns, const T* rpiv, const T* mneg, int nblk, const int* active,
-                          int nper_active, cudaStream_t st, int wpb) {
+                          int nper_active, cudaStream_t st, int wpb, const T* pf = nullptr, const T* pb = nullptr) {
   if (wpb <= 0 || wpb > 8) wpb = 8;
   const long long warps = (long long)nblk * n;
   const int need = (ns + 31) / 32;
+  const bool tab = pf != nullptr && pb != nullptr;
 #define FPG_THOMAS_C(CV)                                                                                    \
   if (need <= CV) {                                                                                         \
     static PerDeviceOnce attr;                                                                               \
     if (attr.first()) {                                                                                            \
-      cudaFuncSetAttribute(k_thomas_reg<T, CV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);   \
+      cudaFuncSetAttribute(k_thomas_reg<T, CV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+      cudaFuncSetAttribute(k_thomas_reg<T, CV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);  \
     }                                                                                                       \
     const size_t per = sizeof(T) * 2 * 32 * thomas_pitch<CV>();                                             \
     int w = wpb;                                                                                            \
     while (w > 1 && per * w > 96 * 1024) w /= 2;                                                            \
     const dim3 grid((unsigned)((warps + w - 1) / w));                                                       \
-    k_thomas_reg<T, CV><<<grid, 32 * w, per * w, st>>>(scratch, n, ns, rpiv, mneg, nblk, active, nper_active); \
+    if (tab && thomas_chunk_rows(ns) == CV)                                                                 \
+      k_thomas_reg<T, CV, true><<<grid, 32 * w, per * w, st>>>(scratch, n, ns, rpiv, mneg, pf, pb, nblk, active, \
+                                                              nper_active);                                 \
+    else                                                                                                    \
+      k_thomas_reg<T, CV, false><<<grid, 32 * w, per * w, st>>>(scratch, n, ns, rpiv, mneg, nullptr, nullptr,  \
+                                                               nblk, active, nper_active);                  \
     return cudaGetLastError();                                                                              \
   }
   FPG_THOMAS_C(1)
@@ -604,7 +636,8 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
                                                       nper_active);
     {
       const cudaError_t te = launch_thomas<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active,
-                                              nper_active, st, tb.mt);
+                                              nper_active, st, tb.mt, thomas_tab<T>(tb, n, L.ns, tb.pfwd),
+                                              thomas_tab<T>(tb, n, L.ns, tb.pbwd));
       if (te != cudaSuccess) return te;
     }
     k_dense_inverse<T, To><<<grid, kFsThreads, smem, st>>>(scratch, out, ob, L, n, (const T*)pl.dense, lpb,
@@ -621,7 +654,8 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
     if (ev) record_event(ev[2], st);
     {
       const cudaError_t te = launch_thomas<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active,
-                                              nper_active, st, tb.mt);
+                                              nper_active, st, tb.mt, thomas_tab<T>(tb, n, L.ns, tb.pfwd),
+                                              thomas_tab<T>(tb, n, L.ns, tb.pbwd));
       if (te != cudaSuccess) return te;
     }
     if (ev) record_event(ev[3], st);
@@ -648,7 +682,8 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
   if (e != cudaSuccess) return e;
   if (ev) record_event(ev[1], st);
   if (ev) record_event(ev[2], st);
-  e = launch_thomas<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st, tb.mt);
+  e = launch_thomas<T>(scratch, n, L.ns, (const T*)tb.rpiv, (const T*)tb.mneg, nblk, active, nper_active, st, tb.mt,
+                       thomas_tab<T>(tb, n, L.ns, tb.pfwd), thomas_tab<T>(tb, n, L.ns, tb.pbwd));
   if (e != cudaSuccess) return e;
   if (ev) record_event(ev[3], st);
   if (ev) record_event(ev[4], st);

@@ -44,6 +44,16 @@ struct LineLayout {
   long long st, ss;
 };
 
+// Rows per lane of the register Thomas kernel for a sweep of ns rows: the smallest
+// compiled chunk covering ns / 32 (0: the sweep is too long for it).
+__host__ __device__ inline int thomas_chunk_rows(int ns) {
+  const int need = (ns + 31) / 32;
+  const int chunks[] = {1, 2, 3, 4, 5, 8, 9, 12, 16, 17, 24, 32, 33};
+  for (int c : chunks)
+    if (need <= c) return c;
+  return 0;
+}
+
 // Everything the fast-solve kernels need for one block kind.
 struct FastSolveTables {
   int n;              // transform length (= domain n)
@@ -52,6 +62,12 @@ struct FastSolveTables {
   DstPlan plan;       // DST-I plan and tables in the compute precision
   const void* rpiv;   // Thomas reciprocal pivots r_s, [n][ns] (s fastest), compute precision
   const void* mneg;   // -delta r_s, [n][ns], compute precision
+  // FP64 only (else null): running products of mneg inside each lane's chunk of
+  // thomas_chunk_rows(ns) rows, from the chunk's first row (pfwd) and from its last
+  // (pbwd), [n][ns]: the products the Thomas kernel's carry fix-ups would form
+  const void* pfwd = nullptr;
+  const void* pbwd = nullptr;
+  int use_products = 1;  // 0: the kernel forms those products itself (same bits)
   int q = 0;          // line pairs per CTA in the DST kernels (0: built-in choice)
   int mt = 0;         // warps (= modes) per CTA in the Thomas kernel (0: 8)
   int fused = 0;      // 1: one-pass cluster kernel when the block fits
