@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Poisson solves/s and HBM GB/s at 1e-10 residual vs plain FP64 GPU; p50/p99 latency"
 # steps of the profiled pass whose per-launch kernel times give the roofline
-PROFILED_STEPS = 3
+PROFILED_STEPS = 5
 L2_FLUSH_BYTES = 512 << 20
 BAD_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
 
