@@ -123,11 +123,16 @@ __host__ __device__ constexpr int thomas_pitch() { return C % 2 == 0 ? C + 1 : C
 // TAB: the carries' running products of m come from the tables pf / pb (the same
 // products in the same order, computed once on the host), which removes the four
 // multiplications per row that form them here; the results are bit-identical.
-template <typename T, int C, bool TAB>
+// FULL: the sweep fills every lane's chunk (ns = 32 C) and C divides 32, so every row
+// is valid and the staging positions are a per-lane base plus compile-time offsets:
+// the same operations on the same values, without the index arithmetic and range
+// tests of the general form (which outnumber the floating-point work otherwise).
+template <typename T, int C, bool TAB, bool FULL>
 __global__ void __launch_bounds__(256)
 k_thomas_reg(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv, const T* __restrict__ mneg,
              const T* __restrict__ pf, const T* __restrict__ pb, int nblk, const int* __restrict__ active,
              int nper_active) {
+  static_assert(!FULL || 32 % C == 0, "the full form needs C | 32");
   constexpr int PC = thomas_pitch<C>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // = b * n + k
@@ -140,13 +145,27 @@ k_thomas_reg(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv,
   T* col = scratch + wg * ns;
   const T* rc = rpiv + (long long)k * ns;
   const T* mc = mneg + (long long)k * ns;
+  if constexpr (FULL) {
+    // s = 32 e + lane: s / C = e (32 / C) + lane / C and s % C = lane % C
+    const int lbase = (lane / C) * PC + lane % C;
+    const T* rcl = rc + lane;
+    const T* mcl = mc + lane;
+    const T* cl = col + lane;
 #pragma unroll
-  for (int e = 0; e < C; ++e) {
-    const int s = e * 32 + lane;
-    const int at = (s / C) * PC + (s % C);
-    const bool ok = s < ns;
-    bf[at] = ok ? rc[s] * col[s] : T(0);
-    bm[at] = ok ? mc[s] : T(0);
+    for (int e = 0; e < C; ++e) {
+      const int at = e * (32 / C) * PC + lbase;
+      bf[at] = rcl[32 * e] * cl[32 * e];
+      bm[at] = mcl[32 * e];
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < C; ++e) {
+      const int s = e * 32 + lane;
+      const int at = (s / C) * PC + (s % C);
+      const bool ok = s < ns;
+      bf[at] = ok ? rc[s] * col[s] : T(0);
+      bm[at] = ok ? mc[s] : T(0);
+    }
   }
   __syncwarp();
   const int s0 = lane * C;
@@ -174,7 +193,7 @@ k_thomas_reg(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv,
   T acc = T(0), pr = T(1);
 #pragma unroll
   for (int e = 0; e < C; ++e) {
-    if (s0 + e < ns) {
+    if (FULL || s0 + e < ns) {
       acc = fma(M(e), acc, x[e]);
       if constexpr (!TAB) pr *= M(e);
       x[e] = acc;
@@ -196,7 +215,7 @@ k_thomas_reg(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv,
     T q = T(1);
 #pragma unroll
     for (int e = 0; e < C; ++e) {
-      if (s0 + e < ns) {
+      if (FULL || s0 + e < ns) {
         if constexpr (TAB)
           q = pfl[e];
         else
@@ -210,7 +229,7 @@ k_thomas_reg(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv,
   pr = T(1);
 #pragma unroll
   for (int e = C - 1; e >= 0; --e) {
-    if (s0 + e < ns) {
+    if (FULL || s0 + e < ns) {
       acc = fma(M(e), acc, x[e]);
       if constexpr (!TAB) pr *= M(e);
       x[e] = acc;
@@ -233,7 +252,7 @@ k_thomas_reg(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv,
     T q = T(1);
 #pragma unroll
     for (int e = C - 1; e >= 0; --e) {
-      if (s0 + e < ns) {
+      if (FULL || s0 + e < ns) {
         if constexpr (TAB)
           q = pbl[e];
         else
@@ -246,10 +265,17 @@ k_thomas_reg(T* __restrict__ scratch, int n, int ns, const T* __restrict__ rpiv,
 #pragma unroll
   for (int e = 0; e < C; ++e) bf[lane * PC + e] = x[e];
   __syncwarp();
+  if constexpr (FULL) {
+    const int lbase = (lane / C) * PC + lane % C;
+    T* cl = col + lane;
 #pragma unroll
-  for (int e = 0; e < C; ++e) {
-    const int s = e * 32 + lane;
-    if (s < ns) col[s] = bf[(s / C) * PC + (s % C)];
+    for (int e = 0; e < C; ++e) cl[32 * e] = bf[e * (32 / C) * PC + lbase];
+  } else {
+#pragma unroll
+    for (int e = 0; e < C; ++e) {
+      const int s = e * 32 + lane;
+      if (s < ns) col[s] = bf[(s / C) * PC + (s % C)];
+    }
   }
 }
 
@@ -410,6 +436,39 @@ const T* thomas_tab(const FastSolveTables& tb, int n, int ns, const void* table)
   return (table != nullptr && tb.use_products && tb.n == n && tb.ns == ns) ? (const T*)table : nullptr;
 }
 
+// One launch of the register Thomas kernel in the form the sweep allows.
+template <typename T, int C, bool TAB, bool FULL>
+cudaError_t thomas_launch_one(dim3 grid, int threads, size_t smem, cudaStream_t st, T* scratch, int n, int ns,
+                              const T* rpiv, const T* mneg, const T* pf, const T* pb, int nblk, const int* active,
+                              int nper_active) {
+  static PerDeviceOnce attr;
+  if (attr.first())
+    cudaFuncSetAttribute(k_thomas_reg<T, C, TAB, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  k_thomas_reg<T, C, TAB, FULL><<<grid, threads, smem, st>>>(scratch, n, ns, rpiv, mneg, TAB ? pf : nullptr,
+                                                            TAB ? pb : nullptr, nblk, active, nper_active);
+  return cudaGetLastError();
+}
+
+template <typename T, int C>
+cudaError_t thomas_launch(bool tab, bool full, dim3 grid, int threads, size_t smem, cudaStream_t st, T* scratch,
+                          int n, int ns, const T* rpiv, const T* mneg, const T* pf, const T* pb, int nblk,
+                          const int* active, int nper_active) {
+  if constexpr (32 % C == 0) {
+    if (full) {
+      if (tab)
+        return thomas_launch_one<T, C, true, true>(grid, threads, smem, st, scratch, n, ns, rpiv, mneg, pf, pb, nblk,
+                                                   active, nper_active);
+      return thomas_launch_one<T, C, false, true>(grid, threads, smem, st, scratch, n, ns, rpiv, mneg, pf, pb, nblk,
+                                                  active, nper_active);
+    }
+  }
+  if (tab)
+    return thomas_launch_one<T, C, true, false>(grid, threads, smem, st, scratch, n, ns, rpiv, mneg, pf, pb, nblk,
+                                                active, nper_active);
+  return thomas_launch_one<T, C, false, false>(grid, threads, smem, st, scratch, n, ns, rpiv, mneg, pf, pb, nblk,
+                                               active, nper_active);
+}
+
 // pf / pb (optional, FP64): the in-chunk products of mneg for chunks of
 // thomas_chunk_rows(ns) rows (FastSolveTables::pfwd / pbwd); bit-identical results.
 template <typename T>
@@ -421,22 +480,14 @@ cudaError_t launch_thomas(T* scratch, int n, int ns, const T* rpiv, const T* mne
   const bool tab = pf != nullptr && pb != nullptr;
 #define FPG_THOMAS_C(CV)                                                                                    \
   if (need <= CV) {                                                                                         \
-    static PerDeviceOnce attr;                                                                               \
-    if (attr.first()) {                                                                                            \
-      cudaFuncSetAttribute(k_thomas_reg<T, CV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
-      cudaFuncSetAttribute(k_thomas_reg<T, CV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);  \
-    }                                                                                                       \
     const size_t per = sizeof(T) * 2 * 32 * thomas_pitch<CV>();                                             \
     int w = wpb;                                                                                            \
     while (w > 1 && per * w > 96 * 1024) w /= 2;                                                            \
     const dim3 grid((unsigned)((warps + w - 1) / w));                                                       \
-    if (tab && thomas_chunk_rows(ns) == CV)                                                                 \
-      k_thomas_reg<T, CV, true><<<grid, 32 * w, per * w, st>>>(scratch, n, ns, rpiv, mneg, pf, pb, nblk, active, \
-                                                              nper_active);                                 \
-    else                                                                                                    \
-      k_thomas_reg<T, CV, false><<<grid, 32 * w, per * w, st>>>(scratch, n, ns, rpiv, mneg, nullptr, nullptr,  \
-                                                               nblk, active, nper_active);                  \
-    return cudaGetLastError();                                                                              \
+    const bool full = (32 % CV == 0) && ns == 32 * CV;                                                      \
+    const bool tb_ok = tab && thomas_chunk_rows(ns) == CV;                                                  \
+    return thomas_launch<T, CV>(tb_ok, full, grid, 32 * w, per * w, st, scratch, n, ns, rpiv, mneg, pf, pb,   \
+                                nblk, active, nper_active);                                                 \
   }
   FPG_THOMAS_C(1)
   FPG_THOMAS_C(2)
