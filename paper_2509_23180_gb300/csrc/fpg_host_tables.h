@@ -28,12 +28,17 @@ struct Carver {
 
 // Host tables in FP64 -------------------------------------------------------
 inline double cos_pi_frac(long long num, long long den) {
-  // cos(pi num / den) with exact folding to [0, pi/2]
+  // cos(pi num / den) with exact folding to the first octant: the integer angle is
+  // reduced to [0, pi/2] by symmetry, and past pi/4 the value is taken as the sine of
+  // the complementary angle, so an entry near zero keeps its relative accuracy and
+  // cos(pi/2) is exactly 0
   long long q = num % (2 * den);
   if (q < 0) q += 2 * den;
   if (q > den) q = 2 * den - q;                   // cos(2pi - x) = cos x
   double sign = 1.0;
   if (2 * q > den) { q = den - q; sign = -1.0; }  // cos(pi - x) = -cos x
+  if (4 * q > den)                                // cos x = sin(pi/2 - x)
+    return sign * std::sin(M_PI * (double)(den - 2 * q) / (double)(2 * den));
   return sign * std::cos(M_PI * (double)q / (double)den);
 }
 

@@ -8,9 +8,8 @@ pivots of every mode.  A small host program built from the library's own header
   * Rader: pin[b] = g^b mod p with g of order p - 1 (so pin is a permutation of
     1..p-1), pout = its inverse powers, and Bhat = DFT(B)/N (numpy FFT), which
     makes the Rader convolution reproduce numpy's DFT of length p;
-  * sinp[j] = sin(pi j / p) within 3e-16 of 40-digit values (an absolute bound:
-    the table is computed as cos(pi/2 - pi j/p), so small entries carry a large
-    relative error, which the DST packing does not see);
+  * sinp[j] = sin(pi j / p) within 4 units in the last place of 40-digit values
+    (a relative bound, which the folding to the first octant gives), sinp[0] = 0;
   * a Thomas sweep with the printed reciprocal pivots solves tridiag(delta,
     d_k, delta) x = f as LAPACK's banded solver does (scipy), with
     d_k = -4 delta + 2 delta cos(k pi/(n+1)) + kappa (Sec. 2.1, Eq. "trans_subeq").
@@ -156,12 +155,16 @@ def test_sine_table(tables, n):
     s = _hex(rec[("SINP", n)])
     assert len(s) == p
     mpmath.mp.dps = 40
-    worst = max(abs(float(mpmath.mpf(s[j]) - mpmath.sin(mpmath.pi * j / p))) for j in range(p))
-    # absolute accuracy (what the packing u_j = sin(pi j/p)(x_j + x_{p-j}) + (x_j - x_{p-j})/2
-    # needs): the table is cos(pi q/den) after exact folding, and the rounding of the
-    # argument pi q/den (up to ~3e-16 near pi/2) carries over; measured worst 2.58e-16,
-    # with j = 0 holding cos(pi/2) = 6.1e-17 in place of 0
-    assert worst <= 3e-16, worst
+    assert s[0] == 0.0
+    # relative accuracy: the folding to the first octant is exact in integers, so each
+    # entry is the sine or cosine of an angle in [0, pi/4] whose only error is the
+    # rounding of pi q/den (a few units in its last place), which the sine passes on
+    # relatively and the cosine damps; measured worst 2.37 * 2^-53 over these sizes,
+    # and the bound of 4 * 2^-53 leaves room for the library function's own error
+    for j in range(1, p):
+        exact = mpmath.sin(mpmath.pi * j / p)
+        err = abs(float((mpmath.mpf(s[j]) - exact) / exact))
+        assert err <= 4 * 2.0 ** -53, (j, err)
 
 
 def test_rader_tables_reproduce_the_dft(tables):
