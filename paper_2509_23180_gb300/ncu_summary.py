@@ -5,7 +5,8 @@
       `--metrics gpu__time_duration.sum --csv` launch list)
   python -m paper_2509_23180_gb300.ncu_summary raw <raw.csv>
       per captured launch: duration, DRAM bytes read+write, DRAM throughput,
-      FP64/FP32 pipe and issue utilisation, occupancy, registers (from
+      FP64/FP32 pipe and issue utilisation, occupancy, registers, stalls and,
+      where captured, instruction counts by class (from
       `ncu -i <report> --page raw --csv`)
 """
 from __future__ import annotations
@@ -73,7 +74,19 @@ WANT = [
     ("smsp__average_warps_issue_stalled_math_pipe_throttle_per_issue_active.ratio", "stall_math"),
     ("smsp__average_warps_issue_stalled_wait_per_issue_active.ratio", "stall_wait"),
     ("smsp__average_warps_issue_stalled_mio_throttle_per_issue_active.ratio", "stall_mio"),
+    ("smsp__issue_active.avg.pct_of_peak_sustained_active", "issue_active_pct"),
 ]
+
+# instruction counts, printed in millions; the FP32 classes are summed into paired
+# (FFMA2, FADD2, FMUL2: two binary32 lanes each) and scalar instructions
+COUNTS = [
+    ("smsp__inst_executed.sum", "warp_inst"),
+    ("smsp__sass_thread_inst_executed.sum", "thread_inst"),
+    ("smsp__sass_thread_inst_executed_op_integer_pred_on.sum", "integer"),
+    ("smsp__sass_thread_inst_executed_op_memory_pred_on.sum", "memory"),
+]
+FP32_PAIRED = ["ffma2", "fadd2", "fmul2"]
+FP32_SCALAR = ["ffma", "fadd", "fmul"]
 
 
 def raw(path: str) -> str:
@@ -105,6 +118,24 @@ def raw(path: str) -> str:
                 parts.append(f"{label}={v / 1e6:.3f}MB")
             else:
                 parts.append(f"{label}={v:.2f}")
+
+        def value(metric):
+            i = col.get(metric)
+            if i is None or not r[i]:
+                return None
+            try:
+                return float(r[i].replace(",", ""))
+            except ValueError:
+                return None
+
+        for metric, label in COUNTS:
+            v = value(metric)
+            if v is not None:
+                parts.append(f"{label}={v / 1e6:.1f}M")
+        for label, ops in (("fp32_paired", FP32_PAIRED), ("fp32_scalar", FP32_SCALAR)):
+            vals = [value(f"smsp__sass_thread_inst_executed_op_{o}_pred_on.sum") for o in ops]
+            if any(v is not None for v in vals):
+                parts.append(f"{label}={sum(v or 0.0 for v in vals) / 1e6:.1f}M")
         out.append("  ".join(parts))
     return "\n".join(out)
 

@@ -44,3 +44,15 @@ def test_raw_page_line(tmp_path):
 
 def test_usage_without_arguments():
     assert S.main(["ncu_summary"]) == 2
+
+
+def test_raw_page_instruction_mix(tmp_path):
+    p = tmp_path / "raw.csv"
+    cols = ["smsp__inst_executed.sum", "smsp__sass_thread_inst_executed_op_integer_pred_on.sum",
+            "smsp__sass_thread_inst_executed_op_ffma2_pred_on.sum", "smsp__sass_thread_inst_executed_op_fadd2_pred_on.sum",
+            "smsp__sass_thread_inst_executed_op_ffma_pred_on.sum"]
+    p.write_text('"Kernel Name",' + ",".join(f'"{c}"' for c in cols) + "\n"
+                 + '"",' + ",".join('"inst"' for _ in cols) + "\n"
+                 + '"k_x(float *)","28,880,000","343,000,000","200,000,000","20,000,000","5,000,000"\n')
+    out = S.raw(str(p))
+    assert out == "k_x  warp_inst=28.9M  integer=343.0M  fp32_paired=220.0M  fp32_scalar=5.0M"
