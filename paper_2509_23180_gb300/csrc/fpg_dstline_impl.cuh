@@ -22,11 +22,11 @@ struct LineCfg;
     static constexpr bool rader = RD;              \
   };
 FPG_LINECFG(float, 65, 13, 5, false, 16, 256)
-FPG_LINECFG(float, 257, 16, 16, true, 12, 192)
+FPG_LINECFG(float, 257, 16, 16, true, 8, 128)
 FPG_LINECFG(float, 513, 27, 19, false, 8, 256)
 FPG_LINECFG(float, 1025, 25, 41, false, 4, 192)
 FPG_LINECFG(double, 65, 13, 5, false, 16, 256)
-FPG_LINECFG(double, 257, 16, 16, true, 4, 256)
+FPG_LINECFG(double, 257, 16, 16, true, 1, 64)
 FPG_LINECFG(double, 513, 27, 19, false, 4, 128)
 #undef FPG_LINECFG
 
