@@ -254,7 +254,7 @@ cudaError_t launch_chain_schur(const void* z, int zprec, long long zstride, cons
   dim3 grid((n + 31) / 32, nrhs * (2 * G.K + 2));
   const size_t smem = sizeof(double) * (5 * n + 2 + 256);
   static PerDeviceOnce attr_set;
-  if (attr_set.first()) {
+  if (auto once = attr_set.first()) {
     cudaFuncSetAttribute(k_chain_schur_lines<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_chain_schur_lines<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }

@@ -249,7 +249,7 @@ cudaError_t launch_cluster_p(const FastSolveTables& tb, const double* in, BatchD
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (attr.first()) {
+  if (auto once = attr.first()) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CS::bytes);
     if (CS::C > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     int clusters = 0;

@@ -820,12 +820,14 @@ cudaError_t fwd_stream_one(const double* in, BatchDesc ib, LineLayout L, const D
     static int per_sm_of[64] = {};
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
-    int per_sm = (dev >= 0 && dev < 64) ? per_sm_of[dev] : 0;
-    if (attr.first() || per_sm == 0) {
+    int per_sm = 0;
+    if (auto once = attr.first()) {  // the occupancy is recorded before the device is marked done
       cudaFuncSetAttribute(k_dst_lines_fwd_stream<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SS::bytes);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dst_lines_fwd_stream<P>, S::NT, SS::bytes);
       if (per_sm < 1) per_sm = 1;
       if (dev >= 0 && dev < 64) per_sm_of[dev] = per_sm;
+    } else if (dev >= 0 && dev < 64) {
+      per_sm = per_sm_of[dev];
     }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long total = (long long)nblk * (L.ns / (2 * S::Q));
@@ -904,7 +906,7 @@ cudaError_t fwd_one(const double* in, BatchDesc ib, LineLayout L, const DstPlan&
                     const int* active, int nper_active, int vec, cudaStream_t st) {
   using S = LineShape<T, P>;
   static PerDeviceOnce attr;
-  if (attr.first()) {
+  if (auto once = attr.first()) {
     cudaFuncSetAttribute(k_dst_lines_fwd<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
   }
   dim3 grid((L.ns + 2 * S::Q - 1) / (2 * S::Q), nblk);
@@ -921,12 +923,14 @@ cudaError_t fwd_bulk_one(const double* in, BatchDesc ib, LineLayout L, const Dst
   static int per_sm_of[64] = {};
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
-  int per_sm = (dev >= 0 && dev < 64) ? per_sm_of[dev] : 0;
-  if (attr.first() || per_sm == 0) {
+  int per_sm = 0;
+  if (auto once = attr.first()) {  // the occupancy is recorded before the device is marked done
     cudaFuncSetAttribute(k_dst_lines_fwd_bulk<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BS::bytes);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dst_lines_fwd_bulk<T, P>, S::NT, BS::bytes);
     if (per_sm < 1) per_sm = 1;
     if (dev >= 0 && dev < 64) per_sm_of[dev] = per_sm;
+  } else if (dev >= 0 && dev < 64) {
+    per_sm = per_sm_of[dev];
   }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int tpb = (L.ns + 2 * S::Q - 1) / (2 * S::Q);
@@ -942,7 +946,7 @@ cudaError_t inv_one(const T* scratch, To* out, BatchDesc ob, LineLayout L, const
                     const int* active, int nper_active, int vec, cudaStream_t st) {
   using S = LineShape<T, P>;
   static PerDeviceOnce attr;
-  if (attr.first()) {
+  if (auto once = attr.first()) {
     cudaFuncSetAttribute(k_dst_lines_inv<T, To, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
   }
   // 2/p for the normalisation, 1/4 for the two left-out factors 1/2 (exact)

@@ -442,7 +442,7 @@ cudaError_t thomas_launch_one(dim3 grid, int threads, size_t smem, cudaStream_t 
                               const T* rpiv, const T* mneg, const T* pf, const T* pb, int nblk, const int* active,
                               int nper_active) {
   static PerDeviceOnce attr;
-  if (attr.first())
+  if (auto once = attr.first())
     cudaFuncSetAttribute(k_thomas_reg<T, C, TAB, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   k_thomas_reg<T, C, TAB, FULL><<<grid, threads, smem, st>>>(scratch, n, ns, rpiv, mneg, TAB ? pf : nullptr,
                                                             TAB ? pb : nullptr, nblk, active, nper_active);
@@ -509,7 +509,7 @@ cudaError_t launch_thomas(T* scratch, int n, int ns, const T* rpiv, const T* mne
   const int wl = (int)std::min<size_t>(8, (size_t)(200 * 1024) / per);
   if (wl >= 1) {
     static PerDeviceOnce attr;
-    if (attr.first()) {
+    if (auto once = attr.first()) {
       cudaFuncSetAttribute(k_thomas_long_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     }
     const dim3 grid((unsigned)((warps + wl - 1) / wl));
@@ -674,7 +674,7 @@ cudaError_t fast_solve_impl(const FastSolveTables& tb, LineLayout L, const doubl
                             int nper_active, cudaStream_t st, cudaEvent_t* ev) {
   const int n = tb.n;
   static PerDeviceOnce attr_set;
-  if (attr_set.first()) {
+  if (auto once = attr_set.first()) {
     cudaFuncSetAttribute(k_dense_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dense_inverse<T, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
@@ -763,7 +763,7 @@ cudaError_t launch_dst_pass(bool forward, const FastSolveTables& tb, LineLayout 
   const DstPlan& pl = tb.plan;
   if (pl.mode == DST_DENSE) {
     static PerDeviceOnce attr_set;
-    if (attr_set.first()) {
+    if (auto once = attr_set.first()) {
       cudaFuncSetAttribute(k_dense_forward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(k_dense_inverse<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            200 * 1024);

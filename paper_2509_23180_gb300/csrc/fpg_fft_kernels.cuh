@@ -98,7 +98,7 @@ template <typename T, int MAXR>
 cudaError_t fft_fwd_launch(dim3 grid, size_t smem, cudaStream_t st, const double* in, BatchDesc ib, LineLayout L,
                            const DstPlan& pl, T* scratch, int Q, const int* active, int nper_active) {
   static PerDeviceOnce attr;
-  if (attr.first()) {
+  if (auto once = attr.first()) {
     cudaFuncSetAttribute(k_fft_forward<T, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
   k_fft_forward<T, MAXR><<<grid, kFftThreads, smem, st>>>(in, ib, L, pl, scratch, Q, active, nper_active);
@@ -109,7 +109,7 @@ template <typename T, typename To, int MAXR>
 cudaError_t fft_inv_launch(dim3 grid, size_t smem, cudaStream_t st, const T* scratch, To* out, BatchDesc ob,
                            LineLayout L, const DstPlan& pl, int Q, const int* active, int nper_active) {
   static PerDeviceOnce attr;
-  if (attr.first()) {
+  if (auto once = attr.first()) {
     cudaFuncSetAttribute(k_fft_inverse<T, To, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
   k_fft_inverse<T, To, MAXR><<<grid, kFftThreads, smem, st>>>(scratch, out, ob, L, pl, Q, active, nper_active);

@@ -210,7 +210,7 @@ cudaError_t launch_fused_impl(int csz, int R, int Q, const FastSolveTables& tb, 
                               BatchDesc ib, To* out, BatchDesc ob, int nblk, const int* active, int nper_active,
                               cudaStream_t st) {
   static PerDeviceOnce attr;
-  if (attr.first()) {
+  if (auto once = attr.first()) {
     cudaFuncSetAttribute(k_fast_solve_fused<T, To, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_fast_solve_fused<T, To, MAXR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   }

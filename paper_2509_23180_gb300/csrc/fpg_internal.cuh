@@ -9,22 +9,9 @@
 
 #include "fpg.h"
 #include "fpg_dst.cuh"
+#include "fpg_once.h"
 
 namespace fpg {
-
-// Function attributes (cudaFuncSetAttribute) apply to the current device only, so
-// a kernel's attributes are set once per device.  `first()` is true the first time
-// it is asked on the current device (and always for device ordinals past 63).
-struct PerDeviceOnce {
-  bool done[64] = {};
-  bool first() {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
-    if (done[dev]) return false;
-    done[dev] = true;
-    return true;
-  }
-};
 
 // ---------------------------------------------------------------------------
 // Batch of blocks of one shape inside larger vectors.  Block b of a launch lives

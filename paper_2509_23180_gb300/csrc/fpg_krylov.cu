@@ -1042,7 +1042,7 @@ cudaError_t launch_schur_gmat(const void* z, int zprec, long long zstride, int n
   dim3 grid((n + kGTile - 1) / kGTile, nrhs);
   const size_t smem = sizeof(double) * (4 * (size_t)n + kGGroups * 4 * kGTile);
   static PerDeviceOnce attr_set;
-  if (attr_set.first()) {
+  if (auto once = attr_set.first()) {
     cudaFuncSetAttribute(k_schur_lines_g<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_schur_lines_g<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
@@ -1061,7 +1061,7 @@ cudaError_t launch_schur_reduced(const void* z, int zprec, long long zstride, in
   dim3 grid((n + 31) / 32, nrhs * narms);
   const size_t smem = sizeof(double) * (5 * n + 2 + 256);
   static PerDeviceOnce attr_set;
-  if (attr_set.first()) {
+  if (auto once = attr_set.first()) {
     cudaFuncSetAttribute(k_schur_lines<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_schur_lines<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
@@ -1168,7 +1168,7 @@ cudaError_t launch_arnoldi_cluster(int csz, const double* V, long long vstride, 
                                    int* active, int* kcyc, int* iters, int max_iters, int do_givens,
                                    cudaStream_t st) {
   static PerDeviceOnce attr;
-  if (attr.first()) {
+  if (auto once = attr.first()) {
     cudaFuncSetAttribute(k_arnoldi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   }
   cudaLaunchConfig_t cfg = {};
@@ -1222,7 +1222,7 @@ cudaError_t launch_reg_impl(int csz, const double* V, long long vstride, const d
                             double* sn, double* g, double* res, int m, const double* tolabs, int* active, int* kcyc,
                             int* iters, int max_iters, int do_givens, int* err, cudaStream_t st) {
   static PerDeviceOnce attr;
-  if (attr.first()) {
+  if (auto once = attr.first()) {
     cudaFuncSetAttribute(k_arnoldi_cluster_reg<Tz, EPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   }
   cudaLaunchConfig_t cfg = {};

@@ -230,7 +230,7 @@ cudaError_t launch_lattice_schur(const void* z, int zprec, long long zstride, do
     const size_t smem = sizeof(double) * (n + 4 * n + 2 + 256);
     const dim3 grid((n + 31) / 32, nrhs * t.nfaces), block(32, 8);
     static PerDeviceOnce attr;
-    if (attr.first()) {
+    if (auto once = attr.first()) {
       cudaFuncSetAttribute(k_lat_faces<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(k_lat_faces<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     }

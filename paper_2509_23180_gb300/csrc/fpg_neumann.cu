@@ -296,7 +296,7 @@ cudaError_t pd_launch(const FastSolveTables& tb, LineLayout L, const double* in,
   const int Q = nm_pairs(nt);
   const size_t smem = nm_smem(nt, Q);
   static PerDeviceOnce attr;
-  if (attr.first()) {
+  if (auto once = attr.first()) {
     cudaFuncSetAttribute(k_rdft_fwd<MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_rdft_inv<MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
@@ -318,7 +318,7 @@ cudaError_t nm_launch(const FastSolveTables& tb, LineLayout L, const double* in,
   const int Q = nm_pairs(nt);
   const size_t smem = nm_smem(nt, Q);
   static PerDeviceOnce attr;
-  if (attr.first()) {
+  if (auto once = attr.first()) {
     cudaFuncSetAttribute(k_dct_fwd<MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dct_inv<MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }

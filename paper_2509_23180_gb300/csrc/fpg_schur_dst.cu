@@ -71,7 +71,7 @@ cudaError_t schur_dst_one(const void* z, int zprec, long long zstride, const Dst
                           const int* arms, int narms, double* corr, const int* active, int nrhs, cudaStream_t st) {
   using S = dl::LineShape<double, P>;
   static PerDeviceOnce attr;
-  if (attr.first()) {
+  if (auto once = attr.first()) {
     cudaFuncSetAttribute(k_schur_lines_dst<P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
     cudaFuncSetAttribute(k_schur_lines_dst<P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
   }
