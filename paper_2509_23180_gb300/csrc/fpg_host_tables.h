@@ -197,4 +197,48 @@ inline HostPlan plan_shape(int n) {
   return P;
 }
 
+// Interface table of the reduced Schur form: c(m) = delta^2/(n+1) sum_k g_k cos(pi k m/(n+1)),
+// m = 0..2n+1, with g_k = [T_k^{-1}]_{N,N} (N = n+1, the arm's sweep length) = last reciprocal pivot.
+inline void fill_ctab(int n, double delta, const std::vector<double>& rpivA, std::vector<double>& c) {
+  const int N = n + 1;
+  c.resize(2 * n + 2);
+  std::vector<double> g(n);
+  for (int k = 1; k <= n; ++k) g[k - 1] = rpivA[(size_t)(k - 1) * N + N - 1];
+  for (int m = 0; m < 2 * n + 2; ++m) {
+    // compensated (Kahan) FP64 summation: exact to ~1 ulp of the sum
+    double acc = 0.0, comp = 0.0;
+    for (int k = 1; k <= n; ++k) {
+      const double term = g[k - 1] * cos_pi_frac((long long)k * m, n + 1) - comp;
+      const double t = acc + term;
+      comp = (t - acc) - term;
+      acc = t;
+    }
+    c[m] = acc * delta * delta / (double)(n + 1);
+  }
+  c.resize(4 * n + 2);
+  for (int m = 0; m < 2 * n; ++m) c[2 * n + 2 + m] = c[m + 2];  // H(m) = T(m + 2)
+}
+
+// The same table for arms with Neumann sides (cell-centred, DCT-II basis
+// u_k(j) = a_k cos(k pi (j + 1/2)/n), a_0^2 = 1/n, a_k^2 = 2/n): with g_k the
+// interface entry of T_k^{-1} (the last reciprocal pivot when the far end is
+// row 0), G_ij = sum_k g_k u_k(i) u_k(j) = T(|i-j|) + T(i+j+1),
+// T(m) = delta^2/n (g_0/2 + sum_{k>=1} g_k cos(pi k m/n)); stored H(m) = -T(m+1).
+inline void fill_ctab_dct(int n, double delta, const std::vector<double>& rpivA, std::vector<double>& c) {
+  c.assign(4 * n + 2, 0.0);
+  std::vector<double> g(n);
+  for (int k = 0; k < n; ++k) g[k] = rpivA[(size_t)k * n + n - 1];
+  for (int m = 0; m < 2 * n + 2; ++m) {
+    double acc = 0.5 * g[0], comp = 0.0;
+    for (int k = 1; k < n; ++k) {
+      const double term = g[k] * cos_pi_frac((long long)k * m, n) - comp;
+      const double t = acc + term;
+      comp = (t - acc) - term;
+      acc = t;
+    }
+    c[m] = acc * delta * delta / (double)n;
+  }
+  for (int m = 0; m < 2 * n; ++m) c[2 * n + 2 + m] = -c[m + 1];
+}
+
 }  // namespace fpg

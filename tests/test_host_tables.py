@@ -12,7 +12,11 @@ pivots of every mode.  A small host program built from the library's own header
     (a relative bound, which the folding to the first octant gives), sinp[0] = 0;
   * a Thomas sweep with the printed reciprocal pivots solves tridiag(delta,
     d_k, delta) x = f as LAPACK's banded solver does (scipy), with
-    d_k = -4 delta + 2 delta cos(k pi/(n+1)) + kappa (Sec. 2.1, Eq. "trans_subeq").
+    d_k = -4 delta + 2 delta cos(k pi/(n+1)) + kappa (Sec. 2.1, Eq. "trans_subeq");
+  * the interface table of the reduced Schur form: G(i, j) = T(|i-j|) - H(i+j), built
+    from the arm's eigenvalues, equals every arm's R_ca A_a^{-1} R_ac on the centre's
+    facing line with A_a^{-1} a sparse LU of the oracle's arm block (a dropped or
+    shifted Hankel part is off by about a third).
 Rader's tables and the pivots are printed from the heap-free forms
 (`rader_tables`, `fill_pivots_into`) that the no-allocation fast solve calls,
 and checked identical to what the domain API's `build_plan` / `fill_pivots` give.
@@ -72,9 +76,25 @@ int main() {
     for (double v : r) std::printf(" %%a", v);
     std::printf("\n");
   }
+  // the reduced Schur term of a Dirichlet arm on the centre's facing line:
+  // G(i, j) = T(|i - j|) - H(i + j) from the interface table, as the domain stores it
+  struct Ct { int n; double kappa; };
+  const Ct cts[] = {%(ctabs)s};
+  int idx = 0;
+  for (const Ct& q : cts) {
+    const double delta = (double)(q.n + 1) * (double)(q.n + 1);
+    std::vector<double> pa, ct;
+    fill_pivots(q.n, q.n + 1, delta, q.kappa, pa);
+    fill_ctab(q.n, delta, pa, ct);
+    std::printf("CTAB %%d %%d %%a", idx++, q.n, q.kappa);
+    for (int i = 0; i < q.n; ++i)
+      for (int j = 0; j < q.n; ++j) std::printf(" %%a", ct[i > j ? i - j : j - i] - ct[2 * q.n + 2 + i + j]);
+    std::printf("\n");
+  }
   return 0;
 }
 """
+CTABS = [(4, 0.0), (8, -10.0), (13, -3.0), (16, 0.0)]
 
 @pytest.fixture(scope="module")
 def tables(tmp_path_factory):
@@ -84,7 +104,8 @@ def tables(tmp_path_factory):
     d = tmp_path_factory.mktemp("tables")
     pv = ", ".join(f"{{{n}, {ns}, {delta!r}, {kappa!r}}}" for n, ns, delta, kappa in PIVOTS)
     src = d / "tables.cu"
-    src.write_text(PROGRAM % {"sizes": ", ".join(map(str, SIZES)), "pivots": pv})
+    cts = ", ".join(f"{{{n}, {kappa!r}}}" for n, kappa in CTABS)
+    src.write_text(PROGRAM % {"sizes": ", ".join(map(str, SIZES)), "pivots": pv, "ctabs": cts})
     probe = d / "modes.cu"
     probe.write_text('#include <cstdio>\n#include "fpg_dst.cuh"\n'
                      'int main() { std::printf("%d %d %d\\n", fpg::DST_DENSE, fpg::DST_STOCKHAM, fpg::DST_RADER); }\n')
@@ -221,3 +242,35 @@ def test_thomas_pivots_solve_the_mode_systems(tables, n, ns, delta, kappa):
         ab[2, :-1] = delta
         want = solve_banded((1, 1), ab, f)
         assert np.allclose(x, want, rtol=1e-12, atol=1e-14 * np.abs(want).max()), (n, k)
+
+
+@pytest.mark.parametrize("case", range(len(CTABS)))
+def test_interface_table_is_the_arms_exact_schur_term(tables, case):
+    """The interface table behind the reduced Schur form (a2): for every arm of the
+    cross, R_ca A_a^{-1} R_ac restricted to the centre's facing line, with A_a^{-1}
+    a sparse LU of the oracle's arm block, equals G(i, j) = T(|i-j|) - H(i+j) built
+    on the host from the arm's eigenvalues (Eq. "Schur_subeq" read as P2)."""
+    from oracle.operator import assemble
+    from oracle.schur import BlockSystem
+    _, rec = tables
+    n_s, kappa_s, *vals = rec[("CTAB", case)]
+    n, kappa = int(n_s), float.fromhex(kappa_s)
+    assert (n, kappa) == CTABS[case]
+    G = _hex(vals).reshape(n, n)
+    bs = BlockSystem(assemble("cross", n, kappa), "cross", n)
+    # the centre's facing line of each arm, in the order of its line index
+    # (centre row-major, x fastest; W/E face columns 0 / n-1, S/N face rows 0 / n-1)
+    lines = {"W": [j * n for j in range(n)], "E": [j * n + n - 1 for j in range(n)],
+             "S": list(range(n)), "N": [(n - 1) * n + i for i in range(n)]}
+    scale = np.abs(G).max()
+    for arm, idx in lines.items():
+        M = np.empty((n, n))
+        for j, cj in enumerate(idx):
+            e = np.zeros(n * n)
+            e[cj] = 1.0
+            col = bs.R_c[arm] @ bs.block_solve(arm, bs.R_a[arm] @ e)
+            M[:, j] = col[idx]
+            rest = np.delete(col, idx)
+            assert np.abs(rest).max() <= 1e-13 * scale  # the term lives on the facing line only
+        err = np.abs(M - G).max() / scale
+        assert err <= 1e-14, (arm, err)  # measured about 5e-16
