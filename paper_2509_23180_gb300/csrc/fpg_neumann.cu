@@ -371,48 +371,6 @@ cudaError_t launch_fast_solve_rdft(const FastSolveTables& tb, LineLayout L, cons
   }
 }
 
-// Host tables of the DCT-II lines: W[m] = e^{-2 pi i m/n}, post[k] = e^{-i pi k/(2n)}
-// (interleaved re, im; n entries each).
-void dct_tables(int n, std::vector<double>& W, std::vector<double>& post) {
-  const double pi = 3.14159265358979323846;
-  W.resize(2 * n);
-  post.resize(2 * n);
-  for (int i = 0; i < n; ++i) {
-    const double a = 2.0 * pi * (double)i / n;
-    W[2 * i] = std::cos(a);
-    W[2 * i + 1] = -std::sin(a);
-    const double b = pi * (double)i / (2.0 * n);
-    post[2 * i] = std::cos(b);
-    post[2 * i + 1] = -std::sin(b);
-  }
-}
-
-// Reciprocal Thomas pivots r[k][s] and m = -delta r of the mode-k sweeps along
-// s of a block with Neumann ends along t:  tridiag(delta, -2 delta + mu_k + kappa,
-// delta), mu_k = -4 delta sin^2(k pi/(2n)), with `end_extra` added to the
-// diagonal of row 0 (end = 0) or of row ns-1 (end = 1) -- -delta for a
-// Dirichlet face half a cell beyond that row, 0 for a vertex-centred end.
-void dct_pivots(int nt, int ns, double delta, double kappa, double end_extra, int end, std::vector<double>& r,
-                std::vector<double>& m) {
-  const double pi = 3.14159265358979323846;
-  r.resize((size_t)nt * ns);
-  m.resize((size_t)nt * ns);
-  for (int k = 0; k < nt; ++k) {
-    const double sk = std::sin(pi * (double)k / (2.0 * nt));
-    const double d = -2.0 * delta - 4.0 * delta * sk * sk + kappa;
-    double* rk = r.data() + (size_t)k * ns;
-    double* mk = m.data() + (size_t)k * ns;
-    double rp = 0.0;
-    for (int s = 0; s < ns; ++s) {
-      double ds = d;
-      if ((end == 0 && s == 0) || (end == 1 && s == ns - 1)) ds += end_extra;
-      rp = s == 0 ? 1.0 / ds : 1.0 / (ds - delta * delta * rp);
-      rk[s] = rp;
-      mk[s] = -delta * rp;
-    }
-  }
-}
-
 // Pivots of the periodic lines: mode m has mu_m = -4 delta sin^2(pi m/n), plain
 // Dirichlet ends along s.
 void rdft_pivots(int nt, int ns, double delta, double kappa, std::vector<double>& r, std::vector<double>& m) {

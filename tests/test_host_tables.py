@@ -91,6 +91,19 @@ int main() {
       for (int j = 0; j < q.n; ++j) std::printf(" %%a", ct[i > j ? i - j : j - i] - ct[2 * q.n + 2 + i + j]);
     std::printf("\n");
   }
+  // the same for arms with Neumann sides (cell-centred, DCT-II lines, the far end a
+  // Dirichlet face half a cell beyond the arm's row 0): H(m) = -T(m + 1)
+  idx = 0;
+  for (const Ct& q : cts) {
+    const double delta = (double)q.n * (double)q.n;
+    std::vector<double> pa, ma, ct;
+    dct_pivots(q.n, q.n, delta, q.kappa, -delta, 0, pa, ma);
+    fill_ctab_dct(q.n, delta, pa, ct);
+    std::printf("CTABN %%d %%d %%a", idx++, q.n, q.kappa);
+    for (int i = 0; i < q.n; ++i)
+      for (int j = 0; j < q.n; ++j) std::printf(" %%a", ct[i > j ? i - j : j - i] - ct[2 * q.n + 2 + i + j]);
+    std::printf("\n");
+  }
   return 0;
 }
 """
@@ -244,20 +257,9 @@ def test_thomas_pivots_solve_the_mode_systems(tables, n, ns, delta, kappa):
         assert np.allclose(x, want, rtol=1e-12, atol=1e-14 * np.abs(want).max()), (n, k)
 
 
-@pytest.mark.parametrize("case", range(len(CTABS)))
-def test_interface_table_is_the_arms_exact_schur_term(tables, case):
-    """The interface table behind the reduced Schur form (a2): for every arm of the
-    cross, R_ca A_a^{-1} R_ac restricted to the centre's facing line, with A_a^{-1}
-    a sparse LU of the oracle's arm block, equals G(i, j) = T(|i-j|) - H(i+j) built
-    on the host from the arm's eigenvalues (Eq. "Schur_subeq" read as P2)."""
-    from oracle.operator import assemble
-    from oracle.schur import BlockSystem
-    _, rec = tables
-    n_s, kappa_s, *vals = rec[("CTAB", case)]
-    n, kappa = int(n_s), float.fromhex(kappa_s)
-    assert (n, kappa) == CTABS[case]
-    G = _hex(vals).reshape(n, n)
-    bs = BlockSystem(assemble("cross", n, kappa), "cross", n)
+def _schur_term_matches(G, bs, n):
+    """Every arm's R_ca A_a^{-1} R_ac, columns by sparse LU solves, against G on the
+    centre's facing line; zero off that line."""
     # the centre's facing line of each arm, in the order of its line index
     # (centre row-major, x fastest; W/E face columns 0 / n-1, S/N face rows 0 / n-1)
     lines = {"W": [j * n for j in range(n)], "E": [j * n + n - 1 for j in range(n)],
@@ -273,4 +275,34 @@ def test_interface_table_is_the_arms_exact_schur_term(tables, case):
             rest = np.delete(col, idx)
             assert np.abs(rest).max() <= 1e-13 * scale  # the term lives on the facing line only
         err = np.abs(M - G).max() / scale
-        assert err <= 1e-14, (arm, err)  # measured about 5e-16
+        assert err <= 1e-14, (arm, err)  # measured at most 5.4e-16 (Dirichlet and Neumann sides)
+
+
+@pytest.mark.parametrize("case", range(len(CTABS)))
+def test_interface_table_is_the_arms_exact_schur_term(tables, case):
+    """The interface table behind the reduced Schur form (a2): for every arm of the
+    cross, R_ca A_a^{-1} R_ac restricted to the centre's facing line, with A_a^{-1}
+    a sparse LU of the oracle's arm block, equals G(i, j) = T(|i-j|) - H(i+j) built
+    on the host from the arm's eigenvalues (Eq. "Schur_subeq" read as P2)."""
+    from oracle.operator import assemble
+    from oracle.schur import BlockSystem
+    _, rec = tables
+    n_s, kappa_s, *vals = rec[("CTAB", case)]
+    n, kappa = int(n_s), float.fromhex(kappa_s)
+    assert (n, kappa) == CTABS[case]
+    _schur_term_matches(_hex(vals).reshape(n, n), BlockSystem(assemble("cross", n, kappa), "cross", n), n)
+
+
+@pytest.mark.parametrize("case", range(len(CTABS)))
+def test_neumann_interface_table_is_the_arms_exact_schur_term(tables, case):
+    """The same for the cross whose arms have Neumann sides (P20, P21): the table
+    built from the DCT-II eigenvalues and the arm's own pivots equals R_ca A_a^{-1}
+    R_ac of the oracle's cell-centred Neumann-sided cross."""
+    from oracle import neumann_cross as NC
+    from oracle.schur import BlockSystem
+    _, rec = tables
+    n_s, kappa_s, *vals = rec[("CTABN", case)]
+    n, kappa = int(n_s), float.fromhex(kappa_s)
+    assert (n, kappa) == CTABS[case]
+    bs = BlockSystem(NC.assemble(n, kappa), "cross", n, blocks=NC.block_ranges(n))
+    _schur_term_matches(_hex(vals).reshape(n, n), bs, n)
