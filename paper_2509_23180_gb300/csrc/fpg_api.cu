@@ -20,8 +20,6 @@ cudaError_t launch_fast_solve(int prec, int out_prec, const FastSolveTables& tb,
                               BatchDesc ib, void* out, BatchDesc ob, int nblk, void* scratch, const int* active,
                               int nper_active, cudaStream_t st, int* launches, cudaEvent_t* ev = nullptr);
 bool schur_dst_supported(int n);
-bool fast_solve_cluster_tables(int n, double delta, double kappa, std::vector<float>& sigma,
-                               std::vector<float>& wseed);
 cudaError_t launch_schur_dst(const void* z, int zprec, long long zstride, int n, const DstPlan& pl, const double* gsc,
                              const int* arms, int narms, double* corr, const int* active, int nrhs, cudaStream_t st);
 cudaError_t launch_schur_gmat(const void* z, int zprec, long long zstride, int n, const double* G, const int* arms_dev,

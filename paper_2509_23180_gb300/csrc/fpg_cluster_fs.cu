@@ -43,8 +43,6 @@
 namespace fpg {
 namespace {
 
-constexpr int kClusterRows = 32;  // R: lines per CTA
-
 template <int P>
 struct ClusterShape {
   using S = dl::LineShape<float, P>;
@@ -299,30 +297,5 @@ cudaError_t launch_fast_solve_cluster(int out_prec, const FastSolveTables& tb, L
                  : launch_cluster_p<513, float>(tb, in, ib, (float*)out, ob, nblk, active, nper_active, st);
 }
 
-// Host tables of the cluster kernel for an n x n Dirichlet block (p = n + 1,
-// 1/h^2 = delta), kappa: sigma[k-1] = 4 sin^2(k pi / 2p) - kappa / delta and,
-// per CTA r of the cluster, the scaled pivot w at its first row s = r R,
-// wseed[r][k-1], from the FP64 recurrence w_0 = 1 + sigma,
-// w_s = sigma + w_{s-1} / (1 + w_{s-1}).  Returns false for lengths the kernel
-// does not take.
-bool fast_solve_cluster_tables(int n, double delta, double kappa, std::vector<float>& sigma,
-                               std::vector<float>& wseed) {
-  const int p = n + 1;
-  if (p != 65 && p != 513) return false;
-  const int R = kClusterRows, C = n / R;
-  sigma.assign(n, 0.0f);
-  wseed.assign((size_t)C * n, 0.0f);
-  for (int k = 1; k <= n; ++k) {
-    const double sh = cos_pi_frac(p - k, 2 * p);  // sin(k pi / 2p)
-    const double sg = 4.0 * sh * sh - kappa / delta;
-    sigma[k - 1] = (float)sg;
-    double w = 1.0 + sg;
-    for (int s = 0; s < n; ++s) {
-      if (s % R == 0) wseed[(size_t)(s / R) * n + (k - 1)] = (float)w;
-      w = sg + w / (1.0 + w);
-    }
-  }
-  return true;
-}
 
 }  // namespace fpg

@@ -104,6 +104,28 @@ int main() {
       for (int j = 0; j < q.n; ++j) std::printf(" %%a", ct[i > j ? i - j : j - i] - ct[2 * q.n + 2 + i + j]);
     std::printf("\n");
   }
+  // the one-pass FP32 cluster kernel's tables: sigma_k and the scaled pivot w at the first
+  // row of every CTA, with the reciprocal Thomas pivots of the same block beside them
+  idx = 0;
+  for (int n : {64, 512}) {
+    for (double kappa : {0.0, -10.0}) {
+      const double delta = (double)(n + 1) * (double)(n + 1);
+      std::vector<float> sigma, wseed;
+      std::vector<double> r;
+      const bool ok = fast_solve_cluster_tables(n, delta, kappa, sigma, wseed);
+      fill_pivots(n, n, delta, kappa, r);
+      std::printf("CLUS %%d %%d %%a %%d %%d", idx++, n, kappa, (int)ok, kClusterRows);
+      for (float v : sigma) std::printf(" %%a", (double)v);
+      for (float v : wseed) std::printf(" %%a", (double)v);
+      for (double v : r) std::printf(" %%a", v);
+      std::printf("\n");
+    }
+  }
+  {
+    std::vector<float> sigma, wseed;
+    std::printf("CLUSNO 0 %%d %%d\n", (int)fast_solve_cluster_tables(256, 257.0 * 257.0, 0.0, sigma, wseed),
+                (int)fast_solve_cluster_tables(1024, 1025.0 * 1025.0, 0.0, sigma, wseed));
+  }
   return 0;
 }
 """
@@ -306,3 +328,35 @@ def test_neumann_interface_table_is_the_arms_exact_schur_term(tables, case):
     assert (n, kappa) == CTABS[case]
     bs = BlockSystem(NC.assemble(n, kappa), "cross", n, blocks=NC.block_ranges(n))
     _schur_term_matches(_hex(vals).reshape(n, n), bs, n)
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_cluster_tables_are_the_scaled_thomas_pivots(tables, case):
+    """The one-pass FP32 fast solve rewrites the LU recurrence of tridiag(delta, d_k,
+    delta), u_s = d_k - delta^2 / u_{s-1}, for w_s = -u_s / delta - 1 (a sum of positive
+    terms, accurate in the lowest modes where u_s is close to -2 delta).  Its host tables
+    must therefore be sigma_k = 4 sin^2(k pi / 2p) - kappa / delta (40-digit values) and,
+    at the first row s = r R of every CTA r, w_s = -1 / (delta r_s) - 1 from the
+    reciprocal pivots r_s that the LAPACK test above pins -- each rounded once to
+    binary32, so within an ulp of binary32."""
+    _, rec = tables
+    n_s, kappa_s, ok, R, *vals = rec[("CLUS", case)]
+    n, kappa, R = int(n_s), float.fromhex(kappa_s), int(R)
+    assert int(ok) == 1 and n % R == 0
+    C, p = n // R, n + 1
+    delta = float(p * p)
+    v = _hex(vals)
+    sigma, wseed, r = v[:n], v[n:n + C * n].reshape(C, n), v[n + C * n:].reshape(n, n)
+    assert len(v) == n + C * n + n * n
+    mpmath.mp.dps = 40
+    s_ref = np.array([float(4 * mpmath.sin(k * mpmath.pi / (2 * p)) ** 2 - mpmath.mpf(kappa) / delta)
+                      for k in range(1, n + 1)])
+    f32 = np.float32
+    assert np.all(np.abs(sigma - s_ref.astype(f32)) <= np.spacing(s_ref.astype(f32))), "sigma"
+    w_ref = -1.0 / (delta * r[:, ::R].T) - 1.0  # [cta][k]
+    assert np.all(np.abs(wseed - w_ref.astype(f32)) <= np.spacing(w_ref.astype(f32))), "w seeds"
+
+
+def test_cluster_tables_only_for_the_kernels_lengths(tables):
+    _, rec = tables
+    assert rec[("CLUSNO", 0)] == ["0", "0"]
