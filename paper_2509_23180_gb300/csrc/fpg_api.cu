@@ -86,7 +86,6 @@ cudaError_t launch_dst_pass(bool forward, const FastSolveTables& tb, LineLayout 
                             double* scratch, double* out, BatchDesc ob, int nblk, cudaStream_t st);
 cudaError_t launch_thomas_any(int prec, void* scratch, int n, int ns, const void* rpiv, const void* mneg, int nblk,
                               const int* active, int nper_active, cudaStream_t st, int wpb);
-void rdft_pivots(int nt, int ns, double delta, double kappa, std::vector<double>& r, std::vector<double>& m);
 int arnoldi_reg_ept(long long len, int csz, int ntcap);
 int arnoldi_reg_threads(long long len, int csz, int ept);
 cudaError_t launch_arnoldi_reg(int csz, int ntcap, const double* V, long long vstride, const double* w,

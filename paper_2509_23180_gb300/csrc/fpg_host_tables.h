@@ -239,6 +239,26 @@ inline void dct_pivots(int nt, int ns, double delta, double kappa, double end_ex
   }
 }
 
+// Pivots of the periodic lines: mode m has mu_m = -4 delta sin^2(pi m/n), plain
+// Dirichlet ends along s.
+inline void rdft_pivots(int nt, int ns, double delta, double kappa, std::vector<double>& r, std::vector<double>& m) {
+  const double pi = 3.14159265358979323846;
+  r.resize((size_t)nt * ns);
+  m.resize((size_t)nt * ns);
+  for (int k = 0; k < nt; ++k) {
+    const double sk = std::sin(pi * (double)k / nt);
+    const double d = -2.0 * delta - 4.0 * delta * sk * sk + kappa;
+    double* rk = r.data() + (size_t)k * ns;
+    double* mk = m.data() + (size_t)k * ns;
+    double rp = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      rp = s == 0 ? 1.0 / d : 1.0 / (d - delta * delta * rp);
+      rk[s] = rp;
+      mk[s] = -delta * rp;
+    }
+  }
+}
+
 // Interface table of the reduced Schur form: c(m) = delta^2/(n+1) sum_k g_k cos(pi k m/(n+1)),
 // m = 0..2n+1, with g_k = [T_k^{-1}]_{N,N} (N = n+1, the arm's sweep length) = last reciprocal pivot.
 inline void fill_ctab(int n, double delta, const std::vector<double>& rpivA, std::vector<double>& c) {

@@ -371,26 +371,6 @@ cudaError_t launch_fast_solve_rdft(const FastSolveTables& tb, LineLayout L, cons
   }
 }
 
-// Pivots of the periodic lines: mode m has mu_m = -4 delta sin^2(pi m/n), plain
-// Dirichlet ends along s.
-void rdft_pivots(int nt, int ns, double delta, double kappa, std::vector<double>& r, std::vector<double>& m) {
-  const double pi = 3.14159265358979323846;
-  r.resize((size_t)nt * ns);
-  m.resize((size_t)nt * ns);
-  for (int k = 0; k < nt; ++k) {
-    const double sk = std::sin(pi * (double)k / nt);
-    const double d = -2.0 * delta - 4.0 * delta * sk * sk + kappa;
-    double* rk = r.data() + (size_t)k * ns;
-    double* mk = m.data() + (size_t)k * ns;
-    double rp = 0.0;
-    for (int s = 0; s < ns; ++s) {
-      rp = s == 0 ? 1.0 / d : 1.0 / (d - delta * delta * rp);
-      rk[s] = rp;
-      mk[s] = -delta * rp;
-    }
-  }
-}
-
 cudaError_t launch_fast_solve_dct(const FastSolveTables& tb, LineLayout L, const double* in, BatchDesc ib,
                                   double* out, BatchDesc ob, int nblk, double* scratch, const int* active,
                                   int nper_active, cudaStream_t st) {

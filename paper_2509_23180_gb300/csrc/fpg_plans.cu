@@ -24,7 +24,6 @@ cudaError_t launch_thomas_any(int prec, void* scratch, int n, int ns, const void
                               const int* active, int nper_active, cudaStream_t st, int wpb);
 bool dct_plan_shape(int n, DstPlan* pl);
 bool rdft_plan_shape(int n, DstPlan* pl);
-void rdft_pivots(int nt, int ns, double delta, double kappa, std::vector<double>& r, std::vector<double>& m);
 
 }  // namespace fpg
 

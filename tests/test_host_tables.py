@@ -13,6 +13,9 @@ pivots of every mode.  A small host program built from the library's own header
   * a Thomas sweep with the printed reciprocal pivots solves tridiag(delta,
     d_k, delta) x = f as LAPACK's banded solver does (scipy), with
     d_k = -4 delta + 2 delta cos(k pi/(n+1)) + kappa (Sec. 2.1, Eq. "trans_subeq");
+  * the Neumann (DCT-II) and periodic (real DFT) lines' pivots solve their mode
+    systems as LAPACK's banded solver does, with the eigenvalues mu_k taken from
+    the oracle's pinned line operators and a Neumann-sided arm's end-row term;
   * the interface table of the reduced Schur form: G(i, j) = T(|i-j|) - H(i+j), built
     from the arm's eigenvalues, equals every arm's R_ca A_a^{-1} R_ac on the centre's
     facing line with A_a^{-1} a sparse LU of the oracle's arm block (a dropped or
@@ -104,6 +107,28 @@ int main() {
       for (int j = 0; j < q.n; ++j) std::printf(" %%a", ct[i > j ? i - j : j - i] - ct[2 * q.n + 2 + i + j]);
     std::printf("\n");
   }
+  // Thomas pivots of the Neumann (DCT-II) and periodic (real DFT) lines
+  struct Dp { int nt, ns; double delta, kappa, extra; int end; };
+  const Dp dps[] = {%(dpivots)s};
+  idx = 0;
+  for (const Dp& q : dps) {
+    std::vector<double> r, m;
+    dct_pivots(q.nt, q.ns, q.delta, q.kappa, q.extra, q.end, r, m);
+    std::printf("DPIV %%d", idx++);
+    for (double v : r) std::printf(" %%a", v);
+    for (double v : m) std::printf(" %%a", v);
+    std::printf("\n");
+  }
+  const Pv rps[] = {%(rpivots)s};
+  idx = 0;
+  for (const Pv& q : rps) {
+    std::vector<double> r, m;
+    rdft_pivots(q.n, q.ns, q.delta, q.kappa, r, m);
+    std::printf("RPIV %%d", idx++);
+    for (double v : r) std::printf(" %%a", v);
+    for (double v : m) std::printf(" %%a", v);
+    std::printf("\n");
+  }
   // the one-pass FP32 cluster kernel's tables: sigma_k and the scaled pivot w at the first
   // row of every CTA, with the reciprocal Thomas pivots of the same block beside them
   idx = 0;
@@ -130,6 +155,11 @@ int main() {
 }
 """
 CTABS = [(4, 0.0), (8, -10.0), (13, -3.0), (16, 0.0)]
+# (nt, ns, delta, kappa, extra on an end row, which end): the Neumann rectangle plan
+# (no extra) and the Neumann-sided arms (-delta at row 0 or at row ns - 1)
+DPIVOTS = [(8, 5, 81.0, 0.0, 0.0, 0), (16, 16, 256.0, -10.0, -256.0, 0), (12, 7, 144.0, -3.0, -144.0, 1)]
+# (nt, ns, delta, kappa): periodic lines
+RPIVOTS = [(8, 6, 81.0, 0.0), (10, 10, 100.0, -10.0)]
 
 @pytest.fixture(scope="module")
 def tables(tmp_path_factory):
@@ -140,7 +170,10 @@ def tables(tmp_path_factory):
     pv = ", ".join(f"{{{n}, {ns}, {delta!r}, {kappa!r}}}" for n, ns, delta, kappa in PIVOTS)
     src = d / "tables.cu"
     cts = ", ".join(f"{{{n}, {kappa!r}}}" for n, kappa in CTABS)
-    src.write_text(PROGRAM % {"sizes": ", ".join(map(str, SIZES)), "pivots": pv, "ctabs": cts})
+    dps = ", ".join(f"{{{a}, {b}, {c!r}, {d!r}, {e!r}, {g}}}" for a, b, c, d, e, g in DPIVOTS)
+    rps = ", ".join(f"{{{a}, {b}, {c!r}, {d!r}}}" for a, b, c, d in RPIVOTS)
+    src.write_text(PROGRAM % {"sizes": ", ".join(map(str, SIZES)), "pivots": pv, "ctabs": cts,
+                              "dpivots": dps, "rpivots": rps})
     probe = d / "modes.cu"
     probe.write_text('#include <cstdio>\n#include "fpg_dst.cuh"\n'
                      'int main() { std::printf("%d %d %d\\n", fpg::DST_DENSE, fpg::DST_STOCKHAM, fpg::DST_RADER); }\n')
@@ -277,6 +310,64 @@ def test_thomas_pivots_solve_the_mode_systems(tables, n, ns, delta, kappa):
         ab[2, :-1] = delta
         want = solve_banded((1, 1), ab, f)
         assert np.allclose(x, want, rtol=1e-12, atol=1e-14 * np.abs(want).max()), (n, k)
+
+
+def _sweep_matches_banded(r, mneg, delta, diag, rng, label):
+    """The library's Thomas sweep (y_s = r_s (f_s - delta y_{s-1}), x_s = y_s + m_s x_{s+1},
+    m_s = -delta r_s) with the printed pivots solves tridiag(delta, diag, delta) x = f as
+    LAPACK's banded solver does."""
+    from scipy.linalg import solve_banded
+    ns = len(r)
+    assert np.array_equal(mneg, -delta * r), label
+    f = rng.standard_normal(ns)
+    y = np.empty(ns)
+    y[0] = r[0] * f[0]
+    for s in range(1, ns):
+        y[s] = r[s] * (f[s] - delta * y[s - 1])
+    x = np.empty(ns)
+    x[-1] = y[-1]
+    for s in range(ns - 2, -1, -1):
+        x[s] = y[s] + mneg[s] * x[s + 1]
+    ab = np.zeros((3, ns))
+    ab[0, 1:] = delta
+    ab[1, :] = diag
+    ab[2, :-1] = delta
+    want = solve_banded((1, 1), ab, f)
+    assert np.allclose(x, want, rtol=1e-12, atol=1e-14 * np.abs(want).max()), label
+
+
+@pytest.mark.parametrize("case", range(len(DPIVOTS)))
+def test_neumann_pivots_solve_the_mode_systems(tables, case):
+    """Mode k of a line whose transform is the DCT-II has the eigenvalue mu_k of the
+    cell-centred Neumann line operator (taken from the oracle, whose eigenpairs are
+    pinned against that matrix): its sweep solves tridiag(delta, -2 delta + mu_k +
+    kappa, delta), with the end row's extra term of a Neumann-sided arm."""
+    from oracle.neumann import neumann_eigenvalues
+    _, rec = tables
+    nt, ns, delta, kappa, extra, end = DPIVOTS[case]
+    v = _hex(rec[("DPIV", case)])
+    r, m = v[:nt * ns].reshape(nt, ns), v[nt * ns:].reshape(nt, ns)
+    mu = neumann_eigenvalues(nt, delta)
+    rng = np.random.default_rng(case)
+    for k in range(nt):
+        diag = np.full(ns, -2 * delta + mu[k] + kappa)
+        diag[0 if end == 0 else ns - 1] += extra
+        _sweep_matches_banded(r[k], m[k], delta, diag, rng, (case, k))
+
+
+@pytest.mark.parametrize("case", range(len(RPIVOTS)))
+def test_periodic_pivots_solve_the_mode_systems(tables, case):
+    """The same for periodic lines, with the circulant's eigenvalues mu_k from the
+    oracle (mode k of the real-DFT coordinates, Re X_k or Im X_k, shares mu_k)."""
+    from oracle.periodic import periodic_eigenvalues
+    _, rec = tables
+    nt, ns, delta, kappa = RPIVOTS[case]
+    v = _hex(rec[("RPIV", case)])
+    r, m = v[:nt * ns].reshape(nt, ns), v[nt * ns:].reshape(nt, ns)
+    mu = periodic_eigenvalues(nt, delta)
+    rng = np.random.default_rng(100 + case)
+    for k in range(nt):
+        _sweep_matches_banded(r[k], m[k], delta, np.full(ns, -2 * delta + mu[k] + kappa), rng, (case, k))
 
 
 def _schur_term_matches(G, bs, n):
