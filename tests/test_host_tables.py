@@ -119,6 +119,14 @@ int main() {
     for (double v : m) std::printf(" %%a", v);
     std::printf("\n");
   }
+  for (int nt : {8, 12, 256}) {
+    std::vector<double> W, post;
+    dct_tables(nt, W, post);
+    std::printf("DCTW %%d", nt);
+    for (double v : W) std::printf(" %%a", v);
+    for (double v : post) std::printf(" %%a", v);
+    std::printf("\n");
+  }
   const Pv rps[] = {%(rpivots)s};
   idx = 0;
   for (const Pv& q : rps) {
@@ -451,3 +459,25 @@ def test_cluster_tables_are_the_scaled_thomas_pivots(tables, case):
 def test_cluster_tables_only_for_the_kernels_lengths(tables):
     _, rec = tables
     assert rec[("CLUSNO", 0)] == ["0", "0"]
+
+
+@pytest.mark.parametrize("nt", [8, 12, 256])
+def test_dct_twiddles(tables, nt):
+    """The DCT-II lines' tables (Makhoul's reordering on a complex FFT of length n):
+    W[m] = e^{-2 pi i m/n} and post[k] = e^{-i pi k/(2n)}, interleaved (re, im), against
+    40-digit values.  The angles are formed in floating point without folding, so each
+    entry may carry the rounding of its angle a (up to |a| 2^-53, passed on with a
+    derivative of at most 1) besides the function's own rounding: the bound is
+    (1 + |a|) 2^-53 per entry (measured up to 4.4e-16 at n = 12, angles near 2 pi)."""
+    _, rec = tables
+    v = _hex(rec[("DCTW", nt)])
+    W, post = v[:2 * nt], v[2 * nt:]
+    assert len(post) == 2 * nt
+    mpmath.mp.dps = 40
+    u = 2.0 ** -53
+    for m in range(nt):
+        a = -2 * mpmath.pi * m / nt
+        b = -mpmath.pi * m / (2 * nt)
+        for got, want, ang in ((W[2 * m], mpmath.cos(a), a), (W[2 * m + 1], mpmath.sin(a), a),
+                               (post[2 * m], mpmath.cos(b), b), (post[2 * m + 1], mpmath.sin(b), b)):
+            assert abs(float(got - want)) <= (1 + abs(float(ang))) * u, (m, float(ang))
