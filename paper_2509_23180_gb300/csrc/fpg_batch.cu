@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "fpg_internal.cuh"
+#include "fpg_pool.h"
 
 namespace fpg {
 
@@ -79,8 +80,6 @@ bool same_key(const fpg_domain_desc& a, const fpg_domain_desc& b) {
          a.schur_mode == b.schur_mode && a.boundary == b.boundary && a.chain == b.chain && a.lattice == b.lattice;
 }
 
-size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
-
 }  // namespace
 }  // namespace fpg
 
@@ -89,7 +88,7 @@ struct fpg_batch {
   std::vector<fpg::KeyQueue*> keys;
   char* pool = nullptr;
   size_t pool_bytes = 0;
-  std::vector<std::pair<size_t, size_t>> free_list;  // (offset, bytes), sorted, coalesced
+  fpg::PoolFreeList free_list;  // (offset, bytes) ranges, sorted, coalesced
   std::vector<fpg::Resident*> doms;
   std::unordered_map<int64_t, fpg::TicketState> tickets;
   int64_t next_ticket = 1;
@@ -100,36 +99,6 @@ struct fpg_batch {
 namespace fpg {
 namespace {
 
-bool pool_take(fpg_batch* b, size_t bytes, size_t* off) {
-  bytes = align256(bytes);
-  for (size_t i = 0; i < b->free_list.size(); ++i) {
-    auto& fr = b->free_list[i];
-    if (fr.second < bytes) continue;
-    *off = fr.first;
-    fr.first += bytes;
-    fr.second -= bytes;
-    if (fr.second == 0) b->free_list.erase(b->free_list.begin() + i);
-    return true;
-  }
-  return false;
-}
-
-void pool_give(fpg_batch* b, size_t off, size_t bytes) {
-  bytes = align256(bytes);
-  auto& fl = b->free_list;
-  auto it = std::lower_bound(fl.begin(), fl.end(), std::make_pair(off, (size_t)0));
-  it = fl.insert(it, {off, bytes});
-  size_t i = it - fl.begin();
-  if (i + 1 < fl.size() && fl[i].first + fl[i].second == fl[i + 1].first) {
-    fl[i].second += fl[i + 1].second;
-    fl.erase(fl.begin() + i + 1);
-  }
-  if (i > 0 && fl[i - 1].first + fl[i - 1].second == fl[i].first) {
-    fl[i - 1].second += fl[i].second;
-    fl.erase(fl.begin() + i);
-  }
-}
-
 void drop_resident(fpg_batch* b, size_t idx) {
   Resident* R = b->doms[idx];
   R->kq->residents--;
@@ -137,7 +106,7 @@ void drop_resident(fpg_batch* b, size_t idx) {
   fpg_destroy_domain(R->d);
   cudaEventDestroy(R->copied);
   cudaStreamDestroy(R->st);
-  pool_give(b, R->off, R->bytes);
+  b->free_list.give(R->off, R->bytes);
   delete R;
   b->doms.erase(b->doms.begin() + idx);
 }
@@ -167,12 +136,12 @@ fpg_status make_resident(fpg_batch* b, KeyQueue* kq, bool may_evict, Resident** 
   if (need > b->pool_bytes) return FPG_EBUDGET;
   size_t off = 0;
   for (;;) {
-    if ((int)b->doms.size() < b->max_domains && pool_take(b, need, &off)) break;
+    if ((int)b->doms.size() < b->max_domains && b->free_list.take(need, &off)) break;
     if (!may_evict || !evict_one(b)) return FPG_EBUDGET;
   }
   Resident* R = new (std::nothrow) Resident();
   if (!R) {
-    pool_give(b, off, need);
+    b->free_list.give(off, need);
     return FPG_ENOMEM;
   }
   R->key = key;
@@ -189,7 +158,7 @@ fpg_status make_resident(fpg_batch* b, KeyQueue* kq, bool may_evict, Resident** 
     if (e != cudaSuccess) record_cuda_error(e, "fpg_batch_admit");
     if (R->copied) cudaEventDestroy(R->copied);
     if (R->st) cudaStreamDestroy(R->st);
-    pool_give(b, off, need);
+    b->free_list.give(off, need);
     delete R;
     return s;
   }
@@ -248,7 +217,7 @@ fpg_status fpg_batch_create(const fpg_batch_desc* desc, void* pool, size_t pool_
   }
   b->pool = static_cast<char*>(pool) + skip;
   b->pool_bytes = (pool_bytes - skip) & ~(size_t)255;
-  b->free_list.push_back({0, b->pool_bytes});
+  b->free_list.reset(b->pool_bytes);
   *out = b;
   return FPG_OK;
 }
